@@ -1,0 +1,162 @@
+"""CPU oracle for the MesonGS++ cost table and budget solve.
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, by __graft_entry__.smoke() and by
+bench.py's CPU-baseline leg.  The product path (the package and its CUDA
+library) never imports it, and it imports nothing from the product.
+
+  oracle.c   C reference of the quantiser, entropy bound, Morton order, ranks
+             (compiled with gcc -O2 -ffp-contract=off, no fast-math)
+  mckp.py    exact references of the 0-1 ILP (brute force, DP) and the tau rule
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+OK, ERR_ARG, ERR_NONFINITE, ERR_RANGE, ERR_NOMEM = 0, -1, -2, -3, -4
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into oracle/_build/liboracle.so (plain gcc, strict FP)."""
+    src = os.path.join(_HERE, "oracle.c")
+    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(src):
+        return _SO
+    os.makedirs(_BUILD, exist_ok=True)
+    tmp = _SO + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
+           "-fexcess-precision=standard", "-Wall", "-o", tmp, src, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+def load(path: str):
+    """Load an oracle shared library from `path` and declare its signatures."""
+    L = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    i64, i32 = ctypes.c_int64, ctypes.c_int32
+    L.oracle_rank.argtypes = [P, i64, P]
+    L.oracle_morton.argtypes = [P, i64, i32, P, P]
+    L.oracle_kept.argtypes = [P, P, i64, i64, P]
+    L.oracle_kept.restype = i64
+    L.oracle_group_cost.argtypes = [P, i64, P, i32, P, P, P, P, P, P, P]
+    L.oracle_cost_table.argtypes = [P, P, i64, i32, P, i32, P, i32, i32, P, P, P, P, P, P, P]
+    L.oracle_quantize.argtypes = [P, P, i64, i32, i64, i32, P, P, P]
+    for f in (L.oracle_rank, L.oracle_morton, L.oracle_group_cost, L.oracle_cost_table,
+              L.oracle_quantize):
+        f.restype = ctypes.c_int
+    return L
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = load(build())
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class OracleError(RuntimeError):
+    def __init__(self, code: int):
+        super().__init__(f"oracle status {code}")
+        self.code = code
+
+
+def _check(rc: int):
+    if rc != OK:
+        raise OracleError(rc)
+
+
+def rank(importance: np.ndarray, L=None) -> np.ndarray:
+    imp = np.ascontiguousarray(importance, dtype=np.float32)
+    out = np.empty(imp.shape[0], dtype=np.int32)
+    _check((L or lib()).oracle_rank(_p(imp), imp.shape[0], _p(out)))
+    return out
+
+
+def morton(attrs: np.ndarray, L=None) -> tuple[np.ndarray, np.ndarray]:
+    """Return (codes[i] uint64, order[p] int64) for attrs [n, C] (channels 0..2 = position)."""
+    a = np.ascontiguousarray(attrs, dtype=np.float32)
+    n, C = a.shape
+    codes = np.empty(n, dtype=np.uint64)
+    order = np.empty(n, dtype=np.int64)
+    _check((L or lib()).oracle_morton(_p(a), n, C, _p(codes), _p(order)))
+    return codes, order
+
+
+def kept(rank_: np.ndarray, order: np.ndarray, keep: int) -> np.ndarray:
+    r = np.ascontiguousarray(rank_, dtype=np.int32)
+    o = np.ascontiguousarray(order, dtype=np.int64)
+    out = np.empty(max(int(keep), 1), dtype=np.int64)
+    k = lib().oracle_kept(_p(r), _p(o), o.shape[0], int(keep), _p(out))
+    return out[:k]
+
+
+def group_cost(vals: np.ndarray, bits, want_codes: bool = False, L=None) -> dict:
+    v = np.ascontiguousarray(vals, dtype=np.float32)
+    b = np.ascontiguousarray(bits, dtype=np.int32)
+    nb = b.shape[0]
+    out = dict(sse=np.empty(nb), l1=np.empty(nb), linf=np.empty(nb, dtype=np.float32),
+               hbits=np.empty(nb), vmin=np.empty(1, dtype=np.float32),
+               vmax=np.empty(1, dtype=np.float32))
+    codes = np.empty((nb, v.shape[0]), dtype=np.uint16) if want_codes else None
+    _check((L or lib()).oracle_group_cost(_p(v), v.shape[0], _p(b), nb, _p(out["sse"]), _p(out["l1"]),
+                                   _p(out["linf"]), _p(out["hbits"]), _p(out["vmin"]),
+                                   _p(out["vmax"]), _p(codes) if codes is not None else None))
+    out["vmin"] = float(out["vmin"][0])
+    out["vmax"] = float(out["vmax"][0])
+    if codes is not None:
+        out["codes"] = codes
+    return out
+
+
+def n_groups(keep: int, G: int) -> int:
+    return (int(keep) + G - 1) // G
+
+
+def cost_table(attrs, importance, keep, bits, G) -> dict:
+    """Whole table, items ordered [r][c][g]; per-option arrays shaped [n_items, n_b]."""
+    a = np.ascontiguousarray(attrs, dtype=np.float32)
+    imp = np.ascontiguousarray(importance, dtype=np.float32)
+    k = np.ascontiguousarray(keep, dtype=np.int64)
+    b = np.ascontiguousarray(bits, dtype=np.int32)
+    n, C = a.shape
+    n_items = sum(C * n_groups(x, G) for x in k)
+    nb = b.shape[0]
+    out = dict(sse=np.empty((n_items, nb)), l1=np.empty((n_items, nb)),
+               linf=np.empty((n_items, nb), dtype=np.float32), hbits=np.empty((n_items, nb)),
+               cnt=np.empty(n_items, dtype=np.int32), vmin=np.empty(n_items, dtype=np.float32),
+               vmax=np.empty(n_items, dtype=np.float32))
+    _check(lib().oracle_cost_table(_p(a), _p(imp), n, C, _p(k), k.shape[0], _p(b), nb, int(G),
+                                   _p(out["sse"]), _p(out["l1"]), _p(out["linf"]),
+                                   _p(out["hbits"]), _p(out["cnt"]), _p(out["vmin"]),
+                                   _p(out["vmax"])))
+    return out
+
+
+def quantize(attrs, importance, keep: int, G: int, q_bits: np.ndarray):
+    """Codes [C, keep] uint16 and min/max [C, n_groups, 2] for one chosen configuration."""
+    a = np.ascontiguousarray(attrs, dtype=np.float32)
+    imp = np.ascontiguousarray(importance, dtype=np.float32)
+    n, C = a.shape
+    ng = n_groups(keep, G)
+    qb = np.ascontiguousarray(q_bits, dtype=np.uint8).reshape(C, ng)
+    codes = np.empty((C, max(int(keep), 1)), dtype=np.uint16)
+    mm = np.empty((C, max(ng, 1), 2), dtype=np.float32)
+    _check(lib().oracle_quantize(_p(a), _p(imp), n, C, int(keep), int(G), _p(qb), _p(codes),
+                                 _p(mm)))
+    return codes[:, :keep], mm[:, :ng]

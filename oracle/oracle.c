@@ -1,0 +1,383 @@
+/*
+ * oracle.c -- plain, slow, obviously-correct CPU reference for the candidate
+ * cost table of MesonGS++'s size-aware configuration search.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the CPU
+ * baseline leg of bench.py may load this library.  It shares no code with the
+ * CUDA path (no headers, helpers or tables in common).
+ *
+ * Arithmetic rules: every per-element quantity is computed in IEEE FP32,
+ * one operation per C statement, compiled with -ffp-contract=off and no
+ * fast-math, so that each "fl(.)" below is exactly one rounding.  Every
+ * accumulation (squared error, absolute error, entropy) is FP64.
+ *
+ * What each function follows (section names of the paper):
+ *   oracle_rank          Sec. III-A "Gaussians Pruning": keep the tau fraction
+ *                        with the largest joint importance I_g.
+ *   oracle_morton        Sec. III-G "Entropy Encoding", last paragraph: Morton
+ *                        order of the coordinates builds the quantisation groups.
+ *   oracle_kept          Sec. III-A + III-G: the kept set, in Morton order.
+ *   oracle_group_cost    Sec. III-D "Group-wise Attribute Quantization" (the
+ *                        quantiser c_q, S_c, Z_c), Sec. III-F "Acceleration"
+ *                        (quality loss Omega with 1-, 2- and inf-norms) and
+ *                        Sec. III-F "Size Estimator" (entropy lower bound
+ *                        tau*N * (-sum p log2 p)).
+ *   oracle_cost_table    the loops of Sec. III-F: every reserve ratio, every
+ *                        (channel, block), every bit-width.
+ *   oracle_quantize      Sec. III-D quantiser for one chosen configuration.
+ *
+ * Readings where the paper is silent (each is listed in the design doc):
+ *   - S_c = (max - min) / 2^b exactly as printed (not 2^b - 1); the element
+ *     equal to max lands at x ~ 2^b and is clamped to 2^b - 1.
+ *   - "rounding to nearest" is round-half-to-even (rintf) for Z_c and c_q.
+ *   - dequantisation (never printed) is the inverse map c_hat = (c_q - Z_c) * S_c
+ *     in FP32; the error is e = c_hat - c in FP32.
+ *   - a group whose scale S underflows to 0 (max == min, or a range too small
+ *     for 2^-b scaling) is degenerate: every code 0, c_hat = c, one symbol.
+ *   - Morton: per-axis min/max over ALL Gaussians; t = (p - lo) / (hi - lo);
+ *     21-bit axis codes floor(t * 2^21) clamped to 2^21 - 1; x bit k -> code
+ *     bit 3k, y -> 3k+1, z -> 3k+2; order by (code, index).
+ *   - importance order: descending importance, ties by ascending index.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORACLE_OK 0
+#define ORACLE_ERR_ARG -1
+#define ORACLE_ERR_NONFINITE -2
+#define ORACLE_ERR_RANGE -3
+#define ORACLE_ERR_NOMEM -4
+
+/* ------------------------------------------------------------------------ */
+/* Importance rank (Sec. III-A).                                              */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    float key;
+    int64_t idx;
+} rank_item;
+
+static int cmp_rank(const void *a, const void *b) {
+    const rank_item *x = (const rank_item *)a;
+    const rank_item *y = (const rank_item *)b;
+    if (x->key > y->key) return -1; /* larger importance first */
+    if (x->key < y->key) return 1;
+    if (x->idx < y->idx) return -1; /* ties: smaller index first */
+    if (x->idx > y->idx) return 1;
+    return 0;
+}
+
+/* rank_out[i] = position of Gaussian i in the order of decreasing importance. */
+int oracle_rank(const float *importance, int64_t n, int32_t *rank_out) {
+    if (n < 0 || (n > 0 && (!importance || !rank_out))) return ORACLE_ERR_ARG;
+    rank_item *items = (rank_item *)malloc(sizeof(rank_item) * (size_t)(n > 0 ? n : 1));
+    if (!items) return ORACLE_ERR_NOMEM;
+    for (int64_t i = 0; i < n; i++) {
+        if (!isfinite(importance[i])) {
+            free(items);
+            return ORACLE_ERR_NONFINITE;
+        }
+        items[i].key = importance[i];
+        items[i].idx = i;
+    }
+    qsort(items, (size_t)n, sizeof(rank_item), cmp_rank);
+    for (int64_t j = 0; j < n; j++) rank_out[items[j].idx] = (int32_t)j;
+    free(items);
+    return ORACLE_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Morton order of the coordinates (Sec. III-G, last paragraph).             */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    uint64_t code;
+    int64_t idx;
+} morton_item;
+
+static int cmp_morton(const void *a, const void *b) {
+    const morton_item *x = (const morton_item *)a;
+    const morton_item *y = (const morton_item *)b;
+    if (x->code < y->code) return -1;
+    if (x->code > y->code) return 1;
+    if (x->idx < y->idx) return -1;
+    if (x->idx > y->idx) return 1;
+    return 0;
+}
+
+/* Quantised axis coordinate in [0, 2^21). */
+static uint32_t axis_code(float p, float lo, float hi) {
+    float d = hi - lo;
+    if (d == 0.0f) return 0;
+    float num = p - lo;
+    float t = num / d;
+    double s = floor((double)t * 2097152.0);
+    if (s > 2097151.0) s = 2097151.0;
+    if (s < 0.0) s = 0.0;
+    return (uint32_t)s;
+}
+
+/* Bit k of x goes to bit 3k, of y to 3k+1, of z to 3k+2 (one bit at a time). */
+static uint64_t interleave3(uint32_t x, uint32_t y, uint32_t z) {
+    uint64_t code = 0;
+    for (int k = 0; k < 21; k++) {
+        code |= (uint64_t)((x >> k) & 1u) << (3 * k);
+        code |= (uint64_t)((y >> k) & 1u) << (3 * k + 1);
+        code |= (uint64_t)((z >> k) & 1u) << (3 * k + 2);
+    }
+    return code;
+}
+
+/*
+ * attrs: [n][n_channels] row-major FP32, channels 0..2 are the position.
+ * code_out[i]: 63-bit Morton code of Gaussian i (may be NULL).
+ * order_out[p]: index of the Gaussian at Morton position p.
+ */
+int oracle_morton(const float *attrs, int64_t n, int32_t n_channels, uint64_t *code_out,
+                  int64_t *order_out) {
+    if (n < 0 || n_channels < 3 || (n > 0 && (!attrs || !order_out))) return ORACLE_ERR_ARG;
+    float lo[3], hi[3];
+    for (int a = 0; a < 3; a++) {
+        lo[a] = INFINITY;
+        hi[a] = -INFINITY;
+    }
+    for (int64_t i = 0; i < n; i++) {
+        for (int a = 0; a < 3; a++) {
+            float p = attrs[i * n_channels + a];
+            if (!isfinite(p)) return ORACLE_ERR_NONFINITE;
+            if (p < lo[a]) lo[a] = p;
+            if (p > hi[a]) hi[a] = p;
+        }
+    }
+    for (int a = 0; a < 3 && n > 0; a++) {
+        float d = hi[a] - lo[a];
+        if (!isfinite(d)) return ORACLE_ERR_RANGE;
+    }
+    morton_item *items = (morton_item *)malloc(sizeof(morton_item) * (size_t)(n > 0 ? n : 1));
+    if (!items) return ORACLE_ERR_NOMEM;
+    for (int64_t i = 0; i < n; i++) {
+        uint32_t q[3];
+        for (int a = 0; a < 3; a++) q[a] = axis_code(attrs[i * n_channels + a], lo[a], hi[a]);
+        items[i].code = interleave3(q[0], q[1], q[2]);
+        items[i].idx = i;
+        if (code_out) code_out[i] = items[i].code;
+    }
+    qsort(items, (size_t)n, sizeof(morton_item), cmp_morton);
+    for (int64_t p = 0; p < n; p++) order_out[p] = items[p].idx;
+    free(items);
+    return ORACLE_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Kept set for one reserve ratio, in Morton order (Sec. III-A, III-G).      */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * kept_out[j] (j < keep) = the j-th Morton position p whose Gaussian
+ * order[p] has rank < keep.  Returns the number written (must equal keep).
+ */
+int64_t oracle_kept(const int32_t *rank, const int64_t *order, int64_t n, int64_t keep,
+                    int64_t *kept_out) {
+    int64_t j = 0;
+    for (int64_t p = 0; p < n; p++) {
+        if ((int64_t)rank[order[p]] < keep) kept_out[j++] = p;
+    }
+    return j;
+}
+
+/* ------------------------------------------------------------------------ */
+/* One quantisation group of one channel, all bit-widths (Sec. III-D, III-F). */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * vals: the n values of the group (n >= 1).
+ * bits[k]: bit-width of option k, 1..16.
+ * Per option k: sse[k] = sum e^2, l1[k] = sum |e|, linf[k] = max |e|,
+ * hbits[k] = -sum_s h_s log2(h_s / n) (entropy lower bound in bits),
+ * codes[k * n + i] (optional) = c_q of element i.
+ * vmin/vmax: the group min and max stored as metadata.
+ */
+int oracle_group_cost(const float *vals, int64_t n, const int32_t *bits, int32_t n_b,
+                      double *sse, double *l1, float *linf, double *hbits, float *vmin,
+                      float *vmax, uint16_t *codes) {
+    if (n < 1 || n_b < 1 || !vals || !bits) return ORACLE_ERR_ARG;
+    float m = vals[0];
+    float M = vals[0];
+    for (int64_t i = 0; i < n; i++) {
+        if (!isfinite(vals[i])) return ORACLE_ERR_NONFINITE;
+        if (vals[i] < m) m = vals[i];
+        if (vals[i] > M) M = vals[i];
+    }
+    float R = M - m;
+    if (!isfinite(R)) return ORACLE_ERR_RANGE;
+    if (vmin) *vmin = m;
+    if (vmax) *vmax = M;
+
+    for (int32_t k = 0; k < n_b; k++) {
+        int b = bits[k];
+        if (b < 1 || b > 16) return ORACLE_ERR_ARG;
+        float twob = (float)(1u << b);  /* 2^b, exact */
+        float top = twob - 1.0f;        /* 2^b - 1, exact */
+        float S = R / twob;             /* S_c = (max - min) / 2^b */
+        double s2 = 0.0, s1 = 0.0;
+        float smax = 0.0f;
+        double h_bits = 0.0;
+        if (S == 0.0f) {
+            /* degenerate group: one symbol, exact reconstruction */
+            if (codes)
+                for (int64_t i = 0; i < n; i++) codes[(int64_t)k * n + i] = 0;
+        } else {
+            float t = M / S;
+            float zr = twob - t;
+            float Z = rintf(zr); /* Z_c = round(2^b - max / S_c) */
+            uint32_t *hist = (uint32_t *)calloc((size_t)1u << b, sizeof(uint32_t));
+            if (!hist) return ORACLE_ERR_NOMEM;
+            for (int64_t i = 0; i < n; i++) {
+                float c = vals[i];
+                float y = c / S;
+                float x = y + Z;                       /* c / S_c + Z_c */
+                float xc = fminf(fmaxf(x, 0.0f), top); /* clamp(., 0, 2^b - 1) */
+                int q = (int)rintf(xc);                /* round to nearest */
+                float qz = (float)q - Z;
+                float chat = qz * S;                   /* dequantised value */
+                float e = chat - c;
+                s2 += (double)e * (double)e;
+                s1 += fabs((double)e);
+                if (fabsf(e) > smax) smax = fabsf(e);
+                hist[q] += 1u;
+                if (codes) codes[(int64_t)k * n + i] = (uint16_t)q;
+            }
+            for (uint32_t s = 0; s < (1u << b); s++) {
+                if (hist[s] > 0) {
+                    double p = (double)hist[s] / (double)n;
+                    h_bits += -(double)hist[s] * log2(p);
+                }
+            }
+            free(hist);
+        }
+        if (sse) sse[k] = s2;
+        if (l1) l1[k] = s1;
+        if (linf) linf[k] = smax;
+        if (hbits) hbits[k] = h_bits;
+    }
+    return ORACLE_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Full cost table (Sec. III-F): every ratio, channel, group, bit-width.     */
+/* ------------------------------------------------------------------------ */
+
+/* Number of groups of size G over a kept set of size keep (last one partial). */
+int64_t oracle_n_groups(int64_t keep, int32_t G) { return (keep + G - 1) / G; }
+
+/*
+ * Items are enumerated r-major, then channel, then group:
+ *   item(r, c, g) = C * sum_{r' < r} n_groups(r') + c * n_groups(r) + g
+ * Per item: cnt, vmin, vmax.  Per (item, option k): index item * n_b + k.
+ * keep[r] must satisfy 0 <= keep[r] <= n.
+ */
+int oracle_cost_table(const float *attrs, const float *importance, int64_t n, int32_t n_channels,
+                      const int64_t *keep, int32_t n_r, const int32_t *bits, int32_t n_b, int32_t G,
+                      double *sse, double *l1, float *linf, double *hbits, int32_t *cnt,
+                      float *vmin, float *vmax) {
+    if (n < 0 || n_channels < 3 || n_r < 1 || n_b < 1 || G < 1) return ORACLE_ERR_ARG;
+    for (int32_t r = 0; r < n_r; r++)
+        if (keep[r] < 0 || keep[r] > n) return ORACLE_ERR_ARG;
+    for (int64_t i = 0; i < n * n_channels; i++)
+        if (!isfinite(attrs[i])) return ORACLE_ERR_NONFINITE;
+    int32_t *rank = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int64_t *order = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    int64_t *kept = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    float *vals = (float *)malloc(sizeof(float) * (size_t)(G));
+    int rc = ORACLE_OK;
+    if (!rank || !order || !kept || !vals) {
+        rc = ORACLE_ERR_NOMEM;
+        goto done;
+    }
+    rc = oracle_rank(importance, n, rank);
+    if (rc) goto done;
+    rc = oracle_morton(attrs, n, n_channels, NULL, order);
+    if (rc) goto done;
+    int64_t item = 0;
+    for (int32_t r = 0; r < n_r; r++) {
+        int64_t K = oracle_kept(rank, order, n, keep[r], kept);
+        int64_t ng = oracle_n_groups(K, G);
+        for (int32_t c = 0; c < n_channels; c++) {
+            for (int64_t g = 0; g < ng; g++, item++) {
+                int64_t start = g * G;
+                int64_t len = K - start < G ? K - start : G;
+                for (int64_t i = 0; i < len; i++)
+                    vals[i] = attrs[order[kept[start + i]] * n_channels + c];
+                cnt[item] = (int32_t)len;
+                rc = oracle_group_cost(vals, len, bits, n_b, sse + item * n_b, l1 + item * n_b,
+                                       linf + item * n_b, hbits + item * n_b, vmin + item,
+                                       vmax + item, NULL);
+                if (rc) goto done;
+            }
+        }
+    }
+done:
+    free(rank);
+    free(order);
+    free(kept);
+    free(vals);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Quantise one chosen configuration (Sec. III-D).                            */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * For one kept-set size `keep` and group size G, quantise every (channel,
+ * group) with its chosen bit-width q_bits[c * n_groups + g].
+ * codes_out[c * keep + j]: code of the j-th kept Gaussian (Morton order).
+ * minmax_out[(c * n_groups + g) * 2 + {0,1}]: group min and max.
+ */
+int oracle_quantize(const float *attrs, const float *importance, int64_t n, int32_t n_channels,
+                    int64_t keep, int32_t G, const uint8_t *q_bits, uint16_t *codes_out,
+                    float *minmax_out) {
+    if (n < 0 || keep < 0 || keep > n || G < 1) return ORACLE_ERR_ARG;
+    int32_t *rank = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int64_t *order = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    int64_t *kept = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    float *vals = (float *)malloc(sizeof(float) * (size_t)G);
+    uint16_t *codes = (uint16_t *)malloc(sizeof(uint16_t) * (size_t)G);
+    int rc = ORACLE_OK;
+    if (!rank || !order || !kept || !vals || !codes) {
+        rc = ORACLE_ERR_NOMEM;
+        goto done;
+    }
+    rc = oracle_rank(importance, n, rank);
+    if (rc) goto done;
+    rc = oracle_morton(attrs, n, n_channels, NULL, order);
+    if (rc) goto done;
+    int64_t K = oracle_kept(rank, order, n, keep, kept);
+    int64_t ng = oracle_n_groups(K, G);
+    for (int32_t c = 0; c < n_channels; c++) {
+        for (int64_t g = 0; g < ng; g++) {
+            int64_t start = g * G;
+            int64_t len = K - start < G ? K - start : G;
+            for (int64_t i = 0; i < len; i++) vals[i] = attrs[order[kept[start + i]] * n_channels + c];
+            int32_t b = q_bits[c * ng + g];
+            double d0;
+            double d1;
+            float d2;
+            double d3;
+            rc = oracle_group_cost(vals, len, &b, 1, &d0, &d1, &d2, &d3,
+                                   &minmax_out[(c * ng + g) * 2], &minmax_out[(c * ng + g) * 2 + 1],
+                                   codes);
+            if (rc) goto done;
+            memcpy(&codes_out[(int64_t)c * K + start], codes, sizeof(uint16_t) * (size_t)len);
+        }
+    }
+done:
+    free(rank);
+    free(order);
+    free(kept);
+    free(vals);
+    free(codes);
+    return rc;
+}

@@ -1,0 +1,190 @@
+"""Pins of the CPU oracle: closed forms, library-routine reductions and
+invariants of the group-wise quantiser (Sec. III-D), the entropy bound
+(Sec. III-F "Size Estimator") and the Morton order (Sec. III-G).
+
+Each check takes an oracle library handle so the same checks can be run
+against deliberately broken copies of the oracle (tests/test_oracle_mutants.py)
+to show that a plausible mistake fails at least one of them.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+from scipy.stats import entropy as scipy_entropy
+
+import oracle
+
+
+def check_grid(L, b_data: int, b_q: int):
+    """Data c_k = k / 2^b_data, k = 0..2^b_data (so min 0, max 1, range 1).
+
+    With R = 1: S = 2^-b_q exactly, max/S = 2^b_q, Z = 0, and c/S = k * 2^(b_q - b_data)
+    exactly, so the code is round-half-even(k * 2^(b_q - b_data)) clamped to 2^b_q - 1,
+    the reconstruction is q * 2^-b_q and the error is exact in double.
+    """
+    n = (1 << b_data) + 1
+    k = np.arange(n, dtype=np.float64)
+    vals = (k / float(1 << b_data)).astype(np.float32)
+    out = oracle.group_cost(vals, [b_q], want_codes=True, L=L)
+    expect_q = np.minimum(np.rint(k * 2.0 ** (b_q - b_data)), (1 << b_q) - 1)
+    assert np.array_equal(out["codes"][0].astype(np.int64), expect_q.astype(np.int64)), (b_data, b_q)
+    err = expect_q / float(1 << b_q) - k / float(1 << b_data)
+    assert math.isclose(out["sse"][0], float(np.sum(err * err)), rel_tol=1e-12, abs_tol=0.0)
+    assert math.isclose(out["l1"][0], float(np.sum(np.abs(err))), rel_tol=1e-12)
+    assert out["linf"][0] == np.float32(np.max(np.abs(err)))
+    counts = np.bincount(expect_q.astype(np.int64))
+    counts = counts[counts > 0]
+    expect_h = n * scipy_entropy(counts, base=2)
+    assert math.isclose(out["hbits"][0], expect_h, rel_tol=1e-10, abs_tol=1e-9)
+    if b_q == b_data:
+        # closed form: 2^b - 1 singletons and one pair -> n log2 n - 2 bits; SSE = 4^-b.
+        assert math.isclose(out["hbits"][0], n * math.log2(n) - 2.0, rel_tol=1e-10)
+        assert math.isclose(out["sse"][0], 4.0 ** (-b_q), rel_tol=1e-12)
+    assert out["vmin"] == 0.0 and out["vmax"] == 1.0
+
+
+def check_dyadic(L, j: int, off: int, b: int):
+    """Data c_k = (k - off) / 2^j, k = 0..2^j: range 1, min -off/2^j, max (2^j - off)/2^j.
+
+    Every FP32 operation of the quantiser is exact on these inputs (dyadic values with
+    few bits), so the result must equal the paper's formula evaluated in exact rational
+    arithmetic: S = R / 2^b, Z = round(2^b - max / S), q = round(clamp(c / S + Z)),
+    c_hat = (q - Z) * S, with round = nearest, ties to even.
+    """
+    from fractions import Fraction as F
+    n = (1 << j) + 1
+    vals_q = [F(k - off, 1 << j) for k in range(n)]
+    vals = np.array([float(v) for v in vals_q], dtype=np.float32)
+    out = oracle.group_cost(vals, [b], want_codes=True, L=L)
+    m, M = min(vals_q), max(vals_q)
+    S = (M - m) / (1 << b)
+    Z = round((1 << b) - M / S)
+    top = (1 << b) - 1
+    q = [round(min(max(v / S + Z, F(0)), F(top))) for v in vals_q]
+    err = [(F(qk) - Z) * S - v for qk, v in zip(q, vals_q)]
+    assert out["codes"][0].astype(np.int64).tolist() == q, (j, off, b)
+    assert math.isclose(out["sse"][0], float(sum(e * e for e in err)), rel_tol=1e-12)
+    assert math.isclose(out["l1"][0], float(sum(abs(e) for e in err)), rel_tol=1e-12)
+    assert out["linf"][0] == np.float32(float(max(abs(e) for e in err)))
+    counts = np.bincount(np.array(q))
+    counts = counts[counts > 0]
+    expect_h = n * scipy_entropy(counts, base=2) if counts.size > 1 else 0.0
+    assert math.isclose(out["hbits"][0], expect_h, rel_tol=1e-10, abs_tol=1e-9)
+
+
+def check_constant(L, value: float, n: int, bits):
+    vals = np.full(n, value, dtype=np.float32)
+    out = oracle.group_cost(vals, bits, want_codes=True, L=L)
+    assert np.all(out["codes"] == 0)
+    assert np.all(out["sse"] == 0.0) and np.all(out["l1"] == 0.0) and np.all(out["linf"] == 0.0)
+    assert np.all(out["hbits"] == 0.0)
+    assert out["vmin"] == np.float32(value) and out["vmax"] == np.float32(value)
+
+
+def check_invariants(L, vals: np.ndarray, bits):
+    """Properties that hold for any finite group."""
+    vals = np.asarray(vals, dtype=np.float32)
+    n = vals.shape[0]
+    out = oracle.group_cost(vals, bits, want_codes=True, L=L)
+    assert out["vmin"] == vals.min() and out["vmax"] == vals.max()
+    order = np.argsort(vals, kind="stable")
+    R = np.float32(vals.max()) - np.float32(vals.min())
+    for k, b in enumerate(bits):
+        q = out["codes"][k].astype(np.int64)
+        assert q.min() >= 0 and q.max() <= (1 << b) - 1
+        # monotone: a larger value never gets a smaller code
+        assert np.all(np.diff(q[order]) >= 0)
+        # entropy bound equals n * H(histogram of the codes) (library routine)
+        counts = np.bincount(q)
+        counts = counts[counts > 0]
+        assert counts.sum() == n
+        expect_h = n * scipy_entropy(counts, base=2) if counts.size > 1 else 0.0
+        assert math.isclose(out["hbits"][k], expect_h, rel_tol=1e-10, abs_tol=1e-9)
+        assert out["hbits"][k] <= n * min(b, math.log2(n)) + 1e-9
+        S = float(R) / float(1 << b)
+        if R > 0 and S > 1e-30:
+            # the max lands at 2^b - 1, the min at 0: Z places the range on the code grid
+            assert q[np.argmax(vals)] == (1 << b) - 1
+            assert q[np.argmin(vals)] <= 1
+            # every reconstruction lies within 1.5 steps (the top code within 1.5 S,
+            # the rest within S/2, plus FP32 rounding of the arithmetic)
+            slack = 1.5 * S + 4e-7 * float(max(abs(vals.min()), abs(vals.max())))
+            assert float(out["linf"][k]) <= slack * (1 + 1e-6), (b, out["linf"][k], S)
+        lin = float(out["linf"][k])
+        assert out["sse"][k] <= n * lin * lin * (1 + 1e-12) + 1e-300
+        assert out["l1"][k] <= n * lin * (1 + 1e-12) + 1e-300
+        assert lin * lin <= out["sse"][k] * (1 + 1e-12) + 1e-300
+        assert out["l1"][k] >= lin * (1 - 1e-12)
+
+
+def check_uniform_noise(L, seed: int = 1):
+    """Textbook: uniform data, step S -> mean squared error ~ S^2 / 12, mean |e| ~ S / 4.
+
+    The top half-step above 2^b - 1 is clamped (S divides by 2^b); at b >= 8 that
+    tail moves the means by under 5%.
+    """
+    rng = np.random.default_rng(seed)
+    vals = rng.uniform(-3.0, 5.0, size=65536).astype(np.float32)
+    for b in (8, 10, 12):
+        out = oracle.group_cost(vals, [b], L=L)
+        S = (float(vals.max()) - float(vals.min())) / (1 << b)
+        mse = out["sse"][0] / vals.shape[0]
+        assert 0.9 < mse / (S * S / 12.0) < 1.1, (b, mse, S)
+        mae = out["l1"][0] / vals.shape[0]
+        assert 0.9 < mae / (S / 4.0) < 1.1
+
+
+def check_two_point(L, m: float, M: float, bits):
+    vals = np.array([m, M, M, m, M], dtype=np.float32)
+    out = oracle.group_cost(vals, bits, want_codes=True, L=L)
+    for k, b in enumerate(bits):
+        q = out["codes"][k]
+        assert np.all(q[[1, 2, 4]] == (1 << b) - 1)
+        assert np.all(q[[0, 3]] <= 1)
+
+
+def spread_bits(v: np.ndarray) -> np.ndarray:
+    """Spread the 21 low bits of v to every third bit (mask-and-shift method)."""
+    x = v.astype(np.uint64) & np.uint64(0x1FFFFF)
+    x = (x | (x << np.uint64(32))) & np.uint64(0x1F00000000FFFF)
+    x = (x | (x << np.uint64(16))) & np.uint64(0x1F0000FF0000FF)
+    x = (x | (x << np.uint64(8))) & np.uint64(0x100F00F00F00F00F)
+    x = (x | (x << np.uint64(4))) & np.uint64(0x10C30C30C30C30C3)
+    x = (x | (x << np.uint64(2))) & np.uint64(0x1249249249249249)
+    return x
+
+
+def check_morton_lattice(L, seed: int = 3, n: int = 2000):
+    """Positions on the 2^-21 lattice of [0, 1]: the axis code is the lattice index."""
+    rng = np.random.default_rng(seed)
+    idx = rng.integers(0, 1 << 21, size=(n, 3)).astype(np.int64)
+    idx[0] = 0
+    idx[1] = (1 << 21) - 1
+    pos = idx.astype(np.float64) / float(1 << 21)
+    pos[1] = 1.0  # the max maps to t = 1 and is clamped to 2^21 - 1
+    attrs = np.zeros((n, 5), dtype=np.float32)
+    attrs[:, :3] = pos.astype(np.float32)
+    attrs[:, 3:] = rng.standard_normal((n, 2)).astype(np.float32)
+    # duplicates exercise the index tiebreak
+    attrs[10] = attrs[20]
+    idx[10] = idx[20]
+    codes, order = oracle.morton(attrs, L=L)
+    expect = (spread_bits(idx[:, 0]) | (spread_bits(idx[:, 1]) << np.uint64(1))
+              | (spread_bits(idx[:, 2]) << np.uint64(2)))
+    assert np.array_equal(codes, expect)
+    expect_order = np.lexsort((np.arange(n), expect))
+    assert np.array_equal(order, expect_order)
+
+
+def check_rank(L, seed: int = 4, n: int = 5000):
+    rng = np.random.default_rng(seed)
+    imp = np.exp(rng.standard_normal(n)).astype(np.float32)
+    imp[100:200] = imp[50]  # ties
+    imp[300] = 0.0
+    imp[301] = -0.0
+    r = oracle.rank(imp, L=L)
+    order = np.lexsort((np.arange(n), -imp.astype(np.float64)))
+    expect = np.empty(n, dtype=np.int64)
+    expect[order] = np.arange(n)
+    assert np.array_equal(r.astype(np.int64), expect)

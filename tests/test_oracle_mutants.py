@@ -1,0 +1,77 @@
+"""Plant plausible mistakes in a copy of the oracle and check that the pins
+catch each one (the mistake is planted on the CPU, in a temporary copy)."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "oracle.c")
+
+MUTANTS = {
+    "scale_2b_minus_1": ("float S = R / twob;", "float S = R / (twob - 1.0f);"),
+    "zero_point_floor": ("float Z = rintf(zr);", "float Z = floorf(zr);"),
+    "zero_point_sign": ("float x = y + Z;", "float x = y - Z;"),
+    "dequant_drops_Z": ("float qz = (float)q - Z;", "float qz = (float)q;"),
+    "error_sign": ("float e = chat - c;", "float e = chat + c;"),
+    "code_truncates": ("int q = (int)rintf(xc);", "int q = (int)xc;"),
+    "range_transposed": ("float R = M - m;", "float R = m - M;"),
+    "sse_not_squared": ("s2 += (double)e * (double)e;", "s2 += fabs((double)e);"),
+    "entropy_drops_n": ("double p = (double)hist[s] / (double)n;", "double p = (double)hist[s];"),
+    "morton_y_bit": ("code |= (uint64_t)((y >> k) & 1u) << (3 * k + 1);",
+                     "code |= (uint64_t)((y >> k) & 1u) << (3 * k + 2);"),
+    "morton_scale": ("double s = floor((double)t * 2097152.0);",
+                     "double s = floor((double)t * 2097151.0);"),
+    "rank_ascending": ("if (x->key > y->key) return -1; /* larger importance first */",
+                       "if (x->key > y->key) return 1;"),
+    "rank_tiebreak": ("if (x->idx < y->idx) return -1; /* ties: smaller index first */",
+                      "if (x->idx < y->idx) return 1;"),
+}
+
+RUNNER = r"""
+import sys, numpy as np
+sys.path.insert(0, {root!r})
+import oracle
+from tests import pins
+L = oracle.load({so!r})
+checks = [
+    lambda: [pins.check_grid(L, b, b) for b in (1, 4, 9, 16)],
+    lambda: [pins.check_grid(L, 10, b) for b in (3, 12)],
+    lambda: [pins.check_dyadic(L, 4, 11, b) for b in range(1, 17)],
+    lambda: [pins.check_dyadic(L, 6, 37, b) for b in range(1, 17)],
+    lambda: pins.check_constant(L, 3.25, 9, list(range(1, 17))),
+    lambda: [pins.check_invariants(L, v, list(range(1, 17))) for v in (
+        np.random.default_rng(0).standard_normal(500).astype(np.float32) * 2 + 1,
+        np.random.default_rng(1).uniform(-4, -3.9, 300).astype(np.float32))],
+    lambda: pins.check_uniform_noise(L),
+    lambda: pins.check_two_point(L, -7.1, 3.3, list(range(1, 17))),
+    lambda: pins.check_morton_lattice(L),
+    lambda: pins.check_rank(L),
+]
+failed = 0
+for c in checks:
+    try:
+        c()
+    except Exception:
+        failed += 1
+print("FAILED_CHECKS", failed)
+sys.exit(0 if failed else 7)
+"""
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(tmp_path, name):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation anchor not found: {old}"
+    mut = tmp_path / "oracle_mut.c"
+    mut.write_text(src.replace(old, new))
+    so = tmp_path / "liboracle_mut.so"
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+                    "-fno-fast-math", "-o", str(so), str(mut), "-lm"], check=True)
+    code = RUNNER.format(root=ROOT, so=str(so))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300)
+    # exit 0 = at least one pin failed on the mutant (what we want); 7 = mutant survived
+    assert r.returncode != 7, f"mutant {name} survived every pin:\n{r.stdout}\n{r.stderr}"
+    assert r.returncode == 0 or r.returncode < 0, r.stderr
