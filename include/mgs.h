@@ -1,0 +1,314 @@
+/*
+ * mgs.h -- C ABI of a GB300 (sm_103a) library that builds the candidate cost
+ * table of MesonGS++'s size-aware configuration search and solves the bit-width
+ * 0-1 ILP over it.
+ *
+ * The problem (Eq. (eq:nilp), Sec. III-E): choose the reserve ratio tau and a
+ * bit-width per (channel, block) to minimise the quality loss subject to the
+ * estimated size <= budget.  Alg. 1 (Sec. III-E/F) samples tau on a grid and
+ * solves a 0-1 ILP (Eq. (eq:ilp)) per tau over a precomputed loss matrix
+ * Omega[C][B][Q] (Sec. III-F "Acceleration") and a size estimate (Sec. III-F
+ * "Size Estimator").  This library computes that matrix for every tau at once
+ * (mgs_build_cost_table), estimates sizes (mgs_estimate_size), solves the ILP
+ * and picks tau (mgs_solve_budget), and emits the codes of a chosen
+ * configuration (mgs_quantize_groups).
+ *
+ * Conventions.
+ *   - Every function returns an mgs_status; MGS_OK is 0, errors are negative.
+ *     mgs_last_error() gives a message for the last failing call on the
+ *     calling thread.  No C++ exception crosses this interface.
+ *   - "device" pointers are CUDA device memory of the context's GPU; "host"
+ *     pointers are CPU memory.  Where a pointer may be either, the library
+ *     asks the CUDA driver which it is.
+ *   - The caller owns every buffer it passes; inputs are never modified.  The
+ *     library owns its handles (mgs_ctx, mgs_scene) and the device memory
+ *     behind them.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Calls that take a stream are ordered on it; a call that writes
+ *     host memory synchronises that stream before returning.
+ *   - Budgets and sizes are bytes (1 MB = 10^6 B).
+ *
+ * Channel layout of a scene (Sec. II "Preliminary"): attrs[i][c] is channel c
+ * of Gaussian i, FP32, row-major; channels 0..2 must be the position (they
+ * define the Morton order, Sec. III-G).  The synthetic scenes of this project
+ * use 59 channels: position(3), SH DC(3), SH rest(45), opacity(1), log-scale(3),
+ * rotation(4).
+ */
+#ifndef MGS_H
+#define MGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t mgs_status;
+
+#define MGS_OK 0
+#define MGS_ERR_INVALID_ARG (-1)   /* a size, pointer or option is out of range */
+#define MGS_ERR_NONFINITE (-2)     /* an attribute or importance is NaN or +-inf */
+#define MGS_ERR_RANGE (-3)         /* a channel's max - min overflows FP32 */
+#define MGS_ERR_OUT_OF_MEMORY (-4) /* device or host allocation failed */
+#define MGS_ERR_CUDA (-5)          /* a CUDA call failed (message has the CUDA error) */
+#define MGS_ERR_INFEASIBLE (-6)    /* no ratio fits the budget even at the lowest bit-widths */
+#define MGS_ERR_TIMEOUT (-7)       /* a bounded wait ran out */
+#define MGS_ERR_BUSY (-8)          /* the resource is in use (e.g. a server at capacity) */
+
+#define MGS_MAX_RATIOS 64      /* kept-set sizes per grid */
+#define MGS_MAX_OPTIONS 16     /* candidate bit-widths per grid */
+#define MGS_MAX_BITS 16        /* largest bit-width */
+#define MGS_MAX_GROUP 16384    /* largest group size G */
+#define MGS_MAX_CHANNELS 256
+
+typedef struct mgs_ctx mgs_ctx;
+typedef struct mgs_scene mgs_scene;
+
+/*
+ * The search grid (Alg. 1's tau loop x Eq. (eq:ilp)'s Q options; Sec. III-D
+ * groups of fixed length G, Tab. tab:robust / Sec. IV "block quantisation").
+ *   keep[r]  kept-set size K_r for reserve ratio r: the K_r most important
+ *            Gaussians are kept (Sec. III-A).  Strictly increasing, 1 <= K_r <= n.
+ *   bits[k]  candidate bit-width b_k, strictly increasing, each in 1..16.
+ *   group_size  G: the kept set, in Morton order (Sec. III-G), is cut into
+ *            consecutive groups of G; the last group holds the remainder.
+ * Both arrays are host memory, read during the call only.
+ */
+typedef struct {
+    int32_t n_ratios;
+    const int64_t *keep;
+    int32_t n_bits;
+    const int32_t *bits;
+    int32_t group_size;
+} mgs_grid;
+
+/*
+ * Layout of one cost table in a single caller-allocated buffer (256-byte
+ * aligned, `total_bytes` long).  Items are the (ratio r, channel c, group g)
+ * triples, enumerated r-major, then c, then g:
+ *     item(r, c, g) = item_begin[r] + c * n_groups[r] + g
+ *     item_begin[r] = n_channels * sum_{r' < r} n_groups[r'],  n_groups[r] = ceil(K_r / G)
+ * Per item and option k (index item * n_bits + k):
+ *     sse   f64  sum of squared dequantisation errors        (Omega, 2-norm squared)
+ *     l1    f64  sum of absolute errors                        (Omega, 1-norm)
+ *     hbits f64  entropy bound -sum_s h_s log2(h_s / n) in bits (Sec. III-F)
+ *     linf  f32  largest absolute error                        (Omega, inf-norm)
+ * Per item: count (i32, group size n), vmin and vmax (f32, the stored
+ * metadata of Sec. III-D).  Offsets are byte offsets from the buffer start.
+ */
+typedef struct {
+    int64_t n_items;
+    int32_t n_bits;
+    int32_t n_ratios;
+    int32_t n_channels;
+    int32_t group_size;
+    int64_t item_begin[MGS_MAX_RATIOS + 1];
+    int64_t n_groups[MGS_MAX_RATIOS];
+    int64_t off_sse;
+    int64_t off_l1;
+    int64_t off_hbits;
+    int64_t off_linf;
+    int64_t off_count;
+    int64_t off_vmin;
+    int64_t off_vmax;
+    int64_t total_bytes;
+} mgs_table_layout;
+
+/* Rate and distortion models of the solver. */
+#define MGS_RATE_ENTROPY 0 /* rate = hbits (entropy bound, Sec. III-F) */
+#define MGS_RATE_FIXED 1   /* rate = n * b bits (Eq. (eq:size_estim), P_ij * Q_ij) */
+#define MGS_NORM_SSE 0     /* Omega = sum of squared errors */
+#define MGS_NORM_L2 1      /* Omega = sum over groups of sqrt(SSE) */
+#define MGS_NORM_L1 2      /* Omega = sum of absolute errors */
+#define MGS_NORM_LINF 3    /* Omega = sum over groups of the largest error */
+
+typedef struct {
+    int32_t rate_model;          /* MGS_RATE_* */
+    int32_t norm;                /* MGS_NORM_* */
+    double const_bytes;          /* C of Eq. (eq:size_estim): exact bytes of coordinates etc. */
+    double meta_bytes_per_group; /* per (channel, group) metadata; 9 = FP32 min + max + 1 B width */
+    double delta_bytes;          /* S_Delta of Eq. (eq:size_estim): calibration offset, usually 0 */
+} mgs_solve_opts;
+
+/*
+ * Result of a budget solve.  The arrays are caller-provided and may be NULL:
+ *   choice[n_channels * n_groups[r]]  option index per (c, g) of the chosen ratio
+ *   ratio_status[n_ratios]   0 = solved, 1 = skipped (top bit-widths stay under
+ *                            the budget: tau too small, Alg. 1), -1 = infeasible
+ *   ratio_objective, ratio_bytes, ratio_lp_bound [n_ratios]
+ */
+typedef struct {
+    int32_t r_index;     /* chosen ratio; -1 if no ratio is feasible */
+    double est_bytes;    /* estimated size of the chosen configuration */
+    double objective;    /* its total distortion */
+    double lp_bound;     /* LP-relaxation lower bound of that ratio's optimum */
+    uint8_t *choice;
+    int32_t *ratio_status;
+    double *ratio_objective;
+    double *ratio_bytes;
+    double *ratio_lp_bound;
+} mgs_solution;
+
+/* ---- context --------------------------------------------------------- */
+
+/* Create a context on CUDA device `device`.  Allocates the entropy table
+ * (L(n) = n log2 n in 32.32 fixed point for n <= MGS_MAX_GROUP). */
+mgs_status mgs_create(int32_t device, mgs_ctx **out);
+/* Destroy a context; its scenes must have been destroyed first. */
+mgs_status mgs_destroy(mgs_ctx *ctx);
+/* Message of the last failing call on this thread ("" if none).  Static
+ * thread-local storage: valid until the next call on the same thread. */
+const char *mgs_last_error(void);
+/* Library version string. */
+const char *mgs_version(void);
+/* Number of CUDA kernels this library has enqueued in this process so far
+ * (a CUDA-graph replay counts the kernels it runs). */
+int64_t mgs_kernel_launches(void);
+
+/* ---- scenes ----------------------------------------------------------- */
+
+/*
+ * Make a scene resident on the device: validate (finite values, finite
+ * per-channel range), rank by importance (Sec. III-A: descending importance,
+ * ties by ascending index), order by Morton code of the position (Sec. III-G:
+ * 21-bit axis codes over the scene's bounding box, ties by index), and copy
+ * the attributes into Morton order in 8-channel slabs.
+ *   attrs       [n][n_channels] FP32 row-major, host or device
+ *   importance  [n] FP32 (joint importance I_g), host or device
+ * Synchronous on `stream`: returns after validation.  Errors:
+ * INVALID_ARG (n < 1, n >= 2^31, n_channels < 3 or > MGS_MAX_CHANNELS),
+ * NONFINITE, RANGE, OUT_OF_MEMORY, CUDA.
+ */
+mgs_status mgs_scene_create(mgs_ctx *ctx, const float *attrs, const float *importance, int64_t n,
+                            int32_t n_channels, void *stream, mgs_scene **out);
+mgs_status mgs_scene_destroy(mgs_scene *scene);
+/* n, channel count and device bytes held by the scene (any may be NULL). */
+mgs_status mgs_scene_info(const mgs_scene *scene, int64_t *n, int32_t *n_channels,
+                          int64_t *device_bytes);
+/* Copy the Morton code of each Gaussian (uint64 [n], index order) and the
+ * Morton permutation (int32 [n]: Gaussian at Morton position p) to device
+ * buffers; either may be NULL. */
+mgs_status mgs_scene_morton(const mgs_scene *scene, uint64_t *codes, int32_t *order, void *stream);
+
+/* ---- cost table --------------------------------------------------------- */
+
+/* Fill `out` for a scene of n Gaussians with n_channels channels. */
+mgs_status mgs_table_layout_for(int64_t n, int32_t n_channels, const mgs_grid *grid,
+                                mgs_table_layout *out);
+
+/*
+ * Build the candidate cost table (Sec. III-F: Omega[c][g][b] for every ratio,
+ * plus the entropy bound per option).  For every ratio r, channel c, group g
+ * and bit-width b: min m and max M of the group's values, S = (M - m) / 2^b,
+ * Z = round(2^b - M / S), codes q = round(clamp(v / S + Z, 0, 2^b - 1))
+ * (Sec. III-D; round = nearest, ties to even), reconstruction
+ * (q - Z) * S, its errors, and the histogram of q.  A group whose S is 0 is
+ * degenerate: all codes 0, no error, zero entropy.  Codes and histograms are
+ * exact FP32 evaluations of those formulas; sums are FP32 per thread and
+ * tree-reduced (relative error below 1e-5 against FP64).
+ *   table  layout.total_bytes bytes, device or host (host: copied back, the
+ *          stream is synchronised).
+ */
+mgs_status mgs_build_cost_table(mgs_ctx *ctx, const mgs_scene *scene, const mgs_grid *grid,
+                                void *table, void *stream);
+
+/*
+ * The same table computed the way a plain per-configuration search does it:
+ * one launch per (ratio, bit-width), each re-reading the group data.  Kept as
+ * the comparator of the fused path; results equal mgs_build_cost_table's up to
+ * the FP32 summation order.
+ */
+mgs_status mgs_build_cost_table_plain(mgs_ctx *ctx, const mgs_scene *scene, const mgs_grid *grid,
+                                      void *table, void *stream);
+
+/*
+ * Several scenes, one grid, one persistent launch over all their
+ * (scene, ratio, group, channel-chunk) work items.  tables[s] follows
+ * mgs_table_layout_for(n_s, C_s, grid) and must be device memory.
+ */
+mgs_status mgs_build_cost_tables_batched(mgs_ctx *ctx, int32_t n_scenes,
+                                         const mgs_scene *const *scenes, const mgs_grid *grid,
+                                         void *const *tables, void *stream);
+
+/* ---- batched plans, CUDA graphs and tile shapes ------------------------- */
+
+typedef struct mgs_plan mgs_plan;
+
+/*
+ * A reusable batched launch: the kept lists of every scene for the grid, the
+ * (scene, ratio) segment table in device memory and the tile shape are built
+ * once; mgs_plan_launch then enqueues one persistent kernel over every
+ * (scene, ratio, group, channel-chunk) work item.  With use_graph != 0 the
+ * first launch captures that work into a CUDA graph and later launches replay
+ * it.  tables[s] follows mgs_table_layout_for(n_s, C_s, grid), device memory;
+ * the scenes and tables must outlive the plan.
+ */
+mgs_status mgs_plan_create(mgs_ctx *ctx, int32_t n_scenes, const mgs_scene *const *scenes,
+                           const mgs_grid *grid, void *const *tables, int32_t use_graph,
+                           void *stream, mgs_plan **out);
+mgs_status mgs_plan_launch(mgs_plan *plan, void *stream);
+mgs_status mgs_plan_destroy(mgs_plan *plan);
+/* Work items and kernel launches of one mgs_plan_launch. */
+mgs_status mgs_plan_info(const mgs_plan *plan, int64_t *work_items, int32_t *launches,
+                         int32_t *tile_config);
+
+/*
+ * Tile shapes of the cost kernel: threads per CTA x elements per thread
+ * (>= G) x channels per work item.  mgs_set_tile_config pins one for a
+ * (group size, bit-width count) pair on this context (-1 restores the
+ * default); mgs_autotune times every shape that can hold the grid's group
+ * size on this scene and pins the fastest.  ms_per_config[count] (may be
+ * NULL) receives each shape's time, or -1 where it does not apply.
+ */
+int32_t mgs_tile_config_count(void);
+const char *mgs_tile_config_name(int32_t config);
+mgs_status mgs_set_tile_config(mgs_ctx *ctx, int32_t group_size, int32_t n_bits, int32_t config);
+mgs_status mgs_autotune(mgs_ctx *ctx, const mgs_scene *scene, const mgs_grid *grid, void *stream,
+                        int32_t *chosen, float *ms_per_config);
+
+/* ---- codes of one configuration ---------------------------------------- */
+
+/*
+ * Quantise one chosen configuration (Sec. III-D): kept-set size `keep`, group
+ * size G, bit-width bits[c * n_groups + g] (uint8, 1..16) per (channel, group).
+ *   codes   [n_channels][keep] uint16, device: code of the j-th kept Gaussian
+ *           in Morton order
+ *   minmax  [n_channels][n_groups][2] FP32, device: group min and max
+ *   bits    device
+ */
+mgs_status mgs_quantize_groups(mgs_ctx *ctx, const mgs_scene *scene, int64_t keep,
+                               int32_t group_size, const uint8_t *bits, uint16_t *codes,
+                               float *minmax, void *stream);
+
+/* ---- size estimate and budget solve (host) ------------------------------ */
+
+/*
+ * Estimated size (Eq. (eq:size_estim)) of ratio r_index with option
+ * choice[c * n_groups[r] + g]:
+ *   bytes = sum rate / 8 + meta_bytes_per_group * n_items(r) + const_bytes + delta_bytes
+ * `table` is host memory laid out by `layout`.
+ */
+mgs_status mgs_estimate_size(const void *table, const mgs_table_layout *layout,
+                             const mgs_grid *grid, int32_t r_index, const uint8_t *choice,
+                             const mgs_solve_opts *opts, double *bytes_out);
+
+/*
+ * Solve Eq. (eq:ilp) for every ratio (a multiple-choice knapsack over the
+ * (channel, group) items) and pick tau per Alg. 1: ratios whose all-top-bit-
+ * width size stays under the budget are skipped (tau too small); among the
+ * others the smallest total distortion wins (ties: larger ratio); if all
+ * feasible ratios are skipped the largest feasible one is taken.  Per ratio
+ * the solver takes the LP relaxation over each item's lower convex hull and
+ * rounds it to an integral choice by greedy upgrades; the LP value is returned
+ * as a lower bound.  `table` is host memory.  INFEASIBLE if no ratio fits.
+ */
+mgs_status mgs_solve_budget(const void *table, const mgs_table_layout *layout,
+                            const mgs_grid *grid, double budget_bytes, const mgs_solve_opts *opts,
+                            mgs_solution *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MGS_H */

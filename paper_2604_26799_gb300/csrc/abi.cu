@@ -1,0 +1,739 @@
+// C-ABI entry points of include/mgs.h: context, scenes, cost tables, codes.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+
+namespace mgs {
+
+static thread_local char g_err[1024];
+static std::atomic<int64_t> g_launches{0};
+
+void count_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+void set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+void clear_error() { g_err[0] = 0; }
+
+bool is_device_pointer(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int64_t n_groups_of(int64_t keep, int32_t G) { return (keep + G - 1) / G; }
+
+mgs_status check_grid(const mgs_grid *grid, int64_t n) {
+    if (!grid || !grid->keep || !grid->bits) {
+        set_error("grid, grid->keep and grid->bits must be non-NULL");
+        return MGS_ERR_INVALID_ARG;
+    }
+    if (grid->n_ratios < 1 || grid->n_ratios > MGS_MAX_RATIOS) {
+        set_error("n_ratios %d outside 1..%d", grid->n_ratios, MGS_MAX_RATIOS);
+        return MGS_ERR_INVALID_ARG;
+    }
+    if (grid->n_bits < 1 || grid->n_bits > MGS_MAX_OPTIONS) {
+        set_error("n_bits %d outside 1..%d", grid->n_bits, MGS_MAX_OPTIONS);
+        return MGS_ERR_INVALID_ARG;
+    }
+    if (grid->group_size < 1 || grid->group_size > MGS_MAX_GROUP) {
+        set_error("group_size %d outside 1..%d", grid->group_size, MGS_MAX_GROUP);
+        return MGS_ERR_INVALID_ARG;
+    }
+    for (int r = 0; r < grid->n_ratios; r++) {
+        int64_t k = grid->keep[r];
+        if (k < 1 || k > n || (r > 0 && k <= grid->keep[r - 1])) {
+            set_error("keep[%d] = %lld: kept-set sizes must increase strictly within 1..%lld", r,
+                      (long long)k, (long long)n);
+            return MGS_ERR_INVALID_ARG;
+        }
+    }
+    for (int k = 0; k < grid->n_bits; k++) {
+        int b = grid->bits[k];
+        if (b < 1 || b > MGS_MAX_BITS || (k > 0 && b <= grid->bits[k - 1])) {
+            set_error("bits[%d] = %d: bit-widths must increase strictly within 1..%d", k, b,
+                      MGS_MAX_BITS);
+            return MGS_ERR_INVALID_ARG;
+        }
+    }
+    return MGS_OK;
+}
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Table sub-array pointers for a buffer laid out by `L`.
+void table_ptrs(void *base, const mgs_table_layout &L, CostSeg *s) {
+    char *b = static_cast<char *>(base);
+    s->sse = reinterpret_cast<double *>(b + L.off_sse);
+    s->l1 = reinterpret_cast<double *>(b + L.off_l1);
+    s->hbits = reinterpret_cast<double *>(b + L.off_hbits);
+    s->linf = reinterpret_cast<float *>(b + L.off_linf);
+    s->cnt = reinterpret_cast<int32_t *>(b + L.off_count);
+    s->vmin = reinterpret_cast<float *>(b + L.off_vmin);
+    s->vmax = reinterpret_cast<float *>(b + L.off_vmax);
+}
+
+int pick_config(mgs_ctx *ctx, int G, int n_bits) {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    for (auto &t : ctx->tiles)
+        if (t.group_size == G && t.n_bits == n_bits) return t.config;
+    return cost_default_config(G);
+}
+
+// Segments of one scene for all ratios of the grid.
+mgs_status scene_segments(mgs_scene *sc, const mgs_grid *grid, void *table, cudaStream_t st,
+                          std::vector<CostSeg> *segs) {
+    mgs_table_layout L;
+    MGS_TRY(mgs_table_layout_for(sc->n, sc->C, grid, &L));
+    const int32_t *pos = nullptr;
+    std::vector<int64_t> off;
+    {
+        std::lock_guard<std::mutex> lk(sc->mu);
+        MGS_TRY(scene_kept(sc, grid->keep, grid->n_ratios, st, &pos, &off));
+    }
+    for (int r = 0; r < grid->n_ratios; r++) {
+        CostSeg s{};
+        s.slabs = sc->d_slabs;
+        s.kept = pos + off[r];
+        s.n = sc->n;
+        s.K = grid->keep[r];
+        s.item_base = L.item_begin[r];
+        s.n_groups = (int32_t)L.n_groups[r];
+        s.C = sc->C;
+        table_ptrs(table, L, &s);
+        segs->push_back(s);
+    }
+    return MGS_OK;
+}
+
+mgs_status run_cost(mgs_ctx *ctx, CostLaunch &launch, cudaStream_t st) {
+    int cfg = pick_config(ctx, launch.group_size, launch.n_bits);
+    CostSeg *d_segs = nullptr;
+    unsigned int *d_counter = nullptr;
+    size_t seg_bytes = align256(sizeof(CostSeg) * std::max<size_t>(launch.segs.size(), 1));
+    void *scratch = nullptr;
+    MGS_CUDA_TRY(cudaMallocAsync(&scratch, seg_bytes + 256, st));
+    d_segs = static_cast<CostSeg *>(scratch);
+    d_counter = reinterpret_cast<unsigned int *>(static_cast<char *>(scratch) + seg_bytes);
+    mgs_status s = cost_launch(ctx, launch, cfg, d_segs, d_counter, st);
+    cudaFreeAsync(scratch, st);
+    return s;
+}
+
+// Host-or-device table: run `fn` on a device table and copy back when needed.
+template <typename F>
+mgs_status with_device_table(void *table, size_t bytes, cudaStream_t st, F fn) {
+    if (is_device_pointer(table)) return fn(table);
+    void *d = nullptr;
+    MGS_CUDA_TRY(cudaMallocAsync(&d, bytes, st));
+    mgs_status s = fn(d);
+    if (s == MGS_OK) {
+        cudaError_t e = cudaMemcpyAsync(table, d, bytes, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            set_error("table copy-back failed: %s", cudaGetErrorString(e));
+            s = MGS_ERR_CUDA;
+        }
+    }
+    cudaFreeAsync(d, st);
+    return s;
+}
+
+}  // namespace
+}  // namespace mgs
+
+using namespace mgs;
+
+extern "C" {
+
+const char *mgs_last_error(void) { return g_err; }
+const char *mgs_version(void) { return "mgs 0.1 (sm_103a)"; }
+int64_t mgs_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+mgs_status mgs_create(int32_t device, mgs_ctx **out) {
+    clear_error();
+    if (!out) {
+        set_error("out is NULL");
+        return MGS_ERR_INVALID_ARG;
+    }
+    int count = 0;
+    MGS_CUDA_TRY(cudaGetDeviceCount(&count));
+    if (device < 0 || device >= count) {
+        set_error("device %d outside 0..%d", device, count - 1);
+        return MGS_ERR_INVALID_ARG;
+    }
+    DeviceGuard g(device);
+    mgs_ctx *ctx = new (std::nothrow) mgs_ctx();
+    if (!ctx) return MGS_ERR_OUT_OF_MEMORY;
+    ctx->device = device;
+    cudaError_t e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) {
+        delete ctx;
+        set_error("cudaDeviceGetAttribute: %s", cudaGetErrorString(e));
+        return MGS_ERR_CUDA;
+    }
+    // L(h) = h log2 h, 32.32 fixed point, h = 0..MGS_MAX_GROUP (L(0) = L(1) = 0).
+    std::vector<unsigned long long> lt(MGS_MAX_GROUP + 1, 0ull);
+    for (int h = 2; h <= MGS_MAX_GROUP; h++)
+        lt[h] = (unsigned long long)std::llround((double)h * std::log2((double)h) * 4294967296.0);
+    e = cudaMalloc(&ctx->d_ltab, sizeof(unsigned long long) * lt.size());
+    if (e == cudaSuccess)
+        e = cudaMemcpy(ctx->d_ltab, lt.data(), sizeof(unsigned long long) * lt.size(),
+                       cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(ctx->d_ltab);
+        delete ctx;
+        set_error("entropy table upload: %s", cudaGetErrorString(e));
+        return MGS_ERR_CUDA;
+    }
+    *out = ctx;
+    return MGS_OK;
+}
+
+mgs_status mgs_destroy(mgs_ctx *ctx) {
+    clear_error();
+    if (!ctx) return MGS_OK;
+    if (ctx->n_scenes != 0) {
+        set_error("%d scenes still alive", ctx->n_scenes);
+        return MGS_ERR_BUSY;
+    }
+    DeviceGuard g(ctx->device);
+    cudaFree(ctx->d_ltab);
+    delete ctx;
+    return MGS_OK;
+}
+
+mgs_status mgs_scene_create(mgs_ctx *ctx, const float *attrs, const float *importance, int64_t n,
+                            int32_t n_channels, void *stream, mgs_scene **out) {
+    clear_error();
+    if (!ctx || !attrs || !importance || !out) {
+        set_error("ctx, attrs, importance and out must be non-NULL");
+        return MGS_ERR_INVALID_ARG;
+    }
+    if (n < 1 || n >= ((int64_t)1 << 31) || n_channels < 3 || n_channels > MGS_MAX_CHANNELS) {
+        set_error("n = %lld must be in 1..2^31-1 and n_channels = %d in 3..%d", (long long)n,
+                  n_channels, MGS_MAX_CHANNELS);
+        return MGS_ERR_INVALID_ARG;
+    }
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const float *d_attrs = attrs, *d_imp = importance;
+    float *stage = nullptr;
+    size_t abytes = sizeof(float) * (size_t)n * n_channels, ibytes = sizeof(float) * (size_t)n;
+    bool host_a = !is_device_pointer(attrs), host_i = !is_device_pointer(importance);
+    if (host_a || host_i) {
+        size_t bytes = align256(host_a ? abytes : 0) + (host_i ? ibytes : 0);
+        if (cudaMallocAsync((void **)&stage, bytes, st) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("staging allocation of %zu bytes failed", bytes);
+            return MGS_ERR_OUT_OF_MEMORY;
+        }
+        char *p = reinterpret_cast<char *>(stage);
+        if (host_a) {
+            MGS_CUDA_TRY(cudaMemcpyAsync(p, attrs, abytes, cudaMemcpyHostToDevice, st));
+            d_attrs = reinterpret_cast<const float *>(p);
+            p += align256(abytes);
+        }
+        if (host_i) {
+            MGS_CUDA_TRY(cudaMemcpyAsync(p, importance, ibytes, cudaMemcpyHostToDevice, st));
+            d_imp = reinterpret_cast<const float *>(p);
+        }
+    }
+    mgs_scene *sc = new (std::nothrow) mgs_scene();
+    if (!sc) return MGS_ERR_OUT_OF_MEMORY;
+    mgs_status s = scene_build(ctx, d_attrs, d_imp, n, n_channels, st, sc);
+    if (stage) cudaFreeAsync(stage, st);
+    if (s != MGS_OK) {
+        cudaFreeAsync(sc->d_slabs, st);
+        cudaFreeAsync(sc->d_rank_m, st);
+        cudaFreeAsync(sc->d_order, st);
+        cudaFreeAsync(sc->d_codes, st);
+        cudaStreamSynchronize(st);
+        delete sc;
+        return s;
+    }
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        ctx->n_scenes++;
+    }
+    *out = sc;
+    return MGS_OK;
+}
+
+mgs_status mgs_scene_destroy(mgs_scene *sc) {
+    clear_error();
+    if (!sc) return MGS_OK;
+    DeviceGuard g(sc->ctx->device);
+    MGS_CUDA_TRY(cudaDeviceSynchronize());
+    cudaFree(sc->d_slabs);
+    cudaFree(sc->d_rank_m);
+    cudaFree(sc->d_order);
+    cudaFree(sc->d_codes);
+    if (sc->kept.pos) cudaFree(sc->kept.pos);
+    {
+        std::lock_guard<std::mutex> lk(sc->ctx->mu);
+        sc->ctx->n_scenes--;
+    }
+    delete sc;
+    return MGS_OK;
+}
+
+mgs_status mgs_scene_info(const mgs_scene *sc, int64_t *n, int32_t *n_channels, int64_t *bytes) {
+    clear_error();
+    if (!sc) {
+        set_error("scene is NULL");
+        return MGS_ERR_INVALID_ARG;
+    }
+    if (n) *n = sc->n;
+    if (n_channels) *n_channels = sc->C;
+    if (bytes) *bytes = sc->device_bytes + (int64_t)sc->kept.bytes;
+    return MGS_OK;
+}
+
+mgs_status mgs_scene_morton(const mgs_scene *sc, uint64_t *codes, int32_t *order, void *stream) {
+    clear_error();
+    if (!sc) {
+        set_error("scene is NULL");
+        return MGS_ERR_INVALID_ARG;
+    }
+    DeviceGuard g(sc->ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (codes)
+        MGS_CUDA_TRY(cudaMemcpyAsync(codes, sc->d_codes, sizeof(uint64_t) * sc->n,
+                                     cudaMemcpyDefault, st));
+    if (order)
+        MGS_CUDA_TRY(cudaMemcpyAsync(order, sc->d_order, sizeof(int32_t) * sc->n, cudaMemcpyDefault,
+                                     st));
+    return MGS_OK;
+}
+
+mgs_status mgs_table_layout_for(int64_t n, int32_t n_channels, const mgs_grid *grid,
+                                mgs_table_layout *out) {
+    if (!out) {
+        set_error("out is NULL");
+        return MGS_ERR_INVALID_ARG;
+    }
+    if (n_channels < 1 || n_channels > MGS_MAX_CHANNELS) {
+        set_error("n_channels %d outside 1..%d", n_channels, MGS_MAX_CHANNELS);
+        return MGS_ERR_INVALID_ARG;
+    }
+    MGS_TRY(check_grid(grid, n));
+    mgs_table_layout L;
+    std::memset(&L, 0, sizeof(L));
+    L.n_bits = grid->n_bits;
+    L.n_ratios = grid->n_ratios;
+    L.n_channels = n_channels;
+    L.group_size = grid->group_size;
+    int64_t items = 0;
+    for (int r = 0; r < grid->n_ratios; r++) {
+        L.item_begin[r] = items;
+        L.n_groups[r] = n_groups_of(grid->keep[r], grid->group_size);
+        items += (int64_t)n_channels * L.n_groups[r];
+    }
+    L.item_begin[grid->n_ratios] = items;
+    L.n_items = items;
+    size_t e = (size_t)items * grid->n_bits;
+    size_t off = 0;
+    L.off_sse = (int64_t)off;
+    off = align256(off + 8 * e);
+    L.off_l1 = (int64_t)off;
+    off = align256(off + 8 * e);
+    L.off_hbits = (int64_t)off;
+    off = align256(off + 8 * e);
+    L.off_linf = (int64_t)off;
+    off = align256(off + 4 * e);
+    L.off_count = (int64_t)off;
+    off = align256(off + 4 * (size_t)items);
+    L.off_vmin = (int64_t)off;
+    off = align256(off + 4 * (size_t)items);
+    L.off_vmax = (int64_t)off;
+    off = align256(off + 4 * (size_t)items);
+    L.total_bytes = (int64_t)off;
+    *out = L;
+    return MGS_OK;
+}
+
+static mgs_status build_table(mgs_ctx *ctx, const mgs_scene *scene, const mgs_grid *grid,
+                              void *table, void *stream, bool plain) {
+    clear_error();
+    if (!ctx || !scene || !table) {
+        set_error("ctx, scene and table must be non-NULL");
+        return MGS_ERR_INVALID_ARG;
+    }
+    mgs_scene *sc = const_cast<mgs_scene *>(scene);
+    mgs_table_layout L;
+    MGS_TRY(mgs_table_layout_for(sc->n, sc->C, grid, &L));
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return with_device_table(table, (size_t)L.total_bytes, st, [&](void *dt) -> mgs_status {
+        std::vector<CostSeg> segs;
+        MGS_TRY(scene_segments(sc, grid, dt, st, &segs));
+        CostLaunch launch;
+        launch.group_size = grid->group_size;
+        launch.n_bits = grid->n_bits;
+        for (int k = 0; k < grid->n_bits; k++) launch.bits[k] = grid->bits[k];
+        if (!plain) {
+            launch.segs = segs;
+            launch.opt_lo = 0;
+            launch.opt_hi = grid->n_bits;
+            return run_cost(ctx, launch, st);
+        }
+        // plain per-configuration loop: one launch per (ratio, bit-width)
+        for (size_t r = 0; r < segs.size(); r++) {
+            for (int k = 0; k < grid->n_bits; k++) {
+                launch.segs.assign(1, segs[r]);
+                launch.opt_lo = k;
+                launch.opt_hi = k + 1;
+                MGS_TRY(run_cost(ctx, launch, st));
+            }
+        }
+        return MGS_OK;
+    });
+}
+
+mgs_status mgs_build_cost_table(mgs_ctx *ctx, const mgs_scene *scene, const mgs_grid *grid,
+                                void *table, void *stream) {
+    return build_table(ctx, scene, grid, table, stream, false);
+}
+
+mgs_status mgs_build_cost_table_plain(mgs_ctx *ctx, const mgs_scene *scene, const mgs_grid *grid,
+                                      void *table, void *stream) {
+    return build_table(ctx, scene, grid, table, stream, true);
+}
+
+mgs_status mgs_build_cost_tables_batched(mgs_ctx *ctx, int32_t n_scenes,
+                                         const mgs_scene *const *scenes, const mgs_grid *grid,
+                                         void *const *tables, void *stream) {
+    clear_error();
+    if (!ctx || n_scenes < 1 || !scenes || !tables) {
+        set_error("ctx, scenes and tables must be non-NULL and n_scenes >= 1");
+        return MGS_ERR_INVALID_ARG;
+    }
+    if ((int64_t)n_scenes * grid->n_ratios > kMaxSegments) {
+        set_error("%d scenes x %d ratios exceed %d segments", n_scenes, grid->n_ratios,
+                  kMaxSegments);
+        return MGS_ERR_INVALID_ARG;
+    }
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CostLaunch launch;
+    launch.group_size = grid->group_size;
+    launch.n_bits = grid->n_bits;
+    for (int k = 0; k < grid->n_bits; k++) launch.bits[k] = grid->bits[k];
+    launch.opt_lo = 0;
+    launch.opt_hi = grid->n_bits;
+    launch.persistent = true;
+    for (int s = 0; s < n_scenes; s++) {
+        if (!scenes[s] || !tables[s] || !is_device_pointer(tables[s])) {
+            set_error("scene %d or its table is NULL or not device memory", s);
+            return MGS_ERR_INVALID_ARG;
+        }
+        MGS_TRY(scene_segments(const_cast<mgs_scene *>(scenes[s]), grid, tables[s], st,
+                               &launch.segs));
+    }
+    return run_cost(ctx, launch, st);
+}
+
+int32_t mgs_tile_config_count(void) { return cost_config_count(); }
+
+const char *mgs_tile_config_name(int32_t config) {
+    if (config < 0 || config >= cost_config_count()) return "";
+    return cost_config(config).name;
+}
+
+mgs_status mgs_set_tile_config(mgs_ctx *ctx, int32_t group_size, int32_t n_bits, int32_t config) {
+    clear_error();
+    if (!ctx || group_size < 1 || group_size > MGS_MAX_GROUP || n_bits < 1 ||
+        n_bits > MGS_MAX_OPTIONS || config < -1 || config >= cost_config_count()) {
+        set_error("bad tile request (G %d, %d bit-widths, config %d)", group_size, n_bits, config);
+        return MGS_ERR_INVALID_ARG;
+    }
+    if (config >= 0 && !cost_config_fits(config, group_size, n_bits)) {
+        set_error("tile %s cannot run G=%d with %d bit-widths", cost_config(config).name,
+                  group_size, n_bits);
+        return MGS_ERR_INVALID_ARG;
+    }
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    auto &v = ctx->tiles;
+    v.erase(std::remove_if(v.begin(), v.end(),
+                           [&](const TileChoice &t) {
+                               return t.group_size == group_size && t.n_bits == n_bits;
+                           }),
+            v.end());
+    if (config >= 0) v.push_back(TileChoice{group_size, n_bits, config});
+    return MGS_OK;
+}
+
+mgs_status mgs_autotune(mgs_ctx *ctx, const mgs_scene *scene, const mgs_grid *grid, void *stream,
+                        int32_t *chosen, float *ms_per_config) {
+    clear_error();
+    if (!ctx || !scene) {
+        set_error("ctx and scene must be non-NULL");
+        return MGS_ERR_INVALID_ARG;
+    }
+    mgs_scene *sc = const_cast<mgs_scene *>(scene);
+    mgs_table_layout L;
+    MGS_TRY(mgs_table_layout_for(sc->n, sc->C, grid, &L));
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    void *table = nullptr, *scratch = nullptr;
+    MGS_CUDA_TRY(cudaMallocAsync(&table, (size_t)L.total_bytes, st));
+    std::vector<CostSeg> segs;
+    mgs_status s = scene_segments(sc, grid, table, st, &segs);
+    const int nc = cost_config_count();
+    size_t seg_bytes = align256(sizeof(CostSeg) * std::max<size_t>(segs.size(), 1));
+    if (s == MGS_OK && cudaMallocAsync(&scratch, seg_bytes + 256, st) != cudaSuccess) {
+        set_error("autotune scratch allocation failed");
+        s = MGS_ERR_OUT_OF_MEMORY;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int best = -1;
+    float best_ms = 0;
+    for (int c = 0; c < nc && s == MGS_OK; c++) {
+        if (ms_per_config) ms_per_config[c] = -1.0f;
+        if (!cost_config_fits(c, grid->group_size, grid->n_bits)) continue;
+        CostLaunch launch;
+        launch.segs = segs;
+        launch.group_size = grid->group_size;
+        launch.n_bits = grid->n_bits;
+        for (int k = 0; k < grid->n_bits; k++) launch.bits[k] = grid->bits[k];
+        launch.opt_hi = grid->n_bits;
+        CostExec *X = nullptr;
+        std::vector<CostSeg> prepared;
+        int64_t n_work = 0;
+        s = cost_exec_create(ctx, launch, c, &X, &prepared, &n_work);
+        if (s != MGS_OK) break;
+        cudaMemcpyAsync(scratch, prepared.data(), sizeof(CostSeg) * prepared.size(),
+                        cudaMemcpyHostToDevice, st);
+        cost_exec_bind(X, static_cast<CostSeg *>(scratch),
+                       reinterpret_cast<unsigned int *>(static_cast<char *>(scratch) + seg_bytes));
+        s = cost_exec_run(X, st);   // warm-up
+        float ms = 0;
+        if (s == MGS_OK) {
+            cudaEventRecord(e0, st);
+            for (int rep = 0; rep < 2 && s == MGS_OK; rep++) s = cost_exec_run(X, st);
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms *= 0.5f;
+        }
+        cost_exec_destroy(X);
+        if (s != MGS_OK) break;
+        if (ms_per_config) ms_per_config[c] = ms;
+        if (best < 0 || ms < best_ms) {
+            best = c;
+            best_ms = ms;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (scratch) cudaFreeAsync(scratch, st);
+    cudaFreeAsync(table, st);
+    cudaStreamSynchronize(st);
+    if (s != MGS_OK) return s;
+    if (best < 0) {
+        set_error("no tile shape holds G=%d", grid->group_size);
+        return MGS_ERR_INVALID_ARG;
+    }
+    if (chosen) *chosen = best;
+    return mgs_set_tile_config(ctx, grid->group_size, grid->n_bits, best);
+}
+
+}  // extern "C"
+
+struct mgs_plan {
+    mgs_ctx *ctx = nullptr;
+    CostExec *exec = nullptr;
+    void *scratch = nullptr;
+    int64_t n_work = 0;
+    int config = -1;
+    bool use_graph = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+};
+
+extern "C" {
+
+mgs_status mgs_plan_create(mgs_ctx *ctx, int32_t n_scenes, const mgs_scene *const *scenes,
+                           const mgs_grid *grid, void *const *tables, int32_t use_graph,
+                           void *stream, mgs_plan **out) {
+    clear_error();
+    if (!ctx || n_scenes < 1 || !scenes || !tables || !grid || !out) {
+        set_error("ctx, scenes, grid, tables and out must be non-NULL and n_scenes >= 1");
+        return MGS_ERR_INVALID_ARG;
+    }
+    if ((int64_t)n_scenes * grid->n_ratios > kMaxSegments) {
+        set_error("%d scenes x %d ratios exceed %d segments", n_scenes, grid->n_ratios,
+                  kMaxSegments);
+        return MGS_ERR_INVALID_ARG;
+    }
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CostLaunch launch;
+    launch.group_size = grid->group_size;
+    launch.n_bits = grid->n_bits;
+    for (int k = 0; k < grid->n_bits; k++) launch.bits[k] = grid->bits[k];
+    launch.opt_hi = grid->n_bits;
+    launch.persistent = true;
+    for (int s = 0; s < n_scenes; s++) {
+        if (!scenes[s] || !tables[s] || !is_device_pointer(tables[s])) {
+            set_error("scene %d or its table is NULL or not device memory", s);
+            return MGS_ERR_INVALID_ARG;
+        }
+        MGS_TRY(scene_segments(const_cast<mgs_scene *>(scenes[s]), grid, tables[s], st,
+                               &launch.segs));
+    }
+    mgs_plan *P = new (std::nothrow) mgs_plan();
+    if (!P) return MGS_ERR_OUT_OF_MEMORY;
+    P->ctx = ctx;
+    P->use_graph = use_graph != 0;
+    P->config = pick_config(ctx, grid->group_size, grid->n_bits);
+    std::vector<CostSeg> prepared;
+    mgs_status s = cost_exec_create(ctx, launch, P->config, &P->exec, &prepared, &P->n_work);
+    size_t seg_bytes = align256(sizeof(CostSeg) * std::max<size_t>(prepared.size(), 1));
+    if (s == MGS_OK && cudaMalloc(&P->scratch, seg_bytes + 256) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("plan scratch allocation failed");
+        s = MGS_ERR_OUT_OF_MEMORY;
+    }
+    if (s == MGS_OK) {
+        cudaError_t e = cudaMemcpyAsync(P->scratch, prepared.data(),
+                                        sizeof(CostSeg) * prepared.size(), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            set_error("plan upload: %s", cudaGetErrorString(e));
+            s = MGS_ERR_CUDA;
+        }
+    }
+    if (s != MGS_OK) {
+        if (P->exec) cost_exec_destroy(P->exec);
+        if (P->scratch) cudaFree(P->scratch);
+        delete P;
+        return s;
+    }
+    cost_exec_bind(P->exec, static_cast<CostSeg *>(P->scratch),
+                   reinterpret_cast<unsigned int *>(static_cast<char *>(P->scratch) + seg_bytes));
+    *out = P;
+    return MGS_OK;
+}
+
+mgs_status mgs_plan_launch(mgs_plan *P, void *stream) {
+    clear_error();
+    if (!P) {
+        set_error("plan is NULL");
+        return MGS_ERR_INVALID_ARG;
+    }
+    DeviceGuard g(P->ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (!P->use_graph) return cost_exec_run(P->exec, st);
+    if (!P->gexec) {
+        if (st == nullptr) {
+            set_error("graph capture needs a non-default stream");
+            return MGS_ERR_INVALID_ARG;
+        }
+        MGS_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        mgs_status s = cost_exec_run(P->exec, st);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(st, &graph);
+        if (s != MGS_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return s;
+        }
+        MGS_CUDA_TRY(e);
+        P->graph = graph;
+        MGS_CUDA_TRY(cudaGraphInstantiate(&P->gexec, graph, 0));
+        count_launches(-1);   // the captured launch did not run; the replay below does
+    }
+    MGS_CUDA_TRY(cudaGraphLaunch(P->gexec, st));
+    count_launches(1);
+    return MGS_OK;
+}
+
+mgs_status mgs_plan_info(const mgs_plan *P, int64_t *work_items, int32_t *launches,
+                         int32_t *tile_config) {
+    if (!P) {
+        set_error("plan is NULL");
+        return MGS_ERR_INVALID_ARG;
+    }
+    if (work_items) *work_items = P->n_work;
+    if (launches) *launches = P->n_work > 0 ? 1 : 0;
+    if (tile_config) *tile_config = P->config;
+    return MGS_OK;
+}
+
+mgs_status mgs_plan_destroy(mgs_plan *P) {
+    clear_error();
+    if (!P) return MGS_OK;
+    DeviceGuard g(P->ctx->device);
+    cudaDeviceSynchronize();
+    if (P->gexec) cudaGraphExecDestroy(P->gexec);
+    if (P->graph) cudaGraphDestroy(P->graph);
+    if (P->exec) cost_exec_destroy(P->exec);
+    if (P->scratch) cudaFree(P->scratch);
+    delete P;
+    return MGS_OK;
+}
+
+mgs_status mgs_quantize_groups(mgs_ctx *ctx, const mgs_scene *scene, int64_t keep,
+                               int32_t group_size, const uint8_t *bits, uint16_t *codes,
+                               float *minmax, void *stream) {
+    clear_error();
+    if (!ctx || !scene || !bits || !codes || !minmax) {
+        set_error("ctx, scene, bits, codes and minmax must be non-NULL");
+        return MGS_ERR_INVALID_ARG;
+    }
+    if (keep < 1 || keep > scene->n || group_size < 1 || group_size > MGS_MAX_GROUP) {
+        set_error("keep %lld or group_size %d out of range", (long long)keep, group_size);
+        return MGS_ERR_INVALID_ARG;
+    }
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    mgs_scene *sc = const_cast<mgs_scene *>(scene);
+    // A one-ratio kept list; the scene's cached lists are left alone.
+    mgs_scene tmp_owner;
+    tmp_owner.ctx = sc->ctx;
+    tmp_owner.n = sc->n;
+    tmp_owner.C = sc->C;
+    tmp_owner.d_rank_m = sc->d_rank_m;
+    const int32_t *pos = nullptr;
+    std::vector<int64_t> off;
+    mgs_status s = scene_kept(&tmp_owner, &keep, 1, st, &pos, &off);
+    if (s == MGS_OK) s = quantize_launch(ctx, sc, pos, keep, group_size, bits, codes, minmax, st);
+    if (tmp_owner.kept.pos) cudaFreeAsync(tmp_owner.kept.pos, st);
+    tmp_owner.kept.pos = nullptr;
+    tmp_owner.d_rank_m = nullptr;
+    return s;
+}
+
+}  // extern "C"

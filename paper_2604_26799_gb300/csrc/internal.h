@@ -1,0 +1,166 @@
+// Internal declarations of the mgs library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/mgs.h"
+
+namespace mgs {
+
+// Thread-local error message behind mgs_last_error().
+void set_error(const char *fmt, ...);
+void clear_error();
+
+#define MGS_CUDA_TRY(expr)                                                                    \
+    do {                                                                                      \
+        cudaError_t e_ = (expr);                                                              \
+        if (e_ != cudaSuccess) {                                                              \
+            mgs::set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, \
+                           __LINE__);                                                         \
+            return MGS_ERR_CUDA;                                                              \
+        }                                                                                     \
+    } while (0)
+
+#define MGS_TRY(expr)                  \
+    do {                               \
+        mgs_status s_ = (expr);        \
+        if (s_ != MGS_OK) return s_;   \
+    } while (0)
+
+constexpr int kSlabWidth = 8;         // channels per slab row (32 bytes)
+constexpr int kLtabFracBits = 32;     // fixed point of L(n) = n log2 n
+constexpr int kMaxSegments = 4096;    // (scene, ratio) pairs in one batched launch
+
+// Device buffer owned by the library (stream-ordered allocation).
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+
+// Kept lists of one keep-array, cached on the scene.
+struct KeptLists {
+    std::vector<int64_t> keep;     // the K_r they were built for
+    std::vector<int64_t> offset;   // start of list r in `pos`
+    int32_t *pos = nullptr;        // concatenated Morton positions, sum_r K_r entries
+    size_t bytes = 0;
+};
+
+// Per-context tile configuration chosen for a group size.
+struct TileChoice {
+    int group_size;
+    int n_bits;
+    int config;   // index into the cost kernel's configuration table
+};
+
+}  // namespace mgs
+
+struct mgs_ctx {
+    int device = 0;
+    int sm_count = 0;
+    unsigned long long *d_ltab = nullptr;   // L(n) for n in [0, MGS_MAX_GROUP], 32.32 fixed point
+    std::mutex mu;
+    std::vector<mgs::TileChoice> tiles;     // autotuned choices
+    int forced_config = -1;                 // testing hook: force a tile configuration
+    int n_scenes = 0;
+};
+
+struct mgs_scene {
+    mgs_ctx *ctx = nullptr;
+    int64_t n = 0;
+    int32_t C = 0;
+    int32_t n_slabs = 0;
+    float *d_slabs = nullptr;     // [n_slabs][n][8] FP32, Morton order, padded channels = 0
+    int32_t *d_rank_m = nullptr;  // importance rank of the Gaussian at Morton position p
+    int32_t *d_order = nullptr;   // Gaussian index at Morton position p
+    uint64_t *d_codes = nullptr;  // Morton code of Gaussian i (index order)
+    int64_t device_bytes = 0;
+    std::mutex mu;
+    mgs::KeptLists kept;
+};
+
+namespace mgs {
+
+// ---- scene pipeline (scene.cu) ----
+mgs_status scene_build(mgs_ctx *ctx, const float *d_attrs, const float *d_imp, int64_t n, int32_t C,
+                       cudaStream_t st, mgs_scene *scene);
+// Build (or reuse) the kept lists of `keep` for the scene.
+mgs_status scene_kept(mgs_scene *scene, const int64_t *keep, int32_t n_r, cudaStream_t st,
+                      const int32_t **pos_out, std::vector<int64_t> *offset_out);
+
+// ---- cost kernels (cost.cu) ----
+struct CostSeg {
+    const float *slabs;
+    const int32_t *kept;   // Morton positions of this ratio's kept set
+    int64_t n;             // scene size (slab stride)
+    int64_t K;             // kept-set size
+    int64_t work_begin;    // first work item of this segment
+    int64_t item_base;     // table item of (r, c = 0, g = 0)
+    int32_t n_groups;
+    int32_t n_chunks;
+    int32_t C;
+    int32_t pad_;
+    double *sse;
+    double *l1;
+    double *hbits;
+    float *linf;
+    int32_t *cnt;
+    float *vmin;
+    float *vmax;
+};
+
+struct CostLaunch {
+    std::vector<CostSeg> segs;
+    int32_t group_size = 0;
+    int32_t n_bits = 0;          // options in the table
+    int32_t bits[MGS_MAX_OPTIONS] = {};
+    int32_t opt_lo = 0;          // options computed by this launch: [opt_lo, opt_hi)
+    int32_t opt_hi = 0;
+    bool persistent = false;
+};
+
+// Tile configurations of the cost kernel.
+struct CostConfig {
+    int threads;
+    int ept;      // elements per thread: threads * ept >= group size
+    int width;    // channels per work item
+    const char *name;
+};
+int cost_config_count();
+const CostConfig &cost_config(int i);
+// Default configuration for a group size (or -1).
+int cost_default_config(int group_size);
+
+// Launch the cost kernel over all segments of `L`.  d_segs is scratch for the
+// segment array (at least segs.size() entries); counter is a device uint (persistent mode).
+mgs_status cost_launch(mgs_ctx *ctx, const CostLaunch &L, int config, CostSeg *d_segs,
+                       unsigned int *d_counter, cudaStream_t st);
+size_t cost_smem_bytes(int config, int group_size, int n_opts);
+bool cost_config_fits(int config, int group_size, int n_opts);
+
+// A prepared launch: work layout, kernel arguments and shape, reusable and
+// capturable (cost_exec_run issues only a memset and a kernel launch).
+struct CostExec;
+mgs_status cost_exec_create(mgs_ctx *ctx, const CostLaunch &L, int config, CostExec **out,
+                            std::vector<CostSeg> *segs, int64_t *n_work);
+void cost_exec_bind(CostExec *X, const CostSeg *d_segs, unsigned int *d_counter);
+mgs_status cost_exec_run(const CostExec *X, cudaStream_t st);
+void cost_exec_destroy(CostExec *X);
+
+// ---- quantise one configuration (quantize.cu) ----
+mgs_status quantize_launch(mgs_ctx *ctx, const mgs_scene *scene, const int32_t *kept, int64_t keep,
+                           int32_t G, const uint8_t *bits, uint16_t *codes, float *minmax,
+                           cudaStream_t st);
+
+// ---- helpers (abi.cu) ----
+// Count kernels enqueued by this library (mgs_kernel_launches()).
+void count_launches(int64_t k);
+bool is_device_pointer(const void *p);
+int64_t n_groups_of(int64_t keep, int32_t G);
+mgs_status check_grid(const mgs_grid *grid, int64_t n);
+
+}  // namespace mgs

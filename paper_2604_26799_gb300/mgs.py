@@ -1,0 +1,323 @@
+"""Thin ctypes binding of include/mgs.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls.  Device
+buffers are torch tensors (their data_ptr is passed); host buffers are numpy
+arrays or torch CPU tensors.  Nothing here computes any step of the method:
+it all runs in libmgs.so, and importing this module fails loudly when the
+library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libmgs.so")
+
+MGS_OK = 0
+ERRORS = {-1: "INVALID_ARG", -2: "NONFINITE", -3: "RANGE", -4: "OUT_OF_MEMORY", -5: "CUDA",
+          -6: "INFEASIBLE", -7: "TIMEOUT", -8: "BUSY"}
+MGS_MAX_RATIOS = 64
+MGS_MAX_OPTIONS = 16
+MGS_RATE_ENTROPY, MGS_RATE_FIXED = 0, 1
+MGS_NORM_SSE, MGS_NORM_L2, MGS_NORM_L1, MGS_NORM_LINF = 0, 1, 2, 3
+
+
+class MgsError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{ERRORS.get(status, status)}: {message}")
+        self.status = status
+
+
+class mgs_grid(ctypes.Structure):
+    _fields_ = [("n_ratios", ctypes.c_int32), ("keep", ctypes.POINTER(ctypes.c_int64)),
+                ("n_bits", ctypes.c_int32), ("bits", ctypes.POINTER(ctypes.c_int32)),
+                ("group_size", ctypes.c_int32)]
+
+
+class mgs_table_layout(ctypes.Structure):
+    _fields_ = [("n_items", ctypes.c_int64), ("n_bits", ctypes.c_int32),
+                ("n_ratios", ctypes.c_int32), ("n_channels", ctypes.c_int32),
+                ("group_size", ctypes.c_int32),
+                ("item_begin", ctypes.c_int64 * (MGS_MAX_RATIOS + 1)),
+                ("n_groups", ctypes.c_int64 * MGS_MAX_RATIOS),
+                ("off_sse", ctypes.c_int64), ("off_l1", ctypes.c_int64),
+                ("off_hbits", ctypes.c_int64), ("off_linf", ctypes.c_int64),
+                ("off_count", ctypes.c_int64), ("off_vmin", ctypes.c_int64),
+                ("off_vmax", ctypes.c_int64), ("total_bytes", ctypes.c_int64)]
+
+
+class mgs_solve_opts(ctypes.Structure):
+    _fields_ = [("rate_model", ctypes.c_int32), ("norm", ctypes.c_int32),
+                ("const_bytes", ctypes.c_double), ("meta_bytes_per_group", ctypes.c_double),
+                ("delta_bytes", ctypes.c_double)]
+
+
+class mgs_solution(ctypes.Structure):
+    _fields_ = [("r_index", ctypes.c_int32), ("est_bytes", ctypes.c_double),
+                ("objective", ctypes.c_double), ("lp_bound", ctypes.c_double),
+                ("choice", ctypes.c_void_p), ("ratio_status", ctypes.c_void_p),
+                ("ratio_objective", ctypes.c_void_p), ("ratio_bytes", ctypes.c_void_p),
+                ("ratio_lp_bound", ctypes.c_void_p)]
+
+
+_lib = None
+
+# name -> argtypes (all return mgs_status unless listed in _RESTYPE)
+_P = ctypes.c_void_p
+_SIGS = {
+    "mgs_create": [ctypes.c_int32, ctypes.POINTER(_P)],
+    "mgs_destroy": [_P],
+    "mgs_last_error": [],
+    "mgs_version": [],
+    "mgs_kernel_launches": [],
+    "mgs_scene_create": [_P, _P, _P, ctypes.c_int64, ctypes.c_int32, _P, ctypes.POINTER(_P)],
+    "mgs_scene_destroy": [_P],
+    "mgs_scene_info": [_P, _P, _P, _P],
+    "mgs_scene_morton": [_P, _P, _P, _P],
+    "mgs_table_layout_for": [ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(mgs_grid),
+                             ctypes.POINTER(mgs_table_layout)],
+    "mgs_build_cost_table": [_P, _P, ctypes.POINTER(mgs_grid), _P, _P],
+    "mgs_build_cost_table_plain": [_P, _P, ctypes.POINTER(mgs_grid), _P, _P],
+    "mgs_build_cost_tables_batched": [_P, ctypes.c_int32, _P, ctypes.POINTER(mgs_grid), _P, _P],
+    "mgs_quantize_groups": [_P, _P, ctypes.c_int64, ctypes.c_int32, _P, _P, _P, _P],
+    "mgs_plan_create": [_P, ctypes.c_int32, _P, ctypes.POINTER(mgs_grid), _P, ctypes.c_int32, _P,
+                        ctypes.POINTER(_P)],
+    "mgs_plan_launch": [_P, _P],
+    "mgs_plan_destroy": [_P],
+    "mgs_plan_info": [_P, _P, _P, _P],
+    "mgs_tile_config_count": [],
+    "mgs_tile_config_name": [ctypes.c_int32],
+    "mgs_set_tile_config": [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32],
+    "mgs_autotune": [_P, _P, ctypes.POINTER(mgs_grid), _P, _P, _P],
+    "mgs_estimate_size": [_P, ctypes.POINTER(mgs_table_layout), ctypes.POINTER(mgs_grid),
+                          ctypes.c_int32, _P, ctypes.POINTER(mgs_solve_opts),
+                          ctypes.POINTER(ctypes.c_double)],
+    "mgs_solve_budget": [_P, ctypes.POINTER(mgs_table_layout), ctypes.POINTER(mgs_grid),
+                         ctypes.c_double, ctypes.POINTER(mgs_solve_opts),
+                         ctypes.POINTER(mgs_solution)],
+}
+_RESTYPE = {"mgs_last_error": ctypes.c_char_p, "mgs_version": ctypes.c_char_p,
+            "mgs_tile_config_name": ctypes.c_char_p, "mgs_tile_config_count": ctypes.c_int32,
+            "mgs_kernel_launches": ctypes.c_int64}
+
+
+def lib():
+    """Load libmgs.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with "
+                              "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, args in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = _RESTYPE.get(name, ctypes.c_int32)
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != MGS_OK:
+        raise MgsError(status, lib().mgs_last_error().decode(errors="replace"))
+
+
+def _ptr(x) -> int | None:
+    """Address of a torch tensor or numpy array (None for None)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Grid:
+    """Keeps the ctypes arrays of an mgs_grid alive."""
+
+    def __init__(self, keep, bits, group_size: int):
+        self.keep = np.ascontiguousarray(keep, dtype=np.int64)
+        self.bits = np.ascontiguousarray(bits, dtype=np.int32)
+        self.group_size = int(group_size)
+        self.c = mgs_grid(len(self.keep), self.keep.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                          len(self.bits), self.bits.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                          self.group_size)
+
+
+def mgs_version() -> str:
+    return lib().mgs_version().decode()
+
+
+def mgs_kernel_launches() -> int:
+    return lib().mgs_kernel_launches()
+
+
+def mgs_create(device: int = 0) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().mgs_create(device, ctypes.byref(h)))
+    return h.value
+
+
+def mgs_destroy(ctx: int):
+    _check(lib().mgs_destroy(ctx))
+
+
+def mgs_scene_create(ctx: int, attrs, importance, stream=None) -> int:
+    n, C = attrs.shape
+    h = ctypes.c_void_p()
+    _check(lib().mgs_scene_create(ctx, _ptr(attrs), _ptr(importance), n, C, _stream(stream),
+                                  ctypes.byref(h)))
+    return h.value
+
+
+def mgs_scene_destroy(scene: int):
+    _check(lib().mgs_scene_destroy(scene))
+
+
+def mgs_scene_info(scene: int) -> tuple[int, int, int]:
+    n, c, b = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int64()
+    _check(lib().mgs_scene_info(scene, ctypes.addressof(n), ctypes.addressof(c), ctypes.addressof(b)))
+    return n.value, c.value, b.value
+
+
+def mgs_scene_morton(scene: int, codes=None, order=None, stream=None):
+    _check(lib().mgs_scene_morton(scene, _ptr(codes), _ptr(order), _stream(stream)))
+
+
+def mgs_table_layout_for(n: int, n_channels: int, grid: Grid) -> mgs_table_layout:
+    L = mgs_table_layout()
+    _check(lib().mgs_table_layout_for(n, n_channels, ctypes.byref(grid.c), ctypes.byref(L)))
+    return L
+
+
+def mgs_build_cost_table(ctx: int, scene: int, grid: Grid, table, stream=None):
+    _check(lib().mgs_build_cost_table(ctx, scene, ctypes.byref(grid.c), _ptr(table), _stream(stream)))
+
+
+def mgs_build_cost_table_plain(ctx: int, scene: int, grid: Grid, table, stream=None):
+    _check(lib().mgs_build_cost_table_plain(ctx, scene, ctypes.byref(grid.c), _ptr(table),
+                                            _stream(stream)))
+
+
+def mgs_build_cost_tables_batched(ctx: int, scenes: list[int], grid: Grid, tables: list, stream=None):
+    sc = (ctypes.c_void_p * len(scenes))(*scenes)
+    tb = (ctypes.c_void_p * len(tables))(*[_ptr(t) for t in tables])
+    _check(lib().mgs_build_cost_tables_batched(ctx, len(scenes), sc, ctypes.byref(grid.c), tb,
+                                               _stream(stream)))
+
+
+def mgs_quantize_groups(ctx: int, scene: int, keep: int, group_size: int, bits, codes, minmax,
+                        stream=None):
+    _check(lib().mgs_quantize_groups(ctx, scene, keep, group_size, _ptr(bits), _ptr(codes),
+                                     _ptr(minmax), _stream(stream)))
+
+
+def mgs_plan_create(ctx: int, scenes: list[int], grid: Grid, tables: list, use_graph: bool = False,
+                    stream=None) -> int:
+    sc = (ctypes.c_void_p * len(scenes))(*scenes)
+    tb = (ctypes.c_void_p * len(tables))(*[_ptr(t) for t in tables])
+    h = ctypes.c_void_p()
+    _check(lib().mgs_plan_create(ctx, len(scenes), sc, ctypes.byref(grid.c), tb, int(use_graph),
+                                 _stream(stream), ctypes.byref(h)))
+    return h.value
+
+
+def mgs_plan_launch(plan: int, stream=None):
+    _check(lib().mgs_plan_launch(plan, _stream(stream)))
+
+
+def mgs_plan_destroy(plan: int):
+    _check(lib().mgs_plan_destroy(plan))
+
+
+def mgs_plan_info(plan: int) -> tuple[int, int, int]:
+    w, l, c = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().mgs_plan_info(plan, ctypes.addressof(w), ctypes.addressof(l), ctypes.addressof(c)))
+    return w.value, l.value, c.value
+
+
+def mgs_tile_config_count() -> int:
+    return lib().mgs_tile_config_count()
+
+
+def mgs_tile_config_name(i: int) -> str:
+    return lib().mgs_tile_config_name(i).decode()
+
+
+def mgs_set_tile_config(ctx: int, group_size: int, n_bits: int, config: int):
+    _check(lib().mgs_set_tile_config(ctx, group_size, n_bits, config))
+
+
+def mgs_autotune(ctx: int, scene: int, grid: Grid, stream=None) -> tuple[int, np.ndarray]:
+    chosen = ctypes.c_int32(-1)
+    ms = np.full(mgs_tile_config_count(), -1.0, dtype=np.float32)
+    _check(lib().mgs_autotune(ctx, scene, ctypes.byref(grid.c), _stream(stream),
+                              ctypes.addressof(chosen), ms.ctypes.data))
+    return chosen.value, ms
+
+
+def solve_opts(rate_model: int = MGS_RATE_ENTROPY, norm: int = MGS_NORM_SSE,
+               const_bytes: float = 0.0, meta_bytes_per_group: float = 9.0,
+               delta_bytes: float = 0.0) -> mgs_solve_opts:
+    return mgs_solve_opts(rate_model, norm, const_bytes, meta_bytes_per_group, delta_bytes)
+
+
+def mgs_estimate_size(table_host, layout: mgs_table_layout, grid: Grid, r_index: int, choice,
+                      opts: mgs_solve_opts) -> float:
+    out = ctypes.c_double()
+    ch = np.ascontiguousarray(choice, dtype=np.uint8)
+    _check(lib().mgs_estimate_size(_ptr(table_host), ctypes.byref(layout), ctypes.byref(grid.c),
+                                   r_index, ch.ctypes.data, ctypes.byref(opts), ctypes.byref(out)))
+    return out.value
+
+
+def mgs_solve_budget(table_host, layout: mgs_table_layout, grid: Grid, budget_bytes: float,
+                     opts: mgs_solve_opts) -> dict:
+    nr = layout.n_ratios
+    max_items = max(int(layout.item_begin[r + 1] - layout.item_begin[r]) for r in range(nr))
+    choice = np.zeros(max(max_items, 1), dtype=np.uint8)
+    st = np.zeros(nr, dtype=np.int32)
+    obj = np.zeros(nr)
+    byt = np.zeros(nr)
+    lp = np.zeros(nr)
+    sol = mgs_solution(-1, 0.0, 0.0, 0.0, choice.ctypes.data, st.ctypes.data, obj.ctypes.data,
+                       byt.ctypes.data, lp.ctypes.data)
+    rc = lib().mgs_solve_budget(_ptr(table_host), ctypes.byref(layout), ctypes.byref(grid.c),
+                                float(budget_bytes), ctypes.byref(opts), ctypes.byref(sol))
+    if rc not in (MGS_OK, -6):
+        _check(rc)
+    r = sol.r_index
+    n_items = int(layout.item_begin[r + 1] - layout.item_begin[r]) if r >= 0 else 0
+    return dict(status=rc, r_index=r, est_bytes=sol.est_bytes, objective=sol.objective,
+                lp_bound=sol.lp_bound, choice=choice[:n_items].copy(), ratio_status=st,
+                ratio_objective=obj, ratio_bytes=byt, ratio_lp_bound=lp)
+
+
+def table_views(buf, layout: mgs_table_layout) -> dict:
+    """Typed views of a table buffer (torch uint8 tensor or numpy uint8 array)."""
+    ni, nb = int(layout.n_items), int(layout.n_bits)
+
+    def view(off, count, dtype, shape):
+        if isinstance(buf, np.ndarray):
+            return buf[off:off + count * np.dtype(dtype).itemsize].view(dtype).reshape(shape)
+        import torch
+        tdt = {np.float64: torch.float64, np.float32: torch.float32, np.int32: torch.int32}[dtype]
+        return buf[off:off + count * np.dtype(dtype).itemsize].view(tdt).reshape(shape)
+
+    return dict(sse=view(layout.off_sse, ni * nb, np.float64, (ni, nb)),
+                l1=view(layout.off_l1, ni * nb, np.float64, (ni, nb)),
+                hbits=view(layout.off_hbits, ni * nb, np.float64, (ni, nb)),
+                linf=view(layout.off_linf, ni * nb, np.float32, (ni, nb)),
+                cnt=view(layout.off_count, ni, np.int32, (ni,)),
+                vmin=view(layout.off_vmin, ni, np.float32, (ni,)),
+                vmax=view(layout.off_vmax, ni, np.float32, (ni,)))
