@@ -260,6 +260,15 @@ def run_gpu(args):
             kernel_ms.append(e[2].elapsed_time(e[3]))
         return sol
 
+    # pick the tile shape for this grid on this GPU (one-time, before the timed region)
+    tune = None
+    if not args.no_autotune:
+        sc = mgs.mgs_scene_create(ctx, attrs_d, imp_d, stream=st)
+        chosen, ms_cfg = mgs.mgs_autotune(ctx, sc, grid, stream=st)
+        mgs.mgs_scene_destroy(sc)
+        tune = {"chosen": mgs.mgs_tile_config_name(chosen),
+                "ms": {mgs.mgs_tile_config_name(i): round(float(t), 3)
+                       for i, t in enumerate(ms_cfg) if t > 0}}
     for _ in range(args.warmup):
         sol = step(False)
     torch.cuda.synchronize()
@@ -367,6 +376,7 @@ def run_gpu(args):
                     "h2d_bytes_per_step": int(attrs_h.numel() * 4 + imp_h.numel() * 4),
                     "d2h_bytes_per_step": int(L.total_bytes), "ms_per_step": e2e_ms},
             "gpu_launches": int(launches),
+            "autotune": tune,
             "clocks": clocks,
             "cpu_baseline": cpu,
         }
@@ -386,7 +396,15 @@ def main():
     ap.add_argument("--impl", default="mgs", choices=["mgs", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-loop comparator")
+    ap.add_argument("--no-autotune", action="store_true", help="use the default tile shape")
+    ap.add_argument("--n", type=int, default=None,
+                    help="scene size override (smaller cases for profiling; default 5,270,000)")
     args = ap.parse_args()
+    if args.n is not None:
+        global WORKLOAD
+        import dataclasses
+        WORKLOAD = dataclasses.replace(synth.SCENE, n=args.n,
+                                       name=synth.SCENE.name.replace("N=5.27M", f"N={args.n}"))
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

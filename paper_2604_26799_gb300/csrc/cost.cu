@@ -10,17 +10,34 @@
 //   x = fl(fl(c / S) + Z),  q = rint(min(max(x, 0), 2^b - 1))
 //   c_hat = fl(fl(q - Z) * S),  e = fl(c_hat - c)
 //
-// When S is a normal float, S = R * 2^-b exactly, so fl(c / S) = fl(c / R) * 2^b
-// whenever fl(c / R) is normal or zero; the kernel divides once per element
-// (u = fl(c / R)) and forms x = fma(u, 2^b, Z), which is the same single
-// rounding of the same exact sum.  Groups with a subnormal |u| or a subnormal S
-// take the literal division per element and bit-width.
+// Exact reformulations used on the fast path (each gives the same FP32 bits):
+//  * When S is normal, S = R * 2^-b exactly, so fl(c / S) = fl(c / R) * 2^b
+//    whenever u = fl(c / R) is normal or zero: one division per element serves
+//    every bit-width, and x = fma(u, 2^b, Z) is the same single rounding.
+//  * rint(x) for |x| < 2^22 is fl(x + 1.5 * 2^23) - 1.5 * 2^23; the code sits in
+//    the low mantissa bits of y = fl(x + 1.5 * 2^23), which also address the
+//    histogram.  Clamping y to [1.5 * 2^23, 1.5 * 2^23 + 2^b - 1] equals rounding
+//    the clamped x (the bounds are integers), and fl(q - Z) = fl(y - (1.5 * 2^23 + Z))
+//    when |Z| < 2^22 (the second operand is then an exact integer).
+//  * x is monotone in c, so if the group minimum does not round below 0 no
+//    element does, and the lower clamp is skipped.
+//  * Packed f32x2 adds, subtracts and FMAs are used where no contraction can
+//    arise; the reconstruction product stays a scalar multiply.
+//  * Each channel is scaled by an exact power of two 2^k (R * 2^k in [1, 2)):
+//    c' = c 2^k, S' = S 2^k give c'/S' = c/S and e' = e 2^k exactly, so squares
+//    and sums stay in the normal FP32 range; the sums are rescaled in FP64.
+// Groups where a precondition fails (subnormal S or u, |Z| >= 2^22) take the
+// literal per-element formula.  Pairs of elements use packed f32x2 arithmetic.
 //
-// Histograms live in shared memory: per-lane columns for b <= 6 (no
-// same-address conflicts inside a warp), a direct table for 7 <= b <= 12, and
-// an open-addressing hash of (code, count) for b >= 13.  The entropy bound is
-// accumulated as L(n) - sum L(h) with L(h) = h log2 h in 32.32 fixed point, so
-// it does not depend on the reduction order.
+// Histograms live in shared memory, double-buffered so one barrier per
+// bit-width suffices: per-lane columns for b <= 6 and a direct table for
+// b <= 10 (summed after the pass); for larger b the atomic returns the old
+// count j - 1 and the thread adds delta(j) = L(j) - L(j - 1), L(h) = h log2 h in
+// 32.32 fixed point, so sum_j delta telescopes to sum_bins L(h) with no scan
+// (direct 32-bit counters, 16-bit counter pairs, or an open-addressing hash of
+// (code, count) when 2^b exceeds the table).  Entropy sums are integers, so
+// they do not depend on the reduction order.
+
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -32,15 +49,23 @@ namespace mgs {
 namespace {
 
 constexpr uint32_t kFull = 0xFFFFFFFFu;
-constexpr int kDirectMaxBits = 12;
+constexpr float kMagic = 12582912.0f;          // 1.5 * 2^23
+constexpr uint32_t kMagicBits = 0x4B400000u;   // its bit pattern
 constexpr int kLaneMaxBits = 6;
+constexpr int kDirectMaxBits = 10;
+
+enum HistMode { kLane = 0, kDirect = 1, kDelta32 = 2, kDelta16 = 3, kHash = 4 };
+enum Path { kFast = 0, kFastBottom = 1, kGeneric = 2, kDegenerate = 3 };
 
 struct BitParam {
-    float S, Z, twob, top;
-    float Ss;      // S * 2^k: the step in the group's scaled units (exact)
+    float S, Ss, Z, twob;
+    float MZ;     // 1.5 * 2^23 + Z (exact when |Z| < 2^22)
+    float ytop;   // 1.5 * 2^23 + 2^b - 1
+    float top;    // 2^b - 1
     int b;
-    int literal;   // 1: divide per element and bit-width
-    int degenerate;
+    int mode;
+    int path;
+    int pad[2];
 };
 
 struct KernelArgs {
@@ -51,111 +76,237 @@ struct KernelArgs {
     int32_t n_bits;
     int32_t opt_lo, opt_hi;
     int32_t bits[MGS_MAX_OPTIONS];
-    const unsigned long long *ltab;
+    const unsigned long long *ltab;   // L(h)
+    const unsigned long long *dtab;   // L(h) - L(h - 1)
     unsigned int *counter;
-    uint32_t hash_log2;   // log2 of the hash capacity
+    int32_t hist_words;               // words per histogram buffer (power of two)
+    int32_t double_buffer;
 };
 
-__device__ __forceinline__ uint32_t hash_slot(uint32_t q, uint32_t log2cap) {
-    return (q * 2654435769u) >> (32 - log2cap);
+// ---- packed FP32 pairs ----------------------------------------------------
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+        "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+#define MGS_F2_BINOP(NAME, OP)                                                            \
+    __device__ __forceinline__ float2 NAME(float2 a, float2 b) {                          \
+        float2 d;                                                                         \
+        asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t" \
+            OP " rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"                                 \
+            : "=f"(d.x), "=f"(d.y)                                                        \
+            : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));                                    \
+        return d;                                                                         \
+    }
+MGS_F2_BINOP(fadd2, "add.rn.f32x2")
+MGS_F2_BINOP(fsub2, "sub.rn.f32x2")
+#undef MGS_F2_BINOP
+
+// ---- shared-memory histogram operations ------------------------------------
+__device__ __forceinline__ void red_add(uint32_t addr, uint32_t v) {
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t atom_add(uint32_t addr, uint32_t v) {
+    uint32_t old;
+    asm volatile("atom.shared.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(addr), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ uint32_t atom_cas(uint32_t addr, uint32_t cmp, uint32_t v) {
+    uint32_t old;
+    asm volatile("atom.shared.cas.b32 %0, [%1], %2, %3;" : "=r"(old) : "r"(addr), "r"(cmp), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ uint32_t lds(uint32_t addr) {
+    uint32_t v;
+    asm volatile("ld.volatile.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+    return v;
 }
 
-// Histogram update for one code.
+// Count one code.  y is the code's bit pattern kMagicBits + q.  For the delta
+// modes the return is delta(new count) to be added to the entropy sum.
 template <int MODE>
-__device__ __forceinline__ void hist_add(uint32_t *hist, uint32_t q, int lane, uint32_t log2cap) {
-    if (MODE == 0) {
-        atomicAdd(&hist[q * 32u + lane], 1u);
-    } else if (MODE == 1) {
-        atomicAdd(&hist[q], 1u);
+__device__ __forceinline__ void hist_op(uint32_t y, uint32_t hbase, uint32_t lane_base,
+                                        uint32_t log2cap, const unsigned long long *dtab,
+                                        unsigned long long &hacc) {
+    if (MODE == kLane) {
+        red_add(lane_base + (y << 7), 1u);           // (q * 32 + lane) * 4, magic folded in
+    } else if (MODE == kDirect) {
+        red_add(hbase + (y << 2), 1u);               // q * 4, magic folded in
+    } else if (MODE == kDelta32) {
+        uint32_t old = atom_add(hbase + (y << 2), 1u);
+        hacc += __ldg(&dtab[old + 1u]);
+    } else if (MODE == kDelta16) {
+        const uint32_t q = y - kMagicBits;
+        const uint32_t sh = (q & 1u) << 4;
+        uint32_t old = atom_add(hbase + ((q >> 1) << 2), 1u << sh);
+        hacc += __ldg(&dtab[((old >> sh) & 0xFFFFu) + 1u]);
     } else {
         // slot word: (q + 1) << 15 | count, count < 2^15
+        const uint32_t q = y - kMagicBits;
         const uint32_t key = (q + 1u) << 15;
         const uint32_t mask = (1u << log2cap) - 1u;
-        uint32_t s = hash_slot(q, log2cap);
-        volatile uint32_t *vh = hist;
+        uint32_t s = (q * 2654435769u) >> (32 - log2cap);
+        uint32_t cnt;
         while (true) {
-            uint32_t v = vh[s];
+            const uint32_t a = hbase + (s << 2);
+            uint32_t v = lds(a);
             if (v == 0u) {
-                uint32_t old = atomicCAS(&hist[s], 0u, key | 1u);
-                if (old == 0u) break;
-                v = old;
+                v = atom_cas(a, 0u, key | 1u);
+                if (v == 0u) {
+                    cnt = 0u;
+                    break;
+                }
             }
             if ((v & ~0x7FFFu) == key) {
-                atomicAdd(&hist[s], 1u);
+                cnt = atom_add(a, 1u) & 0x7FFFu;
                 break;
             }
             s = (s + 1u) & mask;
         }
+        hacc += __ldg(&dtab[cnt + 1u]);
     }
 }
 
-// Evaluate one bit-width for this thread's elements of one channel.  c holds
-// the values scaled by 2^k (exact), so err, its square and sums stay in the
-// normal FP32 range whatever the magnitude of the channel.
-template <int T, int EPT, int MODE, bool LITERAL>
-__device__ __forceinline__ void eval_bits(const float (&c)[EPT], const float (&u)[EPT], int nvalid,
-                                          const BitParam &p, uint32_t *hist, uint32_t log2cap,
-                                          float &sse, float &l1, float &linf) {
-    const int lane = threadIdx.x & 31;
+// Fast path for one bit-width over this thread's elements (pairs, packed).
+template <int T, int EPT, int MODE, bool BOTTOM, bool FULL>
+__device__ __forceinline__ void eval_fast(const float (&c)[EPT], const float (&u)[EPT], int nvalid,
+                                          const BitParam &p, uint32_t hbase, uint32_t lane_base,
+                                          uint32_t log2cap, const unsigned long long *dtab,
+                                          float &sse, float &l1, float &linf,
+                                          unsigned long long &hacc) {
+    const float2 tw = make_float2(p.twob, p.twob), zz = make_float2(p.Z, p.Z);
+    const float2 mg = make_float2(kMagic, kMagic), mz = make_float2(p.MZ, p.MZ);
+    float2 s2 = make_float2(0.0f, 0.0f);
+    float la = 0.0f, lb = 0.0f, ma = 0.0f, mb = 0.0f;
 #pragma unroll
-    for (int e = 0; e < EPT; e++) {
-        if (e * T + (int)threadIdx.x < nvalid) {
-            float x;
-            if (LITERAL) {
-                x = __fadd_rn(__fdiv_rn(c[e], p.Ss), p.Z);   // c' / S' == c / S exactly
-            } else {
-                x = __fmaf_rn(u[e], p.twob, p.Z);
+    for (int e = 0; e < EPT; e += 2) {
+        const bool v1 = FULL || (e + 1) * T + (int)threadIdx.x < nvalid;
+        const bool v0 = FULL || e * T + (int)threadIdx.x < nvalid;
+        if (v1) {
+            float2 x = ffma2(make_float2(u[e], u[e + 1]), tw, zz);
+            float2 y = fadd2(x, mg);
+            y.x = fminf(y.x, p.ytop);
+            y.y = fminf(y.y, p.ytop);
+            if (BOTTOM) {
+                y.x = fmaxf(y.x, kMagic);
+                y.y = fmaxf(y.y, kMagic);
             }
-            float xc = fminf(fmaxf(x, 0.0f), p.top);
-            int q = __float2int_rn(xc);
-            float qz = __fsub_rn(__int2float_rn(q), p.Z);
-            float chat = __fmul_rn(qz, p.Ss);                 // c_hat * 2^k
-            float err = __fsub_rn(chat, c[e]);                // e * 2^k
-            sse = __fmaf_rn(err, err, sse);
-            l1 = __fadd_rn(l1, fabsf(err));
-            linf = fmaxf(linf, fabsf(err));
-            hist_add<MODE>(hist, (uint32_t)q, lane, log2cap);
+            // c_hat' = fl(fl(q - Z) * S'): scalar multiplies, so the product is rounded on
+            // its own and never contracted with the subtraction that follows
+            const float2 d = fsub2(y, mz);
+            const float2 ch = make_float2(__fmul_rn(d.x, p.Ss), __fmul_rn(d.y, p.Ss));
+            float2 er = fsub2(ch, make_float2(c[e], c[e + 1]));
+            s2 = ffma2(er, er, s2);
+            la = __fadd_rn(la, fabsf(er.x));
+            lb = __fadd_rn(lb, fabsf(er.y));
+            ma = fmaxf(ma, fabsf(er.x));
+            mb = fmaxf(mb, fabsf(er.y));
+            hist_op<MODE>(__float_as_uint(y.x), hbase, lane_base, log2cap, dtab, hacc);
+            hist_op<MODE>(__float_as_uint(y.y), hbase, lane_base, log2cap, dtab, hacc);
+        } else if (v0) {
+            float x = __fmaf_rn(u[e], p.twob, p.Z);
+            float y = __fadd_rn(x, kMagic);
+            y = fminf(y, p.ytop);
+            if (BOTTOM) y = fmaxf(y, kMagic);
+            float er = __fsub_rn(__fmul_rn(__fsub_rn(y, p.MZ), p.Ss), c[e]);
+            s2.x = __fmaf_rn(er, er, s2.x);
+            la = __fadd_rn(la, fabsf(er));
+            ma = fmaxf(ma, fabsf(er));
+            hist_op<MODE>(__float_as_uint(y), hbase, lane_base, log2cap, dtab, hacc);
         }
     }
+    sse = __fadd_rn(s2.x, s2.y);
+    l1 = __fadd_rn(la, lb);
+    linf = fmaxf(ma, mb);
 }
 
-// Sum of L(h) over the histogram of one bit-width, clearing it.
-template <int T, int MODE>
-__device__ __forceinline__ unsigned long long hist_scan(uint32_t *hist, int b, uint32_t log2cap,
-                                                        const unsigned long long *__restrict__ ltab) {
-    unsigned long long acc = 0;
+// Literal per-element formula (divisions, both clamps); any group.
+template <int T, int EPT, int MODE>
+__device__ __forceinline__ void eval_generic(const float (&c)[EPT], int nvalid, const BitParam &p,
+                                          uint32_t hbase, uint32_t lane_base, uint32_t log2cap,
+                                          const unsigned long long *dtab, float &sse, float &l1,
+                                          float &linf, unsigned long long &hacc) {
+    float s = 0.0f, a = 0.0f, m = 0.0f;
+#pragma unroll
+    for (int e = 0; e < EPT; e++) {
+        if (e * T + (int)threadIdx.x >= nvalid) continue;
+        float x = __fadd_rn(__fdiv_rn(c[e], p.Ss), p.Z);   // c'/S' == c/S exactly
+        float xc = fminf(fmaxf(x, 0.0f), p.top);
+        int q = __float2int_rn(xc);
+        float qz = __fsub_rn(__int2float_rn(q), p.Z);
+        float er = __fsub_rn(__fmul_rn(qz, p.Ss), c[e]);
+        s = __fmaf_rn(er, er, s);
+        a = __fadd_rn(a, fabsf(er));
+        m = fmaxf(m, fabsf(er));
+        hist_op<MODE>(kMagicBits + (uint32_t)q, hbase, lane_base, log2cap, dtab, hacc);
+    }
+    sse = s;
+    l1 = a;
+    linf = m;
+}
+
+template <int T, int EPT, int MODE>
+__device__ __forceinline__ void eval_dispatch(const float (&c)[EPT], const float (&u)[EPT],
+                                              int nvalid, bool full, bool generic,
+                                              const BitParam &p, uint32_t hbase,
+                                              uint32_t lane_base, uint32_t log2cap,
+                                              const unsigned long long *dtab, float &sse,
+                                              float &l1, float &linf, unsigned long long &hacc) {
+    if (generic) {
+        eval_generic<T, EPT, MODE>(c, nvalid, p, hbase, lane_base, log2cap, dtab, sse, l1, linf, hacc);
+    } else if (p.path == kFast) {
+        if (full) eval_fast<T, EPT, MODE, false, true>(c, u, nvalid, p, hbase, lane_base, log2cap, dtab, sse, l1, linf, hacc);
+        else eval_fast<T, EPT, MODE, false, false>(c, u, nvalid, p, hbase, lane_base, log2cap, dtab, sse, l1, linf, hacc);
+    } else {
+        if (full) eval_fast<T, EPT, MODE, true, true>(c, u, nvalid, p, hbase, lane_base, log2cap, dtab, sse, l1, linf, hacc);
+        else eval_fast<T, EPT, MODE, true, false>(c, u, nvalid, p, hbase, lane_base, log2cap, dtab, sse, l1, linf, hacc);
+    }
+}
+
+// After a pass: add sum L(h) of a summed mode to hacc and clear the buffer.
+template <int T>
+__device__ __forceinline__ void hist_finish(uint32_t *hist, int mode, int b, int hist_words,
+                                            const unsigned long long *__restrict__ ltab,
+                                            unsigned long long &hacc) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (MODE == 0) {
+    if (mode == kLane) {
         const int bins = 1 << b;
         for (int k = warp; k < bins; k += T / 32) {
             uint32_t v = hist[k * 32 + lane];
             hist[k * 32 + lane] = 0u;
             uint32_t s = __reduce_add_sync(kFull, v);
-            if (lane == 0 && s) acc += __ldg(&ltab[s]);
+            if (lane == 0 && s) hacc += __ldg(&ltab[s]);
         }
-    } else if (MODE == 1) {
+    } else if (mode == kDirect) {
         const int bins = 1 << b;
+#pragma unroll 4
         for (int k = threadIdx.x; k < bins; k += T) {
             uint32_t v = hist[k];
             if (v) {
-                acc += __ldg(&ltab[v]);
+                hacc += __ldg(&ltab[v]);
                 hist[k] = 0u;
             }
         }
     } else {
-        const int cap = 1 << log2cap;
-        for (int k = threadIdx.x; k < cap; k += T) {
-            uint32_t v = hist[k];
-            if (v) {
-                acc += __ldg(&ltab[v & 0x7FFFu]);
-                hist[k] = 0u;
-            }
-        }
+        int words = mode == kDelta32 ? (1 << b) : (mode == kDelta16 ? (1 << (b - 1)) : hist_words);
+        uint4 *h4 = reinterpret_cast<uint4 *>(hist);
+        for (int k = threadIdx.x; k < words / 4; k += T) h4[k] = make_uint4(0u, 0u, 0u, 0u);
     }
-    return acc;
 }
 
-template <int T>
+__device__ __forceinline__ unsigned long long warp_sum_u64_redux(unsigned long long v) {
+    // three 22-bit slices, each summed exactly with redux.sync
+    uint32_t lo = (uint32_t)(v & 0x3FFFFFull), mid = (uint32_t)((v >> 22) & 0x3FFFFFull),
+             hi = (uint32_t)(v >> 44);
+    lo = __reduce_add_sync(kFull, lo);
+    mid = __reduce_add_sync(kFull, mid);
+    hi = __reduce_add_sync(kFull, hi);
+    return (unsigned long long)lo + ((unsigned long long)mid << 22) + ((unsigned long long)hi << 44);
+}
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = __fadd_rn(v, __shfl_xor_sync(kFull, v, o));
@@ -169,11 +320,6 @@ __device__ __forceinline__ float warp_max(float v) {
 __device__ __forceinline__ float warp_min(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(kFull, v, o));
-    return v;
-}
-__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
     return v;
 }
 
@@ -195,45 +341,30 @@ __device__ __forceinline__ void load_row(const float *p, float (&v)[W]) {
     }
 }
 
-// Shared-memory layout (dynamic): hist | psse | pl1 | plinf | hpart | params | minmax
+// Shared-memory layout (dynamic):
+//   hist[nbuf][hist_words] | psse[n_opts][T] | pl1[n_opts][T] | hpart[n_opts][T/32] (u64)
+//   | plinf[n_opts][T/32] | bp[n_opts] | mm[T/32][W][2]
 struct Smem {
     uint32_t *hist;
-    float *psse, *pl1, *plinf;            // [n_opts][T]
-    unsigned long long *hpart;            // [n_opts][T/32]
-    BitParam *bp;                         // [n_opts]
-    float *mm;                            // [T/32][W][2]
-    int *misc;                            // [4]
+    float *psse, *pl1, *plinf;
+    unsigned long long *hpart;
+    BitParam *bp;
+    float *mm;
 };
 
-template <int T, int W>
-__device__ __forceinline__ Smem carve(unsigned char *base, int hist_words, int n_opts) {
-    Smem s;
+__host__ __device__ inline size_t smem_layout(int T, int W, int hist_words, int nbuf, int n_opts,
+                                              size_t *o) {
     size_t off = 0;
-    s.hist = reinterpret_cast<uint32_t *>(base + off);
-    off += (size_t)hist_words * 4;
-    s.psse = reinterpret_cast<float *>(base + off);
-    off += (size_t)n_opts * T * 4;
-    s.pl1 = reinterpret_cast<float *>(base + off);
-    off += (size_t)n_opts * T * 4;
-    s.plinf = reinterpret_cast<float *>(base + off);
-    off += (size_t)n_opts * T * 4;
+    o[0] = off; off += (size_t)nbuf * hist_words * 4;
+    o[1] = off; off += (size_t)n_opts * T * 4;
+    o[2] = off; off += (size_t)n_opts * T * 4;
     off = (off + 15) & ~(size_t)15;
-    s.hpart = reinterpret_cast<unsigned long long *>(base + off);
-    off += (size_t)n_opts * (T / 32) * 8;
-    s.bp = reinterpret_cast<BitParam *>(base + off);
-    off += (size_t)n_opts * sizeof(BitParam);
-    s.mm = reinterpret_cast<float *>(base + off);
-    off += (size_t)(T / 32) * W * 2 * 4;
-    s.misc = reinterpret_cast<int *>(base + off);
-    return s;
-}
-
-__host__ __device__ inline int hist_words_for(int G, int hash_log2) {
-    int lane_words = (1 << kLaneMaxBits) * 32;
-    int direct_words = 1 << kDirectMaxBits;
-    int hash_words = 1 << hash_log2;
-    int w = lane_words > direct_words ? lane_words : direct_words;
-    return w > hash_words ? w : hash_words;
+    o[3] = off; off += (size_t)n_opts * (T / 32) * 8;
+    o[4] = off; off += (size_t)n_opts * (T / 32) * 4;
+    off = (off + 15) & ~(size_t)15;
+    o[5] = off; off += (size_t)n_opts * sizeof(BitParam);
+    o[6] = off; off += (size_t)(T / 32) * W * 2 * 4;
+    return off;
 }
 
 template <int T, int EPT, int W>
@@ -260,6 +391,7 @@ __device__ void process_item(const KernelArgs &A, const Smem &sm, int64_t work) 
     const int j0 = c0 % kSlabWidth;
     const int64_t gstart = (int64_t)g * A.G;
     const int nvalid = (int)((S.K - gstart) < (int64_t)A.G ? (S.K - gstart) : (int64_t)A.G);
+    const bool full = nvalid >= T * EPT;
 
     // ---- gather: each element's W channels from its slab row
     float v[W][EPT];
@@ -279,25 +411,21 @@ __device__ void process_item(const KernelArgs &A, const Smem &sm, int64_t work) 
     }
 
     // ---- group min / max of every channel of the chunk
-    {
-        float mn[W], mx[W];
 #pragma unroll
-        for (int w = 0; w < W; w++) {
-            mn[w] = FLT_MAX;
-            mx[w] = -FLT_MAX;
+    for (int w = 0; w < W; w++) {
+        float mn = FLT_MAX, mx = -FLT_MAX;
 #pragma unroll
-            for (int e = 0; e < EPT; e++) {
-                if (e * T + (int)threadIdx.x < nvalid) {
-                    mn[w] = fminf(mn[w], v[w][e]);
-                    mx[w] = fmaxf(mx[w], v[w][e]);
-                }
+        for (int e = 0; e < EPT; e++) {
+            if (e * T + (int)threadIdx.x < nvalid) {
+                mn = fminf(mn, v[w][e]);
+                mx = fmaxf(mx, v[w][e]);
             }
-            mn[w] = warp_min(mn[w]);
-            mx[w] = warp_max(mx[w]);
-            if (lane == 0) {
-                sm.mm[(warp * W + w) * 2] = mn[w];
-                sm.mm[(warp * W + w) * 2 + 1] = mx[w];
-            }
+        }
+        mn = warp_min(mn);
+        mx = warp_max(mx);
+        if (lane == 0) {
+            sm.mm[(warp * W + w) * 2] = mn;
+            sm.mm[(warp * W + w) * 2 + 1] = mx;
         }
     }
     __syncthreads();
@@ -314,6 +442,9 @@ __device__ void process_item(const KernelArgs &A, const Smem &sm, int64_t work) 
     __syncthreads();
 
     const int n_opts = A.opt_hi - A.opt_lo;
+    const int hw = A.hist_words;
+    const uint32_t log2cap = 31 - __clz(hw);
+    const uint32_t hist_addr = (uint32_t)__cvta_generic_to_shared(sm.hist);
 #pragma unroll 1
     for (int w = 0; w < W; w++) {
         const int ch = c0 + w;
@@ -330,16 +461,29 @@ __device__ void process_item(const KernelArgs &A, const Smem &sm, int64_t work) 
             p.b = A.bits[A.opt_lo + threadIdx.x];
             p.twob = (float)(1u << p.b);
             p.top = p.twob - 1.0f;
+            p.ytop = kMagic + p.top;
             p.S = __fdiv_rn(R, p.twob);
             p.Ss = __fmul_rn(__fmul_rn(p.S, s1), s2);
-            p.degenerate = p.S == 0.0f;
-            if (!p.degenerate) {
-                float t = __fdiv_rn(M, p.S);
-                p.Z = rintf(__fsub_rn(p.twob, t));
-            } else {
+            p.mode = p.b <= kLaneMaxBits ? kLane
+                   : p.b <= kDirectMaxBits ? kDirect
+                   : (1 << p.b) <= hw ? kDelta32
+                   : (1 << (p.b - 1)) <= hw ? kDelta16 : kHash;
+            if (p.S == 0.0f) {
+                p.path = kDegenerate;
                 p.Z = 0.0f;
+                p.MZ = kMagic;
+            } else {
+                p.Z = rintf(__fsub_rn(p.twob, __fdiv_rn(M, p.S)));
+                p.MZ = __fadd_rn(kMagic, p.Z);
+                if (p.S < FLT_MIN || fabsf(p.Z) >= 4194304.0f) {
+                    p.path = kGeneric;
+                } else {
+                    // the group minimum gives the smallest x: lower clamp only if it rounds below 0
+                    float um = __fdiv_rn(m, R);
+                    float ym = __fadd_rn(__fmaf_rn(um, p.twob, p.Z), kMagic);
+                    p.path = ym < kMagic ? kFastBottom : kFast;
+                }
             }
-            p.literal = p.S < FLT_MIN;
             sm.bp[threadIdx.x] = p;
         }
         if (threadIdx.x == 0) {
@@ -365,59 +509,67 @@ __device__ void process_item(const KernelArgs &A, const Smem &sm, int64_t work) 
             slow |= (u[e] != 0.0f && fabsf(u[e]) <= FLT_MIN && e * T + (int)threadIdx.x < nvalid);
             cw[e] = __fmul_rn(__fmul_rn(cw[e], s1), s2);
         }
-        const int any_slow = __syncthreads_or(slow);
+        const int any_slow = __syncthreads_or(slow);   // also publishes bp
 
 #pragma unroll 1
         for (int k = 0; k < n_opts; k++) {
             const BitParam p = sm.bp[k];
+            const int buf = A.double_buffer ? (k & 1) : 0;
+            uint32_t *hist = sm.hist + (size_t)buf * hw;
+            const uint32_t hbase_raw = hist_addr + (uint32_t)buf * hw * 4u;
             float sse = 0.0f, l1 = 0.0f, linf = 0.0f;
-            if (p.degenerate) {
-                sm.psse[k * T + threadIdx.x] = 0.0f;
-                sm.pl1[k * T + threadIdx.x] = 0.0f;
-                sm.plinf[k * T + threadIdx.x] = 0.0f;
-                if (lane == 0) sm.hpart[k * NW + warp] = warp == 0 ? __ldg(&A.ltab[nvalid]) : 0ull;
-                continue;
-            }
-            const int mode = p.b <= kLaneMaxBits ? 0 : (p.b <= kDirectMaxBits ? 1 : 2);
-            const bool lit = p.literal || any_slow;
-            if (mode == 0) {
-                if (lit) eval_bits<T, EPT, 0, true>(cw, u, nvalid, p, sm.hist, A.hash_log2, sse, l1, linf);
-                else eval_bits<T, EPT, 0, false>(cw, u, nvalid, p, sm.hist, A.hash_log2, sse, l1, linf);
-            } else if (mode == 1) {
-                if (lit) eval_bits<T, EPT, 1, true>(cw, u, nvalid, p, sm.hist, A.hash_log2, sse, l1, linf);
-                else eval_bits<T, EPT, 1, false>(cw, u, nvalid, p, sm.hist, A.hash_log2, sse, l1, linf);
+            unsigned long long hacc = 0ull;
+            if (p.path == kDegenerate) {
+                if (threadIdx.x == 0) hacc = __ldg(&A.ltab[nvalid]);
             } else {
-                if (lit) eval_bits<T, EPT, 2, true>(cw, u, nvalid, p, sm.hist, A.hash_log2, sse, l1, linf);
-                else eval_bits<T, EPT, 2, false>(cw, u, nvalid, p, sm.hist, A.hash_log2, sse, l1, linf);
+                const bool generic = p.path == kGeneric || any_slow;
+                // code bit patterns are kMagicBits + q: fold the offset into the bases
+                const uint32_t lane_base = hbase_raw + lane * 4u - (kMagicBits << 7);
+                const uint32_t dbase = hbase_raw - (kMagicBits << 2);
+                switch (p.mode) {
+                    case kLane:
+                        eval_dispatch<T, EPT, kLane>(cw, u, nvalid, full, generic, p, dbase, lane_base, log2cap, A.dtab, sse, l1, linf, hacc);
+                        break;
+                    case kDirect:
+                        eval_dispatch<T, EPT, kDirect>(cw, u, nvalid, full, generic, p, dbase, lane_base, log2cap, A.dtab, sse, l1, linf, hacc);
+                        break;
+                    case kDelta32:
+                        eval_dispatch<T, EPT, kDelta32>(cw, u, nvalid, full, generic, p, dbase, lane_base, log2cap, A.dtab, sse, l1, linf, hacc);
+                        break;
+                    case kDelta16:
+                        eval_dispatch<T, EPT, kDelta16>(cw, u, nvalid, full, generic, p, hbase_raw, lane_base, log2cap, A.dtab, sse, l1, linf, hacc);
+                        break;
+                    default:
+                        eval_dispatch<T, EPT, kHash>(cw, u, nvalid, full, generic, p, hbase_raw, lane_base, log2cap, A.dtab, sse, l1, linf, hacc);
+                        break;
+                }
             }
             sm.psse[k * T + threadIdx.x] = sse;
             sm.pl1[k * T + threadIdx.x] = l1;
-            sm.plinf[k * T + threadIdx.x] = linf;
-            __syncthreads();
-            unsigned long long acc;
-            if (mode == 0) acc = hist_scan<T, 0>(sm.hist, p.b, A.hash_log2, A.ltab);
-            else if (mode == 1) acc = hist_scan<T, 1>(sm.hist, p.b, A.hash_log2, A.ltab);
-            else acc = hist_scan<T, 2>(sm.hist, p.b, A.hash_log2, A.ltab);
-            acc = warp_sum_u64(acc);
-            if (lane == 0) sm.hpart[k * NW + warp] = acc;
-            __syncthreads();
+            const uint32_t lmax = __reduce_max_sync(kFull, __float_as_uint(linf));
+            if (lane == 0) sm.plinf[k * NW + warp] = __uint_as_float(lmax);
+            __syncthreads();   // every update of this buffer is done
+            if (p.path != kDegenerate) hist_finish<T>(hist, p.mode, p.b, hw, A.ltab, hacc);
+            hacc = warp_sum_u64_redux(hacc);
+            if (lane == 0) sm.hpart[k * NW + warp] = hacc;
+            if (!A.double_buffer) __syncthreads();
         }
         __syncthreads();
-        // ---- reduce the per-thread partials and write this channel's entries
+        // ---- reduce the partials and write this channel's entries
         for (int k = warp; k < n_opts; k += NW) {
-            float a = 0.0f, b = 0.0f, cmax = 0.0f;
+            float a = 0.0f, b = 0.0f;
 #pragma unroll
             for (int j = 0; j < T / 32; j++) {
                 a = __fadd_rn(a, sm.psse[k * T + j * 32 + lane]);
                 b = __fadd_rn(b, sm.pl1[k * T + j * 32 + lane]);
-                cmax = fmaxf(cmax, sm.plinf[k * T + j * 32 + lane]);
             }
-            a = warp_sum<T>(a);
-            b = warp_sum<T>(b);
+            a = warp_sum(a);
+            b = warp_sum(b);
+            float cmax = lane < NW ? sm.plinf[k * NW + lane] : 0.0f;
             cmax = warp_max(cmax);
             unsigned long long hs = 0;
             for (int j = lane; j < NW; j += 32) hs += sm.hpart[k * NW + j];
-            hs = warp_sum_u64(hs);
+            hs = warp_sum_u64_redux(hs);
             if (lane == 0) {
                 const int64_t o = item * A.n_bits + A.opt_lo + k;
                 // undo the 2^k scale in FP64 (exact powers of two)
@@ -435,12 +587,21 @@ __device__ void process_item(const KernelArgs &A, const Smem &sm, int64_t work) 
 }
 
 template <int T, int EPT, int W>
-__global__ void __launch_bounds__(T, (T >= 512 ? 1 : 512 / T)) k_cost(const __grid_constant__ KernelArgs A,
-                                                                      int hist_words) {
+__global__ void __launch_bounds__(T, (T >= 512 ? 1 : 512 / T))
+    k_cost(const __grid_constant__ KernelArgs A, int n_bufs) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n_opts = A.opt_hi - A.opt_lo;
-    Smem sm = carve<T, W>(smem_raw, hist_words, n_opts);
-    for (int i = threadIdx.x; i < hist_words; i += T) sm.hist[i] = 0u;
+    size_t o[7];
+    smem_layout(T, W, A.hist_words, n_bufs, n_opts, o);
+    Smem sm;
+    sm.hist = reinterpret_cast<uint32_t *>(smem_raw + o[0]);
+    sm.psse = reinterpret_cast<float *>(smem_raw + o[1]);
+    sm.pl1 = reinterpret_cast<float *>(smem_raw + o[2]);
+    sm.hpart = reinterpret_cast<unsigned long long *>(smem_raw + o[3]);
+    sm.plinf = reinterpret_cast<float *>(smem_raw + o[4]);
+    sm.bp = reinterpret_cast<BitParam *>(smem_raw + o[5]);
+    sm.mm = reinterpret_cast<float *>(smem_raw + o[6]);
+    for (int i = threadIdx.x; i < n_bufs * A.hist_words; i += T) sm.hist[i] = 0u;
     __syncthreads();
     if (A.counter == nullptr) {
         process_item<T, EPT, W>(A, sm, blockIdx.x);
@@ -473,17 +634,21 @@ const ConfigEntry kConfigs[] = {
     MGS_CFG(128, 8, 8),
     MGS_CFG(256, 4, 8),
     MGS_CFG(512, 32, 1),
+    MGS_CFG(256, 16, 1),
+    MGS_CFG(512, 8, 2),
 };
 #undef MGS_CFG
 constexpr int kNumConfigs = sizeof(kConfigs) / sizeof(kConfigs[0]);
 
-int hash_log2_for(int G) {
-    int cap = 1;
+// Words per histogram buffer: room for a 2G-slot hash (power of two), >= 2048.
+int hist_words_for(int G) {
+    int cap = 2048;
     while (cap < 2 * G) cap <<= 1;
-    int l = 0;
-    while ((1 << l) < cap) l++;
-    return std::max(l, 5);
+    return cap;
 }
+
+// Two buffers (one barrier per bit-width) while they stay small.
+int hist_buffers_for(int G) { return hist_words_for(G) <= 8192 ? 2 : 1; }
 
 }  // namespace
 
@@ -491,27 +656,23 @@ int cost_config_count() { return kNumConfigs; }
 const CostConfig &cost_config(int i) { return kConfigs[i].cfg; }
 
 int cost_default_config(int G) {
-    if (G <= 1024) return 6;    // 128 x 8, W 8
-    if (G <= 2048) return 4;    // 256 x 8, W 8
-    if (G <= 4096) return 0;    // 256 x 16, W 4
+    if (G <= 1024) return 7;    // 256 x 4, W 8
+    if (G <= 2048) return 5;    // 256 x 8, W 4
+    if (G <= 4096) return 1;    // 512 x 8, W 4
     if (G <= 16384) return 8;   // 512 x 32, W 1
     return -1;
 }
 
 size_t cost_smem_bytes(int config, int G, int n_opts) {
     const CostConfig &c = kConfigs[config].cfg;
-    int hw = hist_words_for(G, hash_log2_for(G));
-    size_t off = (size_t)hw * 4 + (size_t)n_opts * c.threads * 4 * 3;
-    off = (off + 15) & ~(size_t)15;
-    off += (size_t)n_opts * (c.threads / 32) * 8 + (size_t)n_opts * sizeof(BitParam) +
-           (size_t)(c.threads / 32) * c.width * 2 * 4 + 16;
-    return off;
+    size_t o[7];
+    return smem_layout(c.threads, c.width, hist_words_for(G), hist_buffers_for(G), n_opts, o);
 }
 
 struct CostExec {
     const ConfigEntry *entry = nullptr;
     KernelArgs args{};
-    int hist_words = 0;
+    int n_bufs = 0;
     size_t smem = 0;
     int64_t grid = 0;
     bool persistent = false;
@@ -546,8 +707,10 @@ mgs_status cost_exec_create(mgs_ctx *ctx, const CostLaunch &L, int config, CostE
     A.opt_hi = L.opt_hi;
     for (int k = 0; k < L.n_bits; k++) A.bits[k] = L.bits[k];
     A.ltab = ctx->d_ltab;
-    A.hash_log2 = (uint32_t)hash_log2_for(L.group_size);
-    X->hist_words = hist_words_for(L.group_size, (int)A.hash_log2);
+    A.dtab = ctx->d_dtab;
+    A.hist_words = hist_words_for(L.group_size);
+    X->n_bufs = hist_buffers_for(L.group_size);
+    A.double_buffer = X->n_bufs == 2;
     X->smem = cost_smem_bytes(config, L.group_size, L.opt_hi - L.opt_lo);
     X->persistent = L.persistent;
     if (X->smem > 227 * 1024) {
@@ -590,7 +753,7 @@ mgs_status cost_exec_run(const CostExec *X, cudaStream_t st) {
     if (X->persistent)
         MGS_CUDA_TRY(cudaMemsetAsync(X->args.counter, 0, sizeof(unsigned int), st));
     X->entry->kernel<<<(unsigned)X->grid, X->entry->cfg.threads, X->smem, st>>>(X->args,
-                                                                                   X->hist_words);
+                                                                                   X->n_bufs);
     count_launches(1);
     MGS_CUDA_TRY(cudaGetLastError());
     return MGS_OK;

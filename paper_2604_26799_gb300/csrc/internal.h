@@ -63,6 +63,7 @@ struct mgs_ctx {
     int device = 0;
     int sm_count = 0;
     unsigned long long *d_ltab = nullptr;   // L(n) for n in [0, MGS_MAX_GROUP], 32.32 fixed point
+    unsigned long long *d_dtab = nullptr;   // L(n) - L(n - 1), same range (0 at n = 0)
     std::mutex mu;
     std::vector<mgs::TileChoice> tiles;     // autotuned choices
     int forced_config = -1;                 // testing hook: force a tile configuration
