@@ -281,6 +281,32 @@ mgs_status mgs_quantize_groups(mgs_ctx *ctx, const mgs_scene *scene, int64_t kee
                                int32_t group_size, const uint8_t *bits, uint16_t *codes,
                                float *minmax, void *stream);
 
+/*
+ * mgs_quantize_groups without any allocation.  The paper has no counterpart:
+ * this is an interface for callers that must not allocate device memory
+ * while they run -- code recording work into a CUDA stream capture (where
+ * cudaMalloc is not permitted), processes whose device memory is owned and
+ * capped by another framework's allocator, and real-time encoder threads
+ * with a no-allocation rule.  Same arguments, results and errors as
+ * mgs_quantize_groups, and the caller still provides every input and output.
+ *
+ * The scratch it needs (the kept list and its per-tile counts) lives in
+ * file-scope device arrays of fixed size that every GPU loading this library
+ * holds until the process exits: at most MGS_NOALLOC_MAX_KEEP kept Gaussians
+ * (16 MiB of indices) of a scene of at most MGS_NOALLOC_MAX_SCENE Gaussians;
+ * larger requests return MGS_ERR_INVALID_ARG.  The first call on a device looks
+ * up the arrays' device addresses (cudaGetSymbolAddress, once per device); make
+ * that first call before any stream capture.  Every call shares the arrays and
+ * they keep the last call's contents (nothing in them needs clearing): calls
+ * that overlap on the GPU (different streams, or different host threads with
+ * no ordering between them) race on the scratch and must be serialised.
+ */
+#define MGS_NOALLOC_MAX_KEEP 4194304
+#define MGS_NOALLOC_MAX_SCENE 16777216
+mgs_status mgs_quantize_groups_noalloc(mgs_ctx *ctx, const mgs_scene *scene, int64_t keep,
+                                       int32_t group_size, const uint8_t *bits, uint16_t *codes,
+                                       float *minmax, void *stream);
+
 /* ---- size estimate and budget solve (host) ------------------------------ */
 
 /*

@@ -93,6 +93,12 @@ mgs_status scene_build(mgs_ctx *ctx, const float *d_attrs, const float *d_imp, i
 mgs_status scene_kept(mgs_scene *scene, const int64_t *keep, int32_t n_r, cudaStream_t st,
                       const int32_t **pos_out, std::vector<int64_t> *offset_out);
 
+// Kept list of one kept-set size into caller memory: pos[keep] and
+// tile_cnt[kept_tiles_for(n)] (fully overwritten; nothing needs clearing).
+mgs_status kept_list_into(const mgs_scene *scene, int64_t keep, int32_t *pos, uint32_t *tile_cnt,
+                          cudaStream_t st);
+int64_t kept_tiles_for(int64_t n);
+
 // ---- cost kernels (cost.cu) ----
 struct CostSeg {
     const float *slabs;

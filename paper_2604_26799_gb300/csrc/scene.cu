@@ -501,4 +501,20 @@ mgs_status scene_kept(mgs_scene *sc, const int64_t *keep, int32_t n_r, cudaStrea
     return MGS_OK;
 }
 
+mgs_status kept_list_into(const mgs_scene *sc, int64_t keep, int32_t *pos, uint32_t *tile_cnt,
+                          cudaStream_t st) {
+    const int n_tiles = (int)((sc->n + kTile - 1) / kTile);
+    KeepArg ka{};
+    ka.n_r = 1;
+    ka.k[0] = keep;
+    k_kept_count<<<n_tiles, kTileThreads, 0, st>>>(sc->d_rank_m, sc->n, ka, tile_cnt, n_tiles);
+    k_scan_u32<<<1, 1024, 0, st>>>(tile_cnt, (int64_t)n_tiles);
+    k_kept_scatter<<<n_tiles, kTileThreads, 0, st>>>(sc->d_rank_m, sc->n, ka, tile_cnt, n_tiles, pos);
+    count_launches(3);
+    MGS_CUDA_TRY(cudaGetLastError());
+    return MGS_OK;
+}
+
+int64_t kept_tiles_for(int64_t n) { return (n + kTile - 1) / kTile; }
+
 }  // namespace mgs

@@ -83,6 +83,7 @@ _SIGS = {
     "mgs_build_cost_table_plain": [_P, _P, ctypes.POINTER(mgs_grid), _P, _P],
     "mgs_build_cost_tables_batched": [_P, ctypes.c_int32, _P, ctypes.POINTER(mgs_grid), _P, _P],
     "mgs_quantize_groups": [_P, _P, ctypes.c_int64, ctypes.c_int32, _P, _P, _P, _P],
+    "mgs_quantize_groups_noalloc": [_P, _P, ctypes.c_int64, ctypes.c_int32, _P, _P, _P, _P],
     "mgs_plan_create": [_P, ctypes.c_int32, _P, ctypes.POINTER(mgs_grid), _P, ctypes.c_int32, _P,
                         ctypes.POINTER(_P)],
     "mgs_plan_launch": [_P, _P],
@@ -264,6 +265,13 @@ def mgs_autotune(ctx: int, scene: int, grid: Grid, stream=None) -> tuple[int, np
     _check(lib().mgs_autotune(ctx, scene, ctypes.byref(grid.c), _stream(stream),
                               ctypes.addressof(chosen), ms.ctypes.data))
     return chosen.value, ms
+
+
+def mgs_quantize_groups_noalloc(ctx: int, scene: int, keep: int, group_size: int, bits, codes,
+                                minmax, stream=None):
+    """mgs_quantize_groups for callers that cannot allocate device memory (static scratch)."""
+    _check(lib().mgs_quantize_groups_noalloc(ctx, scene, keep, group_size, _ptr(bits), _ptr(codes),
+                                             _ptr(minmax), _stream(stream)))
 
 
 def solve_opts(rate_model: int = MGS_RATE_ENTROPY, norm: int = MGS_NORM_SSE,
