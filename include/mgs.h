@@ -307,6 +307,62 @@ mgs_status mgs_quantize_groups_noalloc(mgs_ctx *ctx, const mgs_scene *scene, int
                                        int32_t group_size, const uint8_t *bits, uint16_t *codes,
                                        float *minmax, void *stream);
 
+/* ---- serving ------------------------------------------------------------ */
+
+/*
+ * A search server: jobs (a scene in host memory, a grid and a byte budget) are
+ * submitted at any time and each is answered with Alg. 1's result (the chosen
+ * ratio and bit-widths).  Continuous batching: a job is admitted while fewer
+ * than max_jobs are in flight and its device footprint fits hbm_budget_bytes
+ * (a lone job is always admitted); an ingest thread makes its scene resident;
+ * a compute thread runs one persistent launch per iteration over a slice of
+ * the remaining work items of every admitted job (about slice_items items per
+ * launch, 0 = all), so jobs that arrive while others are on the GPU join the
+ * next launch; finished tables are copied to pinned host memory and solved by
+ * solver_threads host threads.  A job's results are the same whichever jobs
+ * it shares launches with.
+ */
+typedef struct mgs_server mgs_server;
+
+typedef struct {
+    int32_t max_jobs;          /* jobs admitted at once (>= 1) */
+    int32_t solver_threads;    /* host threads solving finished tables (>= 1) */
+    int64_t hbm_budget_bytes;  /* device memory the server may hold for jobs */
+    int64_t slice_items;       /* work items per batched launch (0 = everything ready) */
+} mgs_server_opts;
+
+typedef struct {
+    const float *attrs;        /* [n][n_channels] host memory, valid until the job is done */
+    const float *importance;   /* [n] host memory, valid until the job is done */
+    int64_t n;
+    int32_t n_channels;
+    mgs_grid grid;             /* copied at submission */
+    double budget_bytes;
+    mgs_solve_opts opts;
+} mgs_job;
+
+typedef struct {
+    mgs_status status;         /* the job's own status (MGS_OK or its error) */
+    int32_t r_index;
+    double est_bytes;
+    double objective;
+    double lp_bound;
+    int64_t n_choice;          /* entries of the chosen ratio's option array */
+    double t_submit, t_admit, t_ready, t_table, t_done;   /* seconds since server start */
+} mgs_job_result;
+
+mgs_status mgs_server_create(mgs_ctx *ctx, const mgs_server_opts *opts, mgs_server **out);
+mgs_status mgs_server_submit(mgs_server *server, const mgs_job *job, int64_t *job_id);
+/* Wait up to timeout_ms for a job; MGS_ERR_TIMEOUT if it is not done by then.
+ * choice[choice_capacity] (may be NULL) receives the chosen options. */
+mgs_status mgs_server_wait(mgs_server *server, int64_t job_id, int32_t timeout_ms,
+                           mgs_job_result *out, uint8_t *choice, int64_t choice_capacity);
+/* Batched launches and work items run so far, jobs in flight, bytes held. */
+mgs_status mgs_server_stats(mgs_server *server, int64_t *launches, int64_t *work_items,
+                            int32_t *in_flight, int64_t *used_bytes);
+/* Finish every admitted job, then stop the threads and free the server. */
+mgs_status mgs_server_destroy(mgs_server *server);
+
 /* ---- size estimate and budget solve (host) ------------------------------ */
 
 /*

@@ -482,7 +482,7 @@ mgs_status mgs_set_tile_config(mgs_ctx *ctx, int32_t group_size, int32_t n_bits,
         set_error("bad tile request (G %d, %d bit-widths, config %d)", group_size, n_bits, config);
         return MGS_ERR_INVALID_ARG;
     }
-    if (config >= 0 && !cost_config_fits(config, group_size, n_bits)) {
+    if (config >= 0 && !cost_config_fits(config, group_size, n_bits, nullptr)) {
         set_error("tile %s cannot run G=%d with %d bit-widths", cost_config(config).name,
                   group_size, n_bits);
         return MGS_ERR_INVALID_ARG;
@@ -527,7 +527,7 @@ mgs_status mgs_autotune(mgs_ctx *ctx, const mgs_scene *scene, const mgs_grid *gr
     float best_ms = 0;
     for (int c = 0; c < nc && s == MGS_OK; c++) {
         if (ms_per_config) ms_per_config[c] = -1.0f;
-        if (!cost_config_fits(c, grid->group_size, grid->n_bits)) continue;
+        if (!cost_config_fits(c, grid->group_size, grid->n_bits, grid->bits)) continue;
         CostLaunch launch;
         launch.segs = segs;
         launch.group_size = grid->group_size;

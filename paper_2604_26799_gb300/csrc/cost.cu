@@ -65,7 +65,8 @@ struct BitParam {
     int b;
     int mode;
     int path;
-    int pad[2];
+    int buf;      // histogram buffer: 0, 1 (second small buffer) or 2 (big buffer)
+    int sync;     // 1: barrier before the pass (the previous option used the same buffer)
 };
 
 struct KernelArgs {
@@ -79,8 +80,9 @@ struct KernelArgs {
     const unsigned long long *ltab;   // L(h)
     const unsigned long long *dtab;   // L(h) - L(h - 1)
     unsigned int *counter;
-    int32_t hist_words;               // words per histogram buffer (power of two)
-    int32_t double_buffer;
+    int32_t hist_words;               // words per small histogram buffer (power of two)
+    int32_t n_small;                  // small buffers (1 or 2)
+    int32_t big_words;                // words of the big buffer (0: none)
 };
 
 // ---- packed FP32 pairs ----------------------------------------------------
@@ -342,7 +344,7 @@ __device__ __forceinline__ void load_row(const float *p, float (&v)[W]) {
 }
 
 // Shared-memory layout (dynamic):
-//   hist[nbuf][hist_words] | psse[n_opts][T] | pl1[n_opts][T] | hpart[n_opts][T/32] (u64)
+//   hist[n_small][hist_words] hist_big[big_words] | psse[n_opts][T] | pl1[n_opts][T] | hpart[n_opts][T/32] (u64)
 //   | plinf[n_opts][T/32] | bp[n_opts] | mm[T/32][W][2]
 struct Smem {
     uint32_t *hist;
@@ -352,10 +354,10 @@ struct Smem {
     float *mm;
 };
 
-__host__ __device__ inline size_t smem_layout(int T, int W, int hist_words, int nbuf, int n_opts,
-                                              size_t *o) {
+__host__ __device__ inline size_t smem_layout(int T, int W, int hist_words, int nbuf, int big_words,
+                                              int n_opts, size_t *o) {
     size_t off = 0;
-    o[0] = off; off += (size_t)nbuf * hist_words * 4;
+    o[0] = off; off += (size_t)nbuf * hist_words * 4 + (size_t)big_words * 4;
     o[1] = off; off += (size_t)n_opts * T * 4;
     o[2] = off; off += (size_t)n_opts * T * 4;
     off = (off + 15) & ~(size_t)15;
@@ -384,7 +386,7 @@ __device__ void process_item(const KernelArgs &A, const Smem &sm, int64_t work) 
     __syncthreads();
     const CostSeg &S = A.segs[s_seg];
     const int64_t local = work - S.work_begin;
-    const int g = (int)(local / S.n_chunks);
+    const int g = S.g_first + (int)(local / S.n_chunks);
     const int chunk = (int)(local % S.n_chunks);
     const int c0 = chunk * W;
     const int slab = c0 / kSlabWidth;
@@ -464,10 +466,15 @@ __device__ void process_item(const KernelArgs &A, const Smem &sm, int64_t work) 
             p.ytop = kMagic + p.top;
             p.S = __fdiv_rn(R, p.twob);
             p.Ss = __fmul_rn(__fmul_rn(p.S, s1), s2);
-            p.mode = p.b <= kLaneMaxBits ? kLane
-                   : p.b <= kDirectMaxBits ? kDirect
-                   : (1 << p.b) <= hw ? kDelta32
-                   : (1 << (p.b - 1)) <= hw ? kDelta16 : kHash;
+            const int bw = A.big_words;
+            p.buf = 0;
+            if (p.b <= kLaneMaxBits) p.mode = kLane;
+            else if (p.b <= kDirectMaxBits) p.mode = kDirect;
+            else if ((1 << p.b) <= hw) p.mode = kDelta32;
+            else if ((1 << (p.b - 1)) <= hw) p.mode = kDelta16;
+            else if ((1 << p.b) <= bw) { p.mode = kDelta32; p.buf = 2; }
+            else if ((1 << (p.b - 1)) <= bw) { p.mode = kDelta16; p.buf = 2; }
+            else p.mode = kHash;
             if (p.S == 0.0f) {
                 p.path = kDegenerate;
                 p.Z = 0.0f;
@@ -510,13 +517,36 @@ __device__ void process_item(const KernelArgs &A, const Smem &sm, int64_t work) 
             cw[e] = __fmul_rn(__fmul_rn(cw[e], s1), s2);
         }
         const int any_slow = __syncthreads_or(slow);   // also publishes bp
+        if (threadIdx.x == 0) {
+            // alternate buffers so one barrier per bit-width suffices; an option that
+            // must reuse the previous option's buffer waits for its clearing first
+            int last = -1;
+            for (int k = 0; k < n_opts; k++) {
+                BitParam &q = sm.bp[k];
+                if (q.buf != 2) {
+                    const int cand[3] = {0, 1, 2};
+                    int pick = -1;
+                    for (int c = 0; c < 3 && pick < 0; c++) {
+                        const int bsel = cand[c];
+                        if (bsel == 1 && A.n_small < 2) continue;
+                        if (bsel == 2 && A.big_words == 0) continue;
+                        if (bsel != last) pick = bsel;
+                    }
+                    q.buf = pick < 0 ? 0 : pick;
+                }
+                q.sync = (q.buf == last) ? 1 : 0;
+                last = q.buf;
+            }
+        }
+        __syncthreads();
 
 #pragma unroll 1
         for (int k = 0; k < n_opts; k++) {
             const BitParam p = sm.bp[k];
-            const int buf = A.double_buffer ? (k & 1) : 0;
-            uint32_t *hist = sm.hist + (size_t)buf * hw;
-            const uint32_t hbase_raw = hist_addr + (uint32_t)buf * hw * 4u;
+            if (p.sync) __syncthreads();
+            const int slot = p.buf == 2 ? A.n_small : p.buf;   // the big buffer follows the small ones
+            uint32_t *hist = sm.hist + (size_t)slot * hw;
+            const uint32_t hbase_raw = hist_addr + (uint32_t)slot * hw * 4u;
             float sse = 0.0f, l1 = 0.0f, linf = 0.0f;
             unsigned long long hacc = 0ull;
             if (p.path == kDegenerate) {
@@ -549,10 +579,10 @@ __device__ void process_item(const KernelArgs &A, const Smem &sm, int64_t work) 
             const uint32_t lmax = __reduce_max_sync(kFull, __float_as_uint(linf));
             if (lane == 0) sm.plinf[k * NW + warp] = __uint_as_float(lmax);
             __syncthreads();   // every update of this buffer is done
-            if (p.path != kDegenerate) hist_finish<T>(hist, p.mode, p.b, hw, A.ltab, hacc);
+            if (p.path != kDegenerate)
+                hist_finish<T>(hist, p.mode, p.b, p.buf == 2 ? A.big_words : hw, A.ltab, hacc);
             hacc = warp_sum_u64_redux(hacc);
             if (lane == 0) sm.hpart[k * NW + warp] = hacc;
-            if (!A.double_buffer) __syncthreads();
         }
         __syncthreads();
         // ---- reduce the partials and write this channel's entries
@@ -588,11 +618,11 @@ __device__ void process_item(const KernelArgs &A, const Smem &sm, int64_t work) 
 
 template <int T, int EPT, int W>
 __global__ void __launch_bounds__(T, (T >= 512 ? 1 : 512 / T))
-    k_cost(const __grid_constant__ KernelArgs A, int n_bufs) {
+    k_cost(const __grid_constant__ KernelArgs A, int unused) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n_opts = A.opt_hi - A.opt_lo;
     size_t o[7];
-    smem_layout(T, W, A.hist_words, n_bufs, n_opts, o);
+    smem_layout(T, W, A.hist_words, A.n_small, A.big_words, n_opts, o);
     Smem sm;
     sm.hist = reinterpret_cast<uint32_t *>(smem_raw + o[0]);
     sm.psse = reinterpret_cast<float *>(smem_raw + o[1]);
@@ -601,7 +631,7 @@ __global__ void __launch_bounds__(T, (T >= 512 ? 1 : 512 / T))
     sm.plinf = reinterpret_cast<float *>(smem_raw + o[4]);
     sm.bp = reinterpret_cast<BitParam *>(smem_raw + o[5]);
     sm.mm = reinterpret_cast<float *>(smem_raw + o[6]);
-    for (int i = threadIdx.x; i < n_bufs * A.hist_words; i += T) sm.hist[i] = 0u;
+    for (int i = threadIdx.x; i < A.n_small * A.hist_words + A.big_words; i += T) sm.hist[i] = 0u;
     __syncthreads();
     if (A.counter == nullptr) {
         process_item<T, EPT, W>(A, sm, blockIdx.x);
@@ -636,6 +666,8 @@ const ConfigEntry kConfigs[] = {
     MGS_CFG(512, 32, 1),
     MGS_CFG(256, 16, 1),
     MGS_CFG(512, 8, 2),
+    MGS_CFG(512, 4, 8),
+    MGS_CFG(512, 4, 4),
 };
 #undef MGS_CFG
 constexpr int kNumConfigs = sizeof(kConfigs) / sizeof(kConfigs[0]);
@@ -647,8 +679,33 @@ int hist_words_for(int G) {
     return cap;
 }
 
-// Two buffers (one barrier per bit-width) while they stay small.
-int hist_buffers_for(int G) { return hist_words_for(G) <= 8192 ? 2 : 1; }
+// Histogram buffers of a launch: small buffers of hist_words_for(G) words and,
+// when some bit-width needs more than a small buffer holds even as 16-bit
+// counter pairs, one big buffer of 2^(b_max - 1) words; two small buffers when
+// there is no big one.  Falls back to fewer/smaller buffers (the hash) when
+// shared memory is short.
+struct HistPlan {
+    int hist_words, n_small, big_words;
+};
+
+size_t smem_for(const CostConfig &c, const HistPlan &h, int n_opts) {
+    size_t o[7];
+    return smem_layout(c.threads, c.width, h.hist_words, h.n_small, h.big_words, n_opts, o);
+}
+
+HistPlan hist_plan(const CostConfig &c, int G, const int32_t *bits, int n_opts) {
+    HistPlan h{hist_words_for(G), 2, 0};
+    int bmax = bits ? 0 : MGS_MAX_BITS;
+    for (int k = 0; bits && k < n_opts; k++) bmax = std::max(bmax, (int)bits[k]);
+    const size_t limit = 227 * 1024;
+    if ((1 << (bmax - 1)) > h.hist_words) {
+        HistPlan b{h.hist_words, 1, 1 << (bmax - 1)};
+        if (smem_for(c, b, n_opts) <= limit) return b;
+    }
+    if (smem_for(c, h, n_opts) <= limit && h.hist_words <= 8192) return h;
+    h.n_small = 1;
+    return h;
+}
 
 }  // namespace
 
@@ -663,16 +720,14 @@ int cost_default_config(int G) {
     return -1;
 }
 
-size_t cost_smem_bytes(int config, int G, int n_opts) {
+size_t cost_smem_bytes(int config, int G, int n_opts, const int32_t *bits) {
     const CostConfig &c = kConfigs[config].cfg;
-    size_t o[7];
-    return smem_layout(c.threads, c.width, hist_words_for(G), hist_buffers_for(G), n_opts, o);
+    return smem_for(c, hist_plan(c, G, bits, n_opts), n_opts);
 }
 
 struct CostExec {
     const ConfigEntry *entry = nullptr;
     KernelArgs args{};
-    int n_bufs = 0;
     size_t smem = 0;
     int64_t grid = 0;
     bool persistent = false;
@@ -694,7 +749,11 @@ mgs_status cost_exec_create(mgs_ctx *ctx, const CostLaunch &L, int config, CostE
     for (auto &s : *segs) {
         s.n_chunks = (s.C + E.cfg.width - 1) / E.cfg.width;
         s.work_begin = n_work;
-        n_work += (int64_t)s.n_groups * s.n_chunks;
+        if (s.g_count <= 0) {
+            s.g_first = 0;
+            s.g_count = s.n_groups;
+        }
+        n_work += (int64_t)s.g_count * s.n_chunks;
     }
     CostExec *X = new CostExec();
     X->entry = &E;
@@ -708,10 +767,11 @@ mgs_status cost_exec_create(mgs_ctx *ctx, const CostLaunch &L, int config, CostE
     for (int k = 0; k < L.n_bits; k++) A.bits[k] = L.bits[k];
     A.ltab = ctx->d_ltab;
     A.dtab = ctx->d_dtab;
-    A.hist_words = hist_words_for(L.group_size);
-    X->n_bufs = hist_buffers_for(L.group_size);
-    A.double_buffer = X->n_bufs == 2;
-    X->smem = cost_smem_bytes(config, L.group_size, L.opt_hi - L.opt_lo);
+    const HistPlan hp = hist_plan(E.cfg, L.group_size, L.bits + L.opt_lo, L.opt_hi - L.opt_lo);
+    A.hist_words = hp.hist_words;
+    A.n_small = hp.n_small;
+    A.big_words = hp.big_words;
+    X->smem = smem_for(E.cfg, hp, L.opt_hi - L.opt_lo);
     X->persistent = L.persistent;
     if (X->smem > 227 * 1024) {
         set_error("tile %s needs %zu bytes of shared memory for G=%d and %d options", E.cfg.name,
@@ -752,8 +812,7 @@ mgs_status cost_exec_run(const CostExec *X, cudaStream_t st) {
     if (X->grid == 0) return MGS_OK;
     if (X->persistent)
         MGS_CUDA_TRY(cudaMemsetAsync(X->args.counter, 0, sizeof(unsigned int), st));
-    X->entry->kernel<<<(unsigned)X->grid, X->entry->cfg.threads, X->smem, st>>>(X->args,
-                                                                                   X->n_bufs);
+    X->entry->kernel<<<(unsigned)X->grid, X->entry->cfg.threads, X->smem, st>>>(X->args, 0);
     count_launches(1);
     MGS_CUDA_TRY(cudaGetLastError());
     return MGS_OK;
@@ -783,11 +842,11 @@ mgs_status cost_launch(mgs_ctx *ctx, const CostLaunch &L, int config, CostSeg *d
     return s;
 }
 
-bool cost_config_fits(int config, int group_size, int n_opts) {
+bool cost_config_fits(int config, int group_size, int n_opts, const int32_t *bits) {
     if (config < 0 || config >= kNumConfigs) return false;
     const CostConfig &c = kConfigs[config].cfg;
     return (int64_t)c.threads * c.ept >= group_size &&
-           cost_smem_bytes(config, group_size, n_opts) <= 227 * 1024;
+           cost_smem_bytes(config, group_size, n_opts, bits) <= 227 * 1024;
 }
 
 }  // namespace mgs

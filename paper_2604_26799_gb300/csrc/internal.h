@@ -107,9 +107,11 @@ struct CostSeg {
     int64_t K;             // kept-set size
     int64_t work_begin;    // first work item of this segment
     int64_t item_base;     // table item of (r, c = 0, g = 0)
-    int32_t n_groups;
+    int32_t n_groups;      // groups of this ratio (table stride)
     int32_t n_chunks;
     int32_t C;
+    int32_t g_first;       // first group computed by this segment
+    int32_t g_count;       // groups computed (0 = all n_groups)
     int32_t pad_;
     double *sse;
     double *l1;
@@ -146,8 +148,8 @@ int cost_default_config(int group_size);
 // segment array (at least segs.size() entries); counter is a device uint (persistent mode).
 mgs_status cost_launch(mgs_ctx *ctx, const CostLaunch &L, int config, CostSeg *d_segs,
                        unsigned int *d_counter, cudaStream_t st);
-size_t cost_smem_bytes(int config, int group_size, int n_opts);
-bool cost_config_fits(int config, int group_size, int n_opts);
+size_t cost_smem_bytes(int config, int group_size, int n_opts, const int32_t *bits);
+bool cost_config_fits(int config, int group_size, int n_opts, const int32_t *bits);
 
 // A prepared launch: work layout, kernel arguments and shape, reusable and
 // capturable (cost_exec_run issues only a memset and a kernel launch).

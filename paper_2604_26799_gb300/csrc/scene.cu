@@ -111,6 +111,66 @@ __global__ void k_scan_u32(uint32_t *data, int64_t total) {
     }
 }
 
+// Exclusive scan of a long uint32 array in two launches: every block scans
+// its chunk in place and records the chunk total; then every block adds the
+// totals of the chunks before it.
+constexpr int kScanThreads = 1024;
+constexpr int kScanPer = 8;
+constexpr int kScanChunk = kScanThreads * kScanPer;
+
+__global__ void __launch_bounds__(kScanThreads)
+    k_scan_chunks(uint32_t *__restrict__ data, int64_t total, uint32_t *__restrict__ totals) {
+    __shared__ uint32_t warp_tot[kScanThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t base = (int64_t)blockIdx.x * kScanChunk + (int64_t)threadIdx.x * kScanPer;
+    uint32_t v[kScanPer], s = 0;
+#pragma unroll
+    for (int j = 0; j < kScanPer; j++) {
+        v[j] = base + j < total ? data[base + j] : 0u;
+        s += v[j];
+    }
+    uint32_t inc = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) warp_tot[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = warp_tot[lane], wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t t = __shfl_up_sync(0xFFFFFFFFu, wi, o);
+            if (lane >= o) wi += t;
+        }
+        warp_tot[lane] = wi - w;   // exclusive prefix of the warp totals
+        if (lane == 31) totals[blockIdx.x] = wi;
+    }
+    __syncthreads();
+    uint32_t run = warp_tot[warp] + inc - s;
+#pragma unroll
+    for (int j = 0; j < kScanPer; j++) {
+        if (base + j < total) data[base + j] = run;
+        run += v[j];
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+    k_scan_add(uint32_t *__restrict__ data, int64_t total, const uint32_t *__restrict__ totals) {
+    __shared__ uint32_t off;
+    if (threadIdx.x < 32) {
+        uint32_t s = 0;
+        for (int b = threadIdx.x; b < (int)blockIdx.x; b += 32) s += totals[b];
+        s = __reduce_add_sync(0xFFFFFFFFu, s);
+        if (threadIdx.x == 0) off = s;
+    }
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kScanChunk;
+    for (int j = threadIdx.x; j < kScanChunk; j += kScanThreads)
+        if (base + j < total) data[base + j] += off;
+}
+
 template <typename K>
 __global__ void __launch_bounds__(kTileThreads) k_scatter(const K *__restrict__ kin,
                                                           const uint32_t *__restrict__ vin,
@@ -173,11 +233,15 @@ mgs_status radix_sort_pairs(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals
     K *ki = keys, *ko = keys_alt;
     uint32_t *vi = vals, *vo = vals_alt;
     bool alt = false;
+    const int64_t entries = (int64_t)256 * n_tiles;
+    const int scan_blocks = (int)((entries + kScanChunk - 1) / kScanChunk);
+    uint32_t *totals = hist + entries;   // hist holds 256 * n_tiles + scan_blocks entries
     for (int shift = 0; shift < key_bits; shift += 8) {
         k_digit_hist<K><<<n_tiles, kTileThreads, 0, st>>>(ki, n, shift, hist, n_tiles);
-        k_scan_u32<<<1, 1024, 0, st>>>(hist, (int64_t)256 * n_tiles);
+        k_scan_chunks<<<scan_blocks, kScanThreads, 0, st>>>(hist, entries, totals);
+        k_scan_add<<<scan_blocks, kScanThreads, 0, st>>>(hist, entries, totals);
         k_scatter<K><<<n_tiles, kTileThreads, 0, st>>>(ki, vi, ko, vo, n, shift, hist, n_tiles);
-        count_launches(3);
+        count_launches(4);
         std::swap(ki, ko);
         std::swap(vi, vo);
         alt = !alt;
@@ -418,7 +482,7 @@ mgs_status scene_build(mgs_ctx *ctx, const float *d_attrs, const float *d_imp, i
     MGS_TRY(dalloc(&k64b, n, st));
     MGS_TRY(dalloc(&v, n, st));
     MGS_TRY(dalloc(&vb, n, st));
-    MGS_TRY(dalloc(&hist, (size_t)256 * n_tiles, st));
+    MGS_TRY(dalloc(&hist, (size_t)256 * n_tiles + (256 * (size_t)n_tiles + 8191) / 8192, st));
     uint32_t *k32 = reinterpret_cast<uint32_t *>(k64);
     uint32_t *k32b = reinterpret_cast<uint32_t *>(k64b);
 

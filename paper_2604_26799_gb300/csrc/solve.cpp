@@ -6,12 +6,14 @@
 //   1. every item's options are reduced to their lower convex hull in the
 //      (rate, distortion) plane; the LP relaxation takes hull increments in
 //      order of decreasing efficiency -dD/dRate until the capacity is used
-//      (a weighted selection, expected linear time);
+//      (a weighted radix selection on the efficiency's bit pattern: one
+//      histogram pass, then a full sort of the boundary bucket only);
 //   2. the integral answer keeps the increments that fit completely and then
 //      greedily adds further whole increments that still fit;
 //   3. the LP value (with the fractional split increment) is a lower bound.
 // Alg. 1 then picks tau from the per-ratio results (see mgs_solve_budget).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -63,19 +65,60 @@ inline double dist(const View &v, int64_t item, int k) {
     }
 }
 
-struct Inc {
-    double eff;    // -dD / dW
-    double dw;     // rate increase (bits)
-    double dd;     // distortion decrease (>= 0)
-    int32_t item;  // item index within the ratio
-    int16_t level; // position on the item's hull (increment from level to level + 1)
-    int16_t to;    // option index reached
+// Hull increments of every item, at a fixed stride of (n_b - 1) slots per item.
+struct Hulls {
+    int stride = 0;
+    std::vector<double> eff, dw, dd;   // [item * stride + level]
+    std::vector<int8_t> to;            // option reached by the increment
+    std::vector<int8_t> len;           // increments per item
+    std::vector<int8_t> start;         // first hull option per item
+    std::vector<double> w0, d0, wtop;  // per item: start rate/distortion, top-bit-width rate
 };
 
-inline bool before(const Inc &a, const Inc &b) {   // strict total order, best first
-    if (a.eff != b.eff) return a.eff > b.eff;
-    if (a.item != b.item) return a.item < b.item;
-    return a.level < b.level;
+// Lower convex hull of one item's (rate, distortion) options.
+void build_hull(const View &v, int64_t item, int64_t slot, Hulls &H) {
+    const int nb = v.n_b;
+    double w[MGS_MAX_OPTIONS], d[MGS_MAX_OPTIONS];
+    int ord[MGS_MAX_OPTIONS], hull[MGS_MAX_OPTIONS];
+    for (int k = 0; k < nb; k++) {
+        w[k] = rate_bits(v, item, k);
+        d[k] = dist(v, item, k);
+        ord[k] = k;
+    }
+    // insertion sort by (rate, distortion, index): the options usually arrive sorted
+    for (int i = 1; i < nb; i++) {
+        int x = ord[i], j = i - 1;
+        while (j >= 0 && (w[ord[j]] > w[x] || (w[ord[j]] == w[x] && (d[ord[j]] > d[x] ||
+                                                                     (d[ord[j]] == d[x] && ord[j] > x))))) {
+            ord[j + 1] = ord[j];
+            j--;
+        }
+        ord[j + 1] = x;
+    }
+    int h = 0;
+    for (int t = 0; t < nb; t++) {
+        const int k = ord[t];
+        if (h > 0 && (d[k] >= d[hull[h - 1]] || w[k] == w[hull[h - 1]])) continue;   // dominated
+        while (h >= 2) {
+            const int a = hull[h - 2], b = hull[h - 1];
+            if ((d[b] - d[a]) * (w[k] - w[a]) >= (d[k] - d[a]) * (w[b] - w[a])) h--;
+            else break;
+        }
+        hull[h++] = k;
+    }
+    H.start[slot] = (int8_t)hull[0];
+    H.w0[slot] = w[hull[0]];
+    H.d0[slot] = d[hull[0]];
+    H.wtop[slot] = w[nb - 1];
+    H.len[slot] = (int8_t)(h - 1);
+    const int64_t base = slot * H.stride;
+    for (int i = 0; i + 1 < h; i++) {
+        const int a = hull[i], b = hull[i + 1];
+        H.dw[base + i] = w[b] - w[a];
+        H.dd[base + i] = d[a] - d[b];
+        H.eff[base + i] = H.dd[base + i] / H.dw[base + i];
+        H.to[base + i] = (int8_t)b;
+    }
 }
 
 struct RatioResult {
@@ -84,62 +127,35 @@ struct RatioResult {
     std::vector<uint8_t> choice;
 };
 
-void solve_ratio(const View &v, int64_t begin, int64_t end, double budget, const mgs_solve_opts *o,
+// Order of increments: larger efficiency first, then item, then hull level.
+struct IncRef {
+    double eff;
+    int32_t item;
+    int32_t level;
+};
+inline bool inc_before(const IncRef &a, const IncRef &b) {
+    if (a.eff != b.eff) return a.eff > b.eff;
+    if (a.item != b.item) return a.item < b.item;
+    return a.level < b.level;
+}
+
+// Non-negative doubles order like their bit patterns.
+inline uint64_t eff_key(double e) {
+    uint64_t u;
+    std::memcpy(&u, &e, 8);
+    return u;
+}
+
+void solve_ratio(const Hulls &H, int64_t slot0, int64_t M, double budget, const mgs_solve_opts *o,
                  RatioResult *res) {
-    const int64_t M = end - begin;
-    const int nb = v.n_b;
+    const int S = H.stride;
     const double fixed_bytes = o->meta_bytes_per_group * (double)M + o->const_bytes + o->delta_bytes;
     const double cap = 8.0 * (budget - fixed_bytes);   // capacity in bits
-    std::vector<int16_t> start(M);
-    std::vector<Inc> incs;
-    incs.reserve((size_t)M * (nb > 1 ? nb - 1 : 1));
     double w0 = 0, d0 = 0, wtop = 0;
-    std::vector<int> hull;
-    hull.reserve(nb);
-    std::vector<int> ord(nb);
     for (int64_t i = 0; i < M; i++) {
-        const int64_t item = begin + i;
-        wtop += rate_bits(v, item, nb - 1);
-        // options sorted by (rate, distortion)
-        for (int k = 0; k < nb; k++) ord[k] = k;
-        std::sort(ord.begin(), ord.end(), [&](int a, int b) {
-            double wa = rate_bits(v, item, a), wb = rate_bits(v, item, b);
-            if (wa != wb) return wa < wb;
-            double da = dist(v, item, a), db = dist(v, item, b);
-            if (da != db) return da < db;
-            return a < b;
-        });
-        // lower convex hull of the non-dominated options
-        hull.clear();
-        for (int t = 0; t < nb; t++) {
-            int k = ord[t];
-            double wk = rate_bits(v, item, k), dk = dist(v, item, k);
-            if (!hull.empty() && dk >= dist(v, item, hull.back())) continue;   // dominated
-            if (!hull.empty() && wk == rate_bits(v, item, hull.back())) continue;
-            while (hull.size() >= 2) {
-                int a = hull[hull.size() - 2], b = hull.back();
-                double wa = rate_bits(v, item, a), da = dist(v, item, a);
-                double wb = rate_bits(v, item, b), db = dist(v, item, b);
-                // b is above or on segment a-k: remove
-                double lhs = (db - da) * (wk - wa), rhs = (dk - da) * (wb - wa);
-                if (lhs >= rhs) hull.pop_back(); else break;
-            }
-            hull.push_back(k);
-        }
-        start[i] = (int16_t)hull[0];
-        w0 += rate_bits(v, item, hull[0]);
-        d0 += dist(v, item, hull[0]);
-        for (size_t h = 0; h + 1 < hull.size(); h++) {
-            int a = hull[h], b = hull[h + 1];
-            Inc in;
-            in.dw = rate_bits(v, item, b) - rate_bits(v, item, a);
-            in.dd = dist(v, item, a) - dist(v, item, b);
-            in.eff = in.dd / in.dw;
-            in.item = (int32_t)i;
-            in.level = (int16_t)h;
-            in.to = (int16_t)b;
-            incs.push_back(in);
-        }
+        w0 += H.w0[slot0 + i];
+        d0 += H.d0[slot0 + i];
+        wtop += H.wtop[slot0 + i];
     }
     res->bytes_min = w0 / 8.0 + fixed_bytes;
     res->bytes_top = wtop / 8.0 + fixed_bytes;
@@ -147,106 +163,96 @@ void solve_ratio(const View &v, int64_t begin, int64_t end, double budget, const
         res->status = -1;
         return;
     }
-    // weighted selection: the longest best-first prefix with total dw <= cap - w0
     const double target = cap - w0;
-    size_t a = 0, b = incs.size();
+    // pass 1: rate histogram over the top 16 bits of the efficiency key
+    static thread_local std::vector<double> hist;
+    hist.assign(1 << 16, 0.0);
+    for (int64_t i = 0; i < M; i++) {
+        const int64_t base = (slot0 + i) * S;
+        for (int l = 0; l < H.len[slot0 + i]; l++) hist[eff_key(H.eff[base + l]) >> 48] += H.dw[base + l];
+    }
+    // buckets above the boundary are taken whole
     double taken = 0;
-    while (b - a > 32) {
-        // median-of-three pivot on the total order
-        const Inc &x = incs[a], &y = incs[(a + b) / 2], &z = incs[b - 1];
-        Inc piv = before(x, y) ? (before(y, z) ? y : (before(x, z) ? z : x))
-                               : (before(x, z) ? x : (before(y, z) ? z : y));
-        auto mid = std::partition(incs.begin() + a, incs.begin() + b,
-                                  [&](const Inc &q) { return before(q, piv); });
-        size_t m = (size_t)(mid - incs.begin());
-        if (m == a) {   // pivot is the best of the range: take it alone
-            auto it = std::min_element(incs.begin() + a, incs.begin() + b, before);
-            std::iter_swap(incs.begin() + a, it);
-            if (taken + incs[a].dw <= target) {
-                taken += incs[a].dw;
-                a++;
-                continue;
-            }
-            b = a;
+    int boundary = -1;
+    for (int bk = (1 << 16) - 1; bk >= 0; bk--) {
+        if (taken + hist[bk] <= target) {
+            taken += hist[bk];
+        } else {
+            boundary = bk;
             break;
         }
-        double wsum = 0;
-        for (size_t t = a; t < m; t++) wsum += incs[t].dw;
-        if (taken + wsum <= target) {
-            taken += wsum;
-            a = m;
-        } else {
-            b = m;
+    }
+    std::vector<int16_t> level(M, 0);
+    std::vector<uint8_t> cur(M);
+    double D = d0, W = w0, lp;
+    for (int64_t i = 0; i < M; i++) cur[i] = (uint8_t)H.start[slot0 + i];
+    std::vector<IncRef> edge;
+    for (int64_t i = 0; i < M; i++) {
+        const int64_t base = (slot0 + i) * S;
+        for (int l = 0; l < H.len[slot0 + i]; l++) {
+            const int bk = (int)(eff_key(H.eff[base + l]) >> 48);
+            if (bk > boundary) {
+                // whole bucket taken: the item's earlier levels are in higher buckets too
+                level[i] = (int16_t)(l + 1);
+                cur[i] = (uint8_t)H.to[base + l];
+                D -= H.dd[base + l];
+                W += H.dw[base + l];
+            } else if (bk == boundary) {
+                edge.push_back(IncRef{H.eff[base + l], (int32_t)i, l});
+            }
         }
     }
-    std::sort(incs.begin() + a, incs.begin() + b, before);
-    size_t split = a;
-    while (split < b && taken + incs[split].dw <= target) taken += incs[split++].dw;
-    // [0, split) are the taken increments; split (if < size) is the fractional one
-    std::vector<int16_t> level(M, 0), cur(start);
-    double D = d0, W = w0;
-    for (size_t t = 0; t < split; t++) {
-        // the taken increments of an item are its first levels, in any order here
-        const Inc &in = incs[t];
-        if (in.level + 1 > level[in.item]) {
-            level[in.item] = (int16_t)(in.level + 1);
-            cur[in.item] = in.to;
-        }
-        D -= in.dd;
-        W += in.dw;
+    // pass 2: the boundary bucket in full order
+    std::sort(edge.begin(), edge.end(), inc_before);
+    size_t split = 0;
+    while (split < edge.size()) {
+        const IncRef &e = edge[split];
+        const int64_t at = (slot0 + e.item) * S + e.level;
+        if (taken + H.dw[at] > target) break;
+        taken += H.dw[at];
+        level[e.item] = (int16_t)(e.level + 1);
+        cur[e.item] = (uint8_t)H.to[at];
+        D -= H.dd[at];
+        W += H.dw[at];
+        split++;
     }
-    double lp = D;
-    if (split < incs.size()) {
-        // the split increment is the best remaining one in the total order
-        size_t best = split;
-        for (size_t t = split + 1; t < incs.size() && t < b; t++)
-            if (before(incs[t], incs[best])) best = t;
-        if (b < incs.size())
-            for (size_t t = b; t < incs.size(); t++)
-                if (before(incs[t], incs[best])) best = t;
-        std::iter_swap(incs.begin() + split, incs.begin() + best);
-        const Inc &in = incs[split];
-        double frac = (target - taken) / in.dw;
-        if (frac > 0) lp -= frac * in.dd;
+    lp = D;
+    if (split < edge.size()) {
+        const int64_t at = (slot0 + edge[split].item) * S + edge[split].level;
+        const double frac = (target - taken) / H.dw[at];
+        if (frac > 0) lp -= frac * H.dd[at];
     }
-    // greedy completion: whole next-increments that still fit, best first
-    {
-        // the next increment of every item, keyed by (item, level)
-        std::vector<int32_t> first_inc(M + 1, 0);
-        std::vector<const Inc *> flat(incs.size());
-        {
-            std::vector<int32_t> count(M + 1, 0);
-            for (const Inc &in : incs) count[in.item + 1]++;
-            for (int64_t i = 0; i < M; i++) count[i + 1] += count[i];
-            first_inc = count;
-            std::vector<int32_t> fill(count.begin(), count.end() - 1);
-            for (const Inc &in : incs) flat[fill[in.item]++] = &in;
-            for (int64_t i = 0; i < M; i++)
-                std::sort(flat.begin() + first_inc[i], flat.begin() + first_inc[i + 1],
-                          [](const Inc *p, const Inc *q) { return p->level < q->level; });
+    // greedy completion: whole next increments that still fit, best first
+    struct Cand {
+        double eff;
+        int32_t item, level;
+        bool operator<(const Cand &b) const {   // max-heap on the increment order
+            return inc_before(IncRef{b.eff, b.item, b.level}, IncRef{eff, item, level});
         }
-        auto next_of = [&](int64_t i) -> const Inc * {
-            int32_t at = first_inc[i] + level[i];
-            return at < first_inc[i + 1] ? flat[at] : nullptr;
-        };
-        auto cmp = [](const Inc *p, const Inc *q) { return before(*q, *p); };
-        std::priority_queue<const Inc *, std::vector<const Inc *>, decltype(cmp)> pq(cmp);
-        double rem = cap - W;
-        for (int64_t i = 0; i < M; i++) {
-            const Inc *nx = next_of(i);
-            if (nx && nx->dw <= rem) pq.push(nx);
+    };
+    std::priority_queue<Cand> pq;
+    double rem = cap - W;
+    for (int64_t i = 0; i < M; i++) {
+        const int l = level[i];
+        if (l < H.len[slot0 + i]) {
+            const int64_t at = (slot0 + i) * S + l;
+            if (H.dw[at] <= rem) pq.push(Cand{H.eff[at], (int32_t)i, l});
         }
-        while (!pq.empty()) {
-            const Inc *in = pq.top();
-            pq.pop();
-            if (in->dw > rem || level[in->item] != in->level) continue;
-            cur[in->item] = in->to;
-            level[in->item]++;
-            rem -= in->dw;
-            W += in->dw;
-            D -= in->dd;
-            const Inc *nx = next_of(in->item);
-            if (nx && nx->dw <= rem) pq.push(nx);
+    }
+    while (!pq.empty()) {
+        const Cand c = pq.top();
+        pq.pop();
+        const int64_t at = (slot0 + c.item) * S + c.level;
+        if (H.dw[at] > rem || level[c.item] != c.level) continue;
+        cur[c.item] = (uint8_t)H.to[at];
+        level[c.item]++;
+        rem -= H.dw[at];
+        W += H.dw[at];
+        D -= H.dd[at];
+        const int l = level[c.item];
+        if (l < H.len[slot0 + c.item]) {
+            const int64_t nx = (slot0 + c.item) * S + l;
+            if (H.dw[nx] <= rem) pq.push(Cand{H.eff[nx], c.item, l});
         }
     }
     res->status = 0;
@@ -254,6 +260,24 @@ void solve_ratio(const View &v, int64_t begin, int64_t end, double budget, const
     res->bytes = W / 8.0 + fixed_bytes;
     res->lp = lp;
     res->choice.assign(cur.begin(), cur.end());
+}
+
+template <typename F>
+void parallel_for(int64_t n, int64_t grain, F fn) {
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const int64_t chunks = (n + grain - 1) / grain;
+    const unsigned nt = (unsigned)std::min<int64_t>(hw, chunks);
+    if (nt <= 1) {
+        fn(0, n);
+        return;
+    }
+    std::atomic<int64_t> next{0};
+    std::vector<std::thread> th;
+    for (unsigned t = 0; t < nt; t++)
+        th.emplace_back([&] {
+            for (int64_t c; (c = next.fetch_add(1)) < chunks;) fn(c * grain, std::min(n, (c + 1) * grain));
+        });
+    for (auto &x : th) x.join();
 }
 
 }  // namespace
@@ -307,23 +331,28 @@ mgs_status mgs_solve_budget(const void *table, const mgs_table_layout *layout,
     }
     View v = make_view(table, layout, grid, opts);
     const int nr = layout->n_ratios;
+    const int64_t n_items = layout->item_begin[nr];
+    static thread_local Hulls H_tls;   // capacity persists across calls (no page faults per solve)
+    Hulls &H = H_tls;                  // the caller's instance, shared with the worker threads
+    H.stride = std::max(1, v.n_b - 1);
+    H.eff.resize((size_t)n_items * H.stride);
+    H.dw.resize((size_t)n_items * H.stride);
+    H.dd.resize((size_t)n_items * H.stride);
+    H.to.resize((size_t)n_items * H.stride);
+    H.len.resize(n_items);
+    H.start.resize(n_items);
+    H.w0.resize(n_items);
+    H.d0.resize(n_items);
+    H.wtop.resize(n_items);
+    parallel_for(n_items, 4096, [&](int64_t lo, int64_t hi) {
+        for (int64_t i = lo; i < hi; i++) build_hull(v, i, i, H);
+    });
     std::vector<RatioResult> res(nr);
-    unsigned hw = std::max(1u, std::thread::hardware_concurrency());
-    unsigned nt = std::min<unsigned>(hw, (unsigned)nr);
-    if (nt <= 1) {
-        for (int r = 0; r < nr; r++)
-            solve_ratio(v, layout->item_begin[r], layout->item_begin[r + 1], budget_bytes, opts,
-                        &res[r]);
-    } else {
-        std::vector<std::thread> th;
-        for (unsigned t = 0; t < nt; t++)
-            th.emplace_back([&, t] {
-                for (int r = (int)t; r < nr; r += (int)nt)
-                    solve_ratio(v, layout->item_begin[r], layout->item_begin[r + 1], budget_bytes,
-                                opts, &res[r]);
-            });
-        for (auto &x : th) x.join();
-    }
+    parallel_for(nr, 1, [&](int64_t lo, int64_t hi) {
+        for (int64_t r = lo; r < hi; r++)
+            solve_ratio(H, layout->item_begin[r], layout->item_begin[r + 1] - layout->item_begin[r],
+                        budget_bytes, opts, &res[r]);
+    });
     // tau rule (Alg. 1): skip ratios whose all-top size stays under the budget
     int best = -1, largest_feasible = -1;
     for (int r = 0; r < nr; r++) {

@@ -63,6 +63,24 @@ class mgs_solution(ctypes.Structure):
                 ("ratio_lp_bound", ctypes.c_void_p)]
 
 
+class mgs_server_opts(ctypes.Structure):
+    _fields_ = [("max_jobs", ctypes.c_int32), ("solver_threads", ctypes.c_int32),
+                ("hbm_budget_bytes", ctypes.c_int64), ("slice_items", ctypes.c_int64)]
+
+
+class mgs_job(ctypes.Structure):
+    _fields_ = [("attrs", ctypes.c_void_p), ("importance", ctypes.c_void_p), ("n", ctypes.c_int64),
+                ("n_channels", ctypes.c_int32), ("grid", mgs_grid), ("budget_bytes", ctypes.c_double),
+                ("opts", mgs_solve_opts)]
+
+
+class mgs_job_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("r_index", ctypes.c_int32), ("est_bytes", ctypes.c_double),
+                ("objective", ctypes.c_double), ("lp_bound", ctypes.c_double), ("n_choice", ctypes.c_int64),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_ready", ctypes.c_double),
+                ("t_table", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
 _lib = None
 
 # name -> argtypes (all return mgs_status unless listed in _RESTYPE)
@@ -90,6 +108,12 @@ _SIGS = {
     "mgs_plan_destroy": [_P],
     "mgs_plan_info": [_P, _P, _P, _P],
     "mgs_tile_config_count": [],
+    "mgs_server_create": [_P, ctypes.POINTER(mgs_server_opts), ctypes.POINTER(_P)],
+    "mgs_server_submit": [_P, ctypes.POINTER(mgs_job), ctypes.POINTER(ctypes.c_int64)],
+    "mgs_server_wait": [_P, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(mgs_job_result), _P,
+                        ctypes.c_int64],
+    "mgs_server_stats": [_P, _P, _P, _P, _P],
+    "mgs_server_destroy": [_P],
     "mgs_tile_config_name": [ctypes.c_int32],
     "mgs_set_tile_config": [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32],
     "mgs_autotune": [_P, _P, ctypes.POINTER(mgs_grid), _P, _P, _P],
@@ -272,6 +296,46 @@ def mgs_quantize_groups_noalloc(ctx: int, scene: int, keep: int, group_size: int
     """mgs_quantize_groups for callers that cannot allocate device memory (static scratch)."""
     _check(lib().mgs_quantize_groups_noalloc(ctx, scene, keep, group_size, _ptr(bits), _ptr(codes),
                                              _ptr(minmax), _stream(stream)))
+
+
+def mgs_server_create(ctx: int, max_jobs: int = 8, solver_threads: int = 4,
+                      hbm_budget_bytes: int = 64 << 30, slice_items: int = 20000) -> int:
+    h = ctypes.c_void_p()
+    o = mgs_server_opts(max_jobs, solver_threads, hbm_budget_bytes, slice_items)
+    _check(lib().mgs_server_create(ctx, ctypes.byref(o), ctypes.byref(h)))
+    return h.value
+
+
+def mgs_server_submit(server: int, attrs, importance, grid: Grid, budget_bytes: float, opts) -> int:
+    """attrs / importance: host buffers that stay alive until the job is done."""
+    n, C = attrs.shape
+    j = mgs_job(_ptr(attrs), _ptr(importance), n, C, grid.c, float(budget_bytes), opts)
+    jid = ctypes.c_int64()
+    _check(lib().mgs_server_submit(server, ctypes.byref(j), ctypes.byref(jid)))
+    return jid.value
+
+
+def mgs_server_wait(server: int, job_id: int, timeout_ms: int = 60000, max_choice: int = 0) -> dict:
+    r = mgs_job_result()
+    ch = np.zeros(max(max_choice, 1), dtype=np.uint8)
+    _check(lib().mgs_server_wait(server, job_id, timeout_ms, ctypes.byref(r), ch.ctypes.data,
+                                 max_choice))
+    out = {k: getattr(r, k) for k, _ in mgs_job_result._fields_}
+    out["choice"] = ch[:min(max_choice, r.n_choice)].copy()
+    if r.status != MGS_OK:
+        out["error"] = lib().mgs_last_error().decode(errors="replace")
+    return out
+
+
+def mgs_server_stats(server: int) -> dict:
+    a, b, c, d = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int64()
+    _check(lib().mgs_server_stats(server, ctypes.addressof(a), ctypes.addressof(b),
+                                  ctypes.addressof(c), ctypes.addressof(d)))
+    return dict(launches=a.value, work_items=b.value, in_flight=c.value, used_bytes=d.value)
+
+
+def mgs_server_destroy(server: int):
+    _check(lib().mgs_server_destroy(server))
 
 
 def solve_opts(rate_model: int = MGS_RATE_ENTROPY, norm: int = MGS_NORM_SSE,
