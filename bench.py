@@ -388,12 +388,222 @@ def run_gpu(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# Other workloads (one JSON line each; the default is the scene-scale search)
+# ---------------------------------------------------------------------------
+def _events(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def run_batch(args):
+    """16 scenes of uneven size (log-uniform 3e5..6e6), 10 ratios x 10 bit-widths, in one
+    persistent launch replayed from a CUDA graph; group sizes 1024 / 4096 / 16384, tile
+    shape autotuned per group size.  Compared with one launch per scene."""
+    import torch
+    from paper_2604_26799_gb300 import mgs
+    dev = torch.device("cuda", 0)
+    sizes = [int(x) for x in synth.batch_sizes(16, 300_000, 6_000_000, seed=3)]
+    bits = list(synth.SCENE.bits)
+    ctx = mgs.mgs_create(0)
+    st = torch.cuda.Stream(device=dev)
+    scenes = []
+    for i, n in enumerate(sizes):
+        a, imp = synth.make_scene(n, seed=100 + i)
+        scenes.append(mgs.mgs_scene_create(ctx, torch.from_numpy(a).to(dev), torch.from_numpy(imp).to(dev),
+                                           stream=st))
+        del a, imp
+    keeps = [synth.keep_counts(n, list(synth.tenths())) for n in sizes]
+    evals = sum(int(k.sum()) for k in keeps) * N_CH * len(bits)
+    per_g = {}
+    for G in (1024, 4096, 16384):
+        grids = [mgs.Grid(k, bits, G) for k in keeps]
+        lays = [mgs.mgs_table_layout_for(n, N_CH, g) for n, g in zip(sizes, grids)]
+        tables = [torch.empty(L.total_bytes, dtype=torch.uint8, device=dev) for L in lays]
+        big = int(np.argmax(sizes))
+        chosen, _ = mgs.mgs_autotune(ctx, scenes[big], grids[big], stream=st)
+        with torch.cuda.stream(st):
+            plan = mgs.mgs_plan_create(ctx, scenes, grids, tables, use_graph=True, stream=st)
+            singles = [mgs.mgs_plan_create(ctx, [sc], [g], [t], use_graph=False, stream=st)
+                       for sc, g, t in zip(scenes, grids, tables)]
+            for _ in range(max(1, args.warmup)):
+                mgs.mgs_plan_launch(plan, st)
+                for p in singles:
+                    mgs.mgs_plan_launch(p, st)
+            a, b = _events(torch)
+            a.record(st)
+            for _ in range(args.steps):
+                mgs.mgs_plan_launch(plan, st)
+            b.record(st)
+            b.synchronize()
+            batched_ms = a.elapsed_time(b) / args.steps
+            a.record(st)
+            for _ in range(args.steps):
+                for p in singles:
+                    mgs.mgs_plan_launch(p, st)
+            b.record(st)
+            b.synchronize()
+            seq_ms = a.elapsed_time(b) / args.steps
+            mgs.mgs_plan_destroy(plan)
+            for p in singles:
+                mgs.mgs_plan_destroy(p)
+        per_g[str(G)] = {"tile": mgs.mgs_tile_config_name(chosen), "batched_graph_ms": batched_ms,
+                         "batched_evals_per_s": evals / (batched_ms * 1e-3),
+                         "one_launch_per_scene_ms": seq_ms}
+        del tables
+        torch.cuda.synchronize()
+    for sc in scenes:
+        mgs.mgs_scene_destroy(sc)
+    mgs.mgs_destroy(ctx)
+    best = max(per_g.values(), key=lambda x: x["batched_evals_per_s"])
+    print(json.dumps({"metric": METRIC, "value": best["batched_evals_per_s"], "unit": UNIT, "n_gpus": 1,
+                      "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+                      "dtype": "f32", "data": "synthetic",
+                      "config": {"workload": "batched: 16 scenes, N log-uniform 3e5..6e6 (total %d), "
+                                             "10 ratios x 10 bit-widths, one persistent launch in a CUDA graph"
+                                             % sum(sizes), "sizes": sizes},
+                      "evals_per_pass": evals, "per_group_size": per_g}))
+
+
+def run_serve(args):
+    """Poisson job stream (20 jobs/s; N log-uniform 1e5..6e6; budget U[5, 60] MB; each a
+    10 x 10 search) through the continuous-batching server; p50/p99 time from submission to
+    the ILP answer.  Compared with a one-job-at-a-time plain per-(ratio, bit-width) loop fed
+    the same arrivals (its service times measured per scene)."""
+    import torch
+    from paper_2604_26799_gb300 import mgs
+    dev = torch.device("cuda", 0)
+    n_jobs = int(os.environ.get("MGS_SERVE_JOBS", "120"))
+    t_arr, job_sizes, budgets = synth.poisson_arrivals(n_jobs, 20.0, seed=7)
+    # a pool of resident host scenes; job j uses the pool scene closest to its drawn size
+    pool_n = sorted({int(x) for x in np.quantile(job_sizes, np.linspace(0, 1, 12))})
+    pool = []
+    for i, n in enumerate(pool_n):
+        a, imp = synth.make_scene(n, seed=200 + i)
+        pool.append((torch.from_numpy(a).pin_memory(), torch.from_numpy(imp).pin_memory(), n))
+        del a, imp
+    pick = [int(np.argmin([abs(np.log(p[2]) - np.log(n)) for p in pool])) for n in job_sizes]
+    bits = list(synth.SCENE.bits)
+    grids = [mgs.Grid(synth.keep_counts(p[2], list(synth.tenths())), bits, 4096) for p in pool]
+    opts = mgs.solve_opts()
+    ctx = mgs.mgs_create(0)
+    # warm-up: one job per pool scene (also the plain loop's service time per scene)
+    plain_service = []
+    st = torch.cuda.Stream(device=dev)
+    for (a, imp, n), g in zip(pool, grids):
+        L = mgs.mgs_table_layout_for(n, N_CH, g)
+        tab = torch.empty(L.total_bytes, dtype=torch.uint8).pin_memory()
+        t0 = time.perf_counter()
+        sc = mgs.mgs_scene_create(ctx, a, imp, stream=st)
+        mgs.mgs_build_cost_table_plain(ctx, sc, g, tab, stream=st)
+        mgs.mgs_solve_budget(tab.numpy(), L, g, 30e6, opts)
+        mgs.mgs_scene_destroy(sc)
+        plain_service.append(time.perf_counter() - t0)
+    srv = mgs.mgs_server_create(ctx, max_jobs=8, solver_threads=8, hbm_budget_bytes=120 << 30,
+                                slice_items=40_000)
+    ids, sub_wall = [], []
+    t_start = time.perf_counter()
+    for j in range(n_jobs):
+        now = time.perf_counter() - t_start
+        if t_arr[j] > now:
+            time.sleep(t_arr[j] - now)
+        a, imp, n = pool[pick[j]]
+        ids.append(mgs.mgs_server_submit(srv, a, imp, grids[pick[j]], float(budgets[j]), opts))
+    res = [mgs.mgs_server_wait(srv, i, timeout_ms=600_000) for i in ids]
+    stats = mgs.mgs_server_stats(srv)
+    mgs.mgs_server_destroy(srv)
+    mgs.mgs_destroy(ctx)
+    lat = np.array([r["t_done"] - r["t_submit"] for r in res])
+    ok = sum(1 for r in res if r["status"] == 0)
+    span = max(r["t_done"] for r in res) - min(r["t_submit"] for r in res)
+    # the plain loop, one job at a time, same arrivals
+    finish, plain_lat = 0.0, []
+    for j in range(n_jobs):
+        start = max(t_arr[j], finish)
+        finish = start + plain_service[pick[j]]
+        plain_lat.append(finish - t_arr[j])
+    plain_lat = np.array(plain_lat)
+    evals = sum(int(synth.keep_counts(pool[pick[j]][2], list(synth.tenths())).sum()) for j in range(n_jobs)) \
+        * N_CH * len(bits)
+    print(json.dumps({
+        "metric": "served search latency (submission to ILP answer)", "unit": "s",
+        "value": float(np.percentile(lat, 50)), "p50_s": float(np.percentile(lat, 50)),
+        "p99_s": float(np.percentile(lat, 99)), "jobs_per_s": n_jobs / span, "jobs_ok": ok,
+        "jobs": n_jobs, "evals_per_s": evals / span, "higher_is_better": False,
+        "plain_loop_p50_s": float(np.percentile(plain_lat, 50)),
+        "plain_loop_p99_s": float(np.percentile(plain_lat, 99)),
+        "server": stats, "data": "synthetic",
+        "config": {"workload": "serving: Poisson 20 jobs/s, N log-uniform 1e5..6e6 (12-scene pool), "
+                               "budget U[5,60] MB, 10 ratios x 10 bit-widths, G 4096",
+                   "pool_sizes": pool_n}}))
+
+
+def run_large(args):
+    """6 M Gaussians, 20 ratios (0.05..1.00), bit-widths 1..16, groups of 2048; ILP at 8 budgets."""
+    import torch
+    from paper_2604_26799_gb300 import mgs
+    dev = torch.device("cuda", 0)
+    w = synth.LARGE
+    a, imp = synth.make_scene(w.n, seed=w.seed)
+    a_d, i_d = torch.from_numpy(a).to(dev), torch.from_numpy(imp).to(dev)
+    del a
+    grid = mgs.Grid(w.keep(), list(w.bits), w.group_size)
+    ctx = mgs.mgs_create(0)
+    st = torch.cuda.Stream(device=dev)
+    L = mgs.mgs_table_layout_for(w.n, N_CH, grid)
+    tab = torch.empty(L.total_bytes, dtype=torch.uint8, device=dev)
+    tab_h = torch.empty(L.total_bytes, dtype=torch.uint8).pin_memory()
+    sc = mgs.mgs_scene_create(ctx, a_d, i_d, stream=st)
+    chosen, _ = mgs.mgs_autotune(ctx, sc, grid, stream=st)
+    mgs.mgs_scene_destroy(sc)
+    budgets = [10e6, 20e6, 40e6, 60e6, 80e6, 120e6, 160e6, 240e6]
+    phase = {"scene": [], "kernel": [], "d2h": [], "solve_8_budgets": []}
+    evals = int(w.keep().sum()) * N_CH * len(w.bits)
+    total = 0.0
+    for step in range(args.warmup + args.steps):
+        with torch.cuda.stream(st):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            e[0].record(st)
+            sc = mgs.mgs_scene_create(ctx, a_d, i_d, stream=st)
+            plan = mgs.mgs_plan_create(ctx, [sc], grid, [tab], stream=st)
+            e[1].record(st)
+            mgs.mgs_plan_launch(plan, st)
+            e[2].record(st)
+            tab_h.copy_(tab, non_blocking=True)
+            e[3].record(st)
+            e[3].synchronize()
+            t0 = time.perf_counter()
+            sols = [mgs.mgs_solve_budget(tab_h.numpy(), L, grid, b, mgs.solve_opts()) for b in budgets]
+            ts = time.perf_counter() - t0
+            mgs.mgs_plan_destroy(plan)
+            mgs.mgs_scene_destroy(sc)
+        if step >= args.warmup:
+            phase["scene"].append(e[0].elapsed_time(e[1]))
+            phase["kernel"].append(e[1].elapsed_time(e[2]))
+            phase["d2h"].append(e[2].elapsed_time(e[3]))
+            phase["solve_8_budgets"].append(ts * 1e3)
+            total += e[0].elapsed_time(e[3]) + ts * 1e3
+    mgs.mgs_destroy(ctx)
+    ms = total / args.steps
+    print(json.dumps({"metric": METRIC, "value": evals / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                      "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+                      "config": {"workload": w.name}, "tile": mgs.mgs_tile_config_name(chosen),
+                      "kernel_evals_per_s": evals / (statistics.mean(phase["kernel"]) * 1e-3),
+                      "phase_ms": {k: statistics.mean(v) for k, v in phase.items()},
+                      "solutions": [{"budget": b, "r_index": s["r_index"], "est_bytes": s["est_bytes"]}
+                                    for b, s in zip(budgets, sols)]}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mgs", choices=["mgs", "reference"])
+    ap.add_argument("--workload", default="scene", choices=["scene", "batch", "serve", "large"],
+                    help="scene: the scene-scale search (default); batch: 16 uneven scenes in one "
+                         "graph-replayed launch; serve: Poisson job stream through the server; "
+                         "large: 6 M Gaussians x 20 ratios x 16 bit-widths")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-loop comparator")
     ap.add_argument("--no-autotune", action="store_true", help="use the default tile shape")
@@ -407,6 +617,12 @@ def main():
                                        name=synth.SCENE.name.replace("N=5.27M", f"N={args.n}"))
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
+    if args.workload == "large":
+        return run_large(args)
     return run_gpu(args)
 
 

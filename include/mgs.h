@@ -223,12 +223,13 @@ mgs_status mgs_build_cost_table_plain(mgs_ctx *ctx, const mgs_scene *scene, cons
                                       void *table, void *stream);
 
 /*
- * Several scenes, one grid, one persistent launch over all their
- * (scene, ratio, group, channel-chunk) work items.  tables[s] follows
- * mgs_table_layout_for(n_s, C_s, grid) and must be device memory.
+ * Several scenes, one persistent launch over all their (scene, ratio, group,
+ * channel-chunk) work items.  grids[s] is scene s's grid (its own kept-set
+ * sizes); all grids share the group size and the bit-widths.  tables[s]
+ * follows mgs_table_layout_for(n_s, C_s, &grids[s]) and must be device memory.
  */
 mgs_status mgs_build_cost_tables_batched(mgs_ctx *ctx, int32_t n_scenes,
-                                         const mgs_scene *const *scenes, const mgs_grid *grid,
+                                         const mgs_scene *const *scenes, const mgs_grid *grids,
                                          void *const *tables, void *stream);
 
 /* ---- batched plans, CUDA graphs and tile shapes ------------------------- */
@@ -241,11 +242,12 @@ typedef struct mgs_plan mgs_plan;
  * once; mgs_plan_launch then enqueues one persistent kernel over every
  * (scene, ratio, group, channel-chunk) work item.  With use_graph != 0 the
  * first launch captures that work into a CUDA graph and later launches replay
- * it.  tables[s] follows mgs_table_layout_for(n_s, C_s, grid), device memory;
+ * it.  grids[s] is scene s's grid (all share the group size and bit-widths);
+ * tables[s] follows mgs_table_layout_for(n_s, C_s, &grids[s]), device memory;
  * the scenes and tables must outlive the plan.
  */
 mgs_status mgs_plan_create(mgs_ctx *ctx, int32_t n_scenes, const mgs_scene *const *scenes,
-                           const mgs_grid *grid, void *const *tables, int32_t use_graph,
+                           const mgs_grid *grids, void *const *tables, int32_t use_graph,
                            void *stream, mgs_plan **out);
 mgs_status mgs_plan_launch(mgs_plan *plan, void *stream);
 mgs_status mgs_plan_destroy(mgs_plan *plan);

@@ -435,34 +435,48 @@ mgs_status mgs_build_cost_table_plain(mgs_ctx *ctx, const mgs_scene *scene, cons
     return build_table(ctx, scene, grid, table, stream, true);
 }
 
+static mgs_status same_shape(int32_t n, const mgs_grid *grids) {
+    for (int s = 1; s < n; s++) {
+        if (grids[s].group_size != grids[0].group_size || grids[s].n_bits != grids[0].n_bits ||
+            !grids[s].bits || !grids[0].bits ||
+            std::memcmp(grids[s].bits, grids[0].bits, sizeof(int32_t) * grids[0].n_bits) != 0) {
+            set_error("grid %d differs from grid 0 in group size or bit-widths", s);
+            return MGS_ERR_INVALID_ARG;
+        }
+    }
+    return MGS_OK;
+}
+
 mgs_status mgs_build_cost_tables_batched(mgs_ctx *ctx, int32_t n_scenes,
-                                         const mgs_scene *const *scenes, const mgs_grid *grid,
+                                         const mgs_scene *const *scenes, const mgs_grid *grids,
                                          void *const *tables, void *stream) {
     clear_error();
-    if (!ctx || n_scenes < 1 || !scenes || !tables) {
-        set_error("ctx, scenes and tables must be non-NULL and n_scenes >= 1");
+    if (!ctx || n_scenes < 1 || !scenes || !tables || !grids) {
+        set_error("ctx, scenes, grids and tables must be non-NULL and n_scenes >= 1");
         return MGS_ERR_INVALID_ARG;
     }
-    if ((int64_t)n_scenes * grid->n_ratios > kMaxSegments) {
-        set_error("%d scenes x %d ratios exceed %d segments", n_scenes, grid->n_ratios,
-                  kMaxSegments);
+    MGS_TRY(same_shape(n_scenes, grids));
+    int64_t n_segs = 0;
+    for (int s = 0; s < n_scenes; s++) n_segs += grids[s].n_ratios;
+    if (n_segs > kMaxSegments) {
+        set_error("%lld (scene, ratio) segments exceed %d", (long long)n_segs, kMaxSegments);
         return MGS_ERR_INVALID_ARG;
     }
     DeviceGuard g(ctx->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     CostLaunch launch;
-    launch.group_size = grid->group_size;
-    launch.n_bits = grid->n_bits;
-    for (int k = 0; k < grid->n_bits; k++) launch.bits[k] = grid->bits[k];
+    launch.group_size = grids[0].group_size;
+    launch.n_bits = grids[0].n_bits;
+    for (int k = 0; k < grids[0].n_bits; k++) launch.bits[k] = grids[0].bits[k];
     launch.opt_lo = 0;
-    launch.opt_hi = grid->n_bits;
+    launch.opt_hi = grids[0].n_bits;
     launch.persistent = true;
     for (int s = 0; s < n_scenes; s++) {
         if (!scenes[s] || !tables[s] || !is_device_pointer(tables[s])) {
             set_error("scene %d or its table is NULL or not device memory", s);
             return MGS_ERR_INVALID_ARG;
         }
-        MGS_TRY(scene_segments(const_cast<mgs_scene *>(scenes[s]), grid, tables[s], st,
+        MGS_TRY(scene_segments(const_cast<mgs_scene *>(scenes[s]), &grids[s], tables[s], st,
                                &launch.segs));
     }
     return run_cost(ctx, launch, st);
@@ -591,18 +605,21 @@ struct mgs_plan {
 extern "C" {
 
 mgs_status mgs_plan_create(mgs_ctx *ctx, int32_t n_scenes, const mgs_scene *const *scenes,
-                           const mgs_grid *grid, void *const *tables, int32_t use_graph,
+                           const mgs_grid *grids, void *const *tables, int32_t use_graph,
                            void *stream, mgs_plan **out) {
     clear_error();
-    if (!ctx || n_scenes < 1 || !scenes || !tables || !grid || !out) {
-        set_error("ctx, scenes, grid, tables and out must be non-NULL and n_scenes >= 1");
+    if (!ctx || n_scenes < 1 || !scenes || !tables || !grids || !out) {
+        set_error("ctx, scenes, grids, tables and out must be non-NULL and n_scenes >= 1");
         return MGS_ERR_INVALID_ARG;
     }
-    if ((int64_t)n_scenes * grid->n_ratios > kMaxSegments) {
-        set_error("%d scenes x %d ratios exceed %d segments", n_scenes, grid->n_ratios,
-                  kMaxSegments);
+    MGS_TRY(same_shape(n_scenes, grids));
+    int64_t n_segs = 0;
+    for (int s = 0; s < n_scenes; s++) n_segs += grids[s].n_ratios;
+    if (n_segs > kMaxSegments) {
+        set_error("%lld (scene, ratio) segments exceed %d", (long long)n_segs, kMaxSegments);
         return MGS_ERR_INVALID_ARG;
     }
+    const mgs_grid *grid = &grids[0];
     DeviceGuard g(ctx->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     CostLaunch launch;
@@ -616,7 +633,7 @@ mgs_status mgs_plan_create(mgs_ctx *ctx, int32_t n_scenes, const mgs_scene *cons
             set_error("scene %d or its table is NULL or not device memory", s);
             return MGS_ERR_INVALID_ARG;
         }
-        MGS_TRY(scene_segments(const_cast<mgs_scene *>(scenes[s]), grid, tables[s], st,
+        MGS_TRY(scene_segments(const_cast<mgs_scene *>(scenes[s]), &grids[s], tables[s], st,
                                &launch.segs));
     }
     mgs_plan *P = new (std::nothrow) mgs_plan();

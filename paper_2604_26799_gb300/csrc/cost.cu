@@ -29,14 +29,15 @@
 // Groups where a precondition fails (subnormal S or u, |Z| >= 2^22) take the
 // literal per-element formula.  Pairs of elements use packed f32x2 arithmetic.
 //
-// Histograms live in shared memory, double-buffered so one barrier per
-// bit-width suffices: per-lane columns for b <= 6 and a direct table for
-// b <= 10 (summed after the pass); for larger b the atomic returns the old
-// count j - 1 and the thread adds delta(j) = L(j) - L(j - 1), L(h) = h log2 h in
-// 32.32 fixed point, so sum_j delta telescopes to sum_bins L(h) with no scan
-// (direct 32-bit counters, 16-bit counter pairs, or an open-addressing hash of
-// (code, count) when 2^b exceeds the table).  Entropy sums are integers, so
-// they do not depend on the reduction order.
+// Histograms live in shared memory, in two buffers that consecutive
+// bit-widths alternate between, so one barrier per bit-width suffices:
+// per-lane columns for b <= 6 and a direct table for b <= 10 (summed after the
+// pass); for larger b the atomic returns the old count j - 1 and the thread
+// adds delta(j) = L(j) - L(j - 1), L(h) = h log2 h in 32.32 fixed point, so
+// sum_j delta telescopes to sum_bins L(h) with no scan (direct 32-bit counters
+// or 16-bit counter pairs; a table larger than the big buffer is counted in
+// windows, one pass over the elements per window).  Entropy sums are
+// integers, so they do not depend on the reduction order.
 
 #include <cuda_runtime.h>
 
@@ -54,7 +55,7 @@ constexpr uint32_t kMagicBits = 0x4B400000u;   // its bit pattern
 constexpr int kLaneMaxBits = 6;
 constexpr int kDirectMaxBits = 10;
 
-enum HistMode { kLane = 0, kDirect = 1, kDelta32 = 2, kDelta16 = 3, kHash = 4 };
+enum HistMode { kLane = 0, kDirect = 1, kDelta32 = 2, kDelta16 = 3 };
 enum Path { kFast = 0, kFastBottom = 1, kGeneric = 2, kDegenerate = 3 };
 
 struct BitParam {
@@ -67,6 +68,9 @@ struct BitParam {
     int path;
     int buf;      // histogram buffer: 0, 1 (second small buffer) or 2 (big buffer)
     int sync;     // 1: barrier before the pass (the previous option used the same buffer)
+    int windows;  // passes over the elements (16-bit pairs larger than the big buffer)
+    int wwords;   // words counted per pass (16-bit-pair mode)
+    int pad[2];
 };
 
 struct KernelArgs {
@@ -110,11 +114,11 @@ MGS_F2_BINOP(fsub2, "sub.rn.f32x2")
 
 // ---- shared-memory histogram operations ------------------------------------
 __device__ __forceinline__ void red_add(uint32_t addr, uint32_t v) {
-    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(v));
 }
 __device__ __forceinline__ uint32_t atom_add(uint32_t addr, uint32_t v) {
     uint32_t old;
-    asm volatile("atom.shared.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(addr), "r"(v) : "memory");
+    asm volatile("atom.shared.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(addr), "r"(v));
     return old;
 }
 __device__ __forceinline__ uint32_t atom_cas(uint32_t addr, uint32_t cmp, uint32_t v) {
@@ -132,7 +136,7 @@ __device__ __forceinline__ uint32_t lds(uint32_t addr) {
 // modes the return is delta(new count) to be added to the entropy sum.
 template <int MODE>
 __device__ __forceinline__ void hist_op(uint32_t y, uint32_t hbase, uint32_t lane_base,
-                                        uint32_t log2cap, const unsigned long long *dtab,
+                                        uint32_t wlo, uint32_t wn, const unsigned long long *dtab,
                                         unsigned long long &hacc) {
     if (MODE == kLane) {
         red_add(lane_base + (y << 7), 1u);           // (q * 32 + lane) * 4, magic folded in
@@ -141,35 +145,16 @@ __device__ __forceinline__ void hist_op(uint32_t y, uint32_t hbase, uint32_t lan
     } else if (MODE == kDelta32) {
         uint32_t old = atom_add(hbase + (y << 2), 1u);
         hacc += __ldg(&dtab[old + 1u]);
-    } else if (MODE == kDelta16) {
-        const uint32_t q = y - kMagicBits;
-        const uint32_t sh = (q & 1u) << 4;
-        uint32_t old = atom_add(hbase + ((q >> 1) << 2), 1u << sh);
-        hacc += __ldg(&dtab[((old >> sh) & 0xFFFFu) + 1u]);
     } else {
-        // slot word: (q + 1) << 15 | count, count < 2^15
+        // 16-bit counter pairs; only codes whose word lies in the current window
+        // [wlo, wlo + wn) are counted by this pass
         const uint32_t q = y - kMagicBits;
-        const uint32_t key = (q + 1u) << 15;
-        const uint32_t mask = (1u << log2cap) - 1u;
-        uint32_t s = (q * 2654435769u) >> (32 - log2cap);
-        uint32_t cnt;
-        while (true) {
-            const uint32_t a = hbase + (s << 2);
-            uint32_t v = lds(a);
-            if (v == 0u) {
-                v = atom_cas(a, 0u, key | 1u);
-                if (v == 0u) {
-                    cnt = 0u;
-                    break;
-                }
-            }
-            if ((v & ~0x7FFFu) == key) {
-                cnt = atom_add(a, 1u) & 0x7FFFu;
-                break;
-            }
-            s = (s + 1u) & mask;
+        const uint32_t word = (q >> 1) - wlo;
+        if (word < wn) {
+            const uint32_t sh = (q & 1u) << 4;
+            uint32_t old = atom_add(hbase + (word << 2), 1u << sh);
+            hacc += __ldg(&dtab[((old >> sh) & 0xFFFFu) + 1u]);
         }
-        hacc += __ldg(&dtab[cnt + 1u]);
     }
 }
 
@@ -177,7 +162,7 @@ __device__ __forceinline__ void hist_op(uint32_t y, uint32_t hbase, uint32_t lan
 template <int T, int EPT, int MODE, bool BOTTOM, bool FULL>
 __device__ __forceinline__ void eval_fast(const float (&c)[EPT], const float (&u)[EPT], int nvalid,
                                           const BitParam &p, uint32_t hbase, uint32_t lane_base,
-                                          uint32_t log2cap, const unsigned long long *dtab,
+                                          uint32_t wlo, uint32_t wn, const unsigned long long *dtab,
                                           float &sse, float &l1, float &linf,
                                           unsigned long long &hacc) {
     const float2 tw = make_float2(p.twob, p.twob), zz = make_float2(p.Z, p.Z);
@@ -207,8 +192,8 @@ __device__ __forceinline__ void eval_fast(const float (&c)[EPT], const float (&u
             lb = __fadd_rn(lb, fabsf(er.y));
             ma = fmaxf(ma, fabsf(er.x));
             mb = fmaxf(mb, fabsf(er.y));
-            hist_op<MODE>(__float_as_uint(y.x), hbase, lane_base, log2cap, dtab, hacc);
-            hist_op<MODE>(__float_as_uint(y.y), hbase, lane_base, log2cap, dtab, hacc);
+            hist_op<MODE>(__float_as_uint(y.x), hbase, lane_base, wlo, wn, dtab, hacc);
+            hist_op<MODE>(__float_as_uint(y.y), hbase, lane_base, wlo, wn, dtab, hacc);
         } else if (v0) {
             float x = __fmaf_rn(u[e], p.twob, p.Z);
             float y = __fadd_rn(x, kMagic);
@@ -218,7 +203,7 @@ __device__ __forceinline__ void eval_fast(const float (&c)[EPT], const float (&u
             s2.x = __fmaf_rn(er, er, s2.x);
             la = __fadd_rn(la, fabsf(er));
             ma = fmaxf(ma, fabsf(er));
-            hist_op<MODE>(__float_as_uint(y), hbase, lane_base, log2cap, dtab, hacc);
+            hist_op<MODE>(__float_as_uint(y), hbase, lane_base, wlo, wn, dtab, hacc);
         }
     }
     sse = __fadd_rn(s2.x, s2.y);
@@ -229,8 +214,8 @@ __device__ __forceinline__ void eval_fast(const float (&c)[EPT], const float (&u
 // Literal per-element formula (divisions, both clamps); any group.
 template <int T, int EPT, int MODE>
 __device__ __forceinline__ void eval_generic(const float (&c)[EPT], int nvalid, const BitParam &p,
-                                          uint32_t hbase, uint32_t lane_base, uint32_t log2cap,
-                                          const unsigned long long *dtab, float &sse, float &l1,
+                                          uint32_t hbase, uint32_t lane_base, uint32_t wlo,
+                                          uint32_t wn, const unsigned long long *dtab, float &sse, float &l1,
                                           float &linf, unsigned long long &hacc) {
     float s = 0.0f, a = 0.0f, m = 0.0f;
 #pragma unroll
@@ -244,34 +229,58 @@ __device__ __forceinline__ void eval_generic(const float (&c)[EPT], int nvalid, 
         s = __fmaf_rn(er, er, s);
         a = __fadd_rn(a, fabsf(er));
         m = fmaxf(m, fabsf(er));
-        hist_op<MODE>(kMagicBits + (uint32_t)q, hbase, lane_base, log2cap, dtab, hacc);
+        hist_op<MODE>(kMagicBits + (uint32_t)q, hbase, lane_base, wlo, wn, dtab, hacc);
     }
     sse = s;
     l1 = a;
     linf = m;
 }
 
+// Count-only pass of one window of a 16-bit-pair table (codes as in eval_*).
+template <int T, int EPT>
+__device__ __forceinline__ void count_window(const float (&c)[EPT], const float (&u)[EPT], int nvalid,
+                                          bool generic, const BitParam &p, uint32_t hbase,
+                                          uint32_t wlo, uint32_t wn,
+                                          const unsigned long long *dtab,
+                                          unsigned long long &hacc) {
+#pragma unroll
+    for (int e = 0; e < EPT; e++) {
+        if (e * T + (int)threadIdx.x >= nvalid) continue;
+        uint32_t y;
+        if (generic) {
+            float x = __fadd_rn(__fdiv_rn(c[e], p.Ss), p.Z);
+            y = kMagicBits + (uint32_t)__float2int_rn(fminf(fmaxf(x, 0.0f), p.top));
+        } else {
+            float yf = fminf(__fadd_rn(__fmaf_rn(u[e], p.twob, p.Z), kMagic), p.ytop);
+            if (p.path == kFastBottom) yf = fmaxf(yf, kMagic);
+            y = __float_as_uint(yf);
+        }
+        hist_op<kDelta16>(y, hbase, 0u, wlo, wn, dtab, hacc);
+    }
+}
+
 template <int T, int EPT, int MODE>
 __device__ __forceinline__ void eval_dispatch(const float (&c)[EPT], const float (&u)[EPT],
                                               int nvalid, bool full, bool generic,
                                               const BitParam &p, uint32_t hbase,
-                                              uint32_t lane_base, uint32_t log2cap,
+                                              uint32_t lane_base, uint32_t wlo, uint32_t wn,
                                               const unsigned long long *dtab, float &sse,
                                               float &l1, float &linf, unsigned long long &hacc) {
     if (generic) {
-        eval_generic<T, EPT, MODE>(c, nvalid, p, hbase, lane_base, log2cap, dtab, sse, l1, linf, hacc);
+        eval_generic<T, EPT, MODE>(c, nvalid, p, hbase, lane_base, wlo, wn, dtab, sse, l1, linf, hacc);
     } else if (p.path == kFast) {
-        if (full) eval_fast<T, EPT, MODE, false, true>(c, u, nvalid, p, hbase, lane_base, log2cap, dtab, sse, l1, linf, hacc);
-        else eval_fast<T, EPT, MODE, false, false>(c, u, nvalid, p, hbase, lane_base, log2cap, dtab, sse, l1, linf, hacc);
+        if (full) eval_fast<T, EPT, MODE, false, true>(c, u, nvalid, p, hbase, lane_base, wlo, wn, dtab, sse, l1, linf, hacc);
+        else eval_fast<T, EPT, MODE, false, false>(c, u, nvalid, p, hbase, lane_base, wlo, wn, dtab, sse, l1, linf, hacc);
     } else {
-        if (full) eval_fast<T, EPT, MODE, true, true>(c, u, nvalid, p, hbase, lane_base, log2cap, dtab, sse, l1, linf, hacc);
-        else eval_fast<T, EPT, MODE, true, false>(c, u, nvalid, p, hbase, lane_base, log2cap, dtab, sse, l1, linf, hacc);
+        if (full) eval_fast<T, EPT, MODE, true, true>(c, u, nvalid, p, hbase, lane_base, wlo, wn, dtab, sse, l1, linf, hacc);
+        else eval_fast<T, EPT, MODE, true, false>(c, u, nvalid, p, hbase, lane_base, wlo, wn, dtab, sse, l1, linf, hacc);
     }
 }
 
-// After a pass: add sum L(h) of a summed mode to hacc and clear the buffer.
+// After a pass: add sum L(h) of a summed mode to hacc and clear the buffer
+// (the first clear_words words for the delta modes).
 template <int T>
-__device__ __forceinline__ void hist_finish(uint32_t *hist, int mode, int b, int hist_words,
+__device__ __forceinline__ void hist_finish(uint32_t *hist, int mode, int b, int clear_words,
                                             const unsigned long long *__restrict__ ltab,
                                             unsigned long long &hacc) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -294,9 +303,8 @@ __device__ __forceinline__ void hist_finish(uint32_t *hist, int mode, int b, int
             }
         }
     } else {
-        int words = mode == kDelta32 ? (1 << b) : (mode == kDelta16 ? (1 << (b - 1)) : hist_words);
         uint4 *h4 = reinterpret_cast<uint4 *>(hist);
-        for (int k = threadIdx.x; k < words / 4; k += T) h4[k] = make_uint4(0u, 0u, 0u, 0u);
+        for (int k = threadIdx.x; k < clear_words / 4; k += T) h4[k] = make_uint4(0u, 0u, 0u, 0u);
     }
 }
 
@@ -445,7 +453,6 @@ __device__ void process_item(const KernelArgs &A, const Smem &sm, int64_t work) 
 
     const int n_opts = A.opt_hi - A.opt_lo;
     const int hw = A.hist_words;
-    const uint32_t log2cap = 31 - __clz(hw);
     const uint32_t hist_addr = (uint32_t)__cvta_generic_to_shared(sm.hist);
 #pragma unroll 1
     for (int w = 0; w < W; w++) {
@@ -468,13 +475,20 @@ __device__ void process_item(const KernelArgs &A, const Smem &sm, int64_t work) 
             p.Ss = __fmul_rn(__fmul_rn(p.S, s1), s2);
             const int bw = A.big_words;
             p.buf = 0;
+            p.windows = 1;
+            p.wwords = 1 << (p.b - 1);
             if (p.b <= kLaneMaxBits) p.mode = kLane;
             else if (p.b <= kDirectMaxBits) p.mode = kDirect;
             else if ((1 << p.b) <= hw) p.mode = kDelta32;
             else if ((1 << (p.b - 1)) <= hw) p.mode = kDelta16;
             else if ((1 << p.b) <= bw) { p.mode = kDelta32; p.buf = 2; }
-            else if ((1 << (p.b - 1)) <= bw) { p.mode = kDelta16; p.buf = 2; }
-            else p.mode = kHash;
+            else {
+                // 16-bit pairs in the big buffer, in windows of bw words
+                p.mode = kDelta16;
+                p.buf = 2;
+                p.wwords = min(1 << (p.b - 1), bw);
+                p.windows = (1 << (p.b - 1)) / p.wwords;
+            }
             if (p.S == 0.0f) {
                 p.path = kDegenerate;
                 p.Z = 0.0f;
@@ -556,22 +570,30 @@ __device__ void process_item(const KernelArgs &A, const Smem &sm, int64_t work) 
                 // code bit patterns are kMagicBits + q: fold the offset into the bases
                 const uint32_t lane_base = hbase_raw + lane * 4u - (kMagicBits << 7);
                 const uint32_t dbase = hbase_raw - (kMagicBits << 2);
+                const uint32_t wn = (uint32_t)p.wwords;   // window 0 (the whole table if one)
                 switch (p.mode) {
                     case kLane:
-                        eval_dispatch<T, EPT, kLane>(cw, u, nvalid, full, generic, p, dbase, lane_base, log2cap, A.dtab, sse, l1, linf, hacc);
+                        eval_dispatch<T, EPT, kLane>(cw, u, nvalid, full, generic, p, dbase, lane_base, 0u, wn, A.dtab, sse, l1, linf, hacc);
                         break;
                     case kDirect:
-                        eval_dispatch<T, EPT, kDirect>(cw, u, nvalid, full, generic, p, dbase, lane_base, log2cap, A.dtab, sse, l1, linf, hacc);
+                        eval_dispatch<T, EPT, kDirect>(cw, u, nvalid, full, generic, p, dbase, lane_base, 0u, wn, A.dtab, sse, l1, linf, hacc);
                         break;
                     case kDelta32:
-                        eval_dispatch<T, EPT, kDelta32>(cw, u, nvalid, full, generic, p, dbase, lane_base, log2cap, A.dtab, sse, l1, linf, hacc);
-                        break;
-                    case kDelta16:
-                        eval_dispatch<T, EPT, kDelta16>(cw, u, nvalid, full, generic, p, hbase_raw, lane_base, log2cap, A.dtab, sse, l1, linf, hacc);
+                        eval_dispatch<T, EPT, kDelta32>(cw, u, nvalid, full, generic, p, dbase, lane_base, 0u, wn, A.dtab, sse, l1, linf, hacc);
                         break;
                     default:
-                        eval_dispatch<T, EPT, kHash>(cw, u, nvalid, full, generic, p, hbase_raw, lane_base, log2cap, A.dtab, sse, l1, linf, hacc);
+                        eval_dispatch<T, EPT, kDelta16>(cw, u, nvalid, full, generic, p, hbase_raw, lane_base, 0u, wn, A.dtab, sse, l1, linf, hacc);
                         break;
+                }
+                // further windows of a 16-bit-pair table: wait for every count, clear,
+                // wait, count the next range of codes (the errors are already summed)
+#pragma unroll 1
+                for (int win = 1; win < p.windows; win++) {
+                    __syncthreads();
+                    hist_finish<T>(hist, kDelta16, p.b, p.wwords, A.ltab, hacc);
+                    __syncthreads();
+                    count_window<T, EPT>(cw, u, nvalid, generic, p, hbase_raw, (uint32_t)(win * p.wwords), wn,
+                                         A.dtab, hacc);
                 }
             }
             sm.psse[k * T + threadIdx.x] = sse;
@@ -580,7 +602,7 @@ __device__ void process_item(const KernelArgs &A, const Smem &sm, int64_t work) 
             if (lane == 0) sm.plinf[k * NW + warp] = __uint_as_float(lmax);
             __syncthreads();   // every update of this buffer is done
             if (p.path != kDegenerate)
-                hist_finish<T>(hist, p.mode, p.b, p.buf == 2 ? A.big_words : hw, A.ltab, hacc);
+                hist_finish<T>(hist, p.mode, p.b, p.mode == kDelta32 ? (1 << p.b) : p.wwords, A.ltab, hacc);
             hacc = warp_sum_u64_redux(hacc);
             if (lane == 0) sm.hpart[k * NW + warp] = hacc;
         }
@@ -623,6 +645,7 @@ __global__ void __launch_bounds__(T, (T >= 512 ? 1 : 512 / T))
     const int n_opts = A.opt_hi - A.opt_lo;
     size_t o[7];
     smem_layout(T, W, A.hist_words, A.n_small, A.big_words, n_opts, o);
+    static_assert(EPT % 2 == 0, "elements are processed in pairs");
     Smem sm;
     sm.hist = reinterpret_cast<uint32_t *>(smem_raw + o[0]);
     sm.psse = reinterpret_cast<float *>(smem_raw + o[1]);
@@ -672,21 +695,15 @@ const ConfigEntry kConfigs[] = {
 #undef MGS_CFG
 constexpr int kNumConfigs = sizeof(kConfigs) / sizeof(kConfigs[0]);
 
-// Words per histogram buffer: room for a 2G-slot hash (power of two), >= 2048.
-int hist_words_for(int G) {
-    int cap = 2048;
-    while (cap < 2 * G) cap <<= 1;
-    return cap;
-}
-
-// Histogram buffers of a launch: small buffers of hist_words_for(G) words and,
-// when some bit-width needs more than a small buffer holds even as 16-bit
-// counter pairs, one big buffer of 2^(b_max - 1) words; two small buffers when
-// there is no big one.  Falls back to fewer/smaller buffers (the hash) when
-// shared memory is short.
+// Histogram buffers of a launch.  Small buffers hold the per-lane columns
+// (b <= 6), the direct tables (b <= 10) and the delta tables that fit; a big
+// buffer of 16384 words takes larger bit-widths (32-bit counters up to b = 14,
+// 16-bit pairs for b = 15, and b = 16 in two windows).  With a big buffer there
+// is one small buffer (options alternate between the two); otherwise two.
 struct HistPlan {
     int hist_words, n_small, big_words;
 };
+constexpr int kBigWords = 16384;
 
 size_t smem_for(const CostConfig &c, const HistPlan &h, int n_opts) {
     size_t o[7];
@@ -694,16 +711,14 @@ size_t smem_for(const CostConfig &c, const HistPlan &h, int n_opts) {
 }
 
 HistPlan hist_plan(const CostConfig &c, int G, const int32_t *bits, int n_opts) {
-    HistPlan h{hist_words_for(G), 2, 0};
+    (void)c;
+    HistPlan h{G <= 2048 ? 2048 : 4096, 2, 0};
     int bmax = bits ? 0 : MGS_MAX_BITS;
     for (int k = 0; bits && k < n_opts; k++) bmax = std::max(bmax, (int)bits[k]);
-    const size_t limit = 227 * 1024;
     if ((1 << (bmax - 1)) > h.hist_words) {
-        HistPlan b{h.hist_words, 1, 1 << (bmax - 1)};
-        if (smem_for(c, b, n_opts) <= limit) return b;
+        h.n_small = 1;
+        h.big_words = kBigWords;
     }
-    if (smem_for(c, h, n_opts) <= limit && h.hist_words <= 8192) return h;
-    h.n_small = 1;
     return h;
 }
 

@@ -99,11 +99,10 @@ _SIGS = {
                              ctypes.POINTER(mgs_table_layout)],
     "mgs_build_cost_table": [_P, _P, ctypes.POINTER(mgs_grid), _P, _P],
     "mgs_build_cost_table_plain": [_P, _P, ctypes.POINTER(mgs_grid), _P, _P],
-    "mgs_build_cost_tables_batched": [_P, ctypes.c_int32, _P, ctypes.POINTER(mgs_grid), _P, _P],
+    "mgs_build_cost_tables_batched": [_P, ctypes.c_int32, _P, _P, _P, _P],
     "mgs_quantize_groups": [_P, _P, ctypes.c_int64, ctypes.c_int32, _P, _P, _P, _P],
     "mgs_quantize_groups_noalloc": [_P, _P, ctypes.c_int64, ctypes.c_int32, _P, _P, _P, _P],
-    "mgs_plan_create": [_P, ctypes.c_int32, _P, ctypes.POINTER(mgs_grid), _P, ctypes.c_int32, _P,
-                        ctypes.POINTER(_P)],
+    "mgs_plan_create": [_P, ctypes.c_int32, _P, _P, _P, ctypes.c_int32, _P, ctypes.POINTER(_P)],
     "mgs_plan_launch": [_P, _P],
     "mgs_plan_destroy": [_P],
     "mgs_plan_info": [_P, _P, _P, _P],
@@ -234,10 +233,19 @@ def mgs_build_cost_table_plain(ctx: int, scene: int, grid: Grid, table, stream=N
                                             _stream(stream)))
 
 
-def mgs_build_cost_tables_batched(ctx: int, scenes: list[int], grid: Grid, tables: list, stream=None):
+def _grids(grids, n):
+    """One Grid, or a list of Grids (one per scene), as a C array of mgs_grid."""
+    if isinstance(grids, Grid):
+        grids = [grids] * n
+    arr = (mgs_grid * n)(*[g.c for g in grids])
+    return arr, grids   # keep the Grid objects (and their arrays) alive
+
+
+def mgs_build_cost_tables_batched(ctx: int, scenes: list[int], grids, tables: list, stream=None):
     sc = (ctypes.c_void_p * len(scenes))(*scenes)
     tb = (ctypes.c_void_p * len(tables))(*[_ptr(t) for t in tables])
-    _check(lib().mgs_build_cost_tables_batched(ctx, len(scenes), sc, ctypes.byref(grid.c), tb,
+    ga, _keep = _grids(grids, len(scenes))
+    _check(lib().mgs_build_cost_tables_batched(ctx, len(scenes), sc, ctypes.addressof(ga), tb,
                                                _stream(stream)))
 
 
@@ -247,12 +255,13 @@ def mgs_quantize_groups(ctx: int, scene: int, keep: int, group_size: int, bits, 
                                      _ptr(minmax), _stream(stream)))
 
 
-def mgs_plan_create(ctx: int, scenes: list[int], grid: Grid, tables: list, use_graph: bool = False,
+def mgs_plan_create(ctx: int, scenes: list[int], grids, tables: list, use_graph: bool = False,
                     stream=None) -> int:
     sc = (ctypes.c_void_p * len(scenes))(*scenes)
     tb = (ctypes.c_void_p * len(tables))(*[_ptr(t) for t in tables])
+    ga, _keep = _grids(grids, len(scenes))
     h = ctypes.c_void_p()
-    _check(lib().mgs_plan_create(ctx, len(scenes), sc, ctypes.byref(grid.c), tb, int(use_graph),
+    _check(lib().mgs_plan_create(ctx, len(scenes), sc, ctypes.addressof(ga), tb, int(use_graph),
                                  _stream(stream), ctypes.byref(h)))
     return h.value
 

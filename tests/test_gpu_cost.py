@@ -185,23 +185,22 @@ def test_batched_plan_and_graph_equal_single(ctx):
     bits = [2, 4, 8, 12, 14, 16]
     G = 2048
     sizes = [3000, 17_000, 9000]
-    scenes, tables, singles, lays = [], [], [], []
-    grid_keep = [1000, 2000, 3000]
-    grid = mgs.Grid(grid_keep, bits, G)
+    scenes, tables, singles, grids = [], [], [], []
     try:
         for i, n in enumerate(sizes):
             attrs, imp = synth.make_scene(n, seed=20 + i)
             sc = mgs.mgs_scene_create(ctx, torch.from_numpy(attrs).to(dev), torch.from_numpy(imp).to(dev))
             scenes.append(sc)
+            grid = mgs.Grid(synth.keep_counts(n, [(1, 3), (2, 3), (3, 3)]), bits, G)   # per-scene sizes
+            grids.append(grid)
             L = mgs.mgs_table_layout_for(n, attrs.shape[1], grid)
-            lays.append(L)
             tables.append(torch.zeros(L.total_bytes, dtype=torch.uint8, device=dev))
             one = torch.zeros(L.total_bytes, dtype=torch.uint8, device=dev)
             mgs.mgs_build_cost_table(ctx, sc, grid, one)
             singles.append(one)
         st = torch.cuda.Stream()
         with torch.cuda.stream(st):
-            plan = mgs.mgs_plan_create(ctx, scenes, grid, tables, use_graph=True, stream=st)
+            plan = mgs.mgs_plan_create(ctx, scenes, grids, tables, use_graph=True, stream=st)
             try:
                 for rep in range(3):
                     for t in tables:
@@ -218,10 +217,15 @@ def test_batched_plan_and_graph_equal_single(ctx):
         # the one-shot batched call gives the same tables
         for t in tables:
             t.zero_()
-        mgs.mgs_build_cost_tables_batched(ctx, scenes, grid, tables)
+        mgs.mgs_build_cost_tables_batched(ctx, scenes, grids, tables)
         torch.cuda.synchronize()
         for t, o in zip(tables, singles):
             assert torch.equal(t, o)
+        # grids that disagree in bit-widths cannot share a launch
+        bad = [grids[0], mgs.Grid(grids[1].keep, [2, 4, 8], G), grids[2]]
+        with pytest.raises(mgs.MgsError) as e:
+            mgs.mgs_build_cost_tables_batched(ctx, scenes, bad, tables)
+        assert e.value.status == -1
     finally:
         for sc in scenes:
             mgs.mgs_scene_destroy(sc)
