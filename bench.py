@@ -572,7 +572,7 @@ def run_large(args):
             e[3].record(st)
             e[3].synchronize()
             t0 = time.perf_counter()
-            sols = [mgs.mgs_solve_budget(tab_h.numpy(), L, grid, b, mgs.solve_opts()) for b in budgets]
+            sols = mgs.mgs_solve_budgets(tab_h.numpy(), L, grid, budgets, mgs.solve_opts())
             ts = time.perf_counter() - t0
             mgs.mgs_plan_destroy(plan)
             mgs.mgs_scene_destroy(sc)

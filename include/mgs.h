@@ -152,8 +152,8 @@ typedef struct {
 
 /* ---- context --------------------------------------------------------- */
 
-/* Create a context on CUDA device `device`.  Allocates the entropy table
- * (L(n) = n log2 n in 32.32 fixed point for n <= MGS_MAX_GROUP). */
+/* Create a context on CUDA device `device`.  Allocates the entropy tables
+ * (L(n) = n log2 n and L(n) - L(n - 1) in units of 2^-22 bits, n <= MGS_MAX_GROUP). */
 mgs_status mgs_create(int32_t device, mgs_ctx **out);
 /* Destroy a context; its scenes must have been destroyed first. */
 mgs_status mgs_destroy(mgs_ctx *ctx);
@@ -205,8 +205,10 @@ mgs_status mgs_table_layout_for(int64_t n, int32_t n_channels, const mgs_grid *g
  * (Sec. III-D; round = nearest, ties to even), reconstruction
  * (q - Z) * S, its errors, and the histogram of q.  A group whose S is 0 is
  * degenerate: all codes 0, no error, zero entropy.  Codes and histograms are
- * exact FP32 evaluations of those formulas; sums are FP32 per thread and
- * tree-reduced (relative error below 1e-5 against FP64).
+ * exact FP32 evaluations of those formulas; error sums are FP32 per thread and
+ * tree-reduced (relative error below 1e-5 against FP64); the entropy bound is
+ * an integer sum of L(h) = h log2 h rounded to 2^-22 bits (error at most
+ * (bins + 1) * 2^-23 bits).
  *   table  layout.total_bytes bytes, device or host (host: copied back, the
  *          stream is synchronised).
  */
@@ -390,6 +392,16 @@ mgs_status mgs_estimate_size(const void *table, const mgs_table_layout *layout,
 mgs_status mgs_solve_budget(const void *table, const mgs_table_layout *layout,
                             const mgs_grid *grid, double budget_bytes, const mgs_solve_opts *opts,
                             mgs_solution *out);
+
+/*
+ * mgs_solve_budget for several budgets over the same table: the per-item hulls
+ * are built once and every (budget, ratio) pair is solved in parallel.
+ * out[i] answers budgets[i]; returns MGS_ERR_INFEASIBLE if any budget is
+ * infeasible (that entry has r_index = -1; the others are filled).
+ */
+mgs_status mgs_solve_budgets(const void *table, const mgs_table_layout *layout,
+                             const mgs_grid *grid, int32_t n_budgets, const double *budgets,
+                             const mgs_solve_opts *opts, mgs_solution *out);
 
 #ifdef __cplusplus
 }

@@ -201,19 +201,20 @@ mgs_status mgs_create(int32_t device, mgs_ctx **out) {
         set_error("cudaDeviceGetAttribute: %s", cudaGetErrorString(e));
         return MGS_ERR_CUDA;
     }
-    // L(h) = h log2 h, 32.32 fixed point, h = 0..MGS_MAX_GROUP (L(0) = L(1) = 0), and its
-    // increments L(h) - L(h - 1), which telescope exactly back to L.
-    std::vector<unsigned long long> lt(MGS_MAX_GROUP + 1, 0ull), dt(MGS_MAX_GROUP + 1, 0ull);
+    // L(h) = h log2 h in units of 2^-22 bits, h = 0..MGS_MAX_GROUP (L(0) = L(1) = 0), and
+    // its increments L(h) - L(h - 1) (< 2^26), which telescope exactly back to L.
+    std::vector<unsigned long long> lt(MGS_MAX_GROUP + 1, 0ull);
+    std::vector<uint32_t> dt(MGS_MAX_GROUP + 1, 0u);
     for (int h = 2; h <= MGS_MAX_GROUP; h++)
-        lt[h] = (unsigned long long)std::llround((double)h * std::log2((double)h) * 4294967296.0);
-    for (int h = 1; h <= MGS_MAX_GROUP; h++) dt[h] = lt[h] - lt[h - 1];
-    const size_t tb = sizeof(unsigned long long) * lt.size();
-    e = cudaMalloc(&ctx->d_ltab, 2 * tb);
+        lt[h] = (unsigned long long)std::llround((double)h * std::log2((double)h) * 4194304.0);
+    for (int h = 1; h <= MGS_MAX_GROUP; h++) dt[h] = (uint32_t)(lt[h] - lt[h - 1]);
+    const size_t lb = sizeof(unsigned long long) * lt.size(), db = sizeof(uint32_t) * dt.size();
+    e = cudaMalloc(&ctx->d_ltab, lb + db);
     if (e == cudaSuccess) {
-        ctx->d_dtab = ctx->d_ltab + lt.size();
-        e = cudaMemcpy(ctx->d_ltab, lt.data(), tb, cudaMemcpyHostToDevice);
+        ctx->d_dtab = reinterpret_cast<uint32_t *>(ctx->d_ltab + lt.size());
+        e = cudaMemcpy(ctx->d_ltab, lt.data(), lb, cudaMemcpyHostToDevice);
     }
-    if (e == cudaSuccess) e = cudaMemcpy(ctx->d_dtab, dt.data(), tb, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(ctx->d_dtab, dt.data(), db, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(ctx->d_ltab);
         delete ctx;

@@ -33,7 +33,7 @@
 // bit-widths alternate between, so one barrier per bit-width suffices:
 // per-lane columns for b <= 6 and a direct table for b <= 10 (summed after the
 // pass); for larger b the atomic returns the old count j - 1 and the thread
-// adds delta(j) = L(j) - L(j - 1), L(h) = h log2 h in 32.32 fixed point, so
+// adds delta(j) = L(j) - L(j - 1), L(h) = h log2 h in units of 2^-22 bits, so
 // sum_j delta telescopes to sum_bins L(h) with no scan (direct 32-bit counters
 // or 16-bit counter pairs; a table larger than the big buffer is counted in
 // windows, one pass over the elements per window).  Entropy sums are
@@ -81,8 +81,8 @@ struct KernelArgs {
     int32_t n_bits;
     int32_t opt_lo, opt_hi;
     int32_t bits[MGS_MAX_OPTIONS];
-    const unsigned long long *ltab;   // L(h)
-    const unsigned long long *dtab;   // L(h) - L(h - 1)
+    const unsigned long long *ltab;   // L(h) in 2^-22 bits
+    const uint32_t *dtab;             // L(h) - L(h - 1) in 2^-22 bits (< 2^26)
     unsigned int *counter;
     int32_t hist_words;               // words per small histogram buffer (power of two)
     int32_t n_small;                  // small buffers (1 or 2)
@@ -136,15 +136,15 @@ __device__ __forceinline__ uint32_t lds(uint32_t addr) {
 // modes the return is delta(new count) to be added to the entropy sum.
 template <int MODE>
 __device__ __forceinline__ void hist_op(uint32_t y, uint32_t hbase, uint32_t lane_base,
-                                        uint32_t wlo, uint32_t wn, const unsigned long long *dtab,
-                                        unsigned long long &hacc) {
+                                        uint32_t wlo, uint32_t wn, const uint32_t *dtab,
+                                        uint32_t &dacc) {
     if (MODE == kLane) {
         red_add(lane_base + (y << 7), 1u);           // (q * 32 + lane) * 4, magic folded in
     } else if (MODE == kDirect) {
         red_add(hbase + (y << 2), 1u);               // q * 4, magic folded in
     } else if (MODE == kDelta32) {
         uint32_t old = atom_add(hbase + (y << 2), 1u);
-        hacc += __ldg(&dtab[old + 1u]);
+        dacc += __ldg(&dtab[old + 1u]);
     } else {
         // 16-bit counter pairs; only codes whose word lies in the current window
         // [wlo, wlo + wn) are counted by this pass
@@ -153,7 +153,7 @@ __device__ __forceinline__ void hist_op(uint32_t y, uint32_t hbase, uint32_t lan
         if (word < wn) {
             const uint32_t sh = (q & 1u) << 4;
             uint32_t old = atom_add(hbase + (word << 2), 1u << sh);
-            hacc += __ldg(&dtab[((old >> sh) & 0xFFFFu) + 1u]);
+            dacc += __ldg(&dtab[((old >> sh) & 0xFFFFu) + 1u]);
         }
     }
 }
@@ -162,13 +162,14 @@ __device__ __forceinline__ void hist_op(uint32_t y, uint32_t hbase, uint32_t lan
 template <int T, int EPT, int MODE, bool BOTTOM, bool FULL>
 __device__ __forceinline__ void eval_fast(const float (&c)[EPT], const float (&u)[EPT], int nvalid,
                                           const BitParam &p, uint32_t hbase, uint32_t lane_base,
-                                          uint32_t wlo, uint32_t wn, const unsigned long long *dtab,
+                                          uint32_t wlo, uint32_t wn, const uint32_t *dtab,
                                           float &sse, float &l1, float &linf,
                                           unsigned long long &hacc) {
     const float2 tw = make_float2(p.twob, p.twob), zz = make_float2(p.Z, p.Z);
     const float2 mg = make_float2(kMagic, kMagic), mz = make_float2(p.MZ, p.MZ);
     float2 s2 = make_float2(0.0f, 0.0f);
     float la = 0.0f, lb = 0.0f, ma = 0.0f, mb = 0.0f;
+    uint32_t dacc = 0;   // delta sums: at most EPT * 2^26 < 2^32
 #pragma unroll
     for (int e = 0; e < EPT; e += 2) {
         const bool v1 = FULL || (e + 1) * T + (int)threadIdx.x < nvalid;
@@ -192,8 +193,8 @@ __device__ __forceinline__ void eval_fast(const float (&c)[EPT], const float (&u
             lb = __fadd_rn(lb, fabsf(er.y));
             ma = fmaxf(ma, fabsf(er.x));
             mb = fmaxf(mb, fabsf(er.y));
-            hist_op<MODE>(__float_as_uint(y.x), hbase, lane_base, wlo, wn, dtab, hacc);
-            hist_op<MODE>(__float_as_uint(y.y), hbase, lane_base, wlo, wn, dtab, hacc);
+            hist_op<MODE>(__float_as_uint(y.x), hbase, lane_base, wlo, wn, dtab, dacc);
+            hist_op<MODE>(__float_as_uint(y.y), hbase, lane_base, wlo, wn, dtab, dacc);
         } else if (v0) {
             float x = __fmaf_rn(u[e], p.twob, p.Z);
             float y = __fadd_rn(x, kMagic);
@@ -203,21 +204,23 @@ __device__ __forceinline__ void eval_fast(const float (&c)[EPT], const float (&u
             s2.x = __fmaf_rn(er, er, s2.x);
             la = __fadd_rn(la, fabsf(er));
             ma = fmaxf(ma, fabsf(er));
-            hist_op<MODE>(__float_as_uint(y), hbase, lane_base, wlo, wn, dtab, hacc);
+            hist_op<MODE>(__float_as_uint(y), hbase, lane_base, wlo, wn, dtab, dacc);
         }
     }
     sse = __fadd_rn(s2.x, s2.y);
     l1 = __fadd_rn(la, lb);
     linf = fmaxf(ma, mb);
+    hacc += dacc;
 }
 
 // Literal per-element formula (divisions, both clamps); any group.
 template <int T, int EPT, int MODE>
 __device__ __forceinline__ void eval_generic(const float (&c)[EPT], int nvalid, const BitParam &p,
                                           uint32_t hbase, uint32_t lane_base, uint32_t wlo,
-                                          uint32_t wn, const unsigned long long *dtab, float &sse, float &l1,
+                                          uint32_t wn, const uint32_t *dtab, float &sse, float &l1,
                                           float &linf, unsigned long long &hacc) {
     float s = 0.0f, a = 0.0f, m = 0.0f;
+    uint32_t dacc = 0;
 #pragma unroll
     for (int e = 0; e < EPT; e++) {
         if (e * T + (int)threadIdx.x >= nvalid) continue;
@@ -229,11 +232,12 @@ __device__ __forceinline__ void eval_generic(const float (&c)[EPT], int nvalid, 
         s = __fmaf_rn(er, er, s);
         a = __fadd_rn(a, fabsf(er));
         m = fmaxf(m, fabsf(er));
-        hist_op<MODE>(kMagicBits + (uint32_t)q, hbase, lane_base, wlo, wn, dtab, hacc);
+        hist_op<MODE>(kMagicBits + (uint32_t)q, hbase, lane_base, wlo, wn, dtab, dacc);
     }
     sse = s;
     l1 = a;
     linf = m;
+    hacc += dacc;
 }
 
 // Count-only pass of one window of a 16-bit-pair table (codes as in eval_*).
@@ -241,8 +245,9 @@ template <int T, int EPT>
 __device__ __forceinline__ void count_window(const float (&c)[EPT], const float (&u)[EPT], int nvalid,
                                           bool generic, const BitParam &p, uint32_t hbase,
                                           uint32_t wlo, uint32_t wn,
-                                          const unsigned long long *dtab,
+                                          const uint32_t *dtab,
                                           unsigned long long &hacc) {
+    uint32_t dacc = 0;
 #pragma unroll
     for (int e = 0; e < EPT; e++) {
         if (e * T + (int)threadIdx.x >= nvalid) continue;
@@ -255,8 +260,9 @@ __device__ __forceinline__ void count_window(const float (&c)[EPT], const float 
             if (p.path == kFastBottom) yf = fmaxf(yf, kMagic);
             y = __float_as_uint(yf);
         }
-        hist_op<kDelta16>(y, hbase, 0u, wlo, wn, dtab, hacc);
+        hist_op<kDelta16>(y, hbase, 0u, wlo, wn, dtab, dacc);
     }
+    hacc += dacc;
 }
 
 template <int T, int EPT, int MODE>
@@ -264,7 +270,7 @@ __device__ __forceinline__ void eval_dispatch(const float (&c)[EPT], const float
                                               int nvalid, bool full, bool generic,
                                               const BitParam &p, uint32_t hbase,
                                               uint32_t lane_base, uint32_t wlo, uint32_t wn,
-                                              const unsigned long long *dtab, float &sse,
+                                              const uint32_t *dtab, float &sse,
                                               float &l1, float &linf, unsigned long long &hacc) {
     if (generic) {
         eval_generic<T, EPT, MODE>(c, nvalid, p, hbase, lane_base, wlo, wn, dtab, sse, l1, linf, hacc);
@@ -286,6 +292,7 @@ __device__ __forceinline__ void hist_finish(uint32_t *hist, int mode, int b, int
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (mode == kLane) {
         const int bins = 1 << b;
+#pragma unroll 2
         for (int k = warp; k < bins; k += T / 32) {
             uint32_t v = hist[k * 32 + lane];
             hist[k * 32 + lane] = 0u;
@@ -309,13 +316,12 @@ __device__ __forceinline__ void hist_finish(uint32_t *hist, int mode, int b, int
 }
 
 __device__ __forceinline__ unsigned long long warp_sum_u64_redux(unsigned long long v) {
-    // three 22-bit slices, each summed exactly with redux.sync
-    uint32_t lo = (uint32_t)(v & 0x3FFFFFull), mid = (uint32_t)((v >> 22) & 0x3FFFFFull),
-             hi = (uint32_t)(v >> 44);
+    // v < 2^48 (entropy sums of one group in 2^-22 bits): two 24-bit slices, each
+    // summed exactly with redux.sync (32 x 2^24 < 2^32)
+    uint32_t lo = (uint32_t)(v & 0xFFFFFFull), hi = (uint32_t)(v >> 24);
     lo = __reduce_add_sync(kFull, lo);
-    mid = __reduce_add_sync(kFull, mid);
     hi = __reduce_add_sync(kFull, hi);
-    return (unsigned long long)lo + ((unsigned long long)mid << 22) + ((unsigned long long)hi << 44);
+    return (unsigned long long)lo + ((unsigned long long)hi << 24);
 }
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
@@ -631,7 +637,7 @@ __device__ void process_item(const KernelArgs &A, const Smem &sm, int64_t work) 
                 S.l1[o] = (double)b * inv;
                 S.linf[o] = (float)((double)cmax * inv);
                 unsigned long long ln = __ldg(&A.ltab[nvalid]);
-                S.hbits[o] = (double)(long long)(ln - hs) * (1.0 / 4294967296.0);
+                S.hbits[o] = (double)(long long)(ln - hs) * (1.0 / 4194304.0);   // 2^-22
             }
         }
         __syncthreads();

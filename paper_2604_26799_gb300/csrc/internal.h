@@ -33,7 +33,7 @@ void clear_error();
     } while (0)
 
 constexpr int kSlabWidth = 8;         // channels per slab row (32 bytes)
-constexpr int kLtabFracBits = 32;     // fixed point of L(n) = n log2 n
+constexpr int kLtabFracBits = 22;     // fixed point of L(n) = n log2 n
 constexpr int kMaxSegments = 4096;    // (scene, ratio) pairs in one batched launch
 
 // Device buffer owned by the library (stream-ordered allocation).
@@ -62,8 +62,8 @@ struct TileChoice {
 struct mgs_ctx {
     int device = 0;
     int sm_count = 0;
-    unsigned long long *d_ltab = nullptr;   // L(n) for n in [0, MGS_MAX_GROUP], 32.32 fixed point
-    unsigned long long *d_dtab = nullptr;   // L(n) - L(n - 1), same range (0 at n = 0)
+    unsigned long long *d_ltab = nullptr;   // L(n) = n log2 n for n in [0, MGS_MAX_GROUP], 2^-22 bits
+    uint32_t *d_dtab = nullptr;             // L(n) - L(n - 1), same range and unit (0 at n = 0)
     std::mutex mu;
     std::vector<mgs::TileChoice> tiles;     // autotuned choices
     int forced_config = -1;                 // testing hook: force a tile configuration

@@ -315,20 +315,24 @@ mgs_status mgs_estimate_size(const void *table, const mgs_table_layout *layout,
     return MGS_OK;
 }
 
-mgs_status mgs_solve_budget(const void *table, const mgs_table_layout *layout,
-                            const mgs_grid *grid, double budget_bytes, const mgs_solve_opts *opts,
-                            mgs_solution *out) {
+mgs_status mgs_solve_budgets(const void *table, const mgs_table_layout *layout,
+                             const mgs_grid *grid, int32_t n_budgets, const double *budgets,
+                             const mgs_solve_opts *opts, mgs_solution *out) {
     clear_error();
-    if (!table || !layout || !grid || !opts || !out) {
-        set_error("table, layout, grid, opts and out must be non-NULL");
+    if (!table || !layout || !grid || !opts || !out || !budgets || n_budgets < 1) {
+        set_error("table, layout, grid, budgets, opts and out must be non-NULL; n_budgets >= 1");
         return MGS_ERR_INVALID_ARG;
     }
     if (grid->n_bits != layout->n_bits || grid->n_ratios != layout->n_ratios ||
-        opts->rate_model < 0 || opts->rate_model > 1 || opts->norm < 0 || opts->norm > 3 ||
-        !(budget_bytes >= 0)) {
+        opts->rate_model < 0 || opts->rate_model > 1 || opts->norm < 0 || opts->norm > 3) {
         set_error("grid/layout mismatch or bad options");
         return MGS_ERR_INVALID_ARG;
     }
+    for (int i = 0; i < n_budgets; i++)
+        if (!(budgets[i] >= 0)) {
+            set_error("budget %d is negative or NaN", i);
+            return MGS_ERR_INVALID_ARG;
+        }
     View v = make_view(table, layout, grid, opts);
     const int nr = layout->n_ratios;
     const int64_t n_items = layout->item_begin[nr];
@@ -347,44 +351,58 @@ mgs_status mgs_solve_budget(const void *table, const mgs_table_layout *layout,
     parallel_for(n_items, 4096, [&](int64_t lo, int64_t hi) {
         for (int64_t i = lo; i < hi; i++) build_hull(v, i, i, H);
     });
-    std::vector<RatioResult> res(nr);
-    parallel_for(nr, 1, [&](int64_t lo, int64_t hi) {
-        for (int64_t r = lo; r < hi; r++)
+    // every (budget, ratio) pair is independent once the hulls exist
+    std::vector<RatioResult> res((size_t)n_budgets * nr);
+    parallel_for((int64_t)n_budgets * nr, 1, [&](int64_t lo, int64_t hi) {
+        for (int64_t t = lo; t < hi; t++) {
+            const int bi = (int)(t / nr), r = (int)(t % nr);
             solve_ratio(H, layout->item_begin[r], layout->item_begin[r + 1] - layout->item_begin[r],
-                        budget_bytes, opts, &res[r]);
+                        budgets[bi], opts, &res[t]);
+        }
     });
-    // tau rule (Alg. 1): skip ratios whose all-top size stays under the budget
-    int best = -1, largest_feasible = -1;
-    for (int r = 0; r < nr; r++) {
-        if (res[r].status < 0) continue;
-        largest_feasible = r;
-        if (res[r].bytes_top < budget_bytes) {
-            res[r].status = 1;
+    mgs_status worst = MGS_OK;
+    for (int bi = 0; bi < n_budgets; bi++) {
+        RatioResult *rr = &res[(size_t)bi * nr];
+        mgs_solution *o = &out[bi];
+        // tau rule (Alg. 1): skip ratios whose all-top size stays under the budget
+        int best = -1, largest_feasible = -1;
+        for (int r = 0; r < nr; r++) {
+            if (rr[r].status < 0) continue;
+            largest_feasible = r;
+            if (rr[r].bytes_top < budgets[bi]) {
+                rr[r].status = 1;
+                continue;
+            }
+            if (best < 0 || rr[r].objective <= rr[best].objective) best = r;
+        }
+        if (best < 0) best = largest_feasible;
+        for (int r = 0; r < nr; r++) {
+            if (o->ratio_status) o->ratio_status[r] = rr[r].status;
+            if (o->ratio_objective) o->ratio_objective[r] = rr[r].objective;
+            if (o->ratio_bytes) o->ratio_bytes[r] = rr[r].bytes;
+            if (o->ratio_lp_bound) o->ratio_lp_bound[r] = rr[r].lp;
+        }
+        o->r_index = best;
+        if (best < 0) {
+            o->est_bytes = 0;
+            o->objective = 0;
+            o->lp_bound = 0;
+            set_error("no ratio fits a budget of %.0f bytes", budgets[bi]);
+            worst = MGS_ERR_INFEASIBLE;
             continue;
         }
-        if (best < 0 || res[r].objective <= res[best].objective) best = r;
+        o->est_bytes = rr[best].bytes;
+        o->objective = rr[best].objective;
+        o->lp_bound = rr[best].lp;
+        if (o->choice) std::memcpy(o->choice, rr[best].choice.data(), rr[best].choice.size());
     }
-    if (best < 0) best = largest_feasible;
-    for (int r = 0; r < nr; r++) {
-        if (out->ratio_status) out->ratio_status[r] = res[r].status;
-        if (out->ratio_objective) out->ratio_objective[r] = res[r].objective;
-        if (out->ratio_bytes) out->ratio_bytes[r] = res[r].bytes;
-        if (out->ratio_lp_bound) out->ratio_lp_bound[r] = res[r].lp;
-    }
-    out->r_index = best;
-    if (best < 0) {
-        out->est_bytes = 0;
-        out->objective = 0;
-        out->lp_bound = 0;
-        set_error("no ratio fits a budget of %.0f bytes", budget_bytes);
-        return MGS_ERR_INFEASIBLE;
-    }
-    out->est_bytes = res[best].bytes;
-    out->objective = res[best].objective;
-    out->lp_bound = res[best].lp;
-    if (out->choice)
-        std::memcpy(out->choice, res[best].choice.data(), res[best].choice.size());
-    return MGS_OK;
+    return worst;
+}
+
+mgs_status mgs_solve_budget(const void *table, const mgs_table_layout *layout,
+                            const mgs_grid *grid, double budget_bytes, const mgs_solve_opts *opts,
+                            mgs_solution *out) {
+    return mgs_solve_budgets(table, layout, grid, 1, &budget_bytes, opts, out);
 }
 
 }  // extern "C"

@@ -122,6 +122,8 @@ _SIGS = {
     "mgs_solve_budget": [_P, ctypes.POINTER(mgs_table_layout), ctypes.POINTER(mgs_grid),
                          ctypes.c_double, ctypes.POINTER(mgs_solve_opts),
                          ctypes.POINTER(mgs_solution)],
+    "mgs_solve_budgets": [_P, ctypes.POINTER(mgs_table_layout), ctypes.POINTER(mgs_grid),
+                          ctypes.c_int32, _P, ctypes.POINTER(mgs_solve_opts), _P],
 }
 _RESTYPE = {"mgs_last_error": ctypes.c_char_p, "mgs_version": ctypes.c_char_p,
             "mgs_tile_config_name": ctypes.c_char_p, "mgs_tile_config_count": ctypes.c_int32,
@@ -382,6 +384,34 @@ def mgs_solve_budget(table_host, layout: mgs_table_layout, grid: Grid, budget_by
     return dict(status=rc, r_index=r, est_bytes=sol.est_bytes, objective=sol.objective,
                 lp_bound=sol.lp_bound, choice=choice[:n_items].copy(), ratio_status=st,
                 ratio_objective=obj, ratio_bytes=byt, ratio_lp_bound=lp)
+
+
+def mgs_solve_budgets(table_host, layout: mgs_table_layout, grid: Grid, budgets, opts) -> list[dict]:
+    """One solution per budget; the item hulls are shared."""
+    nb = len(budgets)
+    nr = layout.n_ratios
+    max_items = max(int(layout.item_begin[r + 1] - layout.item_begin[r]) for r in range(nr))
+    bud = np.ascontiguousarray(budgets, dtype=np.float64)
+    keep = []
+    sols = (mgs_solution * nb)()
+    for i in range(nb):
+        arrs = (np.zeros(max(max_items, 1), dtype=np.uint8), np.zeros(nr, dtype=np.int32),
+                np.zeros(nr), np.zeros(nr), np.zeros(nr))
+        keep.append(arrs)
+        sols[i] = mgs_solution(-1, 0.0, 0.0, 0.0, *[a.ctypes.data for a in arrs])
+    rc = lib().mgs_solve_budgets(_ptr(table_host), ctypes.byref(layout), ctypes.byref(grid.c), nb,
+                                 bud.ctypes.data, ctypes.byref(opts), ctypes.addressof(sols))
+    if rc not in (MGS_OK, -6):
+        _check(rc)
+    out = []
+    for i in range(nb):
+        r = sols[i].r_index
+        n_items = int(layout.item_begin[r + 1] - layout.item_begin[r]) if r >= 0 else 0
+        ch, st, ob, by, lp = keep[i]
+        out.append(dict(r_index=r, est_bytes=sols[i].est_bytes, objective=sols[i].objective,
+                        lp_bound=sols[i].lp_bound, choice=ch[:n_items].copy(), ratio_status=st,
+                        ratio_objective=ob, ratio_bytes=by, ratio_lp_bound=lp))
+    return out
 
 
 def table_views(buf, layout: mgs_table_layout) -> dict:

@@ -151,3 +151,17 @@ def test_solver_tau_rule_and_scale(L):
                     assert sol["ratio_lp_bound"][r] <= sol["ratio_objective"][r] * (1 + 1e-12) + 1e-12
             expect = mckp.choose_tau(per_r, budget)
             assert sol["r_index"] == (-1 if expect is None else expect)
+
+
+def test_solve_budgets_equals_one_at_a_time(L):
+    rng = np.random.default_rng(21)
+    keep = np.array([300, 700, 1500], dtype=np.int64)
+    bits = [2, 4, 6, 8, 12, 16]
+    buf, lay, grid, v = synthetic_table(rng, keep, bits, 128, 5)
+    budgets = [2e3, 5e3, 1.2e4, 3e4, 1e9]
+    many = mgs.mgs_solve_budgets(buf, lay, grid, budgets, mgs.solve_opts())
+    for b, m in zip(budgets, many):
+        one = mgs.mgs_solve_budget(buf, lay, grid, b, mgs.solve_opts())
+        assert one["r_index"] == m["r_index"]
+        assert one["est_bytes"] == m["est_bytes"] and one["objective"] == m["objective"]
+        assert np.array_equal(one["choice"], m["choice"])
