@@ -225,13 +225,11 @@ def run_gpu(args):
     ctx = mgs.mgs_create(dev.index)
     L = mgs.mgs_table_layout_for(w.n, N_CH, grid)
     table_d = torch.empty(L.total_bytes, dtype=torch.uint8, device=dev)
-    table_h = torch.empty(L.total_bytes, dtype=torch.uint8).pin_memory()
-    table_np = table_h.numpy()
     opts = mgs.solve_opts()
     st = torch.cuda.Stream(device=dev)
     evals = evals_of(w)
     kernel_ms: list[float] = []
-    phase = {"scene": [], "plan": [], "kernel": [], "d2h": [], "solve": []}
+    phase = {"scene": [], "plan": [], "kernel": [], "solve": []}
 
     def step(record: bool):
         with torch.cuda.stream(st):
@@ -243,20 +241,17 @@ def run_gpu(args):
             e[2].record(st)
             mgs.mgs_plan_launch(plan, st)
             e[3].record(st)
-            table_h.copy_(table_d, non_blocking=True)
+            # the budget solve on the device; only the chosen options come back
+            sol = mgs.mgs_solve_budgets_device(ctx, table_d, L, grid, [w.budget_bytes], opts, stream=st)[0]
             e[4].record(st)
-            e[4].synchronize()
-            t0 = time.perf_counter()
-            sol = mgs.mgs_solve_budget(table_np, L, grid, w.budget_bytes, opts)
-            t_solve = time.perf_counter() - t0
             mgs.mgs_plan_destroy(plan)
             mgs.mgs_scene_destroy(scene)
         if record:
+            e[4].synchronize()
             phase["scene"].append(e[0].elapsed_time(e[1]))
             phase["plan"].append(e[1].elapsed_time(e[2]))
             phase["kernel"].append(e[2].elapsed_time(e[3]))
-            phase["d2h"].append(e[3].elapsed_time(e[4]))
-            phase["solve"].append(1000 * t_solve)
+            phase["solve"].append(e[3].elapsed_time(e[4]))
             kernel_ms.append(e[2].elapsed_time(e[3]))
         return sol
 
@@ -295,8 +290,8 @@ def run_gpu(args):
     if rank == 0 or True:
         def e2e_step():
             scene = mgs.mgs_scene_create(ctx, attrs_h, imp_h, stream=st)
-            mgs.mgs_build_cost_table(ctx, scene, grid, table_h, stream=st)
-            s = mgs.mgs_solve_budget(table_np, L, grid, w.budget_bytes, opts)
+            mgs.mgs_build_cost_table(ctx, scene, grid, table_d, stream=st)
+            s = mgs.mgs_solve_budgets_device(ctx, table_d, L, grid, [w.budget_bytes], opts, stream=st)[0]
             mgs.mgs_scene_destroy(scene)
             return s
         e2e_step()
@@ -307,6 +302,15 @@ def run_gpu(args):
             e2e_step()
         torch.cuda.synchronize()
         e2e_ms = reduce_max(1000 * (time.perf_counter() - t0) / args.steps, ws)
+
+    # the host solver on the same table (comparator for the device solve)
+    table_np = table_d.cpu().numpy()
+    t0 = time.perf_counter()
+    host_sol = mgs.mgs_solve_budget(table_np, L, grid, w.budget_bytes, opts)
+    host_solve_ms = 1000 * (time.perf_counter() - t0)
+    same_as_host = (host_sol["r_index"] == sol["r_index"] and host_sol["objective"] == sol["objective"]
+                    and bool((host_sol["choice"] == sol["choice"]).all()))
+    del table_np
 
     # plain per-configuration loop on the same scene (comparator), table only
     plain_ms = fused_ms = None
@@ -370,11 +374,12 @@ def run_gpu(args):
             "table_evals_per_s": evals / (k_ms * 1e-3),
             "entries_per_s": int(L.n_items) * len(w.bits) / (ms_max * 1e-3),
             "plain_loop_table_ms": plain_ms, "fused_table_ms": fused_ms,
+            "host_solve_ms": host_solve_ms, "device_solve_equals_host": same_as_host,
             "solution": {"r_index": sol["r_index"], "est_bytes": sol["est_bytes"],
                          "objective": sol["objective"], "lp_bound": sol["lp_bound"]},
             "e2e": {"value": evals * ws / (e2e_ms * 1e-3), "unit": UNIT,
                     "h2d_bytes_per_step": int(attrs_h.numel() * 4 + imp_h.numel() * 4),
-                    "d2h_bytes_per_step": int(L.total_bytes), "ms_per_step": e2e_ms},
+                    "d2h_bytes_per_step": int(sol["choice"].nbytes) + 48 * len(w.ratios), "ms_per_step": e2e_ms},
             "gpu_launches": int(launches),
             "autotune": tune,
             "clocks": clocks,
@@ -551,12 +556,11 @@ def run_large(args):
     st = torch.cuda.Stream(device=dev)
     L = mgs.mgs_table_layout_for(w.n, N_CH, grid)
     tab = torch.empty(L.total_bytes, dtype=torch.uint8, device=dev)
-    tab_h = torch.empty(L.total_bytes, dtype=torch.uint8).pin_memory()
     sc = mgs.mgs_scene_create(ctx, a_d, i_d, stream=st)
     chosen, _ = mgs.mgs_autotune(ctx, sc, grid, stream=st)
     mgs.mgs_scene_destroy(sc)
     budgets = [10e6, 20e6, 40e6, 60e6, 80e6, 120e6, 160e6, 240e6]
-    phase = {"scene": [], "kernel": [], "d2h": [], "solve_8_budgets": []}
+    phase = {"scene": [], "kernel": [], "solve_8_budgets": []}
     evals = int(w.keep().sum()) * N_CH * len(w.bits)
     total = 0.0
     for step in range(args.warmup + args.steps):
@@ -568,20 +572,22 @@ def run_large(args):
             e[1].record(st)
             mgs.mgs_plan_launch(plan, st)
             e[2].record(st)
-            tab_h.copy_(tab, non_blocking=True)
+            sols = mgs.mgs_solve_budgets_device(ctx, tab, L, grid, budgets, mgs.solve_opts(), stream=st)
             e[3].record(st)
-            e[3].synchronize()
-            t0 = time.perf_counter()
-            sols = mgs.mgs_solve_budgets(tab_h.numpy(), L, grid, budgets, mgs.solve_opts())
-            ts = time.perf_counter() - t0
             mgs.mgs_plan_destroy(plan)
             mgs.mgs_scene_destroy(sc)
+        e[3].synchronize()
         if step >= args.warmup:
             phase["scene"].append(e[0].elapsed_time(e[1]))
             phase["kernel"].append(e[1].elapsed_time(e[2]))
-            phase["d2h"].append(e[2].elapsed_time(e[3]))
-            phase["solve_8_budgets"].append(ts * 1e3)
-            total += e[0].elapsed_time(e[3]) + ts * 1e3
+            phase["solve_8_budgets"].append(e[2].elapsed_time(e[3]))
+            total += e[0].elapsed_time(e[3])
+    # the host solver on the same table, for comparison
+    tab_np = tab.cpu().numpy()
+    t0 = time.perf_counter()
+    host = mgs.mgs_solve_budgets(tab_np, L, grid, budgets, mgs.solve_opts())
+    host_ms = 1000 * (time.perf_counter() - t0)
+    same = all(a["r_index"] == b["r_index"] and a["objective"] == b["objective"] for a, b in zip(sols, host))
     mgs.mgs_destroy(ctx)
     ms = total / args.steps
     print(json.dumps({"metric": METRIC, "value": evals / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
@@ -590,6 +596,7 @@ def run_large(args):
                       "config": {"workload": w.name}, "tile": mgs.mgs_tile_config_name(chosen),
                       "kernel_evals_per_s": evals / (statistics.mean(phase["kernel"]) * 1e-3),
                       "phase_ms": {k: statistics.mean(v) for k, v in phase.items()},
+                      "host_solve_8_budgets_ms": host_ms, "device_solve_equals_host": same,
                       "solutions": [{"budget": b, "r_index": s["r_index"], "est_bytes": s["est_bytes"]}
                                     for b, s in zip(budgets, sols)]}))
 

@@ -153,7 +153,11 @@ typedef struct {
 /* ---- context --------------------------------------------------------- */
 
 /* Create a context on CUDA device `device`.  Allocates the entropy tables
- * (L(n) = n log2 n and L(n) - L(n - 1) in units of 2^-22 bits, n <= MGS_MAX_GROUP). */
+ * (L(n) = n log2 n and L(n) - L(n - 1) in units of 2^-22 bits, n <= MGS_MAX_GROUP).
+ * Sets the release threshold of the device's default memory pool to keep freed
+ * memory (the library's stream-ordered allocations are then recycled; memory
+ * freed into that pool is not returned to the driver until the process ends
+ * or the pool is trimmed). */
 mgs_status mgs_create(int32_t device, mgs_ctx **out);
 /* Destroy a context; its scenes must have been destroyed first. */
 mgs_status mgs_destroy(mgs_ctx *ctx);
@@ -387,7 +391,10 @@ mgs_status mgs_estimate_size(const void *table, const mgs_table_layout *layout,
  * feasible ratios are skipped the largest feasible one is taken.  Per ratio
  * the solver takes the LP relaxation over each item's lower convex hull and
  * rounds it to an integral choice by greedy upgrades; the LP value is returned
- * as a lower bound.  `table` is host memory.  INFEASIBLE if no ratio fits.
+ * as a lower bound.  Rates are taken in integer units of 2^-22 bits (entropy
+ * rates are rounded to that unit; a cost table's are exact multiples of it),
+ * so size sums are exact.  `table` is host memory.  INFEASIBLE if no ratio
+ * fits.
  */
 mgs_status mgs_solve_budget(const void *table, const mgs_table_layout *layout,
                             const mgs_grid *grid, double budget_bytes, const mgs_solve_opts *opts,
@@ -402,6 +409,23 @@ mgs_status mgs_solve_budget(const void *table, const mgs_table_layout *layout,
 mgs_status mgs_solve_budgets(const void *table, const mgs_table_layout *layout,
                              const mgs_grid *grid, int32_t n_budgets, const double *budgets,
                              const mgs_solve_opts *opts, mgs_solution *out);
+
+/*
+ * mgs_solve_budgets on the device: the same answers bit for bit (the
+ * arithmetic is shared: rates in units of 2^-22 bits, hull increments in
+ * (efficiency, item, level) order, LP split, greedy completion, chunked
+ * pairwise loss sums), computed by two kernels -- one thread per item builds
+ * the hulls, one CTA per (budget, ratio) finds the split key by radix
+ * selection and completes the choice -- then Alg. 1's tau pick on the host.
+ * `table` may be device or host memory (a host table is copied in first).
+ * Device workspace is allocated and freed on `stream`; the call synchronises
+ * `stream` before returning, and `out` (host memory) is filled as by
+ * mgs_solve_budgets.  A budget whose greedy step has more than 4096
+ * candidate increments in one ratio is solved by the host solver instead.
+ */
+mgs_status mgs_solve_budgets_device(mgs_ctx *ctx, const void *table, const mgs_table_layout *layout,
+                                    const mgs_grid *grid, int32_t n_budgets, const double *budgets,
+                                    const mgs_solve_opts *opts, mgs_solution *out, void *stream);
 
 #ifdef __cplusplus
 }

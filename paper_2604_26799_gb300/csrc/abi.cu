@@ -75,19 +75,6 @@ mgs_status check_grid(const mgs_grid *grid, int64_t n) {
 
 namespace {
 
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev) {
-        cudaGetDevice(&prev);
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard() {
-        int cur = -1;
-        cudaGetDevice(&cur);
-        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
-    }
-};
-
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Table sub-array pointers for a buffer laid out by `L`.
@@ -201,6 +188,15 @@ mgs_status mgs_create(int32_t device, mgs_ctx **out) {
         set_error("cudaDeviceGetAttribute: %s", cudaGetErrorString(e));
         return MGS_ERR_CUDA;
     }
+    // stream-ordered allocations (scenes, kept lists, staging, solver workspace) are
+    // recycled from the device's default pool instead of being returned to the
+    // driver at every synchronisation
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();
     // L(h) = h log2 h in units of 2^-22 bits, h = 0..MGS_MAX_GROUP (L(0) = L(1) = 0), and
     // its increments L(h) - L(h - 1) (< 2^26), which telescope exactly back to L.
     std::vector<unsigned long long> lt(MGS_MAX_GROUP + 1, 0ull);

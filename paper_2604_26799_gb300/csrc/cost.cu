@@ -121,16 +121,6 @@ __device__ __forceinline__ uint32_t atom_add(uint32_t addr, uint32_t v) {
     asm volatile("atom.shared.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(addr), "r"(v));
     return old;
 }
-__device__ __forceinline__ uint32_t atom_cas(uint32_t addr, uint32_t cmp, uint32_t v) {
-    uint32_t old;
-    asm volatile("atom.shared.cas.b32 %0, [%1], %2, %3;" : "=r"(old) : "r"(addr), "r"(cmp), "r"(v) : "memory");
-    return old;
-}
-__device__ __forceinline__ uint32_t lds(uint32_t addr) {
-    uint32_t v;
-    asm volatile("ld.volatile.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
-    return v;
-}
 
 // Count one code.  y is the code's bit pattern kMagicBits + q.  For the delta
 // modes the return is delta(new count) to be added to the entropy sum.

@@ -36,6 +36,20 @@ constexpr int kSlabWidth = 8;         // channels per slab row (32 bytes)
 constexpr int kLtabFracBits = 22;     // fixed point of L(n) = n log2 n
 constexpr int kMaxSegments = 4096;    // (scene, ratio) pairs in one batched launch
 
+// Makes `dev` current for a scope and restores the caller's device after.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
 // Device buffer owned by the library (stream-ordered allocation).
 struct DevBuf {
     void *ptr = nullptr;

@@ -21,10 +21,6 @@ __device__ __forceinline__ uint32_t ordered_u32(float f) {
     uint32_t u = __float_as_uint(f);
     return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
-__device__ __forceinline__ float from_ordered_u32(uint32_t o) {
-    uint32_t u = (o & 0x80000000u) ? (o & 0x7FFFFFFFu) : ~o;
-    return __uint_as_float(u);
-}
 
 // ---------------------------------------------------------------------------
 // Validation: per-channel min/max over all Gaussians, finiteness flags.

@@ -1,17 +1,13 @@
-// Size estimate and bit-width 0-1 ILP over a cost table (host C++).
+// Size estimate and bit-width 0-1 ILP over a host cost table (host C++).
 //
 // Eq. (eq:ilp), Sec. III-F: per (channel, block) item pick one bit-width,
-// minimise sum of the loss Omega subject to the estimated size <= budget.
-// That is a multiple-choice knapsack.  Per ratio:
-//   1. every item's options are reduced to their lower convex hull in the
-//      (rate, distortion) plane; the LP relaxation takes hull increments in
-//      order of decreasing efficiency -dD/dRate until the capacity is used
-//      (a weighted radix selection on the efficiency's bit pattern: one
-//      histogram pass, then a full sort of the boundary bucket only);
-//   2. the integral answer keeps the increments that fit completely and then
-//      greedily adds further whole increments that still fit;
-//   3. the LP value (with the fractional split increment) is a lower bound.
-// Alg. 1 then picks tau from the per-ratio results (see mgs_solve_budget).
+// minimise the summed loss Omega subject to the estimated size <= budget, a
+// multiple-choice knapsack per reserve ratio.  The arithmetic (integer rates,
+// hulls, increment order, LP split, greedy completion, tree sums) is defined
+// in solve_def.h and shared with the device solver.  Here the LP split is
+// found by a weighted radix selection on the increment keys: one histogram
+// pass over the top 16 bits, then a sort of the boundary bucket only.
+// Alg. 1 then picks tau from the per-ratio results (see mgs_solve_budgets).
 #include <algorithm>
 #include <atomic>
 #include <cmath>
@@ -22,6 +18,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "solve_def.h"
 
 namespace mgs {
 namespace {
@@ -51,10 +48,6 @@ View make_view(const void *table, const mgs_table_layout *L, const mgs_grid *gri
     return v;
 }
 
-inline double rate_bits(const View &v, int64_t item, int k) {
-    if (v.rate_model == MGS_RATE_FIXED) return (double)v.cnt[item] * v.bits[k];
-    return v.hbits[item * v.n_b + k];
-}
 inline double dist(const View &v, int64_t item, int k) {
     int64_t i = item * v.n_b + k;
     switch (v.norm) {
@@ -65,60 +58,54 @@ inline double dist(const View &v, int64_t item, int k) {
     }
 }
 
-// Hull increments of every item, at a fixed stride of (n_b - 1) slots per item.
+// Lower convex hulls of every item, item-major at a stride of n_b vertices.
 struct Hulls {
-    int stride = 0;
-    std::vector<double> eff, dw, dd;   // [item * stride + level]
-    std::vector<int8_t> to;            // option reached by the increment
-    std::vector<int8_t> len;           // increments per item
-    std::vector<int8_t> start;         // first hull option per item
-    std::vector<double> w0, d0, wtop;  // per item: start rate/distortion, top-bit-width rate
+    int nb = 0;
+    std::vector<uint8_t> nv;     // vertices per item
+    std::vector<int8_t> opt;     // option index of each vertex
+    std::vector<int64_t> w;      // rate of each vertex (2^-22 bit units)
+    std::vector<double> d;       // loss of each vertex
+    std::vector<uint64_t> key;   // key of increment l (vertex l -> l + 1)
+    std::vector<int64_t> wtop;   // rate of the top bit-width option
 };
 
-// Lower convex hull of one item's (rate, distortion) options.
-void build_hull(const View &v, int64_t item, int64_t slot, Hulls &H) {
+void hull_item(const View &v, int64_t item, Hulls &H) {
     const int nb = v.n_b;
-    double w[MGS_MAX_OPTIONS], d[MGS_MAX_OPTIONS];
-    int ord[MGS_MAX_OPTIONS], hull[MGS_MAX_OPTIONS];
+    int64_t w[MGS_MAX_OPTIONS] = {};
+    double d[MGS_MAX_OPTIONS] = {};
     for (int k = 0; k < nb; k++) {
-        w[k] = rate_bits(v, item, k);
+        w[k] = rate_units(v.rate_model, v.hbits[item * nb + k], v.cnt[item], v.bits[k]);
         d[k] = dist(v, item, k);
-        ord[k] = k;
     }
-    // insertion sort by (rate, distortion, index): the options usually arrive sorted
-    for (int i = 1; i < nb; i++) {
-        int x = ord[i], j = i - 1;
-        while (j >= 0 && (w[ord[j]] > w[x] || (w[ord[j]] == w[x] && (d[ord[j]] > d[x] ||
-                                                                     (d[ord[j]] == d[x] && ord[j] > x))))) {
-            ord[j + 1] = ord[j];
-            j--;
+    const int64_t b = item * nb;
+    const int n = build_hull(w, d, nb, &H.opt[b], &H.w[b], &H.d[b]);
+    H.nv[item] = (uint8_t)n;
+    H.wtop[item] = w[nb - 1];
+    for (int l = 0; l + 1 < n; l++) H.key[b + l] = inc_key(H.d[b + l] - H.d[b + l + 1], H.w[b + l + 1] - H.w[b + l]);
+}
+
+// Chunked pairwise sum in item order (the tree of solve_def.h).
+inline double tree32(double *v) {
+    for (int off = 16; off > 0; off >>= 1)
+        for (int l = 0; l < off; l++) v[l] = v[l] + v[l + off];
+    return v[0];
+}
+template <typename F>
+double tree_sum(int64_t n, F x) {
+    double s = 0.0;
+    for (int64_t c0 = 0; c0 < n; c0 += kTreeChunk) {
+        double part[32];
+        for (int wp = 0; wp < 32; wp++) {
+            double v[32];
+            for (int l = 0; l < 32; l++) {
+                const int64_t i = c0 + wp * 32 + l;
+                v[l] = i < n ? x(i) : 0.0;
+            }
+            part[wp] = tree32(v);
         }
-        ord[j + 1] = x;
+        s = s + tree32(part);
     }
-    int h = 0;
-    for (int t = 0; t < nb; t++) {
-        const int k = ord[t];
-        if (h > 0 && (d[k] >= d[hull[h - 1]] || w[k] == w[hull[h - 1]])) continue;   // dominated
-        while (h >= 2) {
-            const int a = hull[h - 2], b = hull[h - 1];
-            if ((d[b] - d[a]) * (w[k] - w[a]) >= (d[k] - d[a]) * (w[b] - w[a])) h--;
-            else break;
-        }
-        hull[h++] = k;
-    }
-    H.start[slot] = (int8_t)hull[0];
-    H.w0[slot] = w[hull[0]];
-    H.d0[slot] = d[hull[0]];
-    H.wtop[slot] = w[nb - 1];
-    H.len[slot] = (int8_t)(h - 1);
-    const int64_t base = slot * H.stride;
-    for (int i = 0; i + 1 < h; i++) {
-        const int a = hull[i], b = hull[i + 1];
-        H.dw[base + i] = w[b] - w[a];
-        H.dd[base + i] = d[a] - d[b];
-        H.eff[base + i] = H.dd[base + i] / H.dw[base + i];
-        H.to[base + i] = (int8_t)b;
-    }
+    return s;
 }
 
 struct RatioResult {
@@ -127,52 +114,45 @@ struct RatioResult {
     std::vector<uint8_t> choice;
 };
 
-// Order of increments: larger efficiency first, then item, then hull level.
+// An increment in the solve order: larger key first, then item, then level.
 struct IncRef {
-    double eff;
+    uint64_t key;
     int32_t item;
     int32_t level;
 };
 inline bool inc_before(const IncRef &a, const IncRef &b) {
-    if (a.eff != b.eff) return a.eff > b.eff;
+    if (a.key != b.key) return a.key > b.key;
     if (a.item != b.item) return a.item < b.item;
     return a.level < b.level;
 }
 
-// Non-negative doubles order like their bit patterns.
-inline uint64_t eff_key(double e) {
-    uint64_t u;
-    std::memcpy(&u, &e, 8);
-    return u;
-}
-
-void solve_ratio(const Hulls &H, int64_t slot0, int64_t M, double budget, const mgs_solve_opts *o,
+void solve_ratio(const Hulls &H, int64_t i0, int64_t M, double budget, const mgs_solve_opts *o,
                  RatioResult *res) {
-    const int S = H.stride;
-    const double fixed_bytes = o->meta_bytes_per_group * (double)M + o->const_bytes + o->delta_bytes;
-    const double cap = 8.0 * (budget - fixed_bytes);   // capacity in bits
-    double w0 = 0, d0 = 0, wtop = 0;
+    const int nb = H.nb;
+    const double fixed = o->meta_bytes_per_group * (double)M + o->const_bytes + o->delta_bytes;
+    int64_t W0 = 0, Wtop = 0;
     for (int64_t i = 0; i < M; i++) {
-        w0 += H.w0[slot0 + i];
-        d0 += H.d0[slot0 + i];
-        wtop += H.wtop[slot0 + i];
+        W0 += H.w[(i0 + i) * nb];
+        Wtop += H.wtop[i0 + i];
     }
-    res->bytes_min = w0 / 8.0 + fixed_bytes;
-    res->bytes_top = wtop / 8.0 + fixed_bytes;
-    if (cap < 0 || w0 > cap) {
+    res->bytes_min = units_to_bytes(W0, fixed);
+    res->bytes_top = units_to_bytes(Wtop, fixed);
+    const int64_t cap = capacity_units(budget, fixed);
+    if (cap < 0 || W0 > cap) {
         res->status = -1;
         return;
     }
-    const double target = cap - w0;
-    // pass 1: rate histogram over the top 16 bits of the efficiency key
-    static thread_local std::vector<double> hist;
-    hist.assign(1 << 16, 0.0);
+    const int64_t target = cap - W0;
+    auto dw_of = [&](int64_t i, int l) { return H.w[(i0 + i) * nb + l + 1] - H.w[(i0 + i) * nb + l]; };
+    // LP split.  Pass 1: rate per bucket of the top 16 key bits; buckets above
+    // the boundary are taken whole.
+    static thread_local std::vector<int64_t> hist;
+    hist.assign(1 << 16, 0);
     for (int64_t i = 0; i < M; i++) {
-        const int64_t base = (slot0 + i) * S;
-        for (int l = 0; l < H.len[slot0 + i]; l++) hist[eff_key(H.eff[base + l]) >> 48] += H.dw[base + l];
+        const int64_t b = (i0 + i) * nb;
+        for (int l = 0; l + 1 < H.nv[i0 + i]; l++) hist[H.key[b + l] >> 48] += dw_of(i, l);
     }
-    // buckets above the boundary are taken whole
-    double taken = 0;
+    int64_t taken = 0;
     int boundary = -1;
     for (int bk = (1 << 16) - 1; bk >= 0; bk--) {
         if (taken + hist[bk] <= target) {
@@ -182,84 +162,64 @@ void solve_ratio(const Hulls &H, int64_t slot0, int64_t M, double budget, const 
             break;
         }
     }
-    std::vector<int16_t> level(M, 0);
-    std::vector<uint8_t> cur(M);
-    double D = d0, W = w0, lp;
-    for (int64_t i = 0; i < M; i++) cur[i] = (uint8_t)H.start[slot0 + i];
-    std::vector<IncRef> edge;
+    static thread_local std::vector<int32_t> level;
+    static thread_local std::vector<IncRef> edge;
+    level.assign(M, 0);
+    edge.clear();
     for (int64_t i = 0; i < M; i++) {
-        const int64_t base = (slot0 + i) * S;
-        for (int l = 0; l < H.len[slot0 + i]; l++) {
-            const int bk = (int)(eff_key(H.eff[base + l]) >> 48);
-            if (bk > boundary) {
-                // whole bucket taken: the item's earlier levels are in higher buckets too
-                level[i] = (int16_t)(l + 1);
-                cur[i] = (uint8_t)H.to[base + l];
-                D -= H.dd[base + l];
-                W += H.dw[base + l];
-            } else if (bk == boundary) {
-                edge.push_back(IncRef{H.eff[base + l], (int32_t)i, l});
-            }
+        const int64_t b = (i0 + i) * nb;
+        for (int l = 0; l + 1 < H.nv[i0 + i]; l++) {
+            const int bk = (int)(H.key[b + l] >> 48);
+            if (bk > boundary) level[i] = l + 1;   // keys fall along an item's levels
+            else if (bk == boundary) edge.push_back(IncRef{H.key[b + l], (int32_t)i, l});
         }
     }
-    // pass 2: the boundary bucket in full order
+    // pass 2: the boundary bucket in full order, up to the split
     std::sort(edge.begin(), edge.end(), inc_before);
-    size_t split = 0;
-    while (split < edge.size()) {
-        const IncRef &e = edge[split];
-        const int64_t at = (slot0 + e.item) * S + e.level;
-        if (taken + H.dw[at] > target) break;
-        taken += H.dw[at];
-        level[e.item] = (int16_t)(e.level + 1);
-        cur[e.item] = (uint8_t)H.to[at];
-        D -= H.dd[at];
-        W += H.dw[at];
-        split++;
-    }
-    lp = D;
-    if (split < edge.size()) {
-        const int64_t at = (slot0 + edge[split].item) * S + edge[split].level;
-        const double frac = (target - taken) / H.dw[at];
-        if (frac > 0) lp -= frac * H.dd[at];
-    }
-    // greedy completion: whole next increments that still fit, best first
-    struct Cand {
-        double eff;
-        int32_t item, level;
-        bool operator<(const Cand &b) const {   // max-heap on the increment order
-            return inc_before(IncRef{b.eff, b.item, b.level}, IncRef{eff, item, level});
+    int64_t split_item = -1;
+    int split_level = 0;
+    for (const IncRef &e : edge) {
+        const int64_t dw = dw_of(e.item, e.level);
+        if (taken + dw > target) {
+            split_item = e.item;
+            split_level = e.level;
+            break;
         }
-    };
-    std::priority_queue<Cand> pq;
-    double rem = cap - W;
-    for (int64_t i = 0; i < M; i++) {
-        const int l = level[i];
-        if (l < H.len[slot0 + i]) {
-            const int64_t at = (slot0 + i) * S + l;
-            if (H.dw[at] <= rem) pq.push(Cand{H.eff[at], (int32_t)i, l});
-        }
+        taken += dw;
+        level[e.item] = e.level + 1;
     }
-    while (!pq.empty()) {
-        const Cand c = pq.top();
-        pq.pop();
-        const int64_t at = (slot0 + c.item) * S + c.level;
-        if (H.dw[at] > rem || level[c.item] != c.level) continue;
-        cur[c.item] = (uint8_t)H.to[at];
-        level[c.item]++;
-        rem -= H.dw[at];
-        W += H.dw[at];
-        D -= H.dd[at];
-        const int l = level[c.item];
-        if (l < H.len[slot0 + c.item]) {
-            const int64_t nx = (slot0 + c.item) * S + l;
-            if (H.dw[nx] <= rem) pq.push(Cand{H.eff[nx], c.item, l});
+    const double d_split = tree_sum(M, [&](int64_t i) { return H.d[(i0 + i) * nb + level[i]]; });
+    double lp = d_split;
+    if (split_item >= 0) {
+        const int64_t b = (i0 + split_item) * nb + split_level;
+        const double frac = (double)(target - taken) / (double)(H.w[b + 1] - H.w[b]);
+        if (frac > 0) lp = lp - frac * (H.d[b] - H.d[b + 1]);
+    }
+    // greedy completion, one take at a time: the first increment in solve order
+    // after the last one taken that is its item's next increment and fits
+    int64_t rem = target - taken;
+    IncRef last{0, -1, 0};
+    while (true) {
+        IncRef best{0, -1, 0};
+        for (int64_t i = 0; i < M; i++) {
+            const int l = level[i];
+            if (l + 1 >= H.nv[i0 + i]) continue;
+            const IncRef c{H.key[(i0 + i) * nb + l], (int32_t)i, l};
+            if (last.item >= 0 && !inc_before(last, c)) continue;   // passed over already
+            if (dw_of(i, l) > rem) continue;
+            if (best.item < 0 || inc_before(c, best)) best = c;
         }
+        if (best.item < 0) break;
+        rem -= dw_of(best.item, best.level);
+        level[best.item]++;
+        last = best;
     }
     res->status = 0;
-    res->objective = D;
-    res->bytes = W / 8.0 + fixed_bytes;
+    res->objective = tree_sum(M, [&](int64_t i) { return H.d[(i0 + i) * nb + level[i]]; });
+    res->bytes = units_to_bytes(W0 + (target - rem), fixed);
     res->lp = lp;
-    res->choice.assign(cur.begin(), cur.end());
+    res->choice.resize(M);
+    for (int64_t i = 0; i < M; i++) res->choice[i] = (uint8_t)H.opt[(i0 + i) * nb + level[i]];
 }
 
 template <typename F>
@@ -301,17 +261,17 @@ mgs_status mgs_estimate_size(const void *table, const mgs_table_layout *layout,
     }
     View v = make_view(table, layout, grid, opts);
     int64_t b = layout->item_begin[r_index], e = layout->item_begin[r_index + 1];
-    double bits = 0;
+    int64_t units = 0;
     for (int64_t i = b; i < e; i++) {
         int k = choice[i - b];
         if (k >= v.n_b) {
             set_error("choice[%lld] = %d outside the %d options", (long long)(i - b), k, v.n_b);
             return MGS_ERR_INVALID_ARG;
         }
-        bits += rate_bits(v, i, k);
+        units += rate_units(v.rate_model, v.hbits[i * v.n_b + k], v.cnt[i], v.bits[k]);
     }
-    *bytes_out = bits / 8.0 + opts->meta_bytes_per_group * (double)(e - b) + opts->const_bytes +
-                 opts->delta_bytes;
+    *bytes_out = units_to_bytes(units, opts->meta_bytes_per_group * (double)(e - b) +
+                                           opts->const_bytes + opts->delta_bytes);
     return MGS_OK;
 }
 
@@ -338,18 +298,15 @@ mgs_status mgs_solve_budgets(const void *table, const mgs_table_layout *layout,
     const int64_t n_items = layout->item_begin[nr];
     static thread_local Hulls H_tls;   // capacity persists across calls (no page faults per solve)
     Hulls &H = H_tls;                  // the caller's instance, shared with the worker threads
-    H.stride = std::max(1, v.n_b - 1);
-    H.eff.resize((size_t)n_items * H.stride);
-    H.dw.resize((size_t)n_items * H.stride);
-    H.dd.resize((size_t)n_items * H.stride);
-    H.to.resize((size_t)n_items * H.stride);
-    H.len.resize(n_items);
-    H.start.resize(n_items);
-    H.w0.resize(n_items);
-    H.d0.resize(n_items);
+    H.nb = v.n_b;
+    H.nv.resize(n_items);
+    H.opt.resize((size_t)n_items * H.nb);
+    H.w.resize((size_t)n_items * H.nb);
+    H.d.resize((size_t)n_items * H.nb);
+    H.key.resize((size_t)n_items * H.nb);
     H.wtop.resize(n_items);
     parallel_for(n_items, 4096, [&](int64_t lo, int64_t hi) {
-        for (int64_t i = lo; i < hi; i++) build_hull(v, i, i, H);
+        for (int64_t i = lo; i < hi; i++) hull_item(v, i, H);
     });
     // every (budget, ratio) pair is independent once the hulls exist
     std::vector<RatioResult> res((size_t)n_budgets * nr);

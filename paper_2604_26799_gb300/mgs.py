@@ -124,6 +124,8 @@ _SIGS = {
                          ctypes.POINTER(mgs_solution)],
     "mgs_solve_budgets": [_P, ctypes.POINTER(mgs_table_layout), ctypes.POINTER(mgs_grid),
                           ctypes.c_int32, _P, ctypes.POINTER(mgs_solve_opts), _P],
+    "mgs_solve_budgets_device": [_P, _P, ctypes.POINTER(mgs_table_layout), ctypes.POINTER(mgs_grid),
+                                 ctypes.c_int32, _P, ctypes.POINTER(mgs_solve_opts), _P, _P],
 }
 _RESTYPE = {"mgs_last_error": ctypes.c_char_p, "mgs_version": ctypes.c_char_p,
             "mgs_tile_config_name": ctypes.c_char_p, "mgs_tile_config_count": ctypes.c_int32,
@@ -388,6 +390,17 @@ def mgs_solve_budget(table_host, layout: mgs_table_layout, grid: Grid, budget_by
 
 def mgs_solve_budgets(table_host, layout: mgs_table_layout, grid: Grid, budgets, opts) -> list[dict]:
     """One solution per budget; the item hulls are shared."""
+    return _solve_many(lambda *a: lib().mgs_solve_budgets(_ptr(table_host), *a), layout, grid, budgets, opts)
+
+
+def mgs_solve_budgets_device(ctx: int, table, layout: mgs_table_layout, grid: Grid, budgets, opts,
+                             stream=None) -> list[dict]:
+    """mgs_solve_budgets computed on the device; `table` may be a device tensor or host array."""
+    return _solve_many(lambda *a: lib().mgs_solve_budgets_device(ctx, _ptr(table), *a, _stream(stream)),
+                       layout, grid, budgets, opts)
+
+
+def _solve_many(call, layout: mgs_table_layout, grid: Grid, budgets, opts) -> list[dict]:
     nb = len(budgets)
     nr = layout.n_ratios
     max_items = max(int(layout.item_begin[r + 1] - layout.item_begin[r]) for r in range(nr))
@@ -399,8 +412,8 @@ def mgs_solve_budgets(table_host, layout: mgs_table_layout, grid: Grid, budgets,
                 np.zeros(nr), np.zeros(nr), np.zeros(nr))
         keep.append(arrs)
         sols[i] = mgs_solution(-1, 0.0, 0.0, 0.0, *[a.ctypes.data for a in arrs])
-    rc = lib().mgs_solve_budgets(_ptr(table_host), ctypes.byref(layout), ctypes.byref(grid.c), nb,
-                                 bud.ctypes.data, ctypes.byref(opts), ctypes.addressof(sols))
+    rc = call(ctypes.byref(layout), ctypes.byref(grid.c), nb, bud.ctypes.data, ctypes.byref(opts),
+              ctypes.addressof(sols))
     if rc not in (MGS_OK, -6):
         _check(rc)
     out = []

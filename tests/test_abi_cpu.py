@@ -85,7 +85,9 @@ def synthetic_table(rng, keep, bits, G, C):
     v["l1"][:] = np.sqrt(v["sse"])
     v["linf"][:] = np.sqrt(v["sse"]).astype(np.float32)
     ent = np.minimum(b[None, :], np.log2(np.maximum(v["cnt"][:, None], 2))) * v["cnt"][:, None]
-    v["hbits"][:] = ent * rng.uniform(0.5, 1.0, (ni, 1))
+    # entropy rates of a cost table are multiples of 2^-22 bits; the solver
+    # works in those units
+    v["hbits"][:] = np.round(ent * rng.uniform(0.5, 1.0, (ni, 1)) * 2.0 ** 22) / 2.0 ** 22
     return buf, lay, grid, v
 
 
