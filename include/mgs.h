@@ -326,16 +326,18 @@ mgs_status mgs_quantize_groups_noalloc(mgs_ctx *ctx, const mgs_scene *scene, int
  * a compute thread runs one persistent launch per iteration over a slice of
  * the remaining work items of every admitted job (about slice_items items per
  * launch, 0 = all), so jobs that arrive while others are on the GPU join the
- * next launch; finished tables are copied to pinned host memory and solved by
- * solver_threads host threads.  A job's results are the same whichever jobs
- * it shares launches with.
+ * next launch; each finished table is solved on the device
+ * (mgs_solve_budgets_device) by one of solver_threads host threads, each with
+ * its own stream, while the next launches run.  A job's results are the same
+ * whichever jobs it shares launches with.
  */
 typedef struct mgs_server mgs_server;
 
 typedef struct {
     int32_t max_jobs;          /* jobs admitted at once (>= 1) */
-    int32_t solver_threads;    /* host threads solving finished tables (>= 1) */
-    int64_t hbm_budget_bytes;  /* device memory the server may hold for jobs */
+    int32_t solver_threads;    /* threads driving the device solve of finished tables (>= 1) */
+    int64_t hbm_budget_bytes;  /* device memory the server may hold for jobs (scene, table,
+                                  solver workspace) */
     int64_t slice_items;       /* work items per batched launch (0 = everything ready) */
 } mgs_server_opts;
 

@@ -1,6 +1,7 @@
 // Serving loop: (scene, byte budget) search jobs arrive at any time; scenes are
 // made resident, their cost-table work is run in shared batched launches, and
-// each finished table is solved on the host.
+// each finished table is solved on the device (mgs_solve_budgets_device) by a
+// solver thread with its own stream, while the next launches run.
 //
 // Continuous batching: jobs are admitted while a slot is free and their
 // device footprint fits the HBM budget.  The compute thread repeatedly builds
@@ -48,13 +49,11 @@ struct Job {
     // resources
     mgs_scene *scene = nullptr;
     void *d_table = nullptr;
-    void *h_table = nullptr;
     mgs_table_layout layout{};
     std::vector<CostSeg> segs;       // one per ratio, whole ratio
     std::vector<int32_t> cursor;     // next group per ratio
     int64_t groups_left = 0;
     int64_t footprint = 0;
-    cudaEvent_t copied = nullptr;
     // result
     JobState state = kPending;
     mgs_status status = MGS_OK;
@@ -82,7 +81,7 @@ struct mgs_server {
     std::map<int64_t, std::unique_ptr<mgs::Job>> jobs;
     int in_flight = 0;
     int64_t used_bytes = 0;
-    cudaStream_t ingest_stream = nullptr, compute_stream = nullptr, copy_stream = nullptr;
+    cudaStream_t ingest_stream = nullptr, compute_stream = nullptr, copy_stream = nullptr;   // copy: frees
     std::thread ingest_thread, compute_thread;
     std::vector<std::thread> solvers;
     // compute-launch scratch
@@ -105,8 +104,11 @@ int64_t job_footprint(const Job &j, const mgs_table_layout &L) {
     int64_t kept = 0;
     for (auto k : j.keep) kept += k * 4;
     // resident scene + kept lists + table, plus the transient staging and sort
-    // scratch of scene creation
-    return slabs + j.n * 16 + kept + L.total_bytes + (int64_t)j.n * j.C * 4 + j.n * 28;
+    // scratch of scene creation and the device solver's hulls and histograms
+    const int64_t nb = (int64_t)j.bits.size(), ni = L.item_begin[L.n_ratios];
+    const int64_t solver = ni * (3 + 17 * nb + 8 * std::max<int64_t>(1, nb - 1)) +
+                           (int64_t)L.n_ratios * 65536 * 12;
+    return slabs + j.n * 16 + kept + L.total_bytes + (int64_t)j.n * j.C * 4 + j.n * 28 + solver;
 }
 
 void fail_job(mgs_server *S, Job *j, mgs_status s, const char *what) {
@@ -137,14 +139,6 @@ void release_job(mgs_server *S, Job *j) {
         j->d_table = nullptr;
     }
     cudaStreamSynchronize(S->copy_stream);
-    if (j->h_table) {
-        cudaFreeHost(j->h_table);
-        j->h_table = nullptr;
-    }
-    if (j->copied) {
-        cudaEventDestroy(j->copied);
-        j->copied = nullptr;
-    }
 }
 
 // Admit pending jobs (FIFO) while slots and memory allow; make scenes resident.
@@ -187,9 +181,8 @@ void ingest_loop(mgs_server *S) {
             mgs_grid g{(int32_t)j->keep.size(), j->keep.data(), (int32_t)j->bits.size(),
                        j->bits.data(), j->G};
             s = mgs_table_layout_for(j->n, j->C, &g, &j->layout);
-            if (s == MGS_OK && (cudaMallocAsync(&j->d_table, j->layout.total_bytes, S->ingest_stream) !=
-                                    cudaSuccess ||
-                                cudaMallocHost(&j->h_table, j->layout.total_bytes) != cudaSuccess)) {
+            if (s == MGS_OK &&
+                cudaMallocAsync(&j->d_table, j->layout.total_bytes, S->ingest_stream) != cudaSuccess) {
                 cudaGetLastError();
                 set_error("table allocation failed");
                 s = MGS_ERR_OUT_OF_MEMORY;
@@ -348,11 +341,7 @@ void compute_loop(mgs_server *S) {
                 S->used_bytes -= j->footprint;
                 continue;
             }
-            j->t_table = now_s(S);
-            cudaEventCreateWithFlags(&j->copied, cudaEventDisableTiming);
-            cudaMemcpyAsync(j->h_table, j->d_table, j->layout.total_bytes, cudaMemcpyDeviceToHost,
-                            S->copy_stream);
-            cudaEventRecord(j->copied, S->copy_stream);
+            j->t_table = now_s(S);   // the compute stream has been synchronised: the table is complete
             j->state = kSolving;
             S->to_solve.push_back(j);
         }
@@ -362,6 +351,14 @@ void compute_loop(mgs_server *S) {
 
 void solve_loop(mgs_server *S) {
     cudaSetDevice(S->ctx->device);
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) st = nullptr;
+    struct StreamGuard {
+        cudaStream_t s;
+        ~StreamGuard() {
+            if (s) cudaStreamDestroy(s);
+        }
+    } guard{st};
     while (true) {
         Job *j = nullptr;
         {
@@ -371,7 +368,11 @@ void solve_loop(mgs_server *S) {
             j = S->to_solve.front();
             S->to_solve.pop_front();
         }
-        mgs_status s = cudaEventSynchronize(j->copied) == cudaSuccess ? MGS_OK : MGS_ERR_CUDA;
+        mgs_status s = MGS_OK;
+        if (!st) {
+            set_error("solver stream creation failed");
+            s = MGS_ERR_CUDA;
+        }
         mgs_solution sol{};
         std::vector<uint8_t> choice;
         if (s == MGS_OK) {
@@ -382,7 +383,7 @@ void solve_loop(mgs_server *S) {
             sol.choice = choice.data();
             mgs_grid g{(int32_t)j->keep.size(), j->keep.data(), (int32_t)j->bits.size(),
                        j->bits.data(), j->G};
-            s = mgs_solve_budget(j->h_table, &j->layout, &g, j->budget, &j->opts, &sol);
+            s = mgs_solve_budgets_device(S->ctx, j->d_table, &j->layout, &g, 1, &j->budget, &j->opts, &sol, st);
         }
         release_job(S, j);   // outside the lock: it waits for the copy stream
         std::lock_guard<std::mutex> lk(S->mu);
