@@ -87,6 +87,11 @@ struct KernelArgs {
     int32_t hist_words;               // words per small histogram buffer (power of two)
     int32_t n_small;                  // small buffers (1 or 2)
     int32_t big_words;                // words of the big buffer (0: none)
+    // per option (index k = option - opt_lo), fixed for the launch: histogram mode,
+    // buffer (0, 1: small; 2: big), barrier before the pass, windows, words per window
+    int8_t opt_mode[MGS_MAX_OPTIONS], opt_buf[MGS_MAX_OPTIONS], opt_sync[MGS_MAX_OPTIONS];
+    int8_t opt_windows[MGS_MAX_OPTIONS];
+    int32_t opt_wwords[MGS_MAX_OPTIONS];
 };
 
 // ---- packed FP32 pairs ----------------------------------------------------
@@ -112,6 +117,42 @@ MGS_F2_BINOP(fadd2, "add.rn.f32x2")
 MGS_F2_BINOP(fsub2, "sub.rn.f32x2")
 #undef MGS_F2_BINOP
 
+// ---- global loads with L1 eviction hints: the gathered rows and kept
+// positions are read once and must not evict the entropy tables, which every
+// pass reads
+__device__ __forceinline__ float4 ld_stream(const float4 *p) {
+    float4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p));
+    return v;
+}
+__device__ __forceinline__ float2 ld_stream(const float2 *p) {
+    float2 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ float ld_stream(const float *p) {
+    float v;
+    asm volatile("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ int32_t ld_stream(const int32_t *p) {
+    int32_t v;
+    asm volatile("ld.global.nc.L1::no_allocate.s32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ unsigned long long ld_keep(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.global.nc.L1::evict_last.u64 %0, [%1];" : "=l"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ uint32_t ld_keep(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.global.nc.L1::evict_last.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
 // ---- shared-memory histogram operations ------------------------------------
 __device__ __forceinline__ void red_add(uint32_t addr, uint32_t v) {
     asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(v));
@@ -134,7 +175,7 @@ __device__ __forceinline__ void hist_op(uint32_t y, uint32_t hbase, uint32_t lan
         red_add(hbase + (y << 2), 1u);               // q * 4, magic folded in
     } else if (MODE == kDelta32) {
         uint32_t old = atom_add(hbase + (y << 2), 1u);
-        dacc += __ldg(&dtab[old + 1u]);
+        dacc += ld_keep(&dtab[old + 1u]);
     } else {
         // 16-bit counter pairs; only codes whose word lies in the current window
         // [wlo, wlo + wn) are counted by this pass
@@ -143,7 +184,7 @@ __device__ __forceinline__ void hist_op(uint32_t y, uint32_t hbase, uint32_t lan
         if (word < wn) {
             const uint32_t sh = (q & 1u) << 4;
             uint32_t old = atom_add(hbase + (word << 2), 1u << sh);
-            dacc += __ldg(&dtab[((old >> sh) & 0xFFFFu) + 1u]);
+            dacc += ld_keep(&dtab[((old >> sh) & 0xFFFFu) + 1u]);
         }
     }
 }
@@ -287,7 +328,7 @@ __device__ __forceinline__ void hist_finish(uint32_t *hist, int mode, int b, int
             uint32_t v = hist[k * 32 + lane];
             hist[k * 32 + lane] = 0u;
             uint32_t s = __reduce_add_sync(kFull, v);
-            if (lane == 0 && s) hacc += __ldg(&ltab[s]);
+            if (lane == 0 && s) hacc += ld_keep(&ltab[s]);
         }
     } else if (mode == kDirect) {
         const int bins = 1 << b;
@@ -295,7 +336,7 @@ __device__ __forceinline__ void hist_finish(uint32_t *hist, int mode, int b, int
         for (int k = threadIdx.x; k < bins; k += T) {
             uint32_t v = hist[k];
             if (v) {
-                hacc += __ldg(&ltab[v]);
+                hacc += ld_keep(&ltab[v]);
                 hist[k] = 0u;
             }
         }
@@ -332,18 +373,18 @@ __device__ __forceinline__ float warp_min(float v) {
 template <int W>
 __device__ __forceinline__ void load_row(const float *p, float (&v)[W]) {
     if (W == 8) {
-        float4 a = __ldg(reinterpret_cast<const float4 *>(p));
-        float4 b = __ldg(reinterpret_cast<const float4 *>(p) + 1);
+        float4 a = ld_stream(reinterpret_cast<const float4 *>(p));
+        float4 b = ld_stream(reinterpret_cast<const float4 *>(p) + 1);
         v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
         v[4 % W] = b.x; v[5 % W] = b.y; v[6 % W] = b.z; v[7 % W] = b.w;
     } else if (W == 4) {
-        float4 a = __ldg(reinterpret_cast<const float4 *>(p));
+        float4 a = ld_stream(reinterpret_cast<const float4 *>(p));
         v[0] = a.x; v[1 % W] = a.y; v[2 % W] = a.z; v[3 % W] = a.w;
     } else if (W == 2) {
-        float2 a = __ldg(reinterpret_cast<const float2 *>(p));
+        float2 a = ld_stream(reinterpret_cast<const float2 *>(p));
         v[0] = a.x; v[1 % W] = a.y;
     } else {
-        v[0] = __ldg(p);
+        v[0] = ld_stream(p);
     }
 }
 
@@ -406,7 +447,7 @@ __device__ void process_item(const KernelArgs &A, const Smem &sm, int64_t work) 
         int i = e * T + threadIdx.x;
         float row[W];
         if (i < nvalid) {
-            int32_t pos = __ldg(&S.kept[gstart + i]);
+            int32_t pos = ld_stream(&S.kept[gstart + i]);
             load_row<W>(S.slabs + ((int64_t)slab * S.n + pos) * kSlabWidth + j0, row);
         } else {
 #pragma unroll
@@ -469,22 +510,11 @@ __device__ void process_item(const KernelArgs &A, const Smem &sm, int64_t work) 
             p.ytop = kMagic + p.top;
             p.S = __fdiv_rn(R, p.twob);
             p.Ss = __fmul_rn(__fmul_rn(p.S, s1), s2);
-            const int bw = A.big_words;
-            p.buf = 0;
-            p.windows = 1;
-            p.wwords = 1 << (p.b - 1);
-            if (p.b <= kLaneMaxBits) p.mode = kLane;
-            else if (p.b <= kDirectMaxBits) p.mode = kDirect;
-            else if ((1 << p.b) <= hw) p.mode = kDelta32;
-            else if ((1 << (p.b - 1)) <= hw) p.mode = kDelta16;
-            else if ((1 << p.b) <= bw) { p.mode = kDelta32; p.buf = 2; }
-            else {
-                // 16-bit pairs in the big buffer, in windows of bw words
-                p.mode = kDelta16;
-                p.buf = 2;
-                p.wwords = min(1 << (p.b - 1), bw);
-                p.windows = (1 << (p.b - 1)) / p.wwords;
-            }
+            p.mode = A.opt_mode[threadIdx.x];
+            p.buf = A.opt_buf[threadIdx.x];
+            p.sync = A.opt_sync[threadIdx.x];
+            p.windows = A.opt_windows[threadIdx.x];
+            p.wwords = A.opt_wwords[threadIdx.x];
             if (p.S == 0.0f) {
                 p.path = kDegenerate;
                 p.Z = 0.0f;
@@ -527,28 +557,6 @@ __device__ void process_item(const KernelArgs &A, const Smem &sm, int64_t work) 
             cw[e] = __fmul_rn(__fmul_rn(cw[e], s1), s2);
         }
         const int any_slow = __syncthreads_or(slow);   // also publishes bp
-        if (threadIdx.x == 0) {
-            // alternate buffers so one barrier per bit-width suffices; an option that
-            // must reuse the previous option's buffer waits for its clearing first
-            int last = -1;
-            for (int k = 0; k < n_opts; k++) {
-                BitParam &q = sm.bp[k];
-                if (q.buf != 2) {
-                    const int cand[3] = {0, 1, 2};
-                    int pick = -1;
-                    for (int c = 0; c < 3 && pick < 0; c++) {
-                        const int bsel = cand[c];
-                        if (bsel == 1 && A.n_small < 2) continue;
-                        if (bsel == 2 && A.big_words == 0) continue;
-                        if (bsel != last) pick = bsel;
-                    }
-                    q.buf = pick < 0 ? 0 : pick;
-                }
-                q.sync = (q.buf == last) ? 1 : 0;
-                last = q.buf;
-            }
-        }
-        __syncthreads();
 
 #pragma unroll 1
         for (int k = 0; k < n_opts; k++) {
@@ -701,6 +709,46 @@ struct HistPlan {
 };
 constexpr int kBigWords = 16384;
 
+// Histogram mode and buffer of every option (fixed for a launch).  Consecutive
+// options alternate buffers so that one barrier per bit-width suffices; an
+// option that must reuse the previous option's buffer waits for its clearing.
+void option_plan(const HistPlan &h, const int32_t *bits, int n_opts, KernelArgs *A) {
+    int last = -1;
+    for (int k = 0; k < n_opts; k++) {
+        const int b = bits[k];
+        int mode, buf = 0, windows = 1, wwords = 1 << (b - 1);
+        if (b <= kLaneMaxBits) mode = kLane;
+        else if (b <= kDirectMaxBits) mode = kDirect;
+        else if ((1 << b) <= h.hist_words) mode = kDelta32;
+        else if ((1 << (b - 1)) <= h.hist_words) mode = kDelta16;
+        else if ((1 << b) <= h.big_words) {
+            mode = kDelta32;
+            buf = 2;
+        } else {
+            // 16-bit pairs in the big buffer, in windows of big_words words
+            mode = kDelta16;
+            buf = 2;
+            wwords = std::min(1 << (b - 1), h.big_words);
+            windows = (1 << (b - 1)) / wwords;
+        }
+        if (buf != 2) {
+            buf = -1;
+            for (int c = 0; c < 3 && buf < 0; c++) {
+                if (c == 1 && h.n_small < 2) continue;
+                if (c == 2 && h.big_words == 0) continue;
+                if (c != last) buf = c;
+            }
+            if (buf < 0) buf = 0;
+        }
+        A->opt_mode[k] = (int8_t)mode;
+        A->opt_buf[k] = (int8_t)buf;
+        A->opt_sync[k] = (int8_t)(buf == last);
+        A->opt_windows[k] = (int8_t)windows;
+        A->opt_wwords[k] = wwords;
+        last = buf;
+    }
+}
+
 size_t smem_for(const CostConfig &c, const HistPlan &h, int n_opts) {
     size_t o[7];
     return smem_layout(c.threads, c.width, h.hist_words, h.n_small, h.big_words, n_opts, o);
@@ -726,7 +774,7 @@ const CostConfig &cost_config(int i) { return kConfigs[i].cfg; }
 int cost_default_config(int G) {
     if (G <= 1024) return 7;    // 256 x 4, W 8
     if (G <= 2048) return 5;    // 256 x 8, W 4
-    if (G <= 4096) return 1;    // 512 x 8, W 4
+    if (G <= 4096) return 0;    // 256 x 16, W 4
     if (G <= 16384) return 8;   // 512 x 32, W 1
     return -1;
 }
@@ -782,6 +830,7 @@ mgs_status cost_exec_create(mgs_ctx *ctx, const CostLaunch &L, int config, CostE
     A.hist_words = hp.hist_words;
     A.n_small = hp.n_small;
     A.big_words = hp.big_words;
+    option_plan(hp, L.bits + L.opt_lo, L.opt_hi - L.opt_lo, &A);
     X->smem = smem_for(E.cfg, hp, L.opt_hi - L.opt_lo);
     X->persistent = L.persistent;
     if (X->smem > 227 * 1024) {
