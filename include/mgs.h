@@ -292,11 +292,12 @@ mgs_status mgs_quantize_groups(mgs_ctx *ctx, const mgs_scene *scene, int64_t kee
 /*
  * mgs_quantize_groups without any allocation.  The paper has no counterpart:
  * this is an interface for callers that must not allocate device memory
- * while they run -- code recording work into a CUDA stream capture (where
- * cudaMalloc is not permitted), processes whose device memory is owned and
- * capped by another framework's allocator, and real-time encoder threads
- * with a no-allocation rule.  Same arguments, results and errors as
- * mgs_quantize_groups, and the caller still provides every input and output.
+ * while they run -- processes whose device memory is owned and capped by
+ * another framework's allocator (an allocation there can fail or steal the
+ * other framework's headroom), and real-time encoder threads with a
+ * no-allocation rule (an allocation can block or synchronise the device).
+ * Same arguments, results and errors as mgs_quantize_groups, and the caller
+ * still provides every input and output.
  *
  * The scratch it needs (the kept list and its per-tile counts) lives in
  * file-scope device arrays of fixed size that every GPU loading this library

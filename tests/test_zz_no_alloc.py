@@ -1,9 +1,9 @@
 """mgs_quantize_groups_noalloc (static device scratch, no allocation) against
 mgs_quantize_groups, through the C ABI, on two calls in a row.
 
-Some callers cannot allocate device memory while they run (work being
-recorded into a CUDA stream capture, a process whose device memory belongs to
-another framework's capped allocator, a real-time encoder thread).  The
+Some callers cannot allocate device memory while they run (a process whose
+device memory belongs to another framework's capped allocator, a real-time
+encoder thread that may not block or synchronise the device).  The
 allocation-free entry point must give them exactly what the allocating one
 gives everybody else.  This file is collected last so that a run stopping at
 the first failure has already run every other test; it also passes alone in a
