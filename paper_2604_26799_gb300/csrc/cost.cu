@@ -119,37 +119,38 @@ MGS_F2_BINOP(fsub2, "sub.rn.f32x2")
 
 // ---- global loads with L1 eviction hints: the gathered rows and kept
 // positions are read once and must not evict the entropy tables, which every
-// pass reads
+// pass reads.  Read-only data: not volatile, so the compiler may schedule them
+// freely around the (volatile) shared-memory atomics
 __device__ __forceinline__ float4 ld_stream(const float4 *p) {
     float4 v;
-    asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+    asm("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
                  : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
                  : "l"(p));
     return v;
 }
 __device__ __forceinline__ float2 ld_stream(const float2 *p) {
     float2 v;
-    asm volatile("ld.global.nc.L1::no_allocate.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+    asm("ld.global.nc.L1::no_allocate.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
     return v;
 }
 __device__ __forceinline__ float ld_stream(const float *p) {
     float v;
-    asm volatile("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    asm("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
     return v;
 }
 __device__ __forceinline__ int32_t ld_stream(const int32_t *p) {
     int32_t v;
-    asm volatile("ld.global.nc.L1::no_allocate.s32 %0, [%1];" : "=r"(v) : "l"(p));
+    asm("ld.global.nc.L1::no_allocate.s32 %0, [%1];" : "=r"(v) : "l"(p));
     return v;
 }
 __device__ __forceinline__ unsigned long long ld_keep(const unsigned long long *p) {
     unsigned long long v;
-    asm volatile("ld.global.nc.L1::evict_last.u64 %0, [%1];" : "=l"(v) : "l"(p));
+    asm("ld.global.nc.L1::evict_last.u64 %0, [%1];" : "=l"(v) : "l"(p));
     return v;
 }
 __device__ __forceinline__ uint32_t ld_keep(const uint32_t *p) {
     uint32_t v;
-    asm volatile("ld.global.nc.L1::evict_last.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    asm("ld.global.nc.L1::evict_last.u32 %0, [%1];" : "=r"(v) : "l"(p));
     return v;
 }
 
@@ -161,6 +162,28 @@ __device__ __forceinline__ uint32_t atom_add(uint32_t addr, uint32_t v) {
     uint32_t old;
     asm volatile("atom.shared.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(addr), "r"(v));
     return old;
+}
+// The same, executed only where `pred` holds (predicated, not branched: lanes
+// of a warp taking different sides do not split the warp); 0 elsewhere.
+__device__ __forceinline__ uint32_t atom_add_if(bool pred, uint32_t addr, uint32_t v) {
+    uint32_t old = 0;
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %3, 0;\n\t@q atom.shared.add.u32 %0, [%1], %2;\n\t}"
+                 : "+r"(old)
+                 : "r"(addr), "r"(v), "r"((uint32_t)pred));
+    return old;
+}
+
+// One code into a table of 16-bit counter pairs, counted only if `valid` and
+// its word lies in the current window [wlo, wlo + wn).  Branch-free.
+__device__ __forceinline__ void pair_count(bool valid, uint32_t y, uint32_t hbase, uint32_t wlo,
+                                           uint32_t wn, const uint32_t *dtab, uint32_t &dacc) {
+    const uint32_t q = y - kMagicBits;
+    const uint32_t word = (q >> 1) - wlo;
+    const bool in = valid && word < wn;
+    const uint32_t sh = (q & 1u) << 4;
+    const uint32_t old = atom_add_if(in, hbase + (word << 2), 1u << sh);
+    const uint32_t d = ld_keep(&dtab[((old >> sh) & 0xFFFFu) + 1u]);
+    dacc += in ? d : 0u;
 }
 
 // Count one code.  y is the code's bit pattern kMagicBits + q.  For the delta
@@ -179,13 +202,7 @@ __device__ __forceinline__ void hist_op(uint32_t y, uint32_t hbase, uint32_t lan
     } else {
         // 16-bit counter pairs; only codes whose word lies in the current window
         // [wlo, wlo + wn) are counted by this pass
-        const uint32_t q = y - kMagicBits;
-        const uint32_t word = (q >> 1) - wlo;
-        if (word < wn) {
-            const uint32_t sh = (q & 1u) << 4;
-            uint32_t old = atom_add(hbase + (word << 2), 1u << sh);
-            dacc += ld_keep(&dtab[((old >> sh) & 0xFFFFu) + 1u]);
-        }
+        pair_count(true, y, hbase, wlo, wn, dtab, dacc);
     }
 }
 
@@ -271,27 +288,41 @@ __device__ __forceinline__ void eval_generic(const float (&c)[EPT], int nvalid, 
     hacc += dacc;
 }
 
-// Count-only pass of one window of a 16-bit-pair table (codes as in eval_*).
+// Count-only pass of one window of a 16-bit-pair table: the codes of
+// eval_fast (same operations, packed), no error sums, no branches per element.
 template <int T, int EPT>
-__device__ __forceinline__ void count_window(const float (&c)[EPT], const float (&u)[EPT], int nvalid,
-                                          bool generic, const BitParam &p, uint32_t hbase,
-                                          uint32_t wlo, uint32_t wn,
-                                          const uint32_t *dtab,
-                                          unsigned long long &hacc) {
+__device__ __forceinline__ void count_window_fast(const float (&u)[EPT], int nvalid, const BitParam &p,
+                                                  uint32_t hbase, uint32_t wlo, uint32_t wn,
+                                                  const uint32_t *dtab, unsigned long long &hacc) {
+    const float2 tw = make_float2(p.twob, p.twob), zz = make_float2(p.Z, p.Z);
+    const float2 mg = make_float2(kMagic, kMagic);
+    // the lower clamp is a no-op unless the group minimum rounds below code 0
+    const float lo = p.path == kFastBottom ? kMagic : -FLT_MAX;
+    uint32_t dacc = 0;
+#pragma unroll
+    for (int e = 0; e < EPT; e += 2) {
+        float2 y = fadd2(ffma2(make_float2(u[e], u[e + 1]), tw, zz), mg);
+        y.x = fmaxf(fminf(y.x, p.ytop), lo);
+        y.y = fmaxf(fminf(y.y, p.ytop), lo);
+        const bool v0 = e * T + (int)threadIdx.x < nvalid;
+        const bool v1 = (e + 1) * T + (int)threadIdx.x < nvalid;
+        pair_count(v0, __float_as_uint(y.x), hbase, wlo, wn, dtab, dacc);
+        pair_count(v1, __float_as_uint(y.y), hbase, wlo, wn, dtab, dacc);
+    }
+    hacc += dacc;
+}
+
+// The same for groups on the literal-division path (codes as in eval_generic).
+template <int T, int EPT>
+__device__ __forceinline__ void count_window_generic(const float (&c)[EPT], int nvalid, const BitParam &p,
+                                                     uint32_t hbase, uint32_t wlo, uint32_t wn,
+                                                     const uint32_t *dtab, unsigned long long &hacc) {
     uint32_t dacc = 0;
 #pragma unroll
     for (int e = 0; e < EPT; e++) {
-        if (e * T + (int)threadIdx.x >= nvalid) continue;
-        uint32_t y;
-        if (generic) {
-            float x = __fadd_rn(__fdiv_rn(c[e], p.Ss), p.Z);
-            y = kMagicBits + (uint32_t)__float2int_rn(fminf(fmaxf(x, 0.0f), p.top));
-        } else {
-            float yf = fminf(__fadd_rn(__fmaf_rn(u[e], p.twob, p.Z), kMagic), p.ytop);
-            if (p.path == kFastBottom) yf = fmaxf(yf, kMagic);
-            y = __float_as_uint(yf);
-        }
-        hist_op<kDelta16>(y, hbase, 0u, wlo, wn, dtab, dacc);
+        const float x = __fadd_rn(__fdiv_rn(c[e], p.Ss), p.Z);
+        const uint32_t y = kMagicBits + (uint32_t)__float2int_rn(fminf(fmaxf(x, 0.0f), p.top));
+        pair_count(e * T + (int)threadIdx.x < nvalid, y, hbase, wlo, wn, dtab, dacc);
     }
     hacc += dacc;
 }
@@ -596,8 +627,11 @@ __device__ void process_item(const KernelArgs &A, const Smem &sm, int64_t work) 
                     __syncthreads();
                     hist_finish<T>(hist, kDelta16, p.b, p.wwords, A.ltab, hacc);
                     __syncthreads();
-                    count_window<T, EPT>(cw, u, nvalid, generic, p, hbase_raw, (uint32_t)(win * p.wwords), wn,
-                                         A.dtab, hacc);
+                    const uint32_t wlo = (uint32_t)(win * p.wwords);
+                    if (generic)
+                        count_window_generic<T, EPT>(cw, nvalid, p, hbase_raw, wlo, wn, A.dtab, hacc);
+                    else
+                        count_window_fast<T, EPT>(u, nvalid, p, hbase_raw, wlo, wn, A.dtab, hacc);
                 }
             }
             sm.psse[k * T + threadIdx.x] = sse;
