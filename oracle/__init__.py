@@ -4,7 +4,8 @@ TEST INFRASTRUCTURE ONLY: imported by tests/, by __graft_entry__.smoke() and by
 bench.py's CPU-baseline leg.  The product path (the package and its CUDA
 library) never imports it, and it imports nothing from the product.
 
-  oracle.c   C reference of the quantiser, entropy bound, Morton order, ranks
+  oracle.c   C reference of the quantiser, entropy bound, Morton order, ranks,
+             and of the preprocessing (importance I_g, Euler angles)
              (compiled with gcc -O2 -ffp-contract=off, no fast-math)
   mckp.py    exact references of the 0-1 ILP (brute force, DP) and the tau rule
 """
@@ -52,8 +53,11 @@ def load(path: str):
     L.oracle_group_cost.argtypes = [P, i64, P, i32, P, P, P, P, P, P, P]
     L.oracle_cost_table.argtypes = [P, P, i64, i32, P, i32, P, i32, i32, P, P, P, P, P, P, P]
     L.oracle_quantize.argtypes = [P, P, i64, i32, i64, i32, P, P, P]
+    L.oracle_euler.argtypes = [P, P]
+    L.oracle_euler.restype = None
+    L.oracle_preprocess.argtypes = [P, i64, i32, P, ctypes.c_double, P, P, P]
     for f in (L.oracle_rank, L.oracle_morton, L.oracle_group_cost, L.oracle_cost_table,
-              L.oracle_quantize):
+              L.oracle_quantize, L.oracle_preprocess):
         f.restype = ctypes.c_int
     return L
 
@@ -160,3 +164,23 @@ def quantize(attrs, importance, keep: int, G: int, q_bits: np.ndarray):
     _check(lib().oracle_quantize(_p(a), _p(imp), n, C, int(keep), int(G), _p(qb), _p(codes),
                                  _p(mm)))
     return codes[:, :keep], mm[:, :ng]
+
+
+def euler(q, L=None) -> np.ndarray:
+    """Euler angles [phi, theta, psi] (FP64) of the quaternion q = [w, x, y, z]."""
+    qq = np.ascontiguousarray(q, dtype=np.float64).reshape(4)
+    e = np.empty(3)
+    (L or lib()).oracle_euler(_p(qq), _p(e))
+    return e
+
+
+def preprocess(attrs, view_importance, beta: float, L=None):
+    """(attrs [n, 58] FP32 with Euler angles, I_g [n] FP32, V_q) for attrs [n, 59]."""
+    a = np.ascontiguousarray(attrs, dtype=np.float32)
+    imp = np.ascontiguousarray(view_importance, dtype=np.float32)
+    n, C = a.shape
+    out = np.empty((n, C - 1), dtype=np.float32)
+    ig = np.empty(n, dtype=np.float32)
+    vq = np.empty(1)
+    _check((L or lib()).oracle_preprocess(_p(a), n, C, _p(imp), float(beta), _p(out), _p(ig), _p(vq)))
+    return out, ig, float(vq[0])

@@ -25,6 +25,12 @@
  *   oracle_cost_table    the loops of Sec. III-F: every reserve ratio, every
  *                        (channel, block), every bit-width.
  *   oracle_quantize      Sec. III-D quantiser for one chosen configuration.
+ *   oracle_euler         Sec. III-D "Attribute Transformation", Replacement:
+ *                        the Euler angles of a rotation quaternion.
+ *   oracle_preprocess    Sec. III-A (view-independent importance I_i =
+ *                        V_norm^beta, joint score I_g = I_d * I_i) and the
+ *                        quaternion -> Euler replacement of Sec. III-D, over
+ *                        a whole scene; FP64 arithmetic, FP32 outputs.
  *
  * Readings where the paper is silent (each is listed in the design doc):
  *   - S_c = (max - min) / 2^b exactly as printed (not 2^b - 1); the element
@@ -38,6 +44,12 @@
  *     21-bit axis codes floor(t * 2^21) clamped to 2^21 - 1; x bit k -> code
  *     bit 3k, y -> 3k+1, z -> 3k+2; order by (code, index).
  *   - importance order: descending importance, ties by ascending index.
+ *   - preprocessing: V = exp(s0 + s1 + s2) from the stored log-scales (the
+ *     product of the scale vector); the normaliser is the lower 0.9-quantile
+ *     of the sorted volumes (index floor(9 (n - 1) / 10), ascending);
+ *     V_norm = min(V / V_q, 1) (1 if V_q = 0); the quaternion [w, x, y, z]
+ *     is normalised first (a zero quaternion gives zero angles) and the
+ *     square roots' arguments are clamped at 0.
  */
 #include <math.h>
 #include <stdint.h>
@@ -380,4 +392,80 @@ done:
     free(vals);
     free(codes);
     return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Preprocessing (Sec. III-A view-independent importance, Sec. III-D Euler).  */
+/* ------------------------------------------------------------------------ */
+
+#define ORACLE_PI 3.14159265358979323846
+#define ORACLE_PRE_CHANNELS 59   /* input layout: 52..54 log-scale, 55..58 quaternion w, x, y, z */
+#define ORACLE_PRE_SCALE0 52
+#define ORACLE_PRE_QUAT0 55
+
+/* Euler angles [phi, theta, psi] of the rotation quaternion q = [w, x, y, z]
+ * with the formula of Sec. III-D, after normalising q. */
+void oracle_euler(const double q_in[4], double e[3]) {
+    double nrm = sqrt(q_in[0] * q_in[0] + q_in[1] * q_in[1] + q_in[2] * q_in[2] + q_in[3] * q_in[3]);
+    if (!(nrm > 0.0)) {
+        e[0] = e[1] = e[2] = 0.0;
+        return;
+    }
+    double w = q_in[0] / nrm, x = q_in[1] / nrm, y = q_in[2] / nrm, z = q_in[3] / nrm;
+    /* roll: rotation about x */
+    e[0] = atan2(2.0 * (w * x + y * z), 1.0 - 2.0 * (x * x + y * y));
+    /* pitch: -pi/2 + 2 atan2(sqrt(1 + 2(wy - xz)), sqrt(1 - 2(wy - xz))) */
+    double t = w * y - x * z;
+    double a = 1.0 + 2.0 * t, b = 1.0 - 2.0 * t;
+    if (a < 0.0) a = 0.0;
+    if (b < 0.0) b = 0.0;
+    e[1] = -ORACLE_PI / 2.0 + 2.0 * atan2(sqrt(a), sqrt(b));
+    /* yaw: rotation about z */
+    e[2] = atan2(2.0 * (w * z + x * y), 1.0 - 2.0 * (y * y + z * z));
+}
+
+static int cmp_double(const void *a, const void *b) {
+    double x = *(const double *)a, y = *(const double *)b;
+    return (x > y) - (x < y);
+}
+
+/* Scene preprocessing.  attrs [n][59] (FP32), view_imp [n] = I_d.  Outputs:
+ * attrs_out [n][58] (channels 0..54 unchanged, 55..57 = phi, theta, psi),
+ * imp_out [n] = I_g = I_d * V_norm^beta, and *vq_out = the volume normaliser. */
+int oracle_preprocess(const float *attrs, int64_t n, int32_t n_channels, const float *view_imp,
+                      double beta, float *attrs_out, float *imp_out, double *vq_out) {
+    if (n < 1 || n_channels != ORACLE_PRE_CHANNELS || !(beta >= 0.0)) return ORACLE_ERR_ARG;
+    double *vol = (double *)malloc(sizeof(double) * (size_t)n);
+    double *sorted = (double *)malloc(sizeof(double) * (size_t)n);
+    if (!vol || !sorted) {
+        free(vol);
+        free(sorted);
+        return ORACLE_ERR_NOMEM;
+    }
+    for (int64_t i = 0; i < n; i++) {
+        const float *r = attrs + i * n_channels;
+        double ls = (double)r[ORACLE_PRE_SCALE0] + (double)r[ORACLE_PRE_SCALE0 + 1] +
+                    (double)r[ORACLE_PRE_SCALE0 + 2];
+        vol[i] = exp(ls);
+        sorted[i] = vol[i];
+        float *o = attrs_out + i * (n_channels - 1);
+        for (int c = 0; c < ORACLE_PRE_QUAT0; c++) o[c] = r[c];
+        double q[4] = {r[ORACLE_PRE_QUAT0], r[ORACLE_PRE_QUAT0 + 1], r[ORACLE_PRE_QUAT0 + 2],
+                       r[ORACLE_PRE_QUAT0 + 3]};
+        double e[3];
+        oracle_euler(q, e);
+        o[ORACLE_PRE_QUAT0] = (float)e[0];
+        o[ORACLE_PRE_QUAT0 + 1] = (float)e[1];
+        o[ORACLE_PRE_QUAT0 + 2] = (float)e[2];
+    }
+    qsort(sorted, (size_t)n, sizeof(double), cmp_double);
+    double vq = sorted[(9 * (n - 1)) / 10];
+    for (int64_t i = 0; i < n; i++) {
+        double vn = vq > 0.0 ? fmin(vol[i] / vq, 1.0) : 1.0;
+        imp_out[i] = (float)((double)view_imp[i] * pow(vn, beta));
+    }
+    if (vq_out) *vq_out = vq;
+    free(vol);
+    free(sorted);
+    return ORACLE_OK;
 }

@@ -188,3 +188,78 @@ def check_rank(L, seed: int = 4, n: int = 5000):
     expect = np.empty(n, dtype=np.int64)
     expect[order] = np.arange(n)
     assert np.array_equal(r.astype(np.int64), expect)
+
+
+# ---- preprocessing (Sec. III-A view-independent importance, Sec. III-D Euler) ----
+
+def quat_matrix(q) -> np.ndarray:
+    """Textbook rotation matrix of a unit quaternion [w, x, y, z] (Hamilton convention)."""
+    w, x, y, z = np.asarray(q, dtype=np.float64) / np.linalg.norm(q)
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                     [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                     [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+
+
+def euler_matrix(e) -> np.ndarray:
+    """The decoder's rotation matrix from [phi, theta, psi] printed in Sec. III-D:
+    R = Rz(psi) Ry(theta) Rx(phi), written entry by entry."""
+    (sf, cf), (st, ct), (sp, cp) = [(math.sin(a), math.cos(a)) for a in e]
+    return np.array([[ct * cp, -cf * sp + sf * st * cp, sf * sp + cf * st * cp],
+                     [ct * sp, cf * cp + sf * st * sp, -sf * cp + cf * st * sp],
+                     [-st, sf * ct, cf * ct]])
+
+
+def check_euler_axes(L):
+    """A rotation by a about one axis gives that angle alone."""
+    for a in (-2.5, -0.7, 0.0, 0.3, 1.2, 3.0):
+        h = a / 2
+        assert np.allclose(oracle.euler([math.cos(h), math.sin(h), 0, 0], L=L), [a, 0, 0], atol=1e-12)
+        assert np.allclose(oracle.euler([math.cos(h), 0, 0, math.sin(h)], L=L), [0, 0, a], atol=1e-12)
+        if abs(a) < math.pi / 2:
+            assert np.allclose(oracle.euler([math.cos(h), 0, math.sin(h), 0], L=L), [0, a, 0], atol=1e-12)
+
+
+def check_euler_roundtrip(L, seed: int = 5, n: int = 400):
+    """The decoder's matrix of the encoded angles is the quaternion's own rotation
+    (away from gimbal lock), and q, -q and 3q give the same angles."""
+    rng = np.random.default_rng(seed)
+    done = 0
+    while done < n:
+        q = rng.standard_normal(4)
+        e = oracle.euler(q, L=L)
+        if abs(abs(e[1]) - math.pi / 2) < 1e-3:
+            continue
+        assert np.allclose(euler_matrix(e), quat_matrix(q), atol=1e-12), q
+        assert np.allclose(oracle.euler(-q, L=L), e, atol=1e-12)
+        assert np.allclose(oracle.euler(3.0 * q, L=L), e, atol=1e-12)
+        assert -math.pi <= e[0] <= math.pi and -math.pi / 2 <= e[1] <= math.pi / 2
+        done += 1
+
+
+def pre_scene(n: int, seed: int):
+    rng = np.random.default_rng(seed)
+    a = rng.standard_normal((n, 59)).astype(np.float32)
+    a[:, 52:55] = rng.normal(-4.0, 1.0, (n, 3)).astype(np.float32)
+    imp = rng.lognormal(0.0, 1.0, n).astype(np.float32)
+    return a, imp
+
+
+def check_preprocess(L, seed: int = 6, n: int = 1000):
+    """Channels pass through; V_q is numpy's lower 0.9-quantile of the volumes;
+    beta = 0 leaves the importance unchanged; beta = 1 scales it by min(V / V_q, 1)."""
+    a, imp = pre_scene(n, seed)
+    out, ig0, vq = oracle.preprocess(a, imp, 0.0, L=L)
+    assert np.array_equal(out[:, :55], a[:, :55])
+    assert np.array_equal(ig0, imp)
+    vol = np.exp(a[:, 52:55].astype(np.float64).sum(axis=1))
+    assert vq == np.quantile(vol, 0.9, method="lower")
+    _, ig1, _ = oracle.preprocess(a, imp, 1.0, L=L)
+    expect = (imp.astype(np.float64) * np.minimum(vol / vq, 1.0)).astype(np.float32)
+    assert np.allclose(ig1, expect, rtol=2e-7, atol=0)
+    # the Gaussians at or above V_q keep their view-dependent score
+    top = vol >= vq
+    assert np.array_equal(ig1[top], imp[top]) and top.sum() == n - (9 * (n - 1)) // 10
+    _, ig2, _ = oracle.preprocess(a, imp, 2.0, L=L)
+    assert np.allclose(ig2, (imp * np.minimum(vol / vq, 1.0) ** 2).astype(np.float32), rtol=2e-7)
+    for i in range(0, n, 97):
+        assert np.allclose(out[i, 55:58], oracle.euler(a[i, 55:59], L=L).astype(np.float32), atol=0)

@@ -27,6 +27,16 @@ MUTANTS = {
                        "if (x->key > y->key) return 1;"),
     "rank_tiebreak": ("if (x->idx < y->idx) return -1; /* ties: smaller index first */",
                       "if (x->idx < y->idx) return 1;"),
+    "euler_roll_sign": ("e[0] = atan2(2.0 * (w * x + y * z),", "e[0] = atan2(2.0 * (w * x - y * z),"),
+    "euler_pitch_offset": ("e[1] = -ORACLE_PI / 2.0 + 2.0 * atan2(sqrt(a), sqrt(b));",
+                           "e[1] = 2.0 * atan2(sqrt(a), sqrt(b));"),
+    "euler_yaw_args": ("e[2] = atan2(2.0 * (w * z + x * y), 1.0 - 2.0 * (y * y + z * z));",
+                       "e[2] = atan2(1.0 - 2.0 * (y * y + z * z), 2.0 * (w * z + x * y));"),
+    "euler_not_normalised": ("double w = q_in[0] / nrm, x = q_in[1] / nrm, y = q_in[2] / nrm, z = q_in[3] / nrm;",
+                             "double w = q_in[0], x = q_in[1], y = q_in[2], z = q_in[3];"),
+    "quantile_index": ("double vq = sorted[(9 * (n - 1)) / 10];", "double vq = sorted[(9 * n) / 10];"),
+    "volume_not_clipped": ("double vn = vq > 0.0 ? fmin(vol[i] / vq, 1.0) : 1.0;",
+                           "double vn = vq > 0.0 ? vol[i] / vq : 1.0;"),
 }
 
 RUNNER = r"""
@@ -48,6 +58,9 @@ checks = [
     lambda: pins.check_two_point(L, -7.1, 3.3, list(range(1, 17))),
     lambda: pins.check_morton_lattice(L),
     lambda: pins.check_rank(L),
+    lambda: pins.check_euler_axes(L),
+    lambda: pins.check_euler_roundtrip(L),
+    lambda: pins.check_preprocess(L),
 ]
 failed = 0
 for c in checks:

@@ -163,3 +163,15 @@ def test_choose_tau_rule():
     # everything skipped -> largest feasible ratio
     assert mckp.choose_tau([mk(True, 1.0, 10), mk(True, 2.0, 20), mk(False, 0, 0)], 100) == 1
     assert mckp.choose_tau([mk(False, 0, 0)], 100) is None
+
+
+def test_euler_axes():
+    pins.check_euler_axes(oracle.lib())
+
+
+def test_euler_roundtrip_against_quaternion_matrix():
+    pins.check_euler_roundtrip(oracle.lib())
+
+
+def test_preprocess_quantile_and_importance():
+    pins.check_preprocess(oracle.lib())
