@@ -186,6 +186,32 @@ int64_t mgs_kernel_launches(void);
  */
 mgs_status mgs_scene_create(mgs_ctx *ctx, const float *attrs, const float *importance, int64_t n,
                             int32_t n_channels, void *stream, mgs_scene **out);
+
+/*
+ * Preprocessing ahead of mgs_scene_create (Sec. III-A "Gaussians Pruning",
+ * view-independent importance; Sec. III-D "Attribute Transformation",
+ * Replacement).  For a 3D-GS scene in the 59-channel layout (channels 52..54
+ * log-scales, 55..58 the rotation quaternion [w, x, y, z]):
+ *   attrs_out [n][58]   channels 0..54 copied; 55..57 = Euler angles
+ *                       [phi, theta, psi] of the normalised quaternion (radians;
+ *                       a zero quaternion gives zeros)
+ *   importance_out [n]  I_g = I_d * V_norm^beta with I_d = view_importance,
+ *                       V = exp(s0 + s1 + s2) the product of the scales,
+ *                       V_norm = min(V / V_q, 1) (1 when V_q = 0), V_q the
+ *                       lower 0.9-quantile of V (the element of ascending rank
+ *                       floor(9 (n - 1) / 10), selected exactly)
+ *   vq_out              (host, may be NULL) V_q
+ * All arrays are device memory.  Volumes and importance in FP32 (CUDA's expf,
+ * powf); Euler angles in FP64 (the printed formula is ill-conditioned near
+ * theta = +-pi/2), rounded to FP32.
+ * Synchronous on `stream` (it returns V_q and the input check); a temporary
+ * device workspace of 4 n + 512 KiB bytes is allocated on `stream`.
+ * Errors: INVALID_ARG (NULL, n < 1, beta < 0 or not finite),
+ * NONFINITE (a log-scale, quaternion or I_d value is NaN or infinite).
+ */
+mgs_status mgs_preprocess(mgs_ctx *ctx, const float *attrs, const float *view_importance, int64_t n,
+                          double beta, float *attrs_out, float *importance_out, float *vq_out,
+                          void *stream);
 mgs_status mgs_scene_destroy(mgs_scene *scene);
 /* n, channel count and device bytes held by the scene (any may be NULL). */
 mgs_status mgs_scene_info(const mgs_scene *scene, int64_t *n, int32_t *n_channels,

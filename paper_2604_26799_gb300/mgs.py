@@ -124,6 +124,7 @@ _SIGS = {
                          ctypes.POINTER(mgs_solution)],
     "mgs_solve_budgets": [_P, ctypes.POINTER(mgs_table_layout), ctypes.POINTER(mgs_grid),
                           ctypes.c_int32, _P, ctypes.POINTER(mgs_solve_opts), _P],
+    "mgs_preprocess": [_P, _P, _P, ctypes.c_int64, ctypes.c_double, _P, _P, _P, _P],
     "mgs_solve_budgets_device": [_P, _P, ctypes.POINTER(mgs_table_layout), ctypes.POINTER(mgs_grid),
                                  ctypes.c_int32, _P, ctypes.POINTER(mgs_solve_opts), _P, _P],
 }
@@ -445,3 +446,20 @@ def table_views(buf, layout: mgs_table_layout) -> dict:
                 cnt=view(layout.off_count, ni, np.int32, (ni,)),
                 vmin=view(layout.off_vmin, ni, np.float32, (ni,)),
                 vmax=view(layout.off_vmax, ni, np.float32, (ni,)))
+
+
+def mgs_preprocess(ctx: int, attrs, view_importance, beta: float, attrs_out=None, importance_out=None,
+                   stream=None):
+    """Euler replacement and importance I_g = I_d * V_norm^beta on the device.
+
+    attrs: [n, 59] float32 device tensor; returns (attrs_out [n, 58], importance_out [n], V_q)."""
+    import torch
+    n = int(attrs.shape[0])
+    if attrs_out is None:
+        attrs_out = torch.empty((n, 58), dtype=torch.float32, device=attrs.device)
+    if importance_out is None:
+        importance_out = torch.empty(n, dtype=torch.float32, device=attrs.device)
+    vq = ctypes.c_float()
+    _check(lib().mgs_preprocess(ctx, _ptr(attrs), _ptr(view_importance), n, float(beta), _ptr(attrs_out),
+                                _ptr(importance_out), ctypes.byref(vq), _stream(stream)))
+    return attrs_out, importance_out, vq.value
