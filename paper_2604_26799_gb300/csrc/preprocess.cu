@@ -1,19 +1,23 @@
 // Scene preprocessing: Sec. III-A's view-independent importance and Sec. III-D's
 // quaternion -> Euler replacement, ahead of the cost tables.
 //
-//   k_pre_copy    channels 0..54 of [n][59] into [n][58] (one thread per output value)
-//   k_pre_rows    per Gaussian: volume V = exp(s0 + s1 + s2) of the stored log-scales
-//                 (FP32), Euler angles of the normalised quaternion [w, x, y, z] (FP64,
-//                 rounded to FP32; channels 55..57 of the output), finiteness of the
-//                 inputs it reads, and a histogram of V's top 16 bits (V >= 0, so its
-//                 bits order like V)
+//   k_pre_tile    64 rows per CTA staged in shared memory: channels 0..54 copied
+//                 into [n][58]; per row the volume V = exp(s0 + s1 + s2) of the stored
+//                 log-scales (FP32), the finiteness of the inputs it reads, a count
+//                 histogram of V's top 16 bits (V >= 0, so its bits order like V), and
+//                 the Euler angles of the normalised quaternion [w, x, y, z] (channels
+//                 55..57) in FP32 where |sin(theta)| <= 0.9
+//   k_pre_euler64 the other rows' angles in FP64 (the printed formula is
+//                 ill-conditioned near theta = +-pi/2), rounded once to FP32
 //   k_pre_select  one CTA: the bucket holding the k-th smallest V, k = floor(9(n-1)/10)
 //   k_pre_hist_lo histogram of the low 16 bits inside that bucket
 //   (k_pre_select again: V_q exactly, the lower 0.9-quantile of the volumes)
 //   k_pre_imp     I_g = I_d * min(V / V_q, 1)^beta (V_norm = 1 when V_q = 0)
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
+#include <cstdint>
 
 #include "internal.h"
 
@@ -29,36 +33,19 @@ struct PreState {
     unsigned int bucket;      // top 16 bits of V_q (after the first selection)
     unsigned int rank_left;   // rank of V_q inside that bucket
     float vq;                 // the normaliser
+    unsigned int n_slow;      // rows whose Euler angles are redone in FP64
 };
 
-__global__ void k_pre_copy(const float *__restrict__ in, float *__restrict__ out, int64_t n) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n * kQuat0) return;
-    const int64_t i = t / kQuat0;
-    const int c = (int)(t - i * kQuat0);
-    out[i * kOutC + c] = in[i * kInC + c];
-}
+constexpr int kTileRows = 64, kTileThreads = 256;
+// |sin(theta)| above which the FP32 evaluation of the printed formula loses
+// accuracy (cos(theta) < 0.44): those rows are redone in FP64
+constexpr float kSlowSin = 0.9f;
 
-__global__ void k_pre_rows(const float *__restrict__ in, const float *__restrict__ view_imp, int64_t n,
-                           float *__restrict__ out, float *__restrict__ vol, unsigned int *__restrict__ hist,
-                           PreState *st) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const float *r = in + i * kInC;
-    const float s0 = r[kScale0], s1 = r[kScale0 + 1], s2 = r[kScale0 + 2];
-    double w = r[kQuat0], x = r[kQuat0 + 1], y = r[kQuat0 + 2], z = r[kQuat0 + 3];
-    const bool finite = isfinite(s0) && isfinite(s1) && isfinite(s2) && isfinite(w) && isfinite(x) &&
-                        isfinite(y) && isfinite(z) && isfinite(view_imp[i]);
-    if (!finite) atomicOr(&st->nonfinite, 1u);
-    const float v = finite ? expf(s0 + s1 + s2) : 0.0f;
-    vol[i] = v;
-    atomicAdd(&hist[__float_as_uint(v) >> 16], 1u);
-    // The printed Euler formula is ill-conditioned near theta = +-pi/2 (through
-    // sqrt(1 -+ 2t) and the small atan2 arguments of phi and psi), so it is
-    // evaluated in FP64 and rounded once to FP32.
+// Euler angles of one quaternion in FP64 (the printed formula, rounded once).
+__device__ void euler64(double w, double x, double y, double z, float *e) {
     double phi = 0.0, theta = 0.0, psi = 0.0;
     const double nrm = sqrt(w * w + x * x + y * y + z * z);
-    if (finite && nrm > 0.0) {
+    if (nrm > 0.0) {
         w /= nrm;
         x /= nrm;
         y /= nrm;
@@ -69,10 +56,92 @@ __global__ void k_pre_rows(const float *__restrict__ in, const float *__restrict
         theta = -1.5707963267948966 + 2.0 * atan2(sqrt(a), sqrt(b));
         psi = atan2(2.0 * (w * z + x * y), 1.0 - 2.0 * (y * y + z * z));
     }
-    float *o = out + i * kOutC;
-    o[kQuat0] = (float)phi;
-    o[kQuat0 + 1] = (float)theta;
-    o[kQuat0 + 2] = (float)psi;
+    e[0] = (float)phi;
+    e[1] = (float)theta;
+    e[2] = (float)psi;
+}
+
+// 64 rows per CTA: the [64][59] input tile is staged in shared memory (16-byte
+// loads when the arrays are 16-byte aligned), 64 threads do the per-row work,
+// and the [64][58] output tile is written back (16-byte stores).
+template <bool VEC>
+__global__ void __launch_bounds__(kTileThreads) k_pre_tile(const float *__restrict__ in,
+                                                           const float *__restrict__ view_imp, int64_t n,
+                                                           float *__restrict__ out, float *__restrict__ vol,
+                                                           unsigned int *__restrict__ hist, PreState *st,
+                                                           int64_t *__restrict__ slow, unsigned int *n_slow) {
+    __shared__ __align__(16) float s_in[kTileRows * kInC];
+    __shared__ float s_e[kTileRows][3];
+    const int tid = threadIdx.x;
+    const int64_t r0 = (int64_t)blockIdx.x * kTileRows;
+    const int rows = (int)(n - r0 < kTileRows ? n - r0 : kTileRows);
+    const float *src = in + r0 * kInC;
+    if (VEC && rows == kTileRows) {
+        for (int j = tid; j < kTileRows * kInC / 4; j += kTileThreads)
+            reinterpret_cast<float4 *>(s_in)[j] = __ldg(reinterpret_cast<const float4 *>(src) + j);
+    } else {
+        for (int j = tid; j < rows * kInC; j += kTileThreads) s_in[j] = __ldg(src + j);
+    }
+    __syncthreads();
+    if (tid < rows) {
+        const int64_t i = r0 + tid;
+        const float *r = s_in + tid * kInC;
+        const float s0 = r[kScale0], s1 = r[kScale0 + 1], s2 = r[kScale0 + 2];
+        float w = r[kQuat0], x = r[kQuat0 + 1], y = r[kQuat0 + 2], z = r[kQuat0 + 3];
+        const bool finite = isfinite(s0) && isfinite(s1) && isfinite(s2) && isfinite(w) && isfinite(x) &&
+                            isfinite(y) && isfinite(z) && isfinite(view_imp[i]);
+        if (!finite) atomicOr(&st->nonfinite, 1u);
+        const float v = finite ? expf(s0 + s1 + s2) : 0.0f;
+        vol[i] = v;
+        atomicAdd(&hist[__float_as_uint(v) >> 16], 1u);
+        float phi = 0.0f, theta = 0.0f, psi = 0.0f;
+        const float nrm = sqrtf(w * w + x * x + y * y + z * z);
+        if (finite && nrm > 0.0f) {
+            w /= nrm;
+            x /= nrm;
+            y /= nrm;
+            z /= nrm;
+            const float t = w * y - x * z;
+            if (fabsf(2.0f * t) > kSlowSin) {
+                slow[atomicAdd(n_slow, 1u)] = i;   // redone in FP64 by k_pre_euler64
+            } else {
+                phi = atan2f(2.0f * (w * x + y * z), 1.0f - 2.0f * (x * x + y * y));
+                theta = -1.57079632679489662f + 2.0f * atan2f(sqrtf(1.0f + 2.0f * t), sqrtf(1.0f - 2.0f * t));
+                psi = atan2f(2.0f * (w * z + x * y), 1.0f - 2.0f * (y * y + z * z));
+            }
+        }
+        s_e[tid][0] = phi;
+        s_e[tid][1] = theta;
+        s_e[tid][2] = psi;
+    }
+    __syncthreads();
+    float *dst = out + r0 * kOutC;
+    auto value = [&](int idx) {
+        const int rr = idx / kOutC, c = idx - rr * kOutC;
+        return c < kQuat0 ? s_in[rr * kInC + c] : s_e[rr][c - kQuat0];
+    };
+    if (VEC && rows == kTileRows) {
+        for (int j = tid; j < kTileRows * kOutC / 4; j += kTileThreads)
+            reinterpret_cast<float4 *>(dst)[j] =
+                make_float4(value(4 * j), value(4 * j + 1), value(4 * j + 2), value(4 * j + 3));
+    } else {
+        for (int j = tid; j < rows * kOutC; j += kTileThreads) dst[j] = value(j);
+    }
+}
+
+// The rows near gimbal lock, in FP64.
+__global__ void k_pre_euler64(const float *__restrict__ in, const int64_t *__restrict__ slow,
+                              const unsigned int *n_slow, float *__restrict__ out) {
+    const unsigned int m = *n_slow;
+    for (unsigned int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) {
+        const int64_t i = slow[k];
+        const float *r = in + i * kInC;
+        float e[3];
+        euler64(r[kQuat0], r[kQuat0 + 1], r[kQuat0 + 2], r[kQuat0 + 3], e);
+        out[i * kOutC + kQuat0] = e[0];
+        out[i * kOutC + kQuat0 + 1] = e[1];
+        out[i * kOutC + kQuat0 + 2] = e[2];
+    }
 }
 
 // One CTA: the bucket of a 2^16-bin count histogram holding the element of
@@ -165,9 +234,11 @@ extern "C" mgs_status mgs_preprocess(mgs_ctx *ctx, const float *attrs, const flo
     DeviceGuard guard(ctx->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const size_t vol_bytes = (sizeof(float) * (size_t)n + 255) & ~(size_t)255;
+    const size_t slow_bytes = (sizeof(int64_t) * (size_t)n + 255) & ~(size_t)255;
     const size_t hist_bytes = sizeof(unsigned int) * kBins;
     char *ws = nullptr;
-    if (cudaMallocAsync(reinterpret_cast<void **>(&ws), vol_bytes + 2 * hist_bytes + 256, st) != cudaSuccess) {
+    if (cudaMallocAsync(reinterpret_cast<void **>(&ws), vol_bytes + slow_bytes + 2 * hist_bytes + 256, st) !=
+        cudaSuccess) {
         cudaGetLastError();
         set_error("preprocessing workspace of %zu bytes could not be allocated", vol_bytes + 2 * hist_bytes);
         return MGS_ERR_OUT_OF_MEMORY;
@@ -178,13 +249,23 @@ extern "C" mgs_status mgs_preprocess(mgs_ctx *ctx, const float *attrs, const flo
         ~Free() { cudaFreeAsync(p, s); }
     } free_ws{ws, st};
     float *vol = reinterpret_cast<float *>(ws);
-    unsigned int *hist_hi = reinterpret_cast<unsigned int *>(ws + vol_bytes);
+    int64_t *slow = reinterpret_cast<int64_t *>(ws + vol_bytes);
+    unsigned int *hist_hi = reinterpret_cast<unsigned int *>(ws + vol_bytes + slow_bytes);
     unsigned int *hist_lo = hist_hi + kBins;
-    PreState *pst = reinterpret_cast<PreState *>(ws + vol_bytes + 2 * hist_bytes);
+    PreState *pst = reinterpret_cast<PreState *>(ws + vol_bytes + slow_bytes + 2 * hist_bytes);
+    unsigned int *n_slow = &pst->n_slow;
     MGS_CUDA_TRY(cudaMemsetAsync(hist_hi, 0, 2 * hist_bytes + sizeof(PreState), st));
     const int64_t want = (9 * (n - 1)) / 10;
-    k_pre_copy<<<blocks_for(n * kQuat0, 256), 256, 0, st>>>(attrs, attrs_out, n);
-    k_pre_rows<<<blocks_for(n, 256), 256, 0, st>>>(attrs, view_importance, n, attrs_out, vol, hist_hi, pst);
+    const bool vec = (reinterpret_cast<uintptr_t>(attrs) % 16 == 0) && (reinterpret_cast<uintptr_t>(attrs_out) % 16 == 0);
+    const unsigned int tiles = blocks_for(n, kTileRows);
+    if (vec)
+        k_pre_tile<true><<<tiles, kTileThreads, 0, st>>>(attrs, view_importance, n, attrs_out, vol, hist_hi, pst,
+                                                          slow, n_slow);
+    else
+        k_pre_tile<false><<<tiles, kTileThreads, 0, st>>>(attrs, view_importance, n, attrs_out, vol, hist_hi, pst,
+                                                           slow, n_slow);
+    const unsigned int slow_blocks = (unsigned int)std::min<int64_t>((int64_t)ctx->sm_count * 4, blocks_for(n, 256));
+    k_pre_euler64<<<slow_blocks, 256, 0, st>>>(attrs, slow, n_slow, attrs_out);
     k_pre_select<<<1, kSelThreads, 0, st>>>(hist_hi, want, pst, 0);
     k_pre_hist_lo<<<blocks_for(n, 256), 256, 0, st>>>(vol, n, pst, hist_lo);
     k_pre_select<<<1, kSelThreads, 0, st>>>(hist_lo, 0, pst, 1);

@@ -1,8 +1,9 @@
 """Preprocessing (Sec. III-A view-independent importance, Sec. III-D Euler
 replacement) on the GPU against the oracle: copied channels bit-exact, V_q
 (an exact order statistic of the device's FP32 volumes) and I_g within FP32
-rounding of the FP64 oracle, Euler angles (FP64 on both sides, rounded
-to FP32) directly and through the decoder's rotation matrix; edge cases; and the cost table of the preprocessed
+rounding of the FP64 oracle, Euler angles (FP32 where well-conditioned,
+FP64 near gimbal lock) directly and through the decoder's rotation matrix;
+edge cases; and the cost table of the preprocessed
 58-channel scene (needs a GB300)."""
 import math
 
@@ -18,8 +19,9 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-# angles: FP64 on both sides, rounded to FP32 (a few ulp of pi)
-ANGLE_TOL = 1e-6
+# angles: FP32 where |sin(theta)| <= 0.9 (a few ulp of pi, conditioning <= 2.3),
+# FP64 rounded once near gimbal lock
+ANGLE_TOL = 2e-6
 MATRIX_TOL = 3e-6
 IMP_RTOL = 2e-5
 
@@ -56,8 +58,8 @@ def compare(attrs, out, ig, vq, ref, sample=None):
     e_ref = r_out[rows, 55:58].astype(np.float64)
     for k in range(0, len(rows), max(1, len(rows) // 2000)):
         assert np.allclose(pins.euler_matrix(e_gpu[k]), pins.euler_matrix(e_ref[k]), atol=MATRIX_TOL), rows[k]
-    # both sides evaluate the formula in FP64 and round once: the angles agree to
-    # FP32 rounding everywhere, gimbal lock included
+    # well-conditioned rows in FP32, the others in FP64 rounded once: the angles
+    # agree everywhere, gimbal lock included
     diff = np.abs(wrap(e_gpu - e_ref))
     bad = np.argwhere(diff > ANGLE_TOL)
     assert bad.size == 0, [(rows[i], c, e_gpu[i], e_ref[i]) for i, c in bad[:5]]
