@@ -1,12 +1,12 @@
 // Scene preprocessing: Sec. III-A's view-independent importance and Sec. III-D's
 // quaternion -> Euler replacement, ahead of the cost tables.
 //
-//   k_pre_tile    64 rows per CTA staged in shared memory: channels 0..54 copied
+//   k_pre_tile    128 rows per CTA staged in shared memory: channels 0..54 copied
 //                 into [n][58]; per row the volume V = exp(s0 + s1 + s2) of the stored
 //                 log-scales (FP32), the finiteness of the inputs it reads, a count
 //                 histogram of V's top 16 bits (V >= 0, so its bits order like V), and
 //                 the Euler angles of the normalised quaternion [w, x, y, z] (channels
-//                 55..57) in FP32 where |sin(theta)| <= 0.9
+//                 55..57) in FP32 where |sin(theta)| <= 0.95
 //   k_pre_euler64 the other rows' angles in FP64 (the printed formula is
 //                 ill-conditioned near theta = +-pi/2), rounded once to FP32
 //   k_pre_select  one CTA: the bucket holding the k-th smallest V, k = floor(9(n-1)/10)
@@ -36,10 +36,10 @@ struct PreState {
     unsigned int n_slow;      // rows whose Euler angles are redone in FP64
 };
 
-constexpr int kTileRows = 64, kTileThreads = 256;
+constexpr int kTileRows = 128, kTileThreads = 128;   // one row per thread
 // |sin(theta)| above which the FP32 evaluation of the printed formula loses
-// accuracy (cos(theta) < 0.44): those rows are redone in FP64
-constexpr float kSlowSin = 0.9f;
+// accuracy (cos(theta) < 0.31): those rows are redone in FP64
+constexpr float kSlowSin = 0.95f;
 
 // Euler angles of one quaternion in FP64 (the printed formula, rounded once).
 __device__ void euler64(double w, double x, double y, double z, float *e) {
@@ -61,9 +61,10 @@ __device__ void euler64(double w, double x, double y, double z, float *e) {
     e[2] = (float)psi;
 }
 
-// 64 rows per CTA: the [64][59] input tile is staged in shared memory (16-byte
-// loads when the arrays are 16-byte aligned), 64 threads do the per-row work,
-// and the [64][58] output tile is written back (16-byte stores).
+// 128 rows per CTA: the [128][59] input tile is staged in shared memory
+// (16-byte loads when the arrays are 16-byte aligned), one thread per row does
+// the per-row work, and the [128][58] output tile is written back (16-byte
+// stores).
 template <bool VEC>
 __global__ void __launch_bounds__(kTileThreads) k_pre_tile(const float *__restrict__ in,
                                                            const float *__restrict__ view_imp, int64_t n,
@@ -93,7 +94,10 @@ __global__ void __launch_bounds__(kTileThreads) k_pre_tile(const float *__restri
         if (!finite) atomicOr(&st->nonfinite, 1u);
         const float v = finite ? expf(s0 + s1 + s2) : 0.0f;
         vol[i] = v;
-        atomicAdd(&hist[__float_as_uint(v) >> 16], 1u);
+        // one atomic per distinct bucket in the warp (volumes cluster in few buckets)
+        const unsigned int bucket = __float_as_uint(v) >> 16;
+        const unsigned int peers = __match_any_sync(__activemask(), bucket);
+        if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&hist[bucket], (unsigned int)__popc(peers));
         float phi = 0.0f, theta = 0.0f, psi = 0.0f;
         const float nrm = sqrtf(w * w + x * x + y * y + z * z);
         if (finite && nrm > 0.0f) {
