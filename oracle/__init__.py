@@ -5,7 +5,7 @@ bench.py's CPU-baseline leg.  The product path (the package and its CUDA
 library) never imports it, and it imports nothing from the product.
 
   oracle.c   C reference of the quantiser, entropy bound, Morton order, ranks,
-             and of the preprocessing (importance I_g, Euler angles)
+             and of the preprocessing (importance I_g, Euler angles) and RAHT
              (compiled with gcc -O2 -ffp-contract=off, no fast-math)
   mckp.py    exact references of the 0-1 ILP (brute force, DP) and the tau rule
 """
@@ -56,8 +56,9 @@ def load(path: str):
     L.oracle_euler.argtypes = [P, P]
     L.oracle_euler.restype = None
     L.oracle_preprocess.argtypes = [P, i64, i32, P, ctypes.c_double, P, P, P]
+    L.oracle_raht.argtypes = [P, i64, i32, P, i32, i32, P, P, P]
     for f in (L.oracle_rank, L.oracle_morton, L.oracle_group_cost, L.oracle_cost_table,
-              L.oracle_quantize, L.oracle_preprocess):
+              L.oracle_quantize, L.oracle_preprocess, L.oracle_raht):
         f.restype = ctypes.c_int
     return L
 
@@ -184,3 +185,16 @@ def preprocess(attrs, view_importance, beta: float, L=None):
     vq = np.empty(1)
     _check((L or lib()).oracle_preprocess(_p(a), n, C, _p(imp), float(beta), _p(out), _p(ig), _p(vq)))
     return out, ig, float(vq[0])
+
+
+def raht(attrs, channels, depth: int, L=None):
+    """(DC [n_c], AC [V - 1, n_c], V) of the RAHT of `channels` at octree depth `depth` (FP64)."""
+    a = np.ascontiguousarray(attrs, dtype=np.float32)
+    ch = np.ascontiguousarray(channels, dtype=np.int32)
+    n, C = a.shape
+    dc = np.empty(ch.shape[0])
+    ac = np.empty((max(n - 1, 1), ch.shape[0]))
+    nv = np.empty(1, dtype=np.int64)
+    _check((L or lib()).oracle_raht(_p(a), n, C, _p(ch), ch.shape[0], int(depth), _p(dc), _p(ac), _p(nv)))
+    V = int(nv[0])
+    return dc, ac[:V - 1], V

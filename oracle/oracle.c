@@ -27,6 +27,10 @@
  *   oracle_quantize      Sec. III-D quantiser for one chosen configuration.
  *   oracle_euler         Sec. III-D "Attribute Transformation", Replacement:
  *                        the Euler angles of a rotation quaternion.
+ *   oracle_raht          Sec. III-D "Region Adaptive Hierarchical Transform":
+ *                        voxels at octree depth d (Gaussians sharing a voxel
+ *                        averaged), merged pairwise along x, y, z from the
+ *                        finest level up; one DC and V - 1 AC coefficients.
  *   oracle_preprocess    Sec. III-A (view-independent importance I_i =
  *                        V_norm^beta, joint score I_g = I_d * I_i) and the
  *                        quaternion -> Euler replacement of Sec. III-D, over
@@ -50,6 +54,15 @@
  *     V_norm = min(V / V_q, 1) (1 if V_q = 0); the quaternion [w, x, y, z]
  *     is normalised first (a zero quaternion gives zero angles) and the
  *     square roots' arguments are clamped at 0.
+ *   - RAHT: the voxel of a Gaussian at depth d is its Morton code >> 3(21 - d)
+ *     (so the x, y, z bits of the voxel code are those of the Morton code);
+ *     a voxel's attribute is the FP64 mean of its Gaussians, summed in Morton
+ *     order, and its weight is 1; step s = 0 .. 3d - 1 merges the nodes whose
+ *     codes agree above bit s + 1 (the lower node first: x1, w1) into
+ *     DC = (sqrt(w1) x1 + sqrt(w2) x2) / sqrt(w1 + w2) and
+ *     AC = (sqrt(w1) x2 - sqrt(w2) x1) / sqrt(w1 + w2), weight w1 + w2; an
+ *     unpaired node passes up unchanged.  ACs are listed step by step, in
+ *     ascending code within a step.
  */
 #include <math.h>
 #include <stdint.h>
@@ -468,4 +481,84 @@ int oracle_preprocess(const float *attrs, int64_t n, int32_t n_channels, const f
     free(vol);
     free(sorted);
     return ORACLE_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* RAHT (Sec. III-D).                                                         */
+/* ------------------------------------------------------------------------ */
+
+/* attrs [n][n_channels]; chan [n_c] the transformed channels; depth 1..21.
+ * dc_out [n_c]; ac_out [(n - 1)][n_c] (capacity); *n_vox_out = V.  FP64. */
+int oracle_raht(const float *attrs, int64_t n, int32_t n_channels, const int32_t *chan, int32_t n_c,
+                int32_t depth, double *dc_out, double *ac_out, int64_t *n_vox_out) {
+    if (n < 1 || n_c < 1 || depth < 1 || depth > 21) return ORACLE_ERR_ARG;
+    for (int32_t k = 0; k < n_c; k++)
+        if (chan[k] < 0 || chan[k] >= n_channels) return ORACLE_ERR_ARG;
+    uint64_t *code = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)n);
+    int64_t *order = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    uint64_t *key = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)n);
+    int64_t *w = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    double *x = (double *)malloc(sizeof(double) * (size_t)n * (size_t)n_c);
+    if (!code || !order || !key || !w || !x) {
+        free(code); free(order); free(key); free(w); free(x);
+        return ORACLE_ERR_NOMEM;
+    }
+    int rc = oracle_morton(attrs, n, n_channels, code, order);
+    if (rc) goto done;
+    /* voxels: runs of equal code >> 3(21 - d) in Morton order, FP64 means */
+    int shift = 3 * (21 - depth);
+    int64_t m = 0;
+    for (int64_t p = 0; p < n;) {
+        uint64_t vc = code[order[p]] >> shift;
+        int64_t q = p;
+        while (q < n && (code[order[q]] >> shift) == vc) q++;
+        for (int32_t k = 0; k < n_c; k++) {
+            double sum = 0.0;
+            for (int64_t t = p; t < q; t++) sum += (double)attrs[order[t] * n_channels + chan[k]];
+            x[m * n_c + k] = sum / (double)(q - p);
+        }
+        key[m] = vc;
+        w[m] = 1;
+        m++;
+        p = q;
+    }
+    *n_vox_out = m;
+    /* merges, finest level first: bit 0 of the voxel code is x, 1 y, 2 z, ... */
+    int64_t n_ac = 0;
+    for (int s = 0; s < 3 * depth; s++) {
+        int64_t out = 0;
+        for (int64_t i = 0; i < m;) {
+            if (i + 1 < m && (key[i] >> 1) == (key[i + 1] >> 1)) {
+                double w1 = (double)w[i], w2 = (double)w[i + 1];
+                double a = sqrt(w1), b = sqrt(w2), sw = sqrt(w1 + w2);
+                for (int32_t k = 0; k < n_c; k++) {
+                    double x1 = x[i * n_c + k], x2 = x[(i + 1) * n_c + k];
+                    double dc = (a * x1 + b * x2) / sw;
+                    double ac = (a * x2 - b * x1) / sw;
+                    ac_out[n_ac * n_c + k] = ac;
+                    x[out * n_c + k] = dc;
+                }
+                n_ac++;
+                w[out] = w[i] + w[i + 1];
+                key[out] = key[i] >> 1;
+                out++;
+                i += 2;
+            } else {
+                for (int32_t k = 0; k < n_c; k++) x[out * n_c + k] = x[i * n_c + k];
+                w[out] = w[i];
+                key[out] = key[i] >> 1;
+                out++;
+                i += 1;
+            }
+        }
+        m = out;
+    }
+    if (m != 1) {
+        rc = ORACLE_ERR_ARG;
+        goto done;
+    }
+    for (int32_t k = 0; k < n_c; k++) dc_out[k] = x[k];
+done:
+    free(code); free(order); free(key); free(w); free(x);
+    return rc;
 }

@@ -263,3 +263,62 @@ def check_preprocess(L, seed: int = 6, n: int = 1000):
     assert np.allclose(ig2, (imp * np.minimum(vol / vq, 1.0) ** 2).astype(np.float32), rtol=2e-7)
     for i in range(0, n, 97):
         assert np.allclose(out[i, 55:58], oracle.euler(a[i, 55:59], L=L).astype(np.float32), atol=0)
+
+
+# ---- RAHT (Sec. III-D) ----
+
+def check_raht_example(L):
+    """Three voxels at depth 1, (0,0,0) = 1, (1,0,0) = 2, (0,1,0) = 4: the x-merge of
+    the first two, then the y-merge of that node (weight 2) with the third."""
+    a = np.zeros((3, 4), np.float32)
+    a[:, :3] = [[0, 0, 0], [1, 0, 0], [0, 1, 0]]
+    a[:, 3] = [1.0, 2.0, 4.0]
+    dc, ac, V = oracle.raht(a, [3], 1, L=L)
+    d1 = 3.0 / math.sqrt(2.0)
+    assert V == 3
+    assert math.isclose(ac[0, 0], 1.0 / math.sqrt(2.0), rel_tol=1e-14)
+    assert math.isclose(ac[1, 0], (math.sqrt(2.0) * 4.0 - d1) / math.sqrt(3.0), rel_tol=1e-14)
+    assert math.isclose(dc[0], 7.0 / math.sqrt(3.0), rel_tol=1e-14)
+
+
+def voxel_means(attrs, channels, depth, L):
+    """Voxel codes and FP64 means, from the Morton codes and numpy grouping."""
+    codes, order = oracle.morton(attrs, L=L)
+    vc = codes[order] >> np.uint64(3 * (21 - depth))
+    uniq, start = np.unique(vc, return_index=True)
+    vals = attrs[order][:, channels].astype(np.float64)
+    counts = np.diff(np.append(start, len(vc)))
+    means = np.add.reduceat(vals, start, axis=0) / counts[:, None]
+    return uniq, means
+
+
+def check_raht_orthonormal(L, seed: int = 8, n: int = 3000):
+    """Leaf weights 1 make the transform orthonormal: the energy of the voxel
+    means equals DC^2 + sum AC^2, and DC = sum / sqrt(V)."""
+    rng = np.random.default_rng(seed)
+    a = rng.uniform(0, 1, (n, 6)).astype(np.float32)
+    a[:, 3:] = rng.standard_normal((n, 3)).astype(np.float32)
+    for depth in (3, 6, 10):
+        dc, ac, V = oracle.raht(a, [3, 4, 5], depth, L=L)
+        uniq, means = voxel_means(a, [3, 4, 5], depth, L)
+        assert V == len(uniq) and ac.shape == (V - 1, 3)
+        energy = (means ** 2).sum(axis=0)
+        assert np.allclose(dc ** 2 + (ac ** 2).sum(axis=0), energy, rtol=1e-11, atol=0)
+        assert np.allclose(dc, means.sum(axis=0) / math.sqrt(V), rtol=1e-12, atol=1e-12)
+
+
+def check_raht_constant_and_dedup(L, seed: int = 9, n: int = 2000):
+    """A constant channel has no AC energy; Gaussians sharing a voxel enter as their mean."""
+    rng = np.random.default_rng(seed)
+    a = rng.uniform(0, 1, (n, 5)).astype(np.float32)
+    a[:, 3] = 2.5
+    dc, ac, V = oracle.raht(a, [3], 7, L=L)
+    assert np.all(np.abs(ac) < 1e-12) and math.isclose(dc[0], 2.5 * math.sqrt(V), rel_tol=1e-13)
+    a[:, 4] = (rng.integers(-1000, 1000, n) / 64.0).astype(np.float32)   # dyadic: +1 is exact
+    b = np.concatenate([a, a], axis=0)              # every Gaussian twice: same voxels
+    b[n:, 4] += 1.0                                  # the copies differ by 1 in channel 4
+    dc1, ac1, V1 = oracle.raht(a, [4], 7, L=L)
+    dc2, ac2, V2 = oracle.raht(b, [4], 7, L=L)
+    assert V1 == V2
+    assert np.allclose(dc2, dc1 + 0.5 * math.sqrt(V1), rtol=1e-12)   # every mean moved by 0.5
+    assert np.allclose(ac2, ac1, atol=1e-10)

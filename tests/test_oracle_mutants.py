@@ -37,6 +37,11 @@ MUTANTS = {
     "quantile_index": ("double vq = sorted[(9 * (n - 1)) / 10];", "double vq = sorted[(9 * n) / 10];"),
     "volume_not_clipped": ("double vn = vq > 0.0 ? fmin(vol[i] / vq, 1.0) : 1.0;",
                            "double vn = vq > 0.0 ? vol[i] / vq : 1.0;"),
+    "raht_ac_sign": ("double ac = (a * x2 - b * x1) / sw;", "double ac = (a * x1 - b * x2) / sw;"),
+    "raht_weights_not_rooted": ("double a = sqrt(w1), b = sqrt(w2), sw = sqrt(w1 + w2);",
+                                "double a = w1, b = w2, sw = sqrt(w1 + w2);"),
+    "raht_mean_not_divided": ("x[m * n_c + k] = sum / (double)(q - p);", "x[m * n_c + k] = sum;"),
+    "raht_weight_not_summed": ("w[out] = w[i] + w[i + 1];", "w[out] = w[i];"),
 }
 
 RUNNER = r"""
@@ -61,6 +66,9 @@ checks = [
     lambda: pins.check_euler_axes(L),
     lambda: pins.check_euler_roundtrip(L),
     lambda: pins.check_preprocess(L),
+    lambda: pins.check_raht_example(L),
+    lambda: pins.check_raht_orthonormal(L),
+    lambda: pins.check_raht_constant_and_dedup(L),
 ]
 failed = 0
 for c in checks:

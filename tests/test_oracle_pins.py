@@ -175,3 +175,15 @@ def test_euler_roundtrip_against_quaternion_matrix():
 
 def test_preprocess_quantile_and_importance():
     pins.check_preprocess(oracle.lib())
+
+
+def test_raht_worked_example():
+    pins.check_raht_example(oracle.lib())
+
+
+def test_raht_orthonormal():
+    pins.check_raht_orthonormal(oracle.lib())
+
+
+def test_raht_constant_and_dedup():
+    pins.check_raht_constant_and_dedup(oracle.lib())
