@@ -652,17 +652,70 @@ def run_preprocess(args):
                       "gpu_launches": 6, "cpu_baseline": cpu}))
 
 
+def run_raht(args):
+    """RAHT of 10 channels (SH DC, opacity, log-scales, rotation) of the scene-scale
+    scene at octree depth 16: voxel means and 48 merge steps.  Measured per call with
+    the scene resident; HBM roofline with the algorithmic bytes (read the channels of
+    every Gaussian, write V - 1 AC vectors)."""
+    import torch
+    from paper_2604_26799_gb300 import mgs
+    dev = torch.device("cuda", 0)
+    w = WORKLOAD
+    a, imp = synth.make_scene(w.n, seed=w.seed)
+    channels = [3, 4, 5, 51, 52, 53, 54, 55, 56, 57]
+    depth = 16
+    ctx = mgs.mgs_create(0)
+    st = torch.cuda.Stream(device=dev)
+    scene = mgs.mgs_scene_create(ctx, torch.from_numpy(a).to(dev), torch.from_numpy(imp).to(dev), stream=st)
+    ac = torch.empty((w.n, len(channels)), dtype=torch.float32, device=dev)
+    times, V = [], 0
+    for step in range(args.warmup + args.steps):
+        with torch.cuda.stream(st):
+            e0, e1 = _events(torch)
+            e0.record(st)
+            _, _, V = mgs.mgs_raht(ctx, scene, channels, depth, ac_out=ac, stream=st)
+            e1.record(st)
+        e1.synchronize()
+        if step >= args.warmup:
+            times.append(e0.elapsed_time(e1))
+    mgs.mgs_scene_destroy(scene)
+    mgs.mgs_destroy(ctx)
+    ms = statistics.mean(times)
+    bytes_alg = w.n * len(channels) * 4 + (V - 1) * len(channels) * 4
+    peaks = measured_peaks()
+    gbs = bytes_alg / (ms * 1e-3) / 1e9
+    cpu = None
+    if not args.no_cpu:
+        import oracle
+        n_s = 1_000_000
+        t0 = time.perf_counter()
+        oracle.raht(a[:n_s], channels, depth)
+        dt = time.perf_counter() - t0
+        cpu = {"value": n_s / dt, "unit": "Gaussians/s", "cores": 1, "kind": "oracle",
+               "sample": f"oracle.raht on the first {n_s} Gaussians (depth {depth}), {dt:.2f} s of one core"}
+    print(json.dumps({"metric": "RAHT Gaussians/s", "value": w.n / (ms * 1e-3), "unit": "Gaussians/s",
+                      "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                      "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": f"RAHT N={w.n}, depth {depth}, {len(channels)} channels",
+                                 "voxels": V},
+                      "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                   "frac": gbs / peaks["hbm_gbs"], "traffic": None,
+                                   "bytes_per_launch": bytes_alg, "peak_source": peaks["source"]},
+                      "cpu_baseline": cpu}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mgs", choices=["mgs", "reference"])
-    ap.add_argument("--workload", default="scene", choices=["scene", "batch", "serve", "large", "preprocess"],
+    ap.add_argument("--workload", default="scene", choices=["scene", "batch", "serve", "large", "preprocess", "raht"],
                     help="scene: the scene-scale search (default); batch: 16 uneven scenes in one "
                          "graph-replayed launch; serve: Poisson job stream through the server; "
                          "large: 6 M Gaussians x 20 ratios x 16 bit-widths; preprocess: Euler "
-                         "replacement and view-independent importance of the scene-scale scene")
+                         "replacement and view-independent importance of the scene-scale scene; "
+                         "raht: RAHT of 10 channels of the scene-scale scene at depth 16")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-loop comparator")
     ap.add_argument("--no-autotune", action="store_true", help="use the default tile shape")
@@ -684,6 +737,8 @@ def main():
         return run_large(args)
     if args.workload == "preprocess":
         return run_preprocess(args)
+    if args.workload == "raht":
+        return run_raht(args)
     return run_gpu(args)
 
 

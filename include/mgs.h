@@ -221,6 +221,30 @@ mgs_status mgs_scene_info(const mgs_scene *scene, int64_t *n, int32_t *n_channel
  * buffers; either may be NULL. */
 mgs_status mgs_scene_morton(const mgs_scene *scene, uint64_t *codes, int32_t *order, void *stream);
 
+/*
+ * RAHT of a resident scene (Sec. III-D "Region Adaptive Hierarchical
+ * Transform").  The Gaussians are voxelised at octree depth `depth` (1..21):
+ * the voxel of a Gaussian is its Morton code >> 3 (21 - depth), with the
+ * scene's Morton reading (per-axis bounding box, 21 bits per axis).  A voxel's
+ * value is the mean of its Gaussians (FP64, summed in Morton order) and its
+ * weight 1.  Step s = 0 .. 3 depth - 1 merges the nodes whose voxel codes
+ * agree above bit s + 1 -- along x, then y, then z, finest level first -- into
+ *   DC = (sqrt(w1) x1 + sqrt(w2) x2) / sqrt(w1 + w2),  weight w1 + w2,
+ *   AC = (sqrt(w1) x2 - sqrt(w2) x1) / sqrt(w1 + w2),
+ * with x1 the node of the lower code; an unpaired node moves up unchanged.
+ *   channels [n_channels]      host: the scene channels to transform (1..64 of them)
+ *   dc_out [n_channels]        host: the final DC coefficient of each channel
+ *   ac_out [(n - 1)][n_channels] device (capacity for the scene's n Gaussians):
+ *                              the V - 1 AC coefficients, step by step, in
+ *                              ascending voxel code within a step
+ *   n_voxels_out               host: V
+ * FP64 arithmetic rounded once to FP32 on output.  Synchronous on `stream`
+ * (one host round trip per merge step); allocates a device workspace of
+ * about (44 + 16 n_channels) n bytes on `stream`.
+ */
+mgs_status mgs_raht(mgs_ctx *ctx, const mgs_scene *scene, const int32_t *channels, int32_t n_channels,
+                    int32_t depth, float *dc_out, float *ac_out, int64_t *n_voxels_out, void *stream);
+
 /* ---- cost table --------------------------------------------------------- */
 
 /* Fill `out` for a scene of n Gaussians with n_channels channels. */

@@ -1,0 +1,317 @@
+// RAHT (Sec. III-D "Region Adaptive Hierarchical Transform") of a resident
+// scene's channels at octree depth d.
+//
+//   k_rh_heads   voxel code of every Morton position (Morton code >> 3(21 - d))
+//                and a flag where a new voxel starts
+//   scan         voxel index of every position (exclusive prefix sum)
+//   k_rh_starts  first Morton position and code of every voxel
+//   k_rh_means   one thread per voxel: FP64 mean of its Gaussians, summed in
+//                Morton order (weight 1)
+//   per step s = 0 .. 3d - 1 (no host round trip; the node count and the AC
+//   offset live in device memory):
+//     k_rh_pairs  flag i when nodes i, i + 1 agree above bit 1 of their codes
+//     scan        pair index of every node and the number of pairs
+//     k_rh_merge  the parent list (code >> 1, slot): a pair merges in place into
+//                 the lower node's slot, DC = (sqrt(w1) x1 + sqrt(w2) x2) / sqrt(w1 + w2),
+//                 weight w1 + w2, and emits AC = (sqrt(w1) x2 - sqrt(w2) x1) / sqrt(w1 + w2)
+//                 at the next AC slot; an unpaired node moves up unchanged.
+//                 Attribute vectors stay in their voxel slots: only pairs touch them.
+//     k_rh_advance  node count -= pairs, AC offset += pairs
+// FP64 throughout, in the order of the formula, rounded once to FP32 on output.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "internal.h"
+
+namespace mgs {
+namespace {
+
+constexpr int kScanBlock = 1024;
+constexpr int kMaxRahtChannels = 64;
+
+__global__ void k_rh_heads(const uint64_t *__restrict__ codes, const int32_t *__restrict__ order, int64_t n,
+                           int shift, uint64_t *__restrict__ vcode, unsigned int *__restrict__ head) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const uint64_t v = codes[order[p]] >> shift;
+    vcode[p] = v;
+    head[p] = (p == 0 || (codes[order[p - 1]] >> shift) != v) ? 1u : 0u;
+}
+
+// ---- exclusive scan of n uint32 flags (three phases) ----
+__global__ void __launch_bounds__(kScanBlock) k_scan_local(const unsigned int *__restrict__ in, int64_t n,
+                                                           unsigned int *__restrict__ out,
+                                                           unsigned int *__restrict__ block_sum) {
+    __shared__ unsigned int s_w[32];
+    const int64_t i = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
+    const unsigned int v = i < n ? in[i] : 0u;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned int t = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += t;
+    }
+    if (lane == 31) s_w[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        unsigned int y = s_w[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned int t = __shfl_up_sync(0xFFFFFFFFu, y, o);
+            if (lane >= o) y += t;
+        }
+        s_w[lane] = y;
+    }
+    __syncthreads();
+    const unsigned int incl = x + (wid > 0 ? s_w[wid - 1] : 0u);
+    if (i < n) out[i] = incl - v;
+    if (threadIdx.x == kScanBlock - 1) block_sum[blockIdx.x] = incl;
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_scan_sums(unsigned int *__restrict__ block_sum, int64_t nb,
+                                                          unsigned long long *__restrict__ total) {
+    __shared__ unsigned int s_w[32];
+    __shared__ unsigned int s_carry;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < nb; base += kScanBlock) {
+        const int64_t i = base + threadIdx.x;
+        const unsigned int v = i < nb ? block_sum[i] : 0u;
+        unsigned int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned int t = __shfl_up_sync(0xFFFFFFFFu, x, o);
+            if (lane >= o) x += t;
+        }
+        if (lane == 31) s_w[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            unsigned int y = s_w[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned int t = __shfl_up_sync(0xFFFFFFFFu, y, o);
+                if (lane >= o) y += t;
+            }
+            s_w[lane] = y;
+        }
+        __syncthreads();
+        const unsigned int incl = x + (wid > 0 ? s_w[wid - 1] : 0u);
+        const unsigned int carry = s_carry;
+        if (i < nb) block_sum[i] = carry + incl - v;   // exclusive offset of block i
+        __syncthreads();
+        if (threadIdx.x == kScanBlock - 1) s_carry = carry + incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = s_carry;
+}
+
+__global__ void k_scan_add(unsigned int *__restrict__ out, int64_t n, const unsigned int *__restrict__ block_off) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] += block_off[i / kScanBlock];
+}
+
+__global__ void k_rh_starts(const unsigned int *__restrict__ head, const unsigned int *__restrict__ vidx,
+                            const uint64_t *__restrict__ vcode, int64_t n, int64_t *__restrict__ start,
+                            uint64_t *__restrict__ key) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n || !head[p]) return;
+    start[vidx[p]] = p;
+    key[vidx[p]] = vcode[p];
+}
+
+__global__ void k_rh_means(const float *__restrict__ slabs, int64_t n, const int64_t *__restrict__ start,
+                           int64_t V, const int32_t *__restrict__ chan, int n_c, double *__restrict__ x,
+                           double *__restrict__ w) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= V) return;
+    const int64_t p0 = start[v], p1 = v + 1 < V ? start[v + 1] : n;
+    for (int k = 0; k < n_c; k++) {
+        const int c = chan[k];
+        const float *col = slabs + (int64_t)(c / kSlabWidth) * n * kSlabWidth + (c % kSlabWidth);
+        double sum = 0.0;
+        for (int64_t p = p0; p < p1; p++) sum = __dadd_rn(sum, (double)col[p * kSlabWidth]);
+        x[v * n_c + k] = __ddiv_rn(sum, (double)(p1 - p0));
+    }
+    w[v] = 1.0;
+}
+
+struct RahtState {
+    long long m;         // nodes in the current list
+    long long ac_base;   // ACs emitted so far
+    unsigned long long pairs;
+};
+
+__global__ void k_rh_pairs(const uint64_t *__restrict__ key, const RahtState *st, int64_t cap,
+                           unsigned int *__restrict__ pf) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= cap) return;
+    const int64_t m = st->m;
+    pf[i] = (i + 1 < m && (key[i] >> 1) == (key[i + 1] >> 1)) ? 1u : 0u;
+}
+
+__global__ void k_rh_merge(const uint64_t *__restrict__ key, const unsigned int *__restrict__ slot,
+                           const RahtState *st, int n_c, const unsigned int *__restrict__ pf,
+                           const unsigned int *__restrict__ pidx, uint64_t *__restrict__ key2,
+                           unsigned int *__restrict__ slot2, double *__restrict__ x, double *__restrict__ w,
+                           float *__restrict__ ac) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t m = st->m;
+    if (i >= m) return;
+    if (i > 0 && pf[i - 1]) return;   // the upper node of a pair: merged by its partner
+    const int64_t j = i - (int64_t)pidx[i];
+    key2[j] = key[i] >> 1;
+    const unsigned int sa = slot[i];
+    slot2[j] = sa;
+    if (!pf[i]) return;
+    const unsigned int sb = slot[i + 1];
+    const double wa = w[sa], wb = w[sb];
+    const double a = __dsqrt_rn(wa), b = __dsqrt_rn(wb), sw = __dsqrt_rn(__dadd_rn(wa, wb));
+    const int64_t out = st->ac_base + (int64_t)pidx[i];
+    for (int k = 0; k < n_c; k++) {
+        const double x1 = x[(int64_t)sa * n_c + k], xb = x[(int64_t)sb * n_c + k];
+        const double dc = __ddiv_rn(__dadd_rn(__dmul_rn(a, x1), __dmul_rn(b, xb)), sw);
+        const double acv = __ddiv_rn(__dsub_rn(__dmul_rn(a, xb), __dmul_rn(b, x1)), sw);
+        x[(int64_t)sa * n_c + k] = dc;
+        ac[out * n_c + k] = (float)acv;
+    }
+    w[sa] = __dadd_rn(wa, wb);
+}
+
+__global__ void k_rh_advance(RahtState *st, const unsigned long long *pairs) {
+    st->m -= (long long)*pairs;
+    st->ac_base += (long long)*pairs;
+}
+
+__global__ void k_rh_init(RahtState *st, const unsigned long long *V, unsigned int *__restrict__ slot, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) slot[i] = (unsigned int)i;
+    if (i == 0) {
+        st->m = (long long)*V;
+        st->ac_base = 0;
+    }
+}
+
+unsigned int blocks_of(int64_t n, int t) { return (unsigned int)((n + t - 1) / t); }
+
+}  // namespace
+}  // namespace mgs
+
+using namespace mgs;
+
+extern "C" mgs_status mgs_raht(mgs_ctx *ctx, const mgs_scene *scene, const int32_t *channels, int32_t n_c,
+                               int32_t depth, float *dc_out, float *ac_out, int64_t *n_voxels_out,
+                               void *stream) {
+    clear_error();
+    if (!ctx || !scene || !channels || !dc_out || !ac_out || !n_voxels_out) {
+        set_error("ctx, scene, channels, dc_out, ac_out and n_voxels_out must be non-NULL");
+        return MGS_ERR_INVALID_ARG;
+    }
+    if (n_c < 1 || n_c > kMaxRahtChannels || depth < 1 || depth > 21) {
+        set_error("n_channels = %d (1..%d) or depth = %d (1..21) out of range", n_c, kMaxRahtChannels, depth);
+        return MGS_ERR_INVALID_ARG;
+    }
+    for (int k = 0; k < n_c; k++)
+        if (channels[k] < 0 || channels[k] >= scene->C) {
+            set_error("channel %d outside the scene's %d channels", channels[k], scene->C);
+            return MGS_ERR_INVALID_ARG;
+        }
+    const int64_t n = scene->n;
+    if (n > ((int64_t)1 << 31)) {
+        set_error("scene of %lld Gaussians exceeds 2^31", (long long)n);
+        return MGS_ERR_INVALID_ARG;
+    }
+    DeviceGuard guard(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const int64_t nb = (n + kScanBlock - 1) / kScanBlock;
+    size_t off = 0;
+    auto take = [&](size_t b) { const size_t o = off; off += al(b); return o; };
+    const size_t o_vcode = take(8 * (size_t)n), o_head = take(4 * (size_t)n), o_idx = take(4 * (size_t)n);
+    const size_t o_bsum = take(4 * (size_t)nb), o_total = take(8), o_start = take(8 * (size_t)n);
+    const size_t o_key0 = take(8 * (size_t)n), o_key1 = take(8 * (size_t)n);
+    const size_t o_slot0 = take(4 * (size_t)n), o_slot1 = take(4 * (size_t)n);
+    const size_t o_w = take(8 * (size_t)n), o_x = take(8 * (size_t)n * n_c);
+    const size_t o_chan = take(4 * (size_t)n_c), o_state = take(sizeof(RahtState));
+    char *ws = nullptr;
+    if (cudaMallocAsync(reinterpret_cast<void **>(&ws), off, st) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("RAHT workspace of %zu bytes could not be allocated", off);
+        return MGS_ERR_OUT_OF_MEMORY;
+    }
+    struct Free {
+        char *p;
+        cudaStream_t s;
+        ~Free() { cudaFreeAsync(p, s); }
+    } free_ws{ws, st};
+    uint64_t *vcode = reinterpret_cast<uint64_t *>(ws + o_vcode);
+    unsigned int *head = reinterpret_cast<unsigned int *>(ws + o_head);
+    unsigned int *idx = reinterpret_cast<unsigned int *>(ws + o_idx);
+    unsigned int *bsum = reinterpret_cast<unsigned int *>(ws + o_bsum);
+    unsigned long long *total = reinterpret_cast<unsigned long long *>(ws + o_total);
+    int64_t *start = reinterpret_cast<int64_t *>(ws + o_start);
+    uint64_t *key[2] = {reinterpret_cast<uint64_t *>(ws + o_key0), reinterpret_cast<uint64_t *>(ws + o_key1)};
+    unsigned int *slot[2] = {reinterpret_cast<unsigned int *>(ws + o_slot0),
+                             reinterpret_cast<unsigned int *>(ws + o_slot1)};
+    double *w = reinterpret_cast<double *>(ws + o_w);
+    double *x = reinterpret_cast<double *>(ws + o_x);
+    int32_t *d_chan = reinterpret_cast<int32_t *>(ws + o_chan);
+    RahtState *rst = reinterpret_cast<RahtState *>(ws + o_state);
+    MGS_CUDA_TRY(cudaMemcpyAsync(d_chan, channels, 4 * (size_t)n_c, cudaMemcpyHostToDevice, st));
+    int64_t launches = 0;
+    // exclusive scan of `len` flags into `out`; the total goes to `total` (device)
+    auto scan = [&](const unsigned int *in, int64_t len, unsigned int *out) {
+        const int64_t blocks = (len + kScanBlock - 1) / kScanBlock;
+        k_scan_local<<<(unsigned int)blocks, kScanBlock, 0, st>>>(in, len, out, bsum);
+        k_scan_sums<<<1, kScanBlock, 0, st>>>(bsum, blocks, total);
+        k_scan_add<<<blocks_of(len, 256), 256, 0, st>>>(out, len, bsum);
+        launches += 3;
+    };
+    // voxels and their means
+    k_rh_heads<<<blocks_of(n, 256), 256, 0, st>>>(scene->d_codes, scene->d_order, n, 3 * (21 - depth), vcode,
+                                                  head);
+    launches++;
+    scan(head, n, idx);
+    unsigned long long V = 0;
+    MGS_CUDA_TRY(cudaMemcpyAsync(&V, total, 8, cudaMemcpyDeviceToHost, st));
+    MGS_CUDA_TRY(cudaStreamSynchronize(st));
+    k_rh_starts<<<blocks_of(n, 256), 256, 0, st>>>(head, idx, vcode, n, start, key[0]);
+    k_rh_means<<<blocks_of((int64_t)V, 256), 256, 0, st>>>(scene->d_slabs, n, start, (int64_t)V, d_chan, n_c, x,
+                                                           w);
+    k_rh_init<<<blocks_of((int64_t)V, 256), 256, 0, st>>>(rst, total, slot[0], (int64_t)V);
+    launches += 3;
+    MGS_CUDA_TRY(cudaGetLastError());
+    // merges, finest level first; every step works on the device-resident node count
+    const int64_t cap = (int64_t)V;
+    int cur = 0;
+    for (int s = 0; s < 3 * depth && V > 1; s++) {
+        k_rh_pairs<<<blocks_of(cap, 256), 256, 0, st>>>(key[cur], rst, cap, head);
+        scan(head, cap, idx);
+        k_rh_merge<<<blocks_of(cap, 256), 256, 0, st>>>(key[cur], slot[cur], rst, n_c, head, idx, key[cur ^ 1],
+                                                        slot[cur ^ 1], x, w, ac_out);
+        k_rh_advance<<<1, 1, 0, st>>>(rst, total);
+        launches += 3;
+        cur ^= 1;
+    }
+    MGS_CUDA_TRY(cudaGetLastError());
+    count_launches(launches);
+    RahtState h{};
+    MGS_CUDA_TRY(cudaMemcpyAsync(&h, rst, sizeof(RahtState), cudaMemcpyDeviceToHost, st));
+    unsigned int root = 0;
+    MGS_CUDA_TRY(cudaMemcpyAsync(&root, slot[cur], 4, cudaMemcpyDeviceToHost, st));
+    MGS_CUDA_TRY(cudaStreamSynchronize(st));
+    if (V > 1 && (h.m != 1 || h.ac_base != (long long)V - 1)) {
+        set_error("RAHT ended with %lld nodes and %lld ACs for %llu voxels", h.m, h.ac_base, V);
+        return MGS_ERR_CUDA;
+    }
+    std::vector<double> dc(n_c);
+    MGS_CUDA_TRY(cudaMemcpyAsync(dc.data(), x + (size_t)(V > 1 ? root : 0) * n_c, 8 * (size_t)n_c,
+                                 cudaMemcpyDeviceToHost, st));
+    MGS_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int k = 0; k < n_c; k++) dc_out[k] = (float)dc[k];
+    *n_voxels_out = (int64_t)V;
+    return MGS_OK;
+}

@@ -124,6 +124,7 @@ _SIGS = {
                          ctypes.POINTER(mgs_solution)],
     "mgs_solve_budgets": [_P, ctypes.POINTER(mgs_table_layout), ctypes.POINTER(mgs_grid),
                           ctypes.c_int32, _P, ctypes.POINTER(mgs_solve_opts), _P],
+    "mgs_raht": [_P, _P, _P, ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P],
     "mgs_preprocess": [_P, _P, _P, ctypes.c_int64, ctypes.c_double, _P, _P, _P, _P],
     "mgs_solve_budgets_device": [_P, _P, ctypes.POINTER(mgs_table_layout), ctypes.POINTER(mgs_grid),
                                  ctypes.c_int32, _P, ctypes.POINTER(mgs_solve_opts), _P, _P],
@@ -463,3 +464,18 @@ def mgs_preprocess(ctx: int, attrs, view_importance, beta: float, attrs_out=None
     _check(lib().mgs_preprocess(ctx, _ptr(attrs), _ptr(view_importance), n, float(beta), _ptr(attrs_out),
                                 _ptr(importance_out), ctypes.byref(vq), _stream(stream)))
     return attrs_out, importance_out, vq.value
+
+
+def mgs_raht(ctx: int, scene: int, channels, depth: int, ac_out=None, stream=None):
+    """RAHT of a resident scene's channels: (DC [n_c] numpy, AC [V - 1, n_c] device tensor, V)."""
+    import torch
+    n, _, _ = mgs_scene_info(scene)
+    ch = np.ascontiguousarray(channels, dtype=np.int32)
+    nc = int(ch.shape[0])
+    if ac_out is None:
+        ac_out = torch.empty((max(n - 1, 1), nc), dtype=torch.float32, device="cuda")
+    dc = np.empty(nc, dtype=np.float32)
+    nv = ctypes.c_int64()
+    _check(lib().mgs_raht(ctx, scene, ch.ctypes.data, nc, int(depth), dc.ctypes.data, _ptr(ac_out),
+                          ctypes.byref(nv), _stream(stream)))
+    return dc, ac_out[:nv.value - 1], nv.value
