@@ -228,9 +228,10 @@ mgs_status mgs_scene_morton(const mgs_scene *scene, uint64_t *codes, int32_t *or
  * scene's Morton reading (per-axis bounding box, 21 bits per axis).  A voxel's
  * value is the mean of its Gaussians (FP64, summed in Morton order) and its
  * weight 1.  Step s = 0 .. 3 depth - 1 merges the nodes whose voxel codes
- * agree above bit s + 1 -- along x, then y, then z, finest level first -- into
- *   DC = (sqrt(w1) x1 + sqrt(w2) x2) / sqrt(w1 + w2),  weight w1 + w2,
- *   AC = (sqrt(w1) x2 - sqrt(w2) x1) / sqrt(w1 + w2),
+ * agree above bit s + 1 -- along x, then y, then z, finest level first -- by
+ * the transform T with entries t1 = sqrt(w1) / sqrt(w1 + w2) and
+ * t2 = sqrt(w2) / sqrt(w1 + w2):
+ *   DC = t1 x1 + t2 x2,  weight w1 + w2,     AC = t1 x2 - t2 x1,
  * with x1 the node of the lower code; an unpaired node moves up unchanged.
  *   channels [n_channels]      host: the scene channels to transform (1..64 of them)
  *   dc_out [n_channels]        host: the final DC coefficient of each channel

@@ -58,10 +58,11 @@
  *     (so the x, y, z bits of the voxel code are those of the Morton code);
  *     a voxel's attribute is the FP64 mean of its Gaussians, summed in Morton
  *     order, and its weight is 1; step s = 0 .. 3d - 1 merges the nodes whose
- *     codes agree above bit s + 1 (the lower node first: x1, w1) into
- *     DC = (sqrt(w1) x1 + sqrt(w2) x2) / sqrt(w1 + w2) and
- *     AC = (sqrt(w1) x2 - sqrt(w2) x1) / sqrt(w1 + w2), weight w1 + w2; an
- *     unpaired node passes up unchanged.  ACs are listed step by step, in
+ *     codes agree above bit s + 1 (the lower node first: x1, w1) by the
+ *     printed T, whose entries t1 = sqrt(w1) / sqrt(w1 + w2) and
+ *     t2 = sqrt(w2) / sqrt(w1 + w2) are formed once per pair:
+ *     DC = t1 x1 + t2 x2, AC = t1 x2 - t2 x1, weight w1 + w2; an unpaired
+ *     node passes up unchanged.  ACs are listed step by step, in
  *     ascending code within a step.
  */
 #include <math.h>
@@ -515,7 +516,7 @@ int oracle_raht(const float *attrs, int64_t n, int32_t n_channels, const int32_t
         for (int32_t k = 0; k < n_c; k++) {
             double sum = 0.0;
             for (int64_t t = p; t < q; t++) sum += (double)attrs[order[t] * n_channels + chan[k]];
-            x[m * n_c + k] = sum / (double)(q - p);
+            x[m * n_c + k] = q - p > 1 ? sum / (double)(q - p) : sum;
         }
         key[m] = vc;
         w[m] = 1;
@@ -529,12 +530,14 @@ int oracle_raht(const float *attrs, int64_t n, int32_t n_channels, const int32_t
         int64_t out = 0;
         for (int64_t i = 0; i < m;) {
             if (i + 1 < m && (key[i] >> 1) == (key[i + 1] >> 1)) {
+                /* the entries of T: sqrt(w1) / sqrt(w1 + w2) and sqrt(w2) / sqrt(w1 + w2) */
                 double w1 = (double)w[i], w2 = (double)w[i + 1];
-                double a = sqrt(w1), b = sqrt(w2), sw = sqrt(w1 + w2);
+                double sw = sqrt(w1 + w2);
+                double t1 = sqrt(w1) / sw, t2 = sqrt(w2) / sw;
                 for (int32_t k = 0; k < n_c; k++) {
                     double x1 = x[i * n_c + k], x2 = x[(i + 1) * n_c + k];
-                    double dc = (a * x1 + b * x2) / sw;
-                    double ac = (a * x2 - b * x1) / sw;
+                    double dc = t1 * x1 + t2 * x2;
+                    double ac = t1 * x2 - t2 * x1;
                     ac_out[n_ac * n_c + k] = ac;
                     x[out * n_c + k] = dc;
                 }

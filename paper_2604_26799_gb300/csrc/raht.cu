@@ -7,16 +7,19 @@
 //   k_rh_starts  first Morton position and code of every voxel
 //   k_rh_means   one thread per voxel: FP64 mean of its Gaussians, summed in
 //                Morton order (weight 1)
-//   per step s = 0 .. 3d - 1 (no host round trip; the node count and the AC
-//   offset live in device memory):
+//   per step s = 0 .. 3d - 1 (the node count, the AC offset, the current list
+//   and the pending level live in device memory; the host reads them once per
+//   octree level to size the grids):
 //     k_rh_pairs  flag i when nodes i, i + 1 agree above bit 1 of their codes
 //     scan        pair index of every node and the number of pairs
 //     k_rh_merge  the parent list (code >> 1, slot): a pair merges in place into
-//                 the lower node's slot, DC = (sqrt(w1) x1 + sqrt(w2) x2) / sqrt(w1 + w2),
-//                 weight w1 + w2, and emits AC = (sqrt(w1) x2 - sqrt(w2) x1) / sqrt(w1 + w2)
-//                 at the next AC slot; an unpaired node moves up unchanged.
+//                 the lower node's slot by the printed T, with its entries
+//                 t1 = sqrt(w1) / sqrt(w1 + w2), t2 = sqrt(w2) / sqrt(w1 + w2) formed
+//                 once per pair: DC = t1 x1 + t2 x2, weight w1 + w2, and it emits
+//                 AC = t1 x2 - t2 x1 at the next AC slot; an unpaired node moves up.
 //                 Attribute vectors stay in their voxel slots: only pairs touch them.
-//     k_rh_advance  node count -= pairs, AC offset += pairs
+//     k_rh_advance  node count -= pairs, AC offset += pairs, swap the lists; a
+//                 step without pairs only raises the pending level
 // FP64 throughout, in the order of the formula, rounded once to FP32 on output.
 #include <cuda_runtime.h>
 
@@ -134,7 +137,7 @@ __global__ void k_rh_means(const float *__restrict__ slabs, int64_t n, const int
         const float *col = slabs + (int64_t)(c / kSlabWidth) * n * kSlabWidth + (c % kSlabWidth);
         double sum = 0.0;
         for (int64_t p = p0; p < p1; p++) sum = __dadd_rn(sum, (double)col[p * kSlabWidth]);
-        x[v * n_c + k] = __ddiv_rn(sum, (double)(p1 - p0));
+        x[v * n_c + k] = p1 - p0 > 1 ? __ddiv_rn(sum, (double)(p1 - p0)) : sum;   // x / 1 = x
     }
     w[v] = 1.0;
 }
@@ -142,48 +145,84 @@ __global__ void k_rh_means(const float *__restrict__ slabs, int64_t n, const int
 struct RahtState {
     long long m;         // nodes in the current list
     long long ac_base;   // ACs emitted so far
-    unsigned long long pairs;
+    int cur;             // which of the two lists is current
+    int pending;         // levels not yet applied to the current list's codes
 };
 
-__global__ void k_rh_pairs(const uint64_t *__restrict__ key, const RahtState *st, int64_t cap,
-                           unsigned int *__restrict__ pf) {
+// Steps whose list has no pair change nothing but the level: they only raise
+// `pending`, and the codes are compared (and shifted when the list is next
+// rewritten) by pending + 1 bits.
+__global__ void k_rh_pairs(const uint64_t *__restrict__ key0, const uint64_t *__restrict__ key1,
+                           const RahtState *st, int64_t cap, unsigned int *__restrict__ pf) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= cap) return;
     const int64_t m = st->m;
-    pf[i] = (i + 1 < m && (key[i] >> 1) == (key[i + 1] >> 1)) ? 1u : 0u;
+    const uint64_t *key = st->cur ? key1 : key0;
+    const int sh = st->pending + 1;
+    pf[i] = (i + 1 < m && (key[i] >> sh) == (key[i + 1] >> sh)) ? 1u : 0u;
 }
 
-__global__ void k_rh_merge(const uint64_t *__restrict__ key, const unsigned int *__restrict__ slot,
-                           const RahtState *st, int n_c, const unsigned int *__restrict__ pf,
-                           const unsigned int *__restrict__ pidx, uint64_t *__restrict__ key2,
-                           unsigned int *__restrict__ slot2, double *__restrict__ x, double *__restrict__ w,
-                           float *__restrict__ ac) {
+__global__ void k_rh_merge(uint64_t *__restrict__ key0, uint64_t *__restrict__ key1,
+                           unsigned int *__restrict__ slot0, unsigned int *__restrict__ slot1,
+                           const RahtState *st, const unsigned long long *pairs, int n_c,
+                           const unsigned int *__restrict__ pf, const unsigned int *__restrict__ pidx,
+                           double *__restrict__ x, double *__restrict__ w, float *__restrict__ ac) {
+    if (*pairs == 0) return;   // nothing to merge at this level
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t m = st->m;
     if (i >= m) return;
     if (i > 0 && pf[i - 1]) return;   // the upper node of a pair: merged by its partner
+    const bool c = st->cur;
+    const uint64_t *key = c ? key1 : key0;
+    const unsigned int *slot = c ? slot1 : slot0;
+    uint64_t *key2 = c ? key0 : key1;
+    unsigned int *slot2 = c ? slot0 : slot1;
     const int64_t j = i - (int64_t)pidx[i];
-    key2[j] = key[i] >> 1;
+    key2[j] = key[i] >> (st->pending + 1);
     const unsigned int sa = slot[i];
     slot2[j] = sa;
     if (!pf[i]) return;
     const unsigned int sb = slot[i + 1];
     const double wa = w[sa], wb = w[sb];
-    const double a = __dsqrt_rn(wa), b = __dsqrt_rn(wb), sw = __dsqrt_rn(__dadd_rn(wa, wb));
+    // the entries of T, once per pair
+    const double sw = __dsqrt_rn(__dadd_rn(wa, wb));
+    const double t1 = __ddiv_rn(__dsqrt_rn(wa), sw), t2 = __ddiv_rn(__dsqrt_rn(wb), sw);
     const int64_t out = st->ac_base + (int64_t)pidx[i];
-    for (int k = 0; k < n_c; k++) {
-        const double x1 = x[(int64_t)sa * n_c + k], xb = x[(int64_t)sb * n_c + k];
-        const double dc = __ddiv_rn(__dadd_rn(__dmul_rn(a, x1), __dmul_rn(b, xb)), sw);
-        const double acv = __ddiv_rn(__dsub_rn(__dmul_rn(a, xb), __dmul_rn(b, x1)), sw);
-        x[(int64_t)sa * n_c + k] = dc;
-        ac[out * n_c + k] = (float)acv;
+    double *xa = x + (int64_t)sa * n_c;
+    const double *xbp = x + (int64_t)sb * n_c;
+    float *acp = ac + out * n_c;
+    int k = 0;
+    for (; k + 4 <= n_c; k += 4) {   // four channels at a time: independent loads in flight
+        double x1[4], x2[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            x1[u] = xa[k + u];
+            x2[u] = xbp[k + u];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            xa[k + u] = __dadd_rn(__dmul_rn(t1, x1[u]), __dmul_rn(t2, x2[u]));
+            acp[k + u] = (float)__dsub_rn(__dmul_rn(t1, x2[u]), __dmul_rn(t2, x1[u]));
+        }
+    }
+    for (; k < n_c; k++) {
+        const double x1 = xa[k], x2 = xbp[k];
+        xa[k] = __dadd_rn(__dmul_rn(t1, x1), __dmul_rn(t2, x2));
+        acp[k] = (float)__dsub_rn(__dmul_rn(t1, x2), __dmul_rn(t2, x1));
     }
     w[sa] = __dadd_rn(wa, wb);
 }
 
 __global__ void k_rh_advance(RahtState *st, const unsigned long long *pairs) {
-    st->m -= (long long)*pairs;
-    st->ac_base += (long long)*pairs;
+    const long long p = (long long)*pairs;
+    if (p == 0) {
+        st->pending++;
+        return;
+    }
+    st->m -= p;
+    st->ac_base += p;
+    st->cur ^= 1;
+    st->pending = 0;
 }
 
 __global__ void k_rh_init(RahtState *st, const unsigned long long *V, unsigned int *__restrict__ slot, int64_t n) {
@@ -192,6 +231,8 @@ __global__ void k_rh_init(RahtState *st, const unsigned long long *V, unsigned i
     if (i == 0) {
         st->m = (long long)*V;
         st->ac_base = 0;
+        st->cur = 0;
+        st->pending = 0;
     }
 }
 
@@ -284,24 +325,30 @@ extern "C" mgs_status mgs_raht(mgs_ctx *ctx, const mgs_scene *scene, const int32
     k_rh_init<<<blocks_of((int64_t)V, 256), 256, 0, st>>>(rst, total, slot[0], (int64_t)V);
     launches += 3;
     MGS_CUDA_TRY(cudaGetLastError());
-    // merges, finest level first; every step works on the device-resident node count
-    const int64_t cap = (int64_t)V;
-    int cur = 0;
-    for (int s = 0; s < 3 * depth && V > 1; s++) {
-        k_rh_pairs<<<blocks_of(cap, 256), 256, 0, st>>>(key[cur], rst, cap, head);
+    // merges, finest level first, on the device-resident node list; once per
+    // octree level (three steps) the host reads the node count to size the grids
+    int64_t cap = (int64_t)V;
+    for (int s = 0; s < 3 * depth && V > 1 && cap > 1; s++) {
+        k_rh_pairs<<<blocks_of(cap, 256), 256, 0, st>>>(key[0], key[1], rst, cap, head);
         scan(head, cap, idx);
-        k_rh_merge<<<blocks_of(cap, 256), 256, 0, st>>>(key[cur], slot[cur], rst, n_c, head, idx, key[cur ^ 1],
-                                                        slot[cur ^ 1], x, w, ac_out);
+        k_rh_merge<<<blocks_of(cap, 256), 256, 0, st>>>(key[0], key[1], slot[0], slot[1], rst, total, n_c, head,
+                                                        idx, x, w, ac_out);
         k_rh_advance<<<1, 1, 0, st>>>(rst, total);
         launches += 3;
-        cur ^= 1;
+        if (s % 3 == 2) {
+            RahtState h{};
+            MGS_CUDA_TRY(cudaMemcpyAsync(&h, rst, sizeof(RahtState), cudaMemcpyDeviceToHost, st));
+            MGS_CUDA_TRY(cudaStreamSynchronize(st));
+            cap = h.m;
+        }
     }
     MGS_CUDA_TRY(cudaGetLastError());
     count_launches(launches);
     RahtState h{};
     MGS_CUDA_TRY(cudaMemcpyAsync(&h, rst, sizeof(RahtState), cudaMemcpyDeviceToHost, st));
+    MGS_CUDA_TRY(cudaStreamSynchronize(st));
     unsigned int root = 0;
-    MGS_CUDA_TRY(cudaMemcpyAsync(&root, slot[cur], 4, cudaMemcpyDeviceToHost, st));
+    MGS_CUDA_TRY(cudaMemcpyAsync(&root, slot[h.cur], 4, cudaMemcpyDeviceToHost, st));
     MGS_CUDA_TRY(cudaStreamSynchronize(st));
     if (V > 1 && (h.m != 1 || h.ac_base != (long long)V - 1)) {
         set_error("RAHT ended with %lld nodes and %lld ACs for %llu voxels", h.m, h.ac_base, V);

@@ -37,10 +37,11 @@ MUTANTS = {
     "quantile_index": ("double vq = sorted[(9 * (n - 1)) / 10];", "double vq = sorted[(9 * n) / 10];"),
     "volume_not_clipped": ("double vn = vq > 0.0 ? fmin(vol[i] / vq, 1.0) : 1.0;",
                            "double vn = vq > 0.0 ? vol[i] / vq : 1.0;"),
-    "raht_ac_sign": ("double ac = (a * x2 - b * x1) / sw;", "double ac = (a * x1 - b * x2) / sw;"),
-    "raht_weights_not_rooted": ("double a = sqrt(w1), b = sqrt(w2), sw = sqrt(w1 + w2);",
-                                "double a = w1, b = w2, sw = sqrt(w1 + w2);"),
-    "raht_mean_not_divided": ("x[m * n_c + k] = sum / (double)(q - p);", "x[m * n_c + k] = sum;"),
+    "raht_ac_sign": ("double ac = t1 * x2 - t2 * x1;", "double ac = t1 * x1 - t2 * x2;"),
+    "raht_weights_not_rooted": ("double t1 = sqrt(w1) / sw, t2 = sqrt(w2) / sw;",
+                                "double t1 = w1 / sw, t2 = w2 / sw;"),
+    "raht_mean_not_divided": ("x[m * n_c + k] = q - p > 1 ? sum / (double)(q - p) : sum;",
+                              "x[m * n_c + k] = sum;"),
     "raht_weight_not_summed": ("w[out] = w[i] + w[i + 1];", "w[out] = w[i];"),
 }
 
