@@ -695,7 +695,7 @@ def run_raht(args):
                "sample": f"oracle.raht on the first {n_s} Gaussians (depth {depth}), {dt:.2f} s of one core"}
     print(json.dumps({"metric": "RAHT Gaussians/s", "value": w.n / (ms * 1e-3), "unit": "Gaussians/s",
                       "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-                      "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+                      "higher_is_better": True, "dtype": "f32", "data": "synthetic",
                       "config": {"workload": f"RAHT N={w.n}, depth {depth}, {len(channels)} channels",
                                  "voxels": V},
                       "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",

@@ -226,8 +226,7 @@ mgs_status mgs_scene_morton(const mgs_scene *scene, uint64_t *codes, int32_t *or
  * Transform").  The Gaussians are voxelised at octree depth `depth` (1..21):
  * the voxel of a Gaussian is its Morton code >> 3 (21 - depth), with the
  * scene's Morton reading (per-axis bounding box, 21 bits per axis).  A voxel's
- * value is the mean of its Gaussians (FP64, summed in Morton order) and its
- * weight 1.  Step s = 0 .. 3 depth - 1 merges the nodes whose voxel codes
+ * value is the mean of its Gaussians (summed in Morton order) and its weight 1.  Step s = 0 .. 3 depth - 1 merges the nodes whose voxel codes
  * agree above bit s + 1 -- along x, then y, then z, finest level first -- by
  * the transform T with entries t1 = sqrt(w1) / sqrt(w1 + w2) and
  * t2 = sqrt(w2) / sqrt(w1 + w2):
@@ -239,9 +238,10 @@ mgs_status mgs_scene_morton(const mgs_scene *scene, uint64_t *codes, int32_t *or
  *                              the V - 1 AC coefficients, step by step, in
  *                              ascending voxel code within a step
  *   n_voxels_out               host: V
- * FP64 arithmetic rounded once to FP32 on output.  Synchronous on `stream`
- * (one host round trip per merge step); allocates a device workspace of
- * about (44 + 16 n_channels) n bytes on `stream`.
+ * FP32 arithmetic (each merge is an orthonormal rotation: a coefficient's
+ * error stays within a few ulp per level of sqrt(w) |x| of its node).
+ * Synchronous on `stream` (one host round trip per octree level); allocates
+ * a device workspace of about (56 + 4 n_channels) n bytes on `stream`.
  */
 mgs_status mgs_raht(mgs_ctx *ctx, const mgs_scene *scene, const int32_t *channels, int32_t n_channels,
                     int32_t depth, float *dc_out, float *ac_out, int64_t *n_voxels_out, void *stream);

@@ -489,9 +489,10 @@ int oracle_preprocess(const float *attrs, int64_t n, int32_t n_channels, const f
 /* ------------------------------------------------------------------------ */
 
 /* attrs [n][n_channels]; chan [n_c] the transformed channels; depth 1..21.
- * dc_out [n_c]; ac_out [(n - 1)][n_c] (capacity); *n_vox_out = V.  FP64. */
+ * dc_out [n_c]; ac_out [(n - 1)][n_c] (capacity); ac_w_out [(n - 1)] (may be
+ * NULL) the weight w1 + w2 of each AC's merge; *n_vox_out = V.  FP64. */
 int oracle_raht(const float *attrs, int64_t n, int32_t n_channels, const int32_t *chan, int32_t n_c,
-                int32_t depth, double *dc_out, double *ac_out, int64_t *n_vox_out) {
+                int32_t depth, double *dc_out, double *ac_out, int64_t *ac_w_out, int64_t *n_vox_out) {
     if (n < 1 || n_c < 1 || depth < 1 || depth > 21) return ORACLE_ERR_ARG;
     for (int32_t k = 0; k < n_c; k++)
         if (chan[k] < 0 || chan[k] >= n_channels) return ORACLE_ERR_ARG;
@@ -541,6 +542,7 @@ int oracle_raht(const float *attrs, int64_t n, int32_t n_channels, const int32_t
                     ac_out[n_ac * n_c + k] = ac;
                     x[out * n_c + k] = dc;
                 }
+                if (ac_w_out) ac_w_out[n_ac] = w[i] + w[i + 1];
                 n_ac++;
                 w[out] = w[i] + w[i + 1];
                 key[out] = key[i] >> 1;

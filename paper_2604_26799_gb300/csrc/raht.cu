@@ -5,7 +5,7 @@
 //                and a flag where a new voxel starts
 //   scan         voxel index of every position (exclusive prefix sum)
 //   k_rh_starts  first Morton position and code of every voxel
-//   k_rh_means   one thread per voxel: FP64 mean of its Gaussians, summed in
+//   k_rh_means   one thread per voxel: mean of its Gaussians, summed in
 //                Morton order (weight 1)
 //   per step s = 0 .. 3d - 1 (the node count, the AC offset, the current list
 //   and the pending level live in device memory; the host reads them once per
@@ -20,7 +20,11 @@
 //                 Attribute vectors stay in their voxel slots: only pairs touch them.
 //     k_rh_advance  node count -= pairs, AC offset += pairs, swap the lists; a
 //                 step without pairs only raises the pending level
-// FP64 throughout, in the order of the formula, rounded once to FP32 on output.
+// FP32 arithmetic with integer weights.  (An FP64 version matched the FP64
+// oracle bit for bit, but GB300's FP64 pipe ran 73-87% busy and bounded it:
+// 11.4 ms for 5.27 M voxels.)  Every merge is an orthonormal rotation, so the
+// FP32 error of a coefficient stays within a few ulp per level of the size
+// sqrt(w) * |x| of the node it comes from.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -127,19 +131,19 @@ __global__ void k_rh_starts(const unsigned int *__restrict__ head, const unsigne
 }
 
 __global__ void k_rh_means(const float *__restrict__ slabs, int64_t n, const int64_t *__restrict__ start,
-                           int64_t V, const int32_t *__restrict__ chan, int n_c, double *__restrict__ x,
-                           double *__restrict__ w) {
+                           int64_t V, const int32_t *__restrict__ chan, int n_c, float *__restrict__ x,
+                           unsigned int *__restrict__ w) {
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= V) return;
     const int64_t p0 = start[v], p1 = v + 1 < V ? start[v + 1] : n;
     for (int k = 0; k < n_c; k++) {
         const int c = chan[k];
         const float *col = slabs + (int64_t)(c / kSlabWidth) * n * kSlabWidth + (c % kSlabWidth);
-        double sum = 0.0;
-        for (int64_t p = p0; p < p1; p++) sum = __dadd_rn(sum, (double)col[p * kSlabWidth]);
-        x[v * n_c + k] = p1 - p0 > 1 ? __ddiv_rn(sum, (double)(p1 - p0)) : sum;   // x / 1 = x
+        float sum = 0.0f;
+        for (int64_t p = p0; p < p1; p++) sum = __fadd_rn(sum, col[p * kSlabWidth]);
+        x[v * n_c + k] = p1 - p0 > 1 ? __fdiv_rn(sum, (float)(p1 - p0)) : sum;
     }
-    w[v] = 1.0;
+    w[v] = 1u;
 }
 
 struct RahtState {
@@ -166,7 +170,7 @@ __global__ void k_rh_merge(uint64_t *__restrict__ key0, uint64_t *__restrict__ k
                            unsigned int *__restrict__ slot0, unsigned int *__restrict__ slot1,
                            const RahtState *st, const unsigned long long *pairs, int n_c,
                            const unsigned int *__restrict__ pf, const unsigned int *__restrict__ pidx,
-                           double *__restrict__ x, double *__restrict__ w, float *__restrict__ ac) {
+                           float *__restrict__ x, unsigned int *__restrict__ w, float *__restrict__ ac) {
     if (*pairs == 0) return;   // nothing to merge at this level
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t m = st->m;
@@ -183,17 +187,17 @@ __global__ void k_rh_merge(uint64_t *__restrict__ key0, uint64_t *__restrict__ k
     slot2[j] = sa;
     if (!pf[i]) return;
     const unsigned int sb = slot[i + 1];
-    const double wa = w[sa], wb = w[sb];
+    const unsigned int wa = w[sa], wb = w[sb];
     // the entries of T, once per pair
-    const double sw = __dsqrt_rn(__dadd_rn(wa, wb));
-    const double t1 = __ddiv_rn(__dsqrt_rn(wa), sw), t2 = __ddiv_rn(__dsqrt_rn(wb), sw);
+    const float sw = __fsqrt_rn((float)(wa + wb));
+    const float t1 = __fdiv_rn(__fsqrt_rn((float)wa), sw), t2 = __fdiv_rn(__fsqrt_rn((float)wb), sw);
     const int64_t out = st->ac_base + (int64_t)pidx[i];
-    double *xa = x + (int64_t)sa * n_c;
-    const double *xbp = x + (int64_t)sb * n_c;
+    float *xa = x + (int64_t)sa * n_c;
+    const float *xbp = x + (int64_t)sb * n_c;
     float *acp = ac + out * n_c;
     int k = 0;
     for (; k + 4 <= n_c; k += 4) {   // four channels at a time: independent loads in flight
-        double x1[4], x2[4];
+        float x1[4], x2[4];
 #pragma unroll
         for (int u = 0; u < 4; u++) {
             x1[u] = xa[k + u];
@@ -201,16 +205,16 @@ __global__ void k_rh_merge(uint64_t *__restrict__ key0, uint64_t *__restrict__ k
         }
 #pragma unroll
         for (int u = 0; u < 4; u++) {
-            xa[k + u] = __dadd_rn(__dmul_rn(t1, x1[u]), __dmul_rn(t2, x2[u]));
-            acp[k + u] = (float)__dsub_rn(__dmul_rn(t1, x2[u]), __dmul_rn(t2, x1[u]));
+            xa[k + u] = __fadd_rn(__fmul_rn(t1, x1[u]), __fmul_rn(t2, x2[u]));
+            acp[k + u] = __fsub_rn(__fmul_rn(t1, x2[u]), __fmul_rn(t2, x1[u]));
         }
     }
     for (; k < n_c; k++) {
-        const double x1 = xa[k], x2 = xbp[k];
-        xa[k] = __dadd_rn(__dmul_rn(t1, x1), __dmul_rn(t2, x2));
-        acp[k] = (float)__dsub_rn(__dmul_rn(t1, x2), __dmul_rn(t2, x1));
+        const float x1 = xa[k], x2 = xbp[k];
+        xa[k] = __fadd_rn(__fmul_rn(t1, x1), __fmul_rn(t2, x2));
+        acp[k] = __fsub_rn(__fmul_rn(t1, x2), __fmul_rn(t2, x1));
     }
-    w[sa] = __dadd_rn(wa, wb);
+    w[sa] = wa + wb;
 }
 
 __global__ void k_rh_advance(RahtState *st, const unsigned long long *pairs) {
@@ -275,7 +279,7 @@ extern "C" mgs_status mgs_raht(mgs_ctx *ctx, const mgs_scene *scene, const int32
     const size_t o_bsum = take(4 * (size_t)nb), o_total = take(8), o_start = take(8 * (size_t)n);
     const size_t o_key0 = take(8 * (size_t)n), o_key1 = take(8 * (size_t)n);
     const size_t o_slot0 = take(4 * (size_t)n), o_slot1 = take(4 * (size_t)n);
-    const size_t o_w = take(8 * (size_t)n), o_x = take(8 * (size_t)n * n_c);
+    const size_t o_w = take(4 * (size_t)n), o_x = take(4 * (size_t)n * n_c);
     const size_t o_chan = take(4 * (size_t)n_c), o_state = take(sizeof(RahtState));
     char *ws = nullptr;
     if (cudaMallocAsync(reinterpret_cast<void **>(&ws), off, st) != cudaSuccess) {
@@ -297,8 +301,8 @@ extern "C" mgs_status mgs_raht(mgs_ctx *ctx, const mgs_scene *scene, const int32
     uint64_t *key[2] = {reinterpret_cast<uint64_t *>(ws + o_key0), reinterpret_cast<uint64_t *>(ws + o_key1)};
     unsigned int *slot[2] = {reinterpret_cast<unsigned int *>(ws + o_slot0),
                              reinterpret_cast<unsigned int *>(ws + o_slot1)};
-    double *w = reinterpret_cast<double *>(ws + o_w);
-    double *x = reinterpret_cast<double *>(ws + o_x);
+    unsigned int *w = reinterpret_cast<unsigned int *>(ws + o_w);
+    float *x = reinterpret_cast<float *>(ws + o_x);
     int32_t *d_chan = reinterpret_cast<int32_t *>(ws + o_chan);
     RahtState *rst = reinterpret_cast<RahtState *>(ws + o_state);
     MGS_CUDA_TRY(cudaMemcpyAsync(d_chan, channels, 4 * (size_t)n_c, cudaMemcpyHostToDevice, st));
@@ -354,11 +358,9 @@ extern "C" mgs_status mgs_raht(mgs_ctx *ctx, const mgs_scene *scene, const int32
         set_error("RAHT ended with %lld nodes and %lld ACs for %llu voxels", h.m, h.ac_base, V);
         return MGS_ERR_CUDA;
     }
-    std::vector<double> dc(n_c);
-    MGS_CUDA_TRY(cudaMemcpyAsync(dc.data(), x + (size_t)(V > 1 ? root : 0) * n_c, 8 * (size_t)n_c,
+    MGS_CUDA_TRY(cudaMemcpyAsync(dc_out, x + (size_t)(V > 1 ? root : 0) * n_c, 4 * (size_t)n_c,
                                  cudaMemcpyDeviceToHost, st));
     MGS_CUDA_TRY(cudaStreamSynchronize(st));
-    for (int k = 0; k < n_c; k++) dc_out[k] = (float)dc[k];
     *n_voxels_out = (int64_t)V;
     return MGS_OK;
 }
