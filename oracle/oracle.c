@@ -489,11 +489,16 @@ int oracle_preprocess(const float *attrs, int64_t n, int32_t n_channels, const f
 /* ------------------------------------------------------------------------ */
 
 /* attrs [n][n_channels]; chan [n_c] the transformed channels; depth 1..21.
- * dc_out [n_c]; ac_out [(n - 1)][n_c] (capacity); ac_w_out [(n - 1)] (may be
- * NULL) the weight w1 + w2 of each AC's merge; *n_vox_out = V.  FP64. */
+ * keep = 0 (or n) transforms every Gaussian; otherwise the kept set of the
+ * `keep` most important (importance [n]), with the whole scene's Morton
+ * reading.  dc_out [n_c]; ac_out [(n - 1)][n_c] (capacity); ac_w_out
+ * [(n - 1)] (may be NULL) the weight w1 + w2 of each AC's merge;
+ * *n_vox_out = V.  FP64. */
 int oracle_raht(const float *attrs, int64_t n, int32_t n_channels, const int32_t *chan, int32_t n_c,
-                int32_t depth, double *dc_out, double *ac_out, int64_t *ac_w_out, int64_t *n_vox_out) {
-    if (n < 1 || n_c < 1 || depth < 1 || depth > 21) return ORACLE_ERR_ARG;
+                int32_t depth, const float *importance, int64_t keep, double *dc_out, double *ac_out,
+                int64_t *ac_w_out, int64_t *n_vox_out) {
+    if (n < 1 || n_c < 1 || depth < 1 || depth > 21 || keep < 0 || keep > n) return ORACLE_ERR_ARG;
+    if (keep > 0 && keep < n && !importance) return ORACLE_ERR_ARG;
     for (int32_t k = 0; k < n_c; k++)
         if (chan[k] < 0 || chan[k] >= n_channels) return ORACLE_ERR_ARG;
     uint64_t *code = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)n);
@@ -501,22 +506,33 @@ int oracle_raht(const float *attrs, int64_t n, int32_t n_channels, const int32_t
     uint64_t *key = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)n);
     int64_t *w = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
     double *x = (double *)malloc(sizeof(double) * (size_t)n * (size_t)n_c);
-    if (!code || !order || !key || !w || !x) {
-        free(code); free(order); free(key); free(w); free(x);
+    int64_t *pos = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    int32_t *rank = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    if (!code || !order || !key || !w || !x || !pos || !rank) {
+        free(code); free(order); free(key); free(w); free(x); free(pos); free(rank);
         return ORACLE_ERR_NOMEM;
     }
     int rc = oracle_morton(attrs, n, n_channels, code, order);
     if (rc) goto done;
+    /* the Morton positions taken: all, or the kept set of the `keep` most important */
+    int64_t K = n;
+    if (keep > 0 && keep < n) {
+        rc = oracle_rank(importance, n, rank);
+        if (rc) goto done;
+        K = oracle_kept(rank, order, n, keep, pos);
+    } else {
+        for (int64_t t = 0; t < n; t++) pos[t] = t;
+    }
     /* voxels: runs of equal code >> 3(21 - d) in Morton order, FP64 means */
     int shift = 3 * (21 - depth);
     int64_t m = 0;
-    for (int64_t p = 0; p < n;) {
-        uint64_t vc = code[order[p]] >> shift;
+    for (int64_t p = 0; p < K;) {
+        uint64_t vc = code[order[pos[p]]] >> shift;
         int64_t q = p;
-        while (q < n && (code[order[q]] >> shift) == vc) q++;
+        while (q < K && (code[order[pos[q]]] >> shift) == vc) q++;
         for (int32_t k = 0; k < n_c; k++) {
             double sum = 0.0;
-            for (int64_t t = p; t < q; t++) sum += (double)attrs[order[t] * n_channels + chan[k]];
+            for (int64_t t = p; t < q; t++) sum += (double)attrs[order[pos[t]] * n_channels + chan[k]];
             x[m * n_c + k] = q - p > 1 ? sum / (double)(q - p) : sum;
         }
         key[m] = vc;
@@ -564,6 +580,6 @@ int oracle_raht(const float *attrs, int64_t n, int32_t n_channels, const int32_t
     }
     for (int32_t k = 0; k < n_c; k++) dc_out[k] = x[k];
 done:
-    free(code); free(order); free(key); free(w); free(x);
+    free(code); free(order); free(key); free(w); free(x); free(pos); free(rank);
     return rc;
 }

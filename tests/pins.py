@@ -322,3 +322,18 @@ def check_raht_constant_and_dedup(L, seed: int = 9, n: int = 2000):
     assert V1 == V2
     assert np.allclose(dc2, dc1 + 0.5 * math.sqrt(V1), rtol=1e-12)   # every mean moved by 0.5
     assert np.allclose(ac2, ac1, atol=1e-10)
+
+
+def check_raht_keep(L, seed: int = 10, n: int = 3000, keep: int = 1200):
+    """The RAHT of a kept set equals the RAHT of those Gaussians alone when they
+    span the whole scene's bounding box (the bbox extremes are made the most
+    important, so both use the same voxel grid)."""
+    rng = np.random.default_rng(seed)
+    a = rng.uniform(0, 1, (n, 5)).astype(np.float32)
+    imp = rng.uniform(0, 1, n).astype(np.float32)
+    ext = np.unique(np.concatenate([np.argmin(a[:, :3], axis=0), np.argmax(a[:, :3], axis=0)]))
+    imp[ext] = 2.0 + np.arange(len(ext))
+    dc, ac, V = oracle.raht(a, [3, 4], 9, L=L, importance=imp, keep=keep)
+    top = np.sort(np.lexsort((np.arange(n), -imp))[:keep])     # the `keep` most important, index order
+    dc2, ac2, V2 = oracle.raht(a[top], [3, 4], 9, L=L)
+    assert V == V2 and np.array_equal(dc, dc2) and np.array_equal(ac, ac2)

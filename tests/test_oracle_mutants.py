@@ -43,6 +43,8 @@ MUTANTS = {
     "raht_mean_not_divided": ("x[m * n_c + k] = q - p > 1 ? sum / (double)(q - p) : sum;",
                               "x[m * n_c + k] = sum;"),
     "raht_weight_not_summed": ("w[out] = w[i] + w[i + 1];", "w[out] = w[i];"),
+    "raht_keep_ignored": ("        K = oracle_kept(rank, order, n, keep, pos);",
+                          "        for (int64_t t = 0; t < n; t++) pos[t] = t;"),
 }
 
 RUNNER = r"""
@@ -70,6 +72,7 @@ checks = [
     lambda: pins.check_raht_example(L),
     lambda: pins.check_raht_orthonormal(L),
     lambda: pins.check_raht_constant_and_dedup(L),
+    lambda: pins.check_raht_keep(L),
 ]
 failed = 0
 for c in checks:

@@ -187,3 +187,7 @@ def test_raht_orthonormal():
 
 def test_raht_constant_and_dedup():
     pins.check_raht_constant_and_dedup(oracle.lib())
+
+
+def test_raht_kept_set():
+    pins.check_raht_keep(oracle.lib())
