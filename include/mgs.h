@@ -233,6 +233,8 @@ mgs_status mgs_scene_morton(const mgs_scene *scene, uint64_t *codes, int32_t *or
  *   DC = t1 x1 + t2 x2,  weight w1 + w2,     AC = t1 x2 - t2 x1,
  * with x1 the node of the lower code; an unpaired node moves up unchanged.
  *   channels [n_channels]      host: the scene channels to transform (1..64 of them)
+ *   keep                       0 (or n): every Gaussian; otherwise the kept set of the
+ *                              `keep` most important (Sec. III-A), as for the cost tables
  *   dc_out [n_channels]        host: the final DC coefficient of each channel
  *   ac_out [(n - 1)][n_channels] device (capacity for the scene's n Gaussians):
  *                              the V - 1 AC coefficients, step by step, in
@@ -244,7 +246,8 @@ mgs_status mgs_scene_morton(const mgs_scene *scene, uint64_t *codes, int32_t *or
  * a device workspace of about (56 + 4 n_channels) n bytes on `stream`.
  */
 mgs_status mgs_raht(mgs_ctx *ctx, const mgs_scene *scene, const int32_t *channels, int32_t n_channels,
-                    int32_t depth, float *dc_out, float *ac_out, int64_t *n_voxels_out, void *stream);
+                    int32_t depth, int64_t keep, float *dc_out, float *ac_out, int64_t *n_voxels_out,
+                    void *stream);
 
 /* ---- cost table --------------------------------------------------------- */
 
@@ -278,6 +281,23 @@ mgs_status mgs_build_cost_table(mgs_ctx *ctx, const mgs_scene *scene, const mgs_
  */
 mgs_status mgs_build_cost_table_plain(mgs_ctx *ctx, const mgs_scene *scene, const mgs_grid *grid,
                                       void *table, void *stream);
+
+/*
+ * The cost table of an arbitrary coefficient array -- e.g. the RAHT AC
+ * coefficients of mgs_raht (Sec. III-D: after RAHT the AC coefficients are
+ * the quantised signal) -- with the same quantiser, errors and entropy bound
+ * as mgs_build_cost_table.  coeffs [m][n_channels] row-major FP32, device.
+ * Ratio r of `grid` takes the first keep[r] coefficients, in their order, cut
+ * into consecutive groups of grid->group_size (no importance ranking and no
+ * Morton reordering: the array's order is the group order).  `table` may be
+ * device or host memory (layout from mgs_table_layout_for(m, n_channels, grid)).
+ * Synchronous on `stream` (it validates the array first); allocates a slab
+ * copy of the coefficients (4 m * ceil(n_channels / 8) * 8 bytes) on `stream`.
+ * Errors: INVALID_ARG, NONFINITE (a NaN or infinite coefficient), RANGE (a
+ * channel's max - min overflows FP32).
+ */
+mgs_status mgs_build_cost_table_coeffs(mgs_ctx *ctx, const float *coeffs, int64_t m, int32_t n_channels,
+                                       const mgs_grid *grid, void *table, void *stream);
 
 /*
  * Several scenes, one persistent launch over all their (scene, ratio, group,

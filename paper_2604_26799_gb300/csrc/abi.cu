@@ -136,6 +136,72 @@ mgs_status run_cost(mgs_ctx *ctx, CostLaunch &launch, cudaStream_t st) {
     return s;
 }
 
+// [m][C] row-major coefficients into [n_slabs][m][8] slabs (padded channels 0).
+__global__ void k_coeff_slabs(const float *__restrict__ in, int64_t m, int C, int n_slabs,
+                              float *__restrict__ slabs) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= m * n_slabs * kSlabWidth) return;
+    const int j = (int)(t % kSlabWidth);
+    const int64_t row = (t / kSlabWidth) % m;
+    const int slab = (int)(t / ((int64_t)kSlabWidth * m));
+    const int c = slab * kSlabWidth + j;
+    slabs[t] = c < C ? in[row * C + c] : 0.0f;
+}
+
+// Finiteness and per-channel range of a [m][C] coefficient array: block (b, c)
+// reduces rows [b * 4096, (b + 1) * 4096) of channel c, one atomic per block.
+__device__ __forceinline__ unsigned int ord_u32(float f) {
+    const unsigned int u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+constexpr int kCheckRows = 4096;
+__global__ void k_coeff_check(const float *__restrict__ in, int64_t m, int C, unsigned int *__restrict__ flag,
+                              unsigned int *__restrict__ mn, unsigned int *__restrict__ mx) {
+    __shared__ unsigned int s_mn[8], s_mx[8], s_bad;
+    const int c = blockIdx.y;
+    const int64_t r0 = (int64_t)blockIdx.x * kCheckRows;
+    const int64_t r1 = r0 + kCheckRows < m ? r0 + kCheckRows : m;
+    unsigned int lo = 0xFFFFFFFFu, hi = 0u, bad = 0u;
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+        const float v = in[r * C + c];
+        if (!isfinite(v)) {
+            bad = 1u;
+        } else {
+            lo = min(lo, ord_u32(v));
+            hi = max(hi, ord_u32(v));
+        }
+    }
+    lo = __reduce_min_sync(0xFFFFFFFFu, lo);
+    hi = __reduce_max_sync(0xFFFFFFFFu, hi);
+    bad = __reduce_or_sync(0xFFFFFFFFu, bad);
+    if (threadIdx.x == 0) s_bad = 0u;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) {
+        s_mn[threadIdx.x >> 5] = lo;
+        s_mx[threadIdx.x >> 5] = hi;
+        if (bad) atomicOr(&s_bad, 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < (int)(blockDim.x >> 5); k++) {
+            lo = min(lo, s_mn[k]);
+            hi = max(hi, s_mx[k]);
+        }
+        lo = min(lo, s_mn[0]);
+        hi = max(hi, s_mx[0]);
+        if (s_bad) atomicOr(flag, 1u);
+        atomicMin(&mn[c], lo);
+        atomicMax(&mx[c], hi);
+    }
+}
+
+float from_ord_u32(unsigned int o) {
+    const unsigned int u = (o & 0x80000000u) ? (o & 0x7FFFFFFFu) : ~o;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
 // Host-or-device table: run `fn` on a device table and copy back when needed.
 template <typename F>
 mgs_status with_device_table(void *table, size_t bytes, cudaStream_t st, F fn) {
@@ -430,6 +496,86 @@ mgs_status mgs_build_cost_table(mgs_ctx *ctx, const mgs_scene *scene, const mgs_
 mgs_status mgs_build_cost_table_plain(mgs_ctx *ctx, const mgs_scene *scene, const mgs_grid *grid,
                                       void *table, void *stream) {
     return build_table(ctx, scene, grid, table, stream, true);
+}
+
+mgs_status mgs_build_cost_table_coeffs(mgs_ctx *ctx, const float *coeffs, int64_t m, int32_t n_channels,
+                                       const mgs_grid *grid, void *table, void *stream) {
+    clear_error();
+    if (!ctx || !coeffs || !grid || !table) {
+        set_error("ctx, coeffs, grid and table must be non-NULL");
+        return MGS_ERR_INVALID_ARG;
+    }
+    mgs_table_layout L;
+    MGS_TRY(mgs_table_layout_for(m, n_channels, grid, &L));
+    if (m > ((int64_t)1 << 31) - 1) {
+        set_error("%lld coefficients exceed 2^31 - 1", (long long)m);
+        return MGS_ERR_INVALID_ARG;
+    }
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // validation: finite values and a finite FP32 range per channel (as for scenes)
+    {
+        unsigned int *chk = nullptr;
+        MGS_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void **>(&chk), sizeof(unsigned int) * (1 + 2 * (size_t)n_channels),
+                                     st));
+        std::vector<unsigned int> h(1 + 2 * (size_t)n_channels, 0u);
+        for (int c = 0; c < n_channels; c++) h[1 + c] = 0xFFFFFFFFu;
+        cudaError_t e = cudaMemcpyAsync(chk, h.data(), sizeof(unsigned int) * h.size(), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) {
+            const dim3 grid((unsigned int)((m + kCheckRows - 1) / kCheckRows), (unsigned int)n_channels);
+            k_coeff_check<<<grid, 256, 0, st>>>(coeffs, m, n_channels, chk, chk + 1, chk + 1 + n_channels);
+            count_launches(1);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), chk, sizeof(unsigned int) * h.size(), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        cudaFreeAsync(chk, st);
+        if (e != cudaSuccess) {
+            set_error("coefficient check failed: %s", cudaGetErrorString(e));
+            return MGS_ERR_CUDA;
+        }
+        if (h[0]) {
+            set_error("a coefficient is NaN or infinite");
+            return MGS_ERR_NONFINITE;
+        }
+        for (int c = 0; c < n_channels; c++) {
+            const float r = from_ord_u32(h[1 + n_channels + c]) - from_ord_u32(h[1 + c]);
+            if (!std::isfinite(r)) {
+                set_error("channel %d: max - min overflows FP32", c);
+                return MGS_ERR_RANGE;
+            }
+        }
+    }
+    const int n_slabs = (n_channels + kSlabWidth - 1) / kSlabWidth;
+    float *slabs = nullptr;
+    MGS_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void **>(&slabs), sizeof(float) * (size_t)m * n_slabs * kSlabWidth,
+                                 st));
+    const int64_t work = m * n_slabs * kSlabWidth;
+    k_coeff_slabs<<<(unsigned int)((work + 255) / 256), 256, 0, st>>>(coeffs, m, n_channels, n_slabs, slabs);
+    count_launches(1);
+    mgs_status s = with_device_table(table, (size_t)L.total_bytes, st, [&](void *dt) -> mgs_status {
+        CostLaunch launch;
+        for (int r = 0; r < grid->n_ratios; r++) {
+            CostSeg c{};
+            c.slabs = slabs;
+            c.kept = nullptr;   // the first K coefficients, in order
+            c.n = m;
+            c.K = grid->keep[r];
+            c.item_base = L.item_begin[r];
+            c.n_groups = (int32_t)L.n_groups[r];
+            c.C = n_channels;
+            table_ptrs(dt, L, &c);
+            launch.segs.push_back(c);
+        }
+        launch.group_size = grid->group_size;
+        launch.n_bits = grid->n_bits;
+        for (int k = 0; k < grid->n_bits; k++) launch.bits[k] = grid->bits[k];
+        launch.opt_lo = 0;
+        launch.opt_hi = grid->n_bits;
+        return run_cost(ctx, launch, st);
+    });
+    cudaFreeAsync(slabs, st);
+    return s;
 }
 
 static mgs_status same_shape(int32_t n, const mgs_grid *grids) {

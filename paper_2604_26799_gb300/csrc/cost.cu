@@ -478,7 +478,7 @@ __device__ void process_item(const KernelArgs &A, const Smem &sm, int64_t work) 
         int i = e * T + threadIdx.x;
         float row[W];
         if (i < nvalid) {
-            int32_t pos = ld_stream(&S.kept[gstart + i]);
+            const int32_t pos = S.kept ? ld_stream(&S.kept[gstart + i]) : (int32_t)(gstart + i);
             load_row<W>(S.slabs + ((int64_t)slab * S.n + pos) * kSlabWidth + j0, row);
         } else {
 #pragma unroll

@@ -116,7 +116,7 @@ int64_t kept_tiles_for(int64_t n);
 // ---- cost kernels (cost.cu) ----
 struct CostSeg {
     const float *slabs;
-    const int32_t *kept;   // Morton positions of this ratio's kept set
+    const int32_t *kept;   // Morton positions of this ratio's kept set (NULL: positions 0..K-1)
     int64_t n;             // scene size (slab stride)
     int64_t K;             // kept-set size
     int64_t work_begin;    // first work item of this segment

@@ -38,13 +38,17 @@ namespace {
 constexpr int kScanBlock = 1024;
 constexpr int kMaxRahtChannels = 64;
 
-__global__ void k_rh_heads(const uint64_t *__restrict__ codes, const int32_t *__restrict__ order, int64_t n,
-                           int shift, uint64_t *__restrict__ vcode, unsigned int *__restrict__ head) {
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
+// t runs over the transformed Gaussians in Morton order: Morton position
+// pos[t] (the kept list), or t itself when pos is NULL.
+__global__ void k_rh_heads(const uint64_t *__restrict__ codes, const int32_t *__restrict__ order,
+                           const int32_t *__restrict__ pos, int64_t K, int shift, uint64_t *__restrict__ vcode,
+                           unsigned int *__restrict__ head) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= K) return;
+    const int64_t p = pos ? pos[t] : t;
     const uint64_t v = codes[order[p]] >> shift;
-    vcode[p] = v;
-    head[p] = (p == 0 || (codes[order[p - 1]] >> shift) != v) ? 1u : 0u;
+    vcode[t] = v;
+    head[t] = (t == 0 || (codes[order[pos ? pos[t - 1] : t - 1]] >> shift) != v) ? 1u : 0u;
 }
 
 // ---- exclusive scan of n uint32 flags (three phases) ----
@@ -130,18 +134,19 @@ __global__ void k_rh_starts(const unsigned int *__restrict__ head, const unsigne
     key[vidx[p]] = vcode[p];
 }
 
-__global__ void k_rh_means(const float *__restrict__ slabs, int64_t n, const int64_t *__restrict__ start,
-                           int64_t V, const int32_t *__restrict__ chan, int n_c, float *__restrict__ x,
+__global__ void k_rh_means(const float *__restrict__ slabs, int64_t n, const int32_t *__restrict__ pos,
+                           int64_t K, const int64_t *__restrict__ start, int64_t V,
+                           const int32_t *__restrict__ chan, int n_c, float *__restrict__ x,
                            unsigned int *__restrict__ w) {
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= V) return;
-    const int64_t p0 = start[v], p1 = v + 1 < V ? start[v + 1] : n;
+    const int64_t t0 = start[v], t1 = v + 1 < V ? start[v + 1] : K;
     for (int k = 0; k < n_c; k++) {
         const int c = chan[k];
         const float *col = slabs + (int64_t)(c / kSlabWidth) * n * kSlabWidth + (c % kSlabWidth);
         float sum = 0.0f;
-        for (int64_t p = p0; p < p1; p++) sum = __fadd_rn(sum, col[p * kSlabWidth]);
-        x[v * n_c + k] = p1 - p0 > 1 ? __fdiv_rn(sum, (float)(p1 - p0)) : sum;
+        for (int64_t t = t0; t < t1; t++) sum = __fadd_rn(sum, col[(int64_t)(pos ? pos[t] : t) * kSlabWidth]);
+        x[v * n_c + k] = t1 - t0 > 1 ? __fdiv_rn(sum, (float)(t1 - t0)) : sum;
     }
     w[v] = 1u;
 }
@@ -248,7 +253,7 @@ unsigned int blocks_of(int64_t n, int t) { return (unsigned int)((n + t - 1) / t
 using namespace mgs;
 
 extern "C" mgs_status mgs_raht(mgs_ctx *ctx, const mgs_scene *scene, const int32_t *channels, int32_t n_c,
-                               int32_t depth, float *dc_out, float *ac_out, int64_t *n_voxels_out,
+                               int32_t depth, int64_t keep, float *dc_out, float *ac_out, int64_t *n_voxels_out,
                                void *stream) {
     clear_error();
     if (!ctx || !scene || !channels || !dc_out || !ac_out || !n_voxels_out) {
@@ -265,6 +270,12 @@ extern "C" mgs_status mgs_raht(mgs_ctx *ctx, const mgs_scene *scene, const int32
             return MGS_ERR_INVALID_ARG;
         }
     const int64_t n = scene->n;
+    if (keep < 0 || keep > n) {
+        set_error("keep = %lld outside 0..%lld", (long long)keep, (long long)n);
+        return MGS_ERR_INVALID_ARG;
+    }
+    const bool subset = keep > 0 && keep < n;
+    const int64_t K = subset ? keep : n;   // Gaussians transformed
     if (n > ((int64_t)1 << 31)) {
         set_error("scene of %lld Gaussians exceeds 2^31", (long long)n);
         return MGS_ERR_INVALID_ARG;
@@ -281,6 +292,7 @@ extern "C" mgs_status mgs_raht(mgs_ctx *ctx, const mgs_scene *scene, const int32
     const size_t o_slot0 = take(4 * (size_t)n), o_slot1 = take(4 * (size_t)n);
     const size_t o_w = take(4 * (size_t)n), o_x = take(4 * (size_t)n * n_c);
     const size_t o_chan = take(4 * (size_t)n_c), o_state = take(sizeof(RahtState));
+    const size_t o_pos = take(subset ? 4 * (size_t)K : 0), o_tiles = take(subset ? 4 * (size_t)kept_tiles_for(n) : 0);
     char *ws = nullptr;
     if (cudaMallocAsync(reinterpret_cast<void **>(&ws), off, st) != cudaSuccess) {
         cudaGetLastError();
@@ -305,6 +317,11 @@ extern "C" mgs_status mgs_raht(mgs_ctx *ctx, const mgs_scene *scene, const int32
     float *x = reinterpret_cast<float *>(ws + o_x);
     int32_t *d_chan = reinterpret_cast<int32_t *>(ws + o_chan);
     RahtState *rst = reinterpret_cast<RahtState *>(ws + o_state);
+    int32_t *pos = nullptr;
+    if (subset) {
+        pos = reinterpret_cast<int32_t *>(ws + o_pos);
+        MGS_TRY(kept_list_into(scene, keep, pos, reinterpret_cast<uint32_t *>(ws + o_tiles), st));
+    }
     MGS_CUDA_TRY(cudaMemcpyAsync(d_chan, channels, 4 * (size_t)n_c, cudaMemcpyHostToDevice, st));
     int64_t launches = 0;
     // exclusive scan of `len` flags into `out`; the total goes to `total` (device)
@@ -316,16 +333,16 @@ extern "C" mgs_status mgs_raht(mgs_ctx *ctx, const mgs_scene *scene, const int32
         launches += 3;
     };
     // voxels and their means
-    k_rh_heads<<<blocks_of(n, 256), 256, 0, st>>>(scene->d_codes, scene->d_order, n, 3 * (21 - depth), vcode,
-                                                  head);
+    k_rh_heads<<<blocks_of(K, 256), 256, 0, st>>>(scene->d_codes, scene->d_order, pos, K, 3 * (21 - depth),
+                                                  vcode, head);
     launches++;
-    scan(head, n, idx);
+    scan(head, K, idx);
     unsigned long long V = 0;
     MGS_CUDA_TRY(cudaMemcpyAsync(&V, total, 8, cudaMemcpyDeviceToHost, st));
     MGS_CUDA_TRY(cudaStreamSynchronize(st));
-    k_rh_starts<<<blocks_of(n, 256), 256, 0, st>>>(head, idx, vcode, n, start, key[0]);
-    k_rh_means<<<blocks_of((int64_t)V, 256), 256, 0, st>>>(scene->d_slabs, n, start, (int64_t)V, d_chan, n_c, x,
-                                                           w);
+    k_rh_starts<<<blocks_of(K, 256), 256, 0, st>>>(head, idx, vcode, K, start, key[0]);
+    k_rh_means<<<blocks_of((int64_t)V, 256), 256, 0, st>>>(scene->d_slabs, n, pos, K, start, (int64_t)V, d_chan,
+                                                           n_c, x, w);
     k_rh_init<<<blocks_of((int64_t)V, 256), 256, 0, st>>>(rst, total, slot[0], (int64_t)V);
     launches += 3;
     MGS_CUDA_TRY(cudaGetLastError());

@@ -124,7 +124,8 @@ _SIGS = {
                          ctypes.POINTER(mgs_solution)],
     "mgs_solve_budgets": [_P, ctypes.POINTER(mgs_table_layout), ctypes.POINTER(mgs_grid),
                           ctypes.c_int32, _P, ctypes.POINTER(mgs_solve_opts), _P],
-    "mgs_raht": [_P, _P, _P, ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P],
+    "mgs_build_cost_table_coeffs": [_P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(mgs_grid), _P, _P],
+    "mgs_raht": [_P, _P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _P, _P, _P, _P],
     "mgs_preprocess": [_P, _P, _P, ctypes.c_int64, ctypes.c_double, _P, _P, _P, _P],
     "mgs_solve_budgets_device": [_P, _P, ctypes.POINTER(mgs_table_layout), ctypes.POINTER(mgs_grid),
                                  ctypes.c_int32, _P, ctypes.POINTER(mgs_solve_opts), _P, _P],
@@ -466,8 +467,9 @@ def mgs_preprocess(ctx: int, attrs, view_importance, beta: float, attrs_out=None
     return attrs_out, importance_out, vq.value
 
 
-def mgs_raht(ctx: int, scene: int, channels, depth: int, ac_out=None, stream=None):
-    """RAHT of a resident scene's channels: (DC [n_c] numpy, AC [V - 1, n_c] device tensor, V)."""
+def mgs_raht(ctx: int, scene: int, channels, depth: int, ac_out=None, stream=None, keep: int = 0):
+    """RAHT of a resident scene's channels (keep > 0: of the `keep` most important Gaussians):
+    (DC [n_c] numpy, AC [V - 1, n_c] device tensor, V)."""
     import torch
     n, _, _ = mgs_scene_info(scene)
     ch = np.ascontiguousarray(channels, dtype=np.int32)
@@ -476,6 +478,13 @@ def mgs_raht(ctx: int, scene: int, channels, depth: int, ac_out=None, stream=Non
         ac_out = torch.empty((max(n - 1, 1), nc), dtype=torch.float32, device="cuda")
     dc = np.empty(nc, dtype=np.float32)
     nv = ctypes.c_int64()
-    _check(lib().mgs_raht(ctx, scene, ch.ctypes.data, nc, int(depth), dc.ctypes.data, _ptr(ac_out),
+    _check(lib().mgs_raht(ctx, scene, ch.ctypes.data, nc, int(depth), int(keep), dc.ctypes.data, _ptr(ac_out),
                           ctypes.byref(nv), _stream(stream)))
     return dc, ac_out[:nv.value - 1], nv.value
+
+
+def mgs_build_cost_table_coeffs(ctx: int, coeffs, grid: "Grid", table, stream=None):
+    """Cost table of a [m, n_channels] float32 device array, groups in array order."""
+    m, nc = int(coeffs.shape[0]), int(coeffs.shape[1])
+    _check(lib().mgs_build_cost_table_coeffs(ctx, _ptr(coeffs), m, nc, ctypes.byref(grid.c), _ptr(table),
+                                             _stream(stream)))

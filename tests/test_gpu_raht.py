@@ -29,21 +29,21 @@ def ctx():
     mgs.mgs_destroy(c)
 
 
-def gpu_raht(ctx, attrs, channels, depth):
+def gpu_raht(ctx, attrs, channels, depth, imp=None, keep=0):
     dev = torch.device("cuda:0")
-    imp = np.ones(attrs.shape[0], np.float32)
+    imp = np.ones(attrs.shape[0], np.float32) if imp is None else imp
     scene = mgs.mgs_scene_create(ctx, torch.from_numpy(attrs).to(dev), torch.from_numpy(imp).to(dev))
     try:
-        dc, ac, V = mgs.mgs_raht(ctx, scene, channels, depth)
+        dc, ac, V = mgs.mgs_raht(ctx, scene, channels, depth, keep=keep)
         torch.cuda.synchronize()
         return dc, ac.cpu().numpy(), V
     finally:
         mgs.mgs_scene_destroy(scene)
 
 
-def close(gpu, attrs, channels, depth):
+def close(gpu, attrs, channels, depth, imp=None, keep=0):
     dc, ac, V = gpu
-    rdc, rac, rV, rw = oracle.raht(attrs, channels, depth, weights=True)
+    rdc, rac, rV, rw = oracle.raht(attrs, channels, depth, weights=True, importance=imp, keep=keep)
     assert V == rV and ac.shape == rac.shape
     S = np.abs(attrs[:, channels]).max(axis=0).astype(np.float64)      # |x| bound per channel
     tol = 3 * depth * 2.5e-7 + 1e-6                                     # ulp-scale per level
@@ -84,3 +84,10 @@ def test_raht_full_size(ctx):
     close(gpu, attrs, CHANNELS, 16)
     dc, ac, V = gpu
     assert V > 1_000_000 and np.all(np.isfinite(ac))
+
+
+@pytest.mark.parametrize("frac", [(1, 10), (1, 2), (9, 10)])
+def test_raht_kept_set_matches_oracle(ctx, frac):
+    attrs, imp = synth.make_scene(30_000, seed=17)
+    keep = int(synth.keep_counts(30_000, [frac])[0])
+    close(gpu_raht(ctx, attrs, CHANNELS, 14, imp=imp, keep=keep), attrs, CHANNELS, 14, imp=imp, keep=keep)
