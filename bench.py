@@ -704,18 +704,89 @@ def run_raht(args):
                       "cpu_baseline": cpu}))
 
 
+def run_raht_search(args):
+    """The search in the RAHT domain (Sec. III-D/F): for every reserve ratio of the
+    scene-scale grid, the RAHT of the kept set's 7 important channels (SH DC, opacity,
+    log-scales) at depth 16, the cost table of its AC coefficients (10 bit-widths,
+    G = 4096) and the device budget solve; tau by the rule of mgs_solve_budget."""
+    import torch
+    from paper_2604_26799_gb300 import mgs
+    dev = torch.device("cuda", 0)
+    w = WORKLOAD
+    a, imp = synth.make_scene(w.n, seed=w.seed)
+    channels = [3, 4, 5, 51, 52, 53, 54]
+    depth, budget = 16, 7e6
+    bits = list(w.bits)
+    keep = w.keep()
+    ctx = mgs.mgs_create(0)
+    st = torch.cuda.Stream(device=dev)
+    scene = mgs.mgs_scene_create(ctx, torch.from_numpy(a).to(dev), torch.from_numpy(imp).to(dev), stream=st)
+    ac = torch.empty((w.n, len(channels)), dtype=torch.float32, device=dev)
+    opts = mgs.solve_opts(const_bytes=4.0 * len(channels))       # the DC coefficients in FP32
+    times, phases, evals, pick = [], {"raht": 0.0, "table": 0.0, "solve": 0.0}, 0, None
+    for step in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        per_r, ev = [], 0
+        ph = {"raht": 0.0, "table": 0.0, "solve": 0.0}
+        with torch.cuda.stream(st):
+            for K in keep:
+                e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+                e[0].record(st)
+                _, acv, V = mgs.mgs_raht(ctx, scene, channels, depth, ac_out=ac, stream=st, keep=int(K))
+                e[1].record(st)
+                grid = mgs.Grid([V - 1], bits, w.group_size)
+                L = mgs.mgs_table_layout_for(V - 1, len(channels), grid)
+                tab = torch.empty(L.total_bytes, dtype=torch.uint8, device=dev)
+                mgs.mgs_build_cost_table_coeffs(ctx, acv, grid, tab, stream=st)
+                e[2].record(st)
+                sol = mgs.mgs_solve_budgets_device(ctx, tab, L, grid, [budget], opts, stream=st)[0]
+                e[3].record(st)
+                e[3].synchronize()
+                ph["raht"] += e[0].elapsed_time(e[1])
+                ph["table"] += e[1].elapsed_time(e[2])
+                ph["solve"] += e[2].elapsed_time(e[3])
+                ev += (V - 1) * len(channels) * len(bits)
+                per_r.append((int(sol["ratio_status"][0]), float(sol["objective"]), float(sol["est_bytes"])))
+        dt = (time.perf_counter() - t0) * 1e3
+        if step >= args.warmup:
+            times.append(dt)
+            for k in ph:
+                phases[k] += ph[k] / args.steps
+            evals = ev
+        best, largest = -1, -1
+        for r, (status, obj, _) in enumerate(per_r):
+            if status < 0:
+                continue
+            largest = r
+            if status == 1:
+                continue
+            if best < 0 or obj <= per_r[best][1]:
+                best = r
+        pick = best if best >= 0 else largest
+    mgs.mgs_scene_destroy(scene)
+    mgs.mgs_destroy(ctx)
+    ms = statistics.mean(times)
+    print(json.dumps({"metric": "RAHT-domain search: AC cost-table evals/s", "value": evals / (ms * 1e-3),
+                      "unit": "evals/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_step": ms, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+                      "config": {"workload": f"RAHT search N={w.n}, 10 ratios, depth {depth}, {len(channels)} "
+                                             f"channels, b={bits}, G={w.group_size}, budget {budget:.0f} B"},
+                      "phase_ms": phases, "tau_index": pick}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mgs", choices=["mgs", "reference"])
-    ap.add_argument("--workload", default="scene", choices=["scene", "batch", "serve", "large", "preprocess", "raht"],
+    ap.add_argument("--workload", default="scene", choices=["scene", "batch", "serve", "large", "preprocess", "raht", "raht_search"],
                     help="scene: the scene-scale search (default); batch: 16 uneven scenes in one "
                          "graph-replayed launch; serve: Poisson job stream through the server; "
                          "large: 6 M Gaussians x 20 ratios x 16 bit-widths; preprocess: Euler "
                          "replacement and view-independent importance of the scene-scale scene; "
-                         "raht: RAHT of 10 channels of the scene-scale scene at depth 16")
+                         "raht: RAHT of 10 channels of the scene-scale scene at depth 16; "
+                         "raht_search: the search over RAHT AC tables for every ratio")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-loop comparator")
     ap.add_argument("--no-autotune", action="store_true", help="use the default tile shape")
@@ -739,6 +810,8 @@ def main():
         return run_preprocess(args)
     if args.workload == "raht":
         return run_raht(args)
+    if args.workload == "raht_search":
+        return run_raht_search(args)
     return run_gpu(args)
 
 

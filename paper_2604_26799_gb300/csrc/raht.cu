@@ -10,8 +10,9 @@
 //   per step s = 0 .. 3d - 1 (the node count, the AC offset, the current list
 //   and the pending level live in device memory; the host reads them once per
 //   octree level to size the grids):
-//     k_rh_pairs  flag i when nodes i, i + 1 agree above bit 1 of their codes
-//     scan        pair index of every node and the number of pairs
+//     k_rh_scan_pairs  flag i when nodes i, i + 1 agree above bit 1 of their
+//                 codes, fused with the block-local scan; k_scan_sums: the block
+//                 offsets and the number of pairs
 //     k_rh_merge  the parent list (code >> 1, slot): a pair merges in place into
 //                 the lower node's slot by the printed T, with its entries
 //                 t1 = sqrt(w1) / sqrt(w1 + w2), t2 = sqrt(w2) / sqrt(w1 + w2) formed
@@ -161,42 +162,76 @@ struct RahtState {
 // Steps whose list has no pair change nothing but the level: they only raise
 // `pending`, and the codes are compared (and shifted when the list is next
 // rewritten) by pending + 1 bits.
-__global__ void k_rh_pairs(const uint64_t *__restrict__ key0, const uint64_t *__restrict__ key1,
-                           const RahtState *st, int64_t cap, unsigned int *__restrict__ pf) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= cap) return;
+// Pair flags of the current list fused with the block-local exclusive scan
+// (the flags are recomputed from the codes by k_rh_merge; no flag array).
+__device__ __forceinline__ unsigned int pair_flag(const uint64_t *key, int64_t i, int64_t m, int sh) {
+    return (i + 1 < m && (key[i] >> sh) == (key[i + 1] >> sh)) ? 1u : 0u;
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_rh_scan_pairs(const uint64_t *__restrict__ key0,
+                                                              const uint64_t *__restrict__ key1,
+                                                              const RahtState *st, int64_t cap,
+                                                              unsigned int *__restrict__ out,
+                                                              unsigned int *__restrict__ block_sum) {
+    __shared__ unsigned int s_w[32];
+    const int64_t i = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
     const int64_t m = st->m;
     const uint64_t *key = st->cur ? key1 : key0;
-    const int sh = st->pending + 1;
-    pf[i] = (i + 1 < m && (key[i] >> sh) == (key[i + 1] >> sh)) ? 1u : 0u;
+    const unsigned int v = i < cap ? pair_flag(key, i, m, st->pending + 1) : 0u;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned int t = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += t;
+    }
+    if (lane == 31) s_w[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        unsigned int y = s_w[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned int t = __shfl_up_sync(0xFFFFFFFFu, y, o);
+            if (lane >= o) y += t;
+        }
+        s_w[lane] = y;
+    }
+    __syncthreads();
+    const unsigned int incl = x + (wid > 0 ? s_w[wid - 1] : 0u);
+    if (i < cap) out[i] = incl - v;
+    if (threadIdx.x == kScanBlock - 1) block_sum[blockIdx.x] = incl;
 }
 
 __global__ void k_rh_merge(uint64_t *__restrict__ key0, uint64_t *__restrict__ key1,
                            unsigned int *__restrict__ slot0, unsigned int *__restrict__ slot1,
                            const RahtState *st, const unsigned long long *pairs, int n_c,
-                           const unsigned int *__restrict__ pf, const unsigned int *__restrict__ pidx,
+                           const unsigned int *__restrict__ local, const unsigned int *__restrict__ block_off,
                            float *__restrict__ x, unsigned int *__restrict__ w, float *__restrict__ ac) {
     if (*pairs == 0) return;   // nothing to merge at this level
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t m = st->m;
     if (i >= m) return;
-    if (i > 0 && pf[i - 1]) return;   // the upper node of a pair: merged by its partner
+    const int sh = st->pending + 1;
+    const uint64_t *kc = st->cur ? key1 : key0;
+    if (i > 0 && pair_flag(kc, i - 1, m, sh)) return;   // the upper node of a pair: merged by its partner
+    const unsigned int pf_i = pair_flag(kc, i, m, sh);
+    const unsigned int pidx_i = local[i] + block_off[i / kScanBlock];
     const bool c = st->cur;
     const uint64_t *key = c ? key1 : key0;
     const unsigned int *slot = c ? slot1 : slot0;
     uint64_t *key2 = c ? key0 : key1;
     unsigned int *slot2 = c ? slot0 : slot1;
-    const int64_t j = i - (int64_t)pidx[i];
-    key2[j] = key[i] >> (st->pending + 1);
+    const int64_t j = i - (int64_t)pidx_i;
+    key2[j] = key[i] >> sh;
     const unsigned int sa = slot[i];
     slot2[j] = sa;
-    if (!pf[i]) return;
+    if (!pf_i) return;
     const unsigned int sb = slot[i + 1];
     const unsigned int wa = w[sa], wb = w[sb];
     // the entries of T, once per pair
     const float sw = __fsqrt_rn((float)(wa + wb));
     const float t1 = __fdiv_rn(__fsqrt_rn((float)wa), sw), t2 = __fdiv_rn(__fsqrt_rn((float)wb), sw);
-    const int64_t out = st->ac_base + (int64_t)pidx[i];
+    const int64_t out = st->ac_base + (int64_t)pidx_i;
     float *xa = x + (int64_t)sa * n_c;
     const float *xbp = x + (int64_t)sb * n_c;
     float *acp = ac + out * n_c;
@@ -350,12 +385,13 @@ extern "C" mgs_status mgs_raht(mgs_ctx *ctx, const mgs_scene *scene, const int32
     // octree level (three steps) the host reads the node count to size the grids
     int64_t cap = (int64_t)V;
     for (int s = 0; s < 3 * depth && V > 1 && cap > 1; s++) {
-        k_rh_pairs<<<blocks_of(cap, 256), 256, 0, st>>>(key[0], key[1], rst, cap, head);
-        scan(head, cap, idx);
-        k_rh_merge<<<blocks_of(cap, 256), 256, 0, st>>>(key[0], key[1], slot[0], slot[1], rst, total, n_c, head,
-                                                        idx, x, w, ac_out);
+        const int64_t blocks = (cap + kScanBlock - 1) / kScanBlock;
+        k_rh_scan_pairs<<<(unsigned int)blocks, kScanBlock, 0, st>>>(key[0], key[1], rst, cap, idx, bsum);
+        k_scan_sums<<<1, kScanBlock, 0, st>>>(bsum, blocks, total);
+        k_rh_merge<<<blocks_of(cap, 256), 256, 0, st>>>(key[0], key[1], slot[0], slot[1], rst, total, n_c, idx,
+                                                        bsum, x, w, ac_out);
         k_rh_advance<<<1, 1, 0, st>>>(rst, total);
-        launches += 3;
+        launches += 4;
         if (s % 3 == 2) {
             RahtState h{};
             MGS_CUDA_TRY(cudaMemcpyAsync(&h, rst, sizeof(RahtState), cudaMemcpyDeviceToHost, st));
