@@ -494,8 +494,8 @@ mgs_status mgs_solve_budgets(const void *table, const mgs_table_layout *layout,
  * `table` may be device or host memory (a host table is copied in first).
  * Device workspace is allocated and freed on `stream`; the call synchronises
  * `stream` before returning, and `out` (host memory) is filled as by
- * mgs_solve_budgets.  A budget whose greedy step has more than 4096
- * candidate increments in one ratio is solved by the host solver instead.
+ * mgs_solve_budgets.  The greedy completion takes one block-wide arg-min
+ * per increment, so any number of increments is completed on the device.
  */
 mgs_status mgs_solve_budgets_device(mgs_ctx *ctx, const void *table, const mgs_table_layout *layout,
                                     const mgs_grid *grid, int32_t n_budgets, const double *budgets,

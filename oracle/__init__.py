@@ -5,7 +5,8 @@ bench.py's CPU-baseline leg.  The product path (the package and its CUDA
 library) never imports it, and it imports nothing from the product.
 
   oracle.c   C reference of the quantiser, entropy bound, Morton order, ranks,
-             and of the preprocessing (importance I_g, Euler angles) and RAHT
+             of the preprocessing (importance I_g, Euler angles), RAHT and the
+             block coder that gives a configuration's actual size
              (compiled with gcc -O2 -ffp-contract=off, no fast-math)
   mckp.py    exact references of the 0-1 ILP (brute force, DP) and the tau rule
 """
@@ -57,6 +58,16 @@ def load(path: str):
     L.oracle_euler.restype = None
     L.oracle_preprocess.argtypes = [P, i64, i32, P, ctypes.c_double, P, P, P]
     L.oracle_raht.argtypes = [P, i64, i32, P, i32, i32, P, i64, P, P, P, P]
+    L.oracle_rans_lanes.argtypes = [i64]
+    L.oracle_rans_lanes.restype = i32
+    L.oracle_block_bound.argtypes = [i64, i32]
+    L.oracle_block_bound.restype = i64
+    L.oracle_encode_block.argtypes = [P, i64, i32, ctypes.c_float, ctypes.c_float, P, i64]
+    L.oracle_encode_block.restype = i64
+    L.oracle_decode_block.argtypes = [P, i64, i64, P, P, P, P]
+    L.oracle_decode_block.restype = i64
+    L.oracle_encode_config.argtypes = [P, P, i64, i32, i64, i32, P, P, i64, P]
+    L.oracle_encode_config.restype = i64
     for f in (L.oracle_rank, L.oracle_morton, L.oracle_group_cost, L.oracle_cost_table,
               L.oracle_quantize, L.oracle_preprocess, L.oracle_raht):
         f.restype = ctypes.c_int
@@ -204,3 +215,55 @@ def raht(attrs, channels, depth: int, L=None, weights: bool = False, importance=
                                     _p(nv)))
     V = int(nv[0])
     return (dc, ac[:V - 1], V, aw[:V - 1]) if weights else (dc, ac[:V - 1], V)
+
+
+def rans_lanes(n: int, L=None) -> int:
+    return int((L or lib()).oracle_rans_lanes(int(n)))
+
+
+def encode_block(codes, b: int, mn: float, mx: float, L=None) -> bytes:
+    """One (channel, group) block of codes in the block format (oracle.c)."""
+    L = L or lib()
+    c = np.ascontiguousarray(codes, dtype=np.uint16)
+    cap = int(L.oracle_block_bound(c.shape[0], int(b)))
+    out = np.zeros(cap, dtype=np.uint8)
+    sz = L.oracle_encode_block(_p(c), c.shape[0], int(b), float(mn), float(mx), _p(out), cap)
+    if sz < 0:
+        raise OracleError(int(sz))
+    return out[:sz].tobytes()
+
+
+def decode_block(buf: bytes, n: int, L=None):
+    """Inverse of encode_block: (codes, b, min, max, bytes consumed)."""
+    L = L or lib()
+    a = np.frombuffer(bytes(buf) + b"\0", dtype=np.uint8)
+    codes = np.zeros(max(int(n), 1), dtype=np.uint16)
+    b = ctypes.c_int32()
+    mn, mx = ctypes.c_float(), ctypes.c_float()
+    used = L.oracle_decode_block(_p(a), len(buf), int(n), _p(codes), ctypes.byref(b),
+                                 ctypes.byref(mn), ctypes.byref(mx))
+    if used < 0:
+        raise OracleError(int(used))
+    return codes[:n], b.value, mn.value, mx.value, int(used)
+
+
+def encode_config(attrs, importance, keep: int, G: int, q_bits: np.ndarray, L=None):
+    """Quantise one configuration and encode every (channel, group) block in
+    (c, g) order: (stream bytes, block sizes [C][n_groups])."""
+    L = L or lib()
+    a = np.ascontiguousarray(attrs, dtype=np.float32)
+    imp = np.ascontiguousarray(importance, dtype=np.float32)
+    n, C = a.shape
+    ng = n_groups(keep, G)
+    qb = np.ascontiguousarray(q_bits, dtype=np.uint8).reshape(C, ng)
+    cap = 0
+    for g in range(ng):
+        ln = min(G, keep - g * G)
+        cap += int(sum(L.oracle_block_bound(ln, int(qb[c, g])) for c in range(C)))
+    out = np.zeros(max(cap, 1), dtype=np.uint8)
+    sizes = np.zeros((C, ng), dtype=np.int64)
+    tot = L.oracle_encode_config(_p(a), _p(imp), n, C, int(keep), int(G), _p(qb), _p(out), cap,
+                                 _p(sizes))
+    if tot < 0:
+        raise OracleError(int(tot))
+    return out[:tot].tobytes(), sizes

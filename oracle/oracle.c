@@ -31,6 +31,14 @@
  *                        voxels at octree depth d (Gaussians sharing a voxel
  *                        averaged), merged pairwise along x, y, z from the
  *                        finest level up; one DC and V - 1 AC coefficients.
+ *   oracle_encode_block  Alg. 1 ("compress the model, obtain its size S_a")
+ *   oracle_decode_block  and Sec. III-G "Entropy Encoding": a lossless coder of
+ *   oracle_encode_config one (channel, group) block of codes, and of a whole
+ *                        configuration, whose byte count is the actual size
+ *                        that calibrates S_Delta of Eq. (eq:size_estim).  The
+ *                        paper codes with torchac + LZ77; the block format
+ *                        here is this library's own (static-model rANS with a
+ *                        raw fallback), written out below.
  *   oracle_preprocess    Sec. III-A (view-independent importance I_i =
  *                        V_norm^beta, joint score I_g = I_d * I_i) and the
  *                        quaternion -> Euler replacement of Sec. III-D, over
@@ -64,6 +72,8 @@
  *     DC = t1 x1 + t2 x2, AC = t1 x2 - t2 x1, weight w1 + w2; an unpaired
  *     node passes up unchanged.  ACs are listed step by step, in
  *     ascending code within a step.
+ *   - block coder (the paper names only torchac and LZ77): see the format
+ *     comment above oracle_encode_block.
  */
 #include <math.h>
 #include <stdint.h>
@@ -582,4 +592,354 @@ int oracle_raht(const float *attrs, int64_t n, int32_t n_channels, const int32_t
 done:
     free(code); free(order); free(key); free(w); free(x); free(pos); free(rank);
     return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Block coder (Alg. 1: actual size S_a; Sec. III-G entropy encoding).        */
+/* ------------------------------------------------------------------------ */
+/*
+ * Format of one (channel, group) block of n codes of b bits (little-endian):
+ *   b:u8  min:f32  max:f32                       (9 bytes of metadata)
+ *   nothing more when max - min == 0 (R = 0: every code is 0), else
+ *   mode:u8  0 = raw, 1 = rANS
+ *   raw   ceil(n b / 8) bytes; bit j of code i is stream bit i b + j, and
+ *         stream bit t is bit t % 8 of byte t / 8
+ *   rANS  table bits (same bit order), zero-padded to a whole byte:
+ *           gamma(D), then for each of the D distinct codes in ascending
+ *           order gamma(gap) and gamma(f): gap = code - previous code (the
+ *           first: code + 1), f its normalised frequency;
+ *         lanes x u32, the encoder's final states, lane 0 first;
+ *         the renormalisation bytes in the order the decoder reads them.
+ *   gamma(x), x >= 1: floor(log2 x) zero bits, then the bits of x from the
+ *   most significant down.
+ * Model: M = 2^k with k = ceil(log2 n) (so M >= n), f = floor(count M / n),
+ * and the shortfall M - sum f added to the most frequent code (the lowest
+ * such code on ties); with n a power of two f is the count itself.
+ * rANS: states in [L, 256 L), L = 2^23, byte-wise renormalisation; lane j of
+ * lanes = min(32, max(1, n / 512)) codes the symbols i = j (mod lanes).
+ * Encoding runs from the last symbol to the first: renormalise (emit the low
+ * byte while x >= 2^(31 - k) f), then x = floor(x / f) M + x mod f + cum.
+ * Decoding runs forwards: slot = x mod M, x = f (x >> k) + slot - cum, then
+ * read bytes while x < L.  The rANS payload is used when it is shorter than
+ * the raw one.
+ */
+#define ORACLE_RANS_L (1u << 23)
+
+typedef struct {
+    uint8_t *p;
+    int64_t bit;
+} oracle_bitw;
+
+static void put_bit(oracle_bitw *w, unsigned v) {
+    if (v) w->p[w->bit >> 3] |= (uint8_t)(1u << (w->bit & 7));
+    w->bit++;
+}
+
+static int floor_log2_u64(uint64_t x) {
+    int k = -1;
+    while (x) {
+        x >>= 1;
+        k++;
+    }
+    return k;
+}
+
+static void put_gamma(oracle_bitw *w, uint64_t x) {
+    int N = floor_log2_u64(x);
+    for (int i = 0; i < N; i++) put_bit(w, 0);
+    for (int j = N; j >= 0; j--) put_bit(w, (unsigned)((x >> j) & 1u));
+}
+
+static int ceil_log2_i64(int64_t n) {
+    int k = 0;
+    while (((int64_t)1 << k) < n) k++;
+    return k;
+}
+
+int32_t oracle_rans_lanes(int64_t n) {
+    int64_t l = n / 512;
+    if (l < 1) l = 1;
+    if (l > 32) l = 32;
+    return (int32_t)l;
+}
+
+int64_t oracle_block_bound(int64_t n, int32_t b) { return 10 + (n * (int64_t)b + 7) / 8; }
+
+/* Encode one block into out (at least oracle_block_bound(n, b) bytes).
+ * Returns the block's size in bytes, or a negative error. */
+int64_t oracle_encode_block(const uint16_t *codes, int64_t n, int32_t b, float mn, float mx,
+                            uint8_t *out, int64_t cap) {
+    if (n < 1 || b < 1 || b > 16 || cap < oracle_block_bound(n, b)) return ORACLE_ERR_ARG;
+    int64_t bound = oracle_block_bound(n, b);
+    memset(out, 0, (size_t)bound);
+    out[0] = (uint8_t)b;
+    memcpy(out + 1, &mn, 4);
+    memcpy(out + 5, &mx, 4);
+    const uint32_t nsym = 1u << b;
+    float R = mx - mn;
+    if (R == 0.0f) {
+        for (int64_t i = 0; i < n; i++)
+            if (codes[i] != 0) return ORACLE_ERR_ARG;
+        return 9;
+    }
+    for (int64_t i = 0; i < n; i++)
+        if (codes[i] >= nsym) return ORACLE_ERR_ARG;
+
+    int64_t raw_payload = 1 + (n * b + 7) / 8;
+    uint32_t *hist = (uint32_t *)calloc(nsym, sizeof(uint32_t));
+    uint32_t *f = (uint32_t *)calloc(nsym, sizeof(uint32_t));
+    uint32_t *cum = (uint32_t *)calloc(nsym, sizeof(uint32_t));
+    uint8_t *em = (uint8_t *)malloc((size_t)(2 * n + 8));
+    uint8_t *tab = (uint8_t *)calloc((size_t)(8 * nsym + 8), 1);
+    int64_t result;
+    if (!hist || !f || !cum || !em || !tab) {
+        result = ORACLE_ERR_NOMEM;
+        goto done;
+    }
+    for (int64_t i = 0; i < n; i++) hist[codes[i]]++;
+
+    /* normalised frequencies */
+    int k = ceil_log2_i64(n);
+    uint64_t M = (uint64_t)1 << k;
+    uint64_t fsum = 0;
+    uint32_t top = 0;
+    for (uint32_t s = 0; s < nsym; s++) {
+        f[s] = (uint32_t)(((uint64_t)hist[s] * M) / (uint64_t)n);
+        fsum += f[s];
+        if (hist[s] > hist[top]) top = s;
+    }
+    f[top] += (uint32_t)(M - fsum);
+    uint32_t run = 0;
+    for (uint32_t s = 0; s < nsym; s++) {
+        cum[s] = run;
+        run += f[s];
+    }
+
+    /* table */
+    oracle_bitw tw = {tab, 0};
+    uint64_t D = 0;
+    for (uint32_t s = 0; s < nsym; s++) D += hist[s] > 0;
+    put_gamma(&tw, D);
+    int64_t prev = -1;
+    for (uint32_t s = 0; s < nsym; s++) {
+        if (!hist[s]) continue;
+        put_gamma(&tw, (uint64_t)((int64_t)s - prev));
+        put_gamma(&tw, f[s]);
+        prev = s;
+    }
+    int64_t tab_bytes = (tw.bit + 7) / 8;
+
+    /* interleaved rANS, last symbol first */
+    int32_t lanes = oracle_rans_lanes(n);
+    uint32_t x[32];
+    for (int j = 0; j < 32; j++) x[j] = ORACLE_RANS_L;
+    int64_t E = 0;
+    for (int64_t i = n - 1; i >= 0; i--) {
+        int lane = (int)(i % lanes);
+        uint32_t s = codes[i];
+        uint64_t xmax = ((uint64_t)(ORACLE_RANS_L >> k) << 8) * f[s];
+        while ((uint64_t)x[lane] >= xmax) {
+            em[E++] = (uint8_t)(x[lane] & 0xffu);
+            x[lane] >>= 8;
+        }
+        x[lane] = (uint32_t)((x[lane] / f[s]) * M + x[lane] % f[s] + cum[s]);
+    }
+    int64_t rans_payload = 1 + tab_bytes + 4 * (int64_t)lanes + E;
+
+    if (rans_payload < raw_payload) {
+        uint8_t *p = out + 9;
+        *p++ = 1;
+        memcpy(p, tab, (size_t)tab_bytes);
+        p += tab_bytes;
+        for (int j = 0; j < lanes; j++) {
+            for (int q = 0; q < 4; q++) *p++ = (uint8_t)(x[j] >> (8 * q));
+        }
+        for (int64_t e = E - 1; e >= 0; e--) *p++ = em[e];
+        result = 9 + rans_payload;
+    } else {
+        out[9] = 0;
+        oracle_bitw rw = {out + 10, 0};
+        for (int64_t i = 0; i < n; i++)
+            for (int j = 0; j < b; j++) put_bit(&rw, (codes[i] >> j) & 1u);
+        result = 9 + raw_payload;
+    }
+done:
+    free(hist);
+    free(f);
+    free(cum);
+    free(em);
+    free(tab);
+    return result;
+}
+
+typedef struct {
+    const uint8_t *p;
+    int64_t bit;
+    int64_t nbits;
+} oracle_bitr;
+
+static int get_bit(oracle_bitr *r, unsigned *v) {
+    if (r->bit >= r->nbits) return 0;
+    *v = (r->p[r->bit >> 3] >> (r->bit & 7)) & 1u;
+    r->bit++;
+    return 1;
+}
+
+static int get_gamma(oracle_bitr *r, uint64_t *x) {
+    int N = 0;
+    unsigned v;
+    for (;;) {
+        if (!get_bit(r, &v)) return 0;
+        if (v) break;
+        if (++N > 40) return 0;
+    }
+    uint64_t val = 1;
+    for (int j = 0; j < N; j++) {
+        if (!get_bit(r, &v)) return 0;
+        val = (val << 1) | v;
+    }
+    *x = val;
+    return 1;
+}
+
+/* Decode one block of n codes from in[0 .. avail).  Returns the bytes the
+ * block occupies, or ORACLE_ERR_ARG if the block is malformed. */
+int64_t oracle_decode_block(const uint8_t *in, int64_t avail, int64_t n, uint16_t *codes,
+                            int32_t *b_out, float *mn_out, float *mx_out) {
+    if (n < 1 || avail < 9) return ORACLE_ERR_ARG;
+    int32_t b = in[0];
+    float mn, mx;
+    memcpy(&mn, in + 1, 4);
+    memcpy(&mx, in + 5, 4);
+    if (b < 1 || b > 16) return ORACLE_ERR_ARG;
+    *b_out = b;
+    *mn_out = mn;
+    *mx_out = mx;
+    float R = mx - mn;
+    if (R == 0.0f) {
+        for (int64_t i = 0; i < n; i++) codes[i] = 0;
+        return 9;
+    }
+    if (avail < 10) return ORACLE_ERR_ARG;
+    const uint32_t nsym = 1u << b;
+    if (in[9] == 0) {
+        int64_t bytes = (n * b + 7) / 8;
+        if (avail < 10 + bytes) return ORACLE_ERR_ARG;
+        oracle_bitr r = {in + 10, 0, 8 * bytes};
+        for (int64_t i = 0; i < n; i++) {
+            unsigned c = 0, v = 0;
+            for (int j = 0; j < b; j++) {
+                get_bit(&r, &v);
+                c |= v << j;
+            }
+            codes[i] = (uint16_t)c;
+        }
+        return 10 + bytes;
+    }
+    if (in[9] != 1) return ORACLE_ERR_ARG;
+    int k = ceil_log2_i64(n);
+    uint32_t M = 1u << k;
+    uint32_t *f = (uint32_t *)calloc(nsym, sizeof(uint32_t));
+    uint32_t *cum = (uint32_t *)calloc(nsym, sizeof(uint32_t));
+    uint16_t *lut = (uint16_t *)malloc(sizeof(uint16_t) * M);
+    int64_t result = ORACLE_ERR_ARG;
+    if (!f || !cum || !lut) {
+        result = ORACLE_ERR_NOMEM;
+        goto done;
+    }
+    oracle_bitr r = {in + 10, 0, 8 * (avail - 10)};
+    uint64_t D, gap, fv;
+    if (!get_gamma(&r, &D) || D < 1 || D > nsym) goto done;
+    int64_t sym = -1;
+    uint64_t total = 0;
+    for (uint64_t e = 0; e < D; e++) {
+        if (!get_gamma(&r, &gap) || !get_gamma(&r, &fv)) goto done;
+        sym += (int64_t)gap;
+        if (sym >= (int64_t)nsym || fv > M) goto done;
+        f[sym] = (uint32_t)fv;
+        total += fv;
+    }
+    if (total != M) goto done;
+    uint32_t run = 0;
+    for (uint32_t s = 0; s < nsym; s++) {
+        cum[s] = run;
+        for (uint32_t t = 0; t < f[s]; t++) lut[run + t] = (uint16_t)s;
+        run += f[s];
+    }
+    int64_t pos = 10 + (r.bit + 7) / 8;
+    int32_t lanes = oracle_rans_lanes(n);
+    if (avail < pos + 4 * lanes) goto done;
+    uint32_t x[32];
+    for (int j = 0; j < lanes; j++) {
+        x[j] = 0;
+        for (int q = 0; q < 4; q++) x[j] |= (uint32_t)in[pos++] << (8 * q);
+    }
+    for (int64_t i = 0; i < n; i++) {
+        int j = (int)(i % lanes);
+        uint32_t slot = x[j] & (M - 1);
+        uint32_t s = lut[slot];
+        codes[i] = (uint16_t)s;
+        x[j] = f[s] * (x[j] >> k) + slot - cum[s];
+        while (x[j] < ORACLE_RANS_L) {
+            if (pos >= avail) goto done;
+            x[j] = (x[j] << 8) | in[pos++];
+        }
+    }
+    for (int j = 0; j < lanes; j++)
+        if (x[j] != ORACLE_RANS_L) goto done;
+    result = pos;
+done:
+    free(f);
+    free(cum);
+    free(lut);
+    return result;
+}
+
+/*
+ * Compress one configuration: quantise (oracle_quantize) and encode every
+ * (channel, group) block in (c, g) order, appended into out[0 .. cap).
+ * block_bytes[c * n_groups + g] receives each block's size.  Returns the
+ * total bytes, or a negative error.
+ */
+int64_t oracle_encode_config(const float *attrs, const float *importance, int64_t n,
+                             int32_t n_channels, int64_t keep, int32_t G, const uint8_t *q_bits,
+                             uint8_t *out, int64_t cap, int64_t *block_bytes) {
+    if (n < 0 || keep < 1 || keep > n || G < 1 || n_channels < 1) return ORACLE_ERR_ARG;
+    int64_t ng = oracle_n_groups(keep, G);
+    uint16_t *codes = (uint16_t *)malloc(sizeof(uint16_t) * (size_t)(keep * n_channels));
+    float *minmax = (float *)malloc(sizeof(float) * (size_t)(2 * ng * n_channels));
+    int64_t total = 0;
+    if (!codes || !minmax) {
+        total = ORACLE_ERR_NOMEM;
+        goto done;
+    }
+    int rc = oracle_quantize(attrs, importance, n, n_channels, keep, G, q_bits, codes, minmax);
+    if (rc) {
+        total = rc;
+        goto done;
+    }
+    for (int32_t c = 0; c < n_channels; c++) {
+        for (int64_t g = 0; g < ng; g++) {
+            int64_t start = g * G;
+            int64_t len = keep - start < G ? keep - start : G;
+            int32_t b = q_bits[c * ng + g];
+            if (total + oracle_block_bound(len, b) > cap) {
+                total = ORACLE_ERR_ARG;
+                goto done;
+            }
+            int64_t sz = oracle_encode_block(&codes[(int64_t)c * keep + start], len, b,
+                                             minmax[(c * ng + g) * 2], minmax[(c * ng + g) * 2 + 1],
+                                             out + total, cap - total);
+            if (sz < 0) {
+                total = sz;
+                goto done;
+            }
+            block_bytes[c * ng + g] = sz;
+            total += sz;
+        }
+    }
+done:
+    free(codes);
+    free(minmax);
+    return total;
 }

@@ -337,3 +337,177 @@ def check_raht_keep(L, seed: int = 10, n: int = 3000, keep: int = 1200):
     top = np.sort(np.lexsort((np.arange(n), -imp))[:keep])     # the `keep` most important, index order
     dc2, ac2, V2 = oracle.raht(a[top], [3, 4], 9, L=L)
     assert V == V2 and np.array_equal(dc, dc2) and np.array_equal(ac, ac2)
+
+
+# ---- block coder (actual size S_a of Alg. 1) ---------------------------------
+
+RANS_L = 1 << 23
+
+
+def read_block_py(buf: bytes, n: int):
+    """Independent pure-Python reader of the block format (slow: small n).
+
+    Returns (codes, b, min, max, bytes used, table) with table = {code: f}
+    (None for raw or R = 0 blocks).  Every field is parsed from the format's
+    definition: metadata, mode byte, gamma-coded table in LSB-first bit
+    order, lane states, then the rANS bytes in decoding order.
+    """
+    import struct
+    b = buf[0]
+    mn, mx = struct.unpack("<ff", bytes(buf[1:9]))
+    if np.float32(mx) - np.float32(mn) == np.float32(0.0):
+        return [0] * n, b, mn, mx, 9, None
+    mode = buf[9]
+    bits = [(byte >> t) & 1 for byte in buf[10:] for t in range(8)]
+    if mode == 0:
+        codes = [sum(bits[i * b + j] << j for j in range(b)) for i in range(n)]
+        return codes, b, mn, mx, 10 + (n * b + 7) // 8, None
+    assert mode == 1, mode
+    pos = 0
+
+    def gamma():
+        nonlocal pos
+        zeros = 0
+        while bits[pos] == 0:
+            zeros += 1
+            pos += 1
+        v = 0
+        for _ in range(zeros + 1):
+            v = 2 * v + bits[pos]
+            pos += 1
+        return v
+
+    table = {}
+    sym = -1
+    for _ in range(gamma()):
+        sym += gamma()
+        table[sym] = gamma()
+    k = (n - 1).bit_length()
+    M = 1 << k
+    assert sum(table.values()) == M and max(table) < (1 << b)
+    cum, run = {}, 0
+    for s in sorted(table):
+        cum[s] = run
+        run += table[s]
+    at = 10 + (pos + 7) // 8
+    lanes = min(32, max(1, n // 512))
+    x = []
+    for j in range(lanes):
+        x.append(int.from_bytes(bytes(buf[at:at + 4]), "little"))
+        at += 4
+    codes = []
+    for i in range(n):
+        j = i % lanes
+        slot = x[j] % M
+        s = next(s for s in table if cum[s] <= slot < cum[s] + table[s])
+        codes.append(s)
+        x[j] = table[s] * (x[j] // M) + slot - cum[s]
+        while x[j] < RANS_L:
+            x[j] = x[j] * 256 + buf[at]
+            at += 1
+    assert all(v == RANS_L for v in x), "final states are not L"
+    return codes, b, mn, mx, at, table
+
+
+def gamma_len(x: int) -> int:
+    return 2 * (int(x).bit_length() - 1) + 1
+
+
+def coder_cases(seed: int):
+    """Blocks with the codes of real quantised groups (Laplacian, Gaussian and
+    two-level data), a uniform block that must fall back to raw, and sizes
+    around the lane and precision boundaries."""
+    rng = np.random.default_rng(seed)
+    for n in (2, 3, 100, 511, 512, 1000, 1024, 1537, 2048):
+        for b in (1, 2, 3, 5, 8, 12, 16):
+            kind = (n + b) % 3
+            if kind == 0:
+                v = rng.laplace(0.0, 0.05, n)
+            elif kind == 1:
+                v = rng.normal(-4.0, 1.0, n)
+            else:
+                v = rng.choice([-1.0, 0.25, 3.0], n, p=[0.7, 0.2, 0.1]) + rng.normal(0, 1e-3, n)
+            out = oracle.group_cost(v.astype(np.float32), [b], want_codes=True)
+            yield out["codes"][0], b, out["vmin"], out["vmax"]
+    yield rng.integers(0, 1 << 16, 600).astype(np.uint16), 16, -1.0, 1.0
+
+
+def check_coder_roundtrip(L, seed: int = 11):
+    """Every block decodes, by the independent reader and by the oracle's own
+    decoder, to the codes it was made from, and uses exactly its bytes."""
+    saw_raw = saw_rans = False
+    for codes, b, mn, mx in coder_cases(seed):
+        n = codes.shape[0]
+        blk = oracle.encode_block(codes, b, mn, mx, L=L)
+        got, gb, gmn, gmx, used, table = read_block_py(blk, n)
+        assert used == len(blk) and gb == b and np.float32(gmn) == np.float32(mn)
+        assert np.array_equal(np.asarray(got, dtype=np.uint16), codes), (n, b)
+        got2, _, _, _, used2 = oracle.decode_block(blk, n, L=L)
+        assert used2 == len(blk) and np.array_equal(got2, codes)
+        raw = 10 + (n * b + 7) // 8
+        assert len(blk) <= raw
+        if table is None:
+            assert len(blk) == raw
+            saw_raw = True
+        else:
+            saw_rans = True
+    assert saw_raw and saw_rans
+    const = oracle.encode_block(np.zeros(37, np.uint16), 7, 2.5, 2.5, L=L)
+    assert len(const) == 9 and read_block_py(const, 37)[0] == [0] * 37
+
+
+def check_coder_entropy(L, seed: int = 12):
+    """With n a power of two the normalised frequencies are the counts, so the
+    ideal code length of the static model is the entropy bound H of the cost
+    table (n * -sum p log2 p).  rANS with states in [2^23, 2^31) and byte
+    renormalisation then spends, over its lanes' states and bytes, between
+    24 and 32 bits per lane above H, up to a rounding loss of at most
+    -log2(1 - M / 2^23) bits per symbol; the table costs exactly the gamma
+    code lengths of D, the gaps and the frequencies."""
+    rng = np.random.default_rng(seed)
+    for n in (1024, 4096, 16384):
+        for b in (2, 4, 8, 12):
+            v = rng.laplace(0.0, 0.05, n).astype(np.float32)
+            out = oracle.group_cost(v, [b], want_codes=True)
+            codes = out["codes"][0]
+            blk = oracle.encode_block(codes, b, out["vmin"], out["vmax"], L=L)
+            if blk[9] == 0:          # the table of a wide, short block outweighs its gain
+                assert b >= 12 and n <= 4096, (n, b)
+                continue
+            counts = np.bincount(codes.astype(np.int64), minlength=1 << b)
+            used = np.nonzero(counts)[0]
+            tbits = gamma_len(len(used))
+            prev = -1
+            for s in used:
+                tbits += gamma_len(int(s) - prev) + gamma_len(int(counts[s]))
+                prev = int(s)
+            lanes = min(32, max(1, n // 512))
+            payload = 8 * (len(blk) - 10 - (tbits + 7) // 8)
+            k = (n - 1).bit_length()
+            eps = n * -math.log2(1.0 - 2.0 ** (k - 23)) + 1e-6
+            over = payload - out["hbits"][0]
+            assert 24 * lanes - eps < over <= 32 * lanes + eps, (n, b, over, lanes)
+
+
+def check_coder_normalisation(L):
+    """n not a power of two: f = floor(count M / n), the shortfall going to the
+    most frequent code, the lowest one on ties; the table read back agrees."""
+    rng = np.random.default_rng(13)
+    for n in (600, 1000, 3000, 5000):
+        codes = np.minimum(rng.geometric(0.05, n) - 1, 255).astype(np.uint16)
+        codes[:2] = [0, 255]
+        blk = oracle.encode_block(codes, 8, -1.0, 1.0, L=L)
+        assert blk[9] == 1
+        table = read_block_py(blk, n)[5]
+        counts = np.bincount(codes.astype(np.int64), minlength=256)
+        M = 1 << (n - 1).bit_length()
+        expect = {int(s): int(counts[s]) * M // n for s in np.nonzero(counts)[0]}
+        top = int(np.argmax(counts))
+        expect[top] += M - sum(expect.values())
+        assert table == expect, n
+    # n = 707, M = 1024, counts 300, 300, 100, 7: floors 434, 434, 144, 10 sum to
+    # 1022; codes 0 and 1 tie for the most frequent and the lower one takes the 2
+    codes = np.array([0] * 300 + [1] * 300 + [2] * 100 + [3] * 7, dtype=np.uint16)
+    blk = oracle.encode_block(codes, 2, 0.0, 1.0, L=L)
+    assert blk[9] == 1
+    assert read_block_py(blk, 707)[5] == {0: 436, 1: 434, 2: 144, 3: 10}

@@ -43,6 +43,19 @@ MUTANTS = {
     "raht_mean_not_divided": ("x[m * n_c + k] = q - p > 1 ? sum / (double)(q - p) : sum;",
                               "x[m * n_c + k] = sum;"),
     "raht_weight_not_summed": ("w[out] = w[i] + w[i + 1];", "w[out] = w[i];"),
+    "rans_cum_dropped": ("x[lane] = (uint32_t)((x[lane] / f[s]) * M + x[lane] % f[s] + cum[s]);",
+                         "x[lane] = (uint32_t)((x[lane] / f[s]) * M + x[lane] % f[s]);"),
+    "rans_lane_reversed": ("int lane = (int)(i % lanes);", "int lane = (int)((n - 1 - i) % lanes);"),
+    "rans_renorm_threshold": ("uint64_t xmax = ((uint64_t)(ORACLE_RANS_L >> k) << 8) * f[s];",
+                              "uint64_t xmax = ((uint64_t)(ORACLE_RANS_L >> k) << 7) * f[s];"),
+    "gamma_lsb_first": ("for (int j = N; j >= 0; j--) put_bit(w, (unsigned)((x >> j) & 1u));",
+                        "for (int j = 0; j <= N; j++) put_bit(w, (unsigned)((x >> j) & 1u));"),
+    "raw_bit_order": ("for (int j = 0; j < b; j++) put_bit(&rw, (codes[i] >> j) & 1u);",
+                      "for (int j = 0; j < b; j++) put_bit(&rw, (codes[i] >> (b - 1 - j)) & 1u);"),
+    "shortfall_to_last_tie": ("if (hist[s] > hist[top]) top = s;", "if (hist[s] >= hist[top]) top = s;"),
+    "mode_choice_inverted": ("if (rans_payload < raw_payload) {", "if (rans_payload > raw_payload) {"),
+    "frequency_not_scaled": ("f[s] = (uint32_t)(((uint64_t)hist[s] * M) / (uint64_t)n);",
+                             "f[s] = hist[s];"),
     "raht_keep_ignored": ("        K = oracle_kept(rank, order, n, keep, pos);",
                           "        for (int64_t t = 0; t < n; t++) pos[t] = t;"),
 }
@@ -73,6 +86,9 @@ checks = [
     lambda: pins.check_raht_orthonormal(L),
     lambda: pins.check_raht_constant_and_dedup(L),
     lambda: pins.check_raht_keep(L),
+    lambda: pins.check_coder_roundtrip(L),
+    lambda: pins.check_coder_entropy(L),
+    lambda: pins.check_coder_normalisation(L),
 ]
 failed = 0
 for c in checks:

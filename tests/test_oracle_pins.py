@@ -191,3 +191,40 @@ def test_raht_constant_and_dedup():
 
 def test_raht_kept_set():
     pins.check_raht_keep(oracle.lib())
+
+
+def test_coder_roundtrip_independent_reader():
+    pins.check_coder_roundtrip(oracle.lib())
+
+
+def test_coder_size_against_entropy_bound():
+    pins.check_coder_entropy(oracle.lib())
+
+
+def test_coder_frequency_normalisation():
+    pins.check_coder_normalisation(oracle.lib())
+
+
+def test_encode_config_concatenates_blocks():
+    """A whole configuration: blocks in (channel, group) order, each readable
+    on its own and equal to the block of that group's quantised codes."""
+    from paper_2604_26799_gb300 import synth
+    attrs, imp = synth.make_scene(3000, seed=21)
+    attrs = attrs[:, :6].copy()
+    keep, G = 2100, 512
+    ng = oracle.n_groups(keep, G)
+    rng = np.random.default_rng(5)
+    q_bits = rng.integers(1, 17, size=(6, ng)).astype(np.uint8)
+    stream, sizes = oracle.encode_config(attrs, imp, keep, G, q_bits)
+    codes, minmax = oracle.quantize(attrs, imp, keep, G, q_bits)
+    at = 0
+    for c in range(6):
+        for g in range(ng):
+            n = min(G, keep - g * G)
+            blk = stream[at:at + int(sizes[c, g])]
+            got, b, mn, mx, used, _ = pins.read_block_py(blk, n)
+            assert used == len(blk) and b == q_bits[c, g]
+            assert np.array_equal(np.asarray(got, np.uint16), codes[c, g * G:g * G + n])
+            assert np.float32(mn) == minmax[c, g, 0] and np.float32(mx) == minmax[c, g, 1]
+            at += len(blk)
+    assert at == len(stream) == int(sizes.sum())
