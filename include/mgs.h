@@ -387,6 +387,108 @@ mgs_status mgs_quantize_groups_noalloc(mgs_ctx *ctx, const mgs_scene *scene, int
                                        int32_t group_size, const uint8_t *bits, uint16_t *codes,
                                        float *minmax, void *stream);
 
+/* ---- block coder: the actual size of a configuration -------------------- */
+
+/*
+ * Compress one configuration and measure it: Alg. 1's "compress the model
+ * with the current hyperparameters, obtain its size S_a", with entropy coding
+ * as in Sec. III-G (the paper codes with torchac + LZ77; this block format is
+ * the library's own).  The kept set of `keep` Gaussians (Sec. III-A, Morton
+ * order) is cut into groups of group_size, each (channel, group) is quantised
+ * with bits[c * n_groups + g] (1..16, host or device memory) exactly as
+ * mgs_quantize_groups does, and each block of n codes is written as
+ *
+ *   b:u8  min:f32  max:f32            metadata (9 bytes, little-endian)
+ *   nothing more when max - min == 0  (R = 0: every code is 0), else
+ *   mode:u8                           0 = raw, 1 = rANS (the shorter one; raw on ties)
+ *   raw:  ceil(n b / 8) bytes: bit j of code i is stream bit i b + j, and
+ *         stream bit t is bit t % 8 of byte t / 8
+ *   rANS: the table's bits (same order), zero-padded to a byte:
+ *           gamma(D), then per distinct code in ascending order gamma(gap)
+ *           and gamma(f), gap = code - previous code (first: code + 1);
+ *         lanes x u32: the encoder's final states, lane 0 first;
+ *         the renormalisation bytes in the order a decoder reads them.
+ *   gamma(x), x >= 1: floor(log2 x) zero bits, then x's bits from the top.
+ *
+ * Model: M = 2^ceil(log2 n); f = floor(count * M / n), and M - sum f is added
+ * to the most frequent code (the lowest one on ties).  rANS: states in
+ * [2^23, 2^31), byte renormalisation (emit the low byte while
+ * x >= 2^(31 - log2 M) * f, then x = floor(x / f) M + x mod f + cum);
+ * lanes = min(32, max(1, n / 512)) interleaved states, lane j coding the
+ * symbols i = j (mod lanes); encoding runs from the last symbol to the first.
+ *
+ * Blocks are concatenated in (channel, group) order.  stream (device memory,
+ * `capacity` bytes; may be NULL to measure only) receives them;
+ * block_bytes[c * n_groups + g] (host or device, may be NULL) each block's
+ * size; *total_bytes (host) the stream's length.  The call allocates its
+ * workspace on `stream` and synchronises it.  Errors: INVALID_ARG (a width
+ * outside 1..16, keep or group_size out of range, capacity too small: the
+ * needed length is still returned in *total_bytes), OUT_OF_MEMORY, CUDA.
+ */
+mgs_status mgs_encode_config(mgs_ctx *ctx, const mgs_scene *scene, int64_t keep,
+                             int32_t group_size, const uint8_t *bits, uint8_t *stream,
+                             int64_t capacity, int32_t *block_bytes, int64_t *total_bytes,
+                             void *cuda_stream);
+/* Largest stream mgs_encode_config can write: C * (10 * n_groups + 2 * keep)
+ * bytes (-1 for invalid arguments). */
+int64_t mgs_encode_bound(int64_t keep, int32_t group_size, int32_t n_channels);
+
+/* ---- Alg. 1 with real compression: the S_Delta calibration loop ---------- */
+
+typedef struct {
+    double budget_bytes;   /* S_T */
+    double tolerance;      /* stop once |S_a - S_T| / S_T < tolerance (Alg. 1: 0.05) */
+    int32_t max_rounds;    /* ILP + compression rounds per ratio after the first compression */
+    int32_t init_bits;     /* Alg. 1's initial width (8); with MGS_RATE_ENTROPY it must be
+                              one of the grid's widths */
+    mgs_solve_opts solve;  /* rate model (MGS_RATE_FIXED: Eq. (eq:size_estim)'s sum P Q),
+                              norm, const_bytes (C, added to every actual size too),
+                              meta_bytes_per_group; delta_bytes is ignored (calibrated) */
+} mgs_calib_opts;
+
+/*
+ * Result of mgs_search_calibrated.  Arrays are caller-provided and may be NULL:
+ *   bits[n_channels * n_groups[r_index]]  the chosen widths (capacity: the
+ *                          largest ratio's n_channels * n_groups)
+ *   ratio_status[n_ratios] 0 converged, 1 skipped (twice the initial size is
+ *                          under the budget: tau too small), 2 not converged in
+ *                          max_rounds, -1 infeasible
+ *   ratio_rounds           compressions run for the ratio
+ *   ratio_actual           its last actual size S_a (bytes, coded + const_bytes)
+ *   ratio_delta            its last S_Delta
+ *   ratio_objective        Omega of its last ILP solution
+ */
+typedef struct {
+    int32_t r_index;       /* chosen ratio; -1 if none converged */
+    int32_t rounds;        /* compressions run in total */
+    double actual_bytes;   /* S_a of the chosen configuration */
+    double est_bytes;      /* its calibrated estimate (Eq. (eq:size_estim) with S_Delta) */
+    double objective;      /* its Omega */
+    uint8_t *bits;
+    int32_t *ratio_status;
+    int32_t *ratio_rounds;
+    double *ratio_actual;
+    double *ratio_delta;
+    double *ratio_objective;
+} mgs_calib_result;
+
+/*
+ * Alg. 1 with real compression.  For each ratio r (grid order): compress with
+ * every width init_bits (mgs_encode_config's coder) to get S_a; skip r when
+ * 2 S_a < S_T; otherwise repeat up to max_rounds times: S_Delta = S_a minus
+ * the estimate (Eq. (eq:size_estim) without S_Delta) of the configuration just
+ * compressed; solve Eq. (eq:ilp) for r alone with that S_Delta (the device
+ * solver); compress the solution; stop once |S_a - S_T| / S_T < tolerance.
+ * Among the converged ratios the smallest Omega wins (ties: the larger
+ * ratio).  `table` is the scene's cost table for `grid` (device memory, laid
+ * out by `layout`).  Synchronises `stream`.  INFEASIBLE if no ratio
+ * converged (the per-ratio arrays are still filled); INVALID_ARG for
+ * mismatched grid, layout and scene or bad options.
+ */
+mgs_status mgs_search_calibrated(mgs_ctx *ctx, const mgs_scene *scene, const mgs_grid *grid,
+                                 const void *table, const mgs_table_layout *layout,
+                                 const mgs_calib_opts *opts, mgs_calib_result *out, void *stream);
+
 /* ---- serving ------------------------------------------------------------ */
 
 /*
@@ -483,6 +585,23 @@ mgs_status mgs_solve_budget(const void *table, const mgs_table_layout *layout,
 mgs_status mgs_solve_budgets(const void *table, const mgs_table_layout *layout,
                              const mgs_grid *grid, int32_t n_budgets, const double *budgets,
                              const mgs_solve_opts *opts, mgs_solution *out);
+
+/*
+ * The paper's hierarchical solve of Eq. (eq:ilp) (Sec. III-F "Hierarchical
+ * Solver"), per ratio: (1) one width per channel, from the multiple-choice
+ * knapsack whose items are the channels (a channel's option sums its groups'
+ * losses, in the chosen norm, and rates; its metadata is its groups'); (2)
+ * channel budgets S_c = A * Q_c / sum_c Q_c, A = budget - const_bytes -
+ * delta_bytes; (3) per channel, the knapsack over its groups within S_c.
+ * Every knapsack is the flat solver's (mgs_solve_budgets).  A ratio is
+ * infeasible when step (1) or any channel's step (3) is.  tau is picked as by
+ * mgs_solve_budget; out->choice and the per-ratio arrays are filled the same
+ * way (ratio_lp_bound holds the sum of the channels' LP bounds).  `table` is
+ * host memory.
+ */
+mgs_status mgs_solve_hierarchical(const void *table, const mgs_table_layout *layout,
+                                  const mgs_grid *grid, double budget_bytes,
+                                  const mgs_solve_opts *opts, mgs_solution *out);
 
 /*
  * mgs_solve_budgets on the device: the same answers bit for bit (the

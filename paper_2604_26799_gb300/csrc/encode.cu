@@ -1,0 +1,557 @@
+// Block coder of one chosen configuration: the actual compressed size S_a of
+// Alg. 1 ("compress the model with the current hyperparameters, obtain its
+// size") and the entropy coding of Sec. III-G, with this library's own block
+// format (static-model rANS with a raw fallback; the format is written out in
+// include/mgs.h above mgs_encode_config).
+//
+// Pipeline (all on `stream`): kept list -> quantise (quantize.cu) -> k_encode,
+// one CTA per (channel, group) block writing into a fixed-size slot ->
+// exclusive scan of the block sizes -> k_enc_gather, which packs the slots
+// into one contiguous stream in (channel, group) order.
+//
+// k_encode per block: stage the codes in shared memory; count them in
+// windows of 4096 codes (16 windows at b = 16, empty windows skipped) and
+// list the distinct codes in ascending order; normalise the counts to
+// M = 2^ceil(log2 n); lay out the gamma-coded table by a block-wide scan of
+// its bit lengths; run the interleaved rANS encoder in one warp (lane j owns
+// symbols i = j mod lanes; the bytes a step emits are ordered by two ballots
+// and written from the end of the stream); then write whichever payload is
+// shorter.
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "internal.h"
+
+namespace mgs {
+namespace {
+
+constexpr int kEncThreads = 128;
+constexpr int kEncWarps = kEncThreads / 32;
+constexpr uint32_t kRansL = 1u << 23;   // states live in [L, 2^31)
+constexpr int kWin = 4096;              // histogram window (codes)
+constexpr int kScanChunk = 1024;        // sizes per CTA of the scan
+
+__host__ __device__ inline int64_t a16(int64_t x) { return (x + 15) & ~(int64_t)15; }
+
+// Shared-memory layout of k_encode for group size G.
+struct EncSmem {
+    int64_t codes, hist, sym, f, cum, em, tab, total;
+    __host__ __device__ explicit EncSmem(int G) {
+        codes = 0;                            // uint16[G]
+        hist = codes + a16(2 * (int64_t)G);   // uint32[kWin] (also the code -> entry map)
+        sym = hist + 4 * kWin;                // uint16[G]: distinct codes, ascending
+        f = sym + a16(2 * (int64_t)G);        // uint16[G]: normalised frequencies (cnt first)
+        cum = f + a16(2 * (int64_t)G);        // uint16[G]
+        em = cum + a16(2 * (int64_t)G);       // uint8[2G + 16]: rANS bytes in emission order
+        tab = em + a16(2 * (int64_t)G + 16);  // uint32 words: the table's bits
+        total = tab + a16(2 * (int64_t)G + 16);
+    }
+};
+
+__device__ __forceinline__ int glen(uint32_t x) { return 2 * (31 - __clz(x)) + 1; }
+
+// Exclusive scan over the CTA of one 64-bit value per thread; *total gets the sum.
+__device__ uint64_t block_excl_scan(uint64_t v, uint64_t *total, uint64_t *s_warp) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint64_t inc = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        uint64_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) s_warp[w] = inc;
+    __syncthreads();
+    uint64_t base = 0, all = 0;
+    for (int k = 0; k < kEncWarps; k++) {
+        if (k < w) base += s_warp[k];
+        all += s_warp[k];
+    }
+    __syncthreads();
+    *total = all;
+    return base + inc - v;
+}
+
+// Writes gamma(x) at bit p of the zeroed word buffer (LSB-first bit order).
+__device__ __forceinline__ void put_gamma(uint32_t *tab, int64_t p, uint32_t x) {
+    const int N = 31 - __clz(x);
+    p += N;   // N zero bits
+    for (int u = 0; u <= N; u++, p++)
+        if ((x >> (N - u)) & 1u) atomicOr(&tab[p >> 5], 1u << (p & 31));
+}
+
+__global__ void __launch_bounds__(kEncThreads)
+    k_encode(const uint16_t *__restrict__ codes, int64_t K, int32_t G, int32_t ng,
+             const uint8_t *__restrict__ bits, const float *__restrict__ minmax,
+             uint8_t *__restrict__ slots, int64_t slot_bytes, int32_t *__restrict__ sizes) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ uint64_t s_warp[kEncWarps];
+    __shared__ uint32_t s_wcnt[16];
+    __shared__ uint32_t s_state[32];
+    __shared__ int s_D, s_E;
+    __shared__ uint32_t s_top;
+
+    const EncSmem L(G);
+    uint16_t *s_codes = reinterpret_cast<uint16_t *>(smem + L.codes);
+    uint32_t *s_hist = reinterpret_cast<uint32_t *>(smem + L.hist);
+    uint16_t *s_sym = reinterpret_cast<uint16_t *>(smem + L.sym);
+    uint16_t *s_f = reinterpret_cast<uint16_t *>(smem + L.f);
+    uint16_t *s_cum = reinterpret_cast<uint16_t *>(smem + L.cum);
+    uint8_t *s_em = smem + L.em;
+    uint32_t *s_tab = reinterpret_cast<uint32_t *>(smem + L.tab);
+
+    const int64_t blk = blockIdx.x;
+    const int c = (int)(blk / ng), g = (int)(blk % ng);
+    const int64_t start = (int64_t)g * G;
+    const int n = (int)((K - start) < (int64_t)G ? (K - start) : (int64_t)G);
+    const int b = bits[blk];
+    const float mn = minmax[2 * blk], mx = minmax[2 * blk + 1];
+    uint8_t *out = slots + blk * slot_bytes;
+    const int t = threadIdx.x;
+
+    if (t < 9) {
+        uint32_t v = t == 0 ? (uint32_t)b : __float_as_uint(t < 5 ? mn : mx) >> (8 * ((t - 1) & 3));
+        out[t] = (uint8_t)v;
+    }
+    if (__fsub_rn(mx, mn) == 0.0f) {   // R = 0: every code is 0, metadata only
+        if (t == 0) sizes[blk] = 9;
+        return;
+    }
+
+    // ---- stage the codes; per-window counts when b > 12 ----
+    const int logW = b < 12 ? b : 12;
+    const int W = 1 << logW;
+    const int nwin = 1 << (b - logW);
+    if (t < 16) s_wcnt[t] = 0;
+    __syncthreads();
+    const uint16_t *src = codes + (int64_t)c * K + start;
+    for (int i = t; i < n; i += kEncThreads) {
+        uint16_t q = src[i];
+        s_codes[i] = q;
+        if (nwin > 1) atomicAdd(&s_wcnt[q >> 12], 1u);
+    }
+    if (t == 0) s_D = 0;
+    __syncthreads();
+
+    // ---- distinct codes (ascending) with their counts ----
+    const int per = (W + kEncThreads - 1) / kEncThreads;
+    for (int w = 0; w < nwin; w++) {
+        if (nwin > 1 && s_wcnt[w] == 0) continue;   // uniform: s_wcnt is settled
+        for (int i = t; i < W; i += kEncThreads) s_hist[i] = 0;
+        __syncthreads();
+        for (int i = t; i < n; i += kEncThreads) {
+            uint32_t q = s_codes[i];
+            if ((int)(q >> logW) == w) atomicAdd(&s_hist[q & (W - 1)], 1u);
+        }
+        __syncthreads();
+        const int lo = t * per, hi = min(W, lo + per);
+        uint32_t mine = 0;
+        for (int i = lo; i < hi; i++) mine += s_hist[i] != 0;
+        uint64_t tot;
+        uint64_t at = (uint64_t)s_D + block_excl_scan(mine, &tot, s_warp);
+        for (int i = lo; i < hi; i++) {
+            uint32_t h = s_hist[i];
+            if (h) {
+                s_sym[at] = (uint16_t)((w << logW) + i);
+                s_f[at] = (uint16_t)h;   // count for now
+                if (nwin == 1) s_hist[i] = (uint32_t)at;   // code -> entry map
+                at++;
+            }
+        }
+        __syncthreads();
+        if (t == 0) s_D += (int)tot;
+        __syncthreads();
+    }
+    const int D = s_D;
+
+    // ---- normalised frequencies: floor(cnt M / n), shortfall to the most frequent ----
+    const int k = 32 - __clz((unsigned)(n - 1));   // ceil(log2 n); n >= 2 here
+    const uint32_t M = 1u << k;
+    uint64_t fsum = 0;
+    uint32_t best = 0;   // (count << 16) | (65535 - entry): max = most frequent, lowest code
+    for (int e = t; e < D; e += kEncThreads) {
+        uint32_t cnt = s_f[e];
+        uint32_t fv = (uint32_t)(((uint64_t)cnt * M) / (uint32_t)n);
+        fsum += fv;
+        best = max(best, (cnt << 16) | (uint32_t)(65535 - e));
+        s_f[e] = (uint16_t)fv;
+    }
+    if (t == 0) s_top = 0;
+    __syncthreads();
+    for (int o = 16; o > 0; o >>= 1) {
+        fsum += __shfl_xor_sync(0xFFFFFFFFu, fsum, o);
+        best = max(best, __shfl_xor_sync(0xFFFFFFFFu, best, o));
+    }
+    if ((t & 31) == 0) {
+        s_warp[t >> 5] = fsum;
+        atomicMax(&s_top, best);
+    }
+    __syncthreads();
+    if (t == 0) {
+        uint64_t all = 0;
+        for (int w = 0; w < kEncWarps; w++) all += s_warp[w];
+        const int top = 65535 - (int)(s_top & 0xFFFFu);
+        s_f[top] = (uint16_t)(s_f[top] + (uint32_t)(M - all));
+    }
+    __syncthreads();
+
+    // ---- cumulative frequencies and table bit offsets (one chunk of entries per thread) ----
+    const int eper = (D + kEncThreads - 1) / kEncThreads;
+    const int e0 = min(D, t * eper), e1 = min(D, e0 + eper);
+    uint32_t fl = 0, bl = 0;
+    for (int e = e0; e < e1; e++) {
+        uint32_t gap = e == 0 ? (uint32_t)s_sym[0] + 1u : (uint32_t)(s_sym[e] - s_sym[e - 1]);
+        fl += s_f[e];
+        bl += glen(gap) + glen(s_f[e]);
+    }
+    uint64_t tot2;
+    const uint64_t pre = block_excl_scan(((uint64_t)fl << 32) | bl, &tot2, s_warp);
+    const int64_t tbits = glen((uint32_t)D) + (int64_t)(tot2 & 0xFFFFFFFFu);
+    {
+        uint32_t run = (uint32_t)(pre >> 32);
+        for (int e = e0; e < e1; e++) {
+            s_cum[e] = (uint16_t)run;
+            run += s_f[e];
+        }
+    }
+
+    // ---- decide whether rANS can beat the raw payload ----
+    const int lanes = min(32, max(1, n >> 9));
+    const int64_t raw_payload = 1 + ((int64_t)n * b + 7) / 8;
+    const int64_t tab_bytes = (tbits + 7) / 8;
+    const int64_t e_cap = raw_payload - 1 - tab_bytes - 4 * (int64_t)lanes;   // rANS iff E < e_cap
+    const bool try_rans = e_cap > 0;
+    __syncthreads();
+
+    if (try_rans && t < 32) {
+        const int j = t;
+        uint32_t x = kRansL;
+        int64_t base = 0;
+        const uint32_t above = ~((2u << j) - 1u);   // lanes > j (0 for j = 31)
+        const uint32_t xunit = 1u << (31 - k);      // (L >> k) << 8
+        const int steps = (n + lanes - 1) / lanes;
+        for (int st = steps - 1; st >= 0; st--) {
+            const int i = st * lanes + j;
+            int cnt = 0;
+            uint32_t b1 = 0, b2 = 0;
+            if (j < lanes && i < n) {
+                const uint32_t s = s_codes[i];
+                int e;
+                if (nwin == 1) {
+                    e = (int)s_hist[s];
+                } else {
+                    int lo = 0, hi = D - 1;
+                    while (lo < hi) {
+                        int mid = (lo + hi) >> 1;
+                        if (s_sym[mid] < s) lo = mid + 1;
+                        else hi = mid;
+                    }
+                    e = lo;
+                }
+                const uint32_t fs = s_f[e], cs = s_cum[e];
+                const uint64_t xmax = (uint64_t)xunit * fs;
+                if (x >= xmax) {
+                    b1 = x & 0xFFu;
+                    x >>= 8;
+                    cnt = 1;
+                    if (x >= xmax) {
+                        b2 = x & 0xFFu;
+                        x >>= 8;
+                        cnt = 2;
+                    }
+                }
+                x = (x / fs) * M + x % fs + cs;
+            }
+            const uint32_t m1 = __ballot_sync(0xFFFFFFFFu, cnt >= 1);
+            const uint32_t m2 = __ballot_sync(0xFFFFFFFFu, cnt == 2);
+            const int64_t idx = base + __popc(m1 & above) + __popc(m2 & above);
+            if (cnt >= 1 && idx < e_cap) s_em[idx] = (uint8_t)b1;
+            if (cnt == 2 && idx + 1 < e_cap) s_em[idx + 1] = (uint8_t)b2;
+            base += __popc(m1) + __popc(m2);
+        }
+        s_state[j] = x;
+        if (j == 0) s_E = (int)(base < e_cap ? base : e_cap);   // e_cap: rANS lost
+    }
+    __syncthreads();
+    const int64_t E = try_rans ? s_E : e_cap;
+    const bool rans = try_rans && E < e_cap;
+
+    if (rans) {
+        const int64_t words = (tab_bytes + 3) / 4;
+        for (int64_t q = t; q < words; q += kEncThreads) s_tab[q] = 0;
+        __syncthreads();
+        if (t == 0) put_gamma(s_tab, 0, (uint32_t)D);
+        int64_t p = glen((uint32_t)D) + (int64_t)(pre & 0xFFFFFFFFu);
+        for (int e = e0; e < e1; e++) {
+            uint32_t gap = e == 0 ? (uint32_t)s_sym[0] + 1u : (uint32_t)(s_sym[e] - s_sym[e - 1]);
+            put_gamma(s_tab, p, gap);
+            p += glen(gap);
+            put_gamma(s_tab, p, s_f[e]);
+            p += glen(s_f[e]);
+        }
+        __syncthreads();
+        if (t == 0) out[9] = 1;
+        const uint8_t *tb = reinterpret_cast<const uint8_t *>(s_tab);
+        for (int64_t q = t; q < tab_bytes; q += kEncThreads) out[10 + q] = tb[q];
+        uint8_t *st = out + 10 + tab_bytes;
+        for (int q = t; q < 4 * lanes; q += kEncThreads) st[q] = (uint8_t)(s_state[q >> 2] >> (8 * (q & 3)));
+        uint8_t *eb = st + 4 * lanes;
+        for (int64_t q = t; q < E; q += kEncThreads) eb[q] = s_em[E - 1 - q];
+        if (t == 0) sizes[blk] = (int32_t)(9 + 1 + tab_bytes + 4 * lanes + E);
+    } else {
+        if (t == 0) out[9] = 0;
+        // 32 stream bits per thread step: the codes overlapping bits [32 wq, 32 wq + 32)
+        const int nb = (int)(raw_payload - 1);
+        const int nwords = (nb + 3) / 4;
+        for (int wq = t; wq < nwords; wq += kEncThreads) {
+            const int lo = 32 * wq;
+            const int i0 = lo / b, i1 = min(n - 1, (lo + 31) / b);
+            uint64_t v = 0;
+            for (int i = i0; i <= i1; i++) {
+                const int p = i * b - lo;
+                const uint64_t q = s_codes[i];
+                v |= p >= 0 ? q << p : q >> (-p);
+            }
+            for (int u = 0; u < 4 && 4 * wq + u < nb; u++) out[10 + 4 * wq + u] = (uint8_t)(v >> (8 * u));
+        }
+        if (t == 0) sizes[blk] = (int32_t)(9 + raw_payload);
+    }
+}
+
+// Exclusive scan of int32 sizes into int64 offsets: per-chunk sums, one CTA
+// over the chunk sums, then the per-chunk scan with its base.
+__global__ void __launch_bounds__(1024)
+    k_enc_chunk_sums(const int32_t *__restrict__ sizes, int64_t m, int64_t *__restrict__ sums) {
+    __shared__ int64_t s[32];
+    const int64_t i = (int64_t)blockIdx.x * kScanChunk + threadIdx.x;
+    int64_t v = i < m ? sizes[i] : 0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t a = 0;
+        for (int w = 0; w < 32; w++) a += s[w];
+        sums[blockIdx.x] = a;
+    }
+}
+
+__global__ void __launch_bounds__(1024)
+    k_enc_scan_sums(int64_t *__restrict__ sums, int64_t nchunks, int64_t *__restrict__ total) {
+    __shared__ int64_t s[32];
+    __shared__ int64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < nchunks; base += 1024) {
+        const int64_t i = base + threadIdx.x;
+        const int64_t v = i < nchunks ? sums[i] : 0;
+        int64_t inc = v;
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        for (int o = 1; o < 32; o <<= 1) {
+            int64_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) s[w] = inc;
+        __syncthreads();
+        int64_t wb = 0, all = 0;
+        for (int k = 0; k < 32; k++) {
+            if (k < w) wb += s[k];
+            all += s[k];
+        }
+        if (i < nchunks) sums[i] = carry + wb + inc - v;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += all;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void __launch_bounds__(1024)
+    k_enc_offsets(const int32_t *__restrict__ sizes, int64_t m, const int64_t *__restrict__ sums,
+                  int64_t *__restrict__ off) {
+    __shared__ int64_t s[32];
+    const int64_t i = (int64_t)blockIdx.x * kScanChunk + threadIdx.x;
+    const int64_t v = i < m ? sizes[i] : 0;
+    int64_t inc = v;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int o = 1; o < 32; o <<= 1) {
+        int64_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) s[w] = inc;
+    __syncthreads();
+    int64_t wb = 0;
+    for (int k = 0; k < w; k++) wb += s[k];
+    if (i < m) off[i] = sums[blockIdx.x] + wb + inc - v;
+}
+
+// Packs each block's slot into the stream at its offset.
+__global__ void __launch_bounds__(256)
+    k_enc_gather(const uint8_t *__restrict__ slots, int64_t slot_bytes,
+                 const int32_t *__restrict__ sizes, const int64_t *__restrict__ off,
+                 uint8_t *__restrict__ stream) {
+    const int64_t blk = blockIdx.x;
+    const uint8_t *src = slots + blk * slot_bytes;
+    uint8_t *dst = stream + off[blk];
+    const int sz = sizes[blk];
+    for (int q = threadIdx.x; q < sz; q += 256) dst[q] = src[q];
+}
+
+}  // namespace
+
+int64_t encode_bound(int64_t keep, int32_t G, int32_t C) {
+    const int64_t ng = n_groups_of(keep, G);
+    return (int64_t)C * (10 * ng + 2 * keep);
+}
+
+mgs_status encode_launch(mgs_ctx *ctx, const mgs_scene *sc, const int32_t *kept, int64_t keep,
+                         int32_t G, const uint8_t *d_bits, uint8_t *stream, int64_t capacity,
+                         int32_t *d_sizes_out, int64_t *total_out, cudaStream_t st) {
+    const int64_t ng = n_groups_of(keep, G);
+    const int64_t m = ng * sc->C;
+    if (m > 0x7FFFFFFFLL) {
+        set_error("%lld blocks exceed one launch", (long long)m);
+        return MGS_ERR_INVALID_ARG;
+    }
+    const int64_t slot_bytes = a16(10 + 2 * (int64_t)G);
+    const int64_t nchunks = (m + kScanChunk - 1) / kScanChunk;
+    const size_t b_codes = (size_t)a16(2 * keep * sc->C), b_mm = (size_t)a16(8 * m);
+    const size_t b_slots = (size_t)(m * slot_bytes), b_sizes = (size_t)a16(4 * m);
+    const size_t b_off = (size_t)a16(8 * m), b_sums = (size_t)a16(8 * (nchunks + 1));
+    unsigned char *ws = nullptr;
+    const size_t ws_bytes = b_codes + b_mm + b_slots + b_sizes + b_off + b_sums;
+    if (cudaMallocAsync(reinterpret_cast<void **>(&ws), ws_bytes, st) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("encoder workspace of %zu bytes", ws_bytes);
+        return MGS_ERR_OUT_OF_MEMORY;
+    }
+    uint16_t *d_codes = reinterpret_cast<uint16_t *>(ws);
+    float *d_mm = reinterpret_cast<float *>(ws + b_codes);
+    uint8_t *d_slots = ws + b_codes + b_mm;
+    int32_t *d_sizes = reinterpret_cast<int32_t *>(d_slots + b_slots);
+    int64_t *d_off = reinterpret_cast<int64_t *>(reinterpret_cast<unsigned char *>(d_sizes) + b_sizes);
+    int64_t *d_sums = reinterpret_cast<int64_t *>(reinterpret_cast<unsigned char *>(d_off) + b_off);
+
+    mgs_status s = quantize_launch(ctx, sc, kept, keep, G, d_bits, d_codes, d_mm, st);
+    int64_t total = 0;
+    if (s == MGS_OK && m > 0) {
+        const EncSmem L(G);
+        const size_t smem = (size_t)L.total;
+        cudaError_t e = cudaFuncSetAttribute(k_encode, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e == cudaSuccess) {
+            k_encode<<<(unsigned)m, kEncThreads, smem, st>>>(d_codes, keep, G, (int32_t)ng, d_bits,
+                                                             d_mm, d_slots, slot_bytes, d_sizes);
+            k_enc_chunk_sums<<<(unsigned)nchunks, 1024, 0, st>>>(d_sizes, m, d_sums);
+            k_enc_scan_sums<<<1, 1024, 0, st>>>(d_sums, nchunks, d_sums + nchunks);
+            k_enc_offsets<<<(unsigned)nchunks, 1024, 0, st>>>(d_sizes, m, d_sums, d_off);
+            count_launches(4);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&total, d_sums + nchunks, 8, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            set_error("block coder: %s", cudaGetErrorString(e));
+            s = MGS_ERR_CUDA;
+        }
+        if (s == MGS_OK && stream) {
+            if (capacity < total) {
+                set_error("stream capacity %lld < %lld bytes", (long long)capacity, (long long)total);
+                s = MGS_ERR_INVALID_ARG;
+            } else {
+                k_enc_gather<<<(unsigned)m, 256, 0, st>>>(d_slots, slot_bytes, d_sizes, d_off, stream);
+                count_launches(1);
+                e = cudaGetLastError();
+                if (e != cudaSuccess) {
+                    set_error("block gather: %s", cudaGetErrorString(e));
+                    s = MGS_ERR_CUDA;
+                }
+            }
+        }
+        if (s == MGS_OK && d_sizes_out) {
+            e = cudaMemcpyAsync(d_sizes_out, d_sizes, 4 * (size_t)m, cudaMemcpyDefault, st);
+            if (e != cudaSuccess) {
+                set_error("block sizes copy: %s", cudaGetErrorString(e));
+                s = MGS_ERR_CUDA;
+            }
+        }
+    }
+    cudaFreeAsync(ws, st);
+    if (s == MGS_OK) {
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            set_error("block coder: %s", cudaGetErrorString(e));
+            s = MGS_ERR_CUDA;
+        }
+    }
+    *total_out = total;
+    return s;
+}
+
+}  // namespace mgs
+
+extern "C" int64_t mgs_encode_bound(int64_t keep, int32_t group_size, int32_t n_channels) {
+    if (keep < 1 || group_size < 1 || n_channels < 1) return -1;
+    return mgs::encode_bound(keep, group_size, n_channels);
+}
+
+extern "C" mgs_status mgs_encode_config(mgs_ctx *ctx, const mgs_scene *scene, int64_t keep,
+                                        int32_t group_size, const uint8_t *bits, uint8_t *stream,
+                                        int64_t capacity, int32_t *block_bytes,
+                                        int64_t *total_bytes, void *cuda_stream) {
+    using namespace mgs;
+    clear_error();
+    if (!ctx || !scene || !bits || !total_bytes) {
+        set_error("ctx, scene, bits and total_bytes must be non-NULL");
+        return MGS_ERR_INVALID_ARG;
+    }
+    if (keep < 1 || keep > scene->n || group_size < 1 || group_size > MGS_MAX_GROUP) {
+        set_error("keep %lld or group_size %d out of range", (long long)keep, group_size);
+        return MGS_ERR_INVALID_ARG;
+    }
+    if (stream && !is_device_pointer(stream)) {
+        set_error("stream must be device memory");
+        return MGS_ERR_INVALID_ARG;
+    }
+    DeviceGuard dg(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const int64_t m = n_groups_of(keep, group_size) * scene->C;
+    // the widths on the device, checked to lie in 1..16
+    std::vector<uint8_t> hb((size_t)m);
+    MGS_CUDA_TRY(cudaMemcpyAsync(hb.data(), bits, (size_t)m, cudaMemcpyDefault, st));
+    MGS_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int64_t i = 0; i < m; i++) {
+        if (hb[i] < 1 || hb[i] > 16) {
+            set_error("bits[%lld] = %d is not in 1..16", (long long)i, (int)hb[i]);
+            return MGS_ERR_INVALID_ARG;
+        }
+    }
+    uint8_t *d_bits = nullptr;
+    MGS_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void **>(&d_bits), (size_t)m, st));
+    cudaError_t e = cudaMemcpyAsync(d_bits, hb.data(), (size_t)m, cudaMemcpyHostToDevice, st);
+    mgs_scene *sc = const_cast<mgs_scene *>(scene);
+    mgs_scene tmp_owner;   // a one-ratio kept list; the scene's cached lists are left alone
+    tmp_owner.ctx = sc->ctx;
+    tmp_owner.n = sc->n;
+    tmp_owner.C = sc->C;
+    tmp_owner.d_rank_m = sc->d_rank_m;
+    mgs_status s = MGS_OK;
+    if (e != cudaSuccess) {
+        set_error("bits copy: %s", cudaGetErrorString(e));
+        s = MGS_ERR_CUDA;
+    }
+    const int32_t *pos = nullptr;
+    std::vector<int64_t> off;
+    if (s == MGS_OK) s = scene_kept(&tmp_owner, &keep, 1, st, &pos, &off);
+    if (s == MGS_OK)
+        s = encode_launch(ctx, sc, pos, keep, group_size, d_bits, stream, capacity, block_bytes,
+                          total_bytes, st);
+    if (tmp_owner.kept.pos) cudaFreeAsync(tmp_owner.kept.pos, st);
+    tmp_owner.kept.pos = nullptr;
+    tmp_owner.d_rank_m = nullptr;
+    cudaFreeAsync(d_bits, st);
+    cudaError_t e2 = cudaStreamSynchronize(st);
+    if (s == MGS_OK && e2 != cudaSuccess) {
+        set_error("encode: %s", cudaGetErrorString(e2));
+        s = MGS_ERR_CUDA;
+    }
+    return s;
+}

@@ -179,6 +179,17 @@ mgs_status quantize_launch(mgs_ctx *ctx, const mgs_scene *scene, const int32_t *
                            int32_t G, const uint8_t *bits, uint16_t *codes, float *minmax,
                            cudaStream_t st);
 
+// ---- block coder (encode.cu) ----
+// Upper bound of a configuration's stream: C * (10 * n_groups + 2 * keep) bytes.
+int64_t encode_bound(int64_t keep, int32_t G, int32_t C);
+// Quantise with d_bits (device, [C][n_groups], each in 1..16) and encode every
+// block; writes the stream when `stream` is non-NULL (capacity checked), the
+// block sizes when d_sizes_out is non-NULL, and the total into *total_out.
+// Synchronises `st`.
+mgs_status encode_launch(mgs_ctx *ctx, const mgs_scene *sc, const int32_t *kept, int64_t keep,
+                         int32_t G, const uint8_t *d_bits, uint8_t *stream, int64_t capacity,
+                         int32_t *d_sizes_out, int64_t *total_out, cudaStream_t st);
+
 // ---- helpers (abi.cu) ----
 // Count kernels enqueued by this library (mgs_kernel_launches()).
 void count_launches(int64_t k);

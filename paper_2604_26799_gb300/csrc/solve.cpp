@@ -362,4 +362,156 @@ mgs_status mgs_solve_budget(const void *table, const mgs_table_layout *layout,
     return mgs_solve_budgets(table, layout, grid, 1, &budget_bytes, opts, out);
 }
 
+// Sec. III-F "Hierarchical Solver": per ratio, (1) one width per channel from
+// the MCKP over channels (each channel an item whose options sum its groups'
+// loss and rate), (2) the channel budgets S_c = A Q_c / sum Q_c of the bytes A
+// left after C and S_Delta, (3) per channel the MCKP over its groups within
+// S_c.  Every sub-problem is the flat solver's.  tau as in mgs_solve_budgets.
+mgs_status mgs_solve_hierarchical(const void *table, const mgs_table_layout *layout,
+                                  const mgs_grid *grid, double budget_bytes,
+                                  const mgs_solve_opts *opts, mgs_solution *out) {
+    clear_error();
+    if (!table || !layout || !grid || !opts || !out) {
+        set_error("table, layout, grid, opts and out must be non-NULL");
+        return MGS_ERR_INVALID_ARG;
+    }
+    if (grid->n_bits != layout->n_bits || grid->n_ratios != layout->n_ratios ||
+        opts->rate_model < 0 || opts->rate_model > 1 || opts->norm < 0 || opts->norm > 3 ||
+        !(budget_bytes >= 0) || layout->n_channels < 1) {
+        set_error("grid/layout mismatch, bad options or budget");
+        return MGS_ERR_INVALID_ARG;
+    }
+    const View v = make_view(table, layout, grid, opts);
+    const int nr = layout->n_ratios, nb = layout->n_bits, C = layout->n_channels;
+    struct Res {
+        int status = -1;
+        double objective = 0, bytes = 0, lp = 0, bytes_top = 0;
+        std::vector<uint8_t> choice;
+    };
+    std::vector<Res> res(nr);
+    for (int r = 0; r < nr; r++) {
+        const int64_t ng = layout->n_groups[r], ib = layout->item_begin[r];
+        Res &R = res[r];
+        // all-top size, for the tau rule
+        int64_t top_units = 0;
+        for (int64_t i = ib; i < ib + C * ng; i++)
+            top_units += rate_units(v.rate_model, v.hbits[i * nb + nb - 1], v.cnt[i], v.bits[nb - 1]);
+        R.bytes_top = units_to_bytes(top_units, opts->meta_bytes_per_group * (double)(C * ng) +
+                                                    opts->const_bytes + opts->delta_bytes);
+        // (1) channel level: a table of C items
+        int64_t one = 1;
+        mgs_grid g1 = *grid;
+        g1.n_ratios = 1;
+        g1.keep = &one;
+        g1.group_size = 1;
+        mgs_table_layout l1;
+        MGS_TRY(mgs_table_layout_for(1, C, &g1, &l1));
+        std::vector<unsigned char> buf((size_t)l1.total_bytes, 0);
+        double *csse = reinterpret_cast<double *>(buf.data() + l1.off_sse);
+        double *chb = reinterpret_cast<double *>(buf.data() + l1.off_hbits);
+        int32_t *ccnt = reinterpret_cast<int32_t *>(buf.data() + l1.off_count);
+        for (int c = 0; c < C; c++) {
+            int64_t n_c = 0;
+            for (int64_t g = 0; g < ng; g++) {
+                const int64_t it = ib + c * ng + g;
+                n_c += v.cnt[it];
+                for (int k = 0; k < nb; k++) {
+                    csse[c * nb + k] += dist(v, it, k);
+                    chb[c * nb + k] += v.hbits[it * nb + k];
+                }
+            }
+            ccnt[c] = (int32_t)n_c;
+        }
+        mgs_solve_opts o1 = *opts;
+        o1.norm = MGS_NORM_SSE;   // the channel items carry the chosen norm's sums
+        o1.meta_bytes_per_group = opts->meta_bytes_per_group * (double)ng;
+        std::vector<uint8_t> qc((size_t)C);
+        mgs_solution s1{};
+        s1.choice = qc.data();
+        mgs_status st = mgs_solve_budgets(buf.data(), &l1, &g1, 1, &budget_bytes, &o1, &s1);
+        if (st == MGS_ERR_INFEASIBLE || s1.r_index < 0) continue;
+        MGS_TRY(st);
+        // (2) channel budgets
+        double qsum = 0;
+        for (int c = 0; c < C; c++) qsum += grid->bits[qc[c]];
+        const double A = budget_bytes - opts->const_bytes - opts->delta_bytes;
+        // (3) group level per channel
+        R.choice.assign((size_t)(C * ng), 0);
+        bool ok = true;
+        int64_t keep_r = grid->keep[r];
+        for (int c = 0; c < C && ok; c++) {
+            mgs_table_layout lv = *layout;
+            const int64_t base = ib + c * ng;
+            lv.n_ratios = 1;
+            lv.n_channels = 1;
+            lv.n_items = ng;
+            lv.item_begin[0] = 0;
+            lv.item_begin[1] = ng;
+            lv.n_groups[0] = ng;
+            lv.off_sse += 8 * base * nb;
+            lv.off_l1 += 8 * base * nb;
+            lv.off_hbits += 8 * base * nb;
+            lv.off_linf += 4 * base * nb;
+            lv.off_count += 4 * base;
+            lv.off_vmin += 4 * base;
+            lv.off_vmax += 4 * base;
+            mgs_grid gv = *grid;
+            gv.n_ratios = 1;
+            gv.keep = &keep_r;
+            mgs_solve_opts o2 = *opts;
+            o2.const_bytes = 0;
+            o2.delta_bytes = 0;
+            const double S_c = A * (double)grid->bits[qc[c]] / qsum;
+            mgs_solution s2{};
+            s2.choice = R.choice.data() + c * ng;
+            st = mgs_solve_budgets(table, &lv, &gv, 1, &S_c, &o2, &s2);
+            if (st == MGS_ERR_INFEASIBLE || s2.r_index < 0) {
+                ok = false;
+                break;
+            }
+            MGS_TRY(st);
+            R.objective += s2.objective;
+            R.bytes += s2.est_bytes;
+            R.lp += s2.lp_bound;
+        }
+        clear_error();
+        if (!ok) {
+            R.choice.clear();
+            R.objective = R.bytes = R.lp = 0;
+            continue;
+        }
+        R.bytes += opts->const_bytes + opts->delta_bytes;
+        R.status = 0;
+    }
+    // tau rule (Alg. 1), as in mgs_solve_budgets
+    int best = -1, largest_feasible = -1;
+    for (int r = 0; r < nr; r++) {
+        if (res[r].status < 0) continue;
+        largest_feasible = r;
+        if (res[r].bytes_top < budget_bytes) {
+            res[r].status = 1;
+            continue;
+        }
+        if (best < 0 || res[r].objective <= res[best].objective) best = r;
+    }
+    if (best < 0) best = largest_feasible;
+    for (int r = 0; r < nr; r++) {
+        if (out->ratio_status) out->ratio_status[r] = res[r].status;
+        if (out->ratio_objective) out->ratio_objective[r] = res[r].objective;
+        if (out->ratio_bytes) out->ratio_bytes[r] = res[r].bytes;
+        if (out->ratio_lp_bound) out->ratio_lp_bound[r] = res[r].lp;
+    }
+    out->r_index = best;
+    if (best < 0) {
+        out->est_bytes = out->objective = out->lp_bound = 0;
+        set_error("no ratio fits a budget of %.0f bytes", budget_bytes);
+        return MGS_ERR_INFEASIBLE;
+    }
+    out->est_bytes = res[best].bytes;
+    out->objective = res[best].objective;
+    out->lp_bound = res[best].lp;
+    if (out->choice) std::memcpy(out->choice, res[best].choice.data(), res[best].choice.size());
+    return MGS_OK;
+}
+
 }  // extern "C"

@@ -63,6 +63,21 @@ class mgs_solution(ctypes.Structure):
                 ("ratio_lp_bound", ctypes.c_void_p)]
 
 
+class mgs_calib_opts(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_double), ("tolerance", ctypes.c_double),
+                ("max_rounds", ctypes.c_int32), ("init_bits", ctypes.c_int32),
+                ("solve", mgs_solve_opts)]
+
+
+class mgs_calib_result(ctypes.Structure):
+    _fields_ = [("r_index", ctypes.c_int32), ("rounds", ctypes.c_int32),
+                ("actual_bytes", ctypes.c_double), ("est_bytes", ctypes.c_double),
+                ("objective", ctypes.c_double), ("bits", ctypes.c_void_p),
+                ("ratio_status", ctypes.c_void_p), ("ratio_rounds", ctypes.c_void_p),
+                ("ratio_actual", ctypes.c_void_p), ("ratio_delta", ctypes.c_void_p),
+                ("ratio_objective", ctypes.c_void_p)]
+
+
 class mgs_server_opts(ctypes.Structure):
     _fields_ = [("max_jobs", ctypes.c_int32), ("solver_threads", ctypes.c_int32),
                 ("hbm_budget_bytes", ctypes.c_int64), ("slice_items", ctypes.c_int64)]
@@ -124,15 +139,21 @@ _SIGS = {
                          ctypes.POINTER(mgs_solution)],
     "mgs_solve_budgets": [_P, ctypes.POINTER(mgs_table_layout), ctypes.POINTER(mgs_grid),
                           ctypes.c_int32, _P, ctypes.POINTER(mgs_solve_opts), _P],
+    "mgs_solve_hierarchical": [_P, ctypes.POINTER(mgs_table_layout), ctypes.POINTER(mgs_grid),
+                               ctypes.c_double, ctypes.POINTER(mgs_solve_opts), _P],
     "mgs_build_cost_table_coeffs": [_P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(mgs_grid), _P, _P],
     "mgs_raht": [_P, _P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _P, _P, _P, _P],
     "mgs_preprocess": [_P, _P, _P, ctypes.c_int64, ctypes.c_double, _P, _P, _P, _P],
+    "mgs_encode_config": [_P, _P, ctypes.c_int64, ctypes.c_int32, _P, _P, ctypes.c_int64, _P, _P, _P],
+    "mgs_encode_bound": [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32],
+    "mgs_search_calibrated": [_P, _P, ctypes.POINTER(mgs_grid), _P, ctypes.POINTER(mgs_table_layout),
+                              ctypes.POINTER(mgs_calib_opts), ctypes.POINTER(mgs_calib_result), _P],
     "mgs_solve_budgets_device": [_P, _P, ctypes.POINTER(mgs_table_layout), ctypes.POINTER(mgs_grid),
                                  ctypes.c_int32, _P, ctypes.POINTER(mgs_solve_opts), _P, _P],
 }
 _RESTYPE = {"mgs_last_error": ctypes.c_char_p, "mgs_version": ctypes.c_char_p,
             "mgs_tile_config_name": ctypes.c_char_p, "mgs_tile_config_count": ctypes.c_int32,
-            "mgs_kernel_launches": ctypes.c_int64}
+            "mgs_kernel_launches": ctypes.c_int64, "mgs_encode_bound": ctypes.c_int64}
 
 
 def lib():
@@ -260,6 +281,24 @@ def mgs_quantize_groups(ctx: int, scene: int, keep: int, group_size: int, bits, 
                         stream=None):
     _check(lib().mgs_quantize_groups(ctx, scene, keep, group_size, _ptr(bits), _ptr(codes),
                                      _ptr(minmax), _stream(stream)))
+
+
+def mgs_encode_bound(keep: int, group_size: int, n_channels: int) -> int:
+    return int(lib().mgs_encode_bound(int(keep), int(group_size), int(n_channels)))
+
+
+def mgs_encode_config(ctx: int, scene: int, keep: int, group_size: int, bits, stream_out=None,
+                      block_bytes=None, stream=None) -> int:
+    """Encode one configuration (bits [C, n_groups] uint8, host or device) into
+    stream_out (a device uint8 tensor, or None to measure only); block_bytes
+    (int32 [C, n_groups], host or device) receives each block's size.
+    Returns the stream's length in bytes."""
+    total = ctypes.c_int64()
+    cap = 0 if stream_out is None else int(stream_out.numel())
+    _check(lib().mgs_encode_config(ctx, scene, int(keep), int(group_size), _ptr(bits),
+                                   _ptr(stream_out), cap, _ptr(block_bytes),
+                                   ctypes.addressof(total), _stream(stream)))
+    return total.value
 
 
 def mgs_plan_create(ctx: int, scenes: list[int], grids, tables: list, use_graph: bool = False,
@@ -396,11 +435,52 @@ def mgs_solve_budgets(table_host, layout: mgs_table_layout, grid: Grid, budgets,
     return _solve_many(lambda *a: lib().mgs_solve_budgets(_ptr(table_host), *a), layout, grid, budgets, opts)
 
 
+def mgs_solve_hierarchical(table_host, layout: mgs_table_layout, grid: "Grid", budget_bytes: float,
+                           opts: mgs_solve_opts) -> dict:
+    """The hierarchical (channel, then group) solve of Sec. III-F on a host table."""
+    return _solve_many(lambda lay, g, nb, bud, o, sols: lib().mgs_solve_hierarchical(
+        _ptr(table_host), lay, g, ctypes.c_double.from_address(bud).value, o, sols),
+        layout, grid, [budget_bytes], opts)[0]
+
+
 def mgs_solve_budgets_device(ctx: int, table, layout: mgs_table_layout, grid: Grid, budgets, opts,
                              stream=None) -> list[dict]:
     """mgs_solve_budgets computed on the device; `table` may be a device tensor or host array."""
     return _solve_many(lambda *a: lib().mgs_solve_budgets_device(ctx, _ptr(table), *a, _stream(stream)),
                        layout, grid, budgets, opts)
+
+
+def mgs_search_calibrated(ctx: int, scene: int, grid: "Grid", table, layout: mgs_table_layout,
+                          budget_bytes: float, tolerance: float = 0.05, max_rounds: int = 8,
+                          init_bits: int = 8, opts: mgs_solve_opts | None = None,
+                          stream=None) -> dict:
+    """Alg. 1 with real compression (see mgs.h).  `table` is the scene's device
+    cost table for `grid`.  The default estimator is Eq. (eq:size_estim)'s
+    linear sum P Q (MGS_RATE_FIXED).  Returns the chosen ratio, its widths
+    [C, n_groups] and the per-ratio record; r_index is -1 when no ratio
+    converged."""
+    if opts is None:
+        opts = solve_opts(rate_model=MGS_RATE_FIXED)
+    nr = layout.n_ratios
+    C = layout.n_channels
+    max_items = max(int(layout.item_begin[r + 1] - layout.item_begin[r]) for r in range(nr))
+    bits = np.zeros(max(max_items, 1), dtype=np.uint8)
+    st = np.zeros(nr, dtype=np.int32)
+    rounds = np.zeros(nr, dtype=np.int32)
+    act, dl, ob = np.zeros(nr), np.zeros(nr), np.zeros(nr)
+    res = mgs_calib_result(-1, 0, 0.0, 0.0, 0.0, bits.ctypes.data, st.ctypes.data, rounds.ctypes.data,
+                           act.ctypes.data, dl.ctypes.data, ob.ctypes.data)
+    co = mgs_calib_opts(float(budget_bytes), float(tolerance), int(max_rounds), int(init_bits), opts)
+    rc = lib().mgs_search_calibrated(ctx, scene, ctypes.byref(grid.c), _ptr(table), ctypes.byref(layout),
+                                     ctypes.byref(co), ctypes.byref(res), _stream(stream))
+    if rc not in (MGS_OK, -6):
+        _check(rc)
+    r = res.r_index
+    ng = int(layout.n_groups[r]) if r >= 0 else 0
+    return dict(r_index=r, rounds=res.rounds, actual_bytes=res.actual_bytes, est_bytes=res.est_bytes,
+                objective=res.objective, bits=bits[:C * ng].reshape(C, ng).copy() if r >= 0 else None,
+                ratio_status=st, ratio_rounds=rounds, ratio_actual=act, ratio_delta=dl,
+                ratio_objective=ob)
 
 
 def _solve_many(call, layout: mgs_table_layout, grid: Grid, budgets, opts) -> list[dict]:
