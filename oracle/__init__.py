@@ -5,8 +5,10 @@ bench.py's CPU-baseline leg.  The product path (the package and its CUDA
 library) never imports it, and it imports nothing from the product.
 
   oracle.c   C reference of the quantiser, entropy bound, Morton order, ranks,
-             of the preprocessing (importance I_g, Euler angles), RAHT and the
-             block coder that gives a configuration's actual size
+             of the preprocessing (importance I_g, Euler angles), RAHT, the
+             block coder that gives a configuration's actual size, and the
+             vector quantisation of the SH coefficients (assignment, mini-batch
+             k-means)
              (compiled with gcc -O2 -ffp-contract=off, no fast-math)
   mckp.py    exact references of the 0-1 ILP (brute force, DP) and the tau rule
 """
@@ -68,6 +70,10 @@ def load(path: str):
     L.oracle_decode_block.restype = i64
     L.oracle_encode_config.argtypes = [P, P, i64, i32, i64, i32, P, P, i64, P]
     L.oracle_encode_config.restype = i64
+    L.oracle_vq_assign.argtypes = [P, i64, i32, P, i32, P, P]
+    L.oracle_vq_update.argtypes = [P, i64, i32, P, i32, P, P, i32, P]
+    for f in (L.oracle_vq_assign, L.oracle_vq_update):
+        f.restype = ctypes.c_int
     for f in (L.oracle_rank, L.oracle_morton, L.oracle_group_cost, L.oracle_cost_table,
               L.oracle_quantize, L.oracle_preprocess, L.oracle_raht):
         f.restype = ctypes.c_int
@@ -267,3 +273,34 @@ def encode_config(attrs, importance, keep: int, G: int, q_bits: np.ndarray, L=No
     if tot < 0:
         raise OracleError(int(tot))
     return out[:tot].tobytes(), sizes
+
+
+def vq_assign(x, codebook, L=None):
+    """Nearest codebook entry per row of x [n, D]: (index int32 [n], score f32 [n])."""
+    L = L or lib()
+    xa = np.ascontiguousarray(x, dtype=np.float32)
+    cb = np.ascontiguousarray(codebook, dtype=np.float32)
+    n, D = xa.shape
+    idx = np.empty(max(n, 1), dtype=np.int32)
+    sc = np.empty(max(n, 1), dtype=np.float32)
+    _check(L.oracle_vq_assign(_p(xa), n, D, _p(cb), cb.shape[0], _p(idx), _p(sc)))
+    return idx[:n], sc[:n]
+
+
+def vq_train(x, codebook, batches, counts=None, L=None):
+    """Mini-batch k-means: one update per row of `batches` [iters, b] (row indices
+    into x).  Returns (codebook, counts, assignments [iters, b])."""
+    L = L or lib()
+    xa = np.ascontiguousarray(x, dtype=np.float32)
+    cb = np.array(codebook, dtype=np.float32, copy=True, order="C")
+    K, D = cb.shape
+    cnt = np.zeros(K, dtype=np.int64) if counts is None else np.array(counts, dtype=np.int64, copy=True)
+    bt = np.ascontiguousarray(batches, dtype=np.int32).reshape(-1, np.shape(batches)[-1])
+    asg = np.empty(bt.shape, dtype=np.int32)
+    for t in range(bt.shape[0]):
+        row = np.ascontiguousarray(bt[t])
+        out = np.empty(max(row.shape[0], 1), dtype=np.int32)
+        _check(L.oracle_vq_update(_p(xa), xa.shape[0], D, _p(cb), K, _p(cnt), _p(row), row.shape[0],
+                                  _p(out)))
+        asg[t] = out[:row.shape[0]]
+    return cb, cnt, asg

@@ -39,6 +39,11 @@
  *                        paper codes with torchac + LZ77; the block format
  *                        here is this library's own (static-model rANS with a
  *                        raw fallback), written out below.
+ *   oracle_vq_assign     Sec. III-D "Clustering 1+D SH Coefficients": the
+ *   oracle_vq_update     nearest codebook entry of each vector, and one
+ *                        batch of the batched (mini-batch) k-means the paper
+ *                        cites: each centre moves to the running mean of
+ *                        every vector ever assigned to it.
  *   oracle_preprocess    Sec. III-A (view-independent importance I_i =
  *                        V_norm^beta, joint score I_g = I_d * I_i) and the
  *                        quaternion -> Euler replacement of Sec. III-D, over
@@ -74,6 +79,14 @@
  *     ascending code within a step.
  *   - block coder (the paper names only torchac and LZ77): see the format
  *     comment above oracle_encode_block.
+ *   - vector quantisation: the score of centre k for vector x is
+ *     fl(|c_k|^2 - 2 x.c_k) (|x|^2 dropped: it does not change the argmin),
+ *     both sums accumulated by fmaf over the dimensions in ascending order;
+ *     the smallest score wins, ties to the lower k.  The mini-batch update
+ *     of a centre with count v and the m batch vectors assigned to it is
+ *     c = (v c + sum x) / (v + m), the sum taken in FP64 in batch order and
+ *     the result rounded once to FP32; this is the per-vector update with
+ *     learning rate 1/count carried out exactly over one batch.
  */
 #include <math.h>
 #include <stdint.h>
@@ -942,4 +955,84 @@ done:
     free(codes);
     free(minmax);
     return total;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Vector quantisation of the 1+D SH coefficients (Sec. III-D).               */
+/* ------------------------------------------------------------------------ */
+
+/* Nearest codebook entry of each of the n vectors x[i][0..D).  idx_out[i]
+ * gets the entry, score_out[i] (may be NULL) its score fl(|c|^2 - 2 x.c). */
+int oracle_vq_assign(const float *x, int64_t n, int32_t D, const float *cb, int32_t K,
+                     int32_t *idx_out, float *score_out) {
+    if (n < 0 || D < 1 || K < 1) return ORACLE_ERR_ARG;
+    float *cc = (float *)malloc(sizeof(float) * (size_t)K);
+    if (!cc) return ORACLE_ERR_NOMEM;
+    for (int32_t k = 0; k < K; k++) {
+        float s = 0.0f;
+        for (int32_t d = 0; d < D; d++) s = fmaf(cb[(int64_t)k * D + d], cb[(int64_t)k * D + d], s);
+        cc[k] = s;
+    }
+    for (int64_t i = 0; i < n; i++) {
+        const float *xi = x + i * D;
+        int32_t best = 0;
+        float best_s = 0.0f;
+        for (int32_t k = 0; k < K; k++) {
+            float dot = 0.0f;
+            for (int32_t d = 0; d < D; d++) dot = fmaf(xi[d], cb[(int64_t)k * D + d], dot);
+            float score = fmaf(-2.0f, dot, cc[k]);
+            if (k == 0 || score < best_s) {
+                best = k;
+                best_s = score;
+            }
+        }
+        idx_out[i] = best;
+        if (score_out) score_out[i] = best_s;
+    }
+    free(cc);
+    return ORACLE_OK;
+}
+
+/* One batch of the mini-batch k-means: the vectors x[rows[j]] (j = 0..b-1)
+ * are assigned to their nearest centre, then every centre moves to the mean
+ * of all vectors assigned to it so far: c = (v c + sum x) / (v + m), with the
+ * count v updated to v + m.  cb [K][D] and counts [K] are updated in place;
+ * assign_out[j] (may be NULL) gets the batch's assignment. */
+int oracle_vq_update(const float *x, int64_t n, int32_t D, float *cb, int32_t K, int64_t *counts,
+                     const int32_t *rows, int32_t b, int32_t *assign_out) {
+    if (n < 1 || D < 1 || K < 1 || b < 0) return ORACLE_ERR_ARG;
+    for (int32_t j = 0; j < b; j++)
+        if (rows[j] < 0 || rows[j] >= n) return ORACLE_ERR_ARG;
+    float *xb = (float *)calloc((size_t)(b > 0 ? b : 1) * D, sizeof(float));
+    int32_t *a = (int32_t *)malloc(sizeof(int32_t) * (size_t)(b > 0 ? b : 1));
+    double *sum = (double *)calloc((size_t)K * D, sizeof(double));
+    int64_t *m = (int64_t *)calloc((size_t)K, sizeof(int64_t));
+    int rc = ORACLE_OK;
+    if (!xb || !a || !sum || !m) {
+        rc = ORACLE_ERR_NOMEM;
+        goto done;
+    }
+    for (int32_t j = 0; j < b; j++) memcpy(xb + (int64_t)j * D, x + (int64_t)rows[j] * D, sizeof(float) * D);
+    rc = oracle_vq_assign(xb, b, D, cb, K, a, NULL);
+    if (rc) goto done;
+    for (int32_t j = 0; j < b; j++) {   /* batch order */
+        m[a[j]]++;
+        for (int32_t d = 0; d < D; d++) sum[(int64_t)a[j] * D + d] += (double)xb[(int64_t)j * D + d];
+    }
+    for (int32_t k = 0; k < K; k++) {
+        if (!m[k]) continue;
+        double v = (double)counts[k];
+        for (int32_t d = 0; d < D; d++) {
+            double num = v * (double)cb[(int64_t)k * D + d] + sum[(int64_t)k * D + d];
+            cb[(int64_t)k * D + d] = (float)(num / (v + (double)m[k]));
+        }
+        counts[k] += m[k];
+    }
+    if (assign_out) memcpy(assign_out, a, sizeof(int32_t) * (size_t)b);
+done:
+    free(xb);
+    free(a);
+    free(sum);
+    free(m);
+    return rc;
 }

@@ -511,3 +511,93 @@ def check_coder_normalisation(L):
     blk = oracle.encode_block(codes, 2, 0.0, 1.0, L=L)
     assert blk[9] == 1
     assert read_block_py(blk, 707)[5] == {0: 436, 1: 434, 2: 144, 3: 10}
+
+
+# ---- vector quantisation of the 1+D SH coefficients -------------------------
+
+def vq_data(seed: int, n: int, K: int, D: int = 45, spread: float = 1.0, noise: float = 0.02):
+    """K well-separated centres in [-spread, spread]^D and n vectors drawn
+    around them (the source centre of each is returned too)."""
+    rng = np.random.default_rng(seed)
+    cent = rng.uniform(-spread, spread, size=(K, D)).astype(np.float32)
+    src = rng.integers(0, K, size=n)
+    x = (cent[src] + rng.normal(0, noise, size=(n, D))).astype(np.float32)
+    return x, cent, src
+
+
+def exact_argmin(x, cb):
+    """FP64 squared distances: argmin and the gap to the runner-up."""
+    d = ((x.astype(np.float64)[:, None, :] - cb.astype(np.float64)[None, :, :]) ** 2).sum(-1)
+    order = np.argsort(d, axis=1, kind="stable")
+    best = order[:, 0]
+    rows = np.arange(x.shape[0])
+    gap = d[rows, order[:, 1]] - d[rows, best] if cb.shape[0] > 1 else np.full(x.shape[0], np.inf)
+    return best, gap, d
+
+
+def check_vq_assign(L, seed: int = 14):
+    """Vectors near well-separated centres go to their source centre; on
+    random data the choice is the FP64 nearest centre wherever the FP64 gap to
+    the runner-up exceeds the FP32 rounding of the scores; a duplicated centre
+    never wins over its lower-index copy."""
+    x, cent, src = vq_data(seed, 600, 64)
+    idx, _ = oracle.vq_assign(x, cent, L=L)
+    assert np.array_equal(idx, src)
+    rng = np.random.default_rng(seed + 1)
+    for K, D, scale in ((37, 45, 0.05), (200, 8, 1.0), (5, 3, 100.0)):
+        x = rng.laplace(0, scale, size=(500, D)).astype(np.float32)
+        cb = rng.laplace(0, scale, size=(K, D)).astype(np.float32)
+        idx, score = oracle.vq_assign(x, cb, L=L)
+        best, gap, d = exact_argmin(x, cb)
+        xx = (x.astype(np.float64) ** 2).sum(1)
+        cc = (cb.astype(np.float64) ** 2).sum(1)
+        tol = 4 * D * 2.0 ** -24 * (xx[:, None] + cc[None, :]).max(1)
+        ok = gap > 2 * tol
+        assert np.array_equal(idx[ok], best[ok]), (K, D)
+        rows = np.arange(x.shape[0])
+        assert np.all(d[rows, idx] - d[rows, best] <= 2 * tol)          # near-ties: still near-optimal
+        assert np.allclose(score.astype(np.float64) + xx, d[rows, idx], rtol=0, atol=tol.max())
+    cb = cent[:10].copy()
+    cb[7] = cb[3]                                                      # a duplicated centre
+    xs = (cb[3] + 1e-3).reshape(1, -1).astype(np.float32)
+    assert oracle.vq_assign(xs, cb, L=L)[0][0] == 3
+
+
+def check_vq_update(L, seed: int = 15):
+    """From zero counts one batch moves each centre to the mean of its batch
+    vectors (centres with none stay); a second batch gives the running mean of
+    both (the per-vector update with rate 1/count, carried out in FP64); a
+    whole-data batch from zero counts is one Lloyd step (scipy's kmeans2)."""
+    from scipy.cluster.vq import kmeans2
+    x, cent, _ = vq_data(seed, 3000, 40, D=12, noise=0.3)
+    rng = np.random.default_rng(seed)
+    init = cent + rng.normal(0, 0.1, cent.shape).astype(np.float32)
+    init[39] = 50.0                                                    # never the nearest: stays
+    b1 = rng.choice(x.shape[0], 700, replace=False).astype(np.int32)
+    b2 = rng.choice(x.shape[0], 900, replace=False).astype(np.int32)
+    cb1, cnt1, a1 = oracle.vq_train(x, init, b1[None, :], L=L)
+    assert cnt1.sum() == 700 and np.array_equal(cnt1, np.bincount(a1[0], minlength=40))
+    assert np.array_equal(cb1[39], init[39]) and cnt1[39] == 0
+    for k in np.nonzero(cnt1)[0]:
+        mean = x[b1[a1[0] == k]].astype(np.float64).mean(0)
+        assert np.allclose(cb1[k], mean, rtol=2.5e-7, atol=1e-7), k
+    cb2, cnt2, a2 = oracle.vq_train(x, cb1, b2[None, :], counts=cnt1, L=L)
+    # the literal per-vector update (Sculley): v += 1, eta = 1 / v, c += eta (x - c), in FP64
+    c = cb1.astype(np.float64)
+    v = cnt1.astype(np.float64)
+    for j, row in enumerate(b2):
+        k = a2[0][j]
+        v[k] += 1
+        c[k] += (x[row].astype(np.float64) - c[k]) / v[k]
+    assert np.array_equal(cnt2, v.astype(np.int64))
+    assert np.allclose(cb2, c, rtol=1e-6, atol=1e-7)
+    # Lloyd: batch = every vector, counts zero
+    allr = np.arange(x.shape[0], dtype=np.int32)[None, :]
+    cbl, _, al = oracle.vq_train(x, init, allr, L=L)
+    import warnings
+    with warnings.catch_warnings():
+        warnings.simplefilter("ignore")
+        ref_cb, ref_lab = kmeans2(x.astype(np.float64), init.astype(np.float64), iter=1, minit="matrix",
+                                  missing="warn")
+    assert np.array_equal(al[0], ref_lab)
+    assert np.allclose(cbl, ref_cb, rtol=1e-6, atol=1e-7)

@@ -56,6 +56,14 @@ MUTANTS = {
     "mode_choice_inverted": ("if (rans_payload < raw_payload) {", "if (rans_payload > raw_payload) {"),
     "frequency_not_scaled": ("f[s] = (uint32_t)(((uint64_t)hist[s] * M) / (uint64_t)n);",
                              "f[s] = hist[s];"),
+    "vq_score_sign": ("float score = fmaf(-2.0f, dot, cc[k]);", "float score = fmaf(2.0f, dot, cc[k]);"),
+    "vq_norm_dropped": ("float score = fmaf(-2.0f, dot, cc[k]);", "float score = -2.0f * dot;"),
+    "vq_tie_to_higher": ("if (k == 0 || score < best_s) {", "if (k == 0 || score <= best_s) {"),
+    "vq_count_ignored": ("double v = (double)counts[k];", "double v = 0.0;"),
+    "vq_mean_over_batch_only": ("cb[(int64_t)k * D + d] = (float)(num / (v + (double)m[k]));",
+                                "cb[(int64_t)k * D + d] = (float)(num / (double)m[k]);"),
+    "vq_batch_row_shift": ("memcpy(xb + (int64_t)j * D, x + (int64_t)rows[j] * D, sizeof(float) * D);",
+                           "memcpy(xb + (int64_t)j * D, x + (int64_t)rows[j] * D + 1, sizeof(float) * (D - 1));"),
     "raht_keep_ignored": ("        K = oracle_kept(rank, order, n, keep, pos);",
                           "        for (int64_t t = 0; t < n; t++) pos[t] = t;"),
 }
@@ -89,6 +97,8 @@ checks = [
     lambda: pins.check_coder_roundtrip(L),
     lambda: pins.check_coder_entropy(L),
     lambda: pins.check_coder_normalisation(L),
+    lambda: pins.check_vq_assign(L),
+    lambda: pins.check_vq_update(L),
 ]
 failed = 0
 for c in checks:

@@ -228,3 +228,11 @@ def test_encode_config_concatenates_blocks():
             assert np.float32(mn) == minmax[c, g, 0] and np.float32(mx) == minmax[c, g, 1]
             at += len(blk)
     assert at == len(stream) == int(sizes.sum())
+
+
+def test_vq_assignment():
+    pins.check_vq_assign(oracle.lib())
+
+
+def test_vq_minibatch_update():
+    pins.check_vq_update(oracle.lib())
