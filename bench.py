@@ -878,6 +878,82 @@ def run_calibrated(args):
                       "fixed_rate": f, "entropy_rate": res["entropy"]}))
 
 
+def run_vq(args):
+    """SH vector quantisation (Sec. III-D) at scene scale: 50 mini-batches of
+    65536 of the 45 SH-rest coefficients of 5.27 M Gaussians against a
+    4096-entry codebook, then the assignment of every vector."""
+    import numpy as np
+    import torch
+    from paper_2604_26799_gb300 import mgs
+    dev = torch.device("cuda", 0)
+    w = WORKLOAD
+    attrs, _ = synth.make_scene(w.n, seed=w.seed)
+    x = np.ascontiguousarray(attrs[:, 6:51])
+    del attrs
+    n, D = x.shape
+    K, iters, batch = synth.VQ_K, synth.VQ_ITERS, synth.VQ_BATCH
+    cb0 = x[synth.vq_init_rows(n, K, seed=1)]
+    bt = synth.vq_batches(n, iters, batch, seed=2)
+    ctx = mgs.mgs_create(0)
+    st = torch.cuda.Stream(device=dev)
+    xd = torch.from_numpy(x).to(dev)
+    btd = torch.from_numpy(bt).to(dev)
+    cb0d = torch.from_numpy(cb0).to(dev)
+    cbd = torch.empty_like(cb0d)
+    cnt = torch.empty(K, dtype=torch.int64, device=dev)
+    idx = torch.empty(n, dtype=torch.int32, device=dev)
+    times, train_ms, assign_ms = [], [], []
+    launches0 = None
+    for step in range(args.warmup + args.steps):
+        with torch.cuda.stream(st):
+            cbd.copy_(cb0d)
+            cnt.zero_()
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            if step == args.warmup:
+                launches0 = mgs.mgs_kernel_launches()
+            e[0].record(st)
+            mgs.mgs_vq_train(ctx, xd, cbd, cnt, btd, stream=st)
+            e[1].record(st)
+            mgs.mgs_vq_assign(ctx, xd, cbd, index_out=idx, stream=st)
+            e[2].record(st)
+            e[2].synchronize()
+        if step >= args.warmup:
+            times.append(e[0].elapsed_time(e[2]))
+            train_ms.append(e[0].elapsed_time(e[1]))
+            assign_ms.append(e[1].elapsed_time(e[2]))
+    launches = (mgs.mgs_kernel_launches() - launches0) // args.steps
+    mgs.mgs_destroy(ctx)
+    ms = statistics.mean(times)
+    evals = (iters * batch + n) * K                       # (vector, centre) scores
+    ops = evals * (D + 1)                                 # D fmaf for the dot, one for the score
+    peaks = measured_peaks()
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak = n_sm * LANES_PER_SM_CLK * sm_mhz * 1e6 / 1e12
+    a_ms = statistics.mean(assign_ms)
+    alu_assign = n * K * (D + 1) / (a_ms * 1e-3) / 1e12
+    cpu = None
+    if not args.no_cpu:
+        import oracle
+        rows = np.random.default_rng(5).choice(n, 2000, replace=False)
+        t0 = time.perf_counter()
+        oracle.vq_assign(x[rows], cb0)
+        dt = time.perf_counter() - t0
+        cpu = {"value": 2000 * K / dt, "unit": "scores/s", "cores": 1, "kind": "oracle",
+               "sample": f"oracle.vq_assign of 2000 of the vectors against the 4096 entries, {dt:.1f} s of one core"}
+    print(json.dumps({"metric": "SH vector quantisation: vector-entry scores/s", "value": evals / (ms * 1e-3),
+                      "unit": "scores/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_step": ms, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+                      "config": {"workload": f"SH VQ N={n}, D={D}, K={K}, {iters} mini-batches of {batch}, "
+                                             "then every vector assigned"},
+                      "train_ms": statistics.mean(train_ms), "assign_ms": a_ms, "gpu_launches": int(launches),
+                      "roofline": {"bound": "alu", "achieved": alu_assign, "peak": alu_peak, "unit": "Tops/s",
+                                   "frac": alu_assign / alu_peak, "traffic": None, "kernel": "k_vq_assign",
+                                   "ops_per_score": D + 1,
+                                   "peak_source": f"{n_sm} SMs x {LANES_PER_SM_CLK} lanes x {sm_mhz:.0f} MHz"},
+                      "cpu_baseline": cpu}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -885,7 +961,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mgs", choices=["mgs", "reference"])
     ap.add_argument("--workload", default="scene", choices=["scene", "batch", "serve", "large", "preprocess", "raht", "raht_search",
-                             "encode", "calibrated"],
+                             "encode", "calibrated", "vq"],
                     help="scene: the scene-scale search (default); batch: 16 uneven scenes in one "
                          "graph-replayed launch; serve: Poisson job stream through the server; "
                          "large: 6 M Gaussians x 20 ratios x 16 bit-widths; preprocess: Euler "
@@ -893,7 +969,8 @@ def main():
                          "raht: RAHT of 10 channels of the scene-scale scene at depth 16; "
                          "raht_search: the search over RAHT AC tables for every ratio; "
                          "encode: the block coder on half the scene; calibrated: Alg. 1 with "
-                         "real compression (the S_Delta loop) at 40 MB")
+                         "real compression (the S_Delta loop) at 40 MB; vq: mini-batch k-means "
+                         "of the SH coefficients and the assignment of every vector")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-loop comparator")
     ap.add_argument("--no-autotune", action="store_true", help="use the default tile shape")
@@ -923,6 +1000,8 @@ def main():
         return run_encode(args)
     if args.workload == "calibrated":
         return run_calibrated(args)
+    if args.workload == "vq":
+        return run_vq(args)
     return run_gpu(args)
 
 

@@ -489,6 +489,52 @@ mgs_status mgs_search_calibrated(mgs_ctx *ctx, const mgs_scene *scene, const mgs
                                  const void *table, const mgs_table_layout *layout,
                                  const mgs_calib_opts *opts, mgs_calib_result *out, void *stream);
 
+/* ---- vector quantisation of the 1+D SH coefficients ----------------------- */
+
+/*
+ * Sec. III-D "Clustering 1+D SH Coefficients": each SH vector is replaced by
+ * the index of a codebook entry.  Decisions are reproducible bit for bit: the
+ * score of entry k for vector x is fl(|c_k|^2 - 2 x.c_k) (|x|^2 is dropped; it
+ * does not change the argmin), both sums accumulated by fmaf over the D
+ * dimensions in ascending order; the smallest score wins, ties to the lower
+ * k.
+ *   x         [n][D] FP32, device, row-major (1 <= D <= 64, n < 2^31)
+ *   codebook  [K][D] FP32, device (1 <= K <= 2^20)
+ *   index_out [n] int32, device: the chosen entry
+ *   score_out [n] FP32, device, may be NULL: its score (add |x|^2 for the
+ *             squared distance)
+ * Stream-ordered; workspace is allocated on `stream`.
+ */
+mgs_status mgs_vq_assign(mgs_ctx *ctx, const float *x, int64_t n, int32_t D, const float *codebook,
+                         int32_t K, int32_t *index_out, float *score_out, void *stream);
+
+/*
+ * The batched clustering the paper cites (Sculley's mini-batch k-means): for
+ * t = 0 .. iters - 1, the vectors x[batches[t][j]] are assigned as by
+ * mgs_vq_assign, then every entry with m > 0 of them moves to the running
+ * mean of all vectors ever assigned to it: c = (v c + sum x) / (v + m), the
+ * sum in FP64 in batch order, rounded once to FP32, and v += m.  This is the
+ * per-vector update with learning rate 1 / count, carried out exactly over
+ * each batch.  The random batches are the caller's (device int32
+ * [iters][batch], each a row of x; checked).  codebook and counts ([K] int64,
+ * zero for a fresh codebook) are updated in place; assign_out ([iters][batch]
+ * int32, device, may be NULL) receives every batch's assignment.
+ * Stream-ordered apart from one host check of the batch indices.
+ */
+mgs_status mgs_vq_train(mgs_ctx *ctx, const float *x, int64_t n, int32_t D, float *codebook,
+                        int32_t K, int64_t *counts, const int32_t *batches, int32_t iters,
+                        int32_t batch, int32_t *assign_out, void *stream);
+
+/*
+ * Budget-first retention: the vectors of rows[0 .. n_retain) (the top-ranked
+ * Gaussians, whose original SH the remaining budget keeps) are appended to
+ * the codebook as entries K, K + 1, ...; their indices are rewritten to
+ * index[rows[j]] = K + j (device memory; rows must be distinct rows of
+ * index).  Appending the vectors themselves is the caller's copy.
+ */
+mgs_status mgs_vq_retain(mgs_ctx *ctx, const int32_t *rows, int64_t n_retain, int32_t K,
+                         int32_t *index, void *stream);
+
 /* ---- serving ------------------------------------------------------------ */
 
 /*

@@ -146,6 +146,10 @@ _SIGS = {
     "mgs_preprocess": [_P, _P, _P, ctypes.c_int64, ctypes.c_double, _P, _P, _P, _P],
     "mgs_encode_config": [_P, _P, ctypes.c_int64, ctypes.c_int32, _P, _P, ctypes.c_int64, _P, _P, _P],
     "mgs_encode_bound": [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32],
+    "mgs_vq_assign": [_P, _P, ctypes.c_int64, ctypes.c_int32, _P, ctypes.c_int32, _P, _P, _P],
+    "mgs_vq_train": [_P, _P, ctypes.c_int64, ctypes.c_int32, _P, ctypes.c_int32, _P, _P, ctypes.c_int32,
+                     ctypes.c_int32, _P, _P],
+    "mgs_vq_retain": [_P, _P, ctypes.c_int64, ctypes.c_int32, _P, _P],
     "mgs_search_calibrated": [_P, _P, ctypes.POINTER(mgs_grid), _P, ctypes.POINTER(mgs_table_layout),
                               ctypes.POINTER(mgs_calib_opts), ctypes.POINTER(mgs_calib_result), _P],
     "mgs_solve_budgets_device": [_P, _P, ctypes.POINTER(mgs_table_layout), ctypes.POINTER(mgs_grid),
@@ -299,6 +303,32 @@ def mgs_encode_config(ctx: int, scene: int, keep: int, group_size: int, bits, st
                                    _ptr(stream_out), cap, _ptr(block_bytes),
                                    ctypes.addressof(total), _stream(stream)))
     return total.value
+
+
+def mgs_vq_assign(ctx: int, x, codebook, index_out=None, score_out=None, stream=None):
+    """Nearest codebook entry of each row of x [n, D] (device tensors).
+    Returns (index int32 [n], score or None)."""
+    import torch
+    n, D = x.shape
+    if index_out is None:
+        index_out = torch.empty(n, dtype=torch.int32, device=x.device)
+    _check(lib().mgs_vq_assign(ctx, _ptr(x), n, D, _ptr(codebook), codebook.shape[0], _ptr(index_out),
+                               _ptr(score_out), _stream(stream)))
+    return index_out, score_out
+
+
+def mgs_vq_train(ctx: int, x, codebook, counts, batches, assign_out=None, stream=None):
+    """Mini-batch k-means over the rows of x: one update per row of `batches`
+    [iters, batch] (device int32).  codebook [K, D] and counts [K] (int64) are
+    updated in place."""
+    n, D = x.shape
+    iters, b = batches.shape
+    _check(lib().mgs_vq_train(ctx, _ptr(x), n, D, _ptr(codebook), codebook.shape[0], _ptr(counts),
+                              _ptr(batches), iters, b, _ptr(assign_out), _stream(stream)))
+
+
+def mgs_vq_retain(ctx: int, rows, K: int, index, stream=None):
+    _check(lib().mgs_vq_retain(ctx, _ptr(rows), int(rows.shape[0]), int(K), _ptr(index), _stream(stream)))
 
 
 def mgs_plan_create(ctx: int, scenes: list[int], grids, tables: list, use_graph: bool = False,

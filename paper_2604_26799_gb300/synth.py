@@ -122,3 +122,21 @@ def poisson_arrivals(n_jobs: int, rate_per_s: float, seed: int,
     sizes = np.exp(rng.uniform(np.log(n_lo), np.log(n_hi), size=n_jobs)).astype(np.int64)
     budgets = rng.uniform(budget_lo, budget_hi, size=n_jobs)
     return t, sizes, budgets
+
+
+def vq_batches(n: int, iters: int, batch: int, seed: int) -> np.ndarray:
+    """Row indices of the mini-batches of the SH clustering: [iters, batch]
+    int32, drawn uniformly (with replacement) from range(n)."""
+    rng = np.random.default_rng(np.random.SeedSequence([int(seed), 0x51A]))
+    return rng.integers(0, n, size=(iters, batch), dtype=np.int64).astype(np.int32)
+
+
+def vq_init_rows(n: int, K: int, seed: int) -> np.ndarray:
+    """K distinct rows whose vectors seed the codebook (int32 [K])."""
+    rng = np.random.default_rng(np.random.SeedSequence([int(seed), 0xC0DE]))
+    return np.sort(rng.choice(n, size=K, replace=False)).astype(np.int32)
+
+
+# SH clustering stand-in: the 45 SH-rest coefficients of the scene-scale
+# scene, a 4096-entry codebook, 50 mini-batches of 65536 vectors.
+VQ_K, VQ_ITERS, VQ_BATCH = 4096, 50, 65536
