@@ -4,19 +4,18 @@
 // format (static-model rANS with a raw fallback; the format is written out in
 // include/mgs.h above mgs_encode_config).
 //
-// Pipeline (all on `stream`): kept list -> quantise (quantize.cu) -> k_encode,
-// one CTA per (channel, group) block writing into a fixed-size slot ->
-// exclusive scan of the block sizes -> k_enc_gather, which packs the slots
-// into one contiguous stream in (channel, group) order.
-//
-// k_encode per block: stage the codes in shared memory; count them in
-// windows of 4096 codes (16 windows at b = 16, empty windows skipped) and
-// list the distinct codes in ascending order; normalise the counts to
-// M = 2^ceil(log2 n); lay out the gamma-coded table by a block-wide scan of
-// its bit lengths; run the interleaved rANS encoder in one warp (lane j owns
-// symbols i = j mod lanes; the bytes a step emits are ordered by two ballots
-// and written from the end of the stream); then write whichever payload is
-// shorter.
+// Pipeline (all on `stream`): kept list -> quantise (quantize.cu) ->
+//   k_enc_model, one CTA per (channel, group) block: count the codes in windows
+//     of 4096 (16 windows at b = 16, empty ones skipped), list the distinct
+//     codes in ascending order, normalise the counts to M = 2^ceil(log2 n), lay
+//     out the gamma-coded table by a block-wide scan of its bit lengths and
+//     write it into the block's slot, and store (f << 16 | cum) for every code;
+//   k_enc_rans, one warp per block: the interleaved rANS encoder (lane j owns
+//     symbols i = j mod lanes; the bytes a step emits are ordered by two
+//     ballots), which needs no shared memory, so many blocks are in flight;
+//   block sizes -> exclusive scan -> k_enc_gather, which writes each block at
+//     its offset (raw blocks bit-packed from the codes, rANS bytes reversed
+//     into decoding order); skipped when only the size is wanted.
 #include <cuda_runtime.h>
 
 #include <vector>
@@ -34,17 +33,15 @@ constexpr int kScanChunk = 1024;        // sizes per CTA of the scan
 
 __host__ __device__ inline int64_t a16(int64_t x) { return (x + 15) & ~(int64_t)15; }
 
-// Shared-memory layout of k_encode for group size G.
+// Shared-memory layout of k_enc_model for group size G.
 struct EncSmem {
-    int64_t codes, hist, sym, f, cum, em, tab, total;
+    int64_t hist, sym, f, cum, tab, total;
     __host__ __device__ explicit EncSmem(int G) {
-        codes = 0;                            // uint16[G]
-        hist = codes + a16(2 * (int64_t)G);   // uint32[kWin] (also the code -> entry map)
+        hist = 0;                             // uint32[kWin] (also the code -> entry map)
         sym = hist + 4 * kWin;                // uint16[G]: distinct codes, ascending
-        f = sym + a16(2 * (int64_t)G);        // uint16[G]: normalised frequencies (cnt first)
+        f = sym + a16(2 * (int64_t)G);        // uint16[G]: normalised frequencies (counts first)
         cum = f + a16(2 * (int64_t)G);        // uint16[G]
-        em = cum + a16(2 * (int64_t)G);       // uint8[2G + 16]: rANS bytes in emission order
-        tab = em + a16(2 * (int64_t)G + 16);  // uint32 words: the table's bits
+        tab = cum + a16(2 * (int64_t)G);      // uint32 words: the table's bits (< 2G + 16 bytes)
         total = tab + a16(2 * (int64_t)G + 16);
     }
 };
@@ -79,57 +76,82 @@ __device__ __forceinline__ void put_gamma(uint32_t *tab, int64_t p, uint32_t x) 
         if ((x >> (N - u)) & 1u) atomicOr(&tab[p >> 5], 1u << (p & 31));
 }
 
+// What k_enc_model leaves for the rANS and gather kernels, per block.
+struct EncInfo {
+    int32_t lanes;       // interleaved rANS states; 0: no rANS attempt (R = 0, or raw is shorter)
+    int32_t k;           // log2 M
+    int32_t tab_bytes;   // the gamma table, zero-padded to a byte
+    int32_t e_cap;       // rANS is used iff its renormalisation byte count E < e_cap
+    int32_t E;           // min(E, e_cap), from k_enc_rans
+    int32_t pad_;
+};
+
+// Block geometry shared by the three kernels.
+struct EncBlock {
+    int c, g, n;
+    int64_t start;
+};
+__device__ __forceinline__ EncBlock enc_block(int64_t blk, int64_t K, int32_t G, int32_t ng) {
+    EncBlock B;
+    B.c = (int)(blk / ng);
+    B.g = (int)(blk % ng);
+    B.start = (int64_t)B.g * G;
+    B.n = (int)((K - B.start) < (int64_t)G ? (K - B.start) : (int64_t)G);
+    return B;
+}
+
+// One CTA per (channel, group) block: metadata, the distinct codes and their
+// normalised frequencies, the gamma table in the block's slot, and the packed
+// (f << 16 | cum) of every code for the rANS kernel.
 __global__ void __launch_bounds__(kEncThreads)
-    k_encode(const uint16_t *__restrict__ codes, int64_t K, int32_t G, int32_t ng,
-             const uint8_t *__restrict__ bits, const float *__restrict__ minmax,
-             uint8_t *__restrict__ slots, int64_t slot_bytes, int32_t *__restrict__ sizes) {
+    k_enc_model(const uint16_t *__restrict__ codes, int64_t K, int32_t G, int32_t ng,
+                const uint8_t *__restrict__ bits, const float *__restrict__ minmax,
+                uint8_t *__restrict__ slots, int64_t slot_bytes, EncInfo *__restrict__ info,
+                uint32_t *__restrict__ fcpos, int32_t *__restrict__ sizes) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint64_t s_warp[kEncWarps];
     __shared__ uint32_t s_wcnt[16];
-    __shared__ uint32_t s_state[32];
-    __shared__ int s_D, s_E;
+    __shared__ int s_D;
     __shared__ uint32_t s_top;
 
     const EncSmem L(G);
-    uint16_t *s_codes = reinterpret_cast<uint16_t *>(smem + L.codes);
     uint32_t *s_hist = reinterpret_cast<uint32_t *>(smem + L.hist);
     uint16_t *s_sym = reinterpret_cast<uint16_t *>(smem + L.sym);
     uint16_t *s_f = reinterpret_cast<uint16_t *>(smem + L.f);
     uint16_t *s_cum = reinterpret_cast<uint16_t *>(smem + L.cum);
-    uint8_t *s_em = smem + L.em;
     uint32_t *s_tab = reinterpret_cast<uint32_t *>(smem + L.tab);
 
     const int64_t blk = blockIdx.x;
-    const int c = (int)(blk / ng), g = (int)(blk % ng);
-    const int64_t start = (int64_t)g * G;
-    const int n = (int)((K - start) < (int64_t)G ? (K - start) : (int64_t)G);
+    const EncBlock B = enc_block(blk, K, G, ng);
+    const int n = B.n;
     const int b = bits[blk];
     const float mn = minmax[2 * blk], mx = minmax[2 * blk + 1];
     uint8_t *out = slots + blk * slot_bytes;
     const int t = threadIdx.x;
+    const uint16_t *src = codes + (int64_t)B.c * K + B.start;
 
     if (t < 9) {
         uint32_t v = t == 0 ? (uint32_t)b : __float_as_uint(t < 5 ? mn : mx) >> (8 * ((t - 1) & 3));
         out[t] = (uint8_t)v;
     }
+    const int64_t raw_payload = 1 + ((int64_t)n * b + 7) / 8;
     if (__fsub_rn(mx, mn) == 0.0f) {   // R = 0: every code is 0, metadata only
-        if (t == 0) sizes[blk] = 9;
+        if (t == 0) {
+            sizes[blk] = 9;
+            info[blk] = EncInfo{0, 0, 0, 0, 0, 0};
+        }
         return;
     }
 
-    // ---- stage the codes; per-window counts when b > 12 ----
+    // ---- per-window counts when b > 12 ----
     const int logW = b < 12 ? b : 12;
     const int W = 1 << logW;
     const int nwin = 1 << (b - logW);
     if (t < 16) s_wcnt[t] = 0;
-    __syncthreads();
-    const uint16_t *src = codes + (int64_t)c * K + start;
-    for (int i = t; i < n; i += kEncThreads) {
-        uint16_t q = src[i];
-        s_codes[i] = q;
-        if (nwin > 1) atomicAdd(&s_wcnt[q >> 12], 1u);
-    }
     if (t == 0) s_D = 0;
+    __syncthreads();
+    if (nwin > 1)
+        for (int i = t; i < n; i += kEncThreads) atomicAdd(&s_wcnt[src[i] >> 12], 1u);
     __syncthreads();
 
     // ---- distinct codes (ascending) with their counts ----
@@ -139,7 +161,7 @@ __global__ void __launch_bounds__(kEncThreads)
         for (int i = t; i < W; i += kEncThreads) s_hist[i] = 0;
         __syncthreads();
         for (int i = t; i < n; i += kEncThreads) {
-            uint32_t q = s_codes[i];
+            uint32_t q = src[i];
             if ((int)(q >> logW) == w) atomicAdd(&s_hist[q & (W - 1)], 1u);
         }
         __syncthreads();
@@ -214,106 +236,115 @@ __global__ void __launch_bounds__(kEncThreads)
         }
     }
 
-    // ---- decide whether rANS can beat the raw payload ----
+    // ---- can rANS beat the raw payload at all? ----
     const int lanes = min(32, max(1, n >> 9));
-    const int64_t raw_payload = 1 + ((int64_t)n * b + 7) / 8;
     const int64_t tab_bytes = (tbits + 7) / 8;
     const int64_t e_cap = raw_payload - 1 - tab_bytes - 4 * (int64_t)lanes;   // rANS iff E < e_cap
-    const bool try_rans = e_cap > 0;
-    __syncthreads();
-
-    if (try_rans && t < 32) {
-        const int j = t;
-        uint32_t x = kRansL;
-        int64_t base = 0;
-        const uint32_t above = ~((2u << j) - 1u);   // lanes > j (0 for j = 31)
-        const uint32_t xunit = 1u << (31 - k);      // (L >> k) << 8
-        const int steps = (n + lanes - 1) / lanes;
-        for (int st = steps - 1; st >= 0; st--) {
-            const int i = st * lanes + j;
-            int cnt = 0;
-            uint32_t b1 = 0, b2 = 0;
-            if (j < lanes && i < n) {
-                const uint32_t s = s_codes[i];
-                int e;
-                if (nwin == 1) {
-                    e = (int)s_hist[s];
-                } else {
-                    int lo = 0, hi = D - 1;
-                    while (lo < hi) {
-                        int mid = (lo + hi) >> 1;
-                        if (s_sym[mid] < s) lo = mid + 1;
-                        else hi = mid;
-                    }
-                    e = lo;
-                }
-                const uint32_t fs = s_f[e], cs = s_cum[e];
-                const uint64_t xmax = (uint64_t)xunit * fs;
-                if (x >= xmax) {
-                    b1 = x & 0xFFu;
-                    x >>= 8;
-                    cnt = 1;
-                    if (x >= xmax) {
-                        b2 = x & 0xFFu;
-                        x >>= 8;
-                        cnt = 2;
-                    }
-                }
-                x = (x / fs) * M + x % fs + cs;
-            }
-            const uint32_t m1 = __ballot_sync(0xFFFFFFFFu, cnt >= 1);
-            const uint32_t m2 = __ballot_sync(0xFFFFFFFFu, cnt == 2);
-            const int64_t idx = base + __popc(m1 & above) + __popc(m2 & above);
-            if (cnt >= 1 && idx < e_cap) s_em[idx] = (uint8_t)b1;
-            if (cnt == 2 && idx + 1 < e_cap) s_em[idx + 1] = (uint8_t)b2;
-            base += __popc(m1) + __popc(m2);
+    if (e_cap <= 0) {
+        if (t == 0) {
+            sizes[blk] = (int32_t)(9 + raw_payload);
+            info[blk] = EncInfo{0, k, 0, 0, 0, 0};
         }
-        s_state[j] = x;
-        if (j == 0) s_E = (int)(base < e_cap ? base : e_cap);   // e_cap: rANS lost
+        return;
+    }
+    __syncthreads();   // s_cum complete
+
+    // ---- (f, cum) of every code, and the table in the slot ----
+    uint32_t *fc = fcpos + (int64_t)B.c * K + B.start;
+    for (int i = t; i < n; i += kEncThreads) {
+        const uint32_t q = src[i];
+        int e;
+        if (nwin == 1) {
+            e = (int)s_hist[q];
+        } else {
+            int lo = 0, hi = D - 1;
+            while (lo < hi) {
+                int mid = (lo + hi) >> 1;
+                if (s_sym[mid] < q) lo = mid + 1;
+                else hi = mid;
+            }
+            e = lo;
+        }
+        fc[i] = ((uint32_t)s_f[e] << 16) | (uint32_t)s_cum[e];
+    }
+    const int64_t words = (tab_bytes + 3) / 4;
+    for (int64_t q = t; q < words; q += kEncThreads) s_tab[q] = 0;
+    __syncthreads();
+    if (t == 0) put_gamma(s_tab, 0, (uint32_t)D);
+    int64_t p = glen((uint32_t)D) + (int64_t)(pre & 0xFFFFFFFFu);
+    for (int e = e0; e < e1; e++) {
+        uint32_t gap = e == 0 ? (uint32_t)s_sym[0] + 1u : (uint32_t)(s_sym[e] - s_sym[e - 1]);
+        put_gamma(s_tab, p, gap);
+        p += glen(gap);
+        put_gamma(s_tab, p, s_f[e]);
+        p += glen(s_f[e]);
     }
     __syncthreads();
-    const int64_t E = try_rans ? s_E : e_cap;
-    const bool rans = try_rans && E < e_cap;
+    const uint8_t *tb = reinterpret_cast<const uint8_t *>(s_tab);
+    for (int64_t q = t; q < tab_bytes; q += kEncThreads) out[10 + q] = tb[q];
+    if (t == 0) info[blk] = EncInfo{lanes, k, (int32_t)tab_bytes, (int32_t)e_cap, 0, 0};
+}
 
-    if (rans) {
-        const int64_t words = (tab_bytes + 3) / 4;
-        for (int64_t q = t; q < words; q += kEncThreads) s_tab[q] = 0;
-        __syncthreads();
-        if (t == 0) put_gamma(s_tab, 0, (uint32_t)D);
-        int64_t p = glen((uint32_t)D) + (int64_t)(pre & 0xFFFFFFFFu);
-        for (int e = e0; e < e1; e++) {
-            uint32_t gap = e == 0 ? (uint32_t)s_sym[0] + 1u : (uint32_t)(s_sym[e] - s_sym[e - 1]);
-            put_gamma(s_tab, p, gap);
-            p += glen(gap);
-            put_gamma(s_tab, p, s_f[e]);
-            p += glen(s_f[e]);
-        }
-        __syncthreads();
-        if (t == 0) out[9] = 1;
-        const uint8_t *tb = reinterpret_cast<const uint8_t *>(s_tab);
-        for (int64_t q = t; q < tab_bytes; q += kEncThreads) out[10 + q] = tb[q];
-        uint8_t *st = out + 10 + tab_bytes;
-        for (int q = t; q < 4 * lanes; q += kEncThreads) st[q] = (uint8_t)(s_state[q >> 2] >> (8 * (q & 3)));
-        uint8_t *eb = st + 4 * lanes;
-        for (int64_t q = t; q < E; q += kEncThreads) eb[q] = s_em[E - 1 - q];
-        if (t == 0) sizes[blk] = (int32_t)(9 + 1 + tab_bytes + 4 * lanes + E);
-    } else {
-        if (t == 0) out[9] = 0;
-        // 32 stream bits per thread step: the codes overlapping bits [32 wq, 32 wq + 32)
-        const int nb = (int)(raw_payload - 1);
-        const int nwords = (nb + 3) / 4;
-        for (int wq = t; wq < nwords; wq += kEncThreads) {
-            const int lo = 32 * wq;
-            const int i0 = lo / b, i1 = min(n - 1, (lo + 31) / b);
-            uint64_t v = 0;
-            for (int i = i0; i <= i1; i++) {
-                const int p = i * b - lo;
-                const uint64_t q = s_codes[i];
-                v |= p >= 0 ? q << p : q >> (-p);
+// One warp per block: the interleaved rANS encoder, last symbol first.  Lane
+// j owns the symbols i = j (mod lanes); each step emits 0-2 bytes per lane,
+// placed by two ballots in emission order (higher lanes first within a
+// step); the bytes go into the slot after the table and the states, and the
+// gather kernel writes them out in reverse, which is decoding order.
+__global__ void __launch_bounds__(kEncThreads)
+    k_enc_rans(const uint32_t *__restrict__ fcpos, int64_t K, int32_t G, int32_t ng, int64_t m,
+               const uint8_t *__restrict__ bits, uint8_t *__restrict__ slots, int64_t slot_bytes,
+               EncInfo *__restrict__ info, int32_t *__restrict__ sizes) {
+    const int64_t blk = (int64_t)blockIdx.x * kEncWarps + (threadIdx.x >> 5);
+    if (blk >= m) return;
+    const EncInfo I = info[blk];
+    if (I.lanes == 0) return;
+    const EncBlock B = enc_block(blk, K, G, ng);
+    const int n = B.n, lanes = I.lanes, k = I.k;
+    const uint32_t M = 1u << k;
+    const uint32_t *fc = fcpos + (int64_t)B.c * K + B.start;
+    uint8_t *out = slots + blk * slot_bytes + 10 + I.tab_bytes;
+    uint8_t *em = out + 4 * lanes;
+    const int64_t e_cap = I.e_cap;
+    const int j = threadIdx.x & 31;
+    uint32_t x = kRansL;
+    int64_t base = 0;
+    const uint32_t above = ~((2u << j) - 1u);   // lanes > j (0 for j = 31)
+    const uint32_t xunit = 1u << (31 - k);      // (L >> k) << 8
+    const int steps = (n + lanes - 1) / lanes;
+    for (int st = steps - 1; st >= 0; st--) {
+        const int i = st * lanes + j;
+        int cnt = 0;
+        uint32_t b1 = 0, b2 = 0;
+        if (j < lanes && i < n) {
+            const uint32_t w = fc[i];
+            const uint32_t fs = w >> 16, cs = w & 0xFFFFu;
+            const uint64_t xmax = (uint64_t)xunit * fs;
+            if (x >= xmax) {
+                b1 = x & 0xFFu;
+                x >>= 8;
+                cnt = 1;
+                if (x >= xmax) {
+                    b2 = x & 0xFFu;
+                    x >>= 8;
+                    cnt = 2;
+                }
             }
-            for (int u = 0; u < 4 && 4 * wq + u < nb; u++) out[10 + 4 * wq + u] = (uint8_t)(v >> (8 * u));
+            x = (x / fs) * M + x % fs + cs;
         }
-        if (t == 0) sizes[blk] = (int32_t)(9 + raw_payload);
+        const uint32_t m1 = __ballot_sync(0xFFFFFFFFu, cnt >= 1);
+        const uint32_t m2 = __ballot_sync(0xFFFFFFFFu, cnt == 2);
+        const int64_t idx = base + __popc(m1 & above) + __popc(m2 & above);
+        if (cnt >= 1 && idx < e_cap) em[idx] = (uint8_t)b1;
+        if (cnt == 2 && idx + 1 < e_cap) em[idx + 1] = (uint8_t)b2;
+        base += __popc(m1) + __popc(m2);
+    }
+    if (j < lanes)
+        for (int q = 0; q < 4; q++) out[4 * j + q] = (uint8_t)(x >> (8 * q));
+    if (j == 0) {
+        const int64_t E = base < e_cap ? base : e_cap;
+        info[blk].E = (int32_t)E;
+        sizes[blk] = E < e_cap ? (int32_t)(10 + I.tab_bytes + 4 * lanes + E)
+                               : (int32_t)(10 + ((int64_t)n * bits[blk] + 7) / 8);
     }
 }
 
@@ -383,16 +414,50 @@ __global__ void __launch_bounds__(1024)
     if (i < m) off[i] = sums[blockIdx.x] + wb + inc - v;
 }
 
-// Packs each block's slot into the stream at its offset.
+// Writes each block at its offset: the metadata, then either the rANS
+// payload (mode, table and states as they are in the slot, the
+// renormalisation bytes reversed into decoding order) or the raw payload,
+// bit-packed from the codes.
 __global__ void __launch_bounds__(256)
-    k_enc_gather(const uint8_t *__restrict__ slots, int64_t slot_bytes,
+    k_enc_gather(const uint16_t *__restrict__ codes, int64_t K, int32_t G, int32_t ng,
+                 const uint8_t *__restrict__ bits, const uint8_t *__restrict__ slots,
+                 int64_t slot_bytes, const EncInfo *__restrict__ info,
                  const int32_t *__restrict__ sizes, const int64_t *__restrict__ off,
                  uint8_t *__restrict__ stream) {
     const int64_t blk = blockIdx.x;
     const uint8_t *src = slots + blk * slot_bytes;
     uint8_t *dst = stream + off[blk];
     const int sz = sizes[blk];
-    for (int q = threadIdx.x; q < sz; q += 256) dst[q] = src[q];
+    const int t = threadIdx.x;
+    if (t < 9) dst[t] = src[t];
+    if (sz == 9) return;
+    const EncInfo I = info[blk];
+    if (I.lanes > 0 && I.E < I.e_cap) {
+        if (t == 0) dst[9] = 1;
+        const int head = I.tab_bytes + 4 * I.lanes;
+        for (int q = t; q < head; q += 256) dst[10 + q] = src[10 + q];
+        const int E = I.E;
+        for (int q = t; q < E; q += 256) dst[10 + head + q] = src[10 + head + E - 1 - q];
+        return;
+    }
+    if (t == 0) dst[9] = 0;
+    const EncBlock B = enc_block(blk, K, G, ng);
+    const int n = B.n, b = bits[blk];
+    const uint16_t *cs = codes + (int64_t)B.c * K + B.start;
+    // 32 stream bits per step: the codes overlapping bits [32 wq, 32 wq + 32)
+    const int nb = (int)(((int64_t)n * b + 7) / 8);
+    const int nwords = (nb + 3) / 4;
+    for (int wq = t; wq < nwords; wq += 256) {
+        const int lo = 32 * wq;
+        const int i0 = lo / b, i1 = min(n - 1, (lo + 31) / b);
+        uint64_t v = 0;
+        for (int i = i0; i <= i1; i++) {
+            const int p = i * b - lo;
+            const uint64_t q = cs[i];
+            v |= p >= 0 ? q << p : q >> (-p);
+        }
+        for (int u = 0; u < 4 && 4 * wq + u < nb; u++) dst[10 + 4 * wq + u] = (uint8_t)(v >> (8 * u));
+    }
 }
 
 }  // namespace
@@ -416,34 +481,48 @@ mgs_status encode_launch(mgs_ctx *ctx, const mgs_scene *sc, const int32_t *kept,
     const size_t b_codes = (size_t)a16(2 * keep * sc->C), b_mm = (size_t)a16(8 * m);
     const size_t b_slots = (size_t)(m * slot_bytes), b_sizes = (size_t)a16(4 * m);
     const size_t b_off = (size_t)a16(8 * m), b_sums = (size_t)a16(8 * (nchunks + 1));
+    const size_t b_info = (size_t)a16((int64_t)sizeof(EncInfo) * m), b_fc = (size_t)a16(4 * keep * sc->C);
     unsigned char *ws = nullptr;
-    const size_t ws_bytes = b_codes + b_mm + b_slots + b_sizes + b_off + b_sums;
+    const size_t ws_bytes = b_codes + b_mm + b_slots + b_sizes + b_off + b_sums + b_info + b_fc;
     if (cudaMallocAsync(reinterpret_cast<void **>(&ws), ws_bytes, st) != cudaSuccess) {
         cudaGetLastError();
         set_error("encoder workspace of %zu bytes", ws_bytes);
         return MGS_ERR_OUT_OF_MEMORY;
     }
-    uint16_t *d_codes = reinterpret_cast<uint16_t *>(ws);
-    float *d_mm = reinterpret_cast<float *>(ws + b_codes);
-    uint8_t *d_slots = ws + b_codes + b_mm;
-    int32_t *d_sizes = reinterpret_cast<int32_t *>(d_slots + b_slots);
-    int64_t *d_off = reinterpret_cast<int64_t *>(reinterpret_cast<unsigned char *>(d_sizes) + b_sizes);
-    int64_t *d_sums = reinterpret_cast<int64_t *>(reinterpret_cast<unsigned char *>(d_off) + b_off);
+    size_t o = 0;
+    uint16_t *d_codes = reinterpret_cast<uint16_t *>(ws + o);
+    o += b_codes;
+    float *d_mm = reinterpret_cast<float *>(ws + o);
+    o += b_mm;
+    uint8_t *d_slots = ws + o;
+    o += b_slots;
+    int32_t *d_sizes = reinterpret_cast<int32_t *>(ws + o);
+    o += b_sizes;
+    int64_t *d_off = reinterpret_cast<int64_t *>(ws + o);
+    o += b_off;
+    int64_t *d_sums = reinterpret_cast<int64_t *>(ws + o);
+    o += b_sums;
+    EncInfo *d_info = reinterpret_cast<EncInfo *>(ws + o);
+    o += b_info;
+    uint32_t *d_fc = reinterpret_cast<uint32_t *>(ws + o);
 
     mgs_status s = quantize_launch(ctx, sc, kept, keep, G, d_bits, d_codes, d_mm, st);
     int64_t total = 0;
     if (s == MGS_OK && m > 0) {
         const EncSmem L(G);
         const size_t smem = (size_t)L.total;
-        cudaError_t e = cudaFuncSetAttribute(k_encode, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_enc_model, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e == cudaSuccess) {
-            k_encode<<<(unsigned)m, kEncThreads, smem, st>>>(d_codes, keep, G, (int32_t)ng, d_bits,
-                                                             d_mm, d_slots, slot_bytes, d_sizes);
+            k_enc_model<<<(unsigned)m, kEncThreads, smem, st>>>(d_codes, keep, G, (int32_t)ng, d_bits,
+                                                                d_mm, d_slots, slot_bytes, d_info,
+                                                                d_fc, d_sizes);
+            k_enc_rans<<<(unsigned)((m + kEncWarps - 1) / kEncWarps), kEncThreads, 0, st>>>(
+                d_fc, keep, G, (int32_t)ng, m, d_bits, d_slots, slot_bytes, d_info, d_sizes);
             k_enc_chunk_sums<<<(unsigned)nchunks, 1024, 0, st>>>(d_sizes, m, d_sums);
             k_enc_scan_sums<<<1, 1024, 0, st>>>(d_sums, nchunks, d_sums + nchunks);
             k_enc_offsets<<<(unsigned)nchunks, 1024, 0, st>>>(d_sizes, m, d_sums, d_off);
-            count_launches(4);
+            count_launches(5);
             e = cudaGetLastError();
         }
         if (e == cudaSuccess) e = cudaMemcpyAsync(&total, d_sums + nchunks, 8, cudaMemcpyDeviceToHost, st);
@@ -457,7 +536,8 @@ mgs_status encode_launch(mgs_ctx *ctx, const mgs_scene *sc, const int32_t *kept,
                 set_error("stream capacity %lld < %lld bytes", (long long)capacity, (long long)total);
                 s = MGS_ERR_INVALID_ARG;
             } else {
-                k_enc_gather<<<(unsigned)m, 256, 0, st>>>(d_slots, slot_bytes, d_sizes, d_off, stream);
+                k_enc_gather<<<(unsigned)m, 256, 0, st>>>(d_codes, keep, G, (int32_t)ng, d_bits, d_slots,
+                                                          slot_bytes, d_info, d_sizes, d_off, stream);
                 count_launches(1);
                 e = cudaGetLastError();
                 if (e != cudaSuccess) {

@@ -10,7 +10,7 @@
 //   assigned to it so far, c = (v c + sum x) / (v + m), the batch's sum taken
 //   in FP64 in batch order and the result rounded once to FP32.
 //
-// k_vq_assign: 128 threads x 2 vectors per thread in registers (the dimension
+// k_vq_assign: 128 threads x 1 or 2 vectors per thread in registers (the dimension
 // padded with zeros to DP, a multiple of 8; adding 0 * 0 leaves an fmaf chain
 // unchanged), codebook tiles of 64 centres staged in shared memory and read
 // as float4 broadcasts.  The update is a one-warp stable counting sort of the
@@ -26,8 +26,8 @@ namespace mgs {
 namespace {
 
 constexpr int kVqThreads = 128;
-constexpr int kVqPts = 2;       // vectors per thread
 constexpr int kVqTile = 64;     // centres per shared-memory tile
+constexpr int kVqSmemCursors = 12288;   // centres whose sort cursors fit in shared memory
 constexpr int kVqMaxK = 1 << 20;
 
 __global__ void k_vq_norms(const float *__restrict__ cb, int32_t K, int32_t D, float *__restrict__ cc) {
@@ -39,7 +39,7 @@ __global__ void k_vq_norms(const float *__restrict__ cb, int32_t K, int32_t D, f
     cc[k] = s;
 }
 
-template <int DP>
+template <int DP, int kVqPts>
 __global__ void __launch_bounds__(kVqThreads)
     k_vq_assign(const float *__restrict__ x, int64_t n, int32_t D, const int32_t *__restrict__ rows,
                 const float *__restrict__ cb, const float *__restrict__ cc, int32_t K,
@@ -114,17 +114,24 @@ __global__ void __launch_bounds__(kVqThreads)
 
 // One warp: stable counting sort of the batch by assigned centre.
 // off[k] (exclusive scan of the counts) is read; perm[off[k] + r] = j for the
-// r-th batch position j assigned to k, in batch order.
+// r-th batch position j assigned to k, in batch order.  The cursors live in
+// shared memory when K fits, else in `gcursor`; the next 32 centre ids are
+// loaded while the current ones are placed.
+template <bool SMEM>
 __global__ void k_vq_perm(const int32_t *__restrict__ a, int32_t b, const int32_t *__restrict__ off,
-                          int32_t K, int32_t *__restrict__ cursor, int32_t *__restrict__ perm) {
+                          int32_t K, int32_t *__restrict__ gcursor, int32_t *__restrict__ perm) {
+    __shared__ int32_t s_cur[SMEM ? kVqSmemCursors : 1];
+    int32_t *cursor = SMEM ? s_cur : gcursor;
     const int lane = threadIdx.x;
     for (int k = lane; k < K; k += 32) cursor[k] = 0;
     __syncwarp();
     const unsigned lt = (1u << lane) - 1u;
+    int next = lane < b ? a[lane] : -1 - lane;
     for (int j0 = 0; j0 < b; j0 += 32) {
         const int j = j0 + lane;
         const bool act = j < b;
-        const int k = act ? a[j] : -1 - lane;   // inactive lanes never match a centre
+        const int k = next;                     // inactive lanes hold distinct negatives
+        next = j + 32 < b ? a[j + 32] : -1 - lane;
         const unsigned peers = __match_any_sync(0xFFFFFFFFu, k);
         int rank = 0, basec = 0;
         if (act) {
@@ -138,6 +145,14 @@ __global__ void k_vq_perm(const int32_t *__restrict__ a, int32_t b, const int32_
         }
         __syncwarp();
     }
+}
+
+// Batch rows outside [0, n): *bad gets 1 (the update is then not run).
+__global__ void k_vq_check_rows(const int32_t *__restrict__ rows, int64_t total, int64_t n,
+                                unsigned int *__restrict__ bad) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool out = i < total && (rows[i] < 0 || (int64_t)rows[i] >= n);
+    if (__any_sync(0xFFFFFFFFu, out) && (threadIdx.x & 31) == 0) atomicOr(bad, 1u);
 }
 
 __global__ void k_vq_count(const int32_t *__restrict__ a, int32_t b, int32_t *__restrict__ m) {
@@ -207,21 +222,26 @@ __global__ void k_vq_retain(const int32_t *__restrict__ rows, int64_t n_retain, 
 using AssignFn = void (*)(const float *, int64_t, int32_t, const int32_t *, const float *,
                           const float *, int32_t, int32_t *, float *);
 
+template <int P>
 AssignFn pick_assign(int D) {
-    if (D <= 8) return k_vq_assign<8>;
-    if (D <= 16) return k_vq_assign<16>;
-    if (D <= 24) return k_vq_assign<24>;
-    if (D <= 32) return k_vq_assign<32>;
-    if (D <= 48) return k_vq_assign<48>;
-    return k_vq_assign<64>;
+    if (D <= 8) return k_vq_assign<8, P>;
+    if (D <= 16) return k_vq_assign<16, P>;
+    if (D <= 24) return k_vq_assign<24, P>;
+    if (D <= 32) return k_vq_assign<32, P>;
+    if (D <= 48) return k_vq_assign<48, P>;
+    return k_vq_assign<64, P>;
 }
 
+// Two vectors per thread when there are enough CTAs to fill the GPU with
+// them; one per thread (twice the CTAs) for batch-sized calls.
 mgs_status assign_launch(const float *x, int64_t n, int32_t D, const int32_t *rows, const float *cb,
                          const float *cc, int32_t K, int32_t *idx, float *score, cudaStream_t st) {
     if (n == 0) return MGS_OK;
-    const int64_t per_cta = (int64_t)kVqThreads * kVqPts;
+    const int P = n >= (int64_t)1 << 20 ? 2 : 1;
+    const int64_t per_cta = (int64_t)kVqThreads * P;
     const int64_t grid = (n + per_cta - 1) / per_cta;
-    pick_assign(D)<<<(unsigned)grid, kVqThreads, 0, st>>>(x, n, D, rows, cb, cc, K, idx, score);
+    AssignFn f = P == 2 ? pick_assign<2>(D) : pick_assign<1>(D);
+    f<<<(unsigned)grid, kVqThreads, 0, st>>>(x, n, D, rows, cb, cc, K, idx, score);
     count_launches(1);
     MGS_CUDA_TRY(cudaGetLastError());
     return MGS_OK;
@@ -291,32 +311,26 @@ extern "C" mgs_status mgs_vq_train(mgs_ctx *ctx, const float *x, int64_t n, int3
     if (iters == 0 || batch == 0) return MGS_OK;
     DeviceGuard dg(ctx->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    // batch rows must index x: checked on the host (one copy of the index array)
+    // every batch row must index x: checked on the device, one flag read back
     {
-        const size_t tot = (size_t)iters * batch;
-        int32_t *h = nullptr;
-        if (cudaMallocHost(reinterpret_cast<void **>(&h), 4 * tot) != cudaSuccess) {
-            cudaGetLastError();
-            set_error("vq: host staging of %zu indices", tot);
-            return MGS_ERR_OUT_OF_MEMORY;
+        unsigned int *bad = nullptr, hbad = 0;
+        const int64_t tot = (int64_t)iters * batch;
+        MGS_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void **>(&bad), sizeof(unsigned int), st));
+        cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(unsigned int), st);
+        if (e == cudaSuccess) {
+            k_vq_check_rows<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(batches, tot, n, bad);
+            count_launches(1);
+            e = cudaGetLastError();
         }
-        cudaError_t e = cudaMemcpyAsync(h, batches, 4 * tot, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof(hbad), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        bool bad = false;
-        int64_t at = 0;
-        if (e == cudaSuccess)
-            for (size_t i = 0; i < tot && !bad; i++)
-                if (h[i] < 0 || h[i] >= n) {
-                    bad = true;
-                    at = (int64_t)i;
-                }
-        cudaFreeHost(h);
+        cudaFreeAsync(bad, st);
         if (e != cudaSuccess) {
-            set_error("vq: batch copy: %s", cudaGetErrorString(e));
+            set_error("vq: batch check: %s", cudaGetErrorString(e));
             return MGS_ERR_CUDA;
         }
-        if (bad) {
-            set_error("vq: batch entry %lld is not a row of x", (long long)at);
+        if (hbad) {
+            set_error("vq: a batch entry is not a row of x");
             return MGS_ERR_INVALID_ARG;
         }
     }
@@ -347,7 +361,10 @@ extern "C" mgs_status mgs_vq_train(mgs_ctx *ctx, const float *x, int64_t n, int3
         if (e == cudaSuccess) {
             k_vq_count<<<(batch + 255) / 256, 256, 0, st>>>(a, batch, m);
             k_vq_scan<<<1, 1024, 0, st>>>(m, K, off);
-            k_vq_perm<<<1, 32, 0, st>>>(a, batch, off, K, cur, perm);
+            if (K <= kVqSmemCursors)
+                k_vq_perm<true><<<1, 32, 0, st>>>(a, batch, off, K, cur, perm);
+            else
+                k_vq_perm<false><<<1, 32, 0, st>>>(a, batch, off, K, cur, perm);
             const int64_t kd = (int64_t)K * D;
             k_vq_move<<<(unsigned)((kd + 255) / 256), 256, 0, st>>>(x, D, rows, perm, off, m, codebook,
                                                                       K, counts);
