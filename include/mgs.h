@@ -516,14 +516,29 @@ mgs_status mgs_vq_assign(mgs_ctx *ctx, const float *x, int64_t n, int32_t D, con
  * sum in FP64 in batch order, rounded once to FP32, and v += m.  This is the
  * per-vector update with learning rate 1 / count, carried out exactly over
  * each batch.  The random batches are the caller's (device int32
- * [iters][batch], each a row of x; checked).  codebook and counts ([K] int64,
- * zero for a fresh codebook) are updated in place; assign_out ([iters][batch]
- * int32, device, may be NULL) receives every batch's assignment.
- * Stream-ordered apart from one host check of the batch indices.
+ * [iters][batch], each a row of x; checked on the device).  codebook and
+ * counts ([K] int64, zero for a fresh codebook; K <= 49152 here) are updated
+ * in place; assign_out ([iters][batch] int32, device, may be NULL) receives
+ * every batch's assignment.  Stream-ordered apart from one 4-byte read-back
+ * of the batch check.
  */
 mgs_status mgs_vq_train(mgs_ctx *ctx, const float *x, int64_t n, int32_t D, float *codebook,
                         int32_t K, int64_t *counts, const int32_t *batches, int32_t iters,
                         int32_t batch, int32_t *assign_out, void *stream);
+
+/*
+ * Where the scores are computed.  By default (enable = 1) x.c is computed on
+ * the tensor cores (tcgen05.mma, TF32 inputs, FP32 accumulators) and every
+ * entry whose approximate score lies within twice the bound of the TF32
+ * error of the best one is re-scored exactly as above, so the results are
+ * the same; enable = 0 scores every entry on the CUDA cores.
+ * mgs_vq_stats returns, and resets, the scores of the tensor path since the
+ * last call and how many of them were re-scored exactly.  With the tensor
+ * path, mgs_vq_assign and mgs_vq_train synchronise `stream` and return
+ * MGS_ERR_TIMEOUT if a bounded wait of the tensor-core pipeline ran out.
+ */
+mgs_status mgs_vq_set_tensor_cores(mgs_ctx *ctx, int32_t enable);
+mgs_status mgs_vq_stats(mgs_ctx *ctx, int64_t *scores, int64_t *rescored);
 
 /*
  * Budget-first retention: the vectors of rows[0 .. n_retain) (the top-ranked

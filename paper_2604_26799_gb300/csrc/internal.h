@@ -82,6 +82,8 @@ struct mgs_ctx {
     std::vector<mgs::TileChoice> tiles;     // autotuned choices
     int forced_config = -1;                 // testing hook: force a tile configuration
     int n_scenes = 0;
+    int vq_tensor = 1;                      // SH assignment on the tensor cores (else CUDA cores)
+    int64_t vq_scores = 0, vq_rescored = 0; // since the last mgs_vq_stats
 };
 
 struct mgs_scene {
@@ -189,6 +191,16 @@ int64_t encode_bound(int64_t keep, int32_t G, int32_t C);
 mgs_status encode_launch(mgs_ctx *ctx, const mgs_scene *sc, const int32_t *kept, int64_t keep,
                          int32_t G, const uint8_t *d_bits, uint8_t *stream, int64_t capacity,
                          int32_t *d_sizes_out, int64_t *total_out, cudaStream_t st);
+
+// ---- SH vector quantisation on the tensor cores (vq_tc.cu) ----
+// Bytes of the codebook's MMA tiles for K entries of D dimensions.
+size_t vq_tc_workspace(int32_t K, int32_t D);
+// Lay out the codebook in `tiles` and assign x[rows[i]] (rows may be NULL)
+// with the exact path's decisions; *stats += entries re-scored exactly,
+// *err |= 1 if a bounded wait ran out (cmax2: 4 bytes of scratch).
+mgs_status vq_assign_tc(const float *x, int64_t n, int32_t D, const int32_t *rows, const float *cb,
+                        int32_t K, int32_t *idx, float *score, unsigned char *tiles, unsigned int *cmax2,
+                        unsigned long long *stats, unsigned int *err, cudaStream_t st);
 
 // ---- helpers (abi.cu) ----
 // Count kernels enqueued by this library (mgs_kernel_launches()).

@@ -10,7 +10,7 @@
 //   assigned to it so far, c = (v c + sum x) / (v + m), the batch's sum taken
 //   in FP64 in batch order and the result rounded once to FP32.
 //
-// k_vq_assign: 128 threads x 1 or 2 vectors per thread in registers (the dimension
+// k_vq_assign: 128 threads x 2 vectors per thread in registers (the dimension
 // padded with zeros to DP, a multiple of 8; adding 0 * 0 leaves an fmaf chain
 // unchanged), codebook tiles of 64 centres staged in shared memory and read
 // as float4 broadcasts.  The update is a one-warp stable counting sort of the
@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include <cfloat>
+#include <mutex>
 
 #include "internal.h"
 
@@ -27,7 +28,7 @@ namespace {
 
 constexpr int kVqThreads = 128;
 constexpr int kVqTile = 64;     // centres per shared-memory tile
-constexpr int kVqSmemCursors = 12288;   // centres whose sort cursors fit in shared memory
+constexpr int kVqMaxTrainK = 49152;      // centres whose sort counters fit in shared memory
 constexpr int kVqMaxK = 1 << 20;
 
 __global__ void k_vq_norms(const float *__restrict__ cb, int32_t K, int32_t D, float *__restrict__ cc) {
@@ -112,38 +113,59 @@ __global__ void __launch_bounds__(kVqThreads)
     }
 }
 
-// One warp: stable counting sort of the batch by assigned centre.
-// off[k] (exclusive scan of the counts) is read; perm[off[k] + r] = j for the
-// r-th batch position j assigned to k, in batch order.  The cursors live in
-// shared memory when K fits, else in `gcursor`; the next 32 centre ids are
-// loaded while the current ones are placed.
-template <bool SMEM>
-__global__ void k_vq_perm(const int32_t *__restrict__ a, int32_t b, const int32_t *__restrict__ off,
-                          int32_t K, int32_t *__restrict__ gcursor, int32_t *__restrict__ perm) {
-    __shared__ int32_t s_cur[SMEM ? kVqSmemCursors : 1];
-    int32_t *cursor = SMEM ? s_cur : gcursor;
-    const int lane = threadIdx.x;
-    for (int k = lane; k < K; k += 32) cursor[k] = 0;
-    __syncwarp();
-    const unsigned lt = (1u << lane) - 1u;
-    int next = lane < b ? a[lane] : -1 - lane;
-    for (int j0 = 0; j0 < b; j0 += 32) {
-        const int j = j0 + lane;
-        const bool act = j < b;
-        const int k = next;                     // inactive lanes hold distinct negatives
-        next = j + 32 < b ? a[j + 32] : -1 - lane;
-        const unsigned peers = __match_any_sync(0xFFFFFFFFu, k);
-        int rank = 0, basec = 0;
-        if (act) {
-            rank = __popc(peers & lt);
-            basec = cursor[k];
+// Stable counting sort of the batch by assigned centre, in three steps over
+// chunks of kVqChunk batch positions: per-chunk counts of every centre; the
+// first slot of every (chunk, centre), the centre's first slot plus the
+// counts of the earlier chunks; then each chunk places its positions, ranked among equal
+// centres by the warps in order (match_any within a warp, running counts in
+// shared memory across the warps), so positions stay in batch order.
+constexpr int kVqChunk = 256;
+
+__global__ void __launch_bounds__(kVqChunk)
+    k_vq_chunk_counts(const int32_t *__restrict__ a, int32_t b, int32_t K, int32_t *__restrict__ cnt) {
+    extern __shared__ int32_t s_cnt[];   // [K]
+    for (int k = threadIdx.x; k < K; k += kVqChunk) s_cnt[k] = 0;
+    __syncthreads();
+    const int j = blockIdx.x * kVqChunk + threadIdx.x;
+    if (j < b) atomicAdd(&s_cnt[a[j]], 1);
+    __syncthreads();
+    for (int k = threadIdx.x; k < K; k += kVqChunk) cnt[(int64_t)k * gridDim.x + blockIdx.x] = s_cnt[k];
+}
+
+// First slot of every (chunk, centre): the centre's first slot off[k] plus
+// the counts of the earlier chunks (one thread per centre, chunks in order).
+__global__ void k_vq_slots(int32_t *__restrict__ cnt, int32_t nch, const int32_t *__restrict__ off,
+                           int32_t K) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    int32_t run = off[k];
+    int32_t *row = cnt + (int64_t)k * nch;
+    for (int c = 0; c < nch; c++) {
+        const int32_t t = row[c];
+        row[c] = run;
+        run += t;
+    }
+}
+
+__global__ void __launch_bounds__(kVqChunk)
+    k_vq_chunk_place(const int32_t *__restrict__ a, int32_t b, int32_t K,
+                     const int32_t *__restrict__ slot, int32_t *__restrict__ perm) {
+    extern __shared__ int32_t s_run[];   // [K]: positions of each centre placed by earlier warps
+    for (int k = threadIdx.x; k < K; k += kVqChunk) s_run[k] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int j = blockIdx.x * kVqChunk + threadIdx.x;
+    const bool act = j < b;
+    const int k = act ? a[j] : -1 - lane;
+    const unsigned peers = __match_any_sync(0xFFFFFFFFu, k);
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+    for (int w = 0; w < kVqChunk / 32; w++) {
+        if (warp == w && act) {
+            perm[slot[(int64_t)k * gridDim.x + blockIdx.x] + s_run[k] + rank] = j;
         }
-        __syncwarp();
-        if (act) {
-            perm[off[k] + basec + rank] = j;
-            if (rank == 0) cursor[k] = basec + __popc(peers);
-        }
-        __syncwarp();
+        __syncthreads();
+        if (warp == w && act && rank == 0) s_run[k] += __popc(peers);
+        __syncthreads();
     }
 }
 
@@ -232,15 +254,15 @@ AssignFn pick_assign(int D) {
     return k_vq_assign<64, P>;
 }
 
-// Two vectors per thread when there are enough CTAs to fill the GPU with
-// them; one per thread (twice the CTAs) for batch-sized calls.
+// Two vectors per thread: each float4 broadcast of the codebook then feeds
+// eight fused multiply-adds (one vector per thread measured 2.8x slower per score).
 mgs_status assign_launch(const float *x, int64_t n, int32_t D, const int32_t *rows, const float *cb,
                          const float *cc, int32_t K, int32_t *idx, float *score, cudaStream_t st) {
     if (n == 0) return MGS_OK;
-    const int P = n >= (int64_t)1 << 20 ? 2 : 1;
+    const int P = 2;
     const int64_t per_cta = (int64_t)kVqThreads * P;
     const int64_t grid = (n + per_cta - 1) / per_cta;
-    AssignFn f = P == 2 ? pick_assign<2>(D) : pick_assign<1>(D);
+    AssignFn f = pick_assign<2>(D);
     f<<<(unsigned)grid, kVqThreads, 0, st>>>(x, n, D, rows, cb, cc, K, idx, score);
     count_launches(1);
     MGS_CUDA_TRY(cudaGetLastError());
@@ -268,6 +290,44 @@ mgs_status check_vq_args(const void *x, int64_t n, int32_t D, const void *cb, in
 
 using namespace mgs;
 
+// Per-call scratch of the tensor path: codebook tiles, then max |c|^2,
+// the re-score count and the error flag.
+struct TcScratch {
+    unsigned char *tiles = nullptr;
+    unsigned int *cmax2 = nullptr;
+    unsigned long long *stats = nullptr;
+    unsigned int *err = nullptr;
+};
+
+static mgs_status tc_scratch(int32_t K, int32_t D, cudaStream_t st, void **base, TcScratch *T) {
+    const size_t tb = (vq_tc_workspace(K, D) + 255) & ~(size_t)255;
+    MGS_CUDA_TRY(cudaMallocAsync(base, tb + 32, st));
+    unsigned char *p = static_cast<unsigned char *>(*base);
+    T->tiles = p;
+    T->stats = reinterpret_cast<unsigned long long *>(p + tb);
+    T->cmax2 = reinterpret_cast<unsigned int *>(p + tb + 8);
+    T->err = reinterpret_cast<unsigned int *>(p + tb + 12);
+    MGS_CUDA_TRY(cudaMemsetAsync(p + tb, 0, 32, st));
+    return MGS_OK;
+}
+
+// Reads the re-score count and the error flag (synchronises `st`).
+static mgs_status tc_finish(mgs_ctx *ctx, const TcScratch &T, int64_t scores, cudaStream_t st) {
+    unsigned long long h[2] = {0, 0};
+    MGS_CUDA_TRY(cudaMemcpyAsync(h, T.stats, 16, cudaMemcpyDeviceToHost, st));
+    MGS_CUDA_TRY(cudaStreamSynchronize(st));
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        ctx->vq_scores += scores;
+        ctx->vq_rescored += (int64_t)h[0];
+    }
+    if ((h[1] >> 32) & 1u) {   // err: the upper half of the second word
+        set_error("vq: a tensor-core wait ran out; the outputs are incomplete");
+        return MGS_ERR_TIMEOUT;
+    }
+    return MGS_OK;
+}
+
 extern "C" mgs_status mgs_vq_assign(mgs_ctx *ctx, const float *x, int64_t n, int32_t D,
                                     const float *codebook, int32_t K, int32_t *index_out,
                                     float *score_out, void *stream) {
@@ -279,6 +339,16 @@ extern "C" mgs_status mgs_vq_assign(mgs_ctx *ctx, const float *x, int64_t n, int
     MGS_TRY(check_vq_args(x, n, D, codebook, K));
     DeviceGuard dg(ctx->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (ctx->vq_tensor) {
+        void *base = nullptr;
+        TcScratch T;
+        MGS_TRY(tc_scratch(K, D, st, &base, &T));
+        mgs_status s = vq_assign_tc(x, n, D, nullptr, codebook, K, index_out, score_out, T.tiles, T.cmax2,
+                                    T.stats, T.err, st);
+        if (s == MGS_OK) s = tc_finish(ctx, T, n * (int64_t)K, st);
+        cudaFreeAsync(base, st);
+        return s;
+    }
     float *cc = nullptr;
     MGS_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void **>(&cc), sizeof(float) * (size_t)K, st));
     k_vq_norms<<<(K + 255) / 256, 256, 0, st>>>(codebook, K, D, cc);
@@ -294,6 +364,29 @@ extern "C" mgs_status mgs_vq_assign(mgs_ctx *ctx, const float *x, int64_t n, int
     return s;
 }
 
+extern "C" mgs_status mgs_vq_set_tensor_cores(mgs_ctx *ctx, int32_t enable) {
+    clear_error();
+    if (!ctx) {
+        set_error("ctx must be non-NULL");
+        return MGS_ERR_INVALID_ARG;
+    }
+    ctx->vq_tensor = enable ? 1 : 0;
+    return MGS_OK;
+}
+
+extern "C" mgs_status mgs_vq_stats(mgs_ctx *ctx, int64_t *scores, int64_t *rescored) {
+    clear_error();
+    if (!ctx || !scores || !rescored) {
+        set_error("ctx, scores and rescored must be non-NULL");
+        return MGS_ERR_INVALID_ARG;
+    }
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    *scores = ctx->vq_scores;
+    *rescored = ctx->vq_rescored;
+    ctx->vq_scores = ctx->vq_rescored = 0;
+    return MGS_OK;
+}
+
 extern "C" mgs_status mgs_vq_train(mgs_ctx *ctx, const float *x, int64_t n, int32_t D,
                                    float *codebook, int32_t K, int64_t *counts,
                                    const int32_t *batches, int32_t iters, int32_t batch,
@@ -306,6 +399,10 @@ extern "C" mgs_status mgs_vq_train(mgs_ctx *ctx, const float *x, int64_t n, int3
     MGS_TRY(check_vq_args(x, n, D, codebook, K));
     if (!is_device_pointer(counts) || !is_device_pointer(batches)) {
         set_error("vq: counts and batches must be device memory");
+        return MGS_ERR_INVALID_ARG;
+    }
+    if (K > kVqMaxTrainK) {
+        set_error("vq train: K = %d exceeds %d", K, kVqMaxTrainK);
         return MGS_ERR_INVALID_ARG;
     }
     if (iters == 0 || batch == 0) return MGS_OK;
@@ -335,7 +432,8 @@ extern "C" mgs_status mgs_vq_train(mgs_ctx *ctx, const float *x, int64_t n, int3
         }
     }
     const size_t b_cc = 4 * (size_t)K, b_m = 4 * (size_t)K, b_off = 4 * (size_t)K,
-                 b_cur = 4 * (size_t)K, b_a = 4 * (size_t)batch, b_perm = 4 * (size_t)batch;
+                 b_cur = 4 * (size_t)K * (size_t)((batch + kVqChunk - 1) / kVqChunk),
+                 b_a = 4 * (size_t)batch, b_perm = 4 * (size_t)batch;
     unsigned char *ws = nullptr;
     const size_t ws_bytes = b_cc + b_m + b_off + b_cur + b_a + b_perm + 64;
     if (cudaMallocAsync(reinterpret_cast<void **>(&ws), ws_bytes, st) != cudaSuccess) {
@@ -343,33 +441,46 @@ extern "C" mgs_status mgs_vq_train(mgs_ctx *ctx, const float *x, int64_t n, int3
         set_error("vq workspace of %zu bytes", ws_bytes);
         return MGS_ERR_OUT_OF_MEMORY;
     }
+    const int smem_k = (int)(sizeof(int32_t) * (size_t)K);
+    if (smem_k > 48 * 1024) {
+        cudaFuncSetAttribute(k_vq_chunk_counts, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_k);
+        cudaFuncSetAttribute(k_vq_chunk_place, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_k);
+    }
     float *cc = reinterpret_cast<float *>(ws);
     int32_t *m = reinterpret_cast<int32_t *>(ws + b_cc);
     int32_t *off = m + K;
-    int32_t *cur = off + K;
-    int32_t *a_ws = cur + K;
+    int32_t *ccnt = off + K;
+    int32_t *a_ws = reinterpret_cast<int32_t *>(reinterpret_cast<unsigned char *>(ccnt) + b_cur);
     int32_t *perm = a_ws + batch;
     mgs_status s = MGS_OK;
+    void *tc_base = nullptr;
+    TcScratch T;
+    if (ctx->vq_tensor) s = tc_scratch(K, D, st, &tc_base, &T);
     for (int t = 0; t < iters && s == MGS_OK; t++) {
         const int32_t *rows = batches + (int64_t)t * batch;
         int32_t *a = assign_out ? assign_out + (int64_t)t * batch : a_ws;
-        k_vq_norms<<<(K + 255) / 256, 256, 0, st>>>(codebook, K, D, cc);
-        count_launches(1);
-        s = assign_launch(x, batch, D, rows, codebook, cc, K, a, nullptr, st);
+        if (ctx->vq_tensor) {
+            s = vq_assign_tc(x, batch, D, rows, codebook, K, a, nullptr, T.tiles, T.cmax2, T.stats, T.err, st);
+        } else {
+            k_vq_norms<<<(K + 255) / 256, 256, 0, st>>>(codebook, K, D, cc);
+            count_launches(1);
+            s = assign_launch(x, batch, D, rows, codebook, cc, K, a, nullptr, st);
+        }
         if (s != MGS_OK) break;
         cudaError_t e = cudaMemsetAsync(m, 0, b_m, st);
         if (e == cudaSuccess) {
             k_vq_count<<<(batch + 255) / 256, 256, 0, st>>>(a, batch, m);
             k_vq_scan<<<1, 1024, 0, st>>>(m, K, off);
-            if (K <= kVqSmemCursors)
-                k_vq_perm<true><<<1, 32, 0, st>>>(a, batch, off, K, cur, perm);
-            else
-                k_vq_perm<false><<<1, 32, 0, st>>>(a, batch, off, K, cur, perm);
+            const unsigned nch = (unsigned)((batch + kVqChunk - 1) / kVqChunk);
+            const size_t ks = sizeof(int32_t) * (size_t)K;
+            k_vq_chunk_counts<<<nch, kVqChunk, ks, st>>>(a, batch, K, ccnt);
+            k_vq_slots<<<(K + 255) / 256, 256, 0, st>>>(ccnt, (int32_t)nch, off, K);
+            k_vq_chunk_place<<<nch, kVqChunk, ks, st>>>(a, batch, K, ccnt, perm);
             const int64_t kd = (int64_t)K * D;
             k_vq_move<<<(unsigned)((kd + 255) / 256), 256, 0, st>>>(x, D, rows, perm, off, m, codebook,
                                                                       K, counts);
             k_vq_counts<<<(K + 255) / 256, 256, 0, st>>>(counts, m, K);
-            count_launches(5);
+            count_launches(7);
             e = cudaGetLastError();
         }
         if (e != cudaSuccess) {
@@ -377,6 +488,8 @@ extern "C" mgs_status mgs_vq_train(mgs_ctx *ctx, const float *x, int64_t n, int3
             s = MGS_ERR_CUDA;
         }
     }
+    if (s == MGS_OK && ctx->vq_tensor) s = tc_finish(ctx, T, (int64_t)iters * batch * K, st);
+    if (tc_base) cudaFreeAsync(tc_base, st);
     cudaFreeAsync(ws, st);
     return s;
 }

@@ -150,6 +150,8 @@ _SIGS = {
     "mgs_vq_train": [_P, _P, ctypes.c_int64, ctypes.c_int32, _P, ctypes.c_int32, _P, _P, ctypes.c_int32,
                      ctypes.c_int32, _P, _P],
     "mgs_vq_retain": [_P, _P, ctypes.c_int64, ctypes.c_int32, _P, _P],
+    "mgs_vq_set_tensor_cores": [_P, ctypes.c_int32],
+    "mgs_vq_stats": [_P, _P, _P],
     "mgs_search_calibrated": [_P, _P, ctypes.POINTER(mgs_grid), _P, ctypes.POINTER(mgs_table_layout),
                               ctypes.POINTER(mgs_calib_opts), ctypes.POINTER(mgs_calib_result), _P],
     "mgs_solve_budgets_device": [_P, _P, ctypes.POINTER(mgs_table_layout), ctypes.POINTER(mgs_grid),
@@ -325,6 +327,18 @@ def mgs_vq_train(ctx: int, x, codebook, counts, batches, assign_out=None, stream
     iters, b = batches.shape
     _check(lib().mgs_vq_train(ctx, _ptr(x), n, D, _ptr(codebook), codebook.shape[0], _ptr(counts),
                               _ptr(batches), iters, b, _ptr(assign_out), _stream(stream)))
+
+
+def mgs_vq_set_tensor_cores(ctx: int, enable: bool):
+    """Score on the tensor cores with exact re-scoring (default) or on the CUDA cores."""
+    _check(lib().mgs_vq_set_tensor_cores(ctx, int(bool(enable))))
+
+
+def mgs_vq_stats(ctx: int) -> tuple[int, int]:
+    """(scores, exactly re-scored entries) of the tensor path since the last call."""
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().mgs_vq_stats(ctx, ctypes.addressof(a), ctypes.addressof(b)))
+    return a.value, b.value
 
 
 def mgs_vq_retain(ctx: int, rows, K: int, index, stream=None):

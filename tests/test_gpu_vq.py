@@ -27,6 +27,15 @@ def ctx():
     mgs.mgs_destroy(c)
 
 
+@pytest.fixture(params=["tensor", "cuda"])
+def path(ctx, request):
+    """Both score paths: tcgen05 with exact re-scores, and the CUDA cores."""
+    mgs.mgs_vq_set_tensor_cores(ctx, request.param == "tensor")
+    mgs.mgs_vq_stats(ctx)
+    yield request.param
+    mgs.mgs_vq_set_tensor_cores(ctx, True)
+
+
 def sh_rows(n, seed, D=45):
     attrs, _ = synth.make_scene(n, seed=seed)
     x = np.ascontiguousarray(attrs[:, 6:51])
@@ -37,7 +46,7 @@ def sh_rows(n, seed, D=45):
 
 @pytest.mark.parametrize("n,D,K", [(20_000, 45, 1000), (777, 3, 70), (5000, 16, 64), (3001, 64, 129),
                                    (1, 45, 7), (300, 45, 1), (2500, 33, 300)])
-def test_assign_matches_oracle(ctx, n, D, K):
+def test_assign_matches_oracle(ctx, path, n, D, K):
     x = sh_rows(n, seed=n + D, D=D)
     rows = synth.vq_init_rows(n, min(K, n), seed=K)
     cb = x[rows] if K <= n else x[np.arange(K) % n]
@@ -52,7 +61,7 @@ def test_assign_matches_oracle(ctx, n, D, K):
     assert np.array_equal(score.cpu().numpy().view(np.uint32), ref_s.view(np.uint32))
 
 
-def test_assign_ties_to_lower_index(ctx):
+def test_assign_ties_to_lower_index(ctx, path):
     x = sh_rows(500, seed=3)
     cb = np.repeat(x[:8], 3, axis=0)              # every entry three times
     dev = torch.device("cuda:0")
@@ -63,7 +72,7 @@ def test_assign_ties_to_lower_index(ctx):
 
 
 @pytest.mark.parametrize("n,K,batch,iters", [(30_000, 256, 4096, 6), (4000, 70, 999, 4), (2000, 5, 1, 3)])
-def test_train_matches_oracle(ctx, n, K, batch, iters):
+def test_train_matches_oracle(ctx, path, n, K, batch, iters):
     x = sh_rows(n, seed=K)
     cb0 = x[synth.vq_init_rows(n, K, seed=n)]
     bt = synth.vq_batches(n, iters, batch, seed=K + batch)
@@ -79,7 +88,7 @@ def test_train_matches_oracle(ctx, n, K, batch, iters):
     assert np.array_equal(cbd.cpu().numpy().view(np.uint32), ref_cb.view(np.uint32))
 
 
-def test_vq_scene_scale(ctx):
+def test_vq_scene_scale(ctx, path):
     """5.27 M x 45, K = 4096: one mini-batch of 65536 (the bench's batch) equal to
     the oracle's, then the final assignment of every vector, checked on a sample."""
     w = synth.SCENE
@@ -122,3 +131,34 @@ def test_retain_and_errors(ctx):
     wide = torch.zeros((10, 65), dtype=torch.float32, device=dev)
     with pytest.raises(mgs.MgsError):                                  # D > 64
         mgs.mgs_vq_assign(ctx, wide, wide[:2].clone())
+
+
+def test_tensor_path_rescores_few(ctx):
+    """The tensor path re-scores every vector's winner and few others: the TF32
+    bound is tight enough that the candidates stay a small multiple of n."""
+    n, K = 20_000, 1024
+    x = sh_rows(n, seed=8)
+    cb = np.ascontiguousarray(x[synth.vq_init_rows(n, K, seed=9)])
+    dev = torch.device("cuda:0")
+    mgs.mgs_vq_set_tensor_cores(ctx, True)
+    mgs.mgs_vq_stats(ctx)
+    idx, _ = mgs.mgs_vq_assign(ctx, torch.from_numpy(x).to(dev), torch.from_numpy(cb).to(dev))
+    scores, rescored = mgs.mgs_vq_stats(ctx)
+    assert scores == n * K
+    assert n <= rescored <= 8 * n, rescored
+    assert np.array_equal(idx.cpu().numpy(), oracle.vq_assign(x, cb)[0])
+
+
+def test_tensor_path_near_ties(ctx):
+    """Entries a few ulp apart and vectors on their midpoints: the approximate
+    scores cannot separate them, the exact re-scores do."""
+    rng = np.random.default_rng(12)
+    base = rng.laplace(0, 0.05, size=(64, 45)).astype(np.float32)
+    cb = np.concatenate([base, np.nextafter(base, np.float32(1)), base * np.float32(1 + 2 ** -20)])
+    x = np.concatenate([base, (base + np.nextafter(base, np.float32(1))) / 2,
+                        rng.laplace(0, 0.05, size=(500, 45)).astype(np.float32)]).astype(np.float32)
+    dev = torch.device("cuda:0")
+    mgs.mgs_vq_set_tensor_cores(ctx, True)
+    idx, _ = mgs.mgs_vq_assign(ctx, torch.from_numpy(np.ascontiguousarray(x)).to(dev),
+                               torch.from_numpy(np.ascontiguousarray(cb)).to(dev))
+    assert np.array_equal(idx.cpu().numpy(), oracle.vq_assign(x, cb)[0])
