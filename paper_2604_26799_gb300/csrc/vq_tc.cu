@@ -40,7 +40,7 @@ constexpr long long kWaitCycles = 1ll << 31;    // ~1 s at 2 GHz: a wait that lo
 constexpr long long kDrainCycles = 1ll << 28;   // draining one's own copies and MMAs
 
 __host__ __device__ constexpr int tile_bytes(int DP) { return kTcN * DP * 4; }
-__host__ __device__ constexpr int tile_stride(int DP) { return tile_bytes(DP) + kTcN * 4; }
+__host__ __device__ constexpr int tile_stride(int DP) { return tile_bytes(DP) + 2 * kTcN * 4; }
 
 // Byte offset of element (row r, column k) in a core-matrix tile.
 __host__ __device__ inline int cm_offset(int r, int k, int DP) {
@@ -152,8 +152,9 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 }
 
 // The codebook in MMA tiles: tile t holds entries 128 t .. 128 t + 127 in the
-// core-matrix layout (zeros beyond K and beyond D), then their exact norms
-// |c|^2 (the fmaf chain of the exact path).  *cmax2 gets max |c|^2 (as bits).
+// core-matrix layout (zeros beyond K and beyond D), then their exact squared
+// norms |c|^2 (the fmaf chain of the exact path), then upper bounds of their
+// norms |c|.  *cmax2 gets max |c|^2 (as bits).
 template <int DP>
 __global__ void k_vq_tc_prep(const float *__restrict__ cb, int32_t K, int32_t D,
                              unsigned char *__restrict__ tiles, unsigned int *__restrict__ cmax2) {
@@ -173,6 +174,7 @@ __global__ void k_vq_tc_prep(const float *__restrict__ cb, int32_t K, int32_t D,
         *reinterpret_cast<float *>(tile + cm_offset(r, k, DP)) = v;
     }
     reinterpret_cast<float *>(tile + tile_bytes(DP))[r] = cc;
+    reinterpret_cast<float *>(tile + tile_bytes(DP))[kTcN + r] = sqrtf(cc) * 1.001f;
     if (e < K) atomicMax(cmax2, __float_as_uint(cc));   // non-negative floats order as integers
 }
 
@@ -210,13 +212,17 @@ __global__ void __launch_bounds__(kTcThreads)
     float xx = 0.0f;
 #pragma unroll
     for (int d = 0; d < DP; d++) xx = __fmaf_rn(xr[d], xr[d], xx);
-    // margin: |approx - exact| <= 2^-8 |x| max|c| + rounding; twice that, doubled
+    // Error bound of entry k's approximate score: TF32 keeps 10 of the 23
+    // fraction bits of each operand, so each product x_d c_d is off by less
+    // than 2^-9 |x_d c_d|, the score by less than 2^-8 |x| |c_k|; with 5 %
+    // allowance for the FP32 accumulation and rounding terms of both scores,
+    // m_k = a |c_k|, a = 1.05 2^-8 |x| + 2^-21 |x| + 2^-22 max|c| (norms
+    // rounded up).  Entry k can be the exact argmin only if
+    // approx_k - m_k <= min_j (approx_j + m_j).
     const float cm2 = __uint_as_float(__ldg(cmax2));
     const float xn = sqrtf(xx) * 1.001f, cn = sqrtf(cm2) * 1.001f;
-    const float xc = xn * cn;
-    const float margin = 0.0078125f * xc + 2.384185791e-7f * (cm2 + 2.0f * xc) + 1e-30f;
-    const float m2 = 2.0f * margin;
-    const bool rescore_all = !(m2 < FLT_MAX);   // a non-finite bound: test every entry exactly
+    const float am = xn * (0.00410156250f + 4.76837158e-7f) + 2.38418579e-7f * cn + 1e-30f;
+    const bool rescore_all = !(am * cn < 1e30f);   // a non-finite bound: test every entry exactly
 
     if (warp == 0) tmem_alloc(&s_tmem, kTcN);
     if (t == 0) {
@@ -240,7 +246,7 @@ __global__ void __launch_bounds__(kTcThreads)
         }
     }
 
-    float best_approx = FLT_MAX;
+    float best_up = FLT_MAX;   // min over the entries seen of approx + m
     float best_s = 0.0f;
     int best_k = -1;
     unsigned long long rescored = 0;
@@ -269,37 +275,66 @@ __global__ void __launch_bounds__(kTcThreads)
         if (s_abort) break;
         tc_fence_after();
 
-        // ---- candidates of this tile (this thread's vector = TMEM lane t): the
-        // approximate test column by column, then exact re-scores in ascending k
+        // ---- candidates of this tile (this thread's vector = TMEM lane t).  A
+        // chunk of 32 entries whose smallest approximate score is above the
+        // threshold holds no candidate (with a finite margin every approximate
+        // score is finite); the others are tested entry by entry and their
+        // candidates re-scored exactly, in ascending k.
         const float *ccs = reinterpret_cast<const float *>(tileB + TB);
+        const float *nrs = ccs + kTcN;
 #pragma unroll 1
         for (int q = 0; q < kTcN / 32; q++) {
             float acc[32];
             tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(q * 32), acc);
             const int k0 = tt * kTcN + q * 32;
+            const float4 *cc4 = reinterpret_cast<const float4 *>(ccs + q * 32);
+            const float4 *nr4 = reinterpret_cast<const float4 *>(nrs + q * 32);
+            float lo[32], up[32];
+#pragma unroll
+            for (int j4 = 0; j4 < 8; j4++) {
+                const float4 c = cc4[j4], nr = nr4[j4];
+                const float cj[4] = {c.x, c.y, c.z, c.w}, nj[4] = {nr.x, nr.y, nr.z, nr.w};
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const float ap = __fmaf_rn(-2.0f, acc[4 * j4 + u], cj[u]);
+                    lo[4 * j4 + u] = __fmaf_rn(-am, nj[u], ap);
+                    up[4 * j4 + u] = __fmaf_rn(am, nj[u], ap);
+                }
+            }
+            const bool whole = k0 + 32 <= K;
+            if (whole && !rescore_all) {
+                float mlo = lo[0], mup = up[0];
+#pragma unroll
+                for (int j = 1; j < 32; j++) {
+                    mlo = fminf(mlo, lo[j]);
+                    mup = fminf(mup, up[j]);
+                }
+                if (mlo > best_up) {   // no candidate in this chunk
+                    best_up = fminf(best_up, mup);
+                    continue;
+                }
+            }
             uint32_t cand = 0;
 #pragma unroll
             for (int j = 0; j < 32; j++) {
-                const float approx = __fmaf_rn(-2.0f, acc[j], ccs[q * 32 + j]);
                 const bool live = k0 + j < K;
-                const bool c = live && (rescore_all || k0 + j == 0 || !(approx > best_approx + m2));
+                if (live) best_up = fminf(best_up, up[j]);
+                const bool c = live && (rescore_all || k0 + j == 0 || !(lo[j] > best_up));
                 cand |= (uint32_t)c << j;
-                if (live) best_approx = fminf(best_approx, approx);
             }
             if (row < 0) cand = 0;
             while (cand) {
                 const int j = __ffs(cand) - 1;
                 cand &= cand - 1u;
-                const int k = k0 + j;
-                const float *c = cb + (int64_t)k * D;
+                const int kk = q * 32 + j;
                 float dot = 0.0f;
 #pragma unroll
                 for (int d = 0; d < DP; d++)
-                    if (d < D) dot = __fmaf_rn(xr[d], __ldg(c + d), dot);
-                const float sc = __fmaf_rn(-2.0f, dot, ccs[q * 32 + j]);
+                    if (d < D) dot = __fmaf_rn(xr[d], *reinterpret_cast<const float *>(tileB + cm_offset(kk, d, DP)), dot);
+                const float sc = __fmaf_rn(-2.0f, dot, ccs[kk]);
                 if (best_k < 0 || sc < best_s) {
                     best_s = sc;
-                    best_k = k;
+                    best_k = k0 + j;
                 }
                 rescored++;
             }
