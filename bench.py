@@ -88,11 +88,20 @@ def barrier(world: int):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons, sampled every 200 ms while running."""
+    """nvidia-smi clocks and throttle reasons, sampled every 50 ms while running.
+    Started before the warm-up (nvidia-smi takes a while to start); mark() and
+    unmark() bracket the timed region, whose samples the summary reports."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,timestamp")
+    t0 = t1 = None
+
+    def mark(self):
+        self.t0 = time.time()
+
+    def unmark(self):
+        self.t1 = time.time()
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
@@ -104,7 +113,7 @@ class ClockSampler:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -122,17 +131,24 @@ class ClockSampler:
     def summary(self) -> dict:
         if self.proc is None or not os.path.exists(self.path):
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        import datetime
         rows = []
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+                ts = datetime.datetime.strptime(parts[9], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9], ts))
             except ValueError:
                 continue
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        if self.t0 is not None and self.t1 is not None:
+            inside = [r for r in rows if self.t0 - 0.05 <= r[3] <= self.t1 + 0.05]
+            if not inside:   # the nearest sample to the timed region
+                inside = [min(rows, key=lambda r: abs(r[3] - 0.5 * (self.t0 + self.t1)))]
+            rows = inside
         mx = max(r[1] for r in rows)
         load = [r for r in rows if r[0] >= 0.5 * mx] or rows
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
@@ -264,14 +280,13 @@ def run_gpu(args):
         tune = {"chosen": mgs.mgs_tile_config_name(chosen),
                 "ms": {mgs.mgs_tile_config_name(i): round(float(t), 3)
                        for i, t in enumerate(ms_cfg) if t > 0}}
-    for _ in range(args.warmup):
-        sol = step(False)
-    torch.cuda.synchronize()
-    barrier(ws)
-    launches0 = mgs.mgs_kernel_launches()
     with ClockSampler(dev.index) as clk:
+        for _ in range(args.warmup):   # nvidia-smi starts meanwhile
+            sol = step(False)
         torch.cuda.synchronize()
         barrier(ws)
+        launches0 = mgs.mgs_kernel_launches()
+        clk.mark()
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(st)
@@ -279,6 +294,7 @@ def run_gpu(args):
             sol = step(True)
         ev1.record(st)
         torch.cuda.synchronize()
+        clk.unmark()
         barrier(ws)
     launches = (mgs.mgs_kernel_launches() - launches0) // args.steps
     ms = ev0.elapsed_time(ev1) / args.steps
@@ -979,7 +995,7 @@ def run_vq(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mgs", choices=["mgs", "reference"])
     ap.add_argument("--workload", default="scene", choices=["scene", "batch", "serve", "large", "preprocess", "raht", "raht_search",

@@ -40,6 +40,7 @@ constexpr long long kWaitCycles = 1ll << 31;    // ~1 s at 2 GHz: a wait that lo
 constexpr long long kDrainCycles = 1ll << 28;   // draining one's own copies and MMAs
 
 __host__ __device__ constexpr int tile_bytes(int DP) { return kTcN * DP * 4; }
+// tile: core matrices, then |c|^2 [128] and upper bounds of |c| [128]
 __host__ __device__ constexpr int tile_stride(int DP) { return tile_bytes(DP) + 2 * kTcN * 4; }
 
 // Byte offset of element (row r, column k) in a core-matrix tile.
@@ -173,8 +174,10 @@ __global__ void k_vq_tc_prep(const float *__restrict__ cb, int32_t K, int32_t D,
         }
         *reinterpret_cast<float *>(tile + cm_offset(r, k, DP)) = v;
     }
-    reinterpret_cast<float *>(tile + tile_bytes(DP))[r] = cc;
-    reinterpret_cast<float *>(tile + tile_bytes(DP))[kTcN + r] = sqrtf(cc) * 1.001f;
+    float *tail = reinterpret_cast<float *>(tile + tile_bytes(DP));
+    const float nr = sqrtf(cc) * 1.001f;
+    tail[r] = cc;
+    tail[kTcN + r] = nr;
     if (e < K) atomicMax(cmax2, __float_as_uint(cc));   // non-negative floats order as integers
 }
 
@@ -289,37 +292,38 @@ __global__ void __launch_bounds__(kTcThreads)
             const int k0 = tt * kTcN + q * 32;
             const float4 *cc4 = reinterpret_cast<const float4 *>(ccs + q * 32);
             const float4 *nr4 = reinterpret_cast<const float4 *>(nrs + q * 32);
-            float lo[32], up[32];
+            float ap[32], lo[32];
+            float mlo = FLT_MAX;
 #pragma unroll
             for (int j4 = 0; j4 < 8; j4++) {
                 const float4 c = cc4[j4], nr = nr4[j4];
                 const float cj[4] = {c.x, c.y, c.z, c.w}, nj[4] = {nr.x, nr.y, nr.z, nr.w};
 #pragma unroll
                 for (int u = 0; u < 4; u++) {
-                    const float ap = __fmaf_rn(-2.0f, acc[4 * j4 + u], cj[u]);
-                    lo[4 * j4 + u] = __fmaf_rn(-am, nj[u], ap);
-                    up[4 * j4 + u] = __fmaf_rn(am, nj[u], ap);
+                    const int j = 4 * j4 + u;
+                    ap[j] = __fmaf_rn(-2.0f, acc[j], cj[u]);
+                    lo[j] = __fmaf_rn(-am, nj[u], ap[j]);
+                    mlo = fminf(mlo, lo[j]);
                 }
             }
+            // no entry of this chunk qualifies when its smallest lower bound exceeds
+            // the threshold (with a finite margin every bound is finite)
             const bool whole = k0 + 32 <= K;
-            if (whole && !rescore_all) {
-                float mlo = lo[0], mup = up[0];
+            if (whole && !rescore_all && mlo > best_up) continue;
 #pragma unroll
-                for (int j = 1; j < 32; j++) {
-                    mlo = fminf(mlo, lo[j]);
-                    mup = fminf(mup, up[j]);
-                }
-                if (mlo > best_up) {   // no candidate in this chunk
-                    best_up = fminf(best_up, mup);
-                    continue;
+            for (int j4 = 0; j4 < 8; j4++) {
+                const float4 nr = nr4[j4];
+                const float nj[4] = {nr.x, nr.y, nr.z, nr.w};
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int j = 4 * j4 + u;
+                    if (k0 + j < K) best_up = fminf(best_up, __fmaf_rn(am, nj[u], ap[j]));
                 }
             }
             uint32_t cand = 0;
 #pragma unroll
             for (int j = 0; j < 32; j++) {
-                const bool live = k0 + j < K;
-                if (live) best_up = fminf(best_up, up[j]);
-                const bool c = live && (rescore_all || k0 + j == 0 || !(lo[j] > best_up));
+                const bool c = k0 + j < K && (rescore_all || k0 + j == 0 || !(lo[j] > best_up));
                 cand |= (uint32_t)c << j;
             }
             if (row < 0) cand = 0;
