@@ -7,20 +7,24 @@
 //   k_rh_starts  first Morton position and code of every voxel
 //   k_rh_means   one thread per voxel: mean of its Gaussians, summed in
 //                Morton order (weight 1)
-//   per step s = 0 .. 3d - 1 (the node count, the AC offset, the current list
-//   and the pending level live in device memory; the host reads them once per
-//   octree level to size the grids):
-//     k_rh_scan_pairs  flag i when nodes i, i + 1 agree above bit 1 of their
-//                 codes, fused with the block-local scan; k_scan_sums: the block
-//                 offsets and the number of pairs
-//     k_rh_merge  the parent list (code >> 1, slot): a pair merges in place into
-//                 the lower node's slot by the printed T, with its entries
-//                 t1 = sqrt(w1) / sqrt(w1 + w2), t2 = sqrt(w2) / sqrt(w1 + w2) formed
-//                 once per pair: DC = t1 x1 + t2 x2, weight w1 + w2, and it emits
-//                 AC = t1 x2 - t2 x1 at the next AC slot; an unpaired node moves up.
-//                 Attribute vectors stay in their voxel slots: only pairs touch them.
-//     k_rh_advance  node count -= pairs, AC offset += pairs, swap the lists; a
-//                 step without pairs only raises the pending level
+//   the merge tree: RAHT step s merges the nodes that are siblings at bit s
+//   of the binary trie over the sorted voxel codes, so the internal node
+//   between voxels g and g + 1 merges at step delta(g) = the highest bit in
+//   which their codes differ, and every merge of the transform is one
+//   internal node:
+//     k_rh_delta, k_rh_delta_slots, k_rh_delta_place  delta of every internal
+//                 node and its AC slot: ACs listed step by step, ascending
+//                 code within a step (a stable counting sort on delta)
+//     k_rh_tree   one thread per voxel walks up; a node [l, r] merges next with
+//                 the neighbour across the split of smaller delta; the first
+//                 child to arrive stops, the second merges both by the printed
+//                 T, with its entries t1 = sqrt(w1) / sqrt(w1 + w2),
+//                 t2 = sqrt(w2) / sqrt(w1 + w2) formed once per pair:
+//                 DC = t1 x1 + t2 x2 (into the left child's slot), weight
+//                 w1 + w2, AC = t1 x2 - t2 x1 at the node's AC slot.
+//   (An earlier version ran the 3d steps as 4 launches each over the whole
+//   node list; with sparse fine levels most of its ~20 heavy steps moved every
+//   node for a handful of pairs.)
 // FP32 arithmetic with integer weights.  (An FP64 version matched the FP64
 // oracle bit for bit, but GB300's FP64 pipe ran 73-87% busy and bounded it:
 // 11.4 ms for 5.27 M voxels.)  Every merge is an orthonormal rotation, so the
@@ -152,131 +156,114 @@ __global__ void k_rh_means(const float *__restrict__ slabs, int64_t n, const int
     w[v] = 1u;
 }
 
-struct RahtState {
-    long long m;         // nodes in the current list
-    long long ac_base;   // ACs emitted so far
-    int cur;             // which of the two lists is current
-    int pending;         // levels not yet applied to the current list's codes
-};
+// ---- the merge tree ----
+// The nodes RAHT merges at step s are siblings at bit s of a binary trie over
+// the sorted voxel codes: the internal node between voxels g and g + 1 merges
+// at step delta(g), the highest bit in which their codes differ.  A node
+// covering voxels [l, r] merges next with the neighbour across the split of
+// smaller delta (l - 1 or r; the two are never equal for distinct codes).
+constexpr int kDeltaKeys = 64;
+constexpr int kDeltaChunk = 1024;
 
-// Steps whose list has no pair change nothing but the level: they only raise
-// `pending`, and the codes are compared (and shifted when the list is next
-// rewritten) by pending + 1 bits.
-// Pair flags of the current list fused with the block-local exclusive scan
-// (the flags are recomputed from the codes by k_rh_merge; no flag array).
-__device__ __forceinline__ unsigned int pair_flag(const uint64_t *key, int64_t i, int64_t m, int sh) {
-    return (i + 1 < m && (key[i] >> sh) == (key[i + 1] >> sh)) ? 1u : 0u;
-}
-
-__global__ void __launch_bounds__(kScanBlock) k_rh_scan_pairs(const uint64_t *__restrict__ key0,
-                                                              const uint64_t *__restrict__ key1,
-                                                              const RahtState *st, int64_t cap,
-                                                              unsigned int *__restrict__ out,
-                                                              unsigned int *__restrict__ block_sum) {
-    __shared__ unsigned int s_w[32];
-    const int64_t i = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
-    const int64_t m = st->m;
-    const uint64_t *key = st->cur ? key1 : key0;
-    const unsigned int v = i < cap ? pair_flag(key, i, m, st->pending + 1) : 0u;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    unsigned int x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const unsigned int t = __shfl_up_sync(0xFFFFFFFFu, x, o);
-        if (lane >= o) x += t;
-    }
-    if (lane == 31) s_w[wid] = x;
+// delta of every internal node, and per chunk of 1024 nodes the count of each delta
+__global__ void __launch_bounds__(kDeltaChunk)
+    k_rh_delta(const uint64_t *__restrict__ vc, int64_t V, unsigned char *__restrict__ delta,
+               unsigned int *__restrict__ cnt) {
+    __shared__ unsigned int s_cnt[kDeltaKeys];
+    if (threadIdx.x < kDeltaKeys) s_cnt[threadIdx.x] = 0;
     __syncthreads();
-    if (wid == 0) {
-        unsigned int y = s_w[lane];
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned int t = __shfl_up_sync(0xFFFFFFFFu, y, o);
-            if (lane >= o) y += t;
-        }
-        s_w[lane] = y;
+    const int64_t g = (int64_t)blockIdx.x * kDeltaChunk + threadIdx.x;
+    if (g < V - 1) {
+        const int d = 63 - __clzll((long long)(vc[g] ^ vc[g + 1]));
+        delta[g] = (unsigned char)d;
+        atomicAdd(&s_cnt[d], 1u);
     }
     __syncthreads();
-    const unsigned int incl = x + (wid > 0 ? s_w[wid - 1] : 0u);
-    if (i < cap) out[i] = incl - v;
-    if (threadIdx.x == kScanBlock - 1) block_sum[blockIdx.x] = incl;
+    if (threadIdx.x < kDeltaKeys) cnt[(int64_t)threadIdx.x * gridDim.x + blockIdx.x] = s_cnt[threadIdx.x];
 }
 
-__global__ void k_rh_merge(uint64_t *__restrict__ key0, uint64_t *__restrict__ key1,
-                           unsigned int *__restrict__ slot0, unsigned int *__restrict__ slot1,
-                           const RahtState *st, const unsigned long long *pairs, int n_c,
-                           const unsigned int *__restrict__ local, const unsigned int *__restrict__ block_off,
-                           float *__restrict__ x, unsigned int *__restrict__ w, float *__restrict__ ac) {
-    if (*pairs == 0) return;   // nothing to merge at this level
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t m = st->m;
-    if (i >= m) return;
-    const int sh = st->pending + 1;
-    const uint64_t *kc = st->cur ? key1 : key0;
-    if (i > 0 && pair_flag(kc, i - 1, m, sh)) return;   // the upper node of a pair: merged by its partner
-    const unsigned int pf_i = pair_flag(kc, i, m, sh);
-    const unsigned int pidx_i = local[i] + block_off[i / kScanBlock];
-    const bool c = st->cur;
-    const uint64_t *key = c ? key1 : key0;
-    const unsigned int *slot = c ? slot1 : slot0;
-    uint64_t *key2 = c ? key0 : key1;
-    unsigned int *slot2 = c ? slot0 : slot1;
-    const int64_t j = i - (int64_t)pidx_i;
-    key2[j] = key[i] >> sh;
-    const unsigned int sa = slot[i];
-    slot2[j] = sa;
-    if (!pf_i) return;
-    const unsigned int sb = slot[i + 1];
-    const unsigned int wa = w[sa], wb = w[sb];
-    // the entries of T, once per pair
-    const float sw = __fsqrt_rn((float)(wa + wb));
-    const float t1 = __fdiv_rn(__fsqrt_rn((float)wa), sw), t2 = __fdiv_rn(__fsqrt_rn((float)wb), sw);
-    const int64_t out = st->ac_base + (int64_t)pidx_i;
-    float *xa = x + (int64_t)sa * n_c;
-    const float *xbp = x + (int64_t)sb * n_c;
-    float *acp = ac + out * n_c;
-    int k = 0;
-    for (; k + 4 <= n_c; k += 4) {   // four channels at a time: independent loads in flight
-        float x1[4], x2[4];
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-            x1[u] = xa[k + u];
-            x2[u] = xbp[k + u];
+// First AC slot of every (delta, chunk): ACs are listed step by step (delta
+// ascending), in ascending code within a step.  One thread per delta value.
+__global__ void k_rh_delta_slots(unsigned int *__restrict__ cnt, int64_t nchunks) {
+    __shared__ unsigned long long s_tot[kDeltaKeys];
+    const int k = threadIdx.x;
+    unsigned int *row = cnt + (int64_t)k * nchunks;
+    unsigned long long tot = 0;
+    for (int64_t c = 0; c < nchunks; c++) tot += row[c];
+    s_tot[k] = tot;
+    __syncthreads();
+    unsigned long long run = 0;
+    for (int q = 0; q < k; q++) run += s_tot[q];
+    for (int64_t c = 0; c < nchunks; c++) {
+        const unsigned int t = row[c];
+        row[c] = (unsigned int)run;
+        run += t;
+    }
+}
+
+// The AC slot of every internal node: its (delta, chunk) slot plus its rank
+// among the chunk's nodes of equal delta, the warps in order.
+__global__ void __launch_bounds__(kDeltaChunk)
+    k_rh_delta_place(const unsigned char *__restrict__ delta, int64_t V, const unsigned int *__restrict__ slot,
+                     unsigned int *__restrict__ acpos) {
+    __shared__ unsigned int s_run[kDeltaKeys];
+    if (threadIdx.x < kDeltaKeys) s_run[threadIdx.x] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t g = (int64_t)blockIdx.x * kDeltaChunk + threadIdx.x;
+    const bool act = g < V - 1;
+    const int k = act ? (int)delta[g] : kDeltaKeys + lane;   // inactive lanes never match
+    const unsigned int peers = __match_any_sync(0xFFFFFFFFu, k);
+    const unsigned int rank = __popc(peers & ((1u << lane) - 1u));
+    for (int w = 0; w < kDeltaChunk / 32; w++) {
+        if (warp == w && act) acpos[g] = slot[(int64_t)k * gridDim.x + blockIdx.x] + s_run[k] + rank;
+        __syncthreads();
+        if (warp == w && act && rank == 0) s_run[k] += __popc(peers);
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ float ld_cg(const float *p) { return __ldcg(p); }
+
+// One thread per voxel, walking up: the first child to reach a node records
+// its extent and stops; the second merges both children by the printed T
+// (entries t1 = sqrt(w1) / sqrt(w1 + w2), t2 = sqrt(w2) / sqrt(w1 + w2), once
+// per pair: DC = t1 x1 + t2 x2 into the left child's slot, AC = t1 x2 - t2 x1
+// at the node's AC slot, weight w1 + w2) and goes on.  A node's value lives in
+// the slot of its leftmost voxel.
+__global__ void k_rh_tree(const unsigned char *__restrict__ delta, const unsigned int *__restrict__ acpos,
+                          int64_t V, int n_c, float *__restrict__ x, unsigned int *__restrict__ w,
+                          int64_t *__restrict__ ext, unsigned int *__restrict__ arrive,
+                          float *__restrict__ ac) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= V) return;
+    int64_t l = v, r = v;
+    while (!(l == 0 && r == V - 1)) {
+        // the parent: the split of smaller delta next to [l, r]
+        const bool left_child = l == 0 || (r < V - 1 && delta[r] < delta[l - 1]);
+        const int64_t g = left_child ? r : l - 1;
+        ext[2 * g + (left_child ? 0 : 1)] = left_child ? l : r;   // my extent, for my sibling
+        __threadfence();
+        if (atomicAdd(&arrive[g], 1u) == 0u) return;   // the sibling merges this node
+        __threadfence();
+        const long long *e2 = reinterpret_cast<const long long *>(ext) + 2 * g;
+        const int64_t ll = left_child ? l : (int64_t)__ldcg(e2);
+        const int64_t rr = left_child ? (int64_t)__ldcg(e2 + 1) : r;
+        const int64_t sa = ll, sb = g + 1;   // the left and right children's slots
+        const unsigned int wa = __ldcg(&w[sa]), wb = __ldcg(&w[sb]);
+        const float sw = __fsqrt_rn((float)(wa + wb));
+        const float t1 = __fdiv_rn(__fsqrt_rn((float)wa), sw), t2 = __fdiv_rn(__fsqrt_rn((float)wb), sw);
+        float *xa = x + sa * n_c;
+        const float *xb = x + sb * n_c;
+        float *acp = ac + (int64_t)acpos[g] * n_c;
+        for (int k = 0; k < n_c; k++) {
+            const float x1 = ld_cg(xa + k), x2 = ld_cg(xb + k);
+            xa[k] = __fadd_rn(__fmul_rn(t1, x1), __fmul_rn(t2, x2));
+            acp[k] = __fsub_rn(__fmul_rn(t1, x2), __fmul_rn(t2, x1));
         }
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-            xa[k + u] = __fadd_rn(__fmul_rn(t1, x1[u]), __fmul_rn(t2, x2[u]));
-            acp[k + u] = __fsub_rn(__fmul_rn(t1, x2[u]), __fmul_rn(t2, x1[u]));
-        }
-    }
-    for (; k < n_c; k++) {
-        const float x1 = xa[k], x2 = xbp[k];
-        xa[k] = __fadd_rn(__fmul_rn(t1, x1), __fmul_rn(t2, x2));
-        acp[k] = __fsub_rn(__fmul_rn(t1, x2), __fmul_rn(t2, x1));
-    }
-    w[sa] = wa + wb;
-}
-
-__global__ void k_rh_advance(RahtState *st, const unsigned long long *pairs) {
-    const long long p = (long long)*pairs;
-    if (p == 0) {
-        st->pending++;
-        return;
-    }
-    st->m -= p;
-    st->ac_base += p;
-    st->cur ^= 1;
-    st->pending = 0;
-}
-
-__global__ void k_rh_init(RahtState *st, const unsigned long long *V, unsigned int *__restrict__ slot, int64_t n) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) slot[i] = (unsigned int)i;
-    if (i == 0) {
-        st->m = (long long)*V;
-        st->ac_base = 0;
-        st->cur = 0;
-        st->pending = 0;
+        w[sa] = wa + wb;
+        l = ll;
+        r = rr;
     }
 }
 
@@ -323,10 +310,12 @@ extern "C" mgs_status mgs_raht(mgs_ctx *ctx, const mgs_scene *scene, const int32
     auto take = [&](size_t b) { const size_t o = off; off += al(b); return o; };
     const size_t o_vcode = take(8 * (size_t)n), o_head = take(4 * (size_t)n), o_idx = take(4 * (size_t)n);
     const size_t o_bsum = take(4 * (size_t)nb), o_total = take(8), o_start = take(8 * (size_t)n);
-    const size_t o_key0 = take(8 * (size_t)n), o_key1 = take(8 * (size_t)n);
-    const size_t o_slot0 = take(4 * (size_t)n), o_slot1 = take(4 * (size_t)n);
+    const int64_t nchunks = (n + kDeltaChunk - 1) / kDeltaChunk;
+    const size_t o_key0 = take(8 * (size_t)n), o_delta = take((size_t)n), o_acpos = take(4 * (size_t)n);
+    const size_t o_dcnt = take(4 * (size_t)kDeltaKeys * (size_t)nchunks), o_ext = take(16 * (size_t)n);
+    const size_t o_arrive = take(4 * (size_t)n);
     const size_t o_w = take(4 * (size_t)n), o_x = take(4 * (size_t)n * n_c);
-    const size_t o_chan = take(4 * (size_t)n_c), o_state = take(sizeof(RahtState));
+    const size_t o_chan = take(4 * (size_t)n_c);
     const size_t o_pos = take(subset ? 4 * (size_t)K : 0), o_tiles = take(subset ? 4 * (size_t)kept_tiles_for(n) : 0);
     char *ws = nullptr;
     if (cudaMallocAsync(reinterpret_cast<void **>(&ws), off, st) != cudaSuccess) {
@@ -345,13 +334,15 @@ extern "C" mgs_status mgs_raht(mgs_ctx *ctx, const mgs_scene *scene, const int32
     unsigned int *bsum = reinterpret_cast<unsigned int *>(ws + o_bsum);
     unsigned long long *total = reinterpret_cast<unsigned long long *>(ws + o_total);
     int64_t *start = reinterpret_cast<int64_t *>(ws + o_start);
-    uint64_t *key[2] = {reinterpret_cast<uint64_t *>(ws + o_key0), reinterpret_cast<uint64_t *>(ws + o_key1)};
-    unsigned int *slot[2] = {reinterpret_cast<unsigned int *>(ws + o_slot0),
-                             reinterpret_cast<unsigned int *>(ws + o_slot1)};
+    uint64_t *vc = reinterpret_cast<uint64_t *>(ws + o_key0);
+    unsigned char *delta = reinterpret_cast<unsigned char *>(ws + o_delta);
+    unsigned int *acpos = reinterpret_cast<unsigned int *>(ws + o_acpos);
+    unsigned int *dcnt = reinterpret_cast<unsigned int *>(ws + o_dcnt);
+    int64_t *ext = reinterpret_cast<int64_t *>(ws + o_ext);
+    unsigned int *arrive = reinterpret_cast<unsigned int *>(ws + o_arrive);
     unsigned int *w = reinterpret_cast<unsigned int *>(ws + o_w);
     float *x = reinterpret_cast<float *>(ws + o_x);
     int32_t *d_chan = reinterpret_cast<int32_t *>(ws + o_chan);
-    RahtState *rst = reinterpret_cast<RahtState *>(ws + o_state);
     int32_t *pos = nullptr;
     if (subset) {
         pos = reinterpret_cast<int32_t *>(ws + o_pos);
@@ -375,44 +366,24 @@ extern "C" mgs_status mgs_raht(mgs_ctx *ctx, const mgs_scene *scene, const int32
     unsigned long long V = 0;
     MGS_CUDA_TRY(cudaMemcpyAsync(&V, total, 8, cudaMemcpyDeviceToHost, st));
     MGS_CUDA_TRY(cudaStreamSynchronize(st));
-    k_rh_starts<<<blocks_of(K, 256), 256, 0, st>>>(head, idx, vcode, K, start, key[0]);
+    k_rh_starts<<<blocks_of(K, 256), 256, 0, st>>>(head, idx, vcode, K, start, vc);
     k_rh_means<<<blocks_of((int64_t)V, 256), 256, 0, st>>>(scene->d_slabs, n, pos, K, start, (int64_t)V, d_chan,
                                                            n_c, x, w);
-    k_rh_init<<<blocks_of((int64_t)V, 256), 256, 0, st>>>(rst, total, slot[0], (int64_t)V);
-    launches += 3;
-    MGS_CUDA_TRY(cudaGetLastError());
-    // merges, finest level first, on the device-resident node list; once per
-    // octree level (three steps) the host reads the node count to size the grids
-    int64_t cap = (int64_t)V;
-    for (int s = 0; s < 3 * depth && V > 1 && cap > 1; s++) {
-        const int64_t blocks = (cap + kScanBlock - 1) / kScanBlock;
-        k_rh_scan_pairs<<<(unsigned int)blocks, kScanBlock, 0, st>>>(key[0], key[1], rst, cap, idx, bsum);
-        k_scan_sums<<<1, kScanBlock, 0, st>>>(bsum, blocks, total);
-        k_rh_merge<<<blocks_of(cap, 256), 256, 0, st>>>(key[0], key[1], slot[0], slot[1], rst, total, n_c, idx,
-                                                        bsum, x, w, ac_out);
-        k_rh_advance<<<1, 1, 0, st>>>(rst, total);
+    launches += 2;
+    if (V > 1) {
+        // the merge tree: AC slots by (step, code), then every voxel walks up
+        const int64_t ch = ((int64_t)V - 1 + kDeltaChunk - 1) / kDeltaChunk;
+        MGS_CUDA_TRY(cudaMemsetAsync(arrive, 0, 4 * (size_t)V, st));
+        k_rh_delta<<<(unsigned int)ch, kDeltaChunk, 0, st>>>(vc, (int64_t)V, delta, dcnt);
+        k_rh_delta_slots<<<1, kDeltaKeys, 0, st>>>(dcnt, ch);
+        k_rh_delta_place<<<(unsigned int)ch, kDeltaChunk, 0, st>>>(delta, (int64_t)V, dcnt, acpos);
+        k_rh_tree<<<blocks_of((int64_t)V, 256), 256, 0, st>>>(delta, acpos, (int64_t)V, n_c, x, w, ext, arrive,
+                                                              ac_out);
         launches += 4;
-        if (s % 3 == 2) {
-            RahtState h{};
-            MGS_CUDA_TRY(cudaMemcpyAsync(&h, rst, sizeof(RahtState), cudaMemcpyDeviceToHost, st));
-            MGS_CUDA_TRY(cudaStreamSynchronize(st));
-            cap = h.m;
-        }
     }
     MGS_CUDA_TRY(cudaGetLastError());
     count_launches(launches);
-    RahtState h{};
-    MGS_CUDA_TRY(cudaMemcpyAsync(&h, rst, sizeof(RahtState), cudaMemcpyDeviceToHost, st));
-    MGS_CUDA_TRY(cudaStreamSynchronize(st));
-    unsigned int root = 0;
-    MGS_CUDA_TRY(cudaMemcpyAsync(&root, slot[h.cur], 4, cudaMemcpyDeviceToHost, st));
-    MGS_CUDA_TRY(cudaStreamSynchronize(st));
-    if (V > 1 && (h.m != 1 || h.ac_base != (long long)V - 1)) {
-        set_error("RAHT ended with %lld nodes and %lld ACs for %llu voxels", h.m, h.ac_base, V);
-        return MGS_ERR_CUDA;
-    }
-    MGS_CUDA_TRY(cudaMemcpyAsync(dc_out, x + (size_t)(V > 1 ? root : 0) * n_c, 4 * (size_t)n_c,
-                                 cudaMemcpyDeviceToHost, st));
+    MGS_CUDA_TRY(cudaMemcpyAsync(dc_out, x, 4 * (size_t)n_c, cudaMemcpyDeviceToHost, st));
     MGS_CUDA_TRY(cudaStreamSynchronize(st));
     *n_voxels_out = (int64_t)V;
     return MGS_OK;
