@@ -14,17 +14,20 @@
 //   internal node:
 //     k_rh_delta, k_rh_delta_slots, k_rh_delta_place  delta of every internal
 //                 node and its AC slot: ACs listed step by step, ascending
-//                 code within a step (a stable counting sort on delta)
-//     k_rh_tree   one thread per voxel walks up; a node [l, r] merges next with
-//                 the neighbour across the split of smaller delta; the first
-//                 child to arrive stops, the second merges both by the printed
-//                 T, with its entries t1 = sqrt(w1) / sqrt(w1 + w2),
+//                 code within a step (a stable counting sort on delta); the
+//                 slots of one step are contiguous
+//     k_rh_step   one launch per step that has merges: its merges join
+//                 disjoint segments (a node's children have smaller deltas,
+//                 so they were formed by earlier launches), one thread each,
+//                 by the printed T with its entries t1 = sqrt(w1) / sqrt(w1 + w2),
 //                 t2 = sqrt(w2) / sqrt(w1 + w2) formed once per pair:
-//                 DC = t1 x1 + t2 x2 (into the left child's slot), weight
-//                 w1 + w2, AC = t1 x2 - t2 x1 at the node's AC slot.
+//                 DC = t1 x1 + t2 x2 (into the left segment's first slot),
+//                 weight w1 + w2, AC = t1 x2 - t2 x1 at the node's AC slot;
+//                 each segment keeps its endpoints at its two ends.
 //   (An earlier version ran the 3d steps as 4 launches each over the whole
 //   node list; with sparse fine levels most of its ~20 heavy steps moved every
-//   node for a handful of pairs.)
+//   node for a handful of pairs.  A version that walked the tree up with one
+//   thread per voxel and arrival counters spent 1.9 ms in grid-wide fences.)
 // FP32 arithmetic with integer weights.  (An FP64 version matched the FP64
 // oracle bit for bit, but GB300's FP64 pipe ran 73-87% busy and bounded it:
 // 11.4 ms for 5.27 M voxels.)  Every merge is an orthonormal rotation, so the
@@ -159,9 +162,7 @@ __global__ void k_rh_means(const float *__restrict__ slabs, int64_t n, const int
 // ---- the merge tree ----
 // The nodes RAHT merges at step s are siblings at bit s of a binary trie over
 // the sorted voxel codes: the internal node between voxels g and g + 1 merges
-// at step delta(g), the highest bit in which their codes differ.  A node
-// covering voxels [l, r] merges next with the neighbour across the split of
-// smaller delta (l - 1 or r; the two are never equal for distinct codes).
+// at step delta(g), the highest bit in which their codes differ.
 constexpr int kDeltaKeys = 64;
 constexpr int kDeltaChunk = 1024;
 
@@ -182,32 +183,54 @@ __global__ void __launch_bounds__(kDeltaChunk)
     if (threadIdx.x < kDeltaKeys) cnt[(int64_t)threadIdx.x * gridDim.x + blockIdx.x] = s_cnt[threadIdx.x];
 }
 
-// First AC slot of every (delta, chunk): ACs are listed step by step (delta
-// ascending), in ascending code within a step.  One thread per delta value.
-__global__ void k_rh_delta_slots(unsigned int *__restrict__ cnt, int64_t nchunks) {
-    __shared__ unsigned long long s_tot[kDeltaKeys];
-    const int k = threadIdx.x;
-    unsigned int *row = cnt + (int64_t)k * nchunks;
-    unsigned long long tot = 0;
-    for (int64_t c = 0; c < nchunks; c++) tot += row[c];
-    s_tot[k] = tot;
+// Per delta value (one CTA each): the exclusive prefix over chunks of its
+// counts, in place, and its total.
+__global__ void __launch_bounds__(1024)
+    k_rh_delta_slots(unsigned int *__restrict__ cnt, int64_t nchunks, unsigned int *__restrict__ total) {
+    __shared__ unsigned int s_w[32];
+    __shared__ unsigned int s_carry;
+    unsigned int *row = cnt + (int64_t)blockIdx.x * nchunks;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_carry = 0;
     __syncthreads();
-    unsigned long long run = 0;
-    for (int q = 0; q < k; q++) run += s_tot[q];
-    for (int64_t c = 0; c < nchunks; c++) {
-        const unsigned int t = row[c];
-        row[c] = (unsigned int)run;
-        run += t;
+    for (int64_t base = 0; base < nchunks; base += 1024) {
+        const int64_t c = base + threadIdx.x;
+        const unsigned int v = c < nchunks ? row[c] : 0u;
+        unsigned int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned int t = __shfl_up_sync(0xFFFFFFFFu, x, o);
+            if (lane >= o) x += t;
+        }
+        if (lane == 31) s_w[wid] = x;
+        __syncthreads();
+        unsigned int wb = 0, all = 0;
+        for (int q = 0; q < 32; q++) {
+            if (q < wid) wb += s_w[q];
+            all += s_w[q];
+        }
+        if (c < nchunks) row[c] = s_carry + wb + x - v;
+        __syncthreads();
+        if (threadIdx.x == 0) s_carry += all;
+        __syncthreads();
     }
+    if (threadIdx.x == 0) total[blockIdx.x] = s_carry;
 }
 
-// The AC slot of every internal node: its (delta, chunk) slot plus its rank
-// among the chunk's nodes of equal delta, the warps in order.
+// The AC slot of every internal node (ACs step by step, ascending code within
+// a step): the totals of the smaller deltas, plus its (delta, chunk) prefix,
+// plus its rank among the chunk's nodes of equal delta, the warps in order.
+// node[slot] is the inverse map.
 __global__ void __launch_bounds__(kDeltaChunk)
-    k_rh_delta_place(const unsigned char *__restrict__ delta, int64_t V, const unsigned int *__restrict__ slot,
-                     unsigned int *__restrict__ acpos) {
-    __shared__ unsigned int s_run[kDeltaKeys];
-    if (threadIdx.x < kDeltaKeys) s_run[threadIdx.x] = 0;
+    k_rh_delta_place(const unsigned char *__restrict__ delta, int64_t V, const unsigned int *__restrict__ prefix,
+                     const unsigned int *__restrict__ total, unsigned int *__restrict__ node) {
+    __shared__ unsigned int s_run[kDeltaKeys], s_base[kDeltaKeys];
+    if (threadIdx.x < kDeltaKeys) {
+        s_run[threadIdx.x] = 0;
+        unsigned int b = 0;
+        for (int q = 0; q < (int)threadIdx.x; q++) b += total[q];
+        s_base[threadIdx.x] = b;
+    }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t g = (int64_t)blockIdx.x * kDeltaChunk + threadIdx.x;
@@ -216,55 +239,63 @@ __global__ void __launch_bounds__(kDeltaChunk)
     const unsigned int peers = __match_any_sync(0xFFFFFFFFu, k);
     const unsigned int rank = __popc(peers & ((1u << lane) - 1u));
     for (int w = 0; w < kDeltaChunk / 32; w++) {
-        if (warp == w && act) acpos[g] = slot[(int64_t)k * gridDim.x + blockIdx.x] + s_run[k] + rank;
+        if (warp == w && act)
+            node[s_base[k] + prefix[(int64_t)k * gridDim.x + blockIdx.x] + s_run[k] + rank] = (unsigned int)g;
         __syncthreads();
         if (warp == w && act && rank == 0) s_run[k] += __popc(peers);
         __syncthreads();
     }
 }
 
-__device__ __forceinline__ float ld_cg(const float *p) { return __ldcg(p); }
-
-// One thread per voxel, walking up: the first child to reach a node records
-// its extent and stops; the second merges both children by the printed T
-// (entries t1 = sqrt(w1) / sqrt(w1 + w2), t2 = sqrt(w2) / sqrt(w1 + w2), once
-// per pair: DC = t1 x1 + t2 x2 into the left child's slot, AC = t1 x2 - t2 x1
-// at the node's AC slot, weight w1 + w2) and goes on.  A node's value lives in
-// the slot of its leftmost voxel.
-__global__ void k_rh_tree(const unsigned char *__restrict__ delta, const unsigned int *__restrict__ acpos,
-                          int64_t V, int n_c, float *__restrict__ x, unsigned int *__restrict__ w,
-                          int64_t *__restrict__ ext, unsigned int *__restrict__ arrive,
-                          float *__restrict__ ac) {
-    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= V) return;
-    int64_t l = v, r = v;
-    while (!(l == 0 && r == V - 1)) {
-        // the parent: the split of smaller delta next to [l, r]
-        const bool left_child = l == 0 || (r < V - 1 && delta[r] < delta[l - 1]);
-        const int64_t g = left_child ? r : l - 1;
-        ext[2 * g + (left_child ? 0 : 1)] = left_child ? l : r;   // my extent, for my sibling
-        __threadfence();
-        if (atomicAdd(&arrive[g], 1u) == 0u) return;   // the sibling merges this node
-        __threadfence();
-        const long long *e2 = reinterpret_cast<const long long *>(ext) + 2 * g;
-        const int64_t ll = left_child ? l : (int64_t)__ldcg(e2);
-        const int64_t rr = left_child ? (int64_t)__ldcg(e2 + 1) : r;
-        const int64_t sa = ll, sb = g + 1;   // the left and right children's slots
-        const unsigned int wa = __ldcg(&w[sa]), wb = __ldcg(&w[sb]);
-        const float sw = __fsqrt_rn((float)(wa + wb));
-        const float t1 = __fdiv_rn(__fsqrt_rn((float)wa), sw), t2 = __fdiv_rn(__fsqrt_rn((float)wb), sw);
-        float *xa = x + sa * n_c;
-        const float *xb = x + sb * n_c;
-        float *acp = ac + (int64_t)acpos[g] * n_c;
-        for (int k = 0; k < n_c; k++) {
-            const float x1 = ld_cg(xa + k), x2 = ld_cg(xb + k);
-            xa[k] = __fadd_rn(__fmul_rn(t1, x1), __fmul_rn(t2, x2));
-            acp[k] = __fsub_rn(__fmul_rn(t1, x2), __fmul_rn(t2, x1));
+// One RAHT step: the m merges of AC slots [a0, a0 + m), all at the same bit,
+// so they touch disjoint segments.  A segment [l, r] keeps its value in slot
+// l and its endpoints at its two ends (endL[r] = l, endR[l] = r).  The node
+// between voxels g and g + 1 merges the segment ending at g with the one
+// starting at g + 1 by the printed T, with its entries t1 = sqrt(w1) /
+// sqrt(w1 + w2), t2 = sqrt(w2) / sqrt(w1 + w2) formed once per pair:
+// DC = t1 x1 + t2 x2, weight w1 + w2, AC = t1 x2 - t2 x1.
+__global__ void k_rh_step(const unsigned int *__restrict__ node, int64_t a0, int64_t m, int n_c,
+                          float *__restrict__ x, unsigned int *__restrict__ w, unsigned int *__restrict__ endL,
+                          unsigned int *__restrict__ endR, float *__restrict__ ac) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= m) return;
+    const int64_t a = a0 + t;
+    const unsigned int g = node[a];
+    const unsigned int l = endL[g], r = endR[g + 1];
+    const int64_t sa = l, sb = (int64_t)g + 1;
+    const unsigned int wa = w[sa], wb = w[sb];
+    const float sw = __fsqrt_rn((float)(wa + wb));
+    const float t1 = __fdiv_rn(__fsqrt_rn((float)wa), sw), t2 = __fdiv_rn(__fsqrt_rn((float)wb), sw);
+    float *xa = x + sa * n_c;
+    const float *xb = x + sb * n_c;
+    float *acp = ac + a * n_c;
+    int k = 0;
+    for (; k + 4 <= n_c; k += 4) {   // four channels at a time: independent loads in flight
+        float x1[4], x2[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            x1[u] = xa[k + u];
+            x2[u] = xb[k + u];
         }
-        w[sa] = wa + wb;
-        l = ll;
-        r = rr;
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            xa[k + u] = __fadd_rn(__fmul_rn(t1, x1[u]), __fmul_rn(t2, x2[u]));
+            acp[k + u] = __fsub_rn(__fmul_rn(t1, x2[u]), __fmul_rn(t2, x1[u]));
+        }
     }
+    for (; k < n_c; k++) {
+        const float x1 = xa[k], x2 = xb[k];
+        xa[k] = __fadd_rn(__fmul_rn(t1, x1), __fmul_rn(t2, x2));
+        acp[k] = __fsub_rn(__fmul_rn(t1, x2), __fmul_rn(t2, x1));
+    }
+    w[sa] = wa + wb;
+    endL[r] = l;
+    endR[l] = r;
+}
+
+__global__ void k_rh_ends(unsigned int *__restrict__ endL, unsigned int *__restrict__ endR, int64_t V) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < V) endL[i] = endR[i] = (unsigned int)i;
 }
 
 unsigned int blocks_of(int64_t n, int t) { return (unsigned int)((n + t - 1) / t); }
@@ -312,8 +343,8 @@ extern "C" mgs_status mgs_raht(mgs_ctx *ctx, const mgs_scene *scene, const int32
     const size_t o_bsum = take(4 * (size_t)nb), o_total = take(8), o_start = take(8 * (size_t)n);
     const int64_t nchunks = (n + kDeltaChunk - 1) / kDeltaChunk;
     const size_t o_key0 = take(8 * (size_t)n), o_delta = take((size_t)n), o_acpos = take(4 * (size_t)n);
-    const size_t o_dcnt = take(4 * (size_t)kDeltaKeys * (size_t)nchunks), o_ext = take(16 * (size_t)n);
-    const size_t o_arrive = take(4 * (size_t)n);
+    const size_t o_dcnt = take(4 * (size_t)kDeltaKeys * (size_t)nchunks), o_dtot = take(4 * kDeltaKeys);
+    const size_t o_endl = take(4 * (size_t)n), o_endr = take(4 * (size_t)n);
     const size_t o_w = take(4 * (size_t)n), o_x = take(4 * (size_t)n * n_c);
     const size_t o_chan = take(4 * (size_t)n_c);
     const size_t o_pos = take(subset ? 4 * (size_t)K : 0), o_tiles = take(subset ? 4 * (size_t)kept_tiles_for(n) : 0);
@@ -336,10 +367,11 @@ extern "C" mgs_status mgs_raht(mgs_ctx *ctx, const mgs_scene *scene, const int32
     int64_t *start = reinterpret_cast<int64_t *>(ws + o_start);
     uint64_t *vc = reinterpret_cast<uint64_t *>(ws + o_key0);
     unsigned char *delta = reinterpret_cast<unsigned char *>(ws + o_delta);
-    unsigned int *acpos = reinterpret_cast<unsigned int *>(ws + o_acpos);
+    unsigned int *node = reinterpret_cast<unsigned int *>(ws + o_acpos);
     unsigned int *dcnt = reinterpret_cast<unsigned int *>(ws + o_dcnt);
-    int64_t *ext = reinterpret_cast<int64_t *>(ws + o_ext);
-    unsigned int *arrive = reinterpret_cast<unsigned int *>(ws + o_arrive);
+    unsigned int *dtot = reinterpret_cast<unsigned int *>(ws + o_dtot);
+    unsigned int *endL = reinterpret_cast<unsigned int *>(ws + o_endl);
+    unsigned int *endR = reinterpret_cast<unsigned int *>(ws + o_endr);
     unsigned int *w = reinterpret_cast<unsigned int *>(ws + o_w);
     float *x = reinterpret_cast<float *>(ws + o_x);
     int32_t *d_chan = reinterpret_cast<int32_t *>(ws + o_chan);
@@ -371,15 +403,29 @@ extern "C" mgs_status mgs_raht(mgs_ctx *ctx, const mgs_scene *scene, const int32
                                                            n_c, x, w);
     launches += 2;
     if (V > 1) {
-        // the merge tree: AC slots by (step, code), then every voxel walks up
+        // the merge tree: AC slots by (step, code); then one launch per step
+        // that has merges, over that step's slots
         const int64_t ch = ((int64_t)V - 1 + kDeltaChunk - 1) / kDeltaChunk;
-        MGS_CUDA_TRY(cudaMemsetAsync(arrive, 0, 4 * (size_t)V, st));
         k_rh_delta<<<(unsigned int)ch, kDeltaChunk, 0, st>>>(vc, (int64_t)V, delta, dcnt);
-        k_rh_delta_slots<<<1, kDeltaKeys, 0, st>>>(dcnt, ch);
-        k_rh_delta_place<<<(unsigned int)ch, kDeltaChunk, 0, st>>>(delta, (int64_t)V, dcnt, acpos);
-        k_rh_tree<<<blocks_of((int64_t)V, 256), 256, 0, st>>>(delta, acpos, (int64_t)V, n_c, x, w, ext, arrive,
-                                                              ac_out);
+        k_rh_delta_slots<<<kDeltaKeys, 1024, 0, st>>>(dcnt, ch, dtot);
+        k_rh_delta_place<<<(unsigned int)ch, kDeltaChunk, 0, st>>>(delta, (int64_t)V, dcnt, dtot, node);
+        k_rh_ends<<<blocks_of((int64_t)V, 256), 256, 0, st>>>(endL, endR, (int64_t)V);
         launches += 4;
+        unsigned int h_tot[kDeltaKeys];
+        MGS_CUDA_TRY(cudaMemcpyAsync(h_tot, dtot, sizeof(h_tot), cudaMemcpyDeviceToHost, st));
+        MGS_CUDA_TRY(cudaStreamSynchronize(st));
+        int64_t a0 = 0;
+        for (int b = 0; b < kDeltaKeys; b++) {
+            if (!h_tot[b]) continue;
+            k_rh_step<<<blocks_of((int64_t)h_tot[b], 256), 256, 0, st>>>(node, a0, (int64_t)h_tot[b], n_c, x, w,
+                                                                        endL, endR, ac_out);
+            launches++;
+            a0 += h_tot[b];
+        }
+        if (a0 != (int64_t)V - 1) {
+            set_error("RAHT: %lld merges for %llu voxels", (long long)a0, V);
+            return MGS_ERR_CUDA;
+        }
     }
     MGS_CUDA_TRY(cudaGetLastError());
     count_launches(launches);
