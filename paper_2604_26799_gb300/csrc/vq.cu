@@ -129,20 +129,21 @@ __global__ void __launch_bounds__(kVqChunk)
     const int j = blockIdx.x * kVqChunk + threadIdx.x;
     if (j < b) atomicAdd(&s_cnt[a[j]], 1);
     __syncthreads();
-    for (int k = threadIdx.x; k < K; k += kVqChunk) cnt[(int64_t)k * gridDim.x + blockIdx.x] = s_cnt[k];
+    for (int k = threadIdx.x; k < K; k += kVqChunk) cnt[(int64_t)blockIdx.x * K + k] = s_cnt[k];
 }
 
 // First slot of every (chunk, centre): the centre's first slot off[k] plus
-// the counts of the earlier chunks (one thread per centre, chunks in order).
+// the counts of the earlier chunks (one thread per centre, chunks in order;
+// the counts are [chunk][centre], so a warp's loads are contiguous).
 __global__ void k_vq_slots(int32_t *__restrict__ cnt, int32_t nch, const int32_t *__restrict__ off,
                            int32_t K) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= K) return;
     int32_t run = off[k];
-    int32_t *row = cnt + (int64_t)k * nch;
     for (int c = 0; c < nch; c++) {
-        const int32_t t = row[c];
-        row[c] = run;
+        int32_t *p = cnt + (int64_t)c * K + k;
+        const int32_t t = *p;
+        *p = run;
         run += t;
     }
 }
@@ -161,7 +162,7 @@ __global__ void __launch_bounds__(kVqChunk)
     const int rank = __popc(peers & ((1u << lane) - 1u));
     for (int w = 0; w < kVqChunk / 32; w++) {
         if (warp == w && act) {
-            perm[slot[(int64_t)k * gridDim.x + blockIdx.x] + s_run[k] + rank] = j;
+            perm[slot[(int64_t)blockIdx.x * K + k] + s_run[k] + rank] = j;
         }
         __syncthreads();
         if (warp == w && act && rank == 0) s_run[k] += __popc(peers);
