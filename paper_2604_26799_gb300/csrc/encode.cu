@@ -10,7 +10,8 @@
 //     codes in ascending order, normalise the counts to M = 2^ceil(log2 n), lay
 //     out the gamma-coded table by a block-wide scan of its bit lengths and
 //     write it into the block's slot, and store (f << 16 | cum) for every code;
-//   k_enc_rans, one warp per block: the interleaved rANS encoder (lane j owns
+//   k_enc_rans, one sub-group of lanes per block (four 4096-code blocks per
+//     warp): the interleaved rANS encoder (lane j owns
 //     symbols i = j mod lanes; the bytes a step emits are ordered by two
 //     ballots), which needs no shared memory, so many blocks are in flight;
 //   block sizes -> exclusive scan -> k_enc_gather, which writes each block at
@@ -18,6 +19,7 @@
 //     into decoding order); skipped when only the size is wanted.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "internal.h"
@@ -285,37 +287,54 @@ __global__ void __launch_bounds__(kEncThreads)
     if (t == 0) info[blk] = EncInfo{lanes, k, (int32_t)tab_bytes, (int32_t)e_cap, 0, 0};
 }
 
-// One warp per block: the interleaved rANS encoder, last symbol first.  Lane
-// j owns the symbols i = j (mod lanes); each step emits 0-2 bytes per lane,
-// placed by two ballots in emission order (higher lanes first within a
-// step); the bytes go into the slot after the table and the states, and the
-// gather kernel writes them out in reverse, which is decoding order.
+// The interleaved rANS encoder, last symbol first, one sub-group of GW lanes
+// per block (GW = 32 / blocks per warp, at least the block's lane count; a
+// 4096-code block has 8 lanes, so four blocks share a warp).  Lane j of a
+// block owns its symbols i = j (mod lanes); each step emits 0-2 bytes per
+// lane, placed by the sub-group's slices of two warp ballots in emission order
+// (higher lanes first within a step); the bytes go into the slot after the
+// table and the states, and the gather kernel writes them out in reverse,
+// which is decoding order.
+template <int GW>
 __global__ void __launch_bounds__(kEncThreads)
     k_enc_rans(const uint32_t *__restrict__ fcpos, int64_t K, int32_t G, int32_t ng, int64_t m,
                const uint8_t *__restrict__ bits, uint8_t *__restrict__ slots, int64_t slot_bytes,
                EncInfo *__restrict__ info, int32_t *__restrict__ sizes) {
-    const int64_t blk = (int64_t)blockIdx.x * kEncWarps + (threadIdx.x >> 5);
-    if (blk >= m) return;
-    const EncInfo I = info[blk];
-    if (I.lanes == 0) return;
-    const EncBlock B = enc_block(blk, K, G, ng);
-    const int n = B.n, lanes = I.lanes, k = I.k;
+    constexpr int PER_WARP = 32 / GW;
+    const int lane = threadIdx.x & 31;
+    const int sub = lane / GW, j = lane % GW;
+    const int64_t blk = ((int64_t)blockIdx.x * kEncWarps + (threadIdx.x >> 5)) * PER_WARP + sub;
+    const bool have = blk < m;
+    EncInfo I = {0, 0, 0, 0, 0, 0};
+    if (have) I = info[blk];
+    const bool live = have && I.lanes > 0;
+    int n = 0;
+    int64_t cstart = 0;
+    if (live) {
+        const EncBlock B = enc_block(blk, K, G, ng);
+        n = B.n;
+        cstart = (int64_t)B.c * K + B.start;
+    }
+    const int lanes = live ? I.lanes : 1, k = I.k;
     const uint32_t M = 1u << k;
-    const uint32_t *fc = fcpos + (int64_t)B.c * K + B.start;
-    uint8_t *out = slots + blk * slot_bytes + 10 + I.tab_bytes;
-    uint8_t *em = out + 4 * lanes;
+    const uint32_t *fc = fcpos + cstart;
+    uint8_t *out = live ? slots + blk * slot_bytes + 10 + I.tab_bytes : nullptr;
+    uint8_t *em = live ? out + 4 * lanes : nullptr;
     const int64_t e_cap = I.e_cap;
-    const int j = threadIdx.x & 31;
     uint32_t x = kRansL;
     int64_t base = 0;
-    const uint32_t above = ~((2u << j) - 1u);   // lanes > j (0 for j = 31)
-    const uint32_t xunit = 1u << (31 - k);      // (L >> k) << 8
-    const int steps = (n + lanes - 1) / lanes;
-    for (int st = steps - 1; st >= 0; st--) {
+    const uint32_t gmask = GW == 32 ? 0xFFFFFFFFu : ((1u << GW) - 1u);
+    const uint32_t above = ~((2u << j) - 1u) & gmask;   // lanes of this sub-group above j
+    const uint32_t xunit = live ? 1u << (31 - k) : 0u;   // (L >> k) << 8
+    const int steps = live ? (n + lanes - 1) / lanes : 0;
+    int max_steps = steps;   // the warp runs as long as its longest block
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) max_steps = max(max_steps, __shfl_xor_sync(0xFFFFFFFFu, max_steps, o));
+    for (int st = max_steps - 1; st >= 0; st--) {
         const int i = st * lanes + j;
         int cnt = 0;
         uint32_t b1 = 0, b2 = 0;
-        if (j < lanes && i < n) {
+        if (live && st < steps && j < lanes && i < n) {
             const uint32_t w = fc[i];
             const uint32_t fs = w >> 16, cs = w & 0xFFFFu;
             const uint64_t xmax = (uint64_t)xunit * fs;
@@ -331,16 +350,16 @@ __global__ void __launch_bounds__(kEncThreads)
             }
             x = (x / fs) * M + x % fs + cs;
         }
-        const uint32_t m1 = __ballot_sync(0xFFFFFFFFu, cnt >= 1);
-        const uint32_t m2 = __ballot_sync(0xFFFFFFFFu, cnt == 2);
+        const uint32_t m1 = (__ballot_sync(0xFFFFFFFFu, cnt >= 1) >> (sub * GW)) & gmask;
+        const uint32_t m2 = (__ballot_sync(0xFFFFFFFFu, cnt == 2) >> (sub * GW)) & gmask;
         const int64_t idx = base + __popc(m1 & above) + __popc(m2 & above);
         if (cnt >= 1 && idx < e_cap) em[idx] = (uint8_t)b1;
         if (cnt == 2 && idx + 1 < e_cap) em[idx + 1] = (uint8_t)b2;
         base += __popc(m1) + __popc(m2);
     }
-    if (j < lanes)
+    if (live && j < lanes)
         for (int q = 0; q < 4; q++) out[4 * j + q] = (uint8_t)(x >> (8 * q));
-    if (j == 0) {
+    if (live && j == 0) {
         const int64_t E = base < e_cap ? base : e_cap;
         info[blk].E = (int32_t)E;
         sizes[blk] = E < e_cap ? (int32_t)(10 + I.tab_bytes + 4 * lanes + E)
@@ -517,8 +536,20 @@ mgs_status encode_launch(mgs_ctx *ctx, const mgs_scene *sc, const int32_t *kept,
             k_enc_model<<<(unsigned)m, kEncThreads, smem, st>>>(d_codes, keep, G, (int32_t)ng, d_bits,
                                                                 d_mm, d_slots, slot_bytes, d_info,
                                                                 d_fc, d_sizes);
-            k_enc_rans<<<(unsigned)((m + kEncWarps - 1) / kEncWarps), kEncThreads, 0, st>>>(
-                d_fc, keep, G, (int32_t)ng, m, d_bits, d_slots, slot_bytes, d_info, d_sizes);
+            // sub-group width: the lanes of a full group, rounded up to a power of two
+            const int full_lanes = std::min(32, std::max(1, G >> 9));
+            const int gw = full_lanes <= 1 ? 1 : full_lanes <= 2 ? 2 : full_lanes <= 4 ? 4
+                         : full_lanes <= 8 ? 8 : full_lanes <= 16 ? 16 : 32;
+            const int64_t per_cta = (int64_t)kEncWarps * (32 / gw);
+            const unsigned grid = (unsigned)((m + per_cta - 1) / per_cta);
+            switch (gw) {
+                case 1: k_enc_rans<1><<<grid, kEncThreads, 0, st>>>(d_fc, keep, G, (int32_t)ng, m, d_bits, d_slots, slot_bytes, d_info, d_sizes); break;
+                case 2: k_enc_rans<2><<<grid, kEncThreads, 0, st>>>(d_fc, keep, G, (int32_t)ng, m, d_bits, d_slots, slot_bytes, d_info, d_sizes); break;
+                case 4: k_enc_rans<4><<<grid, kEncThreads, 0, st>>>(d_fc, keep, G, (int32_t)ng, m, d_bits, d_slots, slot_bytes, d_info, d_sizes); break;
+                case 8: k_enc_rans<8><<<grid, kEncThreads, 0, st>>>(d_fc, keep, G, (int32_t)ng, m, d_bits, d_slots, slot_bytes, d_info, d_sizes); break;
+                case 16: k_enc_rans<16><<<grid, kEncThreads, 0, st>>>(d_fc, keep, G, (int32_t)ng, m, d_bits, d_slots, slot_bytes, d_info, d_sizes); break;
+                default: k_enc_rans<32><<<grid, kEncThreads, 0, st>>>(d_fc, keep, G, (int32_t)ng, m, d_bits, d_slots, slot_bytes, d_info, d_sizes); break;
+            }
             k_enc_chunk_sums<<<(unsigned)nchunks, 1024, 0, st>>>(d_sizes, m, d_sums);
             k_enc_scan_sums<<<1, 1024, 0, st>>>(d_sums, nchunks, d_sums + nchunks);
             k_enc_offsets<<<(unsigned)nchunks, 1024, 0, st>>>(d_sizes, m, d_sums, d_off);
