@@ -242,8 +242,9 @@ mgs_status mgs_scene_morton(const mgs_scene *scene, uint64_t *codes, int32_t *or
  *   n_voxels_out               host: V
  * FP32 arithmetic (each merge is an orthonormal rotation: a coefficient's
  * error stays within a few ulp per level of sqrt(w) |x| of its node).
- * Synchronous on `stream` (one host round trip per octree level); allocates
- * a device workspace of about (56 + 4 n_channels) n bytes on `stream`.
+ * Synchronous on `stream` (three host round trips: the voxel count, the
+ * merges per step, the DC); allocates a device workspace of about
+ * (54 + 4 n_channels) n bytes on `stream`.
  */
 mgs_status mgs_raht(mgs_ctx *ctx, const mgs_scene *scene, const int32_t *channels, int32_t n_channels,
                     int32_t depth, int64_t keep, float *dc_out, float *ac_out, int64_t *n_voxels_out,
