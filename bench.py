@@ -549,6 +549,17 @@ def run_serve(args):
     mgs.mgs_server_destroy(srv)
     mgs.mgs_destroy(ctx)
     lat = np.array([r["t_done"] - r["t_submit"] for r in res])
+    # where the latency goes: waiting for admission, ingest, compute, solve
+    stages = {}
+    for name, a_, b_ in (("admit_wait", "t_submit", "t_admit"), ("ingest", "t_admit", "t_ready"),
+                         ("compute", "t_ready", "t_table"), ("solve", "t_table", "t_done")):
+        d_ = np.array([r[b_] - r[a_] for r in res])
+        stages[name] = {"p50_s": float(np.percentile(d_, 50)), "p99_s": float(np.percentile(d_, 99))}
+    slow = int(np.argmax(lat))
+    stages["slowest_job"] = {"n": int(pool[pick[slow]][2]),
+                             **{k: float(res[slow][v] - res[slow]["t_submit"])
+                                for k, v in (("admit", "t_admit"), ("ready", "t_ready"), ("table", "t_table"),
+                                             ("done", "t_done"))}}
     ok = sum(1 for r in res if r["status"] == 0)
     span = max(r["t_done"] for r in res) - min(r["t_submit"] for r in res)
     # the plain loop, one job at a time, same arrivals
@@ -567,7 +578,7 @@ def run_serve(args):
         "jobs": n_jobs, "evals_per_s": evals / span, "higher_is_better": False,
         "plain_loop_p50_s": float(np.percentile(plain_lat, 50)),
         "plain_loop_p99_s": float(np.percentile(plain_lat, 99)),
-        "server": stats, "data": "synthetic",
+        "server": stats, "stages": stages, "data": "synthetic",
         "config": {"workload": "serving: Poisson 20 jobs/s, N log-uniform 1e5..6e6 (12-scene pool), "
                                "budget U[5,60] MB, 10 ratios x 10 bit-widths, G 4096",
                    "pool_sizes": pool_n}}))
@@ -992,6 +1003,52 @@ def run_vq(args):
                       "cpu_baseline": cpu}))
 
 
+def run_solvers(args):
+    """The 0-1 ILP of the scene-scale cost table at 40 MB three ways: the flat
+    multiple-choice knapsack on the device and on the host (the same answer),
+    and the paper's hierarchical solve (channel widths, then each channel's
+    groups within its share of the budget).  Time, Omega and estimated size."""
+    import torch
+    from paper_2604_26799_gb300 import mgs
+    dev = torch.device("cuda", 0)
+    w = WORKLOAD
+    a, imp = synth.make_scene(w.n, seed=w.seed)
+    ctx = mgs.mgs_create(0)
+    st = torch.cuda.Stream(device=dev)
+    scene = mgs.mgs_scene_create(ctx, torch.from_numpy(a).to(dev), torch.from_numpy(imp).to(dev), stream=st)
+    grid = mgs.Grid(w.keep(), list(w.bits), w.group_size)
+    L = mgs.mgs_table_layout_for(w.n, a.shape[1], grid)
+    tab = torch.empty(L.total_bytes, dtype=torch.uint8, device=dev)
+    mgs.mgs_build_cost_table(ctx, scene, grid, tab, stream=st)
+    st.synchronize()
+    host = tab.cpu().numpy()
+    opts = mgs.solve_opts()
+    res = {}
+    for name, fn in (("flat_device", lambda: mgs.mgs_solve_budgets_device(ctx, tab, L, grid, [w.budget_bytes], opts,
+                                                                         stream=st)[0]),
+                     ("flat_host", lambda: mgs.mgs_solve_budget(host, L, grid, w.budget_bytes, opts)),
+                     ("hierarchical_host", lambda: mgs.mgs_solve_hierarchical(host, L, grid, w.budget_bytes, opts))):
+        times, sol = [], None
+        for step in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            sol = fn()
+            if step >= args.warmup:
+                times.append((time.perf_counter() - t0) * 1e3)
+        res[name] = {"ms": statistics.median(times), "r_index": int(sol["r_index"]),
+                     "objective": float(sol["objective"]), "est_bytes": float(sol["est_bytes"]),
+                     "lp_bound": float(sol["lp_bound"])}
+    mgs.mgs_scene_destroy(scene)
+    mgs.mgs_destroy(ctx)
+    f = res["flat_device"]
+    print(json.dumps({"metric": "0-1 ILP at the budget: time to a configuration", "value": f["ms"], "unit": "ms",
+                      "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": f["ms"],
+                      "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": f"solvers on the scene-scale table (N={w.n}, 10 ratios x "
+                                             f"{len(w.bits)} widths, G={w.group_size}), budget {w.budget_bytes:.0f} B"},
+                      "solvers": res,
+                      "hierarchical_objective_over_flat": res["hierarchical_host"]["objective"] / f["objective"]}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -999,7 +1056,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mgs", choices=["mgs", "reference"])
     ap.add_argument("--workload", default="scene", choices=["scene", "batch", "serve", "large", "preprocess", "raht", "raht_search",
-                             "encode", "calibrated", "vq"],
+                             "encode", "calibrated", "vq", "solvers"],
                     help="scene: the scene-scale search (default); batch: 16 uneven scenes in one "
                          "graph-replayed launch; serve: Poisson job stream through the server; "
                          "large: 6 M Gaussians x 20 ratios x 16 bit-widths; preprocess: Euler "
@@ -1008,7 +1065,8 @@ def main():
                          "raht_search: the search over RAHT AC tables for every ratio; "
                          "encode: the block coder on half the scene; calibrated: Alg. 1 with "
                          "real compression (the S_Delta loop) at 40 MB; vq: mini-batch k-means "
-                         "of the SH coefficients and the assignment of every vector")
+                         "of the SH coefficients and the assignment of every vector; solvers: the flat "
+                         "0-1 ILP (device, host) against the hierarchical solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-loop comparator")
     ap.add_argument("--no-autotune", action="store_true", help="use the default tile shape")
@@ -1040,6 +1098,8 @@ def main():
         return run_calibrated(args)
     if args.workload == "vq":
         return run_vq(args)
+    if args.workload == "solvers":
+        return run_solvers(args)
     return run_gpu(args)
 
 
