@@ -352,7 +352,9 @@ void compute_loop(mgs_server *S) {
 void solve_loop(mgs_server *S) {
     cudaSetDevice(S->ctx->device);
     cudaStream_t st = nullptr;
-    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) st = nullptr;
+    int prio_low = 0, prio_high = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
+    if (cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, prio_high) != cudaSuccess) st = nullptr;
     struct StreamGuard {
         cudaStream_t s;
         ~StreamGuard() {
@@ -428,8 +430,13 @@ mgs_status mgs_server_create(mgs_ctx *ctx, const mgs_server_opts *opts, mgs_serv
     int prev = -1;
     cudaGetDevice(&prev);
     cudaSetDevice(ctx->device);
-    cudaError_t e = cudaStreamCreateWithFlags(&S->ingest_stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->compute_stream, cudaStreamNonBlocking);
+    // ingest and solves ahead of the batched cost launches: a new job's scene
+    // build and a finished job's solve are short and on every job's critical
+    // path, while the persistent cost kernel would otherwise hold every SM
+    int prio_low = 0, prio_high = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
+    cudaError_t e = cudaStreamCreateWithPriority(&S->ingest_stream, cudaStreamNonBlocking, prio_high);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&S->compute_stream, cudaStreamNonBlocking, prio_low);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->copy_stream, cudaStreamNonBlocking);
     if (prev >= 0) cudaSetDevice(prev);
     if (e != cudaSuccess) {
