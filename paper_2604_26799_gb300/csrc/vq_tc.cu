@@ -19,7 +19,9 @@
 // (8 rows x 16 bytes per core matrix, LBO = 128 B between core matrices
 // along K, SBO = 32 DP bytes between 8-row groups), each tile followed by its
 // 128 exact norms, so a tile is one bulk copy (cp.async.bulk, completion on
-// an mbarrier); two tile buffers alternate.  One thread issues DP / 8 MMAs per
+// an mbarrier) into the CTA's one tile buffer, refilled as soon as the four
+// warps have read it; four CTAs per SM overlap one another's copies, MMAs and
+// candidate tests.  One thread issues DP / 8 MMAs per
 // tile and commits them to an mbarrier; the four warps read their 32 TMEM
 // lanes with tcgen05.ld and run the candidate test.  Every wait is bounded:
 // on expiry the CTA records an error flag, drains what it issued, frees its
@@ -36,6 +38,8 @@ namespace {
 constexpr int kTcM = 128;            // vectors per CTA (MMA M, TMEM lanes)
 constexpr int kTcN = 128;            // codebook entries per tile (MMA N, TMEM columns)
 constexpr int kTcThreads = 128;
+constexpr int kTcBufs = 1;           // codebook tile buffers per CTA
+constexpr int kTcCtasPerSm = 4;      // resident CTAs: 4 x 128 TMEM columns = all 512
 constexpr long long kWaitCycles = 1ll << 31;    // ~1 s at 2 GHz: a wait that long is a failure
 constexpr long long kDrainCycles = 1ll << 28;   // draining one's own copies and MMAs
 
@@ -152,6 +156,27 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int j = 0; j < 32; j++) v[j] = __uint_as_float(r[j]);
 }
 
+// Exact score of vector row v of the A tile against entry kk of a codebook
+// tile: the FP32 fmaf chain of the plain search (dimensions ascending), then
+// |c|^2 - 2 x.c in one fmaf.
+template <int DP>
+__device__ __forceinline__ float exact_score(const unsigned char *sA, int v, const unsigned char *tileB,
+                                             int kk, int D, const float *ccs) {
+    float dot = 0.0f;
+#pragma unroll
+    for (int k4 = 0; k4 < DP / 4; k4++) {
+        if (4 * k4 < D) {
+            const float4 a = *reinterpret_cast<const float4 *>(sA + cm_offset(v, 4 * k4, DP));
+            const float4 b = *reinterpret_cast<const float4 *>(tileB + cm_offset(kk, 4 * k4, DP));
+            dot = __fmaf_rn(a.x, b.x, dot);
+            if (4 * k4 + 1 < D) dot = __fmaf_rn(a.y, b.y, dot);
+            if (4 * k4 + 2 < D) dot = __fmaf_rn(a.z, b.z, dot);
+            if (4 * k4 + 3 < D) dot = __fmaf_rn(a.w, b.w, dot);
+        }
+    }
+    return __fmaf_rn(-2.0f, dot, ccs[kk]);
+}
+
 // The codebook in MMA tiles: tile t holds entries 128 t .. 128 t + 127 in the
 // core-matrix layout (zeros beyond K and beyond D), then their exact squared
 // norms |c|^2 (the fmaf chain of the exact path), then upper bounds of their
@@ -182,7 +207,7 @@ __global__ void k_vq_tc_prep(const float *__restrict__ cb, int32_t K, int32_t D,
 }
 
 template <int DP>
-__global__ void __launch_bounds__(kTcThreads)
+__global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm)
     k_vq_assign_tc(const float *__restrict__ x, int64_t n, int32_t D, const int32_t *__restrict__ rows,
                    const unsigned char *__restrict__ tiles, int32_t K, const float *__restrict__ cb,
                    const unsigned int *__restrict__ cmax2, int32_t *__restrict__ idx_out,
@@ -193,8 +218,8 @@ __global__ void __launch_bounds__(kTcThreads)
     constexpr uint32_t IDESC = idesc_tf32(kTcM, kTcN);
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char *sA = smem;                 // TB bytes (the same layout, 128 vectors)
-    unsigned char *sB = smem + TB;            // two tile buffers of TS bytes
-    __shared__ __align__(8) uint64_t bar_full[2];
+    unsigned char *sB = smem + TB;            // kTcBufs tile buffers of TS bytes
+    __shared__ __align__(8) uint64_t bar_full[kTcBufs];
     __shared__ __align__(8) uint64_t bar_mma;
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
@@ -229,8 +254,7 @@ __global__ void __launch_bounds__(kTcThreads)
 
     if (warp == 0) tmem_alloc(&s_tmem, kTcN);
     if (t == 0) {
-        mbar_init(&bar_full[0], 1);
-        mbar_init(&bar_full[1], 1);
+        for (int b = 0; b < kTcBufs; b++) mbar_init(&bar_full[b], 1);
         mbar_init(&bar_mma, 1);
         s_abort = 0;
     }
@@ -240,9 +264,9 @@ __global__ void __launch_bounds__(kTcThreads)
     tc_fence_after();
     const uint32_t tmem = s_tmem;
 
-    int issued[2] = {0, 0};   // bulk copies issued into each buffer (thread 0)
+    int issued[kTcBufs] = {};   // bulk copies issued into each buffer (thread 0)
     if (t == 0) {
-        for (int b = 0; b < 2 && b < ntiles; b++) {
+        for (int b = 0; b < kTcBufs && b < ntiles; b++) {
             mbar_expect_tx(&bar_full[b], TS);
             bulk_load(sB + b * TS, tiles + (int64_t)b * TS, TS, &bar_full[b]);
             issued[b]++;
@@ -257,9 +281,9 @@ __global__ void __launch_bounds__(kTcThreads)
     const uint32_t a_base = smem_u32(sA);
 
     for (int tt = 0; tt < ntiles; tt++) {
-        const int buf = tt & 1;
+        const int buf = tt % kTcBufs;
         unsigned char *tileB = sB + buf * TS;
-        if (!mbar_wait(&bar_full[buf], (uint32_t)((tt >> 1) & 1), err, kWaitCycles)) s_abort = 1;
+        if (!mbar_wait(&bar_full[buf], (uint32_t)((tt / kTcBufs) & 1), err, kWaitCycles)) s_abort = 1;
         if (t == 0 && !s_abort) {
             tc_fence_after();
             const uint32_t b_base = smem_u32(tileB);
@@ -330,12 +354,7 @@ __global__ void __launch_bounds__(kTcThreads)
             while (cand) {
                 const int j = __ffs(cand) - 1;
                 cand &= cand - 1u;
-                const int kk = q * 32 + j;
-                float dot = 0.0f;
-#pragma unroll
-                for (int d = 0; d < DP; d++)
-                    if (d < D) dot = __fmaf_rn(xr[d], *reinterpret_cast<const float *>(tileB + cm_offset(kk, d, DP)), dot);
-                const float sc = __fmaf_rn(-2.0f, dot, ccs[kk]);
+                const float sc = exact_score<DP>(sA, t, tileB, q * 32 + j, D, ccs);
                 if (best_k < 0 || sc < best_s) {
                     best_s = sc;
                     best_k = k0 + j;
@@ -345,9 +364,9 @@ __global__ void __launch_bounds__(kTcThreads)
         }
         tc_fence_before();
         __syncthreads();   // every lane read the accumulators and the norms of this buffer
-        if (t == 0 && tt + 2 < ntiles) {
+        if (t == 0 && tt + kTcBufs < ntiles) {
             mbar_expect_tx(&bar_full[buf], TS);
-            bulk_load(tileB, tiles + (int64_t)(tt + 2) * TS, TS, &bar_full[buf]);
+            bulk_load(tileB, tiles + (int64_t)(tt + kTcBufs) * TS, TS, &bar_full[buf]);
             issued[buf]++;
         }
     }
@@ -357,7 +376,7 @@ __global__ void __launch_bounds__(kTcThreads)
             atomicOr(err, 1u);
             // drain: the last MMA and every bulk copy issued but not consumed
             if (mma_pending >= 0) mbar_wait(&bar_mma, (uint32_t)(mma_pending & 1), nullptr, kDrainCycles);
-            for (int b = 0; b < 2; b++)
+            for (int b = 0; b < kTcBufs; b++)
                 if (issued[b] > 0) mbar_wait(&bar_full[b], (uint32_t)((issued[b] - 1) & 1), nullptr, kDrainCycles);
         }
     } else if (row >= 0) {
@@ -382,12 +401,30 @@ mgs_status launch_tc(const float *x, int64_t n, int32_t D, const int32_t *rows, 
     const int64_t ntiles = ((int64_t)K + kTcN - 1) / kTcN;
     MGS_CUDA_TRY(cudaMemsetAsync(cmax2, 0, sizeof(unsigned int), st));
     k_vq_tc_prep<DP><<<(unsigned)((ntiles * kTcN + 255) / 256), 256, 0, st>>>(cb, K, D, tiles, cmax2);
-    // at least a quarter of the SM's shared memory, so at most four CTAs (4 x 128
-    // TMEM columns = all 512) are resident and tcgen05.alloc never has to wait
-    const size_t need = (size_t)tile_bytes(DP) + 2 * (size_t)tile_stride(DP);
-    const size_t smem = need > 58 * 1024 ? need : 58 * 1024;
+    // the A tile and the codebook buffers, padded with unused shared memory
+    // until at most kTcCtasPerSm CTAs are resident, so that tcgen05.alloc
+    // never has to wait for tensor-memory columns
+    int dev = 0, optin = 0;
+    MGS_CUDA_TRY(cudaGetDevice(&dev));
+    MGS_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cudaFuncAttributes fa{};
+    MGS_CUDA_TRY(cudaFuncGetAttributes(&fa, k_vq_assign_tc<DP>));
+    const size_t limit = (size_t)optin - fa.sharedSizeBytes;   // dynamic bytes a CTA may have
+    const size_t need = (size_t)tile_bytes(DP) + (size_t)kTcBufs * tile_stride(DP);
+    if (need > limit) {
+        set_error("vq tensor path: %zu bytes of shared memory needed, %zu available", need, limit);
+        return MGS_ERR_CUDA;
+    }
     MGS_CUDA_TRY(cudaFuncSetAttribute(k_vq_assign_tc<DP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
+                                      (int)limit));
+    size_t smem = need;
+    for (;;) {
+        int resident = 0;
+        MGS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_vq_assign_tc<DP>, kTcThreads,
+                                                                   smem));
+        if (resident <= kTcCtasPerSm || smem + 1024 > limit) break;
+        smem += 1024;
+    }
     const int64_t grid = (n + kTcM - 1) / kTcM;
     if (grid > 0)
         k_vq_assign_tc<DP><<<(unsigned)grid, kTcThreads, smem, st>>>(x, n, D, rows, tiles, K, cb, cmax2, idx,
