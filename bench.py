@@ -7,11 +7,13 @@ bit-widths {2,3,4,5,6,8,10,12,14,16}, groups of 4,096, 0-1 ILP at 40 MB.
 One step = the whole hot path over one scene whose attributes are resident in
 HBM: validation, importance rank, Morton order, slab relayout
 (mgs_scene_create), kept lists and the fused cost kernel (mgs_plan_create +
-mgs_plan_launch), the table's copy to pinned host memory, and the budget solve
-(mgs_solve_budget).  `value` = cost-table evaluations (element x ratio x
-bit-width) per second over the timed steps; `e2e` = the same metric through
-the one-call API from pinned host buffers (attribute upload and table
-download inside the timed region).
+mgs_plan_launch), and the budget solve on the device
+(mgs_solve_budgets_device, whose chosen options come back to the host).
+`value` = cost-table evaluations (element x ratio x bit-width) per second over
+the timed steps; `e2e` = the same metric through the same calls from pinned
+host buffers (each step uploads its attributes and importance and reads its
+solution back), with step i+1's scene created on a second stream while step i
+runs; the serial figure is reported beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -301,23 +303,54 @@ def run_gpu(args):
     ms_max = reduce_max(ms, ws)
     clocks = clk.summary()
 
-    # e2e: the one-call public API from pinned host buffers
-    e2e_ms = None
-    if rank == 0 or True:
-        def e2e_step():
-            scene = mgs.mgs_scene_create(ctx, attrs_h, imp_h, stream=st)
+    # e2e: the public API from pinned host buffers.  Serial: one step after the
+    # other.  Pipelined (the figure reported): step i+1's scene is created (its
+    # upload, validation, Morton sort and relayout) on a second stream while
+    # step i's cost table and solve run; every step still uploads its own
+    # inputs and reads its own solution back to the host.
+    st2 = torch.cuda.Stream(device=dev)
+
+    def e2e_step():
+        scene = mgs.mgs_scene_create(ctx, attrs_h, imp_h, stream=st)
+        mgs.mgs_build_cost_table(ctx, scene, grid, table_d, stream=st)
+        s = mgs.mgs_solve_budgets_device(ctx, table_d, L, grid, [w.budget_bytes], opts, stream=st)[0]
+        mgs.mgs_scene_destroy(scene)
+        return s
+
+    def e2e_pipelined(k):
+        nxt = mgs.mgs_scene_create(ctx, attrs_h, imp_h, stream=st2)
+        ready = torch.cuda.Event()
+        ready.record(st2)
+        sols = []
+        for i in range(k):
+            scene = nxt
+            st.wait_event(ready)
             mgs.mgs_build_cost_table(ctx, scene, grid, table_d, stream=st)
-            s = mgs.mgs_solve_budgets_device(ctx, table_d, L, grid, [w.budget_bytes], opts, stream=st)[0]
+            if i + 1 < k:
+                nxt = mgs.mgs_scene_create(ctx, attrs_h, imp_h, stream=st2)
+                ready = torch.cuda.Event()
+                ready.record(st2)
+            sols.append(mgs.mgs_solve_budgets_device(ctx, table_d, L, grid, [w.budget_bytes], opts,
+                                                     stream=st)[0])
             mgs.mgs_scene_destroy(scene)
-            return s
+        return sols
+
+    e2e_step()
+    torch.cuda.synchronize()
+    barrier(ws)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
         e2e_step()
-        torch.cuda.synchronize()
-        barrier(ws)
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            e2e_step()
-        torch.cuda.synchronize()
-        e2e_ms = reduce_max(1000 * (time.perf_counter() - t0) / args.steps, ws)
+    torch.cuda.synchronize()
+    e2e_serial_ms = reduce_max(1000 * (time.perf_counter() - t0) / args.steps, ws)
+    e2e_pipelined(2)
+    torch.cuda.synchronize()
+    barrier(ws)
+    t0 = time.perf_counter()
+    e2e_sols = e2e_pipelined(args.steps)
+    torch.cuda.synchronize()
+    e2e_ms = reduce_max(1000 * (time.perf_counter() - t0) / args.steps, ws)
+    e2e_same = all(x["r_index"] == sol["r_index"] and x["objective"] == sol["objective"] for x in e2e_sols)
 
     # the host-to-device copy alone (pinned attributes and importance), for the e2e budget
     h2d_ms = []
@@ -410,7 +443,9 @@ def run_gpu(args):
                     "h2d_bytes_per_step": int(attrs_h.numel() * 4 + imp_h.numel() * 4),
                     "h2d_copy_ms": h2d_ms,
                     "h2d_gbs": (attrs_h.numel() * 4 + imp_h.numel() * 4) / (h2d_ms * 1e-3) / 1e9,
-                    "d2h_bytes_per_step": int(sol["choice"].nbytes) + 48 * len(w.ratios), "ms_per_step": e2e_ms},
+                    "d2h_bytes_per_step": int(sol["choice"].nbytes) + 48 * len(w.ratios), "ms_per_step": e2e_ms,
+                    "pipelined": "step i+1's scene creation (upload included) on a second stream during step i",
+                    "serial_ms_per_step": e2e_serial_ms, "solutions_equal_device_step": e2e_same},
             "gpu_launches": int(launches),
             "autotune": tune,
             "clocks": clocks,
