@@ -41,8 +41,23 @@ __global__ void k_validate(const float *__restrict__ attrs, int64_t total, int32
     int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t stride = (int64_t)gridDim.x * blockDim.x;   // multiple of C
     uint32_t mn = 0xFFFFFFFFu, mx = 0u, bad = 0u;
-    for (int64_t e = gtid; e < total; e += stride) {
-        float v = attrs[e];
+    // eight independent loads in flight per thread (the same channel: the
+    // stride is a multiple of C); min, max and the flag do not depend on order
+    int64_t e = gtid;
+    for (; e + 7 * stride < total; e += 8 * stride) {
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) v[u] = __ldg(attrs + e + u * stride);
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            if (!isfinite(v[u])) bad = 1u;
+            const uint32_t o = ordered_u32(v[u]);
+            mn = min(mn, o);
+            mx = max(mx, o);
+        }
+    }
+    for (; e < total; e += stride) {
+        float v = __ldg(attrs + e);
         if (!isfinite(v)) bad = 1u;
         uint32_t o = ordered_u32(v);
         mn = min(mn, o);
@@ -305,28 +320,33 @@ __global__ void k_morton(const float *__restrict__ attrs, int64_t n, int32_t C, 
 
 // ---------------------------------------------------------------------------
 // Relayout: slabs[s][p][j] = attrs[order[p]][8 s + j] (0 past the last channel),
-// rank_m[p] = rank[order[p]].
+// rank_m[p] = rank[order[p]].  One warp per 32 consecutive positions: the
+// warp reads each source row with coalesced loads (lane = channel) and writes
+// channel c to slab c / 8, so one store fills four whole 32-byte slab rows.
 // ---------------------------------------------------------------------------
 __global__ void k_relayout(const float *__restrict__ attrs, int64_t n, int32_t C, int32_t n_slabs,
                            const uint32_t *__restrict__ order, const int32_t *__restrict__ rank,
                            float *__restrict__ slabs, int32_t *__restrict__ rank_m,
                            int32_t *__restrict__ order_out) {
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    uint32_t i = order[p];
-    rank_m[p] = rank[i];
-    order_out[p] = (int32_t)i;
-    const float *row = attrs + (int64_t)i * C;
-    for (int s = 0; s < n_slabs; s++) {
-        float v[8];
-#pragma unroll
-        for (int j = 0; j < 8; j++) {
-            int c = s * 8 + j;
-            v[j] = c < C ? row[c] : 0.0f;
+    const int lane = threadIdx.x & 31;
+    const int64_t p0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) - lane;   // the warp's first position
+    if (p0 >= n) return;   // whole warps
+    const int nr = n - p0 < 32 ? (int)(n - p0) : 32;
+    uint32_t my_i = 0;
+    if (lane < nr) {
+        my_i = order[p0 + lane];
+        rank_m[p0 + lane] = rank[my_i];
+        order_out[p0 + lane] = (int32_t)my_i;
+    }
+    const int width = 8 * n_slabs;   // channels including the zero padding
+    for (int cb = 0; cb < width; cb += 32) {
+        const int c = cb + lane;
+        float *dst = slabs + (int64_t)(c >> 3) * n * 8 + (c & 7);
+#pragma unroll 8
+        for (int r = 0; r < 32; r++) {
+            const uint32_t i = __shfl_sync(0xFFFFFFFFu, my_i, r);
+            if (r < nr && c < width) dst[(p0 + r) * 8] = c < C ? __ldg(attrs + (int64_t)i * C + c) : 0.0f;
         }
-        float4 *dst = reinterpret_cast<float4 *>(slabs + ((int64_t)s * n + p) * 8);
-        dst[0] = make_float4(v[0], v[1], v[2], v[3]);
-        dst[1] = make_float4(v[4], v[5], v[6], v[7]);
     }
 }
 
