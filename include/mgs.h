@@ -482,7 +482,10 @@ typedef struct {
  * solver); compress the solution; stop once |S_a - S_T| / S_T < tolerance.
  * Among the converged ratios the smallest Omega wins (ties: the larger
  * ratio).  `table` is the scene's cost table for `grid` (device memory, laid
- * out by `layout`).  Synchronises `stream`.  INFEASIBLE if no ratio
+ * out by `layout`).  The ratios run concurrently, each on a host thread (at
+ * most 16) with its own stream that starts after the work already queued on
+ * `stream`; each ratio's rounds, and so the result, are the same as when they
+ * run one after another.  Synchronises `stream`.  INFEASIBLE if no ratio
  * converged (the per-ratio arrays are still filled); INVALID_ARG for
  * mismatched grid, layout and scene or bad options.
  */

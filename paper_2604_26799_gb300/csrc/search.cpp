@@ -10,11 +10,17 @@
 //
 // Each ILP is the device solver on a one-ratio view of the cost table (same
 // buffer, offsets moved to that ratio's items); each compression runs the
-// quantiser and the block coder on the GPU with the scene's kept lists.
+// quantiser and the block coder on the GPU with the scene's kept lists.  The
+// ratios do not depend on one another until the final pick, so each runs its
+// loop on a host thread with its own stream and buffers; every ratio's rounds
+// are the same as when they run one after another.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "internal.h"
@@ -46,6 +52,110 @@ void ratio_view(const mgs_table_layout &L, const mgs_grid &G, int r, mgs_table_l
     *VG = G;
     VG->n_ratios = 1;
     VG->keep = keep_r;
+}
+
+// What one ratio's loop produced.
+struct RatioRun {
+    int32_t status = -1, rounds = 0;
+    double actual = 0.0, delta = 0.0, obj = 0.0, est = 0.0;
+    std::vector<uint8_t> bits;   // the widths of its last compression
+    mgs_status err = MGS_OK;
+    std::string msg;
+};
+
+// Alg. 1's loop for ratio r on stream st: compress at init_bits; skip when
+// twice that is still under the budget; then S_Delta, one-ratio ILP,
+// compression, until the actual size is within the tolerance.
+mgs_status run_ratio(mgs_ctx *ctx, mgs_scene *sc, const mgs_grid *grid, const void *table,
+                     const mgs_table_layout *layout, const mgs_calib_opts *opts, int k0,
+                     const int32_t *kept, int r, cudaStream_t st, RatioRun *R) {
+    const int nb = grid->n_bits;
+    const int32_t G = grid->group_size;
+    const double S_T = opts->budget_bytes;
+    const double cst = opts->solve.const_bytes, meta = opts->solve.meta_bytes_per_group;
+    const int64_t m = layout->item_begin[r + 1] - layout->item_begin[r];
+    const int64_t ib = layout->item_begin[r];
+    const unsigned char *tb = static_cast<const unsigned char *>(table);
+    std::vector<uint8_t> choice((size_t)m), qbits((size_t)m);
+    uint8_t *d_bits = nullptr;
+    MGS_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void **>(&d_bits), (size_t)std::max<int64_t>(m, 1), st));
+    struct Free {
+        uint8_t *p;
+        cudaStream_t st;
+        ~Free() { cudaFreeAsync(p, st); }
+    } free_bits{d_bits, st};
+
+    auto compress = [&](double *S_a) -> mgs_status {
+        int64_t coded = 0;
+        MGS_TRY(encode_launch(ctx, sc, kept, grid->keep[r], G, d_bits, nullptr, 0, nullptr, &coded, st));
+        *S_a = (double)coded + cst;
+        R->rounds++;
+        return MGS_OK;
+    };
+
+    // Q = {init_bits}: compress, and its estimate without S_Delta
+    MGS_CUDA_TRY(cudaMemsetAsync(d_bits, opts->init_bits, (size_t)m, st));
+    double S_a = 0;
+    MGS_TRY(compress(&S_a));
+    double est0 = meta * (double)m + cst;
+    if (opts->solve.rate_model == MGS_RATE_ENTROPY) {
+        std::vector<double> col((size_t)m);
+        MGS_CUDA_TRY(cudaMemcpy2DAsync(col.data(), sizeof(double), tb + layout->off_hbits + 8 * (ib * nb + k0),
+                                       8 * (size_t)nb, sizeof(double), (size_t)m, cudaMemcpyDeviceToHost,
+                                       st));
+        MGS_CUDA_TRY(cudaStreamSynchronize(st));
+        for (int64_t i = 0; i < m; i++) est0 += col[i] / 8.0;
+    } else {
+        std::vector<int32_t> cnt((size_t)m);
+        MGS_CUDA_TRY(cudaMemcpyAsync(cnt.data(), tb + layout->off_count + 4 * ib, 4 * (size_t)m,
+                                     cudaMemcpyDeviceToHost, st));
+        MGS_CUDA_TRY(cudaStreamSynchronize(st));
+        for (int64_t i = 0; i < m; i++) est0 += (double)cnt[i] * opts->init_bits / 8.0;
+    }
+    R->actual = S_a;
+    if (2.0 * S_a < S_T) {   // even twice the widths stay under the budget: tau too small
+        R->status = 1;
+        return MGS_OK;
+    }
+    mgs_table_layout V;
+    mgs_grid VG;
+    int64_t keep_r;
+    ratio_view(*layout, *grid, r, &V, &VG, &keep_r);
+    R->status = 2;
+    for (int round = 0; round < opts->max_rounds; round++) {
+        const double delta = S_a - est0;
+        mgs_solve_opts so = opts->solve;
+        so.delta_bytes = delta;
+        mgs_solution sol{};
+        int32_t st1 = 0;
+        double ob = 0, by = 0, lp = 0;
+        sol.choice = choice.data();
+        sol.ratio_status = &st1;
+        sol.ratio_objective = &ob;
+        sol.ratio_bytes = &by;
+        sol.ratio_lp_bound = &lp;
+        mgs_status e = mgs_solve_budgets_device(ctx, table, &V, &VG, 1, &S_T, &so, &sol, st);
+        if (e == MGS_ERR_INFEASIBLE || sol.r_index < 0) {
+            clear_error();
+            R->status = -1;
+            return MGS_OK;
+        }
+        if (e != MGS_OK) return e;
+        for (int64_t i = 0; i < m; i++) qbits[i] = (uint8_t)grid->bits[choice[i]];
+        MGS_CUDA_TRY(cudaMemcpyAsync(d_bits, qbits.data(), (size_t)m, cudaMemcpyHostToDevice, st));
+        est0 = sol.est_bytes - delta;
+        R->delta = delta;
+        R->obj = sol.objective;
+        R->est = sol.est_bytes;
+        MGS_TRY(compress(&S_a));
+        R->actual = S_a;
+        R->bits.assign(qbits.begin(), qbits.begin() + m);
+        if (std::fabs(S_a - S_T) / S_T < opts->tolerance) {
+            R->status = 0;
+            return MGS_OK;
+        }
+    }
+    return MGS_OK;
 }
 
 }  // namespace
@@ -86,9 +196,6 @@ extern "C" mgs_status mgs_search_calibrated(mgs_ctx *ctx, const mgs_scene *scene
     DeviceGuard dg(ctx->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     mgs_scene *sc = const_cast<mgs_scene *>(scene);
-    const int32_t G = grid->group_size;
-    const double S_T = opts->budget_bytes;
-    const double cst = opts->solve.const_bytes, meta = opts->solve.meta_bytes_per_group;
 
     const int32_t *pos = nullptr;
     std::vector<int64_t> off;
@@ -96,143 +203,75 @@ extern "C" mgs_status mgs_search_calibrated(mgs_ctx *ctx, const mgs_scene *scene
         std::lock_guard<std::mutex> lk(sc->mu);
         MGS_TRY(scene_kept(sc, grid->keep, nr, st, &pos, &off));
     }
-    int64_t max_m = 0;
-    for (int r = 0; r < nr; r++) max_m = std::max(max_m, layout->item_begin[r + 1] - layout->item_begin[r]);
-    uint8_t *d_bits = nullptr;
-    MGS_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void **>(&d_bits), (size_t)max_m, st));
-    std::vector<uint8_t> choice((size_t)max_m), qbits((size_t)max_m);
-    std::vector<std::vector<uint8_t>> final_bits(nr);
-    std::vector<double> col((size_t)max_m);
-    std::vector<int32_t> cnt((size_t)max_m);
-    std::vector<int32_t> r_status(nr, -1), r_rounds(nr, 0);
-    std::vector<double> r_actual(nr, 0.0), r_delta(nr, 0.0), r_obj(nr, 0.0), r_est(nr, 0.0);
-    int32_t total_rounds = 0;
-    mgs_status s = MGS_OK;
+    // every ratio's stream starts after the caller's work and the kept lists
+    cudaEvent_t ready = nullptr;
+    MGS_CUDA_TRY(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    if (cudaEventRecord(ready, st) != cudaSuccess) {
+        cudaEventDestroy(ready);
+        set_error("event record failed");
+        return MGS_ERR_CUDA;
+    }
 
-    auto compress = [&](int r, double *S_a) -> mgs_status {
-        int64_t coded = 0;
-        MGS_TRY(encode_launch(ctx, sc, pos + off[r], grid->keep[r], G, d_bits, nullptr, 0, nullptr,
-                              &coded, st));
-        *S_a = (double)coded + cst;
-        total_rounds++;
-        r_rounds[r]++;
-        return MGS_OK;
-    };
-
-    for (int r = 0; r < nr && s == MGS_OK; r++) {
-        const int64_t m = layout->item_begin[r + 1] - layout->item_begin[r];
-        const unsigned char *tb = static_cast<const unsigned char *>(table);
-        const int64_t ib = layout->item_begin[r];
-        // Q = {init_bits}: compress, and its estimate without S_Delta
-        if (cudaMemsetAsync(d_bits, opts->init_bits, (size_t)m, st) != cudaSuccess) {
-            set_error("memset failed");
-            s = MGS_ERR_CUDA;
-            break;
-        }
-        double S_a = 0;
-        s = compress(r, &S_a);
-        if (s != MGS_OK) break;
-        double est0 = meta * (double)m + cst;
-        if (opts->solve.rate_model == MGS_RATE_ENTROPY) {
-            cudaError_t e = cudaMemcpy2DAsync(col.data(), sizeof(double),
-                                              tb + layout->off_hbits + 8 * (ib * nb + k0),
-                                              8 * (size_t)nb, sizeof(double), (size_t)m,
-                                              cudaMemcpyDeviceToHost, st);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-            if (e != cudaSuccess) {
-                set_error("entropy column copy: %s", cudaGetErrorString(e));
-                s = MGS_ERR_CUDA;
-                break;
+    std::vector<RatioRun> runs(nr);
+    std::atomic<int> next{0};
+    auto worker = [&]() {
+        DeviceGuard g(ctx->device);
+        cudaStream_t ws = nullptr;
+        if (cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamWaitEvent(ws, ready, 0) != cudaSuccess) {
+            for (int r; (r = next.fetch_add(1)) < nr;) {
+                runs[r].err = MGS_ERR_CUDA;
+                runs[r].msg = "stream creation failed";
             }
-            for (int64_t i = 0; i < m; i++) est0 += col[i] / 8.0;
-        } else {
-            cudaError_t e = cudaMemcpyAsync(cnt.data(), tb + layout->off_count + 4 * ib, 4 * (size_t)m,
-                                            cudaMemcpyDeviceToHost, st);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-            if (e != cudaSuccess) {
-                set_error("group count copy: %s", cudaGetErrorString(e));
-                s = MGS_ERR_CUDA;
-                break;
-            }
-            for (int64_t i = 0; i < m; i++) est0 += (double)cnt[i] * opts->init_bits / 8.0;
+            if (ws) cudaStreamDestroy(ws);
+            return;
         }
-        r_actual[r] = S_a;
-        if (2.0 * S_a < S_T) {   // even twice the widths stay under the budget: tau too small
-            r_status[r] = 1;
-            continue;
-        }
-        mgs_table_layout V;
-        mgs_grid VG;
-        int64_t keep_r;
-        ratio_view(*layout, *grid, r, &V, &VG, &keep_r);
-        r_status[r] = 2;
-        for (int round = 0; round < opts->max_rounds; round++) {
-            const double delta = S_a - est0;
-            mgs_solve_opts so = opts->solve;
-            so.delta_bytes = delta;
-            mgs_solution sol{};
-            int32_t st1 = 0;
-            double ob = 0, by = 0, lp = 0;
-            sol.choice = choice.data();
-            sol.ratio_status = &st1;
-            sol.ratio_objective = &ob;
-            sol.ratio_bytes = &by;
-            sol.ratio_lp_bound = &lp;
-            mgs_status e = mgs_solve_budgets_device(ctx, table, &V, &VG, 1, &S_T, &so, &sol, st);
-            if (e == MGS_ERR_INFEASIBLE || sol.r_index < 0) {
-                clear_error();
-                r_status[r] = -1;
-                break;
-            }
+        for (int r; (r = next.fetch_add(1)) < nr;) {
+            clear_error();
+            const mgs_status e = run_ratio(ctx, sc, grid, table, layout, opts, k0, pos + off[r], r, ws, &runs[r]);
             if (e != MGS_OK) {
-                s = e;
-                break;
-            }
-            for (int64_t i = 0; i < m; i++) qbits[i] = (uint8_t)grid->bits[choice[i]];
-            if (cudaMemcpyAsync(d_bits, qbits.data(), (size_t)m, cudaMemcpyHostToDevice, st) !=
-                cudaSuccess) {
-                set_error("bits copy failed");
-                s = MGS_ERR_CUDA;
-                break;
-            }
-            est0 = sol.est_bytes - delta;
-            r_delta[r] = delta;
-            r_obj[r] = sol.objective;
-            r_est[r] = sol.est_bytes;
-            s = compress(r, &S_a);
-            if (s != MGS_OK) break;
-            r_actual[r] = S_a;
-            final_bits[r].assign(qbits.begin(), qbits.begin() + m);
-            if (std::fabs(S_a - S_T) / S_T < opts->tolerance) {
-                r_status[r] = 0;
-                break;
+                runs[r].err = e;
+                runs[r].msg = mgs_last_error();
             }
         }
-    }
-    cudaFreeAsync(d_bits, st);
-    if (s == MGS_OK && cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaStreamSynchronize(ws);
+        cudaStreamDestroy(ws);
+    };
+    const int n_workers = std::min(nr, 16);
+    std::vector<std::thread> pool;
+    for (int w = 1; w < n_workers; w++) pool.emplace_back(worker);
+    worker();
+    for (auto &th : pool) th.join();
+    cudaEventDestroy(ready);
+    if (cudaStreamSynchronize(st) != cudaSuccess) {
         set_error("calibrated search: stream error");
-        s = MGS_ERR_CUDA;
+        return MGS_ERR_CUDA;
     }
-    if (s != MGS_OK) return s;
+    for (int r = 0; r < nr; r++)
+        if (runs[r].err != MGS_OK) {
+            set_error("%s", runs[r].msg.c_str());
+            return runs[r].err;
+        }
 
     int best = -1;
+    int32_t total_rounds = 0;
     for (int r = 0; r < nr; r++) {
-        if (r_status[r] != 0) continue;
-        if (best < 0 || r_obj[r] <= r_obj[best]) best = r;   // ties: the larger ratio
+        total_rounds += runs[r].rounds;
+        if (runs[r].status != 0) continue;
+        if (best < 0 || runs[r].obj <= runs[best].obj) best = r;   // ties: the larger ratio
     }
     out->r_index = best;
     out->rounds = total_rounds;
-    out->actual_bytes = best >= 0 ? r_actual[best] : 0.0;
-    out->est_bytes = best >= 0 ? r_est[best] : 0.0;
-    out->objective = best >= 0 ? r_obj[best] : 0.0;
-    if (out->bits && best >= 0) std::copy(final_bits[best].begin(), final_bits[best].end(), out->bits);
+    out->actual_bytes = best >= 0 ? runs[best].actual : 0.0;
+    out->est_bytes = best >= 0 ? runs[best].est : 0.0;
+    out->objective = best >= 0 ? runs[best].obj : 0.0;
+    if (out->bits && best >= 0) std::copy(runs[best].bits.begin(), runs[best].bits.end(), out->bits);
     for (int r = 0; r < nr; r++) {
-        if (out->ratio_status) out->ratio_status[r] = r_status[r];
-        if (out->ratio_rounds) out->ratio_rounds[r] = r_rounds[r];
-        if (out->ratio_actual) out->ratio_actual[r] = r_actual[r];
-        if (out->ratio_delta) out->ratio_delta[r] = r_delta[r];
-        if (out->ratio_objective) out->ratio_objective[r] = r_obj[r];
+        if (out->ratio_status) out->ratio_status[r] = runs[r].status;
+        if (out->ratio_rounds) out->ratio_rounds[r] = runs[r].rounds;
+        if (out->ratio_actual) out->ratio_actual[r] = runs[r].actual;
+        if (out->ratio_delta) out->ratio_delta[r] = runs[r].delta;
+        if (out->ratio_objective) out->ratio_objective[r] = runs[r].obj;
     }
     if (best < 0) {
         set_error("no ratio reached the budget within the tolerance");
