@@ -570,7 +570,7 @@ def run_serve(args):
         mgs.mgs_scene_destroy(sc)
         plain_service.append(time.perf_counter() - t0)
     srv = mgs.mgs_server_create(ctx, max_jobs=8, solver_threads=8, hbm_budget_bytes=120 << 30,
-                                slice_items=40_000)
+                                slice_items=args.slice_items)
     ids, sub_wall = [], []
     t_start = time.perf_counter()
     for j in range(n_jobs):
@@ -616,7 +616,7 @@ def run_serve(args):
         "server": stats, "stages": stages, "data": "synthetic",
         "config": {"workload": "serving: Poisson 20 jobs/s, N log-uniform 1e5..6e6 (12-scene pool), "
                                "budget U[5,60] MB, 10 ratios x 10 bit-widths, G 4096",
-                   "pool_sizes": pool_n}}))
+                   "pool_sizes": pool_n, "slice_items": args.slice_items}}))
 
 
 def run_large(args):
@@ -1103,6 +1103,8 @@ def main():
                          "of the SH coefficients and the assignment of every vector; solvers: the flat "
                          "0-1 ILP (device, host) against the hierarchical solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--slice-items", type=int, default=40_000,
+                    help="serve: cost-table work items per batched launch")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-loop comparator")
     ap.add_argument("--no-autotune", action="store_true", help="use the default tile shape")
     ap.add_argument("--n", type=int, default=None,
