@@ -353,23 +353,28 @@ __device__ __forceinline__ void hist_finish(uint32_t *hist, int mode, int b, int
                                             unsigned long long &hacc) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (mode == kLane) {
+        // the warp's j-th bin count is kept by lane j (bins / warps <= 32 for
+        // b <= 6), so the table lookups of all its bins go out together
+        static_assert((1 << kLaneMaxBits) / (T / 32) <= 32, "one lane per bin of a warp");
         const int bins = 1 << b;
-#pragma unroll 2
-        for (int k = warp; k < bins; k += T / 32) {
-            uint32_t v = hist[k * 32 + lane];
+        uint32_t mine = 0;
+        int j = 0;
+#pragma unroll 4
+        for (int k = warp; k < bins; k += T / 32, j++) {
+            const uint32_t v = hist[k * 32 + lane];
             hist[k * 32 + lane] = 0u;
-            uint32_t s = __reduce_add_sync(kFull, v);
-            if (lane == 0 && s) hacc += ld_keep(&ltab[s]);
+            const uint32_t s = __reduce_add_sync(kFull, v);
+            mine = lane == j ? s : mine;
         }
+        hacc += ld_keep(&ltab[mine]);   // L(0) = 0 for lanes without a bin
     } else if (mode == kDirect) {
+        // branch-free: L(0) = 0, so an empty bin adds nothing
         const int bins = 1 << b;
 #pragma unroll 4
         for (int k = threadIdx.x; k < bins; k += T) {
-            uint32_t v = hist[k];
-            if (v) {
-                hacc += ld_keep(&ltab[v]);
-                hist[k] = 0u;
-            }
+            const uint32_t v = hist[k];
+            hist[k] = 0u;
+            hacc += ld_keep(&ltab[v]);
         }
     } else {
         uint4 *h4 = reinterpret_cast<uint4 *>(hist);
