@@ -133,18 +133,38 @@ __global__ void __launch_bounds__(kVqChunk)
 }
 
 // First slot of every (chunk, centre): the centre's first slot off[k] plus
-// the counts of the earlier chunks (one thread per centre, chunks in order;
-// the counts are [chunk][centre], so a warp's loads are contiguous).
-__global__ void k_vq_slots(int32_t *__restrict__ cnt, int32_t nch, const int32_t *__restrict__ off,
-                           int32_t K) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+// the counts of the earlier chunks (the counts are [chunk][centre], so a
+// warp's loads are contiguous).
+// One CTA per 32 entries (a lane each); its warps split the chunks into
+// contiguous ranges: each warp sums its range (independent loads), the warps'
+// sums give each range's start, then each warp writes its range's prefixes.
+constexpr int kSlotWarps = 8;
+__global__ void __launch_bounds__(32 * kSlotWarps)
+    k_vq_slots(int32_t *__restrict__ cnt, int32_t nch, const int32_t *__restrict__ off, int32_t K) {
+    __shared__ int32_t part[kSlotWarps][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int k = blockIdx.x * 32 + lane;
+    const int per = (nch + kSlotWarps - 1) / kSlotWarps;
+    const int c0 = warp * per, c1 = min(nch, c0 + per);
+    int32_t sum = 0;
+    if (k < K) {
+#pragma unroll 8
+        for (int c = c0; c < c1; c++) sum += cnt[(int64_t)c * K + k];
+    }
+    part[warp][lane] = sum;
+    __syncthreads();
     if (k >= K) return;
     int32_t run = off[k];
-    for (int c = 0; c < nch; c++) {
-        int32_t *p = cnt + (int64_t)c * K + k;
-        const int32_t t = *p;
-        *p = run;
-        run += t;
+    for (int w = 0; w < warp; w++) run += part[w][lane];
+    for (int cb = c0; cb < c1; cb += 8) {
+        int32_t t[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) t[u] = cb + u < c1 ? cnt[(int64_t)(cb + u) * K + k] : 0;
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            if (cb + u < c1) cnt[(int64_t)(cb + u) * K + k] = run;
+            run += t[u];
+        }
     }
 }
 
@@ -225,7 +245,20 @@ __global__ void k_vq_move(const float *__restrict__ x, int32_t D, const int32_t 
     if (!mk) return;
     double sum = 0.0;
     const int o = off[k];
-    for (int r = 0; r < mk; r++) sum = __dadd_rn(sum, (double)x[(int64_t)rows[perm[o + r]] * D + d]);
+    // eight vectors at a time: their row indices, then their values, are
+    // loaded together; the sum still runs in batch order
+    int r = 0;
+    for (; r + 8 <= mk; r += 8) {
+        int64_t ri[8];
+        float xv[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) ri[u] = rows[perm[o + r + u]];
+#pragma unroll
+        for (int u = 0; u < 8; u++) xv[u] = x[ri[u] * D + d];
+#pragma unroll
+        for (int u = 0; u < 8; u++) sum = __dadd_rn(sum, (double)xv[u]);
+    }
+    for (; r < mk; r++) sum = __dadd_rn(sum, (double)x[(int64_t)rows[perm[o + r]] * D + d]);
     const double v = (double)counts[k];
     const double num = __dadd_rn(__dmul_rn(v, (double)cb[t]), sum);
     cb[t] = __double2float_rn(__ddiv_rn(num, __dadd_rn(v, (double)mk)));
@@ -475,7 +508,7 @@ extern "C" mgs_status mgs_vq_train(mgs_ctx *ctx, const float *x, int64_t n, int3
             const unsigned nch = (unsigned)((batch + kVqChunk - 1) / kVqChunk);
             const size_t ks = sizeof(int32_t) * (size_t)K;
             k_vq_chunk_counts<<<nch, kVqChunk, ks, st>>>(a, batch, K, ccnt);
-            k_vq_slots<<<(K + 255) / 256, 256, 0, st>>>(ccnt, (int32_t)nch, off, K);
+            k_vq_slots<<<(K + 31) / 32, 32 * kSlotWarps, 0, st>>>(ccnt, (int32_t)nch, off, K);
             k_vq_chunk_place<<<nch, kVqChunk, ks, st>>>(a, batch, K, ccnt, perm);
             const int64_t kd = (int64_t)K * D;
             k_vq_move<<<(unsigned)((kd + 255) / 256), 256, 0, st>>>(x, D, rows, perm, off, m, codebook,
