@@ -39,12 +39,16 @@ __host__ __device__ inline int64_t a16(int64_t x) { return (x + 15) & ~(int64_t)
 struct EncSmem {
     int64_t hist, sym, f, cum, tab, total;
     __host__ __device__ explicit EncSmem(int G) {
-        hist = 0;                             // uint32[kWin] (also the code -> entry map)
-        sym = hist + 4 * kWin;                // uint16[G]: distinct codes, ascending
+        // uint16[kWin] counts as 16-bit pairs in 32-bit words (a count is at most
+        // G <= 16384), then the code -> entry map; once the map has been read,
+        // the same bytes hold the table's bits (uint32 words, < 2G + 16 bytes)
+        hist = 0;
+        tab = 0;
+        const int64_t shared_bytes = 2 * (int64_t)G + 16 > 2 * kWin ? 2 * (int64_t)G + 16 : 2 * kWin;
+        sym = a16(shared_bytes);              // uint16[G]: distinct codes, ascending
         f = sym + a16(2 * (int64_t)G);        // uint16[G]: normalised frequencies (counts first)
         cum = f + a16(2 * (int64_t)G);        // uint16[G]
-        tab = cum + a16(2 * (int64_t)G);      // uint32 words: the table's bits (< 2G + 16 bytes)
-        total = tab + a16(2 * (int64_t)G + 16);
+        total = cum + a16(2 * (int64_t)G);
     }
 };
 
@@ -117,7 +121,8 @@ __global__ void __launch_bounds__(kEncThreads)
     __shared__ uint32_t s_top;
 
     const EncSmem L(G);
-    uint32_t *s_hist = reinterpret_cast<uint32_t *>(smem + L.hist);
+    uint32_t *s_hw = reinterpret_cast<uint32_t *>(smem + L.hist);   // counter pairs
+    uint16_t *s_hist = reinterpret_cast<uint16_t *>(smem + L.hist);
     uint16_t *s_sym = reinterpret_cast<uint16_t *>(smem + L.sym);
     uint16_t *s_f = reinterpret_cast<uint16_t *>(smem + L.f);
     uint16_t *s_cum = reinterpret_cast<uint16_t *>(smem + L.cum);
@@ -160,11 +165,12 @@ __global__ void __launch_bounds__(kEncThreads)
     const int per = (W + kEncThreads - 1) / kEncThreads;
     for (int w = 0; w < nwin; w++) {
         if (nwin > 1 && s_wcnt[w] == 0) continue;   // uniform: s_wcnt is settled
-        for (int i = t; i < W; i += kEncThreads) s_hist[i] = 0;
+        for (int i = t; i < W / 2; i += kEncThreads) s_hw[i] = 0;   // W >= 2
         __syncthreads();
         for (int i = t; i < n; i += kEncThreads) {
             uint32_t q = src[i];
-            if ((int)(q >> logW) == w) atomicAdd(&s_hist[q & (W - 1)], 1u);
+            const uint32_t c = q & (W - 1);
+            if ((int)(q >> logW) == w) atomicAdd(&s_hw[c >> 1], 1u << (16 * (c & 1)));
         }
         __syncthreads();
         const int lo = t * per, hi = min(W, lo + per);
@@ -177,7 +183,7 @@ __global__ void __launch_bounds__(kEncThreads)
             if (h) {
                 s_sym[at] = (uint16_t)((w << logW) + i);
                 s_f[at] = (uint16_t)h;   // count for now
-                if (nwin == 1) s_hist[i] = (uint32_t)at;   // code -> entry map
+                if (nwin == 1) s_hist[i] = (uint16_t)at;   // code -> entry map
                 at++;
             }
         }
@@ -269,6 +275,7 @@ __global__ void __launch_bounds__(kEncThreads)
         }
         fc[i] = ((uint32_t)s_f[e] << 16) | (uint32_t)s_cum[e];
     }
+    __syncthreads();   // the map is read: its bytes now hold the table
     const int64_t words = (tab_bytes + 3) / 4;
     for (int64_t q = t; q < words; q += kEncThreads) s_tab[q] = 0;
     __syncthreads();
