@@ -182,6 +182,9 @@ __global__ void __launch_bounds__(kScanThreads)
         if (base + j < total) data[base + j] += off;
 }
 
+// The tile's pairs are first placed in shared memory in (digit, tile order)
+// order -- the same stable ranks as before -- and then written out from there,
+// so consecutive threads store consecutive positions of a digit's bucket.
 template <typename K>
 __global__ void __launch_bounds__(kTileThreads) k_scatter(const K *__restrict__ kin,
                                                           const uint32_t *__restrict__ vin,
@@ -190,12 +193,18 @@ __global__ void __launch_bounds__(kTileThreads) k_scatter(const K *__restrict__ 
                                                           int shift,
                                                           const uint32_t *__restrict__ offs,
                                                           int n_tiles) {
+    extern __shared__ __align__(16) unsigned char s_pairs[];   // K[kTile], then uint32[kTile]
+    K *skey = reinterpret_cast<K *>(s_pairs);
+    uint32_t *sval = reinterpret_cast<uint32_t *>(s_pairs + sizeof(K) * kTile);
     __shared__ uint32_t wcnt[kWarps][257];
+    __shared__ uint32_t tdo[256];         // first tile slot of each digit
+    __shared__ uint32_t wtot[kWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < kWarps * 257; i += kTileThreads) (&wcnt[0][0])[i] = 0;
     __syncthreads();
     const uint32_t lt = (1u << lane) - 1u;
-    const int64_t base = (int64_t)blockIdx.x * kTile + warp * (kTile / kWarps);
+    const int64_t tile0 = (int64_t)blockIdx.x * kTile;
+    const int64_t base = tile0 + warp * (kTile / kWarps);
     K key[kTileItems];
     uint32_t val[kTileItems], local[kTileItems], dig[kTileItems];
 #pragma unroll
@@ -214,25 +223,46 @@ __global__ void __launch_bounds__(kTileThreads) k_scatter(const K *__restrict__ 
         __syncwarp();
     }
     __syncthreads();
-    // exclusive scan over warps, per digit
+    // exclusive scan over warps, per digit (thread = digit), then over the
+    // digits' tile totals
+    uint32_t cnt = 0;
     {
-        int d = threadIdx.x;   // 256 threads = 256 digits
-        uint32_t run = 0;
+        const int d = threadIdx.x;   // 256 threads = 256 digits
         for (int w = 0; w < kWarps; w++) {
             uint32_t v = wcnt[w][d];
-            wcnt[w][d] = run;
-            run += v;
+            wcnt[w][d] = cnt;
+            cnt += v;
         }
     }
+    uint32_t inc = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) wtot[warp] = inc;
+    __syncthreads();
+    uint32_t wpre = 0;
+    for (int w = 0; w < warp; w++) wpre += wtot[w];
+    tdo[threadIdx.x] = wpre + inc - cnt;
     __syncthreads();
 #pragma unroll
     for (int c = 0; c < kTileItems; c++) {
         if (dig[c] < 256u) {
-            uint32_t d = dig[c];
-            uint64_t pos = (uint64_t)offs[(int64_t)d * n_tiles + blockIdx.x] + wcnt[warp][d] + local[c];
-            kout[pos] = key[c];
-            vout[pos] = val[c];
+            const uint32_t sp = tdo[dig[c]] + wcnt[warp][dig[c]] + local[c];
+            skey[sp] = key[c];
+            sval[sp] = val[c];
         }
+    }
+    __syncthreads();
+    const int nv = n - tile0 < (int64_t)kTile ? (int)(n - tile0) : kTile;
+#pragma unroll 4
+    for (int j = threadIdx.x; j < nv; j += kTileThreads) {
+        const K kk = skey[j];
+        const uint32_t d = (uint32_t)(kk >> shift) & 255u;
+        const uint64_t pos = (uint64_t)offs[(int64_t)d * n_tiles + blockIdx.x] + (uint32_t)(j - tdo[d]);
+        kout[pos] = kk;
+        vout[pos] = sval[j];
     }
 }
 
@@ -247,11 +277,14 @@ mgs_status radix_sort_pairs(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals
     const int64_t entries = (int64_t)256 * n_tiles;
     const int scan_blocks = (int)((entries + kScanChunk - 1) / kScanChunk);
     uint32_t *totals = hist + entries;   // hist holds 256 * n_tiles + scan_blocks entries
+    const int kScatterSmem = (int)((sizeof(K) + sizeof(uint32_t)) * kTile);   // the tile's pairs
+    MGS_CUDA_TRY(cudaFuncSetAttribute(k_scatter<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      kScatterSmem));
     for (int shift = 0; shift < key_bits; shift += 8) {
         k_digit_hist<K><<<n_tiles, kTileThreads, 0, st>>>(ki, n, shift, hist, n_tiles);
         k_scan_chunks<<<scan_blocks, kScanThreads, 0, st>>>(hist, entries, totals);
         k_scan_add<<<scan_blocks, kScanThreads, 0, st>>>(hist, entries, totals);
-        k_scatter<K><<<n_tiles, kTileThreads, 0, st>>>(ki, vi, ko, vo, n, shift, hist, n_tiles);
+        k_scatter<K><<<n_tiles, kTileThreads, kScatterSmem, st>>>(ki, vi, ko, vo, n, shift, hist, n_tiles);
         count_launches(4);
         std::swap(ki, ko);
         std::swap(vi, vo);
