@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -81,6 +82,7 @@ struct mgs_server {
     std::map<int64_t, std::unique_ptr<mgs::Job>> jobs;
     int in_flight = 0;
     int64_t used_bytes = 0;
+    std::atomic<int> ingesting{0};   // scene builds in flight: cost launches are shortened
     cudaStream_t ingest_stream = nullptr, compute_stream = nullptr, copy_stream = nullptr;   // copy: frees
     std::thread ingest_thread, compute_thread;
     std::vector<std::thread> solvers;
@@ -174,6 +176,7 @@ void ingest_loop(mgs_server *S) {
             S->used_bytes += j->footprint;
             j->state = kIngesting;
             j->t_admit = now_s(S);
+            S->ingesting++;
         }
         mgs_status s = mgs_scene_create(S->ctx, j->attrs, j->importance, j->n, j->C,
                                         S->ingest_stream, &j->scene);
@@ -224,6 +227,7 @@ void ingest_loop(mgs_server *S) {
                 s = MGS_ERR_CUDA;
             }
         }
+        S->ingesting--;
         std::lock_guard<std::mutex> lk(S->mu);
         if (s != MGS_OK) {
             fail_job(S, j, s, "ingest");
@@ -264,6 +268,10 @@ void compute_loop(mgs_server *S) {
             int64_t budget_groups =
                 S->opts.slice_items > 0 ? std::max<int64_t>(1, S->opts.slice_items / chunks_per_group)
                                         : INT64_MAX;
+            // a launch holds every SM until its slice is done, so while a new job's
+            // scene is being built the slices are an eighth as long
+            if (S->ingesting.load() > 0 && budget_groups != INT64_MAX)
+                budget_groups = std::max<int64_t>(1, budget_groups / 8);
             int64_t share = std::max<int64_t>(1, budget_groups / (int64_t)batch.size());
             for (Job *j : batch) {
                 int64_t take = std::min<int64_t>(share, j->groups_left);
