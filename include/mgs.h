@@ -564,8 +564,9 @@ mgs_status mgs_vq_retain(mgs_ctx *ctx, const int32_t *rows, int64_t n_retain, in
  * (a lone job is always admitted); an ingest thread makes its scene resident;
  * a compute thread runs one persistent launch per iteration over a slice of
  * the remaining work items of every admitted job (about slice_items items per
- * launch, 0 = all), so jobs that arrive while others are on the GPU join the
- * next launch; each finished table is solved on the device
+ * launch, 0 = all; an eighth of that while a scene is being made resident, so
+ * that its build is not held up by a long launch), so jobs that arrive while
+ * others are on the GPU join the next launch; each finished table is solved on the device
  * (mgs_solve_budgets_device) by one of solver_threads host threads, each with
  * its own stream, while the next launches run.  A job's results are the same
  * whichever jobs it shares launches with.
