@@ -29,6 +29,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -108,11 +109,17 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+        # the raw samples: a temporary file, or where MGS_CLOCKS_CSV says (kept)
+        self.keep = os.environ.get("MGS_CLOCKS_CSV")
+        if self.keep:
+            self.path = self.keep
+        else:
+            fd, self.path = tempfile.mkstemp(prefix=f"mgs_clocks_gpu{gpu_index}_", suffix=".csv")
+            os.close(fd)
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            os.makedirs(os.path.dirname(os.path.abspath(self.path)), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "50"],
@@ -135,7 +142,14 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         import datetime
         rows = []
-        for line in open(self.path):
+        with open(self.path) as fh:
+            lines = fh.read().splitlines()
+        if not self.keep:
+            try:
+                os.remove(self.path)
+            except OSError:
+                pass
+        for line in lines:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 10:
                 continue

@@ -18,7 +18,7 @@ Distortion (Sec. III-F "Acceleration", Omega = |A_hat - A| with the 1-, 2- or
 inf-norm): "sse" sums squared errors (default), "l2" sums per-group 2-norms
 sqrt(SSE), "l1" and "linf" the other two norms.
 
-Reserve-ratio pick (Alg. 1 with the reading stated in the design doc): a ratio is
+Reserve-ratio pick (Alg. 1, read as follows where it is silent): a ratio is
 skipped when even the top bit-width everywhere stays under the budget (tau too
 small); among the other feasible ratios the smallest total distortion wins,
 ties to the larger ratio.  If every feasible ratio is skipped, the largest

@@ -49,7 +49,7 @@
  *                        quaternion -> Euler replacement of Sec. III-D, over
  *                        a whole scene; FP64 arithmetic, FP32 outputs.
  *
- * Readings where the paper is silent (each is listed in the design doc):
+ * Readings where the paper is silent, fixed here as follows:
  *   - S_c = (max - min) / 2^b exactly as printed (not 2^b - 1); the element
  *     equal to max lands at x ~ 2^b and is clamped to 2^b - 1.
  *   - "rounding to nearest" is round-half-to-even (rintf) for Z_c and c_q.
