@@ -37,7 +37,7 @@ def build(force: bool = False) -> str:
         return _SO
     os.makedirs(_BUILD, exist_ok=True)
     tmp = _SO + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread", "-ffp-contract=off", "-fno-fast-math",
            "-fexcess-precision=standard", "-Wall", "-o", tmp, src, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _SO)
@@ -55,6 +55,7 @@ def load(path: str):
     L.oracle_kept.restype = i64
     L.oracle_group_cost.argtypes = [P, i64, P, i32, P, P, P, P, P, P, P]
     L.oracle_cost_table.argtypes = [P, P, i64, i32, P, i32, P, i32, i32, P, P, P, P, P, P, P]
+    L.oracle_cost_table_mt.argtypes = [P, P, i64, i32, P, i32, P, i32, i32, P, P, P, P, P, P, P, i32]
     L.oracle_quantize.argtypes = [P, P, i64, i32, i64, i32, P, P, P]
     L.oracle_euler.argtypes = [P, P]
     L.oracle_euler.restype = None
@@ -74,7 +75,7 @@ def load(path: str):
     L.oracle_vq_update.argtypes = [P, i64, i32, P, i32, P, P, i32, P]
     for f in (L.oracle_vq_assign, L.oracle_vq_update):
         f.restype = ctypes.c_int
-    for f in (L.oracle_rank, L.oracle_morton, L.oracle_group_cost, L.oracle_cost_table,
+    for f in (L.oracle_rank, L.oracle_morton, L.oracle_group_cost, L.oracle_cost_table, L.oracle_cost_table_mt,
               L.oracle_quantize, L.oracle_preprocess, L.oracle_raht):
         f.restype = ctypes.c_int
     return L
@@ -150,8 +151,9 @@ def n_groups(keep: int, G: int) -> int:
     return (int(keep) + G - 1) // G
 
 
-def cost_table(attrs, importance, keep, bits, G) -> dict:
-    """Whole table, items ordered [r][c][g]; per-option arrays shaped [n_items, n_b]."""
+def cost_table(attrs, importance, keep, bits, G, threads: int = 1) -> dict:
+    """Whole table, items ordered [r][c][g]; per-option arrays shaped [n_items, n_b].
+    threads > 1 spreads the independent items over that many threads (same entries)."""
     a = np.ascontiguousarray(attrs, dtype=np.float32)
     imp = np.ascontiguousarray(importance, dtype=np.float32)
     k = np.ascontiguousarray(keep, dtype=np.int64)
@@ -163,10 +165,12 @@ def cost_table(attrs, importance, keep, bits, G) -> dict:
                linf=np.empty((n_items, nb), dtype=np.float32), hbits=np.empty((n_items, nb)),
                cnt=np.empty(n_items, dtype=np.int32), vmin=np.empty(n_items, dtype=np.float32),
                vmax=np.empty(n_items, dtype=np.float32))
-    _check(lib().oracle_cost_table(_p(a), _p(imp), n, C, _p(k), k.shape[0], _p(b), nb, int(G),
-                                   _p(out["sse"]), _p(out["l1"]), _p(out["linf"]),
-                                   _p(out["hbits"]), _p(out["cnt"]), _p(out["vmin"]),
-                                   _p(out["vmax"])))
+    args = (_p(a), _p(imp), n, C, _p(k), k.shape[0], _p(b), nb, int(G), _p(out["sse"]), _p(out["l1"]),
+            _p(out["linf"]), _p(out["hbits"]), _p(out["cnt"]), _p(out["vmin"]), _p(out["vmax"]))
+    if threads > 1:
+        _check(lib().oracle_cost_table_mt(*args, int(threads)))
+    else:
+        _check(lib().oracle_cost_table(*args))
     return out
 
 

@@ -24,6 +24,8 @@
  *                        tau*N * (-sum p log2 p)).
  *   oracle_cost_table    the loops of Sec. III-F: every reserve ratio, every
  *                        (channel, block), every bit-width.
+ *   oracle_cost_table_mt the same items spread over POSIX threads (same
+ *                        entries; used to time the oracle on every core).
  *   oracle_quantize      Sec. III-D quantiser for one chosen configuration.
  *   oracle_euler         Sec. III-D "Attribute Transformation", Replacement:
  *                        the Euler angles of a rotation quaternion.
@@ -89,6 +91,7 @@
  *     learning rate 1/count carried out exactly over one batch.
  */
 #include <math.h>
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -372,6 +375,128 @@ done:
     free(order);
     free(kept);
     free(vals);
+    return rc;
+}
+
+/*
+ * The same table with its independent (ratio, channel, group) items handed
+ * out to n_threads POSIX threads (the CPU baseline on every host core).  The
+ * ranks, the Morton order and the kept sets are computed once, as above; each
+ * item runs oracle_group_cost unchanged, so every entry equals the
+ * single-threaded table's.  n_threads < 1 means 1.
+ */
+typedef struct {
+    const float *attrs;
+    int32_t n_channels, n_b, G, n_r;
+    const int32_t *bits;
+    const int64_t *order;
+    int64_t **kept;          /* per ratio: kept set (Morton positions into order) */
+    const int64_t *K, *ng, *item0;   /* per ratio; item0 has n_r + 1 entries */
+    double *sse, *l1, *hbits;
+    float *linf, *vmin, *vmax;
+    int32_t *cnt;
+    int64_t next;
+    int rc;
+    pthread_mutex_t mu;
+} oracle_table_job;
+
+static void *oracle_table_worker(void *arg) {
+    oracle_table_job *J = (oracle_table_job *)arg;
+    float *vals = (float *)malloc(sizeof(float) * (size_t)J->G);
+    if (!vals) {
+        pthread_mutex_lock(&J->mu);
+        J->rc = ORACLE_ERR_NOMEM;
+        pthread_mutex_unlock(&J->mu);
+        return NULL;
+    }
+    for (;;) {
+        pthread_mutex_lock(&J->mu);
+        int64_t item = J->next;
+        int stop = J->rc != ORACLE_OK || item >= J->item0[J->n_r];
+        if (!stop) J->next = item + 1;
+        pthread_mutex_unlock(&J->mu);
+        if (stop) break;
+        int32_t r = 0;
+        while (J->item0[r + 1] <= item) r++;
+        int64_t local = item - J->item0[r];
+        int64_t c = local / J->ng[r], g = local % J->ng[r];
+        int64_t start = g * J->G;
+        int64_t len = J->K[r] - start < J->G ? J->K[r] - start : J->G;
+        for (int64_t i = 0; i < len; i++)
+            vals[i] = J->attrs[J->order[J->kept[r][start + i]] * J->n_channels + c];
+        J->cnt[item] = (int32_t)len;
+        int rc = oracle_group_cost(vals, len, J->bits, J->n_b, J->sse + item * J->n_b,
+                                   J->l1 + item * J->n_b, J->linf + item * J->n_b,
+                                   J->hbits + item * J->n_b, J->vmin + item, J->vmax + item, NULL);
+        if (rc) {
+            pthread_mutex_lock(&J->mu);
+            J->rc = rc;
+            pthread_mutex_unlock(&J->mu);
+        }
+    }
+    free(vals);
+    return NULL;
+}
+
+int oracle_cost_table_mt(const float *attrs, const float *importance, int64_t n, int32_t n_channels,
+                         const int64_t *keep, int32_t n_r, const int32_t *bits, int32_t n_b, int32_t G,
+                         double *sse, double *l1, float *linf, double *hbits, int32_t *cnt,
+                         float *vmin, float *vmax, int32_t n_threads) {
+    if (n < 0 || n_channels < 3 || n_r < 1 || n_b < 1 || G < 1) return ORACLE_ERR_ARG;
+    for (int32_t r = 0; r < n_r; r++)
+        if (keep[r] < 0 || keep[r] > n) return ORACLE_ERR_ARG;
+    for (int64_t i = 0; i < n * n_channels; i++)
+        if (!isfinite(attrs[i])) return ORACLE_ERR_NONFINITE;
+    if (n_threads < 1) n_threads = 1;
+    int32_t *rank = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int64_t *order = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    int64_t **kept = (int64_t **)calloc((size_t)n_r, sizeof(int64_t *));
+    int64_t *K = (int64_t *)malloc(sizeof(int64_t) * (size_t)n_r);
+    int64_t *ng = (int64_t *)malloc(sizeof(int64_t) * (size_t)n_r);
+    int64_t *item0 = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n_r + 1));
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)n_threads);
+    int rc = ORACLE_OK;
+    if (!rank || !order || !kept || !K || !ng || !item0 || !th) {
+        rc = ORACLE_ERR_NOMEM;
+        goto done;
+    }
+    rc = oracle_rank(importance, n, rank);
+    if (rc) goto done;
+    rc = oracle_morton(attrs, n, n_channels, NULL, order);
+    if (rc) goto done;
+    item0[0] = 0;
+    for (int32_t r = 0; r < n_r; r++) {
+        kept[r] = (int64_t *)malloc(sizeof(int64_t) * (size_t)(keep[r] > 0 ? keep[r] : 1));
+        if (!kept[r]) {
+            rc = ORACLE_ERR_NOMEM;
+            goto done;
+        }
+        K[r] = oracle_kept(rank, order, n, keep[r], kept[r]);
+        ng[r] = oracle_n_groups(K[r], G);
+        item0[r + 1] = item0[r] + ng[r] * n_channels;
+    }
+    {
+        oracle_table_job J = {attrs, n_channels, n_b, G, n_r, bits, order, kept, K, ng, item0,
+                              sse, l1, hbits, linf, vmin, vmax, cnt, 0, ORACLE_OK};
+        pthread_mutex_init(&J.mu, NULL);
+        int started = 0;
+        for (; started < n_threads; started++)
+            if (pthread_create(&th[started], NULL, oracle_table_worker, &J) != 0) break;
+        if (started == 0) oracle_table_worker(&J);
+        for (int t = 0; t < started; t++) pthread_join(th[t], NULL);
+        pthread_mutex_destroy(&J.mu);
+        rc = J.rc;
+    }
+done:
+    if (kept)
+        for (int32_t r = 0; r < n_r; r++) free(kept[r]);
+    free(kept);
+    free(rank);
+    free(order);
+    free(K);
+    free(ng);
+    free(item0);
+    free(th);
     return rc;
 }
 

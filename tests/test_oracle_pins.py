@@ -132,6 +132,18 @@ def test_cost_table_items_match_group_cost(oracle_lib):
     assert item == t["cnt"].shape[0]
 
 
+def test_threaded_table_equals_serial(oracle_lib):
+    """The CPU baseline's threaded driver gives the serial table entry for entry."""
+    attrs, imp = _tiny_scene()
+    keep = np.array([30, 150, 300], dtype=np.int64)
+    bits = [1, 3, 8, 16]
+    a = oracle.cost_table(attrs, imp, keep, bits, 16)
+    for threads in (2, 7):
+        b = oracle.cost_table(attrs, imp, keep, bits, 16, threads=threads)
+        for key in a:
+            assert np.array_equal(a[key], b[key]), (threads, key)
+
+
 def test_mckp_dp_equals_bruteforce():
     rng = np.random.default_rng(11)
     for trial in range(25):
