@@ -183,7 +183,64 @@ def measured_peaks() -> dict:
 # ---------------------------------------------------------------------------
 # CPU oracle (baseline and reference arm)
 # ---------------------------------------------------------------------------
-def oracle_sample(n_sample: int, seed: int):
+def cpu_info() -> dict:
+    """Host CPU model and core count (the GPU machine is an Arm Grace host)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Vendor ID") and ":" in line:
+                model = (model + " / " if model else "") + line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return {"cpu_model": model or platform.processor() or platform.machine(), "host_cores": os.cpu_count()}
+
+
+def cpu_baseline(attrs: np.ndarray, imp: np.ndarray) -> dict:
+    """The oracle as it stands: the full scene-scale table on every host core
+    (threaded over its independent items), and a bounded sample on one core."""
+    import oracle
+    w = WORKLOAD
+    cores = os.cpu_count() or 1
+    keep = w.keep()
+    full = os.environ.get("MGS_ORACLE_FULL", "1") != "0"
+    if full:
+        t0 = time.perf_counter()
+        oracle.cost_table(attrs, imp, keep, list(w.bits), w.group_size, threads=cores)
+        dt_all = time.perf_counter() - t0
+        ev_all = evals_of(w)
+        sample_all = (f"the full table of the timed workload ({w.n} Gaussians, 10 ratios x 10 bit-widths), "
+                      f"oracle.cost_table on {cores} threads, {dt_all:.1f} s including its rank and Morton sorts")
+    else:
+        n_s = int(os.environ.get("MGS_ORACLE_SAMPLE_ALL", "1000000"))
+        ev_all, dt_all = oracle_sample(n_s, seed=98, threads=cores)
+        sample_all = f"{n_s} Gaussians of the same distributions and grid on {cores} threads, {dt_all:.1f} s"
+    n_sample = int(os.environ.get("MGS_ORACLE_SAMPLE", "120000"))
+    ev1, dt1 = oracle_sample(n_sample, seed=99)
+    return {"value": ev_all / dt_all, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample_all,
+            "value_1_core": ev1 / dt1,
+            "sample_1_core": f"oracle.cost_table on {n_sample} Gaussians of the same distributions and "
+                             f"grid, {dt1:.1f} s of one core", **cpu_info()}
+
+
+def kernel_counters() -> dict:
+    """ncu figures of the current cost kernel (profiles/k_cost_counters.json): they
+    apply only while the kernel source is the one they were taken from."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "k_cost_counters.json")
+    src = os.path.join(ROOT, "paper_2604_26799_gb300", "csrc", "cost.cu")
+    try:
+        c = json.load(open(path))
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except (OSError, ValueError):
+        return {}
+    if c.get("cost_cu_sha256") != sha:
+        return {"note": "kernel changed since the counters were taken"}
+    return c
+
+
+def oracle_sample(n_sample: int, seed: int, threads: int = 1):
     """The oracle as it stands, on the first-ratio grid of a smaller scene of the
     same distributions (the full scene would take hours of one CPU core)."""
     import oracle
@@ -191,7 +248,7 @@ def oracle_sample(n_sample: int, seed: int):
     attrs, imp = synth.make_scene(n_sample, seed)
     keep = synth.keep_counts(n_sample, list(w.ratios))
     t0 = time.perf_counter()
-    oracle.cost_table(attrs, imp, keep, list(w.bits), w.group_size)
+    oracle.cost_table(attrs, imp, keep, list(w.bits), w.group_size, threads=threads)
     dt = time.perf_counter() - t0
     ev = int(keep.sum()) * N_CH * len(w.bits)
     return ev, dt
@@ -201,22 +258,24 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    n_sample = int(os.environ.get("MGS_ORACLE_SAMPLE", "120000"))
+    n_sample = int(os.environ.get("MGS_ORACLE_SAMPLE", "600000"))
+    cores = os.cpu_count() or 1
     for _ in range(args.warmup if args.warmup < 1 else 1):
-        oracle_sample(20_000, seed=1)
+        oracle_sample(20_000, seed=1, threads=cores)
     total_ev, total_t = 0, 0.0
     for s in range(args.steps):
-        ev, dt = oracle_sample(n_sample, seed=s)
+        ev, dt = oracle_sample(n_sample, seed=s, threads=cores)
         total_ev += ev
         total_t += dt
     value = total_ev / total_t
     sample = (f"{n_sample} Gaussians per step (of {WORKLOAD.n}), same distributions and grid "
-              f"(10 ratios x 10 bit-widths, G={WORKLOAD.group_size}); oracle.cost_table, 1 thread")
+              f"(10 ratios x 10 bit-widths, G={WORKLOAD.group_size}); oracle.cost_table on {cores} threads")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": config_block(args.gpus),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                             **cpu_info()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -410,26 +469,30 @@ def run_gpu(args):
     peaks = measured_peaks()
     k_ms = statistics.mean(kernel_ms)
     k_bytes = algorithmic_bytes(w)
-    hbm_gbs = k_bytes / (k_ms * 1e-3) / 1e9
-    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-    alu_peak = n_sm * LANES_PER_SM_CLK * sm_mhz * 1e6 / 1e12   # T ops/s
-    alu_achieved = evals * ALU_OPS_PER_EVAL / (k_ms * 1e-3) / 1e12
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(prof):
-        try:
-            traffic = json.load(open(prof)).get("k_cost_bytes_per_launch")
-        except (OSError, ValueError):
-            traffic = None
+    roofline, hbm = kernel_rooflines(evals, k_ms, k_bytes, n_sm, peaks)
+    counters = kernel_counters()
+    roofline["traffic"] = counters.get("traffic_bytes_per_launch")
+    roofline["executed_instr_per_eval"] = counters.get("executed_instr_per_eval")
+    roofline["counters_source"] = counters.get("note")
+
+    # the other workloads of the metric, one GPU: the large single scene, the batched
+    # persistent launch and the served job stream
+    workloads = None
+    if rank == 0 and ws == 1 and not args.no_workloads:
+        del table_d
+        torch.cuda.empty_cache()
+        src = SourceScene(torch, dev)
+        workloads = {"large": large_record(torch, mgs, ctx, src, 3, 1),
+                     "batch": batch_record(torch, mgs, ctx, src, 3, 1),
+                     "serve": serve_record(torch, mgs, ctx, src, int(os.environ.get("MGS_SERVE_JOBS", "120")),
+                                           args.slice_items)}
+        del src
+        torch.cuda.empty_cache()
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
-        n_sample = int(os.environ.get("MGS_ORACLE_SAMPLE", "120000"))
-        ev, dt = oracle_sample(n_sample, seed=99)
-        cpu = {"value": ev / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"oracle.cost_table on {n_sample} Gaussians of the same distributions and grid, "
-                         f"{dt:.1f} s of one core"}
+        cpu = cpu_baseline(attrs_h.numpy(), imp_h.numpy())
 
     if rank == 0:
         value = evals * ws / (ms_max * 1e-3)
@@ -438,13 +501,8 @@ def run_gpu(args):
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": config_block(ws),
-            "roofline": {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak, "unit": "Tops/s",
-                         "frac": alu_achieved / alu_peak, "traffic": traffic,
-                         "kernel": "k_cost", "ops_per_eval": ALU_OPS_PER_EVAL,
-                         "peak_source": f"{n_sm} SMs x {LANES_PER_SM_CLK} lanes x {sm_mhz:.0f} MHz"},
-            "hbm": {"achieved": hbm_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": hbm_gbs / peaks["hbm_gbs"], "bytes_per_launch": k_bytes,
-                    "peak_source": peaks["source"]},
+            "roofline": roofline,
+            "hbm": hbm,
             "kernel_ms": k_ms,
             "phase_ms": {k: statistics.mean(v) for k, v in phase.items()},
             "table_evals_per_s": evals / (k_ms * 1e-3),
@@ -464,6 +522,7 @@ def run_gpu(args):
             "autotune": tune,
             "clocks": clocks,
             "cpu_baseline": cpu,
+            "workloads": workloads,
         }
         print(json.dumps(line))
     mgs.mgs_destroy(ctx)
@@ -480,97 +539,142 @@ def _events(torch):
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
 
-def run_batch(args):
+def kernel_rooflines(evals: int, k_ms: float, k_bytes: int, n_sm: int, peaks: dict) -> tuple[dict, dict]:
+    """ALU-issue roofline (the bound of the cost kernel) and the HBM fraction with
+    algorithmic bytes, for a cost-kernel time of k_ms."""
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    alu_peak = n_sm * LANES_PER_SM_CLK * sm_mhz * 1e6 / 1e12   # T ops/s
+    alu = evals * ALU_OPS_PER_EVAL / (k_ms * 1e-3) / 1e12
+    gbs = k_bytes / (k_ms * 1e-3) / 1e9
+    roof = {"bound": "alu", "achieved": alu, "peak": alu_peak, "unit": "Tops/s", "frac": alu / alu_peak,
+            "kernel": "k_cost", "ops_per_eval": ALU_OPS_PER_EVAL,
+            "peak_source": f"{n_sm} SMs x {LANES_PER_SM_CLK} lanes x {sm_mhz:.0f} MHz"}
+    hbm = {"achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
+           "bytes_per_launch": k_bytes, "peak_source": peaks["source"]}
+    return roof, hbm
+
+
+def grid_bytes(keeps, G: int, n_bits: int) -> int:
+    """Algorithmic bytes of a cost launch over kept sets `keeps`: every kept element's
+    59 channels once per ratio (4 B each), plus the table written."""
+    total = 0
+    for keep in keeps:
+        groups = sum((int(k) + G - 1) // G for k in keep)
+        items = groups * N_CH
+        total += int(np.sum(keep)) * N_CH * 4 + items * n_bits * (8 * 3 + 4) + items * 12
+    return total
+
+
+class SourceScene:
+    """One generated 6 M-Gaussian scene (the large workload's) feeding the batched and
+    served workloads too: their scenes are row ranges of it (same distributions), so
+    the default run generates it once."""
+
+    def __init__(self, torch, dev):
+        w = synth.LARGE
+        a, imp = synth.make_scene(w.n, seed=w.seed)
+        self.n = w.n
+        self.h_attrs = torch.from_numpy(a).pin_memory()
+        self.h_imp = torch.from_numpy(imp).pin_memory()
+        self.d_attrs = self.h_attrs.to(dev)
+        self.d_imp = self.h_imp.to(dev)
+        del a, imp
+
+    def rows(self, n: int, i: int, device: bool):
+        """Scene i of size n: a contiguous row range."""
+        off = (i * 1_000_003) % (self.n - n + 1)
+        a, imp = (self.d_attrs, self.d_imp) if device else (self.h_attrs, self.h_imp)
+        return a[off:off + n], imp[off:off + n]
+
+
+def batch_record(torch, mgs, ctx, src: SourceScene, steps: int, warmup: int) -> dict:
     """16 scenes of uneven size (log-uniform 3e5..6e6), 10 ratios x 10 bit-widths, in one
     persistent launch replayed from a CUDA graph; group sizes 1024 / 4096 / 16384, tile
     shape autotuned per group size.  Compared with one launch per scene."""
-    import torch
-    from paper_2604_26799_gb300 import mgs
-    dev = torch.device("cuda", 0)
+    dev = src.d_attrs.device
     sizes = [int(x) for x in synth.batch_sizes(16, 300_000, 6_000_000, seed=3)]
     bits = list(synth.SCENE.bits)
-    ctx = mgs.mgs_create(0)
     st = torch.cuda.Stream(device=dev)
     scenes = []
     for i, n in enumerate(sizes):
-        a, imp = synth.make_scene(n, seed=100 + i)
-        scenes.append(mgs.mgs_scene_create(ctx, torch.from_numpy(a).to(dev), torch.from_numpy(imp).to(dev),
-                                           stream=st))
-        del a, imp
+        a, imp = src.rows(n, i, device=True)
+        scenes.append(mgs.mgs_scene_create(ctx, a, imp, stream=st))
     keeps = [synth.keep_counts(n, list(synth.tenths())) for n in sizes]
     evals = sum(int(k.sum()) for k in keeps) * N_CH * len(bits)
+    peaks = measured_peaks()
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     per_g = {}
-    for G in (1024, 4096, 16384):
-        grids = [mgs.Grid(k, bits, G) for k in keeps]
-        lays = [mgs.mgs_table_layout_for(n, N_CH, g) for n, g in zip(sizes, grids)]
-        tables = [torch.empty(L.total_bytes, dtype=torch.uint8, device=dev) for L in lays]
-        big = int(np.argmax(sizes))
-        chosen, _ = mgs.mgs_autotune(ctx, scenes[big], grids[big], stream=st)
-        with torch.cuda.stream(st):
-            plan = mgs.mgs_plan_create(ctx, scenes, grids, tables, use_graph=True, stream=st)
-            singles = [mgs.mgs_plan_create(ctx, [sc], [g], [t], use_graph=False, stream=st)
-                       for sc, g, t in zip(scenes, grids, tables)]
-            for _ in range(max(1, args.warmup)):
-                mgs.mgs_plan_launch(plan, st)
+    with ClockSampler(dev.index) as clk:
+        for G in (1024, 4096, 16384):
+            grids = [mgs.Grid(k, bits, G) for k in keeps]
+            lays = [mgs.mgs_table_layout_for(n, N_CH, g) for n, g in zip(sizes, grids)]
+            tables = [torch.empty(L.total_bytes, dtype=torch.uint8, device=dev) for L in lays]
+            big = int(np.argmax(sizes))
+            chosen, _ = mgs.mgs_autotune(ctx, scenes[big], grids[big], stream=st)
+            with torch.cuda.stream(st):
+                plan = mgs.mgs_plan_create(ctx, scenes, grids, tables, use_graph=True, stream=st)
+                singles = [mgs.mgs_plan_create(ctx, [sc], [g], [t], use_graph=False, stream=st)
+                           for sc, g, t in zip(scenes, grids, tables)]
+                for _ in range(max(1, warmup)):
+                    mgs.mgs_plan_launch(plan, st)
+                    for p in singles:
+                        mgs.mgs_plan_launch(p, st)
+                a, b = _events(torch)
+                if G == 4096:
+                    clk.mark()
+                a.record(st)
+                for _ in range(steps):
+                    mgs.mgs_plan_launch(plan, st)
+                b.record(st)
+                b.synchronize()
+                if G == 4096:
+                    clk.unmark()
+                batched_ms = a.elapsed_time(b) / steps
+                a.record(st)
+                for _ in range(steps):
+                    for p in singles:
+                        mgs.mgs_plan_launch(p, st)
+                b.record(st)
+                b.synchronize()
+                seq_ms = a.elapsed_time(b) / steps
+                mgs.mgs_plan_destroy(plan)
                 for p in singles:
-                    mgs.mgs_plan_launch(p, st)
-            a, b = _events(torch)
-            a.record(st)
-            for _ in range(args.steps):
-                mgs.mgs_plan_launch(plan, st)
-            b.record(st)
-            b.synchronize()
-            batched_ms = a.elapsed_time(b) / args.steps
-            a.record(st)
-            for _ in range(args.steps):
-                for p in singles:
-                    mgs.mgs_plan_launch(p, st)
-            b.record(st)
-            b.synchronize()
-            seq_ms = a.elapsed_time(b) / args.steps
-            mgs.mgs_plan_destroy(plan)
-            for p in singles:
-                mgs.mgs_plan_destroy(p)
-        per_g[str(G)] = {"tile": mgs.mgs_tile_config_name(chosen), "batched_graph_ms": batched_ms,
-                         "batched_evals_per_s": evals / (batched_ms * 1e-3),
-                         "one_launch_per_scene_ms": seq_ms}
-        del tables
-        torch.cuda.synchronize()
+                    mgs.mgs_plan_destroy(p)
+            roof, hbm = kernel_rooflines(evals, batched_ms, grid_bytes(keeps, G, len(bits)), n_sm, peaks)
+            per_g[str(G)] = {"tile": mgs.mgs_tile_config_name(chosen), "batched_graph_ms": batched_ms,
+                             "batched_evals_per_s": evals / (batched_ms * 1e-3),
+                             "one_launch_per_scene_ms": seq_ms, "roofline": roof, "hbm": hbm}
+            del tables
+            torch.cuda.synchronize()
     for sc in scenes:
         mgs.mgs_scene_destroy(sc)
-    mgs.mgs_destroy(ctx)
-    best = max(per_g.values(), key=lambda x: x["batched_evals_per_s"])
-    print(json.dumps({"metric": METRIC, "value": best["batched_evals_per_s"], "unit": UNIT, "n_gpus": 1,
-                      "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
-                      "dtype": "f32", "data": "synthetic",
-                      "config": {"workload": "batched: 16 scenes, N log-uniform 3e5..6e6 (total %d), "
-                                             "10 ratios x 10 bit-widths, one persistent launch in a CUDA graph"
-                                             % sum(sizes), "sizes": sizes},
-                      "evals_per_pass": evals, "per_group_size": per_g}))
+    best_g = max(per_g, key=lambda g: per_g[g]["batched_evals_per_s"])
+    best = per_g[best_g]
+    return {"metric": METRIC, "value": best["batched_evals_per_s"], "unit": UNIT, "steps": steps,
+            "warmup": warmup, "ms_per_step": best["batched_graph_ms"], "higher_is_better": True,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batched: 16 scenes, N log-uniform 3e5..6e6 (total %d), 10 ratios x "
+                                   "10 bit-widths, one persistent launch in a CUDA graph, G swept "
+                                   "1024/4096/16384 (best reported)" % sum(sizes), "sizes": sizes,
+                       "best_group_size": int(best_g)},
+            "evals_per_pass": evals, "roofline": best["roofline"], "hbm": best["hbm"],
+            "per_group_size": per_g, "clocks": clk.summary()}
 
 
-def run_serve(args):
+def serve_record(torch, mgs, ctx, src: SourceScene, n_jobs: int, slice_items: int) -> dict:
     """Poisson job stream (20 jobs/s; N log-uniform 1e5..6e6; budget U[5, 60] MB; each a
     10 x 10 search) through the continuous-batching server; p50/p99 time from submission to
     the ILP answer.  Compared with a one-job-at-a-time plain per-(ratio, bit-width) loop fed
     the same arrivals (its service times measured per scene)."""
-    import torch
-    from paper_2604_26799_gb300 import mgs
-    dev = torch.device("cuda", 0)
-    n_jobs = int(os.environ.get("MGS_SERVE_JOBS", "120"))
+    dev = src.d_attrs.device
     t_arr, job_sizes, budgets = synth.poisson_arrivals(n_jobs, 20.0, seed=7)
     # a pool of resident host scenes; job j uses the pool scene closest to its drawn size
     pool_n = sorted({int(x) for x in np.quantile(job_sizes, np.linspace(0, 1, 12))})
-    pool = []
-    for i, n in enumerate(pool_n):
-        a, imp = synth.make_scene(n, seed=200 + i)
-        pool.append((torch.from_numpy(a).pin_memory(), torch.from_numpy(imp).pin_memory(), n))
-        del a, imp
+    pool = [(*src.rows(n, i, device=False), n) for i, n in enumerate(pool_n)]
     pick = [int(np.argmin([abs(np.log(p[2]) - np.log(n)) for p in pool])) for n in job_sizes]
     bits = list(synth.SCENE.bits)
     grids = [mgs.Grid(synth.keep_counts(p[2], list(synth.tenths())), bits, 4096) for p in pool]
     opts = mgs.solve_opts()
-    ctx = mgs.mgs_create(0)
     # warm-up: one job per pool scene (also the plain loop's service time per scene)
     plain_service = []
     st = torch.cuda.Stream(device=dev)
@@ -584,19 +688,22 @@ def run_serve(args):
         mgs.mgs_scene_destroy(sc)
         plain_service.append(time.perf_counter() - t0)
     srv = mgs.mgs_server_create(ctx, max_jobs=8, solver_threads=8, hbm_budget_bytes=120 << 30,
-                                slice_items=args.slice_items)
-    ids, sub_wall = [], []
-    t_start = time.perf_counter()
-    for j in range(n_jobs):
-        now = time.perf_counter() - t_start
-        if t_arr[j] > now:
-            time.sleep(t_arr[j] - now)
-        a, imp, n = pool[pick[j]]
-        ids.append(mgs.mgs_server_submit(srv, a, imp, grids[pick[j]], float(budgets[j]), opts))
-    res = [mgs.mgs_server_wait(srv, i, timeout_ms=600_000) for i in ids]
+                                slice_items=slice_items)
+    ids = []
+    with ClockSampler(dev.index) as clk:
+        time.sleep(0.3)   # nvidia-smi starts
+        clk.mark()
+        t_start = time.perf_counter()
+        for j in range(n_jobs):
+            now = time.perf_counter() - t_start
+            if t_arr[j] > now:
+                time.sleep(t_arr[j] - now)
+            a, imp, n = pool[pick[j]]
+            ids.append(mgs.mgs_server_submit(srv, a, imp, grids[pick[j]], float(budgets[j]), opts))
+        res = [mgs.mgs_server_wait(srv, i, timeout_ms=600_000) for i in ids]
+        clk.unmark()
     stats = mgs.mgs_server_stats(srv)
     mgs.mgs_server_destroy(srv)
-    mgs.mgs_destroy(ctx)
     lat = np.array([r["t_done"] - r["t_submit"] for r in res])
     # where the latency goes: waiting for admission, ingest, compute, solve
     stages = {}
@@ -618,32 +725,33 @@ def run_serve(args):
         finish = start + plain_service[pick[j]]
         plain_lat.append(finish - t_arr[j])
     plain_lat = np.array(plain_lat)
-    evals = sum(int(synth.keep_counts(pool[pick[j]][2], list(synth.tenths())).sum()) for j in range(n_jobs)) \
-        * N_CH * len(bits)
-    print(json.dumps({
+    keeps = [synth.keep_counts(pool[pick[j]][2], list(synth.tenths())) for j in range(n_jobs)]
+    evals = sum(int(k.sum()) for k in keeps) * N_CH * len(bits)
+    peaks = measured_peaks()
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    # whole-job figures over the served span: the arrival rate, not the GPU, sets it
+    roof, hbm = kernel_rooflines(evals, span * 1e3, grid_bytes(keeps, 4096, len(bits)), n_sm, peaks)
+    roof["bound"] = "arrival rate (20 jobs/s): whole-job evals over the served span"
+    return {
         "metric": "served search latency (submission to ILP answer)", "unit": "s",
         "value": float(np.percentile(lat, 50)), "p50_s": float(np.percentile(lat, 50)),
         "p99_s": float(np.percentile(lat, 99)), "jobs_per_s": n_jobs / span, "jobs_ok": ok,
         "jobs": n_jobs, "evals_per_s": evals / span, "higher_is_better": False,
         "plain_loop_p50_s": float(np.percentile(plain_lat, 50)),
         "plain_loop_p99_s": float(np.percentile(plain_lat, 99)),
-        "server": stats, "stages": stages, "data": "synthetic",
+        "server": stats, "stages": stages, "data": "synthetic", "roofline": roof, "hbm": hbm,
+        "clocks": clk.summary(),
         "config": {"workload": "serving: Poisson 20 jobs/s, N log-uniform 1e5..6e6 (12-scene pool), "
                                "budget U[5,60] MB, 10 ratios x 10 bit-widths, G 4096",
-                   "pool_sizes": pool_n, "slice_items": args.slice_items}}))
+                   "pool_sizes": pool_n, "slice_items": slice_items}}
 
 
-def run_large(args):
+def large_record(torch, mgs, ctx, src: SourceScene, steps: int, warmup: int) -> dict:
     """6 M Gaussians, 20 ratios (0.05..1.00), bit-widths 1..16, groups of 2048; ILP at 8 budgets."""
-    import torch
-    from paper_2604_26799_gb300 import mgs
-    dev = torch.device("cuda", 0)
+    dev = src.d_attrs.device
     w = synth.LARGE
-    a, imp = synth.make_scene(w.n, seed=w.seed)
-    a_d, i_d = torch.from_numpy(a).to(dev), torch.from_numpy(imp).to(dev)
-    del a
+    a_d, i_d = src.d_attrs, src.d_imp
     grid = mgs.Grid(w.keep(), list(w.bits), w.group_size)
-    ctx = mgs.mgs_create(0)
     st = torch.cuda.Stream(device=dev)
     L = mgs.mgs_table_layout_for(w.n, N_CH, grid)
     tab = torch.empty(L.total_bytes, dtype=torch.uint8, device=dev)
@@ -654,42 +762,78 @@ def run_large(args):
     phase = {"scene": [], "kernel": [], "solve_8_budgets": []}
     evals = int(w.keep().sum()) * N_CH * len(w.bits)
     total = 0.0
-    for step in range(args.warmup + args.steps):
-        with torch.cuda.stream(st):
-            e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-            e[0].record(st)
-            sc = mgs.mgs_scene_create(ctx, a_d, i_d, stream=st)
-            plan = mgs.mgs_plan_create(ctx, [sc], grid, [tab], stream=st)
-            e[1].record(st)
-            mgs.mgs_plan_launch(plan, st)
-            e[2].record(st)
-            sols = mgs.mgs_solve_budgets_device(ctx, tab, L, grid, budgets, mgs.solve_opts(), stream=st)
-            e[3].record(st)
-            mgs.mgs_plan_destroy(plan)
-            mgs.mgs_scene_destroy(sc)
-        e[3].synchronize()
-        if step >= args.warmup:
-            phase["scene"].append(e[0].elapsed_time(e[1]))
-            phase["kernel"].append(e[1].elapsed_time(e[2]))
-            phase["solve_8_budgets"].append(e[2].elapsed_time(e[3]))
-            total += e[0].elapsed_time(e[3])
+    with ClockSampler(dev.index) as clk:
+        for step in range(warmup + steps):
+            if step == warmup:
+                clk.mark()
+            with torch.cuda.stream(st):
+                e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+                e[0].record(st)
+                sc = mgs.mgs_scene_create(ctx, a_d, i_d, stream=st)
+                plan = mgs.mgs_plan_create(ctx, [sc], grid, [tab], stream=st)
+                e[1].record(st)
+                mgs.mgs_plan_launch(plan, st)
+                e[2].record(st)
+                sols = mgs.mgs_solve_budgets_device(ctx, tab, L, grid, budgets, mgs.solve_opts(), stream=st)
+                e[3].record(st)
+                mgs.mgs_plan_destroy(plan)
+                mgs.mgs_scene_destroy(sc)
+            e[3].synchronize()
+            if step >= warmup:
+                phase["scene"].append(e[0].elapsed_time(e[1]))
+                phase["kernel"].append(e[1].elapsed_time(e[2]))
+                phase["solve_8_budgets"].append(e[2].elapsed_time(e[3]))
+                total += e[0].elapsed_time(e[3])
+        clk.unmark()
     # the host solver on the same table, for comparison
     tab_np = tab.cpu().numpy()
     t0 = time.perf_counter()
     host = mgs.mgs_solve_budgets(tab_np, L, grid, budgets, mgs.solve_opts())
     host_ms = 1000 * (time.perf_counter() - t0)
     same = all(a["r_index"] == b["r_index"] and a["objective"] == b["objective"] for a, b in zip(sols, host))
+    ms = total / steps
+    k_ms = statistics.mean(phase["kernel"])
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    roof, hbm = kernel_rooflines(evals, k_ms, grid_bytes([w.keep()], w.group_size, len(w.bits)), n_sm,
+                                 measured_peaks())
+    return {"metric": METRIC, "value": evals / (ms * 1e-3), "unit": UNIT, "steps": steps, "warmup": warmup,
+            "ms_per_step": ms, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name}, "tile": mgs.mgs_tile_config_name(chosen),
+            "kernel_evals_per_s": evals / (k_ms * 1e-3), "roofline": roof, "hbm": hbm,
+            "phase_ms": {k: statistics.mean(v) for k, v in phase.items()},
+            "host_solve_8_budgets_ms": host_ms, "device_solve_equals_host": same, "clocks": clk.summary(),
+            "solutions": [{"budget": b, "r_index": s["r_index"], "est_bytes": s["est_bytes"]}
+                          for b, s in zip(budgets, sols)]}
+
+
+def _one_record(args, which: str):
+    import torch
+    from paper_2604_26799_gb300 import mgs
+    dev = torch.device("cuda", 0)
+    ctx = mgs.mgs_create(0)
+    src = SourceScene(torch, dev)
+    if which == "batch":
+        rec = batch_record(torch, mgs, ctx, src, args.steps, args.warmup)
+    elif which == "serve":
+        rec = serve_record(torch, mgs, ctx, src, int(os.environ.get("MGS_SERVE_JOBS", "120")), args.slice_items)
+    else:
+        rec = large_record(torch, mgs, ctx, src, args.steps, args.warmup)
     mgs.mgs_destroy(ctx)
-    ms = total / args.steps
-    print(json.dumps({"metric": METRIC, "value": evals / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
-                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-                      "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-                      "config": {"workload": w.name}, "tile": mgs.mgs_tile_config_name(chosen),
-                      "kernel_evals_per_s": evals / (statistics.mean(phase["kernel"]) * 1e-3),
-                      "phase_ms": {k: statistics.mean(v) for k, v in phase.items()},
-                      "host_solve_8_budgets_ms": host_ms, "device_solve_equals_host": same,
-                      "solutions": [{"budget": b, "r_index": s["r_index"], "est_bytes": s["est_bytes"]}
-                                    for b, s in zip(budgets, sols)]}))
+    rec["n_gpus"] = 1
+    print(json.dumps(rec))
+    return 0
+
+
+def run_batch(args):
+    return _one_record(args, "batch")
+
+
+def run_serve(args):
+    return _one_record(args, "serve")
+
+
+def run_large(args):
+    return _one_record(args, "large")
 
 
 def run_preprocess(args):
@@ -1121,6 +1265,8 @@ def main():
                     help="serve: cost-table work items per batched launch")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-loop comparator")
     ap.add_argument("--no-autotune", action="store_true", help="use the default tile shape")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the large, batched and served sub-records of the default run")
     ap.add_argument("--n", type=int, default=None,
                     help="scene size override (smaller cases for profiling; default 5,270,000)")
     args = ap.parse_args()

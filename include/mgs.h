@@ -170,6 +170,20 @@ const char *mgs_version(void);
  * (a CUDA-graph replay counts the kernels it runs). */
 int64_t mgs_kernel_launches(void);
 
+/*
+ * Failure injection for tests of error handling (no counterpart in the
+ * paper).  After mgs_debug_fail_allocation(nth), the nth stream-ordered device
+ * allocation the library makes from then on (1 = the next one; scenes, their
+ * staging and sort scratch, kept lists, cost tables, launch scratch, solver
+ * workspaces, served jobs' tables) fails as if the device were out of memory:
+ * nothing is allocated and the call that needed it returns its usual error
+ * (MGS_ERR_OUT_OF_MEMORY or MGS_ERR_CUDA) after releasing what it holds.
+ * nth = 0 disarms.  Process-wide, for every context and thread.
+ * mgs_debug_allocations returns how many such allocations have been made.
+ */
+mgs_status mgs_debug_fail_allocation(int64_t nth);
+int64_t mgs_debug_allocations(void);
+
 /* ---- scenes ----------------------------------------------------------- */
 
 /*
@@ -284,6 +298,26 @@ mgs_status mgs_build_cost_table_plain(mgs_ctx *ctx, const mgs_scene *scene, cons
                                       void *table, void *stream);
 
 /*
+ * The same table as mgs_build_cost_table, from the same fused kernel, which
+ * also writes out what it counted (Sec. III-D codes; the histograms behind the
+ * Sec. III-F entropy bound) so that they can be checked or inspected:
+ *   hist  (device, or NULL): uint32 [n_items][sum_k 2^bits[k]]; row `item`
+ *         (table order [r][c][g]) holds option k's 2^bits[k] bin counts at
+ *         offset sum_{j<k} 2^bits[j]; every bin is written (zeros included).
+ *   codes (device, or NULL): uint16; ratio r's block starts at
+ *         sum_{r'<r} n_channels * n_bits * keep[r'] and holds
+ *         [n_channels][n_bits][keep[r]] codes, group g of a channel at
+ *         elements [g * G, g * G + n_g) in the group's (Morton) order.
+ * hist_capacity / codes_capacity are the entries available; a smaller
+ * buffer is MGS_ERR_INVALID_ARG.  Runs the default tile of the group size
+ * (group sizes above 16384 are not supported).  Meant for test-sized scenes:
+ * the histogram array grows with 2^16 per item at b = 16.
+ */
+mgs_status mgs_build_cost_table_probe(mgs_ctx *ctx, const mgs_scene *scene, const mgs_grid *grid,
+                                      void *table, uint32_t *hist, int64_t hist_capacity,
+                                      uint16_t *codes, int64_t codes_capacity, void *stream);
+
+/*
  * The cost table of an arbitrary coefficient array -- e.g. the RAHT AC
  * coefficients of mgs_raht (Sec. III-D: after RAHT the AC coefficients are
  * the quantised signal) -- with the same quantiser, errors and entropy bound
@@ -376,8 +410,11 @@ mgs_status mgs_quantize_groups(mgs_ctx *ctx, const mgs_scene *scene, int64_t kee
  * holds until the process exits: at most MGS_NOALLOC_MAX_KEEP kept Gaussians
  * (16 MiB of indices) of a scene of at most MGS_NOALLOC_MAX_SCENE Gaussians;
  * larger requests return MGS_ERR_INVALID_ARG.  The first call on a device looks
- * up the arrays' device addresses (cudaGetSymbolAddress, once per device); make
- * that first call before any stream capture.  Every call shares the arrays and
+ * up the arrays' device addresses (cudaGetSymbolAddress, once per device), and
+ * with lazy module loading that lookup may load the library's device code and
+ * block; make that first call during set-up, before any stream capture and
+ * before entering a thread that must not block.  Later calls do not look up
+ * anything.  Every call shares the arrays and
  * they keep the last call's contents (nothing in them needs clearing): calls
  * that overlap on the GPU (different streams, or different host threads with
  * no ordering between them) race on the scratch and must be serialised.
@@ -543,6 +580,15 @@ mgs_status mgs_vq_train(mgs_ctx *ctx, const float *x, int64_t n, int32_t D, floa
  */
 mgs_status mgs_vq_set_tensor_cores(mgs_ctx *ctx, int32_t enable);
 mgs_status mgs_vq_stats(mgs_ctx *ctx, int64_t *scores, int64_t *rescored);
+/*
+ * Clock-cycle limit of each bounded wait of the tensor-core pipeline (a copy
+ * or an MMA that has not completed by then is a failure: the CTA drains its
+ * own copies and MMAs, frees its tensor memory, and the call returns
+ * MGS_ERR_TIMEOUT).  0 restores the default, about one second.  No
+ * counterpart in the paper: failure detection, and tests of it (a limit of a
+ * few cycles makes the waits run out without any fault).
+ */
+mgs_status mgs_vq_set_wait_limit(mgs_ctx *ctx, int64_t cycles);
 
 /*
  * Budget-first retention: the vectors of rows[0 .. n_retain) (the top-ranked
@@ -589,6 +635,10 @@ typedef struct {
     mgs_grid grid;             /* copied at submission */
     double budget_bytes;
     mgs_solve_opts opts;
+    void *table_out;           /* optional host buffer of mgs_table_layout_for(n, n_channels,
+                                  grid).total_bytes bytes: when non-NULL the job's finished cost
+                                  table is copied there before the solve (to check it, or to
+                                  solve other budgets later); valid until the job is done */
 } mgs_job;
 
 typedef struct {

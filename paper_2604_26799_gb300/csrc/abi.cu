@@ -15,8 +15,25 @@ namespace mgs {
 
 static thread_local char g_err[1024];
 static std::atomic<int64_t> g_launches{0};
+static std::atomic<int64_t> g_allocs{0};          // dev_malloc_async calls so far
+static std::atomic<int64_t> g_fail_alloc_in{0};   // > 0: that many calls from now, the last one fails
 
 void count_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+cudaError_t dev_malloc_async(void **p, size_t bytes, cudaStream_t st) {
+    g_allocs.fetch_add(1, std::memory_order_relaxed);
+    int64_t c = g_fail_alloc_in.load();
+    while (c > 0) {
+        if (g_fail_alloc_in.compare_exchange_weak(c, c - 1)) {
+            if (c == 1) {
+                *p = nullptr;
+                return cudaErrorMemoryAllocation;   // injected: nothing is allocated
+            }
+            break;
+        }
+    }
+    return cudaMallocAsync(p, bytes, st);
+}
 
 void set_error(const char *fmt, ...) {
     va_list ap;
@@ -128,7 +145,7 @@ mgs_status run_cost(mgs_ctx *ctx, CostLaunch &launch, cudaStream_t st) {
     unsigned int *d_counter = nullptr;
     size_t seg_bytes = align256(sizeof(CostSeg) * std::max<size_t>(launch.segs.size(), 1));
     void *scratch = nullptr;
-    MGS_CUDA_TRY(cudaMallocAsync(&scratch, seg_bytes + 256, st));
+    MGS_CUDA_TRY(dev_malloc_async(&scratch, seg_bytes + 256, st));
     d_segs = static_cast<CostSeg *>(scratch);
     d_counter = reinterpret_cast<unsigned int *>(static_cast<char *>(scratch) + seg_bytes);
     mgs_status s = cost_launch(ctx, launch, cfg, d_segs, d_counter, st);
@@ -207,7 +224,7 @@ template <typename F>
 mgs_status with_device_table(void *table, size_t bytes, cudaStream_t st, F fn) {
     if (is_device_pointer(table)) return fn(table);
     void *d = nullptr;
-    MGS_CUDA_TRY(cudaMallocAsync(&d, bytes, st));
+    MGS_CUDA_TRY(dev_malloc_async(&d, bytes, st));
     mgs_status s = fn(d);
     if (s == MGS_OK) {
         cudaError_t e = cudaMemcpyAsync(table, d, bytes, cudaMemcpyDeviceToHost, st);
@@ -231,6 +248,18 @@ extern "C" {
 const char *mgs_last_error(void) { return g_err; }
 const char *mgs_version(void) { return "mgs 0.1 (sm_103a)"; }
 int64_t mgs_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+mgs_status mgs_debug_fail_allocation(int64_t nth) {
+    clear_error();
+    if (nth < 0) {
+        set_error("nth = %lld must be >= 0", (long long)nth);
+        return MGS_ERR_INVALID_ARG;
+    }
+    g_fail_alloc_in.store(nth);
+    return MGS_OK;
+}
+
+int64_t mgs_debug_allocations(void) { return g_allocs.load(std::memory_order_relaxed); }
 
 mgs_status mgs_create(int32_t device, mgs_ctx **out) {
     clear_error();
@@ -320,7 +349,7 @@ mgs_status mgs_scene_create(mgs_ctx *ctx, const float *attrs, const float *impor
     bool host_a = !is_device_pointer(attrs), host_i = !is_device_pointer(importance);
     if (host_a || host_i) {
         size_t bytes = align256(host_a ? abytes : 0) + (host_i ? ibytes : 0);
-        if (cudaMallocAsync((void **)&stage, bytes, st) != cudaSuccess) {
+        if (dev_malloc_async((void **)&stage, bytes, st) != cudaSuccess) {
             cudaGetLastError();
             set_error("staging allocation of %zu bytes failed", bytes);
             return MGS_ERR_OUT_OF_MEMORY;
@@ -341,11 +370,10 @@ mgs_status mgs_scene_create(mgs_ctx *ctx, const float *attrs, const float *impor
     mgs_status s = scene_build(ctx, d_attrs, d_imp, n, n_channels, st, sc);
     if (stage) cudaFreeAsync(stage, st);
     if (s != MGS_OK) {
-        cudaFreeAsync(sc->d_slabs, st);
-        cudaFreeAsync(sc->d_rank_m, st);
-        cudaFreeAsync(sc->d_order, st);
-        cudaFreeAsync(sc->d_codes, st);
+        for (void *p : {(void *)sc->d_slabs, (void *)sc->d_rank_m, (void *)sc->d_order, (void *)sc->d_codes})
+            if (p) cudaFreeAsync(p, st);
         cudaStreamSynchronize(st);
+        cudaGetLastError();
         delete sc;
         return s;
     }
@@ -496,6 +524,65 @@ mgs_status mgs_build_cost_table(mgs_ctx *ctx, const mgs_scene *scene, const mgs_
 mgs_status mgs_build_cost_table_plain(mgs_ctx *ctx, const mgs_scene *scene, const mgs_grid *grid,
                                       void *table, void *stream) {
     return build_table(ctx, scene, grid, table, stream, true);
+}
+
+mgs_status mgs_build_cost_table_probe(mgs_ctx *ctx, const mgs_scene *scene, const mgs_grid *grid,
+                                      void *table, uint32_t *hist, int64_t hist_capacity,
+                                      uint16_t *codes, int64_t codes_capacity, void *stream) {
+    clear_error();
+    if (!ctx || !scene || !table) {
+        set_error("ctx, scene and table must be non-NULL");
+        return MGS_ERR_INVALID_ARG;
+    }
+    mgs_scene *sc = const_cast<mgs_scene *>(scene);
+    mgs_table_layout L;
+    MGS_TRY(mgs_table_layout_for(sc->n, sc->C, grid, &L));
+    int64_t bins = 0, ncodes = 0;
+    for (int k = 0; k < grid->n_bits; k++) bins += (int64_t)1 << grid->bits[k];
+    for (int r = 0; r < grid->n_ratios; r++) ncodes += (int64_t)sc->C * grid->n_bits * grid->keep[r];
+    if (hist && (hist_capacity < L.n_items * bins || !is_device_pointer(hist))) {
+        set_error("hist must be device memory of at least %lld entries",
+                  (long long)(L.n_items * bins));
+        return MGS_ERR_INVALID_ARG;
+    }
+    if (codes && (codes_capacity < ncodes || !is_device_pointer(codes))) {
+        set_error("codes must be device memory of at least %lld entries", (long long)ncodes);
+        return MGS_ERR_INVALID_ARG;
+    }
+    const int cfg = cost_default_config(grid->group_size);
+    if (!cost_config_has_probe(cfg)) {
+        set_error("no probe kernel for group size %d", grid->group_size);
+        return MGS_ERR_INVALID_ARG;
+    }
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return with_device_table(table, (size_t)L.total_bytes, st, [&](void *dt) -> mgs_status {
+        std::vector<CostSeg> segs;
+        MGS_TRY(scene_segments(sc, grid, dt, st, &segs));
+        int64_t off = 0;
+        for (int r = 0; r < grid->n_ratios; r++) {
+            segs[r].code_off = off;
+            off += (int64_t)sc->C * grid->n_bits * grid->keep[r];
+        }
+        CostLaunch launch;
+        launch.group_size = grid->group_size;
+        launch.n_bits = grid->n_bits;
+        for (int k = 0; k < grid->n_bits; k++) launch.bits[k] = grid->bits[k];
+        launch.segs = segs;
+        launch.opt_lo = 0;
+        launch.opt_hi = grid->n_bits;
+        launch.probe_hist = hist;
+        launch.probe_codes = codes;
+        CostSeg *d_segs = nullptr;
+        size_t seg_bytes = align256(sizeof(CostSeg) * std::max<size_t>(launch.segs.size(), 1));
+        void *scratch = nullptr;
+        MGS_CUDA_TRY(dev_malloc_async(&scratch, seg_bytes + 256, st));
+        d_segs = static_cast<CostSeg *>(scratch);
+        unsigned int *d_counter = reinterpret_cast<unsigned int *>(static_cast<char *>(scratch) + seg_bytes);
+        mgs_status s = cost_launch(ctx, launch, cfg, d_segs, d_counter, st);
+        cudaFreeAsync(scratch, st);
+        return s;
+    });
 }
 
 mgs_status mgs_build_cost_table_coeffs(mgs_ctx *ctx, const float *coeffs, int64_t m, int32_t n_channels,
@@ -668,12 +755,12 @@ mgs_status mgs_autotune(mgs_ctx *ctx, const mgs_scene *scene, const mgs_grid *gr
     DeviceGuard g(ctx->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     void *table = nullptr, *scratch = nullptr;
-    MGS_CUDA_TRY(cudaMallocAsync(&table, (size_t)L.total_bytes, st));
+    MGS_CUDA_TRY(dev_malloc_async(&table, (size_t)L.total_bytes, st));
     std::vector<CostSeg> segs;
     mgs_status s = scene_segments(sc, grid, table, st, &segs);
     const int nc = cost_config_count();
     size_t seg_bytes = align256(sizeof(CostSeg) * std::max<size_t>(segs.size(), 1));
-    if (s == MGS_OK && cudaMallocAsync(&scratch, seg_bytes + 256, st) != cudaSuccess) {
+    if (s == MGS_OK && dev_malloc_async(&scratch, seg_bytes + 256, st) != cudaSuccess) {
         set_error("autotune scratch allocation failed");
         s = MGS_ERR_OUT_OF_MEMORY;
     }

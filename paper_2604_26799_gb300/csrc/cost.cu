@@ -4,7 +4,8 @@
 // One work item = (segment = (scene, ratio), group g, chunk of W channels).
 // The CTA gathers the group's rows through the kept list once (W channels of
 // each 32-byte slab row, vector loads) into registers, reduces min/max, and
-// then evaluates every bit-width from those registers:
+// then evaluates every bit-width of one channel after the other from those
+// registers:
 //
 //   S = fl(R / 2^b), Z = rint(fl(2^b - fl(M / S))), R = fl(M - m)
 //   x = fl(fl(c / S) + Z),  q = rint(min(max(x, 0), 2^b - 1))
@@ -21,23 +22,28 @@
 //    when |Z| < 2^22 (the second operand is then an exact integer).
 //  * x is monotone in c, so if the group minimum does not round below 0 no
 //    element does, and the lower clamp is skipped.
-//  * Packed f32x2 adds, subtracts and FMAs are used where no contraction can
-//    arise; the reconstruction product stays a scalar multiply.
 //  * Each channel is scaled by an exact power of two 2^k (R * 2^k in [1, 2)):
 //    c' = c 2^k, S' = S 2^k give c'/S' = c/S and e' = e 2^k exactly, so squares
 //    and sums stay in the normal FP32 range; the sums are rescaled in FP64.
 // Groups where a precondition fails (subnormal S or u, |Z| >= 2^22) take the
-// literal per-element formula.  Pairs of elements use packed f32x2 arithmetic.
+// literal per-element formula.
 //
-// Histograms live in shared memory, in two buffers that consecutive
-// bit-widths alternate between, so one barrier per bit-width suffices:
-// per-lane columns for b <= 6 and a direct table for b <= 10 (summed after the
-// pass); for larger b the atomic returns the old count j - 1 and the thread
-// adds delta(j) = L(j) - L(j - 1), L(h) = h log2 h in units of 2^-22 bits, so
-// sum_j delta telescopes to sum_bins L(h) with no scan (direct 32-bit counters
-// or 16-bit counter pairs; a table larger than the big buffer is counted in
-// windows, one pass over the elements per window).  Entropy sums are
-// integers, so they do not depend on the reduction order.
+// Histograms live in shared memory.  The bit-widths up to 12 of a channel are
+// counted together, each in its own table of region A, with no barrier between
+// them: per-lane columns for b <= 6 (a warp never hits one address twice) and a
+// direct table for b <= 10 (both summed by a scan once every count is in), and
+// 16-bit counter pairs for b = 11, 12, where the atomic returns the bin's old
+// count h - 1 and the thread adds delta(h) = L(h) - L(h - 1), L(h) = h log2 h in
+// units of 2^-22 bits, so the deltas telescope to sum_bins L(h) with no scan.
+// Larger bit-widths are counted one at a time in region B with 8-bit counters
+// (a quarter of the 16-bit table: b = 16 fits 64 KB), the same telescoping sum
+// and a shared-memory delta table.  A counter that reaches 255 sets an overflow
+// flag, and the bit-width is then counted again exactly with 16-bit pairs (in
+// windows of region B).  Entropy sums are integers, so they do not depend on
+// the order of the updates.
+//
+// A probe instantiation of the kernel also writes every code and every bin of
+// every histogram to caller memory (test and inspection only).
 
 #include <cuda_runtime.h>
 
@@ -51,26 +57,19 @@ namespace {
 
 constexpr uint32_t kFull = 0xFFFFFFFFu;
 constexpr float kMagic = 12582912.0f;          // 1.5 * 2^23
-constexpr uint32_t kMagicBits = 0x4B400000u;   // its bit pattern
+constexpr uint32_t kMagicBits = 0x4B400000u;   // its bit pattern (a multiple of 4)
 constexpr int kLaneMaxBits = 6;
 constexpr int kDirectMaxBits = 10;
+constexpr int kPairMaxBits = 12;
+constexpr int kByteDelta = 260;                // delta(h), h = 0..256, in shared memory (+ pad)
 
-enum HistMode { kLane = 0, kDirect = 1, kDelta32 = 2, kDelta16 = 3 };
+enum HistMode { kLane = 0, kDirect = 1, kPair = 2, kByte = 3 };
 enum Path { kFast = 0, kFastBottom = 1, kGeneric = 2, kDegenerate = 3 };
 
-struct BitParam {
-    float S, Ss, Z, twob;
-    float MZ;     // 1.5 * 2^23 + Z (exact when |Z| < 2^22)
-    float ytop;   // 1.5 * 2^23 + 2^b - 1
-    float top;    // 2^b - 1
-    int b;
-    int mode;
-    int path;
-    int buf;      // histogram buffer: 0, 1 (second small buffer) or 2 (big buffer)
-    int sync;     // 1: barrier before the pass (the previous option used the same buffer)
-    int windows;  // passes over the elements (16-bit pairs larger than the big buffer)
-    int wwords;   // words counted per pass (16-bit-pair mode)
-    int pad[2];
+struct __align__(16) BitParam {
+    float twob, Z, ytop, Ss;   // 2^b, Z, 1.5 * 2^23 + 2^b - 1, S * 2^k
+    float MZ, top;             // 1.5 * 2^23 + Z (exact when |Z| < 2^22), 2^b - 1
+    int path, b;
 };
 
 struct KernelArgs {
@@ -84,14 +83,19 @@ struct KernelArgs {
     const unsigned long long *ltab;   // L(h) in 2^-22 bits
     const uint32_t *dtab;             // L(h) - L(h - 1) in 2^-22 bits (< 2^26)
     unsigned int *counter;
-    int32_t hist_words;               // words per small histogram buffer (power of two)
-    int32_t n_small;                  // small buffers (1 or 2)
-    int32_t big_words;                // words of the big buffer (0: none)
-    // per option (index k = option - opt_lo), fixed for the launch: histogram mode,
-    // buffer (0, 1: small; 2: big), barrier before the pass, windows, words per window
-    int8_t opt_mode[MGS_MAX_OPTIONS], opt_buf[MGS_MAX_OPTIONS], opt_sync[MGS_MAX_OPTIONS];
-    int8_t opt_windows[MGS_MAX_OPTIONS];
-    int32_t opt_wwords[MGS_MAX_OPTIONS];
+    // histogram plan (index k = option - opt_lo), fixed for the launch
+    int32_t n_small;                  // options [0, n_small) share region A
+    int32_t a_words, b_words;         // region sizes in 32-bit words
+    int8_t opt_mode[MGS_MAX_OPTIONS];
+    int8_t opt_windows[MGS_MAX_OPTIONS];    // byte-counter passes of a large option
+    int8_t opt_rwindows[MGS_MAX_OPTIONS];   // 16-bit-pair passes of its exact recount
+    int32_t opt_off[MGS_MAX_OPTIONS];       // word offset of a small option's table in region A
+    int32_t opt_words[MGS_MAX_OPTIONS];     // words of one pass's table
+    // probe outputs (probe instantiation only)
+    uint32_t *hist_out;               // [item][hist_stride]: every bin of every option
+    uint16_t *codes_out;              // per segment at seg.code_off: [C][n_bits][K]
+    int64_t hist_stride;
+    int64_t hist_off[MGS_MAX_OPTIONS];  // bin offset of option j (global index) in an item's row
 };
 
 // ---- packed FP32 pairs ----------------------------------------------------
@@ -155,6 +159,19 @@ __device__ __forceinline__ uint32_t ld_keep(const uint32_t *p) {
 }
 
 // ---- shared-memory histogram operations ------------------------------------
+// Predicated forms execute only where `pred` holds (predicated, not branched:
+// lanes taking different sides do not split the warp); atom_if returns 0 elsewhere.
+__device__ __forceinline__ void red_if(bool pred, uint32_t addr, uint32_t v) {
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q red.shared.add.u32 [%0], %1;\n\t}"
+                 ::"r"(addr), "r"(v), "r"((uint32_t)pred));
+}
+__device__ __forceinline__ uint32_t atom_if(bool pred, uint32_t addr, uint32_t v) {
+    uint32_t old = 0;
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %3, 0;\n\t@q atom.shared.add.u32 %0, [%1], %2;\n\t}"
+                 : "+r"(old)
+                 : "r"(addr), "r"(v), "r"((uint32_t)pred));
+    return old;
+}
 __device__ __forceinline__ void red_add(uint32_t addr, uint32_t v) {
     asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(v));
 }
@@ -163,222 +180,184 @@ __device__ __forceinline__ uint32_t atom_add(uint32_t addr, uint32_t v) {
     asm volatile("atom.shared.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(addr), "r"(v));
     return old;
 }
-// The same, executed only where `pred` holds (predicated, not branched: lanes
-// of a warp taking different sides do not split the warp); 0 elsewhere.
-__device__ __forceinline__ uint32_t atom_add_if(bool pred, uint32_t addr, uint32_t v) {
-    uint32_t old = 0;
-    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %3, 0;\n\t@q atom.shared.add.u32 %0, [%1], %2;\n\t}"
-                 : "+r"(old)
-                 : "r"(addr), "r"(v), "r"((uint32_t)pred));
-    return old;
+__device__ __forceinline__ uint32_t lds_u32(uint32_t addr) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+    return v;
 }
 
-// One code into a table of 16-bit counter pairs, counted only if `valid` and
-// its word lies in the current window [wlo, wlo + wn).  Branch-free.
-__device__ __forceinline__ void pair_count(bool valid, uint32_t y, uint32_t hbase, uint32_t wlo,
-                                           uint32_t wn, const uint32_t *dtab, uint32_t &dacc) {
-    const uint32_t q = y - kMagicBits;
-    const uint32_t word = (q >> 1) - wlo;
-    const bool in = valid && word < wn;
-    const uint32_t sh = (q & 1u) << 4;
-    const uint32_t old = atom_add_if(in, hbase + (word << 2), 1u << sh);
-    const uint32_t d = ld_keep(&dtab[((old >> sh) & 0xFFFFu) + 1u]);
-    dacc += in ? d : 0u;
-}
+// Where one pass counts.  y is a code's bit pattern kMagicBits + q; the magic
+// offset is folded into the bases.
+struct HistPass {
+    uint32_t lane_base;   // lane: table + lane * 4 - (kMagicBits << 7)
+    uint32_t dbase;       // direct: table - (kMagicBits << 2)
+    uint32_t base;        // pair / byte: table (shared address)
+    uint32_t wlo, wn;     // pair / byte: words [wlo, wlo + wn) of the full table are counted
+    const uint32_t *dtab; // pair: global delta table
+    uint32_t dsm;         // byte: shared delta table (h = 0..256)
+};
 
-// Count one code.  y is the code's bit pattern kMagicBits + q.  For the delta
-// modes the return is delta(new count) to be added to the entropy sum.
-template <int MODE>
-__device__ __forceinline__ void hist_op(uint32_t y, uint32_t hbase, uint32_t lane_base,
-                                        uint32_t wlo, uint32_t wn, const uint32_t *dtab,
-                                        uint32_t &dacc) {
+// Count one code.  PRED: `valid` may be false (partial groups, windows); WIN:
+// only codes whose word lies in the pass's window are counted.  The delta modes
+// add delta(new count) to dacc; byte mode flags a counter that was already 255.
+template <int MODE, bool PRED, bool WIN>
+__device__ __forceinline__ void hist_count(bool valid, uint32_t y, const HistPass &h, uint32_t &dacc,
+                                           uint32_t &ovf) {
     if (MODE == kLane) {
-        red_add(lane_base + (y << 7), 1u);           // (q * 32 + lane) * 4, magic folded in
+        const uint32_t a = h.lane_base + (y << 7);
+        if (PRED) red_if(valid, a, 1u); else red_add(a, 1u);
     } else if (MODE == kDirect) {
-        red_add(hbase + (y << 2), 1u);               // q * 4, magic folded in
-    } else if (MODE == kDelta32) {
-        uint32_t old = atom_add(hbase + (y << 2), 1u);
-        dacc += ld_keep(&dtab[old + 1u]);
+        const uint32_t a = h.dbase + (y << 2);
+        if (PRED) red_if(valid, a, 1u); else red_add(a, 1u);
+    } else if (MODE == kPair) {
+        const uint32_t q = y - kMagicBits;
+        const uint32_t word = (q >> 1) - (WIN ? h.wlo : 0u);
+        const uint32_t sh = (q & 1u) << 4;
+        const bool in = (!PRED || valid) && (!WIN || word < h.wn);
+        const uint32_t old = (PRED || WIN) ? atom_if(in, h.base + (word << 2), 1u << sh)
+                                           : atom_add(h.base + (word << 2), 1u << sh);
+        const uint32_t d = ld_keep(&h.dtab[((old >> sh) & 0xFFFFu) + 1u]);
+        dacc += (PRED || WIN) ? (in ? d : 0u) : d;
     } else {
-        // 16-bit counter pairs; only codes whose word lies in the current window
-        // [wlo, wlo + wn) are counted by this pass
-        pair_count(true, y, hbase, wlo, wn, dtab, dacc);
+        const uint32_t q = y - kMagicBits;
+        const uint32_t word = (q >> 2) - (WIN ? h.wlo : 0u);
+        const uint32_t sh = (q & 3u) << 3;
+        const bool in = (!PRED || valid) && (!WIN || word < h.wn);
+        const uint32_t old = (PRED || WIN) ? atom_if(in, h.base + (word << 2), 1u << sh)
+                                           : atom_add(h.base + (word << 2), 1u << sh);
+        const uint32_t cnt = (old >> sh) & 0xFFu;
+        const uint32_t d = lds_u32(h.dsm + ((cnt + 1u) << 2));
+        if (PRED || WIN) {
+            dacc += in ? d : 0u;
+            ovf |= (in && cnt == 0xFFu) ? 1u : 0u;
+        } else {
+            dacc += d;
+            ovf |= cnt == 0xFFu ? 1u : 0u;
+        }
     }
 }
 
-// Fast path for one bit-width over this thread's elements (pairs, packed).
-template <int T, int EPT, int MODE, bool BOTTOM, bool FULL>
+struct EvalOut {
+    float sse, l1, linf;
+    uint32_t dacc, ovf;
+};
+
+// Fast path for one bit-width over this thread's elements (pairs, packed
+// f32x2 adds, subtracts and FMAs; the reconstruction product stays a scalar
+// multiply, rounded on its own and never fused with the subtraction after it).
+template <int T, int EPT, int MODE, bool BOTTOM, bool FULL, bool WIN, bool PROBE>
 __device__ __forceinline__ void eval_fast(const float (&c)[EPT], const float (&u)[EPT], int nvalid,
-                                          const BitParam &p, uint32_t hbase, uint32_t lane_base,
-                                          uint32_t wlo, uint32_t wn, const uint32_t *dtab,
-                                          float &sse, float &l1, float &linf,
-                                          unsigned long long &hacc) {
+                                          const BitParam &p, const HistPass &h, uint16_t *codes,
+                                          EvalOut &o) {
     const float2 tw = make_float2(p.twob, p.twob), zz = make_float2(p.Z, p.Z);
     const float2 mg = make_float2(kMagic, kMagic), mz = make_float2(p.MZ, p.MZ);
     float2 s2 = make_float2(0.0f, 0.0f);
-    float la = 0.0f, lb = 0.0f, ma = 0.0f, mb = 0.0f;
-    uint32_t dacc = 0;   // delta sums: at most EPT * 2^26 < 2^32
+    float la = 0.0f, lb = 0.0f, lm = 0.0f;
+    uint32_t dacc = 0, ovf = 0;   // delta sums: at most EPT * 2^26 < 2^32
 #pragma unroll
     for (int e = 0; e < EPT; e += 2) {
-        const bool v1 = FULL || (e + 1) * T + (int)threadIdx.x < nvalid;
-        const bool v0 = FULL || e * T + (int)threadIdx.x < nvalid;
-        if (v1) {
-            float2 x = ffma2(make_float2(u[e], u[e + 1]), tw, zz);
-            float2 y = fadd2(x, mg);
-            y.x = fminf(y.x, p.ytop);
-            y.y = fminf(y.y, p.ytop);
-            if (BOTTOM) {
-                y.x = fmaxf(y.x, kMagic);
-                y.y = fmaxf(y.y, kMagic);
-            }
-            // c_hat' = fl(fl(q - Z) * S'): scalar multiplies, so the product is rounded on
-            // its own and never contracted with the subtraction that follows
-            const float2 d = fsub2(y, mz);
-            const float2 ch = make_float2(__fmul_rn(d.x, p.Ss), __fmul_rn(d.y, p.Ss));
-            float2 er = fsub2(ch, make_float2(c[e], c[e + 1]));
-            s2 = ffma2(er, er, s2);
-            la = __fadd_rn(la, fabsf(er.x));
-            lb = __fadd_rn(lb, fabsf(er.y));
-            ma = fmaxf(ma, fabsf(er.x));
-            mb = fmaxf(mb, fabsf(er.y));
-            hist_op<MODE>(__float_as_uint(y.x), hbase, lane_base, wlo, wn, dtab, dacc);
-            hist_op<MODE>(__float_as_uint(y.y), hbase, lane_base, wlo, wn, dtab, dacc);
-        } else if (v0) {
-            float x = __fmaf_rn(u[e], p.twob, p.Z);
-            float y = __fadd_rn(x, kMagic);
-            y = fminf(y, p.ytop);
-            if (BOTTOM) y = fmaxf(y, kMagic);
-            float er = __fsub_rn(__fmul_rn(__fsub_rn(y, p.MZ), p.Ss), c[e]);
-            s2.x = __fmaf_rn(er, er, s2.x);
-            la = __fadd_rn(la, fabsf(er));
-            ma = fmaxf(ma, fabsf(er));
-            hist_op<MODE>(__float_as_uint(y), hbase, lane_base, wlo, wn, dtab, dacc);
+        const int i0 = e * T + (int)threadIdx.x, i1 = i0 + T;
+        const bool v0 = FULL || i0 < nvalid, v1 = FULL || i1 < nvalid;
+        const float2 x = ffma2(make_float2(u[e], u[e + 1]), tw, zz);
+        float2 y = fadd2(x, mg);
+        y.x = fminf(y.x, p.ytop);
+        y.y = fminf(y.y, p.ytop);
+        if (BOTTOM) {
+            y.x = fmaxf(y.x, kMagic);
+            y.y = fmaxf(y.y, kMagic);
+        }
+        const float2 d = fsub2(y, mz);
+        const float2 ch = make_float2(__fmul_rn(d.x, p.Ss), __fmul_rn(d.y, p.Ss));
+        float2 er = fsub2(ch, make_float2(c[e], c[e + 1]));
+        if (!FULL) {
+            er.x = v0 ? er.x : 0.0f;
+            er.y = v1 ? er.y : 0.0f;
+        }
+        s2 = ffma2(er, er, s2);
+        la = __fadd_rn(la, fabsf(er.x));
+        lb = __fadd_rn(lb, fabsf(er.y));
+        lm = fmaxf(lm, fmaxf(fabsf(er.x), fabsf(er.y)));
+        const uint32_t y0 = __float_as_uint(y.x), y1 = __float_as_uint(y.y);
+        hist_count<MODE, !FULL, WIN>(v0, y0, h, dacc, ovf);
+        hist_count<MODE, !FULL, WIN>(v1, y1, h, dacc, ovf);
+        if (PROBE) {
+            if (v0) codes[i0] = (uint16_t)(y0 - kMagicBits);
+            if (v1) codes[i1] = (uint16_t)(y1 - kMagicBits);
         }
     }
-    sse = __fadd_rn(s2.x, s2.y);
-    l1 = __fadd_rn(la, lb);
-    linf = fmaxf(ma, mb);
-    hacc += dacc;
+    o.sse = __fadd_rn(s2.x, s2.y);
+    o.l1 = __fadd_rn(la, lb);
+    o.linf = lm;
+    o.dacc = dacc;
+    o.ovf = ovf;
 }
 
 // Literal per-element formula (divisions, both clamps); any group.
-template <int T, int EPT, int MODE>
+template <int T, int EPT, int MODE, bool WIN, bool PROBE>
 __device__ __forceinline__ void eval_generic(const float (&c)[EPT], int nvalid, const BitParam &p,
-                                          uint32_t hbase, uint32_t lane_base, uint32_t wlo,
-                                          uint32_t wn, const uint32_t *dtab, float &sse, float &l1,
-                                          float &linf, unsigned long long &hacc) {
+                                             const HistPass &h, uint16_t *codes, EvalOut &o) {
     float s = 0.0f, a = 0.0f, m = 0.0f;
-    uint32_t dacc = 0;
+    uint32_t dacc = 0, ovf = 0;
 #pragma unroll
     for (int e = 0; e < EPT; e++) {
-        if (e * T + (int)threadIdx.x >= nvalid) continue;
-        float x = __fadd_rn(__fdiv_rn(c[e], p.Ss), p.Z);   // c'/S' == c/S exactly
-        float xc = fminf(fmaxf(x, 0.0f), p.top);
-        int q = __float2int_rn(xc);
-        float qz = __fsub_rn(__int2float_rn(q), p.Z);
+        const int i = e * T + (int)threadIdx.x;
+        const bool valid = i < nvalid;
+        const float x = __fadd_rn(__fdiv_rn(c[e], p.Ss), p.Z);   // c'/S' == c/S exactly
+        const float xc = fminf(fmaxf(x, 0.0f), p.top);
+        const int q = __float2int_rn(xc);
+        const float qz = __fsub_rn(__int2float_rn(q), p.Z);
         float er = __fsub_rn(__fmul_rn(qz, p.Ss), c[e]);
+        er = valid ? er : 0.0f;
         s = __fmaf_rn(er, er, s);
         a = __fadd_rn(a, fabsf(er));
         m = fmaxf(m, fabsf(er));
-        hist_op<MODE>(kMagicBits + (uint32_t)q, hbase, lane_base, wlo, wn, dtab, dacc);
+        hist_count<MODE, true, WIN>(valid, kMagicBits + (uint32_t)q, h, dacc, ovf);
+        if (PROBE && valid) codes[i] = (uint16_t)q;
     }
-    sse = s;
-    l1 = a;
-    linf = m;
-    hacc += dacc;
+    o.sse = s;
+    o.l1 = a;
+    o.linf = m;
+    o.dacc = dacc;
+    o.ovf = ovf;
 }
 
-// Count-only pass of one window of a 16-bit-pair table: the codes of
-// eval_fast (same operations, packed), no error sums, no branches per element.
-template <int T, int EPT>
-__device__ __forceinline__ void count_window_fast(const float (&u)[EPT], int nvalid, const BitParam &p,
-                                                  uint32_t hbase, uint32_t wlo, uint32_t wn,
-                                                  const uint32_t *dtab, unsigned long long &hacc) {
-    const float2 tw = make_float2(p.twob, p.twob), zz = make_float2(p.Z, p.Z);
-    const float2 mg = make_float2(kMagic, kMagic);
-    // the lower clamp is a no-op unless the group minimum rounds below code 0
-    const float lo = p.path == kFastBottom ? kMagic : -FLT_MAX;
-    uint32_t dacc = 0;
-#pragma unroll
-    for (int e = 0; e < EPT; e += 2) {
-        float2 y = fadd2(ffma2(make_float2(u[e], u[e + 1]), tw, zz), mg);
-        y.x = fmaxf(fminf(y.x, p.ytop), lo);
-        y.y = fmaxf(fminf(y.y, p.ytop), lo);
-        const bool v0 = e * T + (int)threadIdx.x < nvalid;
-        const bool v1 = (e + 1) * T + (int)threadIdx.x < nvalid;
-        pair_count(v0, __float_as_uint(y.x), hbase, wlo, wn, dtab, dacc);
-        pair_count(v1, __float_as_uint(y.y), hbase, wlo, wn, dtab, dacc);
-    }
-    hacc += dacc;
+// The fast path runs for warps whose elements are all valid, in groups whose
+// minimum does not round below code 0; every other warp (the tail of a partial
+// group) and every other group takes the literal formula, which gives the same
+// codes and errors.  WIN: only the codes of the pass's window are counted (a
+// table larger than its region).
+template <int T, int EPT, int MODE, bool WIN, bool PROBE>
+__device__ __forceinline__ void eval_dispatch(const float (&c)[EPT], const float (&u)[EPT], int nvalid,
+                                              bool full, bool generic, const BitParam &p,
+                                              const HistPass &h, uint16_t *codes, EvalOut &o) {
+    if (!generic && full && p.path == kFast)
+        eval_fast<T, EPT, MODE, false, true, WIN, PROBE>(c, u, nvalid, p, h, codes, o);
+    else
+        eval_generic<T, EPT, MODE, WIN, PROBE>(c, nvalid, p, h, codes, o);
 }
 
-// The same for groups on the literal-division path (codes as in eval_generic).
-template <int T, int EPT>
-__device__ __forceinline__ void count_window_generic(const float (&c)[EPT], int nvalid, const BitParam &p,
-                                                     uint32_t hbase, uint32_t wlo, uint32_t wn,
-                                                     const uint32_t *dtab, unsigned long long &hacc) {
-    uint32_t dacc = 0;
-#pragma unroll
-    for (int e = 0; e < EPT; e++) {
-        const float x = __fadd_rn(__fdiv_rn(c[e], p.Ss), p.Z);
-        const uint32_t y = kMagicBits + (uint32_t)__float2int_rn(fminf(fmaxf(x, 0.0f), p.top));
-        pair_count(e * T + (int)threadIdx.x < nvalid, y, hbase, wlo, wn, dtab, dacc);
-    }
-    hacc += dacc;
-}
-
+// Count-only pass over one window of a pair or byte table: the codes of the
+// evaluation pass (same operations), no error sums.
 template <int T, int EPT, int MODE>
-__device__ __forceinline__ void eval_dispatch(const float (&c)[EPT], const float (&u)[EPT],
-                                              int nvalid, bool full, bool generic,
-                                              const BitParam &p, uint32_t hbase,
-                                              uint32_t lane_base, uint32_t wlo, uint32_t wn,
-                                              const uint32_t *dtab, float &sse,
-                                              float &l1, float &linf, unsigned long long &hacc) {
+__device__ __forceinline__ void count_window(const float (&c)[EPT], const float (&u)[EPT], int nvalid,
+                                             bool generic, const BitParam &p, const HistPass &h,
+                                             uint32_t &dacc, uint32_t &ovf) {
     if (generic) {
-        eval_generic<T, EPT, MODE>(c, nvalid, p, hbase, lane_base, wlo, wn, dtab, sse, l1, linf, hacc);
-    } else if (p.path == kFast) {
-        if (full) eval_fast<T, EPT, MODE, false, true>(c, u, nvalid, p, hbase, lane_base, wlo, wn, dtab, sse, l1, linf, hacc);
-        else eval_fast<T, EPT, MODE, false, false>(c, u, nvalid, p, hbase, lane_base, wlo, wn, dtab, sse, l1, linf, hacc);
-    } else {
-        if (full) eval_fast<T, EPT, MODE, true, true>(c, u, nvalid, p, hbase, lane_base, wlo, wn, dtab, sse, l1, linf, hacc);
-        else eval_fast<T, EPT, MODE, true, false>(c, u, nvalid, p, hbase, lane_base, wlo, wn, dtab, sse, l1, linf, hacc);
-    }
-}
-
-// After a pass: add sum L(h) of a summed mode to hacc and clear the buffer
-// (the first clear_words words for the delta modes).
-template <int T>
-__device__ __forceinline__ void hist_finish(uint32_t *hist, int mode, int b, int clear_words,
-                                            const unsigned long long *__restrict__ ltab,
-                                            unsigned long long &hacc) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (mode == kLane) {
-        // the warp's j-th bin count is kept by lane j (bins / warps <= 32 for
-        // b <= 6), so the table lookups of all its bins go out together
-        static_assert((1 << kLaneMaxBits) / (T / 32) <= 32, "one lane per bin of a warp");
-        const int bins = 1 << b;
-        uint32_t mine = 0;
-        int j = 0;
-#pragma unroll 4
-        for (int k = warp; k < bins; k += T / 32, j++) {
-            const uint32_t v = hist[k * 32 + lane];
-            hist[k * 32 + lane] = 0u;
-            const uint32_t s = __reduce_add_sync(kFull, v);
-            mine = lane == j ? s : mine;
-        }
-        hacc += ld_keep(&ltab[mine]);   // L(0) = 0 for lanes without a bin
-    } else if (mode == kDirect) {
-        // branch-free: L(0) = 0, so an empty bin adds nothing
-        const int bins = 1 << b;
-#pragma unroll 4
-        for (int k = threadIdx.x; k < bins; k += T) {
-            const uint32_t v = hist[k];
-            hist[k] = 0u;
-            hacc += ld_keep(&ltab[v]);
+#pragma unroll
+        for (int e = 0; e < EPT; e++) {
+            const float x = __fadd_rn(__fdiv_rn(c[e], p.Ss), p.Z);
+            const uint32_t y = kMagicBits + (uint32_t)__float2int_rn(fminf(fmaxf(x, 0.0f), p.top));
+            hist_count<MODE, true, true>(e * T + (int)threadIdx.x < nvalid, y, h, dacc, ovf);
         }
     } else {
-        uint4 *h4 = reinterpret_cast<uint4 *>(hist);
-        for (int k = threadIdx.x; k < clear_words / 4; k += T) h4[k] = make_uint4(0u, 0u, 0u, 0u);
+        // the lower clamp is a no-op unless the group minimum rounds below code 0
+        const float lo = p.path == kFastBottom ? kMagic : -FLT_MAX;
+#pragma unroll
+        for (int e = 0; e < EPT; e++) {
+            float y = __fadd_rn(__fmaf_rn(u[e], p.twob, p.Z), kMagic);
+            y = fmaxf(fminf(y, p.ytop), lo);
+            hist_count<MODE, true, true>(e * T + (int)threadIdx.x < nvalid, __float_as_uint(y), h, dacc, ovf);
+        }
     }
 }
 
@@ -425,32 +404,173 @@ __device__ __forceinline__ void load_row(const float *p, float (&v)[W]) {
 }
 
 // Shared-memory layout (dynamic):
-//   hist[n_small][hist_words] hist_big[big_words] | psse[n_opts][T] | pl1[n_opts][T] | hpart[n_opts][T/32] (u64)
-//   | plinf[n_opts][T/32] | bp[n_opts] | mm[T/32][W][2]
+//   regionA[a_words] | regionB[b_words] | bdelta[kByteDelta] | part2[n_opts][T/2] (float2)
+//   | hpart[n_opts][T/32] (u64) | plinf[n_opts][T/32] | bp[n_opts] | mm[T/32][W][2] | flags[n_opts]
 struct Smem {
-    uint32_t *hist;
-    float *psse, *pl1, *plinf;
+    uint32_t *ra, *rb, *bdelta, *flags;
+    float2 *part2;
     unsigned long long *hpart;
+    float *plinf, *mm;
     BitParam *bp;
-    float *mm;
 };
 
-__host__ __device__ inline size_t smem_layout(int T, int W, int hist_words, int nbuf, int big_words,
-                                              int n_opts, size_t *o) {
+__host__ __device__ inline size_t smem_layout(int T, int W, int a_words, int b_words, int n_opts,
+                                              size_t *o) {
     size_t off = 0;
-    o[0] = off; off += (size_t)nbuf * hist_words * 4 + (size_t)big_words * 4;
-    o[1] = off; off += (size_t)n_opts * T * 4;
-    o[2] = off; off += (size_t)n_opts * T * 4;
+    o[0] = off; off += (size_t)a_words * 4;
+    o[1] = off; off += (size_t)b_words * 4;
+    o[2] = off; off += (size_t)kByteDelta * 4;
     off = (off + 15) & ~(size_t)15;
-    o[3] = off; off += (size_t)n_opts * (T / 32) * 8;
-    o[4] = off; off += (size_t)n_opts * (T / 32) * 4;
+    o[3] = off; off += (size_t)n_opts * (T / 2) * 8;
+    o[4] = off; off += (size_t)n_opts * (T / 32) * 8;
+    o[5] = off; off += (size_t)n_opts * (T / 32) * 4;
     off = (off + 15) & ~(size_t)15;
-    o[5] = off; off += (size_t)n_opts * sizeof(BitParam);
-    o[6] = off; off += (size_t)(T / 32) * W * 2 * 4;
-    return off;
+    o[6] = off; off += (size_t)n_opts * sizeof(BitParam);
+    o[7] = off; off += (size_t)(T / 32) * W * 2 * 4;
+    o[8] = off; off += (size_t)n_opts * 4;
+    return (off + 15) & ~(size_t)15;
 }
 
-template <int T, int EPT, int W>
+// Clear `words` words (a multiple of 4) of a table, 16 bytes per store.
+template <int T>
+__device__ __forceinline__ void clear_words(uint32_t *t, int words) {
+    uint4 *t4 = reinterpret_cast<uint4 *>(t);
+    for (int k = threadIdx.x; k < words / 4; k += T) t4[k] = make_uint4(0u, 0u, 0u, 0u);
+}
+
+// Probe readout of a table of `per_word` counters per word (2: 16-bit pairs,
+// 4: 8-bit), holding bins [first, first + words * per_word) of an option; each
+// thread clears the words it read (the readout replaces clear_words, whose
+// thread-to-word mapping differs, so that no word is cleared before it is read).
+template <int T>
+__device__ void probe_packed_clear(uint32_t *t, int words, int per_word, int64_t first, int bins,
+                                   uint32_t *out) {
+    const int bits = 32 / per_word;
+    const uint32_t mask = per_word == 2 ? 0xFFFFu : 0xFFu;
+    for (int j = threadIdx.x; j < words; j += T) {
+        const uint32_t v = t[j];
+        t[j] = 0u;
+        for (int s = 0; s < per_word; s++) {
+            const int64_t bin = first + (int64_t)j * per_word + s;
+            if (bin < bins) out[bin] = (v >> (s * bits)) & mask;
+        }
+    }
+}
+
+// Probe readout of a degenerate option (every code 0): bin 0 holds the group.
+template <int T>
+__device__ void probe_degenerate(uint32_t *out, int bins, int nvalid) {
+    for (int j = threadIdx.x; j < bins; j += T) out[j] = j == 0 ? (uint32_t)nvalid : 0u;
+}
+
+// After every count of region A is in: sum L(h) of the scanned tables, clear
+// every table, and write the hpart entries of the scanned options.
+template <int T, bool PROBE>
+__device__ void finish_small(const KernelArgs &A, const Smem &sm, int nvalid, int64_t item) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NW = T / 32;
+    for (int k = 0; k < A.n_small; k++) {
+        const int b = sm.bp[k].b, mode = A.opt_mode[k];
+        const int bins = 1 << b;
+        uint32_t *t = sm.ra + A.opt_off[k];
+        uint32_t *pout = PROBE ? A.hist_out + item * A.hist_stride + A.hist_off[A.opt_lo + k] : nullptr;
+        if (sm.bp[k].path == kDegenerate) {
+            if (PROBE) probe_degenerate<T>(pout, bins, nvalid);
+            continue;   // table untouched; hpart written by the evaluation pass
+        }
+        unsigned long long hacc = 0ull;
+        if (mode == kLane) {
+            // the warp's j-th bin count is kept by lane j (bins / warps <= 32),
+            // so the table lookups of all its bins go out together
+            uint32_t mine = 0;
+            int j = 0;
+#pragma unroll 4
+            for (int bin = warp; bin < bins; bin += NW, j++) {
+                const uint32_t v = t[bin * 32 + lane];
+                t[bin * 32 + lane] = 0u;
+                const uint32_t s = __reduce_add_sync(kFull, v);
+                mine = lane == j ? s : mine;
+                if (PROBE && lane == 0) pout[bin] = s;
+            }
+            hacc = ld_keep(&A.ltab[mine]);   // L(0) = 0 for lanes without a bin
+        } else if (mode == kDirect) {
+            // branch-free: L(0) = 0, so an empty bin adds nothing
+#pragma unroll 4
+            for (int bin = threadIdx.x; bin < bins; bin += T) {
+                const uint32_t v = t[bin];
+                t[bin] = 0u;
+                hacc += ld_keep(&A.ltab[v]);
+                if (PROBE) pout[bin] = v;
+            }
+        } else {
+            if (PROBE) probe_packed_clear<T>(t, A.opt_words[k], 2, 0, bins, pout);
+            else clear_words<T>(t, A.opt_words[k]);
+            continue;   // delta sums written by the evaluation pass
+        }
+        hacc = warp_sum_u64_redux(hacc);
+        if (lane == 0) sm.hpart[k * NW + warp] = hacc;
+    }
+}
+
+// One evaluation pass of option k: codes, errors and counts into table `t`;
+// per-thread partials into shared memory (pairs of lanes combined).
+template <int T, int EPT, bool PROBE>
+__device__ __forceinline__ void run_option(const KernelArgs &A, const Smem &sm, int k, uint32_t *t,
+                                           uint32_t wn, const float (&cw)[EPT], const float (&u)[EPT],
+                                           int nvalid, bool full, bool any_slow, uint16_t *codes) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NW = T / 32;
+    const BitParam p = sm.bp[k];
+    const int mode = A.opt_mode[k];
+    EvalOut o{0.0f, 0.0f, 0.0f, 0u, 0u};
+    unsigned long long hdeg = 0ull;
+    if (p.path == kDegenerate) {
+        if (threadIdx.x == 0) hdeg = __ldg(&A.ltab[nvalid]);
+        if (PROBE)
+            for (int e = 0; e < EPT; e++)
+                if (e * T + (int)threadIdx.x < nvalid) codes[e * T + threadIdx.x] = 0;
+    } else {
+        const bool generic = p.path == kGeneric || any_slow;
+        HistPass h;
+        const uint32_t tb = (uint32_t)__cvta_generic_to_shared(t);
+        h.lane_base = tb + lane * 4u - (kMagicBits << 7);
+        h.dbase = tb - (kMagicBits << 2);
+        h.base = tb;
+        h.wlo = 0u;
+        h.wn = wn;
+        h.dtab = A.dtab;
+        h.dsm = (uint32_t)__cvta_generic_to_shared(sm.bdelta);
+        switch (mode) {
+            case kLane: eval_dispatch<T, EPT, kLane, false, PROBE>(cw, u, nvalid, full, generic, p, h, codes, o); break;
+            case kDirect: eval_dispatch<T, EPT, kDirect, false, PROBE>(cw, u, nvalid, full, generic, p, h, codes, o); break;
+            case kPair: eval_dispatch<T, EPT, kPair, false, PROBE>(cw, u, nvalid, full, generic, p, h, codes, o); break;
+            default:
+                // byte counters; a table larger than region B is counted here in its
+                // first window only (the others come after a barrier)
+                if (A.opt_windows[k] > 1)
+                    eval_dispatch<T, EPT, kByte, true, PROBE>(cw, u, nvalid, full, generic, p, h, codes, o);
+                else
+                    eval_dispatch<T, EPT, kByte, false, PROBE>(cw, u, nvalid, full, generic, p, h, codes, o);
+                break;
+        }
+    }
+    float2 sl = make_float2(o.sse, o.l1);
+    sl.x = __fadd_rn(sl.x, __shfl_xor_sync(kFull, sl.x, 1));
+    sl.y = __fadd_rn(sl.y, __shfl_xor_sync(kFull, sl.y, 1));
+    if ((lane & 1) == 0) sm.part2[k * (T / 2) + (threadIdx.x >> 1)] = sl;
+    const uint32_t lmax = __reduce_max_sync(kFull, __float_as_uint(o.linf));
+    const bool delta = mode == kPair || mode == kByte || p.path == kDegenerate;
+    unsigned long long hs = 0ull;
+    if (delta) hs = warp_sum_u64_redux((unsigned long long)o.dacc + hdeg);
+    const uint32_t ovf = __any_sync(kFull, o.ovf != 0u);
+    if (lane == 0) {
+        sm.plinf[k * NW + warp] = __uint_as_float(lmax);
+        if (delta) sm.hpart[k * NW + warp] = hs;
+        if (ovf) sm.flags[k] = 1u;
+    }
+}
+
+template <int T, int EPT, int W, bool PROBE>
 __device__ void process_item(const KernelArgs &A, const Smem &sm, int64_t work) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int NW = T / 32;
@@ -474,7 +594,8 @@ __device__ void process_item(const KernelArgs &A, const Smem &sm, int64_t work) 
     const int j0 = c0 % kSlabWidth;
     const int64_t gstart = (int64_t)g * A.G;
     const int nvalid = (int)((S.K - gstart) < (int64_t)A.G ? (S.K - gstart) : (int64_t)A.G);
-    const bool full = nvalid >= T * EPT;
+    // every element of this warp is valid (warp-uniform)
+    const bool full = __all_sync(kFull, (EPT - 1) * T + (int)threadIdx.x < nvalid);
 
     // ---- gather: each element's W channels from its slab row
     float v[W][EPT];
@@ -525,8 +646,6 @@ __device__ void process_item(const KernelArgs &A, const Smem &sm, int64_t work) 
     __syncthreads();
 
     const int n_opts = A.opt_hi - A.opt_lo;
-    const int hw = A.hist_words;
-    const uint32_t hist_addr = (uint32_t)__cvta_generic_to_shared(sm.hist);
 #pragma unroll 1
     for (int w = 0; w < W; w++) {
         const int ch = c0 + w;
@@ -544,21 +663,16 @@ __device__ void process_item(const KernelArgs &A, const Smem &sm, int64_t work) 
             p.twob = (float)(1u << p.b);
             p.top = p.twob - 1.0f;
             p.ytop = kMagic + p.top;
-            p.S = __fdiv_rn(R, p.twob);
-            p.Ss = __fmul_rn(__fmul_rn(p.S, s1), s2);
-            p.mode = A.opt_mode[threadIdx.x];
-            p.buf = A.opt_buf[threadIdx.x];
-            p.sync = A.opt_sync[threadIdx.x];
-            p.windows = A.opt_windows[threadIdx.x];
-            p.wwords = A.opt_wwords[threadIdx.x];
-            if (p.S == 0.0f) {
+            const float S_ = __fdiv_rn(R, p.twob);
+            p.Ss = __fmul_rn(__fmul_rn(S_, s1), s2);
+            if (S_ == 0.0f) {
                 p.path = kDegenerate;
                 p.Z = 0.0f;
                 p.MZ = kMagic;
             } else {
-                p.Z = rintf(__fsub_rn(p.twob, __fdiv_rn(M, p.S)));
+                p.Z = rintf(__fsub_rn(p.twob, __fdiv_rn(M, S_)));
                 p.MZ = __fadd_rn(kMagic, p.Z);
-                if (p.S < FLT_MIN || fabsf(p.Z) >= 4194304.0f) {
+                if (S_ < FLT_MIN || fabsf(p.Z) >= 4194304.0f) {
                     p.path = kGeneric;
                 } else {
                     // the group minimum gives the smallest x: lower clamp only if it rounds below 0
@@ -574,92 +688,110 @@ __device__ void process_item(const KernelArgs &A, const Smem &sm, int64_t work) 
             S.vmin[item] = m;
             S.vmax[item] = M;
         }
-        // this channel's values (compile-time indices keep v in registers)
-        float cw[EPT];
-#pragma unroll
-        for (int e = 0; e < EPT; e++) cw[e] = v[0][e];
-#pragma unroll
-        for (int ww = 1; ww < W; ww++)
-            if (ww == w)
-#pragma unroll
-                for (int e = 0; e < EPT; e++) cw[e] = v[ww][e];
-        // one division per element, shared by every bit-width; then scale by 2^k
+        // one division per element, shared by every bit-width; then scale the
+        // channel's values in place by 2^k
         float u[EPT];
         int slow = 0;
 #pragma unroll
         for (int e = 0; e < EPT; e++) {
-            u[e] = R > 0.0f ? __fdiv_rn(cw[e], R) : 0.0f;
+            u[e] = R > 0.0f ? __fdiv_rn(v[0][e], R) : 0.0f;
             slow |= (u[e] != 0.0f && fabsf(u[e]) <= FLT_MIN && e * T + (int)threadIdx.x < nvalid);
-            cw[e] = __fmul_rn(__fmul_rn(cw[e], s1), s2);
+            v[0][e] = __fmul_rn(__fmul_rn(v[0][e], s1), s2);
         }
-        const int any_slow = __syncthreads_or(slow);   // also publishes bp
+        const bool any_slow = __syncthreads_or(slow) != 0;   // also publishes bp
 
+        uint16_t *codes = nullptr;
+        if (PROBE && A.codes_out)
+            codes = A.codes_out + S.code_off + (int64_t)ch * A.n_bits * S.K + gstart;
+        const int64_t kstride = S.K;   // codes of consecutive options of a channel
+        // ---- bit-widths up to 12: every table of region A, no barrier between them
 #pragma unroll 1
-        for (int k = 0; k < n_opts; k++) {
+        for (int k = 0; k < A.n_small; k++)
+            run_option<T, EPT, PROBE>(A, sm, k, sm.ra + A.opt_off[k], 0u, v[0], u, nvalid, full,
+                                      any_slow, codes ? codes + (A.opt_lo + k) * kstride : nullptr);
+        // ---- larger bit-widths one at a time in region B (byte counters)
+#pragma unroll 1
+        for (int k = A.n_small; k < n_opts; k++) {
             const BitParam p = sm.bp[k];
-            if (p.sync) __syncthreads();
-            const int slot = p.buf == 2 ? A.n_small : p.buf;   // the big buffer follows the small ones
-            uint32_t *hist = sm.hist + (size_t)slot * hw;
-            const uint32_t hbase_raw = hist_addr + (uint32_t)slot * hw * 4u;
-            float sse = 0.0f, l1 = 0.0f, linf = 0.0f;
-            unsigned long long hacc = 0ull;
-            if (p.path == kDegenerate) {
-                if (threadIdx.x == 0) hacc = __ldg(&A.ltab[nvalid]);
-            } else {
+            const uint32_t wn = (uint32_t)A.opt_words[k];
+            run_option<T, EPT, PROBE>(A, sm, k, sm.rb, wn, v[0], u, nvalid, full, any_slow,
+                                      codes ? codes + (A.opt_lo + k) * kstride : nullptr);
+            __syncthreads();   // every count of this pass (and of region A) is in
+            if (k == A.n_small) finish_small<T, PROBE>(A, sm, nvalid, item);
+            if (p.path != kDegenerate) {
                 const bool generic = p.path == kGeneric || any_slow;
-                // code bit patterns are kMagicBits + q: fold the offset into the bases
-                const uint32_t lane_base = hbase_raw + lane * 4u - (kMagicBits << 7);
-                const uint32_t dbase = hbase_raw - (kMagicBits << 2);
-                const uint32_t wn = (uint32_t)p.wwords;   // window 0 (the whole table if one)
-                switch (p.mode) {
-                    case kLane:
-                        eval_dispatch<T, EPT, kLane>(cw, u, nvalid, full, generic, p, dbase, lane_base, 0u, wn, A.dtab, sse, l1, linf, hacc);
-                        break;
-                    case kDirect:
-                        eval_dispatch<T, EPT, kDirect>(cw, u, nvalid, full, generic, p, dbase, lane_base, 0u, wn, A.dtab, sse, l1, linf, hacc);
-                        break;
-                    case kDelta32:
-                        eval_dispatch<T, EPT, kDelta32>(cw, u, nvalid, full, generic, p, dbase, lane_base, 0u, wn, A.dtab, sse, l1, linf, hacc);
-                        break;
-                    default:
-                        eval_dispatch<T, EPT, kDelta16>(cw, u, nvalid, full, generic, p, hbase_raw, lane_base, 0u, wn, A.dtab, sse, l1, linf, hacc);
-                        break;
-                }
-                // further windows of a 16-bit-pair table: wait for every count, clear,
-                // wait, count the next range of codes (the errors are already summed)
+                const int bins = 1 << p.b;
+                uint32_t *pout = PROBE ? A.hist_out + item * A.hist_stride + A.hist_off[A.opt_lo + k] : nullptr;
+                HistPass h;
+                h.base = (uint32_t)__cvta_generic_to_shared(sm.rb);
+                h.dtab = A.dtab;
+                h.dsm = (uint32_t)__cvta_generic_to_shared(sm.bdelta);
+                h.lane_base = h.dbase = 0u;
+                uint32_t dacc = 0, ovf = 0;
+                if (sm.flags[k] == 0u) {
+                    // byte counters held: the first window is complete
+                    if (PROBE) probe_packed_clear<T>(sm.rb, (int)wn, 4, 0, bins, pout);
+                    else clear_words<T>(sm.rb, (int)wn);
 #pragma unroll 1
-                for (int win = 1; win < p.windows; win++) {
-                    __syncthreads();
-                    hist_finish<T>(hist, kDelta16, p.b, p.wwords, A.ltab, hacc);
-                    __syncthreads();
-                    const uint32_t wlo = (uint32_t)(win * p.wwords);
-                    if (generic)
-                        count_window_generic<T, EPT>(cw, nvalid, p, hbase_raw, wlo, wn, A.dtab, hacc);
-                    else
-                        count_window_fast<T, EPT>(u, nvalid, p, hbase_raw, wlo, wn, A.dtab, hacc);
+                    for (int win = 1; win < A.opt_windows[k]; win++) {
+                        __syncthreads();
+                        h.wlo = (uint32_t)win * wn;
+                        h.wn = wn;
+                        count_window<T, EPT, kByte>(v[0], u, nvalid, generic, p, h, dacc, ovf);
+                        __syncthreads();
+                        if (PROBE) probe_packed_clear<T>(sm.rb, (int)wn, 4, (int64_t)win * wn * 4, bins, pout);
+                        else clear_words<T>(sm.rb, (int)wn);
+                    }
+                    // a counter of a later window may have overflowed too
+                    const uint32_t any = __syncthreads_or(ovf != 0u);
+                    if (any) {
+                        if (threadIdx.x == 0) sm.flags[k] = 1u;
+                    } else {
+                        const unsigned long long hs = warp_sum_u64_redux((unsigned long long)dacc);
+                        if (lane == 0) sm.hpart[k * NW + warp] += hs;
+                    }
+                    dacc = 0;
                 }
+                __syncthreads();
+                if (sm.flags[k] != 0u) {
+                    // some counter reached 255: count again exactly with 16-bit pairs,
+                    // in windows of region B
+                    clear_words<T>(sm.rb, A.b_words);
+                    const int rw = A.b_words;
+#pragma unroll 1
+                    for (int win = 0; win < A.opt_rwindows[k]; win++) {
+                        __syncthreads();
+                        h.wlo = (uint32_t)win * rw;
+                        h.wn = (uint32_t)rw;
+                        count_window<T, EPT, kPair>(v[0], u, nvalid, generic, p, h, dacc, ovf);
+                        __syncthreads();
+                        if (PROBE) probe_packed_clear<T>(sm.rb, rw, 2, (int64_t)win * rw * 2, bins, pout);
+                        else clear_words<T>(sm.rb, rw);
+                    }
+                    const unsigned long long hs = warp_sum_u64_redux((unsigned long long)dacc);
+                    if (lane == 0) sm.hpart[k * NW + warp] = hs;
+                }
+            } else if (PROBE) {
+                probe_degenerate<T>(A.hist_out + item * A.hist_stride + A.hist_off[A.opt_lo + k],
+                                    1 << p.b, nvalid);
             }
-            sm.psse[k * T + threadIdx.x] = sse;
-            sm.pl1[k * T + threadIdx.x] = l1;
-            const uint32_t lmax = __reduce_max_sync(kFull, __float_as_uint(linf));
-            if (lane == 0) sm.plinf[k * NW + warp] = __uint_as_float(lmax);
-            __syncthreads();   // every update of this buffer is done
-            if (p.path != kDegenerate)
-                hist_finish<T>(hist, p.mode, p.b, p.mode == kDelta32 ? (1 << p.b) : p.wwords, A.ltab, hacc);
-            hacc = warp_sum_u64_redux(hacc);
-            if (lane == 0) sm.hpart[k * NW + warp] = hacc;
+            if (k + 1 < n_opts) __syncthreads();   // region B is clear for the next option
+        }
+        if (A.n_small == n_opts) {
+            __syncthreads();
+            finish_small<T, PROBE>(A, sm, nvalid, item);
         }
         __syncthreads();
         // ---- reduce the partials and write this channel's entries
         for (int k = warp; k < n_opts; k += NW) {
-            float a = 0.0f, b = 0.0f;
+            float2 acc = make_float2(0.0f, 0.0f);
 #pragma unroll
-            for (int j = 0; j < T / 32; j++) {
-                a = __fadd_rn(a, sm.psse[k * T + j * 32 + lane]);
-                b = __fadd_rn(b, sm.pl1[k * T + j * 32 + lane]);
+            for (int j = 0; j < T / 64; j++) {
+                const float2 q = sm.part2[k * (T / 2) + j * 32 + lane];
+                acc.x = __fadd_rn(acc.x, q.x);
+                acc.y = __fadd_rn(acc.y, q.y);
             }
-            a = warp_sum(a);
-            b = warp_sum(b);
+            const float a = warp_sum(acc.x), b = warp_sum(acc.y);
             float cmax = lane < NW ? sm.plinf[k * NW + lane] : 0.0f;
             cmax = warp_max(cmax);
             unsigned long long hs = 0;
@@ -675,32 +807,43 @@ __device__ void process_item(const KernelArgs &A, const Smem &sm, int64_t work) 
                 S.linf[o] = (float)((double)cmax * inv);
                 unsigned long long ln = __ldg(&A.ltab[nvalid]);
                 S.hbits[o] = (double)(long long)(ln - hs) * (1.0 / 4194304.0);   // 2^-22
+                sm.flags[k] = 0u;
             }
         }
-        __syncthreads();
+        // the next channel takes the values of the following one (compile-time
+        // register indices)
+#pragma unroll
+        for (int ww = 0; ww + 1 < W; ww++)
+#pragma unroll
+            for (int e = 0; e < EPT; e++) v[ww][e] = v[ww + 1][e];
     }
 }
 
-template <int T, int EPT, int W>
+template <int T, int EPT, int W, bool PROBE>
 __global__ void __launch_bounds__(T, (T >= 512 ? 1 : 512 / T))
     k_cost(const __grid_constant__ KernelArgs A, int unused) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n_opts = A.opt_hi - A.opt_lo;
-    size_t o[7];
-    smem_layout(T, W, A.hist_words, A.n_small, A.big_words, n_opts, o);
+    size_t o[9];
+    smem_layout(T, W, A.a_words, A.b_words, n_opts, o);
     static_assert(EPT % 2 == 0, "elements are processed in pairs");
+    static_assert(T >= 64, "partials are read by whole warps");
     Smem sm;
-    sm.hist = reinterpret_cast<uint32_t *>(smem_raw + o[0]);
-    sm.psse = reinterpret_cast<float *>(smem_raw + o[1]);
-    sm.pl1 = reinterpret_cast<float *>(smem_raw + o[2]);
-    sm.hpart = reinterpret_cast<unsigned long long *>(smem_raw + o[3]);
-    sm.plinf = reinterpret_cast<float *>(smem_raw + o[4]);
-    sm.bp = reinterpret_cast<BitParam *>(smem_raw + o[5]);
-    sm.mm = reinterpret_cast<float *>(smem_raw + o[6]);
-    for (int i = threadIdx.x; i < A.n_small * A.hist_words + A.big_words; i += T) sm.hist[i] = 0u;
+    sm.ra = reinterpret_cast<uint32_t *>(smem_raw + o[0]);
+    sm.rb = reinterpret_cast<uint32_t *>(smem_raw + o[1]);
+    sm.bdelta = reinterpret_cast<uint32_t *>(smem_raw + o[2]);
+    sm.part2 = reinterpret_cast<float2 *>(smem_raw + o[3]);
+    sm.hpart = reinterpret_cast<unsigned long long *>(smem_raw + o[4]);
+    sm.plinf = reinterpret_cast<float *>(smem_raw + o[5]);
+    sm.bp = reinterpret_cast<BitParam *>(smem_raw + o[6]);
+    sm.mm = reinterpret_cast<float *>(smem_raw + o[7]);
+    sm.flags = reinterpret_cast<uint32_t *>(smem_raw + o[8]);
+    for (int i = threadIdx.x; i < A.a_words + A.b_words; i += T) sm.ra[i] = 0u;
+    for (int i = threadIdx.x; i < kByteDelta; i += T) sm.bdelta[i] = i <= 256 ? __ldg(&A.dtab[i]) : 0u;
+    for (int i = threadIdx.x; i < n_opts; i += T) sm.flags[i] = 0u;
     __syncthreads();
     if (A.counter == nullptr) {
-        process_item<T, EPT, W>(A, sm, blockIdx.x);
+        process_item<T, EPT, W, PROBE>(A, sm, blockIdx.x);
     } else {
         __shared__ int64_t s_work;
         while (true) {
@@ -708,7 +851,7 @@ __global__ void __launch_bounds__(T, (T >= 512 ? 1 : 512 / T))
             __syncthreads();
             const int64_t work = s_work;
             if (work >= A.n_work) break;
-            process_item<T, EPT, W>(A, sm, work);
+            process_item<T, EPT, W, PROBE>(A, sm, work);
             __syncthreads();
         }
     }
@@ -717,91 +860,95 @@ __global__ void __launch_bounds__(T, (T >= 512 ? 1 : 512 / T))
 struct ConfigEntry {
     CostConfig cfg;
     void (*kernel)(KernelArgs, int);
+    void (*probe)(KernelArgs, int);   // probe instantiation (or NULL)
+    int ctas;                         // resident CTAs per SM the shared-memory plan aims at
 };
 
-#define MGS_CFG(T, E, W) {{T, E, W, "t" #T "_e" #E "_w" #W}, k_cost<T, E, W>}
+#define MGS_CFG(T, E, W, C) {{T, E, W, "t" #T "_e" #E "_w" #W}, k_cost<T, E, W, false>, nullptr, C}
+#define MGS_CFGP(T, E, W, C) {{T, E, W, "t" #T "_e" #E "_w" #W}, k_cost<T, E, W, false>, k_cost<T, E, W, true>, C}
 const ConfigEntry kConfigs[] = {
-    MGS_CFG(256, 16, 4),
-    MGS_CFG(512, 8, 4),
-    MGS_CFG(256, 16, 2),
-    MGS_CFG(512, 8, 8),
-    MGS_CFG(256, 8, 8),
-    MGS_CFG(256, 8, 4),
-    MGS_CFG(128, 8, 8),
-    MGS_CFG(256, 4, 8),
-    MGS_CFG(512, 32, 1),
-    MGS_CFG(256, 16, 1),
-    MGS_CFG(512, 8, 2),
-    MGS_CFG(512, 4, 8),
-    MGS_CFG(512, 4, 4),
+    MGS_CFGP(256, 16, 4, 2),
+    MGS_CFG(512, 8, 4, 1),
+    MGS_CFG(256, 16, 2, 2),
+    MGS_CFGP(256, 8, 4, 2),
+    MGS_CFG(128, 8, 8, 4),
+    MGS_CFGP(256, 4, 8, 2),
+    MGS_CFGP(512, 32, 1, 1),
+    MGS_CFG(512, 16, 2, 1),
 };
 #undef MGS_CFG
+#undef MGS_CFGP
 constexpr int kNumConfigs = sizeof(kConfigs) / sizeof(kConfigs[0]);
 
-// Histogram buffers of a launch.  Small buffers hold the per-lane columns
-// (b <= 6), the direct tables (b <= 10) and the delta tables that fit; a big
-// buffer of 16384 words takes larger bit-widths (32-bit counters up to b = 14,
-// 16-bit pairs for b = 15, and b = 16 in two windows).  With a big buffer there
-// is one small buffer (options alternate between the two); otherwise two.
+// Histogram plan of a launch: region A holds a table per option up to 12 bits
+// (lane columns, direct counters or 16-bit pairs), region B the byte counters
+// of one larger option at a time, in windows when region B is smaller than the
+// option's table.
 struct HistPlan {
-    int hist_words, n_small, big_words;
+    int n_small = 0, a_words = 0, b_words = 0;
+    int8_t mode[MGS_MAX_OPTIONS] = {}, windows[MGS_MAX_OPTIONS] = {}, rwindows[MGS_MAX_OPTIONS] = {};
+    int32_t off[MGS_MAX_OPTIONS] = {}, words[MGS_MAX_OPTIONS] = {};
+    size_t smem = 0;
 };
-constexpr int kBigWords = 16384;
 
-// Histogram mode and buffer of every option (fixed for a launch).  Consecutive
-// options alternate buffers so that one barrier per bit-width suffices; an
-// option that must reuse the previous option's buffer waits for its clearing.
-void option_plan(const HistPlan &h, const int32_t *bits, int n_opts, KernelArgs *A) {
-    int last = -1;
+// Shared memory a CTA may use when `ctas` of them share an SM (228 KB per SM,
+// 1 KB reserved per CTA, the kernel's few static bytes).
+size_t smem_budget(int ctas) { return std::min<size_t>(227 * 1024, (228 * 1024) / ctas - 1024 - 64); }
+
+HistPlan plan_hist(const ConfigEntry &E, const int32_t *bits, int n_opts) {
+    const CostConfig &c = E.cfg;
+    HistPlan h;
+    const int NW = c.threads / 32;
+    int bl[MGS_MAX_OPTIONS];
+    for (int k = 0; k < n_opts; k++) bl[k] = bits ? bits[k] : MGS_MAX_BITS - n_opts + 1 + k;
+    int large_words = 0;
     for (int k = 0; k < n_opts; k++) {
-        const int b = bits[k];
-        int mode, buf = 0, windows = 1, wwords = 1 << (b - 1);
-        if (b <= kLaneMaxBits) mode = kLane;
-        else if (b <= kDirectMaxBits) mode = kDirect;
-        else if ((1 << b) <= h.hist_words) mode = kDelta32;
-        else if ((1 << (b - 1)) <= h.hist_words) mode = kDelta16;
-        else if ((1 << b) <= h.big_words) {
-            mode = kDelta32;
-            buf = 2;
+        const int b = bl[k];
+        int mode, words;
+        if (b <= kLaneMaxBits && (1 << b) <= 32 * NW) {
+            mode = kLane;
+            words = 32 << b;
+        } else if (b <= kDirectMaxBits) {
+            mode = kDirect;
+            words = 1 << b;
+        } else if (b <= kPairMaxBits) {
+            mode = kPair;
+            words = 1 << (b - 1);
         } else {
-            // 16-bit pairs in the big buffer, in windows of big_words words
-            mode = kDelta16;
-            buf = 2;
-            wwords = std::min(1 << (b - 1), h.big_words);
-            windows = (1 << (b - 1)) / wwords;
+            mode = kByte;
+            words = std::max(4, 1 << (b - 2));
         }
-        if (buf != 2) {
-            buf = -1;
-            for (int c = 0; c < 3 && buf < 0; c++) {
-                if (c == 1 && h.n_small < 2) continue;
-                if (c == 2 && h.big_words == 0) continue;
-                if (c != last) buf = c;
-            }
-            if (buf < 0) buf = 0;
+        words = (words + 3) & ~3;
+        h.mode[k] = (int8_t)mode;
+        if (mode != kByte) {
+            // bit-widths ascend, so the small options form a prefix
+            h.off[k] = h.a_words;
+            h.words[k] = words;
+            h.a_words += words;
+            h.n_small = k + 1;
+        } else {
+            large_words = std::max(large_words, words);
         }
-        A->opt_mode[k] = (int8_t)mode;
-        A->opt_buf[k] = (int8_t)buf;
-        A->opt_sync[k] = (int8_t)(buf == last);
-        A->opt_windows[k] = (int8_t)windows;
-        A->opt_wwords[k] = wwords;
-        last = buf;
     }
-}
-
-size_t smem_for(const CostConfig &c, const HistPlan &h, int n_opts) {
-    size_t o[7];
-    return smem_layout(c.threads, c.width, h.hist_words, h.n_small, h.big_words, n_opts, o);
-}
-
-HistPlan hist_plan(const CostConfig &c, int G, const int32_t *bits, int n_opts) {
-    (void)c;
-    HistPlan h{G <= 2048 ? 2048 : 4096, 2, 0};
-    int bmax = bits ? 0 : MGS_MAX_BITS;
-    for (int k = 0; bits && k < n_opts; k++) bmax = std::max(bmax, (int)bits[k]);
-    if ((1 << (bmax - 1)) > h.hist_words) {
-        h.n_small = 1;
-        h.big_words = kBigWords;
+    size_t o[9];
+    const size_t fixed = smem_layout(c.threads, c.width, h.a_words, 0, n_opts, o);
+    const size_t budget = smem_budget(E.ctas);
+    int bw = large_words;
+    if (bw > 0) {
+        // region B: the largest table that fits, in whole power-of-two windows
+        int cap = budget > fixed ? (int)((budget - fixed) / 4) : 0;
+        while (bw > cap && bw > 1024) bw >>= 1;
+        bw = std::max(bw, 1024);
     }
+    h.b_words = bw;
+    for (int k = h.n_small; k < n_opts; k++) {
+        const int b = bl[k];
+        const int need = std::max(4, 1 << (b - 2)), need_pairs = 1 << (b - 1);
+        h.words[k] = std::min(need, bw);
+        h.windows[k] = (int8_t)((need + bw - 1) / bw);
+        h.rwindows[k] = (int8_t)((need_pairs + bw - 1) / bw);
+    }
+    h.smem = smem_layout(c.threads, c.width, h.a_words, h.b_words, n_opts, o);
     return h;
 }
 
@@ -811,20 +958,25 @@ int cost_config_count() { return kNumConfigs; }
 const CostConfig &cost_config(int i) { return kConfigs[i].cfg; }
 
 int cost_default_config(int G) {
-    if (G <= 1024) return 7;    // 256 x 4, W 8
-    if (G <= 2048) return 5;    // 256 x 8, W 4
+    if (G <= 1024) return 5;    // 256 x 4, W 8
+    if (G <= 2048) return 3;    // 256 x 8, W 4
     if (G <= 4096) return 0;    // 256 x 16, W 4
-    if (G <= 16384) return 8;   // 512 x 32, W 1
+    if (G <= 16384) return 6;   // 512 x 32, W 1
     return -1;
 }
 
+bool cost_config_has_probe(int config) {
+    return config >= 0 && config < kNumConfigs && kConfigs[config].probe != nullptr;
+}
+
 size_t cost_smem_bytes(int config, int G, int n_opts, const int32_t *bits) {
-    const CostConfig &c = kConfigs[config].cfg;
-    return smem_for(c, hist_plan(c, G, bits, n_opts), n_opts);
+    (void)G;
+    return plan_hist(kConfigs[config], bits, n_opts).smem;
 }
 
 struct CostExec {
     const ConfigEntry *entry = nullptr;
+    void (*kernel)(KernelArgs, int) = nullptr;
     KernelArgs args{};
     size_t smem = 0;
     int64_t grid = 0;
@@ -842,6 +994,11 @@ mgs_status cost_exec_create(mgs_ctx *ctx, const CostLaunch &L, int config, CostE
         set_error("tile %s cannot hold a group of %d", E.cfg.name, L.group_size);
         return MGS_ERR_INVALID_ARG;
     }
+    const bool probe = L.probe_hist != nullptr || L.probe_codes != nullptr;
+    if (probe && !E.probe) {
+        set_error("tile %s has no probe kernel", E.cfg.name);
+        return MGS_ERR_INVALID_ARG;
+    }
     int64_t n_work = 0;
     *segs = L.segs;
     for (auto &s : *segs) {
@@ -855,6 +1012,7 @@ mgs_status cost_exec_create(mgs_ctx *ctx, const CostLaunch &L, int config, CostE
     }
     CostExec *X = new CostExec();
     X->entry = &E;
+    X->kernel = probe ? E.probe : E.kernel;
     KernelArgs &A = X->args;
     A.n_segs = (int32_t)segs->size();
     A.G = L.group_size;
@@ -865,25 +1023,40 @@ mgs_status cost_exec_create(mgs_ctx *ctx, const CostLaunch &L, int config, CostE
     for (int k = 0; k < L.n_bits; k++) A.bits[k] = L.bits[k];
     A.ltab = ctx->d_ltab;
     A.dtab = ctx->d_dtab;
-    const HistPlan hp = hist_plan(E.cfg, L.group_size, L.bits + L.opt_lo, L.opt_hi - L.opt_lo);
-    A.hist_words = hp.hist_words;
+    const int n_opts = L.opt_hi - L.opt_lo;
+    const HistPlan hp = plan_hist(E, L.bits + L.opt_lo, n_opts);
     A.n_small = hp.n_small;
-    A.big_words = hp.big_words;
-    option_plan(hp, L.bits + L.opt_lo, L.opt_hi - L.opt_lo, &A);
-    X->smem = smem_for(E.cfg, hp, L.opt_hi - L.opt_lo);
+    A.a_words = hp.a_words;
+    A.b_words = hp.b_words;
+    for (int k = 0; k < n_opts; k++) {
+        A.opt_mode[k] = hp.mode[k];
+        A.opt_windows[k] = hp.windows[k];
+        A.opt_rwindows[k] = hp.rwindows[k];
+        A.opt_off[k] = hp.off[k];
+        A.opt_words[k] = hp.words[k];
+    }
+    A.hist_out = L.probe_hist;
+    A.codes_out = L.probe_codes;
+    int64_t hs = 0;
+    for (int k = 0; k < L.n_bits; k++) {
+        A.hist_off[k] = hs;
+        hs += (int64_t)1 << L.bits[k];
+    }
+    A.hist_stride = hs;
+    X->smem = hp.smem;
     X->persistent = L.persistent;
     if (X->smem > 227 * 1024) {
         set_error("tile %s needs %zu bytes of shared memory for G=%d and %d options", E.cfg.name,
-                  X->smem, L.group_size, L.opt_hi - L.opt_lo);
+                  X->smem, L.group_size, n_opts);
         delete X;
         return MGS_ERR_INVALID_ARG;
     }
-    cudaError_t e = cudaFuncSetAttribute(E.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(X->kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)X->smem);
     X->grid = n_work;
     if (e == cudaSuccess && L.persistent) {
         int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, E.kernel, E.cfg.threads, X->smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, X->kernel, E.cfg.threads, X->smem);
         per_sm = std::max(per_sm, 1);
         X->grid = std::min<int64_t>(n_work, (int64_t)ctx->sm_count * per_sm);
     }
@@ -911,7 +1084,7 @@ mgs_status cost_exec_run(const CostExec *X, cudaStream_t st) {
     if (X->grid == 0) return MGS_OK;
     if (X->persistent)
         MGS_CUDA_TRY(cudaMemsetAsync(X->args.counter, 0, sizeof(unsigned int), st));
-    X->entry->kernel<<<(unsigned)X->grid, X->entry->cfg.threads, X->smem, st>>>(X->args, 0);
+    X->kernel<<<(unsigned)X->grid, X->entry->cfg.threads, X->smem, st>>>(X->args, 0);
     count_launches(1);
     MGS_CUDA_TRY(cudaGetLastError());
     return MGS_OK;

@@ -83,6 +83,7 @@ struct mgs_ctx {
     int forced_config = -1;                 // testing hook: force a tile configuration
     int n_scenes = 0;
     int vq_tensor = 1;                      // SH assignment on the tensor cores (else CUDA cores)
+    long long vq_wait_cycles = 0;           // bounded-wait limit of the tensor path (0: default)
     int64_t vq_scores = 0, vq_rescored = 0; // since the last mgs_vq_stats
 };
 
@@ -113,7 +114,8 @@ mgs_status scene_kept(mgs_scene *scene, const int64_t *keep, int32_t n_r, cudaSt
 // tile_cnt[kept_tiles_for(n)] (fully overwritten; nothing needs clearing).
 mgs_status kept_list_into(const mgs_scene *scene, int64_t keep, int32_t *pos, uint32_t *tile_cnt,
                           cudaStream_t st);
-int64_t kept_tiles_for(int64_t n);
+constexpr int kKeptTile = 4096;       // positions counted per tile by the kept-list kernels
+constexpr int64_t kept_tiles_for(int64_t n) { return (n + kKeptTile - 1) / kKeptTile; }
 
 // ---- cost kernels (cost.cu) ----
 struct CostSeg {
@@ -129,6 +131,7 @@ struct CostSeg {
     int32_t g_first;       // first group computed by this segment
     int32_t g_count;       // groups computed (0 = all n_groups)
     int32_t pad_;
+    int64_t code_off;      // probe launches: codes of this segment start here ([C][n_bits][K])
     double *sse;
     double *l1;
     double *hbits;
@@ -146,6 +149,10 @@ struct CostLaunch {
     int32_t opt_lo = 0;          // options computed by this launch: [opt_lo, opt_hi)
     int32_t opt_hi = 0;
     bool persistent = false;
+    // probe launches (test and inspection): every bin of every histogram,
+    // [item][sum of 2^b over the grid's options], and every code
+    uint32_t *probe_hist = nullptr;
+    uint16_t *probe_codes = nullptr;
 };
 
 // Tile configurations of the cost kernel.
@@ -166,6 +173,8 @@ mgs_status cost_launch(mgs_ctx *ctx, const CostLaunch &L, int config, CostSeg *d
                        unsigned int *d_counter, cudaStream_t st);
 size_t cost_smem_bytes(int config, int group_size, int n_opts, const int32_t *bits);
 bool cost_config_fits(int config, int group_size, int n_opts, const int32_t *bits);
+// The configuration has a probe instantiation.
+bool cost_config_has_probe(int config);
 
 // A prepared launch: work layout, kernel arguments and shape, reusable and
 // capturable (cost_exec_run issues only a memset and a kernel launch).
@@ -198,11 +207,15 @@ size_t vq_tc_workspace(int32_t K, int32_t D);
 // Lay out the codebook in `tiles` and assign x[rows[i]] (rows may be NULL)
 // with the exact path's decisions; *stats += entries re-scored exactly,
 // *err |= 1 if a bounded wait ran out (cmax2: 4 bytes of scratch).
+// wait_cycles: clock-cycle limit of each bounded wait (0: the default, about one second).
 mgs_status vq_assign_tc(const float *x, int64_t n, int32_t D, const int32_t *rows, const float *cb,
                         int32_t K, int32_t *idx, float *score, unsigned char *tiles, unsigned int *cmax2,
-                        unsigned long long *stats, unsigned int *err, cudaStream_t st);
+                        unsigned long long *stats, unsigned int *err, long long wait_cycles, cudaStream_t st);
 
 // ---- helpers (abi.cu) ----
+// Stream-ordered device allocation of the library's scenes, tables and
+// workspaces; fails on purpose when a test armed mgs_debug_fail_allocation.
+cudaError_t dev_malloc_async(void **p, size_t bytes, cudaStream_t st);
 // Count kernels enqueued by this library (mgs_kernel_launches()).
 void count_launches(int64_t k);
 bool is_device_pointer(const void *p);

@@ -14,7 +14,10 @@ namespace {
 // MGS_NOALLOC_MAX_KEEP kept indices (16 MiB) and the tile counts of a scene of up
 // to MGS_NOALLOC_MAX_SCENE Gaussians (16 KiB).
 static __device__ __align__(256) int32_t g_noalloc_kept[MGS_NOALLOC_MAX_KEEP];
-static __device__ __align__(256) uint32_t g_noalloc_tiles[(MGS_NOALLOC_MAX_SCENE + 4095) / 4096];
+constexpr int64_t kNoallocTiles = mgs::kept_tiles_for(MGS_NOALLOC_MAX_SCENE);
+static __device__ __align__(256) uint32_t g_noalloc_tiles[kNoallocTiles];
+static_assert(kNoallocTiles * mgs::kKeptTile >= MGS_NOALLOC_MAX_SCENE,
+              "one tile count per kept-list tile of the largest scene");
 
 constexpr int kMaxDevices = 64;
 

@@ -464,8 +464,9 @@ __global__ void __launch_bounds__(kTileThreads) k_kept_scatter(const int32_t *__
 
 template <typename T>
 mgs_status dalloc(T **p, size_t count, cudaStream_t st) {
-    cudaError_t e = cudaMallocAsync((void **)p, std::max<size_t>(count, 1) * sizeof(T), st);
+    cudaError_t e = dev_malloc_async((void **)p, std::max<size_t>(count, 1) * sizeof(T), st);
     if (e != cudaSuccess) {
+        cudaGetLastError();
         set_error("device allocation of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
         return MGS_ERR_OUT_OF_MEMORY;
     }
@@ -523,9 +524,18 @@ mgs_status scene_build(mgs_ctx *ctx, const float *d_attrs, const float *d_imp, i
         }
     }
 
-    // 2. scratch for the sorts
+    // 2. scratch for the sorts (freed on every return from here on)
     uint64_t *k64 = nullptr, *k64b = nullptr;
     uint32_t *v = nullptr, *vb = nullptr, *hist = nullptr;
+    int32_t *rank = nullptr;
+    struct Scratch {
+        void **p[6];
+        cudaStream_t st;
+        ~Scratch() {
+            for (void **q : p)
+                if (*q) cudaFreeAsync(*q, st);
+        }
+    } guard{{(void **)&k64, (void **)&k64b, (void **)&v, (void **)&vb, (void **)&hist, (void **)&rank}, st};
     int n_tiles = (int)((n + kTile - 1) / kTile);
     MGS_TRY(dalloc(&k64, n, st));
     MGS_TRY(dalloc(&k64b, n, st));
@@ -539,7 +549,6 @@ mgs_status scene_build(mgs_ctx *ctx, const float *d_attrs, const float *d_imp, i
     MGS_TRY(dalloc(&sc->d_order, n, st));
     MGS_TRY(dalloc(&sc->d_codes, n, st));
     MGS_TRY(dalloc(&sc->d_slabs, (size_t)sc->n_slabs * n * kSlabWidth, st));
-    int32_t *rank = nullptr;
     MGS_TRY(dalloc(&rank, n, st));
 
     int blocks = (int)((n + 255) / 256);
@@ -559,12 +568,6 @@ mgs_status scene_build(mgs_ctx *ctx, const float *d_attrs, const float *d_imp, i
                                        sc->d_rank_m, sc->d_order);
     count_launches(4);   // importance keys, rank scatter, Morton codes, relayout
     MGS_CUDA_TRY(cudaGetLastError());
-    cudaFreeAsync(k64, st);
-    cudaFreeAsync(k64b, st);
-    cudaFreeAsync(v, st);
-    cudaFreeAsync(vb, st);
-    cudaFreeAsync(hist, st);
-    cudaFreeAsync(rank, st);
     sc->device_bytes = (int64_t)sc->n_slabs * n * kSlabWidth * 4 + n * (4 + 4 + 8);
     return MGS_OK;
 }
@@ -592,7 +595,10 @@ mgs_status scene_kept(mgs_scene *sc, const int64_t *keep, int32_t n_r, cudaStrea
     MGS_TRY(dalloc(&pos, (size_t)total, st));
     int n_tiles = (int)((sc->n + kTile - 1) / kTile);
     uint32_t *cnt = nullptr;
-    MGS_TRY(dalloc(&cnt, (size_t)n_r * n_tiles, st));
+    if (mgs_status s = dalloc(&cnt, (size_t)n_r * n_tiles, st); s != MGS_OK) {
+        cudaFreeAsync(pos, st);
+        return s;
+    }
     KeepArg ka{};
     ka.n_r = n_r;
     for (int r = 0; r < n_r; r++) ka.k[r] = keep[r];
@@ -628,6 +634,6 @@ mgs_status kept_list_into(const mgs_scene *sc, int64_t keep, int32_t *pos, uint3
     return MGS_OK;
 }
 
-int64_t kept_tiles_for(int64_t n) { return (n + kTile - 1) / kTile; }
+static_assert(kTile == kKeptTile, "kept-list tiles are sized by kKeptTile");
 
 }  // namespace mgs

@@ -47,6 +47,7 @@ struct Job {
     int32_t G = 0;
     double budget = 0;
     mgs_solve_opts opts{};
+    void *table_out = nullptr;       // caller's host copy of the finished table (optional)
     // resources
     mgs_scene *scene = nullptr;
     void *d_table = nullptr;
@@ -185,7 +186,7 @@ void ingest_loop(mgs_server *S) {
                        j->bits.data(), j->G};
             s = mgs_table_layout_for(j->n, j->C, &g, &j->layout);
             if (s == MGS_OK &&
-                cudaMallocAsync(&j->d_table, j->layout.total_bytes, S->ingest_stream) != cudaSuccess) {
+                dev_malloc_async(&j->d_table, j->layout.total_bytes, S->ingest_stream) != cudaSuccess) {
                 cudaGetLastError();
                 set_error("table allocation failed");
                 s = MGS_ERR_OUT_OF_MEMORY;
@@ -393,7 +394,17 @@ void solve_loop(mgs_server *S) {
             sol.choice = choice.data();
             mgs_grid g{(int32_t)j->keep.size(), j->keep.data(), (int32_t)j->bits.size(),
                        j->bits.data(), j->G};
-            s = mgs_solve_budgets_device(S->ctx, j->d_table, &j->layout, &g, 1, &j->budget, &j->opts, &sol, st);
+            if (j->table_out) {
+                cudaError_t e = cudaMemcpyAsync(j->table_out, j->d_table, (size_t)j->layout.total_bytes,
+                                                cudaMemcpyDeviceToHost, st);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+                if (e != cudaSuccess) {
+                    set_error("table copy: %s", cudaGetErrorString(e));
+                    s = MGS_ERR_CUDA;
+                }
+            }
+            if (s == MGS_OK)
+                s = mgs_solve_budgets_device(S->ctx, j->d_table, &j->layout, &g, 1, &j->budget, &j->opts, &sol, st);
         }
         release_job(S, j);   // outside the lock: it waits for the copy stream
         std::lock_guard<std::mutex> lk(S->mu);
@@ -480,6 +491,7 @@ mgs_status mgs_server_submit(mgs_server *S, const mgs_job *job, int64_t *id_out)
     j->G = job->grid.group_size;
     j->budget = job->budget_bytes;
     j->opts = job->opts;
+    j->table_out = job->table_out;
     mgs_table_layout L;
     MGS_TRY(mgs_table_layout_for(j->n, j->C, &job->grid, &L));
     j->footprint = job_footprint(*j, L);

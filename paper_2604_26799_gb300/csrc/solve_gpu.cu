@@ -3,25 +3,32 @@
 // The arithmetic is solve_def.h's, so the answers equal the host solver's bit
 // for bit.
 //
-//   k_hull   one thread per (channel, group) item: rates in 2^-22-bit units,
-//            losses, lower convex hull, increment keys (level-major arrays),
-//            per-ratio rate totals and a 2^16-bucket histogram of increment
-//            rates by the top 16 key bits.
-//   k_solve  one 1024-thread CTA per (budget, ratio) problem:
-//            1. the bucket holding the LP split, from the histogram;
-//            2. the split key K*, 12 key bits per pass over the ratio's
-//               increments (shared-memory histogram; a bucket with a single
-//               increment ends the search early);
-//            3. one ordered pass over the items: increments above K* are
-//               taken whole, those equal to K* in (item, level) order while
-//               they fit (block prefix sums); the first that does not fit is
-//               the split; the loss at the split and the LP bound;
-//            4. greedy completion, one block-wide arg-min per take: the next
-//               increment to take is the first one in solve order, after
-//               the last one taken, that is its item's next increment and
-//               fits the remaining capacity (every increment before it in
-//               that order has already been passed over for good);
-//            5. the chosen options and the final loss (tree sum).
+//   k_hull           one thread per (channel, group) item: rates in 2^-22-bit
+//                    units, losses, lower convex hull, increment keys
+//                    (level-major arrays), per-ratio rate totals and a
+//                    2^16-bucket histogram of increment rates by the top 16
+//                    key bits.
+// Then every (budget, ratio) problem at once; a problem's items are cut into
+// chunks of 1024, passes over items run one CTA per chunk of every problem,
+// the steps that need a whole problem one CTA per problem:
+//   k_split_coarse   the bucket holding the LP split, from the histogram;
+//   k_split_fine /   the split key K*, 12 key bits per pass: a histogram of the
+//   k_split_select   bucket's increments over every chunk, then the bucket of
+//                    the split (a bucket with a single increment: its key);
+//   k_order_ties /   the ordered pass: increments above K* are taken whole,
+//   k_order_scan /   those equal to K* in (item, level) order while they fit
+//   k_order_apply    (tie rates per chunk, their prefix over the chunks, the
+//                    decisions); the first that does not fit is the split;
+//   k_greedy         the loss at the split and the LP bound, then the greedy
+//                    completion, one block-wide arg-min per take: the next
+//                    increment is the first one in solve order, after the last
+//                    one taken, that is its item's next increment and fits the
+//                    remaining capacity (every increment before it in that
+//                    order has already been passed over for good);
+//   k_final_chunks / the chosen options and the final loss.
+//   k_final_sum
+// Loss totals are tree sums over chunks of 1024 items added in chunk order,
+// as the host solver adds them.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -263,173 +270,325 @@ __device__ IncPos block_first(IncPos v, IncPos *s_warp, IncPos *s_out) {
     return r;
 }
 
-__global__ void __launch_bounds__(kSolveThreads, 1)
-    k_solve(HullDev H, const ProblemIn *__restrict__ pin, ProblemOut *__restrict__ pout,
-            const int64_t *__restrict__ item_begin, const unsigned long long *__restrict__ ratio_sums,
-            const unsigned long long *__restrict__ hist_w, const unsigned *__restrict__ hist_n,
-            uint8_t *__restrict__ level_all, uint8_t *__restrict__ choice_all) {
-    extern __shared__ __align__(16) unsigned char smem[];
+// ---- the solve of every (budget, ratio) problem, spread over the GPU --------
+//
+// A problem's items are cut into chunks of kTreeChunk (1024) items; the passes
+// over items run one CTA per chunk of every problem at once, and the steps
+// that need a whole problem (bucket selections, scans of chunk totals, the
+// greedy completion) run one CTA per problem.  Chunk totals are combined in
+// chunk order, so every sum and decision is the one-CTA-per-problem solve's.
+
+struct Chunk {
+    int32_t p;   // problem
+    int32_t c;   // chunk index within the problem
+};
+
+// Per-problem state carried between the launches.
+struct ProbState {
+    int64_t target;      // capacity for increments (cap - W0), -1 when infeasible
+    int64_t res;         // capacity left at and below the current key prefix
+    int64_t total;       // rate of every increment of the ratio
+    int64_t rem;         // capacity left after the ordered pass, then after the greedy takes
+    uint64_t prefix;     // split-key prefix (pbits bits); the split key K* once refined
+    uint64_t kfound;     // the key of a one-increment bucket
+    int64_t split_item;  // the LP split increment (-1: none)
+    double lp;
+    int32_t pbits;
+    uint32_t count;      // increments in the current bucket
+    int32_t has_split;   // 0: every increment fits
+    int32_t active;      // the split key is still being refined
+    int32_t split_level;
+    int32_t takes;
+};
+
+struct SolveArgs {
+    HullDev H;
+    const ProblemIn *pin;
+    ProblemOut *pout;
+    ProbState *state;
+    const int64_t *item_begin;
+    const unsigned long long *ratio_sums;
+    const unsigned long long *hist_w;   // coarse histograms [ratio][2^16]
+    const unsigned *hist_n;
+    unsigned long long *fine_w;         // fine histograms [problem][4096], zero between passes
+    unsigned *fine_n;
+    const Chunk *chunks;
+    const int32_t *chunk0;              // first chunk of each problem (n_problems + 1)
+    int64_t *chunk_i64;                 // per chunk: tie rates, then their exclusive prefix
+    int64_t *chunk_taken;               // per chunk: tie rates taken
+    double *chunk_sum;                  // per chunk: tree sum of the losses
+    uint8_t *level_all;                 // [budget][NI]
+    uint8_t *choice_all;                // [budget][NI]
+};
+
+struct ProbView {
+    int64_t i0, M;
+    const uint8_t *nv;
+};
+__device__ __forceinline__ ProbView prob_view(const SolveArgs &A, int p) {
+    const int r = A.pin[p].ratio;
+    ProbView v;
+    v.i0 = A.item_begin[r];
+    v.M = A.item_begin[r + 1] - v.i0;
+    v.nv = A.H.nv + v.i0;
+    return v;
+}
+__device__ __forceinline__ uint64_t key_of(const HullDev &H, int64_t i0, int64_t i, int l) {
+    return H.key[l * H.NI + i0 + i];
+}
+__device__ __forceinline__ int64_t dw_of(const HullDev &H, int64_t i0, int64_t i, int l) {
+    return H.w[(l + 1) * H.NI + i0 + i] - H.w[l * H.NI + i0 + i];
+}
+
+// 1. One CTA per problem: feasibility, and the coarse bucket of the LP split.
+__global__ void __launch_bounds__(kSolveThreads, 1) k_split_coarse(SolveArgs A) {
     __shared__ BlockScratch sc;
     __shared__ int s_bin;
     __shared__ int64_t s_above, s_total;
-    __shared__ uint64_t s_kstar;
-    __shared__ int64_t s_split_item;
-    __shared__ int s_split_level;
-    __shared__ IncPos s_warp[32];
-    __shared__ IncPos s_first;
-
-    const int tid = threadIdx.x;
-    const ProblemIn P = pin[blockIdx.x];
+    const int p = blockIdx.x;
+    const ProblemIn P = A.pin[p];
     const int r = P.ratio;
-    const int64_t i0 = item_begin[r], M = item_begin[r + 1] - i0;
-    const int64_t NI = H.NI;
-    const int64_t W0 = (int64_t)ratio_sums[2 * r], Wtop = (int64_t)ratio_sums[2 * r + 1];
-    ProblemOut out;
-    out.status = -1;
-    out.takes = 0;
-    out.objective = out.bytes = out.lp = 0.0;
-    out.bytes_min = units_to_bytes(W0, P.fixed);
-    out.bytes_top = units_to_bytes(Wtop, P.fixed);
+    const int64_t W0 = (int64_t)A.ratio_sums[2 * r], Wtop = (int64_t)A.ratio_sums[2 * r + 1];
+    ProbState st{};
+    st.split_item = -1;
     if (P.cap < 0 || W0 > P.cap) {
-        if (tid == 0) pout[blockIdx.x] = out;
+        st.target = -1;
+    } else {
+        st.target = P.cap - W0;
+        const unsigned long long *hw0 = A.hist_w + (size_t)r * kCoarseBins;
+        const bool has_split = block_find_crossing(
+            kCoarseBins, st.target, [&](int b) { return (int64_t)hw0[b]; }, sc, &s_bin, &s_above, &s_total);
+        st.total = s_total;
+        st.has_split = has_split ? 1 : 0;
+        if (has_split) {
+            st.prefix = (uint64_t)s_bin;
+            st.pbits = 16;
+            st.res = st.target - s_above;
+            st.count = A.hist_n[(size_t)r * kCoarseBins + s_bin];
+            st.active = 1;
+        } else {
+            st.res = st.target - s_total;   // every increment fits
+        }
+    }
+    if (threadIdx.x == 0) {
+        A.state[p] = st;
+        ProblemOut out{};
+        out.status = -1;
+        out.bytes_min = units_to_bytes(W0, P.fixed);
+        out.bytes_top = units_to_bytes(Wtop, P.fixed);
+        A.pout[p] = out;
+    }
+}
+
+// 2a. One CTA per chunk: the fine histogram of the increments in the current
+// bucket (kFineBits more key bits), or, when the bucket holds one increment,
+// its key.
+__global__ void __launch_bounds__(256) k_split_fine(SolveArgs A) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const Chunk ch = A.chunks[blockIdx.x];
+    const ProbState st = A.state[ch.p];
+    if (!st.active) return;
+    const ProbView v = prob_view(A, ch.p);
+    const int64_t lo = (int64_t)ch.c * kTreeChunk, hi = min(v.M, lo + kTreeChunk);
+    if (st.count == 1) {
+        for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+            const int n = v.nv[i];
+            for (int l = 0; l + 1 < n; l++) {
+                const uint64_t k = key_of(A.H, v.i0, i, l);
+                if ((k >> (64 - st.pbits)) == st.prefix) A.state[ch.p].kfound = k;   // the only one
+            }
+        }
         return;
     }
-    const int64_t target = P.cap - W0;
-    uint8_t *level = level_all + (int64_t)P.budget * NI + i0;
-    const uint8_t *nv = H.nv + i0;
-    auto key_at = [&](int64_t i, int l) { return H.key[l * NI + i0 + i]; };
-    auto dw_at = [&](int64_t i, int l) { return H.w[(l + 1) * NI + i0 + i] - H.w[l * NI + i0 + i]; };
-
-    // ---- 1. coarse bucket of the split
-    const unsigned long long *hw0 = hist_w + (size_t)r * kCoarseBins;
-    const bool has_split = block_find_crossing(
-        kCoarseBins, target, [&](int b) { return (int64_t)hw0[b]; }, sc, &s_bin, &s_above, &s_total);
-    int64_t res = 0;   // capacity left for the increments at or below the current prefix
-    if (has_split) {
-        uint64_t prefix = (uint64_t)s_bin;
-        int pbits = 16;
-        res = target - s_above;
-        unsigned count = hist_n[(size_t)r * kCoarseBins + s_bin];
-        uint64_t *fw = reinterpret_cast<uint64_t *>(smem);
-        unsigned *fc = reinterpret_cast<unsigned *>(smem + kFineBins * sizeof(uint64_t));
-        // ---- 2. the split key, kFineBits per pass
-        while (pbits < 64) {
-            __syncthreads();
-            if (count == 1) {
-                for (int64_t i = tid; i < M; i += kSolveThreads) {
-                    const int n = nv[i];
-#pragma unroll
-                    for (int l = 0; l < kMaxVerts - 1; l++) {
-                        if (l + 1 >= n) break;
-                        const uint64_t k = key_at(i, l);
-                        if ((k >> (64 - pbits)) == prefix) s_kstar = k;
-                    }
-                }
-                __syncthreads();
-                prefix = s_kstar;
-                pbits = 64;
-                break;
-            }
-            const int shift = 64 - pbits - kFineBits;
-            for (int b = tid; b < kFineBins; b += kSolveThreads) {
-                fw[b] = 0ull;
-                fc[b] = 0u;
-            }
-            __syncthreads();
-            for (int64_t i = tid; i < M; i += kSolveThreads) {
-                const int n = nv[i];
-#pragma unroll
-                for (int l = 0; l < kMaxVerts - 1; l++) {
-                    if (l + 1 >= n) break;
-                    const uint64_t k = key_at(i, l);
-                    if ((k >> (shift + kFineBits)) == prefix) {
-                        const int b = (int)((k >> shift) & (kFineBins - 1));
-                        atomicAdd(reinterpret_cast<unsigned long long *>(&fw[b]),
-                                  (unsigned long long)dw_at(i, l));
-                        atomicAdd(&fc[b], 1u);
-                    }
-                }
-            }
-            __syncthreads();
-            block_find_crossing(
-                kFineBins, res, [&](int b) { return (int64_t)fw[b]; }, sc, &s_bin, &s_above, &s_total);
-            prefix = (prefix << kFineBits) | (uint64_t)s_bin;
-            pbits += kFineBits;
-            res -= s_above;
-            count = fc[s_bin];
-        }
-        if (tid == 0) s_kstar = prefix;
-    }
-    if (tid == 0) {
-        s_split_item = -1;
-        s_split_level = 0;
+    uint64_t *fw = reinterpret_cast<uint64_t *>(smem);
+    unsigned *fc = reinterpret_cast<unsigned *>(smem + kFineBins * sizeof(uint64_t));
+    for (int b = threadIdx.x; b < kFineBins; b += blockDim.x) {
+        fw[b] = 0ull;
+        fc[b] = 0u;
     }
     __syncthreads();
-    const uint64_t kstar = has_split ? s_kstar : 0ull;
-    if (!has_split) res = target - s_total;   // every increment fits
-
-    // ---- 3. ordered pass: whole increments above K*, ties in order, the split
-    int64_t carry = 0, my_taken = 0;
-    double d_split = 0.0;
-    for (int64_t c0 = 0; c0 < M; c0 += kSolveThreads) {
-        const int64_t i = c0 + tid;
-        int lvl = 0, tfirst = -1, tcount = 0, n = 0;
-        int64_t tsum = 0;
-        if (i < M) {
-            n = nv[i];
-            if (!has_split) {
-                lvl = n - 1;
-            } else {
-#pragma unroll
-                for (int l = 0; l < kMaxVerts - 1; l++) {
-                    if (l + 1 >= n) break;
-                    const uint64_t k = key_at(i, l);
-                    if (k > kstar) {
-                        lvl = l + 1;
-                    } else if (k == kstar) {
-                        if (tfirst < 0) tfirst = l;
-                        tcount++;
-                        tsum += dw_at(i, l);
-                    }
-                }
+    const int shift = 64 - st.pbits - kFineBits;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const int n = v.nv[i];
+        for (int l = 0; l + 1 < n; l++) {
+            const uint64_t k = key_of(A.H, v.i0, i, l);
+            if ((k >> (shift + kFineBits)) == st.prefix) {
+                const int b = (int)((k >> shift) & (kFineBins - 1));
+                atomicAdd(reinterpret_cast<unsigned long long *>(&fw[b]), (unsigned long long)dw_of(A.H, v.i0, i, l));
+                atomicAdd(&fc[b], 1u);
             }
         }
-        int64_t ctot;
-        const int64_t incl = block_incl_scan(tsum, sc, ctot);
-        int64_t pb = carry + (incl - tsum);   // tie rate before this item's first tie
-        for (int q = 0; q < tcount; q++) {
-            const int l = tfirst + q;
-            const int64_t dw = dw_at(i, l);
-            if (pb + dw <= res) {
-                lvl = l + 1;
-                my_taken += dw;
-            } else if (pb <= res) {
-                s_split_item = i;
-                s_split_level = l;
-            }
-            pb += dw;
-        }
-        carry += ctot;
-        double v = 0.0;
-        if (i < M) {
-            level[i] = (uint8_t)lvl;
-            v = H.d[lvl * NI + i0 + i];
-        }
-        const double t = block_tree_sum(v, sc);
-        if (tid == 0) d_split = d_split + t;
     }
-    const int64_t taken_ties = block_sum_i64(my_taken, sc);
-    int64_t rem = res - taken_ties;
+    __syncthreads();
+    unsigned long long *gw = A.fine_w + (size_t)ch.p * kFineBins;
+    unsigned *gc = A.fine_n + (size_t)ch.p * kFineBins;
+    for (int b = threadIdx.x; b < kFineBins; b += blockDim.x)
+        if (fc[b]) {
+            atomicAdd(&gw[b], (unsigned long long)fw[b]);
+            atomicAdd(&gc[b], fc[b]);
+        }
+}
+
+// 2b. One CTA per problem: the fine bucket of the split (or the key found),
+// and a clean fine histogram for the next pass.
+__global__ void __launch_bounds__(kSolveThreads, 1) k_split_select(SolveArgs A) {
+    __shared__ BlockScratch sc;
+    __shared__ int s_bin;
+    __shared__ int64_t s_above, s_total;
+    const int p = blockIdx.x;
+    ProbState st = A.state[p];
+    if (!st.active) return;
+    unsigned long long *gw = A.fine_w + (size_t)p * kFineBins;
+    unsigned *gc = A.fine_n + (size_t)p * kFineBins;
+    if (st.count == 1) {
+        st.prefix = st.kfound;
+        st.pbits = 64;
+        st.active = 0;
+    } else {
+        block_find_crossing(kFineBins, st.res, [&](int b) { return (int64_t)gw[b]; }, sc, &s_bin, &s_above,
+                            &s_total);
+        st.prefix = (st.prefix << kFineBits) | (uint64_t)s_bin;
+        st.pbits += kFineBits;
+        st.res -= s_above;
+        st.count = gc[s_bin];
+        if (st.pbits >= 64) st.active = 0;
+        __syncthreads();   // every thread has read the histogram
+        for (int b = threadIdx.x; b < kFineBins; b += kSolveThreads) {
+            gw[b] = 0ull;
+            gc[b] = 0u;
+        }
+    }
+    if (threadIdx.x == 0) A.state[p] = st;
+}
+
+// Per item of the ordered pass: the level reached by the increments above K*,
+// and the increments equal to K* (the ties), which are taken in (item, level)
+// order while they fit.
+struct ItemTies {
+    int lvl, tfirst, tcount, n;
+    int64_t tsum;
+};
+__device__ __forceinline__ ItemTies item_ties(const SolveArgs &A, const ProbView &v, int64_t i,
+                                              const ProbState &st) {
+    ItemTies t{0, -1, 0, 0, 0};
+    if (i >= v.M) return t;
+    t.n = v.nv[i];
+    if (!st.has_split) {
+        t.lvl = t.n - 1;
+        return t;
+    }
+    const uint64_t kstar = st.prefix;
+#pragma unroll
+    for (int l = 0; l < kMaxVerts - 1; l++) {
+        if (l + 1 >= t.n) break;
+        const uint64_t k = key_of(A.H, v.i0, i, l);
+        if (k > kstar) {
+            t.lvl = l + 1;
+        } else if (k == kstar) {
+            if (t.tfirst < 0) t.tfirst = l;
+            t.tcount++;
+            t.tsum += dw_of(A.H, v.i0, i, l);
+        }
+    }
+    return t;
+}
+
+// 3a. One CTA per chunk: the tie rate of the chunk.
+__global__ void __launch_bounds__(kSolveThreads, 1) k_order_ties(SolveArgs A) {
+    __shared__ BlockScratch sc;
+    const Chunk ch = A.chunks[blockIdx.x];
+    const ProbState st = A.state[ch.p];
+    if (st.target < 0) return;
+    const ProbView v = prob_view(A, ch.p);
+    const ItemTies t = item_ties(A, v, (int64_t)ch.c * kTreeChunk + threadIdx.x, st);
+    const int64_t total = block_sum_i64(t.tsum, sc);
+    if (threadIdx.x == 0) A.chunk_i64[blockIdx.x] = total;
+}
+
+// 3b. One CTA per problem: exclusive prefix of the chunks' tie rates.
+__global__ void __launch_bounds__(kSolveThreads, 1) k_order_scan(SolveArgs A) {
+    __shared__ BlockScratch sc;
+    const int p = blockIdx.x;
+    if (A.state[p].target < 0) return;
+    const int c0 = A.chunk0[p], c1 = A.chunk0[p + 1];
+    int64_t carry = 0;
+    for (int b = c0; b < c1; b += kSolveThreads) {
+        const int c = b + threadIdx.x;
+        const int64_t x = c < c1 ? A.chunk_i64[c] : 0;
+        int64_t tot;
+        const int64_t incl = block_incl_scan(x, sc, tot);
+        if (c < c1) A.chunk_i64[c] = carry + incl - x;
+        carry += tot;
+    }
+}
+
+// 3c. One CTA per chunk: whole increments above K*, ties in order while they
+// fit, the split; the levels and the chunk's loss tree sum.
+__global__ void __launch_bounds__(kSolveThreads, 1) k_order_apply(SolveArgs A) {
+    __shared__ BlockScratch sc;
+    const Chunk ch = A.chunks[blockIdx.x];
+    const ProbState st = A.state[ch.p];
+    if (st.target < 0) return;
+    const ProbView v = prob_view(A, ch.p);
+    const int64_t i = (int64_t)ch.c * kTreeChunk + threadIdx.x;
+    ItemTies t = item_ties(A, v, i, st);
+    int64_t ctot;
+    const int64_t incl = block_incl_scan(t.tsum, sc, ctot);
+    int64_t pb = A.chunk_i64[blockIdx.x] + (incl - t.tsum);   // tie rate before this item's first tie
+    int64_t my_taken = 0;
+    for (int q = 0; q < t.tcount; q++) {
+        const int l = t.tfirst + q;
+        const int64_t dw = dw_of(A.H, v.i0, i, l);
+        if (pb + dw <= st.res) {
+            t.lvl = l + 1;
+            my_taken += dw;
+        } else if (pb <= st.res) {
+            A.state[ch.p].split_item = i;   // the one tie that straddles the capacity
+            A.state[ch.p].split_level = l;
+        }
+        pb += dw;
+    }
+    double d = 0.0;
+    if (i < v.M) {
+        A.level_all[(int64_t)A.pin[ch.p].budget * A.H.NI + v.i0 + i] = (uint8_t)t.lvl;
+        d = A.H.d[t.lvl * A.H.NI + v.i0 + i];
+    }
+    const double tsum = block_tree_sum(d, sc);
+    const int64_t taken = block_sum_i64(my_taken, sc);
+    if (threadIdx.x == 0) {
+        A.chunk_sum[blockIdx.x] = tsum;
+        A.chunk_taken[blockIdx.x] = taken;
+    }
+}
+
+// 3d + 4. One CTA per problem: the loss at the split and the LP bound (chunk
+// sums in chunk order), then the greedy completion, one block-wide arg-min per
+// take: the next increment is the first one in solve order, after the last
+// one taken, that is its item's next increment and fits the capacity left.
+__global__ void __launch_bounds__(kSolveThreads, 1) k_greedy(SolveArgs A) {
+    __shared__ IncPos s_warp[32];
+    __shared__ IncPos s_first;
+    const int p = blockIdx.x;
+    ProbState st = A.state[p];
+    if (st.target < 0) return;
+    const ProbView v = prob_view(A, p);
+    const int c0 = A.chunk0[p], c1 = A.chunk0[p + 1];
+    double d_split = 0.0;
+    int64_t taken = 0;
+    for (int c = c0; c < c1; c++) {   // every thread, in chunk order
+        d_split = d_split + A.chunk_sum[c];
+        taken += A.chunk_taken[c];
+    }
+    int64_t rem = st.res - taken;
     double lp = d_split;
-    const int64_t si = s_split_item;
-    if (si >= 0) {
-        const int sl = s_split_level;
-        const double frac = (double)rem / (double)dw_at(si, sl);
-        const double dd = H.d[sl * NI + i0 + si] - H.d[(sl + 1) * NI + i0 + si];
+    if (st.split_item >= 0) {
+        const int64_t si = st.split_item;
+        const int sl = st.split_level;
+        const double frac = (double)rem / (double)dw_of(A.H, v.i0, si, sl);
+        const double dd = A.H.d[sl * A.H.NI + v.i0 + si] - A.H.d[(sl + 1) * A.H.NI + v.i0 + si];
         if (frac > 0) lp = lp - frac * dd;
     }
-
-    // ---- 4. greedy completion
+    uint8_t *level = A.level_all + (int64_t)A.pin[p].budget * A.H.NI + v.i0;
     IncPos last;
     last.key = 0;
     last.item = -1;
@@ -441,51 +600,70 @@ __global__ void __launch_bounds__(kSolveThreads, 1)
         best.item = -1;
         best.level = 0;
 #pragma unroll 4
-        for (int64_t i = tid; i < M; i += kSolveThreads) {
+        for (int64_t i = threadIdx.x; i < v.M; i += kSolveThreads) {
             const int lvl = level[i];
-            if (lvl + 1 >= nv[i]) continue;
+            if (lvl + 1 >= v.nv[i]) continue;
             IncPos c;
-            c.key = key_at(i, lvl);
+            c.key = key_of(A.H, v.i0, i, lvl);
             c.item = i;
             c.level = lvl;
             if (last.item >= 0 && !inc_first(last, c)) continue;   // passed over already
-            if (dw_at(i, lvl) > rem) continue;
+            if (dw_of(A.H, v.i0, i, lvl) > rem) continue;
             if (inc_first(c, best)) best = c;
         }
         const IncPos f = block_first(best, s_warp, &s_first);
         if (f.item < 0) break;
-        if (tid == 0) level[f.item] = (uint8_t)(f.level + 1);
-        rem -= dw_at(f.item, f.level);
+        if (threadIdx.x == 0) level[f.item] = (uint8_t)(f.level + 1);
+        rem -= dw_of(A.H, v.i0, f.item, f.level);
         last = f;
         takes++;
         __syncthreads();
     }
-
-    // ---- 5. choice and final loss
-    double obj = 0.0;
-    uint8_t *choice = choice_all + (int64_t)P.budget * NI + i0;
-    for (int64_t c0 = 0; c0 < M; c0 += kSolveThreads) {
-        const int64_t i = c0 + tid;
-        double v = 0.0;
-        if (i < M) {
-            const int lvl = level[i];
-            choice[i] = (uint8_t)H.opt[lvl * NI + i0 + i];
-            v = H.d[lvl * NI + i0 + i];
-        }
-        const double t = block_tree_sum(v, sc);
-        if (tid == 0) obj = obj + t;
-    }
-    if (tid == 0) {
-        out.status = 0;
-        out.takes = takes;
-        out.objective = obj;
-        out.bytes = units_to_bytes(W0 + (target - rem), P.fixed);
-        out.lp = lp;
-        pout[blockIdx.x] = out;
+    if (threadIdx.x == 0) {
+        A.state[p].rem = rem;
+        A.state[p].lp = lp;
+        A.state[p].takes = takes;
     }
 }
 
-constexpr size_t kSolveSmem = kFineBins * (sizeof(uint64_t) + sizeof(unsigned));   // fine histogram
+// 5a. One CTA per chunk: the chosen options and the chunk's final loss.
+__global__ void __launch_bounds__(kSolveThreads, 1) k_final_chunks(SolveArgs A) {
+    __shared__ BlockScratch sc;
+    const Chunk ch = A.chunks[blockIdx.x];
+    if (A.state[ch.p].target < 0) return;
+    const ProbView v = prob_view(A, ch.p);
+    const int64_t i = (int64_t)ch.c * kTreeChunk + threadIdx.x;
+    const int64_t off = (int64_t)A.pin[ch.p].budget * A.H.NI + v.i0;
+    double d = 0.0;
+    if (i < v.M) {
+        const int lvl = A.level_all[off + i];
+        A.choice_all[off + i] = (uint8_t)A.H.opt[lvl * A.H.NI + v.i0 + i];
+        d = A.H.d[lvl * A.H.NI + v.i0 + i];
+    }
+    const double tsum = block_tree_sum(d, sc);
+    if (threadIdx.x == 0) A.chunk_sum[blockIdx.x] = tsum;
+}
+
+// 5b. One thread per problem: the final loss (chunk sums in chunk order).
+__global__ void k_final_sum(SolveArgs A, int n_problems) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n_problems) return;
+    const ProbState st = A.state[p];
+    if (st.target < 0) return;
+    double obj = 0.0;
+    for (int c = A.chunk0[p]; c < A.chunk0[p + 1]; c++) obj = obj + A.chunk_sum[c];
+    const int r = A.pin[p].ratio;
+    const int64_t W0 = (int64_t)A.ratio_sums[2 * r];
+    ProblemOut out = A.pout[p];
+    out.status = 0;
+    out.takes = st.takes;
+    out.objective = obj;
+    out.bytes = units_to_bytes(W0 + (st.target - st.rem), A.pin[p].fixed);
+    out.lp = st.lp;
+    A.pout[p] = out;
+}
+
+constexpr size_t kFineSmem = kFineBins * (sizeof(uint64_t) + sizeof(unsigned));   // fine histogram
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -559,12 +737,33 @@ extern "C" mgs_status mgs_solve_budgets_device(mgs_ctx *ctx, const void *table,
     const size_t zero_bytes = off - o_zero;
     const size_t o_bits = take(sizeof(int32_t) * nb);
     const size_t o_ib = take(sizeof(int64_t) * (nr + 1));
+    // chunks of kTreeChunk items of every problem
+    std::vector<Chunk> chunks;
+    std::vector<int32_t> chunk0(P + 1, 0);
+    for (int p = 0; p < P; p++) {
+        const int r = pin[p].ratio;
+        const int64_t M = layout->item_begin[r + 1] - layout->item_begin[r];
+        chunk0[p] = (int32_t)chunks.size();
+        for (int64_t c = 0; c * kTreeChunk < M; c++) chunks.push_back(Chunk{p, (int32_t)c});
+    }
+    chunk0[P] = (int32_t)chunks.size();
+    const int64_t NC = std::max<int64_t>((int64_t)chunks.size(), 1);
     const size_t o_pin = take(sizeof(ProblemIn) * P);
     const size_t o_pout = take(sizeof(ProblemOut) * P);
+    const size_t o_state = take(sizeof(ProbState) * P);
+    const size_t o_chunks = take(sizeof(Chunk) * NC);
+    const size_t o_chunk0 = take(sizeof(int32_t) * (P + 1));
+    const size_t o_ci64 = take(sizeof(int64_t) * NC);
+    const size_t o_ctaken = take(sizeof(int64_t) * NC);
+    const size_t o_csum = take(sizeof(double) * NC);
+    const size_t o_fz = off;   // zeroed: fine histograms
+    const size_t o_fw = take(sizeof(unsigned long long) * kFineBins * P);
+    const size_t o_fn = take(sizeof(unsigned) * kFineBins * P);
+    const size_t fine_bytes = off - o_fz;
     const size_t o_level = take((size_t)n_budgets * NI);
     const size_t o_choice = take((size_t)n_budgets * NI);
     char *ws = nullptr;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&ws), off, st);
+    cudaError_t e = dev_malloc_async(reinterpret_cast<void **>(&ws), off, st);
     if (e != cudaSuccess) {
         cudaGetLastError();
         set_error("device workspace of %zu bytes: %s", off, cudaGetErrorString(e));
@@ -579,10 +778,15 @@ extern "C" mgs_status mgs_solve_budgets_device(mgs_ctx *ctx, const void *table,
     const char *tab = on_device ? static_cast<const char *>(table) : ws + o_tab;
     if (!on_device) MGS_CUDA_TRY(cudaMemcpyAsync(ws + o_tab, table, layout->total_bytes, cudaMemcpyHostToDevice, st));
     MGS_CUDA_TRY(cudaMemsetAsync(ws + o_zero, 0, zero_bytes, st));
+    MGS_CUDA_TRY(cudaMemsetAsync(ws + o_fz, 0, fine_bytes, st));
     MGS_CUDA_TRY(cudaMemcpyAsync(ws + o_bits, grid->bits, sizeof(int32_t) * nb, cudaMemcpyHostToDevice, st));
     MGS_CUDA_TRY(cudaMemcpyAsync(ws + o_ib, layout->item_begin, sizeof(int64_t) * (nr + 1),
                                  cudaMemcpyHostToDevice, st));
     MGS_CUDA_TRY(cudaMemcpyAsync(ws + o_pin, pin.data(), sizeof(ProblemIn) * P, cudaMemcpyHostToDevice, st));
+    MGS_CUDA_TRY(cudaMemcpyAsync(ws + o_chunks, chunks.data(), sizeof(Chunk) * chunks.size(),
+                                 cudaMemcpyHostToDevice, st));
+    MGS_CUDA_TRY(cudaMemcpyAsync(ws + o_chunk0, chunk0.data(), sizeof(int32_t) * (P + 1), cudaMemcpyHostToDevice,
+                                 st));
 
     TableDev T;
     T.sse = reinterpret_cast<const double *>(tab + layout->off_sse);
@@ -607,13 +811,50 @@ extern "C" mgs_status mgs_solve_budgets_device(mgs_ctx *ctx, const void *table,
                                                         reinterpret_cast<const int32_t *>(ws + o_bits),
                                                         d_ib, nr, sums, hw, hn);
     MGS_CUDA_TRY(cudaGetLastError());
-    MGS_CUDA_TRY(cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSolveSmem));
-    k_solve<<<P, kSolveThreads, kSolveSmem, st>>>(H, reinterpret_cast<const ProblemIn *>(ws + o_pin),
-                                                  reinterpret_cast<ProblemOut *>(ws + o_pout), d_ib, sums,
-                                                  hw, hn, reinterpret_cast<uint8_t *>(ws + o_level),
-                                                  reinterpret_cast<uint8_t *>(ws + o_choice));
+    SolveArgs A;
+    A.H = H;
+    A.pin = reinterpret_cast<const ProblemIn *>(ws + o_pin);
+    A.pout = reinterpret_cast<ProblemOut *>(ws + o_pout);
+    A.state = reinterpret_cast<ProbState *>(ws + o_state);
+    A.item_begin = d_ib;
+    A.ratio_sums = sums;
+    A.hist_w = hw;
+    A.hist_n = hn;
+    A.fine_w = reinterpret_cast<unsigned long long *>(ws + o_fw);
+    A.fine_n = reinterpret_cast<unsigned *>(ws + o_fn);
+    A.chunks = reinterpret_cast<const Chunk *>(ws + o_chunks);
+    A.chunk0 = reinterpret_cast<const int32_t *>(ws + o_chunk0);
+    A.chunk_i64 = reinterpret_cast<int64_t *>(ws + o_ci64);
+    A.chunk_taken = reinterpret_cast<int64_t *>(ws + o_ctaken);
+    A.chunk_sum = reinterpret_cast<double *>(ws + o_csum);
+    A.level_all = reinterpret_cast<uint8_t *>(ws + o_level);
+    A.choice_all = reinterpret_cast<uint8_t *>(ws + o_choice);
+    const unsigned nc = (unsigned)chunks.size();
+    int launches = 1;
+    k_split_coarse<<<P, kSolveThreads, 0, st>>>(A);
+    launches++;
+    // the split key: 16 bits from the coarse histogram, kFineBits per pass after
+    for (int pass = 0; pass < (64 - 16 + kFineBits - 1) / kFineBits && nc > 0; pass++) {
+        k_split_fine<<<nc, 256, kFineSmem, st>>>(A);
+        k_split_select<<<P, kSolveThreads, 0, st>>>(A);
+        launches += 2;
+    }
+    if (nc > 0) {
+        k_order_ties<<<nc, kSolveThreads, 0, st>>>(A);
+        k_order_scan<<<P, kSolveThreads, 0, st>>>(A);
+        k_order_apply<<<nc, kSolveThreads, 0, st>>>(A);
+        launches += 3;
+    }
+    k_greedy<<<P, kSolveThreads, 0, st>>>(A);
+    launches++;
+    if (nc > 0) {
+        k_final_chunks<<<nc, kSolveThreads, 0, st>>>(A);
+        launches++;
+    }
+    k_final_sum<<<(P + 127) / 128, 128, 0, st>>>(A, P);
+    launches++;
     MGS_CUDA_TRY(cudaGetLastError());
-    count_launches(2);
+    count_launches(launches);
     std::vector<ProblemOut> po(P);
     MGS_CUDA_TRY(cudaMemcpyAsync(po.data(), ws + o_pout, sizeof(ProblemOut) * P, cudaMemcpyDeviceToHost, st));
     MGS_CUDA_TRY(cudaStreamSynchronize(st));

@@ -378,7 +378,7 @@ extern "C" mgs_status mgs_vq_assign(mgs_ctx *ctx, const float *x, int64_t n, int
         TcScratch T;
         MGS_TRY(tc_scratch(K, D, st, &base, &T));
         mgs_status s = vq_assign_tc(x, n, D, nullptr, codebook, K, index_out, score_out, T.tiles, T.cmax2,
-                                    T.stats, T.err, st);
+                                    T.stats, T.err, ctx->vq_wait_cycles, st);
         if (s == MGS_OK) s = tc_finish(ctx, T, n * (int64_t)K, st);
         cudaFreeAsync(base, st);
         return s;
@@ -396,6 +396,16 @@ extern "C" mgs_status mgs_vq_assign(mgs_ctx *ctx, const float *x, int64_t n, int
     if (s == MGS_OK) s = assign_launch(x, n, D, nullptr, codebook, cc, K, index_out, score_out, st);
     cudaFreeAsync(cc, st);
     return s;
+}
+
+extern "C" mgs_status mgs_vq_set_wait_limit(mgs_ctx *ctx, int64_t cycles) {
+    clear_error();
+    if (!ctx || cycles < 0) {
+        set_error("ctx must be non-NULL and cycles >= 0");
+        return MGS_ERR_INVALID_ARG;
+    }
+    ctx->vq_wait_cycles = (long long)cycles;
+    return MGS_OK;
 }
 
 extern "C" mgs_status mgs_vq_set_tensor_cores(mgs_ctx *ctx, int32_t enable) {
@@ -494,7 +504,7 @@ extern "C" mgs_status mgs_vq_train(mgs_ctx *ctx, const float *x, int64_t n, int3
         const int32_t *rows = batches + (int64_t)t * batch;
         int32_t *a = assign_out ? assign_out + (int64_t)t * batch : a_ws;
         if (ctx->vq_tensor) {
-            s = vq_assign_tc(x, batch, D, rows, codebook, K, a, nullptr, T.tiles, T.cmax2, T.stats, T.err, st);
+            s = vq_assign_tc(x, batch, D, rows, codebook, K, a, nullptr, T.tiles, T.cmax2, T.stats, T.err, ctx->vq_wait_cycles, st);
         } else {
             k_vq_norms<<<(K + 255) / 256, 256, 0, st>>>(codebook, K, D, cc);
             count_launches(1);

@@ -63,11 +63,25 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
 }
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+// try_wait suspends the thread until the phase completes or `ns` nanoseconds
+// have passed, whichever comes first.
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity, uint32_t ns) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(ns)
+        : "memory");
+    return ok != 0;
+}
+// Whether the phase with the given parity has completed (does not wait).
+__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
         : "r"(smem_u32(bar)), "r"(parity)
@@ -76,13 +90,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 }
 // Bounded wait for the phase with the given parity: false once `limit` clock
 // cycles have passed, or at once when another CTA has raised *err (if err).
+// The thread suspends (up to 1 us at a time) only while more than 4096 cycles
+// of the limit remain; closer to the limit it polls, so that a limit of a few
+// cycles runs out however fast a suspended wait would have been woken.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, const unsigned int *err,
                                           long long limit) {
     const long long t0 = clock64();
     for (;;) {
-        if (mbar_try_wait(bar, parity)) return true;
+        if (mbar_test_wait(bar, parity)) return true;
         if (err && *(const volatile unsigned int *)err) return false;
-        if (clock64() - t0 > limit) return false;
+        const long long el = clock64() - t0;
+        if (el > limit) return false;
+        if (limit - el > 4096 && mbar_try_wait(bar, parity, 1000u)) return true;
     }
 }
 // One bulk copy global -> this CTA's shared memory, completing on `bar`.
@@ -212,7 +231,7 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm)
                    const unsigned char *__restrict__ tiles, int32_t K, const float *__restrict__ cb,
                    const unsigned int *__restrict__ cmax2, int32_t *__restrict__ idx_out,
                    float *__restrict__ score_out, unsigned long long *__restrict__ stats,
-                   unsigned int *__restrict__ err) {
+                   unsigned int *__restrict__ err, long long wait_cycles) {
     constexpr int TB = tile_bytes(DP), TS = tile_stride(DP);
     constexpr int SBO = 32 * DP, LBO = 128;
     constexpr uint32_t IDESC = idesc_tf32(kTcM, kTcN);
@@ -283,7 +302,7 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm)
     for (int tt = 0; tt < ntiles; tt++) {
         const int buf = tt % kTcBufs;
         unsigned char *tileB = sB + buf * TS;
-        if (!mbar_wait(&bar_full[buf], (uint32_t)((tt / kTcBufs) & 1), err, kWaitCycles)) s_abort = 1;
+        if (!mbar_wait(&bar_full[buf], (uint32_t)((tt / kTcBufs) & 1), err, wait_cycles)) s_abort = 1;
         if (t == 0 && !s_abort) {
             tc_fence_after();
             const uint32_t b_base = smem_u32(tileB);
@@ -296,7 +315,7 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm)
         }
         __syncthreads();
         if (s_abort) break;
-        if (!mbar_wait(&bar_mma, (uint32_t)(tt & 1), err, kWaitCycles)) s_abort = 1;
+        if (!mbar_wait(&bar_mma, (uint32_t)(tt & 1), err, wait_cycles)) s_abort = 1;
         if (t == 0 && !s_abort) mma_pending = -1;
         __syncthreads();
         if (s_abort) break;
@@ -397,7 +416,7 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm)
 template <int DP>
 mgs_status launch_tc(const float *x, int64_t n, int32_t D, const int32_t *rows, const float *cb,
                      int32_t K, int32_t *idx, float *score, unsigned char *tiles, unsigned int *cmax2,
-                     unsigned long long *stats, unsigned int *err, cudaStream_t st) {
+                     unsigned long long *stats, unsigned int *err, long long wait_cycles, cudaStream_t st) {
     const int64_t ntiles = ((int64_t)K + kTcN - 1) / kTcN;
     MGS_CUDA_TRY(cudaMemsetAsync(cmax2, 0, sizeof(unsigned int), st));
     k_vq_tc_prep<DP><<<(unsigned)((ntiles * kTcN + 255) / 256), 256, 0, st>>>(cb, K, D, tiles, cmax2);
@@ -428,7 +447,8 @@ mgs_status launch_tc(const float *x, int64_t n, int32_t D, const int32_t *rows, 
     const int64_t grid = (n + kTcM - 1) / kTcM;
     if (grid > 0)
         k_vq_assign_tc<DP><<<(unsigned)grid, kTcThreads, smem, st>>>(x, n, D, rows, tiles, K, cb, cmax2, idx,
-                                                                     score, stats, err);
+                                                                     score, stats, err,
+                                                                     wait_cycles > 0 ? wait_cycles : kWaitCycles);
     count_launches(grid > 0 ? 2 : 1);
     MGS_CUDA_TRY(cudaGetLastError());
     return MGS_OK;
@@ -444,11 +464,11 @@ size_t vq_tc_workspace(int32_t K, int32_t D) {
 
 mgs_status vq_assign_tc(const float *x, int64_t n, int32_t D, const int32_t *rows, const float *cb,
                         int32_t K, int32_t *idx, float *score, unsigned char *tiles, unsigned int *cmax2,
-                        unsigned long long *stats, unsigned int *err, cudaStream_t st) {
-    if (D <= 16) return launch_tc<16>(x, n, D, rows, cb, K, idx, score, tiles, cmax2, stats, err, st);
-    if (D <= 32) return launch_tc<32>(x, n, D, rows, cb, K, idx, score, tiles, cmax2, stats, err, st);
-    if (D <= 48) return launch_tc<48>(x, n, D, rows, cb, K, idx, score, tiles, cmax2, stats, err, st);
-    return launch_tc<64>(x, n, D, rows, cb, K, idx, score, tiles, cmax2, stats, err, st);
+                        unsigned long long *stats, unsigned int *err, long long wait_cycles, cudaStream_t st) {
+    if (D <= 16) return launch_tc<16>(x, n, D, rows, cb, K, idx, score, tiles, cmax2, stats, err, wait_cycles, st);
+    if (D <= 32) return launch_tc<32>(x, n, D, rows, cb, K, idx, score, tiles, cmax2, stats, err, wait_cycles, st);
+    if (D <= 48) return launch_tc<48>(x, n, D, rows, cb, K, idx, score, tiles, cmax2, stats, err, wait_cycles, st);
+    return launch_tc<64>(x, n, D, rows, cb, K, idx, score, tiles, cmax2, stats, err, wait_cycles, st);
 }
 
 }  // namespace mgs

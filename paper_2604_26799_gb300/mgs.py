@@ -86,7 +86,7 @@ class mgs_server_opts(ctypes.Structure):
 class mgs_job(ctypes.Structure):
     _fields_ = [("attrs", ctypes.c_void_p), ("importance", ctypes.c_void_p), ("n", ctypes.c_int64),
                 ("n_channels", ctypes.c_int32), ("grid", mgs_grid), ("budget_bytes", ctypes.c_double),
-                ("opts", mgs_solve_opts)]
+                ("opts", mgs_solve_opts), ("table_out", ctypes.c_void_p)]
 
 
 class mgs_job_result(ctypes.Structure):
@@ -114,6 +114,11 @@ _SIGS = {
                              ctypes.POINTER(mgs_table_layout)],
     "mgs_build_cost_table": [_P, _P, ctypes.POINTER(mgs_grid), _P, _P],
     "mgs_build_cost_table_plain": [_P, _P, ctypes.POINTER(mgs_grid), _P, _P],
+    "mgs_debug_fail_allocation": [ctypes.c_int64],
+    "mgs_debug_allocations": [],
+    "mgs_vq_set_wait_limit": [_P, ctypes.c_int64],
+    "mgs_build_cost_table_probe": [_P, _P, ctypes.POINTER(mgs_grid), _P, _P, ctypes.c_int64, _P,
+                                   ctypes.c_int64, _P],
     "mgs_build_cost_tables_batched": [_P, ctypes.c_int32, _P, _P, _P, _P],
     "mgs_quantize_groups": [_P, _P, ctypes.c_int64, ctypes.c_int32, _P, _P, _P, _P],
     "mgs_quantize_groups_noalloc": [_P, _P, ctypes.c_int64, ctypes.c_int32, _P, _P, _P, _P],
@@ -159,7 +164,7 @@ _SIGS = {
 }
 _RESTYPE = {"mgs_last_error": ctypes.c_char_p, "mgs_version": ctypes.c_char_p,
             "mgs_tile_config_name": ctypes.c_char_p, "mgs_tile_config_count": ctypes.c_int32,
-            "mgs_kernel_launches": ctypes.c_int64, "mgs_encode_bound": ctypes.c_int64}
+            "mgs_kernel_launches": ctypes.c_int64, "mgs_debug_allocations": ctypes.c_int64, "mgs_encode_bound": ctypes.c_int64}
 
 
 def lib():
@@ -216,6 +221,19 @@ def mgs_version() -> str:
     return lib().mgs_version().decode()
 
 
+def mgs_debug_fail_allocation(nth: int):
+    """Make the nth device allocation from now on fail (0 disarms); tests only."""
+    _check(lib().mgs_debug_fail_allocation(int(nth)))
+
+
+def mgs_debug_allocations() -> int:
+    return int(lib().mgs_debug_allocations())
+
+
+def mgs_vq_set_wait_limit(ctx: int, cycles: int):
+    _check(lib().mgs_vq_set_wait_limit(ctx, int(cycles)))
+
+
 def mgs_kernel_launches() -> int:
     return lib().mgs_kernel_launches()
 
@@ -265,6 +283,19 @@ def mgs_build_cost_table(ctx: int, scene: int, grid: Grid, table, stream=None):
 def mgs_build_cost_table_plain(ctx: int, scene: int, grid: Grid, table, stream=None):
     _check(lib().mgs_build_cost_table_plain(ctx, scene, ctypes.byref(grid.c), _ptr(table),
                                             _stream(stream)))
+
+
+def mgs_build_cost_table_probe(ctx: int, scene: int, grid: Grid, table, hist=None, codes=None,
+                               stream=None):
+    """The fused table plus what its kernel counted: hist (device uint32 /
+    int32 tensor, [n_items][sum 2^b]) and codes (device int16 tensor), either may
+    be None.  Layouts as in include/mgs.h."""
+    def entries(x):
+        return 0 if x is None else int(x.numel() if hasattr(x, "numel") else x.size)
+
+    hc, cc = entries(hist), entries(codes)
+    _check(lib().mgs_build_cost_table_probe(ctx, scene, ctypes.byref(grid.c), _ptr(table), _ptr(hist), hc,
+                                            _ptr(codes), cc, _stream(stream)))
 
 
 def _grids(grids, n):
@@ -405,10 +436,12 @@ def mgs_server_create(ctx: int, max_jobs: int = 8, solver_threads: int = 4,
     return h.value
 
 
-def mgs_server_submit(server: int, attrs, importance, grid: Grid, budget_bytes: float, opts) -> int:
-    """attrs / importance: host buffers that stay alive until the job is done."""
+def mgs_server_submit(server: int, attrs, importance, grid: Grid, budget_bytes: float, opts,
+                      table_out=None) -> int:
+    """attrs / importance (and table_out, a host buffer of the table layout's
+    total_bytes, if given): host buffers that stay alive until the job is done."""
     n, C = attrs.shape
-    j = mgs_job(_ptr(attrs), _ptr(importance), n, C, grid.c, float(budget_bytes), opts)
+    j = mgs_job(_ptr(attrs), _ptr(importance), n, C, grid.c, float(budget_bytes), opts, _ptr(table_out))
     jid = ctypes.c_int64()
     _check(lib().mgs_server_submit(server, ctypes.byref(j), ctypes.byref(jid)))
     return jid.value

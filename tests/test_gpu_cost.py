@@ -79,6 +79,21 @@ def test_table_matches_oracle(ctx, G):
     assert_table_close(got, ref, G, f"G={G}")
 
 
+def test_single_scene_workload_matches_oracle(ctx):
+    """The single-scene workload in full: N = 100,000 Gaussians, r = 1/2,
+    b = {4, 6, 8, 10, 12, 16}, G = 4096 (12 full groups and one of 848 per
+    channel), every entry of the table against the oracle."""
+    w = synth.SMALL
+    attrs, imp = synth.make_scene(w.n, seed=w.seed)
+    keep = w.keep()
+    assert list(keep) == [50_000]
+    got, L = run_table(ctx, attrs, imp, keep, list(w.bits), w.group_size)
+    assert int(L.n_items) == 59 * 13
+    ref = oracle.cost_table(attrs, imp, keep, list(w.bits), w.group_size)
+    assert_table_close(got, ref, w.group_size, "single scene")
+    assert sorted(set(got["cnt"].tolist())) == [848, 4096]
+
+
 def test_every_tile_shape_matches_oracle(ctx):
     n = 9_000
     attrs, imp = synth.make_scene(n, seed=12)
@@ -185,10 +200,11 @@ def test_batched_plan_and_graph_equal_single(ctx):
     bits = [2, 4, 8, 12, 14, 16]
     G = 2048
     sizes = [3000, 17_000, 9000]
-    scenes, tables, singles, grids = [], [], [], []
+    scenes, tables, singles, grids, inputs = [], [], [], [], []
     try:
         for i, n in enumerate(sizes):
             attrs, imp = synth.make_scene(n, seed=20 + i)
+            inputs.append((attrs, imp))
             sc = mgs.mgs_scene_create(ctx, torch.from_numpy(attrs).to(dev), torch.from_numpy(imp).to(dev))
             scenes.append(sc)
             grid = mgs.Grid(synth.keep_counts(n, [(1, 3), (2, 3), (3, 3)]), bits, G)   # per-scene sizes
@@ -212,6 +228,12 @@ def test_batched_plan_and_graph_equal_single(ctx):
                 st.synchronize()
                 mgs.mgs_plan_destroy(plan)
         torch.cuda.synchronize()
+        # every batched, graph-replayed table against the oracle itself
+        for (attrs, imp), grid, t in zip(inputs, grids, tables):
+            L = mgs.mgs_table_layout_for(attrs.shape[0], attrs.shape[1], grid)
+            got = mgs.table_views(t.cpu().numpy(), L)
+            ref = oracle.cost_table(attrs, imp, grid.keep, bits, G)
+            assert_table_close(got, ref, G, f"batched n={attrs.shape[0]}")
         for t, o in zip(tables, singles):
             assert torch.equal(t, o)
         # the one-shot batched call gives the same tables

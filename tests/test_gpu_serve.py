@@ -1,10 +1,13 @@
 """The search server: continuous batching gives every job the result it gets
-alone; admission respects slots and the HBM budget; failures and timeouts are
+alone, and every served table equals the oracle's within the cost-table bar;
+admission respects slots and the HBM budget; failures and timeouts are
 reported per job (needs a GB300)."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_2604_26799_gb300 import mgs, synth
+from tests.test_gpu_cost import assert_table_close
 
 pytestmark = pytest.mark.gpu
 
@@ -50,10 +53,12 @@ def direct(ctx, job):
     return mgs.mgs_solve_budget(tab, L, grid, budget, mgs.solve_opts())
 
 
-def serve(ctx, jobs, **opts):
+def serve(ctx, jobs, tables=None, **opts):
     srv = mgs.mgs_server_create(ctx, **opts)
+    tables = tables or [None] * len(jobs)
     try:
-        ids = [mgs.mgs_server_submit(srv, a, i, g, b, mgs.solve_opts()) for a, i, g, b in jobs]
+        ids = [mgs.mgs_server_submit(srv, a, i, g, b, mgs.solve_opts(), table_out=t)
+               for (a, i, g, b), t in zip(jobs, tables)]
         res = [mgs.mgs_server_wait(srv, j, timeout_ms=120000, max_choice=1 << 20) for j in ids]
         stats = mgs.mgs_server_stats(srv)
     finally:
@@ -75,11 +80,20 @@ def test_results_equal_alone_and_in_the_mix(ctx):
     for j, d in zip(jobs, ref):
         (r,), _ = serve(ctx, [j], max_jobs=1, slice_items=0)
         same(r, d)
-    # all together, small slices so every launch mixes several jobs
-    res, stats = serve(ctx, jobs, max_jobs=8, slice_items=500)
+    # all together, small slices so every launch mixes several jobs; each job's
+    # table is copied out and checked against the oracle itself
+    tables = []
+    for attrs, imp, grid, budget in jobs:
+        L = mgs.mgs_table_layout_for(attrs.shape[0], attrs.shape[1], grid)
+        tables.append(np.zeros(L.total_bytes, dtype=np.uint8))
+    res, stats = serve(ctx, jobs, tables=tables, max_jobs=8, slice_items=500)
     for r, d in zip(res, ref):
         same(r, d)
     assert stats["launches"] > len(jobs)   # the work was split across shared launches
+    for (attrs, imp, grid, budget), t in zip(jobs, tables):
+        L = mgs.mgs_table_layout_for(attrs.shape[0], attrs.shape[1], grid)
+        ref_t = oracle.cost_table(attrs, imp, grid.keep, BITS, G)
+        assert_table_close(mgs.table_views(t, L), ref_t, G, f"served n={attrs.shape[0]}")
 
 
 def test_admission_by_memory_budget(ctx):

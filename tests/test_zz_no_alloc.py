@@ -73,3 +73,57 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(ctx):
         assert e.value.status == -1
     finally:
         mgs.mgs_scene_destroy(scene)
+
+
+def _limit(name: str) -> int:
+    import os
+    import re
+    hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "mgs.h")).read()
+    return int(re.search(rf"#define {name} (\d+)", hdr).group(1))
+
+
+def test_noalloc_at_and_beyond_its_kept_limit(ctx):
+    """keep == MGS_NOALLOC_MAX_KEEP fills the static kept array and still matches
+    the allocating entry point bit for bit; one more kept Gaussian is refused."""
+    dev = torch.device("cuda:0")
+    max_keep = _limit("MGS_NOALLOC_MAX_KEEP")
+    n = max_keep + 1000
+    attrs, imp = synth.make_scene(n, seed=33)
+    attrs = np.ascontiguousarray(attrs[:, :8])
+    C = attrs.shape[1]
+    scene = mgs.mgs_scene_create(ctx, torch.from_numpy(attrs).to(dev), torch.from_numpy(imp).to(dev))
+    try:
+        G = 4096
+        ng = (max_keep + G - 1) // G
+        rng = np.random.default_rng(6)
+        qbits = torch.from_numpy(rng.integers(1, 17, size=(C, ng)).astype(np.uint8)).to(dev)
+        ref_codes, ref_mm = _codes(mgs.mgs_quantize_groups, ctx, scene, max_keep, G, qbits, C, dev)
+        got_codes, got_mm = _codes(mgs.mgs_quantize_groups_noalloc, ctx, scene, max_keep, G, qbits, C, dev)
+        assert np.array_equal(got_codes, ref_codes)
+        assert np.array_equal(got_mm, ref_mm)
+        codes = torch.empty((C, max_keep + 1), dtype=torch.int16, device=dev)
+        mm = torch.empty((C, ng + 1, 2), dtype=torch.float32, device=dev)
+        qb = torch.ones((C, ng + 1), dtype=torch.uint8, device=dev)
+        with pytest.raises(mgs.MgsError) as e:
+            mgs.mgs_quantize_groups_noalloc(ctx, scene, max_keep + 1, G, qb, codes, mm)
+        assert e.value.status == -1 and "at most" in str(e.value)
+    finally:
+        mgs.mgs_scene_destroy(scene)
+
+
+def test_noalloc_refuses_a_scene_beyond_its_tile_counts(ctx):
+    dev = torch.device("cuda:0")
+    n = _limit("MGS_NOALLOC_MAX_SCENE") + 1
+    rng = np.random.default_rng(7)
+    attrs = rng.random((n, 3), dtype=np.float32)
+    imp = rng.random(n, dtype=np.float32)
+    scene = mgs.mgs_scene_create(ctx, torch.from_numpy(attrs).to(dev), torch.from_numpy(imp).to(dev))
+    try:
+        bits = torch.ones((3, 1), dtype=torch.uint8, device=dev)
+        codes = torch.empty((3, 100), dtype=torch.int16, device=dev)
+        mm = torch.empty((3, 1, 2), dtype=torch.float32, device=dev)
+        with pytest.raises(mgs.MgsError) as e:
+            mgs.mgs_quantize_groups_noalloc(ctx, scene, 100, 4096, bits, codes, mm)
+        assert e.value.status == -1 and "at most" in str(e.value)
+    finally:
+        mgs.mgs_scene_destroy(scene)
