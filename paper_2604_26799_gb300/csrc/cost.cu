@@ -158,6 +158,64 @@ __device__ __forceinline__ uint32_t ld_keep(const uint32_t *p) {
     return v;
 }
 
+// ---- tensor memory: the gathered tile of a slab (8 channels) is kept in this
+// CTA's TMEM, one lane per thread, channel-major columns, so that only the
+// channel being evaluated occupies registers.
+__device__ __forceinline__ void tm_alloc(uint32_t *dst, uint32_t ncols) {   // one whole warp
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "r"(ncols) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tm_dealloc(uint32_t taddr, uint32_t ncols) {   // the same warp
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tm_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tm_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// Four consecutive 32-bit columns of this thread's lane.
+__device__ __forceinline__ void tm_st4(uint32_t taddr, float a, float b, float c, float d) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr),
+                 "r"(__float_as_uint(a)), "r"(__float_as_uint(b)), "r"(__float_as_uint(c)),
+                 "r"(__float_as_uint(d))
+                 : "memory");
+}
+__device__ __forceinline__ void tm_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+// N (8 or 16) consecutive columns of this thread's lane into v.
+template <int N>
+__device__ __forceinline__ void tm_ld(uint32_t taddr, float (&v)[N]) {
+    static_assert(N == 8 || N == 16, "8 or 16 columns");
+    uint32_t r[16];
+    if (N == 16) {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+            "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+              "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+              "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr)
+            : "memory");
+    } else {
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                       "=r"(r[7])
+                     : "r"(taddr)
+                     : "memory");
+    }
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < N; j++) v[j] = __uint_as_float(r[j]);
+}
+// TMEM columns of a CTA: T/128 column blocks (warps w and w + 4 share lanes) of
+// EPT x W columns, rounded up to a power of two (at least 32).
+__host__ __device__ constexpr int tm_cols(int T, int EPT, int W) {
+    int c = (T / 128 > 0 ? T / 128 : 1) * EPT * W, p = 32;
+    while (p < c) p <<= 1;
+    return p;
+}
+
 // ---- shared-memory histogram operations ------------------------------------
 // Predicated forms execute only where `pred` holds (predicated, not branched:
 // lanes taking different sides do not split the warp); atom_if returns 0 elsewhere.
@@ -464,51 +522,63 @@ __device__ void probe_degenerate(uint32_t *out, int bins, int nvalid) {
 }
 
 // After every count of region A is in: sum L(h) of the scanned tables, clear
-// every table, and write the hpart entries of the scanned options.
+// every table, and write the hpart rows of the scanned options.  Each option is
+// finished by one warp (options round-robin over the warps), so the table
+// scans and their L(h) lookups of all options are in flight together.
 template <int T, bool PROBE>
 __device__ void finish_small(const KernelArgs &A, const Smem &sm, int nvalid, int64_t item) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int NW = T / 32;
-    for (int k = 0; k < A.n_small; k++) {
+    for (int k = warp; k < A.n_small; k += NW) {
         const int b = sm.bp[k].b, mode = A.opt_mode[k];
         const int bins = 1 << b;
         uint32_t *t = sm.ra + A.opt_off[k];
         uint32_t *pout = PROBE ? A.hist_out + item * A.hist_stride + A.hist_off[A.opt_lo + k] : nullptr;
         if (sm.bp[k].path == kDegenerate) {
-            if (PROBE) probe_degenerate<T>(pout, bins, nvalid);
+            if (PROBE)
+                for (int j = lane; j < bins; j += 32) pout[j] = j == 0 ? (uint32_t)nvalid : 0u;
             continue;   // table untouched; hpart written by the evaluation pass
         }
         unsigned long long hacc = 0ull;
         if (mode == kLane) {
-            // the warp's j-th bin count is kept by lane j (bins / warps <= 32),
-            // so the table lookups of all its bins go out together
-            uint32_t mine = 0;
-            int j = 0;
+            // bin r's 32 lane columns are summed across the warp; lane r % 32 keeps
+            // the total (at most two bins per lane for b <= 6)
+            uint32_t mine0 = 0, mine1 = 0;
 #pragma unroll 4
-            for (int bin = warp; bin < bins; bin += NW, j++) {
+            for (int bin = 0; bin < bins; bin++) {
                 const uint32_t v = t[bin * 32 + lane];
                 t[bin * 32 + lane] = 0u;
                 const uint32_t s = __reduce_add_sync(kFull, v);
-                mine = lane == j ? s : mine;
+                if (bin < 32) mine0 = lane == bin ? s : mine0;
+                else mine1 = lane == bin - 32 ? s : mine1;
                 if (PROBE && lane == 0) pout[bin] = s;
             }
-            hacc = ld_keep(&A.ltab[mine]);   // L(0) = 0 for lanes without a bin
+            hacc = ld_keep(&A.ltab[mine0]) + ld_keep(&A.ltab[mine1]);   // L(0) = 0
         } else if (mode == kDirect) {
             // branch-free: L(0) = 0, so an empty bin adds nothing
-#pragma unroll 4
-            for (int bin = threadIdx.x; bin < bins; bin += T) {
+#pragma unroll 8
+            for (int bin = lane; bin < bins; bin += 32) {
                 const uint32_t v = t[bin];
                 t[bin] = 0u;
                 hacc += ld_keep(&A.ltab[v]);
                 if (PROBE) pout[bin] = v;
             }
         } else {
-            if (PROBE) probe_packed_clear<T>(t, A.opt_words[k], 2, 0, bins, pout);
-            else clear_words<T>(t, A.opt_words[k]);
-            continue;   // delta sums written by the evaluation pass
+            // 16-bit pairs: the delta sums were written by the evaluation pass
+            const int words = A.opt_words[k];
+            for (int j = lane; j < words; j += 32) {
+                const uint32_t v = t[j];
+                t[j] = 0u;
+                if (PROBE) {
+                    if (2 * j < bins) pout[2 * j] = v & 0xFFFFu;
+                    if (2 * j + 1 < bins) pout[2 * j + 1] = v >> 16;
+                }
+            }
+            continue;
         }
         hacc = warp_sum_u64_redux(hacc);
-        if (lane == 0) sm.hpart[k * NW + warp] = hacc;
+        // this warp's sum is the option's total: the other warps' slots are zero
+        for (int j = lane; j < NW; j += 32) sm.hpart[k * NW + j] = j == 0 ? hacc : 0ull;
     }
 }
 
@@ -517,7 +587,8 @@ __device__ void finish_small(const KernelArgs &A, const Smem &sm, int nvalid, in
 template <int T, int EPT, bool PROBE>
 __device__ __forceinline__ void run_option(const KernelArgs &A, const Smem &sm, int k, uint32_t *t,
                                            uint32_t wn, const float (&cw)[EPT], const float (&u)[EPT],
-                                           int nvalid, bool full, bool any_slow, uint16_t *codes) {
+                                           int nvalid, unsigned long long lnv, bool full, bool any_slow,
+                                           uint16_t *codes) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int NW = T / 32;
     const BitParam p = sm.bp[k];
@@ -525,7 +596,7 @@ __device__ __forceinline__ void run_option(const KernelArgs &A, const Smem &sm, 
     EvalOut o{0.0f, 0.0f, 0.0f, 0u, 0u};
     unsigned long long hdeg = 0ull;
     if (p.path == kDegenerate) {
-        if (threadIdx.x == 0) hdeg = __ldg(&A.ltab[nvalid]);
+        if (threadIdx.x == 0) hdeg = lnv;
         if (PROBE)
             for (int e = 0; e < EPT; e++)
                 if (e * T + (int)threadIdx.x < nvalid) codes[e * T + threadIdx.x] = 0;
@@ -570,8 +641,10 @@ __device__ __forceinline__ void run_option(const KernelArgs &A, const Smem &sm, 
     }
 }
 
-template <int T, int EPT, int W, bool PROBE>
-__device__ void process_item(const KernelArgs &A, const Smem &sm, int64_t work) {
+// TM: the item is a whole slab (W = 8), staged in TMEM at column base `tm`
+// (this thread's lane and column block); else the W channels stay in registers.
+template <int T, int EPT, int W, bool PROBE, bool TM>
+__device__ void process_item(const KernelArgs &A, const Smem &sm, int64_t work, uint32_t tm) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int NW = T / 32;
     // ---- decode the work item
@@ -596,37 +669,75 @@ __device__ void process_item(const KernelArgs &A, const Smem &sm, int64_t work) 
     const int nvalid = (int)((S.K - gstart) < (int64_t)A.G ? (S.K - gstart) : (int64_t)A.G);
     // every element of this warp is valid (warp-uniform)
     const bool full = __all_sync(kFull, (EPT - 1) * T + (int)threadIdx.x < nvalid);
+    const unsigned long long lnv = __ldg(&A.ltab[nvalid]);   // L(n) of the group
 
-    // ---- gather: each element's W channels from its slab row
-    float v[W][EPT];
+    // ---- gather: each element's W channels from its slab row, and the
+    // per-thread min / max of every channel of the chunk
+    float v[TM ? 1 : W][EPT];   // TM: the channel being evaluated; else all W channels
+    float tmn[W], tmx[W];
 #pragma unroll
-    for (int e = 0; e < EPT; e++) {
-        int i = e * T + threadIdx.x;
-        float row[W];
-        if (i < nvalid) {
-            const int32_t pos = S.kept ? ld_stream(&S.kept[gstart + i]) : (int32_t)(gstart + i);
-            load_row<W>(S.slabs + ((int64_t)slab * S.n + pos) * kSlabWidth + j0, row);
-        } else {
+    for (int w = 0; w < W; w++) {
+        tmn[w] = FLT_MAX;
+        tmx[w] = -FLT_MAX;
+    }
+    if constexpr (TM) {
+        static_assert(W == kSlabWidth && EPT % 8 == 0, "a TMEM tile holds whole slab rows, 8 elements per batch");
+        int32_t pos[EPT];
 #pragma unroll
-            for (int w = 0; w < W; w++) row[w] = 0.0f;
+        for (int e = 0; e < EPT; e++) {
+            const int i = e * T + threadIdx.x;
+            pos[e] = i < nvalid ? (S.kept ? ld_stream(&S.kept[gstart + i]) : (int32_t)(gstart + i)) : -1;
         }
 #pragma unroll
-        for (int w = 0; w < W; w++) v[w][e] = row[w];
+        for (int e0 = 0; e0 < EPT; e0 += 8) {
+            float r[8][W];
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                if (pos[e0 + j] >= 0) {
+                    load_row<W>(S.slabs + ((int64_t)slab * S.n + pos[e0 + j]) * kSlabWidth, r[j]);
+#pragma unroll
+                    for (int w = 0; w < W; w++) {
+                        tmn[w] = fminf(tmn[w], r[j][w]);
+                        tmx[w] = fmaxf(tmx[w], r[j][w]);
+                    }
+                } else {
+#pragma unroll
+                    for (int w = 0; w < W; w++) r[j][w] = 0.0f;
+                }
+            }
+#pragma unroll
+            for (int w = 0; w < W; w++) {
+                tm_st4(tm + (uint32_t)(w * EPT + e0), r[0][w], r[1][w], r[2][w], r[3][w]);
+                tm_st4(tm + (uint32_t)(w * EPT + e0 + 4), r[4][w], r[5][w], r[6][w], r[7][w]);
+            }
+        }
+        tm_wait_st();
+    } else {
+#pragma unroll
+        for (int e = 0; e < EPT; e++) {
+            int i = e * T + threadIdx.x;
+            float row[W];
+            if (i < nvalid) {
+                const int32_t pos = S.kept ? ld_stream(&S.kept[gstart + i]) : (int32_t)(gstart + i);
+                load_row<W>(S.slabs + ((int64_t)slab * S.n + pos) * kSlabWidth + j0, row);
+#pragma unroll
+                for (int w = 0; w < W; w++) {
+                    tmn[w] = fminf(tmn[w], row[w]);
+                    tmx[w] = fmaxf(tmx[w], row[w]);
+                }
+            } else {
+#pragma unroll
+                for (int w = 0; w < W; w++) row[w] = 0.0f;
+            }
+#pragma unroll
+            for (int w = 0; w < W; w++) v[TM ? 0 : w][e] = row[w];
+        }
     }
 
     // ---- group min / max of every channel of the chunk
 #pragma unroll
     for (int w = 0; w < W; w++) {
-        float mn = FLT_MAX, mx = -FLT_MAX;
-#pragma unroll
-        for (int e = 0; e < EPT; e++) {
-            if (e * T + (int)threadIdx.x < nvalid) {
-                mn = fminf(mn, v[w][e]);
-                mx = fmaxf(mx, v[w][e]);
-            }
-        }
-        mn = warp_min(mn);
-        mx = warp_max(mx);
+        const float mn = warp_min(tmn[w]), mx = warp_max(tmx[w]);
         if (lane == 0) {
             sm.mm[(warp * W + w) * 2] = mn;
             sm.mm[(warp * W + w) * 2 + 1] = mx;
@@ -690,6 +801,7 @@ __device__ void process_item(const KernelArgs &A, const Smem &sm, int64_t work) 
         }
         // one division per element, shared by every bit-width; then scale the
         // channel's values in place by 2^k
+        if constexpr (TM) tm_ld<EPT>(tm + (uint32_t)(w * EPT), v[0]);   // this channel's values
         float u[EPT];
         int slow = 0;
 #pragma unroll
@@ -707,14 +819,14 @@ __device__ void process_item(const KernelArgs &A, const Smem &sm, int64_t work) 
         // ---- bit-widths up to 12: every table of region A, no barrier between them
 #pragma unroll 1
         for (int k = 0; k < A.n_small; k++)
-            run_option<T, EPT, PROBE>(A, sm, k, sm.ra + A.opt_off[k], 0u, v[0], u, nvalid, full,
+            run_option<T, EPT, PROBE>(A, sm, k, sm.ra + A.opt_off[k], 0u, v[0], u, nvalid, lnv, full,
                                       any_slow, codes ? codes + (A.opt_lo + k) * kstride : nullptr);
         // ---- larger bit-widths one at a time in region B (byte counters)
 #pragma unroll 1
         for (int k = A.n_small; k < n_opts; k++) {
             const BitParam p = sm.bp[k];
             const uint32_t wn = (uint32_t)A.opt_words[k];
-            run_option<T, EPT, PROBE>(A, sm, k, sm.rb, wn, v[0], u, nvalid, full, any_slow,
+            run_option<T, EPT, PROBE>(A, sm, k, sm.rb, wn, v[0], u, nvalid, lnv, full, any_slow,
                                       codes ? codes + (A.opt_lo + k) * kstride : nullptr);
             __syncthreads();   // every count of this pass (and of region A) is in
             if (k == A.n_small) finish_small<T, PROBE>(A, sm, nvalid, item);
@@ -805,22 +917,23 @@ __device__ void process_item(const KernelArgs &A, const Smem &sm, int64_t work) 
                 S.sse[o] = (double)a * inv2;
                 S.l1[o] = (double)b * inv;
                 S.linf[o] = (float)((double)cmax * inv);
-                unsigned long long ln = __ldg(&A.ltab[nvalid]);
-                S.hbits[o] = (double)(long long)(ln - hs) * (1.0 / 4194304.0);   // 2^-22
+                S.hbits[o] = (double)(long long)(lnv - hs) * (1.0 / 4194304.0);   // 2^-22
                 sm.flags[k] = 0u;
             }
         }
         // the next channel takes the values of the following one (compile-time
         // register indices)
+        if constexpr (!TM) {
 #pragma unroll
-        for (int ww = 0; ww + 1 < W; ww++)
+            for (int ww = 0; ww + 1 < (TM ? 1 : W); ww++)
 #pragma unroll
-            for (int e = 0; e < EPT; e++) v[ww][e] = v[ww + 1][e];
+                for (int e = 0; e < EPT; e++) v[ww][e] = v[ww + 1][e];
+        }
     }
 }
 
-template <int T, int EPT, int W, bool PROBE>
-__global__ void __launch_bounds__(T, (T >= 512 ? 1 : 512 / T))
+template <int T, int EPT, int W, bool PROBE, int MINB, bool TM>
+__global__ void __launch_bounds__(T, MINB)
     k_cost(const __grid_constant__ KernelArgs A, int unused) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n_opts = A.opt_hi - A.opt_lo;
@@ -841,9 +954,22 @@ __global__ void __launch_bounds__(T, (T >= 512 ? 1 : 512 / T))
     for (int i = threadIdx.x; i < A.a_words + A.b_words; i += T) sm.ra[i] = 0u;
     for (int i = threadIdx.x; i < kByteDelta; i += T) sm.bdelta[i] = i <= 256 ? __ldg(&A.dtab[i]) : 0u;
     for (int i = threadIdx.x; i < n_opts; i += T) sm.flags[i] = 0u;
+    // TMEM for the gathered tile: at most 512 / tm_cols CTAs share an SM (the
+    // launch pads shared memory so), so the allocation never waits on another
+    // CTA of this kernel
+    constexpr int kCols = tm_cols(T, EPT, W);
+    __shared__ uint32_t s_tmem;
+    if (TM && (threadIdx.x >> 5) == 0) tm_alloc(&s_tmem, kCols);
+    if (TM) tm_fence_before();
     __syncthreads();
+    uint32_t tm = 0;
+    if (TM) {
+        tm_fence_after();
+        const int warp = threadIdx.x >> 5;
+        tm = s_tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)((warp >> 2) * EPT * W);
+    }
     if (A.counter == nullptr) {
-        process_item<T, EPT, W, PROBE>(A, sm, blockIdx.x);
+        process_item<T, EPT, W, PROBE, TM>(A, sm, blockIdx.x, tm);
     } else {
         __shared__ int64_t s_work;
         while (true) {
@@ -851,9 +977,15 @@ __global__ void __launch_bounds__(T, (T >= 512 ? 1 : 512 / T))
             __syncthreads();
             const int64_t work = s_work;
             if (work >= A.n_work) break;
-            process_item<T, EPT, W, PROBE>(A, sm, work);
+            process_item<T, EPT, W, PROBE, TM>(A, sm, work, tm);
             __syncthreads();
         }
+    }
+    if (TM) {
+        tm_fence_before();
+        __syncthreads();
+        tm_fence_after();
+        if ((threadIdx.x >> 5) == 0) tm_dealloc(s_tmem, kCols);
     }
 }
 
@@ -862,10 +994,21 @@ struct ConfigEntry {
     void (*kernel)(KernelArgs, int);
     void (*probe)(KernelArgs, int);   // probe instantiation (or NULL)
     int ctas;                         // resident CTAs per SM the shared-memory plan aims at
+    int tm_cols;                      // TMEM columns of a CTA (0: the tile stays in registers)
 };
 
-#define MGS_CFG(T, E, W, C) {{T, E, W, "t" #T "_e" #E "_w" #W}, k_cost<T, E, W, false>, nullptr, C}
-#define MGS_CFGP(T, E, W, C) {{T, E, W, "t" #T "_e" #E "_w" #W}, k_cost<T, E, W, false>, k_cost<T, E, W, true>, C}
+// {threads, elements per thread, channels per item, name}, the kernel, its
+// probe instantiation, the CTAs per SM that its registers (launch bounds) and
+// shared-memory plan aim at, and its TMEM columns ("tm" shapes keep the whole
+// slab's tile in tensor memory).
+#define MGS_NAME(T, E, W, C, X) "t" #T "_e" #E "_w" #W "_c" #C X
+#define MGS_CFG(T, E, W, C) \
+    {{T, E, W, MGS_NAME(T, E, W, C, "")}, k_cost<T, E, W, false, C, false>, nullptr, C, 0}
+#define MGS_CFGP(T, E, W, C) \
+    {{T, E, W, MGS_NAME(T, E, W, C, "")}, k_cost<T, E, W, false, C, false>, k_cost<T, E, W, true, C, false>, C, 0}
+#define MGS_CFGT(T, E, C)                                                                   \
+    {{T, E, 8, MGS_NAME(T, E, 8, C, "_tm")}, k_cost<T, E, 8, false, C, true>, k_cost<T, E, 8, true, C, true>, C, \
+     tm_cols(T, E, 8)}
 const ConfigEntry kConfigs[] = {
     MGS_CFGP(256, 16, 4, 2),
     MGS_CFG(512, 8, 4, 1),
@@ -874,10 +1017,16 @@ const ConfigEntry kConfigs[] = {
     MGS_CFG(128, 8, 8, 4),
     MGS_CFGP(256, 4, 8, 2),
     MGS_CFGP(512, 32, 1, 1),
-    MGS_CFG(512, 16, 2, 1),
+    MGS_CFG(256, 16, 1, 2),
+    MGS_CFG(256, 16, 1, 3),
+    MGS_CFGT(256, 16, 2),
+    MGS_CFGT(256, 8, 2),
+    MGS_CFGT(128, 8, 4),
 };
 #undef MGS_CFG
 #undef MGS_CFGP
+#undef MGS_CFGT
+#undef MGS_NAME
 constexpr int kNumConfigs = sizeof(kConfigs) / sizeof(kConfigs[0]);
 
 // Histogram plan of a launch: region A holds a table per option up to 12 bits
@@ -892,8 +1041,8 @@ struct HistPlan {
 };
 
 // Shared memory a CTA may use when `ctas` of them share an SM (228 KB per SM,
-// 1 KB reserved per CTA, the kernel's few static bytes).
-size_t smem_budget(int ctas) { return std::min<size_t>(227 * 1024, (228 * 1024) / ctas - 1024 - 64); }
+// 1 KB reserved per CTA, and up to 512 bytes of the kernel's static variables).
+size_t smem_budget(int ctas) { return std::min<size_t>(227 * 1024 - 512, (228 * 1024) / ctas - 1024 - 512); }
 
 HistPlan plan_hist(const ConfigEntry &E, const int32_t *bits, int n_opts) {
     const CostConfig &c = E.cfg;
@@ -958,9 +1107,9 @@ int cost_config_count() { return kNumConfigs; }
 const CostConfig &cost_config(int i) { return kConfigs[i].cfg; }
 
 int cost_default_config(int G) {
-    if (G <= 1024) return 5;    // 256 x 4, W 8
-    if (G <= 2048) return 3;    // 256 x 8, W 4
-    if (G <= 4096) return 0;    // 256 x 16, W 4
+    if (G <= 1024) return 11;   // 128 x 8, slab tile in TMEM
+    if (G <= 2048) return 10;   // 256 x 8, slab tile in TMEM
+    if (G <= 4096) return 9;    // 256 x 16, slab tile in TMEM
     if (G <= 16384) return 6;   // 512 x 32, W 1
     return -1;
 }
@@ -1051,12 +1200,36 @@ mgs_status cost_exec_create(mgs_ctx *ctx, const CostLaunch &L, int config, CostE
         delete X;
         return MGS_ERR_INVALID_ARG;
     }
-    cudaError_t e = cudaFuncSetAttribute(X->kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)X->smem);
+    cudaError_t e = cudaSuccess;
+    if (E.tm_cols > 0) {
+        // at most 512 / tm_cols CTAs of this kernel per SM, so tcgen05.alloc never waits
+        // on a CTA of the same kernel: pad the shared memory until occupancy says so
+        const int max_ctas = 512 / E.tm_cols;
+        int optin = 0;
+        cudaFuncAttributes fa{};
+        e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, X->kernel);
+        const size_t limit = e == cudaSuccess ? (size_t)optin - fa.sharedSizeBytes : 0;
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(X->kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit);
+        for (; e == cudaSuccess;) {
+            int per_sm = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, X->kernel, E.cfg.threads, X->smem);
+            if (e != cudaSuccess || per_sm <= max_ctas || X->smem + 1024 > limit) break;
+            X->smem += 1024;
+        }
+    }
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(X->kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)X->smem);
     X->grid = n_work;
     if (e == cudaSuccess && L.persistent) {
         int per_sm = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, X->kernel, E.cfg.threads, X->smem);
+        // the occupancy calculator reports one CTA per SM for any kernel that
+        // allocates tensor memory (it cannot know how many columns a CTA takes);
+        // these CTAs take tm_cols each and their registers and shared memory are
+        // planned for `ctas` per SM.  Surplus CTAs of a persistent launch only find
+        // the work counter exhausted.
+        if (E.tm_cols > 0) per_sm = std::max(per_sm, std::min(E.ctas, 512 / E.tm_cols));
         per_sm = std::max(per_sm, 1);
         X->grid = std::min<int64_t>(n_work, (int64_t)ctx->sm_count * per_sm);
     }
