@@ -844,27 +844,31 @@ __device__ void process_item(const KernelArgs &A, const Smem &sm, int64_t work, 
                     // byte counters held: the first window is complete
                     if (PROBE) probe_packed_clear<T>(sm.rb, (int)wn, 4, 0, bins, pout);
                     else clear_words<T>(sm.rb, (int)wn);
+                    if (A.opt_windows[k] > 1) {
 #pragma unroll 1
-                    for (int win = 1; win < A.opt_windows[k]; win++) {
-                        __syncthreads();
-                        h.wlo = (uint32_t)win * wn;
-                        h.wn = wn;
-                        count_window<T, EPT, kByte>(v[0], u, nvalid, generic, p, h, dacc, ovf);
-                        __syncthreads();
-                        if (PROBE) probe_packed_clear<T>(sm.rb, (int)wn, 4, (int64_t)win * wn * 4, bins, pout);
-                        else clear_words<T>(sm.rb, (int)wn);
+                        for (int win = 1; win < A.opt_windows[k]; win++) {
+                            __syncthreads();
+                            h.wlo = (uint32_t)win * wn;
+                            h.wn = wn;
+                            count_window<T, EPT, kByte>(v[0], u, nvalid, generic, p, h, dacc, ovf);
+                            __syncthreads();
+                            if (PROBE) probe_packed_clear<T>(sm.rb, (int)wn, 4, (int64_t)win * wn * 4, bins, pout);
+                            else clear_words<T>(sm.rb, (int)wn);
+                        }
+                        // a counter of a later window may have overflowed too
+                        const uint32_t any = __syncthreads_or(ovf != 0u);
+                        if (any) {
+                            if (threadIdx.x == 0) sm.flags[k] = 1u;
+                        } else {
+                            const unsigned long long hs = warp_sum_u64_redux((unsigned long long)dacc);
+                            if (lane == 0) sm.hpart[k * NW + warp] += hs;
+                        }
+                        dacc = 0;
+                        __syncthreads();   // the flag of the later windows is visible
                     }
-                    // a counter of a later window may have overflowed too
-                    const uint32_t any = __syncthreads_or(ovf != 0u);
-                    if (any) {
-                        if (threadIdx.x == 0) sm.flags[k] = 1u;
-                    } else {
-                        const unsigned long long hs = warp_sum_u64_redux((unsigned long long)dacc);
-                        if (lane == 0) sm.hpart[k * NW + warp] += hs;
-                    }
-                    dacc = 0;
+                    // one window: the flag was set by the evaluation pass, before the
+                    // barrier after it, and nothing has written it since
                 }
-                __syncthreads();
                 if (sm.flags[k] != 0u) {
                     // some counter reached 255: count again exactly with 16-bit pairs,
                     // in windows of region B
