@@ -218,10 +218,11 @@ def cpu_baseline(attrs: np.ndarray, imp: np.ndarray) -> dict:
         sample_all = f"{n_s} Gaussians of the same distributions and grid on {cores} threads, {dt_all:.1f} s"
     n_sample = int(os.environ.get("MGS_ORACLE_SAMPLE", "120000"))
     ev1, dt1 = oracle_sample(n_sample, seed=99)
+    sample_1 = (f"oracle.cost_table on {n_sample} Gaussians of the same distributions and "
+                f"grid, {dt1:.1f} s of one core")
     return {"value": ev_all / dt_all, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample_all,
-            "value_1_core": ev1 / dt1,
-            "sample_1_core": f"oracle.cost_table on {n_sample} Gaussians of the same distributions and "
-                             f"grid, {dt1:.1f} s of one core", **cpu_info()}
+            "cores_all": {"cores": cores, "value": ev_all / dt_all, "sample": sample_all},
+            "cores_1": {"cores": 1, "value": ev1 / dt1, "sample": sample_1}, **cpu_info()}
 
 
 def kernel_counters() -> dict:

@@ -3,9 +3,10 @@
 //
 // One work item = (segment = (scene, ratio), group g, chunk of W channels).
 // The CTA gathers the group's rows through the kept list once (W channels of
-// each 32-byte slab row, vector loads) into registers, reduces min/max, and
-// then evaluates every bit-width of one channel after the other from those
-// registers:
+// each 32-byte slab row, vector loads), reduces min/max, and then evaluates
+// every bit-width of one channel after the other.  The gathered tile stays in
+// registers, or (TM tile shapes) in tensor memory, one TMEM lane per thread,
+// from which one channel at a time is loaded into registers:
 //
 //   S = fl(R / 2^b), Z = rint(fl(2^b - fl(M / S))), R = fl(M - m)
 //   x = fl(fl(c / S) + Z),  q = rint(min(max(x, 0), 2^b - 1))
