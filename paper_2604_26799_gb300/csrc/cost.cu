@@ -73,6 +73,15 @@ struct __align__(16) BitParam {
     int path, b;
 };
 
+// Per channel of a work item: the group's range and the exact power-of-two
+// scale 2^k = s1 * s2 that brings R into [1, 2).
+struct __align__(16) ChanParam {
+    float m, M;      // group min, max
+    float Rs, rcp;   // R * 2^k and RN(1 / (R * 2^k))
+    float s1, s2;
+    int kexp, pad;
+};
+
 struct KernelArgs {
     const CostSeg *segs;
     int32_t n_segs;
@@ -86,11 +95,14 @@ struct KernelArgs {
     unsigned int *counter;
     // histogram plan (index k = option - opt_lo), fixed for the launch
     int32_t n_small;                  // options [0, n_small) share region A
+    int32_t n_lane, n_direct;         // of which [0, n_lane) lane tables, then n_direct direct ones
+    int32_t concurrent;               // every large option has its own table in region B
     int32_t a_words, b_words;         // region sizes in 32-bit words
     int8_t opt_mode[MGS_MAX_OPTIONS];
     int8_t opt_windows[MGS_MAX_OPTIONS];    // byte-counter passes of a large option
     int8_t opt_rwindows[MGS_MAX_OPTIONS];   // 16-bit-pair passes of its exact recount
-    int32_t opt_off[MGS_MAX_OPTIONS];       // word offset of a small option's table in region A
+    int32_t opt_off[MGS_MAX_OPTIONS];       // word offset of an option's table in region A (small)
+                                            // or, when concurrent, in region B (large)
     int32_t opt_words[MGS_MAX_OPTIONS];     // words of one pass's table
     // probe outputs (probe instantiation only)
     uint32_t *hist_out;               // [item][hist_stride]: every bin of every option
@@ -120,6 +132,7 @@ __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
     }
 MGS_F2_BINOP(fadd2, "add.rn.f32x2")
 MGS_F2_BINOP(fsub2, "sub.rn.f32x2")
+MGS_F2_BINOP(fmul2, "mul.rn.f32x2")
 #undef MGS_F2_BINOP
 
 // ---- global loads with L1 eviction hints: the gathered rows and kept
@@ -184,26 +197,34 @@ __device__ __forceinline__ void tm_st4(uint32_t taddr, float a, float b, float c
                  : "memory");
 }
 __device__ __forceinline__ void tm_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
-// N (8 or 16) consecutive columns of this thread's lane into v.
+// 16 or 8 consecutive columns of this thread's lane (no wait).
+__device__ __forceinline__ void tm_ld16(uint32_t taddr, uint32_t *r) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+}
+__device__ __forceinline__ void tm_ld8(uint32_t taddr, uint32_t *r) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                   "=r"(r[7])
+                 : "r"(taddr)
+                 : "memory");
+}
+// N (8, 16 or 32) consecutive columns of this thread's lane into v.
 template <int N>
 __device__ __forceinline__ void tm_ld(uint32_t taddr, float (&v)[N]) {
-    static_assert(N == 8 || N == 16, "8 or 16 columns");
-    uint32_t r[16];
-    if (N == 16) {
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-            "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
-            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-              "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-              "=r"(r[14]), "=r"(r[15])
-            : "r"(taddr)
-            : "memory");
+    static_assert(N == 8 || N % 16 == 0, "8 or a multiple of 16 columns");
+    uint32_t r[N];
+    if constexpr (N == 8) {
+        tm_ld8(taddr, r);
     } else {
-        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                       "=r"(r[7])
-                     : "r"(taddr)
-                     : "memory");
+#pragma unroll
+        for (int j = 0; j < N; j += 16) tm_ld16(taddr + (uint32_t)j, r + j);
     }
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
@@ -245,6 +266,19 @@ __device__ __forceinline__ uint32_t lds_u32(uint32_t addr) {
     return v;
 }
 
+// Byte permutes: b4e places byte 0 of a at byte position sel & 3 (the other
+// bytes come from zeros); f4e brings byte sel & 3 of a down to byte 0.
+__device__ __forceinline__ uint32_t byte_at(uint32_t a, uint32_t sel) {
+    uint32_t d;
+    asm("prmt.b32.b4e %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(0u), "r"(sel));
+    return d;
+}
+__device__ __forceinline__ uint32_t byte_from(uint32_t a, uint32_t sel) {
+    uint32_t d;
+    asm("prmt.b32.f4e %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(0u), "r"(sel));
+    return d & 0xFFu;
+}
+
 // Where one pass counts.  y is a code's bit pattern kMagicBits + q; the magic
 // offset is folded into the bases.
 struct HistPass {
@@ -252,13 +286,15 @@ struct HistPass {
     uint32_t dbase;       // direct: table - (kMagicBits << 2)
     uint32_t base;        // pair / byte: table (shared address)
     uint32_t wlo, wn;     // pair / byte: words [wlo, wlo + wn) of the full table are counted
+    uint32_t boff, wn4;   // byte: kMagicBits + 4 wlo, 4 wn
     const uint32_t *dtab; // pair: global delta table
     uint32_t dsm;         // byte: shared delta table (h = 0..256)
 };
 
 // Count one code.  PRED: `valid` may be false (partial groups, windows); WIN:
 // only codes whose word lies in the pass's window are counted.  The delta modes
-// add delta(new count) to dacc; byte mode flags a counter that was already 255.
+// add delta(new count) to dacc; byte mode keeps in ovf the largest count a
+// counter had before its increment (255: it overflowed).
 template <int MODE, bool PRED, bool WIN>
 __device__ __forceinline__ void hist_count(bool valid, uint32_t y, const HistPass &h, uint32_t &dacc,
                                            uint32_t &ovf) {
@@ -278,21 +314,16 @@ __device__ __forceinline__ void hist_count(bool valid, uint32_t y, const HistPas
         const uint32_t d = ld_keep(&h.dtab[((old >> sh) & 0xFFFFu) + 1u]);
         dacc += (PRED || WIN) ? (in ? d : 0u) : d;
     } else {
-        const uint32_t q = y - kMagicBits;
-        const uint32_t word = (q >> 2) - (WIN ? h.wlo : 0u);
-        const uint32_t sh = (q & 3u) << 3;
-        const bool in = (!PRED || valid) && (!WIN || word < h.wn);
-        const uint32_t old = (PRED || WIN) ? atom_if(in, h.base + (word << 2), 1u << sh)
-                                           : atom_add(h.base + (word << 2), 1u << sh);
-        const uint32_t cnt = (old >> sh) & 0xFFu;
-        const uint32_t d = lds_u32(h.dsm + ((cnt + 1u) << 2));
-        if (PRED || WIN) {
-            dacc += in ? d : 0u;
-            ovf |= (in && cnt == 0xFFu) ? 1u : 0u;
-        } else {
-            dacc += d;
-            ovf |= cnt == 0xFFu ? 1u : 0u;
-        }
+        // kMagicBits is a multiple of 4: the counter is byte y & 3 of the word at
+        // byte offset (y & ~3) - kMagicBits of the full table
+        const uint32_t off = (y & ~3u) - h.boff;
+        const bool in = (!PRED || valid) && (!WIN || off < h.wn4);
+        const uint32_t inc = byte_at(1u, y);
+        const uint32_t old = (PRED || WIN) ? atom_if(in, h.base + off, inc) : atom_add(h.base + off, inc);
+        const uint32_t cnt = byte_from(old, y);   // 0 where nothing was counted
+        const uint32_t d = lds_u32(h.dsm + 4u + (cnt << 2));
+        dacc += (PRED || WIN) ? (in ? d : 0u) : d;
+        ovf = max(ovf, cnt);
     }
 }
 
@@ -302,14 +333,16 @@ struct EvalOut {
 };
 
 // Fast path for one bit-width over this thread's elements (pairs, packed
-// f32x2 adds, subtracts and FMAs; the reconstruction product stays a scalar
-// multiply, rounded on its own and never fused with the subtraction after it).
+// f32x2 adds, subtracts and FMAs).  The reconstruction product (q - Z) S is an
+// FMA with a zero addend: the same single rounding as the product, and an FMA
+// result is never fused with the subtraction after it.
 template <int T, int EPT, int MODE, bool BOTTOM, bool FULL, bool WIN, bool PROBE>
-__device__ __forceinline__ void eval_fast(const float (&c)[EPT], const float (&u)[EPT], int nvalid,
+__device__ __forceinline__ void eval_fast(const float2 (&c)[EPT / 2], const float2 (&u)[EPT / 2], int nvalid,
                                           const BitParam &p, const HistPass &h, uint16_t *codes,
                                           EvalOut &o) {
     const float2 tw = make_float2(p.twob, p.twob), zz = make_float2(p.Z, p.Z);
     const float2 mg = make_float2(kMagic, kMagic), mz = make_float2(p.MZ, p.MZ);
+    const float2 ss = make_float2(p.Ss, p.Ss), zero = make_float2(0.0f, 0.0f);
     float2 s2 = make_float2(0.0f, 0.0f);
     float la = 0.0f, lb = 0.0f, lm = 0.0f;
     uint32_t dacc = 0, ovf = 0;   // delta sums: at most EPT * 2^26 < 2^32
@@ -317,7 +350,7 @@ __device__ __forceinline__ void eval_fast(const float (&c)[EPT], const float (&u
     for (int e = 0; e < EPT; e += 2) {
         const int i0 = e * T + (int)threadIdx.x, i1 = i0 + T;
         const bool v0 = FULL || i0 < nvalid, v1 = FULL || i1 < nvalid;
-        const float2 x = ffma2(make_float2(u[e], u[e + 1]), tw, zz);
+        const float2 x = ffma2(u[e / 2], tw, zz);
         float2 y = fadd2(x, mg);
         y.x = fminf(y.x, p.ytop);
         y.y = fminf(y.y, p.ytop);
@@ -326,8 +359,8 @@ __device__ __forceinline__ void eval_fast(const float (&c)[EPT], const float (&u
             y.y = fmaxf(y.y, kMagic);
         }
         const float2 d = fsub2(y, mz);
-        const float2 ch = make_float2(__fmul_rn(d.x, p.Ss), __fmul_rn(d.y, p.Ss));
-        float2 er = fsub2(ch, make_float2(c[e], c[e + 1]));
+        const float2 ch = ffma2(d, ss, zero);   // d = q - Z is never -0
+        float2 er = fsub2(ch, c[e / 2]);
         if (!FULL) {
             er.x = v0 ? er.x : 0.0f;
             er.y = v1 ? er.y : 0.0f;
@@ -348,12 +381,12 @@ __device__ __forceinline__ void eval_fast(const float (&c)[EPT], const float (&u
     o.l1 = __fadd_rn(la, lb);
     o.linf = lm;
     o.dacc = dacc;
-    o.ovf = ovf;
+    o.ovf = ovf >= 0xFFu;
 }
 
 // Literal per-element formula (divisions, both clamps); any group.
 template <int T, int EPT, int MODE, bool WIN, bool PROBE>
-__device__ __forceinline__ void eval_generic(const float (&c)[EPT], int nvalid, const BitParam &p,
+__device__ __forceinline__ void eval_generic(const float2 (&c2)[EPT / 2], int nvalid, const BitParam &p,
                                              const HistPass &h, uint16_t *codes, EvalOut &o) {
     float s = 0.0f, a = 0.0f, m = 0.0f;
     uint32_t dacc = 0, ovf = 0;
@@ -361,11 +394,12 @@ __device__ __forceinline__ void eval_generic(const float (&c)[EPT], int nvalid, 
     for (int e = 0; e < EPT; e++) {
         const int i = e * T + (int)threadIdx.x;
         const bool valid = i < nvalid;
-        const float x = __fadd_rn(__fdiv_rn(c[e], p.Ss), p.Z);   // c'/S' == c/S exactly
+        const float ce = (e & 1) ? c2[e / 2].y : c2[e / 2].x;
+        const float x = __fadd_rn(__fdiv_rn(ce, p.Ss), p.Z);   // c'/S' == c/S exactly
         const float xc = fminf(fmaxf(x, 0.0f), p.top);
         const int q = __float2int_rn(xc);
         const float qz = __fsub_rn(__int2float_rn(q), p.Z);
-        float er = __fsub_rn(__fmul_rn(qz, p.Ss), c[e]);
+        float er = __fsub_rn(__fmul_rn(qz, p.Ss), ce);
         er = valid ? er : 0.0f;
         s = __fmaf_rn(er, er, s);
         a = __fadd_rn(a, fabsf(er));
@@ -377,7 +411,7 @@ __device__ __forceinline__ void eval_generic(const float (&c)[EPT], int nvalid, 
     o.l1 = a;
     o.linf = m;
     o.dacc = dacc;
-    o.ovf = ovf;
+    o.ovf = ovf >= 0xFFu;
 }
 
 // The fast path runs for warps whose elements are all valid, in groups whose
@@ -386,7 +420,7 @@ __device__ __forceinline__ void eval_generic(const float (&c)[EPT], int nvalid, 
 // codes and errors.  WIN: only the codes of the pass's window are counted (a
 // table larger than its region).
 template <int T, int EPT, int MODE, bool WIN, bool PROBE>
-__device__ __forceinline__ void eval_dispatch(const float (&c)[EPT], const float (&u)[EPT], int nvalid,
+__device__ __forceinline__ void eval_dispatch(const float2 (&c)[EPT / 2], const float2 (&u)[EPT / 2], int nvalid,
                                               bool full, bool generic, const BitParam &p,
                                               const HistPass &h, uint16_t *codes, EvalOut &o) {
     if (!generic && full && p.path == kFast)
@@ -398,13 +432,14 @@ __device__ __forceinline__ void eval_dispatch(const float (&c)[EPT], const float
 // Count-only pass over one window of a pair or byte table: the codes of the
 // evaluation pass (same operations), no error sums.
 template <int T, int EPT, int MODE>
-__device__ __forceinline__ void count_window(const float (&c)[EPT], const float (&u)[EPT], int nvalid,
-                                             bool generic, const BitParam &p, const HistPass &h,
+__device__ __forceinline__ void count_window(const float2 (&c)[EPT / 2], const float2 (&u)[EPT / 2],
+                                             int nvalid, bool generic, const BitParam &p, const HistPass &h,
                                              uint32_t &dacc, uint32_t &ovf) {
     if (generic) {
 #pragma unroll
         for (int e = 0; e < EPT; e++) {
-            const float x = __fadd_rn(__fdiv_rn(c[e], p.Ss), p.Z);
+            const float ce = (e & 1) ? c[e / 2].y : c[e / 2].x;
+            const float x = __fadd_rn(__fdiv_rn(ce, p.Ss), p.Z);
             const uint32_t y = kMagicBits + (uint32_t)__float2int_rn(fminf(fmaxf(x, 0.0f), p.top));
             hist_count<MODE, true, true>(e * T + (int)threadIdx.x < nvalid, y, h, dacc, ovf);
         }
@@ -413,7 +448,8 @@ __device__ __forceinline__ void count_window(const float (&c)[EPT], const float 
         const float lo = p.path == kFastBottom ? kMagic : -FLT_MAX;
 #pragma unroll
         for (int e = 0; e < EPT; e++) {
-            float y = __fadd_rn(__fmaf_rn(u[e], p.twob, p.Z), kMagic);
+            const float ue = (e & 1) ? u[e / 2].y : u[e / 2].x;
+            float y = __fadd_rn(__fmaf_rn(ue, p.twob, p.Z), kMagic);
             y = fmaxf(fminf(y, p.ytop), lo);
             hist_count<MODE, true, true>(e * T + (int)threadIdx.x < nvalid, __float_as_uint(y), h, dacc, ovf);
         }
@@ -427,11 +463,6 @@ __device__ __forceinline__ unsigned long long warp_sum_u64_redux(unsigned long l
     lo = __reduce_add_sync(kFull, lo);
     hi = __reduce_add_sync(kFull, hi);
     return (unsigned long long)lo + ((unsigned long long)hi << 24);
-}
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = __fadd_rn(v, __shfl_xor_sync(kFull, v, o));
-    return v;
 }
 __device__ __forceinline__ float warp_max(float v) {
 #pragma unroll
@@ -462,31 +493,37 @@ __device__ __forceinline__ void load_row(const float *p, float (&v)[W]) {
     }
 }
 
-// Shared-memory layout (dynamic):
-//   regionA[a_words] | regionB[b_words] | bdelta[kByteDelta] | part2[n_opts][T/2] (float2)
-//   | hpart[n_opts][T/32] (u64) | plinf[n_opts][T/32] | bp[n_opts] | mm[T/32][W][2] | flags[n_opts]
+// Shared-memory layout (dynamic).  The per-warp partials of a channel's
+// options are double-buffered by channel parity, so that one warp reduces a
+// channel while the others evaluate the next:
+//   regionA[a_words] | regionB[b_words] | bdelta[kByteDelta]
+//   | part2[2][n_opts][NW] (float2) | hpart[2][n_opts][NW] (u64) | plinf[2][n_opts][NW]
+//   | bp[W][n_opts] | ch[W] | mm[NW][W][2] | flags[2][n_opts]
 struct Smem {
     uint32_t *ra, *rb, *bdelta, *flags;
     float2 *part2;
     unsigned long long *hpart;
     float *plinf, *mm;
     BitParam *bp;
+    ChanParam *ch;
 };
 
 __host__ __device__ inline size_t smem_layout(int T, int W, int a_words, int b_words, int n_opts,
                                               size_t *o) {
+    const int NW = T / 32;
     size_t off = 0;
     o[0] = off; off += (size_t)a_words * 4;
     o[1] = off; off += (size_t)b_words * 4;
     o[2] = off; off += (size_t)kByteDelta * 4;
     off = (off + 15) & ~(size_t)15;
-    o[3] = off; off += (size_t)n_opts * (T / 2) * 8;
-    o[4] = off; off += (size_t)n_opts * (T / 32) * 8;
-    o[5] = off; off += (size_t)n_opts * (T / 32) * 4;
+    o[3] = off; off += (size_t)2 * n_opts * NW * 8;
+    o[4] = off; off += (size_t)2 * n_opts * NW * 8;
+    o[5] = off; off += (size_t)2 * n_opts * NW * 4;
     off = (off + 15) & ~(size_t)15;
-    o[6] = off; off += (size_t)n_opts * sizeof(BitParam);
-    o[7] = off; off += (size_t)(T / 32) * W * 2 * 4;
-    o[8] = off; off += (size_t)n_opts * 4;
+    o[6] = off; off += (size_t)W * n_opts * sizeof(BitParam);
+    o[7] = off; off += (size_t)W * sizeof(ChanParam);
+    o[8] = off; off += (size_t)NW * W * 2 * 4;
+    o[9] = off; off += (size_t)2 * n_opts * 4;
     return (off + 15) & ~(size_t)15;
 }
 
@@ -523,77 +560,72 @@ __device__ void probe_degenerate(uint32_t *out, int bins, int nvalid) {
 }
 
 // After every count of region A is in: sum L(h) of the scanned tables, clear
-// every table, and write the hpart rows of the scanned options.  Each option is
-// finished by one warp (options round-robin over the warps), so the table
-// scans and their L(h) lookups of all options are in flight together.
+// every table, and add each option's sum to its hpart row.  Every thread takes
+// bins of every option (a lane table's bin is its 32 lane columns, read as
+// 16-byte chunks in a rotated order so that eight threads hit eight distinct
+// bank groups), so the work is spread evenly over the warps; the integer sums
+// do not depend on which thread adds what.
 template <int T, bool PROBE>
-__device__ void finish_small(const KernelArgs &A, const Smem &sm, int nvalid, int64_t item) {
+__device__ void finish_small(const KernelArgs &A, const Smem &sm, const BitParam *bpw, int par,
+                             int nvalid, int64_t item) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int NW = T / 32;
-    for (int k = warp; k < A.n_small; k += NW) {
-        const int b = sm.bp[k].b, mode = A.opt_mode[k];
-        const int bins = 1 << b;
+    const int n_opts = A.opt_hi - A.opt_lo;
+    for (int k = 0; k < A.n_small; k++) {
+        const BitParam &bp = bpw[k];
+        const int bins = 1 << bp.b;
         uint32_t *t = sm.ra + A.opt_off[k];
         uint32_t *pout = PROBE ? A.hist_out + item * A.hist_stride + A.hist_off[A.opt_lo + k] : nullptr;
-        if (sm.bp[k].path == kDegenerate) {
-            if (PROBE)
-                for (int j = lane; j < bins; j += 32) pout[j] = j == 0 ? (uint32_t)nvalid : 0u;
+        if (bp.path == kDegenerate) {
+            if (PROBE) probe_degenerate<T>(pout, bins, nvalid);
             continue;   // table untouched; hpart written by the evaluation pass
         }
-        unsigned long long hacc = 0ull;
-        if (mode == kLane) {
-            // bin r's 32 lane columns are summed across the warp; lane r % 32 keeps
-            // the total (at most two bins per lane for b <= 6)
-            uint32_t mine0 = 0, mine1 = 0;
-#pragma unroll 4
-            for (int bin = 0; bin < bins; bin++) {
-                const uint32_t v = t[bin * 32 + lane];
-                t[bin * 32 + lane] = 0u;
-                const uint32_t s = __reduce_add_sync(kFull, v);
-                if (bin < 32) mine0 = lane == bin ? s : mine0;
-                else mine1 = lane == bin - 32 ? s : mine1;
-                if (PROBE && lane == 0) pout[bin] = s;
+        unsigned long long acc = 0ull;
+        if (k < A.n_lane) {
+            for (int j = threadIdx.x; j < bins; j += T) {
+                uint4 *row = reinterpret_cast<uint4 *>(t + j * 32);
+                uint32_t s = 0;
+#pragma unroll
+                for (int q = 0; q < 8; q++) {
+                    const uint4 v = row[(q + j) & 7];
+                    s += v.x + v.y + v.z + v.w;
+                }
+#pragma unroll
+                for (int q = 0; q < 8; q++) row[(q + j) & 7] = make_uint4(0u, 0u, 0u, 0u);
+                acc += ld_keep(&A.ltab[s]);
+                if (PROBE) pout[j] = s;
             }
-            hacc = ld_keep(&A.ltab[mine0]) + ld_keep(&A.ltab[mine1]);   // L(0) = 0
-        } else if (mode == kDirect) {
-            // branch-free: L(0) = 0, so an empty bin adds nothing
-#pragma unroll 8
-            for (int bin = lane; bin < bins; bin += 32) {
-                const uint32_t v = t[bin];
-                t[bin] = 0u;
-                hacc += ld_keep(&A.ltab[v]);
-                if (PROBE) pout[bin] = v;
-            }
-        } else {
-            // 16-bit pairs: the delta sums were written by the evaluation pass
-            const int words = A.opt_words[k];
-            for (int j = lane; j < words; j += 32) {
+        } else if (k < A.n_lane + A.n_direct) {
+            // L(0) = 0, so an empty bin adds nothing
+            for (int j = threadIdx.x; j < bins; j += T) {
                 const uint32_t v = t[j];
                 t[j] = 0u;
-                if (PROBE) {
-                    if (2 * j < bins) pout[2 * j] = v & 0xFFFFu;
-                    if (2 * j + 1 < bins) pout[2 * j + 1] = v >> 16;
-                }
+                acc += ld_keep(&A.ltab[v]);
+                if (PROBE) pout[j] = v;
             }
+        } else {
+            // 16-bit pairs: the delta sums were added by the evaluation pass
+            if (PROBE) probe_packed_clear<T>(t, A.opt_words[k], 2, 0, bins, pout);
+            else clear_words<T>(t, A.opt_words[k]);
             continue;
         }
-        hacc = warp_sum_u64_redux(hacc);
-        // this warp's sum is the option's total: the other warps' slots are zero
-        for (int j = lane; j < NW; j += 32) sm.hpart[k * NW + j] = j == 0 ? hacc : 0ull;
+        acc = warp_sum_u64_redux(acc);
+        if (lane == 0 && acc != 0ull) atomicAdd(&sm.hpart[(par * n_opts + k) * NW + warp], acc);
     }
 }
 
 // One evaluation pass of option k: codes, errors and counts into table `t`;
-// per-thread partials into shared memory (pairs of lanes combined).
-template <int T, int EPT, bool PROBE>
-__device__ __forceinline__ void run_option(const KernelArgs &A, const Smem &sm, int k, uint32_t *t,
-                                           uint32_t wn, const float (&cw)[EPT], const float (&u)[EPT],
+// the warp's sums into its slot of the option's partials (parity `par`).
+template <int T, int EPT, bool PROBE, int MODE, bool WIN>
+__device__ __forceinline__ void run_option(const KernelArgs &A, const Smem &sm, int k, int par,
+                                           const BitParam &pp, uint32_t *t, uint32_t wn,
+                                           const float2 (&cw)[EPT / 2], const float2 (&u)[EPT / 2],
                                            int nvalid, unsigned long long lnv, bool full, bool any_slow,
                                            uint16_t *codes) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int NW = T / 32;
-    const BitParam p = sm.bp[k];
-    const int mode = A.opt_mode[k];
+    const int n_opts = A.opt_hi - A.opt_lo;
+    const BitParam p = pp;
     EvalOut o{0.0f, 0.0f, 0.0f, 0u, 0u};
     unsigned long long hdeg = 0ull;
     if (p.path == kDegenerate) {
@@ -610,42 +642,131 @@ __device__ __forceinline__ void run_option(const KernelArgs &A, const Smem &sm, 
         h.base = tb;
         h.wlo = 0u;
         h.wn = wn;
+        h.boff = kMagicBits;
+        h.wn4 = wn * 4u;
         h.dtab = A.dtab;
         h.dsm = (uint32_t)__cvta_generic_to_shared(sm.bdelta);
-        switch (mode) {
-            case kLane: eval_dispatch<T, EPT, kLane, false, PROBE>(cw, u, nvalid, full, generic, p, h, codes, o); break;
-            case kDirect: eval_dispatch<T, EPT, kDirect, false, PROBE>(cw, u, nvalid, full, generic, p, h, codes, o); break;
-            case kPair: eval_dispatch<T, EPT, kPair, false, PROBE>(cw, u, nvalid, full, generic, p, h, codes, o); break;
-            default:
-                // byte counters; a table larger than region B is counted here in its
-                // first window only (the others come after a barrier)
-                if (A.opt_windows[k] > 1)
-                    eval_dispatch<T, EPT, kByte, true, PROBE>(cw, u, nvalid, full, generic, p, h, codes, o);
-                else
-                    eval_dispatch<T, EPT, kByte, false, PROBE>(cw, u, nvalid, full, generic, p, h, codes, o);
-                break;
+        eval_dispatch<T, EPT, MODE, WIN, PROBE>(cw, u, nvalid, full, generic, p, h, codes, o);
+    }
+    // the warp's sums, in a fixed shuffle tree: the first step leaves the SSE
+    // halves in lanes 0-15 and the L1 halves in lanes 16-31, so that one tree
+    // of four more steps ends with the SSE in lane 0 and the L1 in lane 16
+    const bool upper = (lane & 16) != 0;
+    float sl = __fadd_rn(upper ? o.l1 : o.sse, __shfl_xor_sync(kFull, upper ? o.sse : o.l1, 16));
+#pragma unroll
+    for (int off = 8; off > 0; off >>= 1) sl = __fadd_rn(sl, __shfl_xor_sync(kFull, sl, off));
+    const uint32_t lmax = __reduce_max_sync(kFull, __float_as_uint(o.linf));
+    constexpr bool kDelta = MODE == kPair || MODE == kByte;
+    const unsigned long long hs = warp_sum_u64_redux((unsigned long long)o.dacc + hdeg);
+    const uint32_t ovf = kDelta ? __any_sync(kFull, o.ovf != 0u) : 0u;
+    const int slot = (par * n_opts + k) * NW + warp;
+    if (lane == 16) sm.part2[slot].y = sl;
+    if (lane == 0) {
+        sm.part2[slot].x = sl;
+        sm.plinf[slot] = __uint_as_float(lmax);
+        sm.hpart[slot] = hs;
+        if (ovf) sm.flags[par * n_opts + k] = 1u;
+    }
+}
+
+// Sums of one channel's options over the warps' slots (fixed order), written
+// to the table; the slots' flags are reset for the channel after next.
+template <int T>
+__device__ __forceinline__ void reduce_channel(const KernelArgs &A, const Smem &sm, const CostSeg &S,
+                                               int par, int64_t item, int kexp, unsigned long long lnv) {
+    constexpr int NW = T / 32;
+    const int n_opts = A.opt_hi - A.opt_lo;
+    const int j = threadIdx.x & 31;
+    if (j >= n_opts) return;
+    float a = 0.0f, b = 0.0f, cmax = 0.0f;
+    unsigned long long hs = 0ull;
+    const int base = (par * n_opts + j) * NW;
+#pragma unroll
+    for (int q = 0; q < NW; q++) {
+        const float2 v = sm.part2[base + q];
+        a = __fadd_rn(a, v.x);
+        b = __fadd_rn(b, v.y);
+        cmax = fmaxf(cmax, sm.plinf[base + q]);
+        hs += sm.hpart[base + q];
+    }
+    sm.flags[par * n_opts + j] = 0u;
+    const int64_t o = item * A.n_bits + A.opt_lo + j;
+    // undo the 2^k scale in FP64 (exact powers of two)
+    const double inv = __longlong_as_double((long long)(1023 - kexp) << 52);
+    const double inv2 = __longlong_as_double((long long)(1023 - 2 * kexp) << 52);
+    S.sse[o] = (double)a * inv2;
+    S.l1[o] = (double)b * inv;
+    S.linf[o] = (float)((double)cmax * inv);
+    S.hbits[o] = (double)(long long)(lnv - hs) * (1.0 / 4194304.0);   // 2^-22
+}
+
+// The parameters of option k (bit-width b) of a channel (Sec. III-D): S, Z, and
+// which evaluation path the group takes.
+__device__ __forceinline__ BitParam make_param(int b, float m, float M, float R, float s1, float s2) {
+    BitParam p;
+    p.b = b;
+    p.twob = (float)(1u << b);
+    p.top = p.twob - 1.0f;
+    p.ytop = kMagic + p.top;
+    const float S_ = __fdiv_rn(R, p.twob);
+    p.Ss = __fmul_rn(__fmul_rn(S_, s1), s2);
+    if (S_ == 0.0f) {
+        p.path = kDegenerate;
+        p.Z = 0.0f;
+        p.MZ = kMagic;
+    } else {
+        p.Z = rintf(__fsub_rn(p.twob, __fdiv_rn(M, S_)));
+        p.MZ = __fadd_rn(kMagic, p.Z);
+        if (S_ < FLT_MIN || fabsf(p.Z) >= 4194304.0f) {
+            p.path = kGeneric;
+        } else {
+            // the group minimum gives the smallest x: lower clamp only if it rounds below 0
+            const float um = __fdiv_rn(m, R);
+            const float ym = __fadd_rn(__fmaf_rn(um, p.twob, p.Z), kMagic);
+            p.path = ym < kMagic ? kFastBottom : kFast;
         }
     }
-    float2 sl = make_float2(o.sse, o.l1);
-    sl.x = __fadd_rn(sl.x, __shfl_xor_sync(kFull, sl.x, 1));
-    sl.y = __fadd_rn(sl.y, __shfl_xor_sync(kFull, sl.y, 1));
-    if ((lane & 1) == 0) sm.part2[k * (T / 2) + (threadIdx.x >> 1)] = sl;
-    const uint32_t lmax = __reduce_max_sync(kFull, __float_as_uint(o.linf));
-    const bool delta = mode == kPair || mode == kByte || p.path == kDegenerate;
-    unsigned long long hs = 0ull;
-    if (delta) hs = warp_sum_u64_redux((unsigned long long)o.dacc + hdeg);
-    const uint32_t ovf = __any_sync(kFull, o.ovf != 0u);
-    if (lane == 0) {
-        sm.plinf[k * NW + warp] = __uint_as_float(lmax);
-        if (delta) sm.hpart[k * NW + warp] = hs;
-        if (ovf) sm.flags[k] = 1u;
+    return p;
+}
+
+// A large option whose byte counters overflowed: count it again exactly with
+// 16-bit pairs, in windows of region B (which this clears first), and replace
+// the warps' entropy sums.
+template <int T, int EPT, bool PROBE>
+__device__ void recount_pairs(const KernelArgs &A, const Smem &sm, int k, int par, const BitParam &p,
+                              const float2 (&cv)[EPT / 2], const float2 (&uv)[EPT / 2], int nvalid,
+                              bool generic, uint32_t *pout) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NW = T / 32;
+    const int n_opts = A.opt_hi - A.opt_lo;
+    const int bins = 1 << p.b;
+    HistPass h;
+    h.base = (uint32_t)__cvta_generic_to_shared(sm.rb);
+    h.dtab = A.dtab;
+    h.dsm = (uint32_t)__cvta_generic_to_shared(sm.bdelta);
+    h.lane_base = h.dbase = 0u;
+    uint32_t dacc = 0, ovf = 0;
+    clear_words<T>(sm.rb, A.b_words);
+    const int rw = A.b_words;
+#pragma unroll 1
+    for (int win = 0; win < A.opt_rwindows[k]; win++) {
+        __syncthreads();
+        h.wlo = (uint32_t)win * rw;
+        h.wn = (uint32_t)rw;
+        count_window<T, EPT, kPair>(cv, uv, nvalid, generic, p, h, dacc, ovf);
+        __syncthreads();
+        if (PROBE) probe_packed_clear<T>(sm.rb, rw, 2, (int64_t)win * rw * 2, bins, pout);
+        else clear_words<T>(sm.rb, rw);
     }
+    const unsigned long long hs = warp_sum_u64_redux((unsigned long long)dacc);
+    if (lane == 0) sm.hpart[(par * n_opts + k) * NW + warp] = hs;
 }
 
 // TM: the item is a whole slab (W = 8), staged in TMEM at column base `tm`
 // (this thread's lane and column block); else the W channels stay in registers.
+// `par` is the parity of the partials' buffers, carried from item to item.
 template <int T, int EPT, int W, bool PROBE, bool TM>
-__device__ void process_item(const KernelArgs &A, const Smem &sm, int64_t work, uint32_t tm) {
+__device__ void process_item(const KernelArgs &A, const Smem &sm, int64_t work, uint32_t tm, int &par) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int NW = T / 32;
     // ---- decode the work item
@@ -671,9 +792,10 @@ __device__ void process_item(const KernelArgs &A, const Smem &sm, int64_t work, 
     // every element of this warp is valid (warp-uniform)
     const bool full = __all_sync(kFull, (EPT - 1) * T + (int)threadIdx.x < nvalid);
     const unsigned long long lnv = __ldg(&A.ltab[nvalid]);   // L(n) of the group
+    const int n_opts = A.opt_hi - A.opt_lo;
 
     // ---- gather: each element's W channels from its slab row, and the
-    // per-thread min / max of every channel of the chunk
+    // per-thread min / max of every channel
     float v[TM ? 1 : W][EPT];   // TM: the channel being evaluated; else all W channels
     float tmn[W], tmx[W];
 #pragma unroll
@@ -735,7 +857,7 @@ __device__ void process_item(const KernelArgs &A, const Smem &sm, int64_t work, 
         }
     }
 
-    // ---- group min / max of every channel of the chunk
+    // ---- warp min / max of every channel
 #pragma unroll
     for (int w = 0; w < W; w++) {
         const float mn = warp_min(tmn[w]), mx = warp_max(tmx[w]);
@@ -745,103 +867,159 @@ __device__ void process_item(const KernelArgs &A, const Smem &sm, int64_t work, 
         }
     }
     __syncthreads();
-    if (threadIdx.x < W) {
-        int w = threadIdx.x;
-        float a = FLT_MAX, b = -FLT_MAX;
-        for (int k = 0; k < NW; k++) {
-            a = fminf(a, sm.mm[(k * W + w) * 2]);
-            b = fmaxf(b, sm.mm[(k * W + w) * 2 + 1]);
+    // ---- every (channel, option) parameter of the item at once
+    for (int i = threadIdx.x; i < W * n_opts; i += T) {
+        const int w = i / n_opts, k = i - w * n_opts;
+        float m = FLT_MAX, M = -FLT_MAX;
+        for (int q = 0; q < NW; q++) {
+            m = fminf(m, sm.mm[(q * W + w) * 2]);
+            M = fmaxf(M, sm.mm[(q * W + w) * 2 + 1]);
         }
-        sm.mm[w * 2] = a;
-        sm.mm[w * 2 + 1] = b;
-    }
-    __syncthreads();
-
-    const int n_opts = A.opt_hi - A.opt_lo;
-#pragma unroll 1
-    for (int w = 0; w < W; w++) {
-        const int ch = c0 + w;
-        if (ch >= S.C) break;
-        const float m = sm.mm[w * 2], M = sm.mm[w * 2 + 1];
         const float R = __fsub_rn(M, m);
-        const int64_t item = S.item_base + (int64_t)ch * S.n_groups + g;
         // exact power-of-two scale 2^k = s1 * s2 with R * 2^k in [1, 2)
         const int kexp = R > 0.0f ? -ilogbf(R) : 0;
         const int k1 = kexp / 2, k2 = kexp - k1;
         const float s1 = __int_as_float((k1 + 127) << 23), s2 = __int_as_float((k2 + 127) << 23);
-        if (threadIdx.x < n_opts) {
-            BitParam p;
-            p.b = A.bits[A.opt_lo + threadIdx.x];
-            p.twob = (float)(1u << p.b);
-            p.top = p.twob - 1.0f;
-            p.ytop = kMagic + p.top;
-            const float S_ = __fdiv_rn(R, p.twob);
-            p.Ss = __fmul_rn(__fmul_rn(S_, s1), s2);
-            if (S_ == 0.0f) {
-                p.path = kDegenerate;
-                p.Z = 0.0f;
-                p.MZ = kMagic;
-            } else {
-                p.Z = rintf(__fsub_rn(p.twob, __fdiv_rn(M, S_)));
-                p.MZ = __fadd_rn(kMagic, p.Z);
-                if (S_ < FLT_MIN || fabsf(p.Z) >= 4194304.0f) {
-                    p.path = kGeneric;
-                } else {
-                    // the group minimum gives the smallest x: lower clamp only if it rounds below 0
-                    float um = __fdiv_rn(m, R);
-                    float ym = __fadd_rn(__fmaf_rn(um, p.twob, p.Z), kMagic);
-                    p.path = ym < kMagic ? kFastBottom : kFast;
-                }
+        if (k == 0) {
+            ChanParam c;
+            c.m = m;
+            c.M = M;
+            c.Rs = __fmul_rn(__fmul_rn(R, s1), s2);
+            c.rcp = R > 0.0f ? __frcp_rn(c.Rs) : 0.0f;
+            c.s1 = s1;
+            c.s2 = s2;
+            c.kexp = kexp;
+            c.pad = 0;
+            sm.ch[w] = c;
+            if (c0 + w < S.C) {
+                const int64_t item = S.item_base + (int64_t)(c0 + w) * S.n_groups + g;
+                S.cnt[item] = nvalid;
+                S.vmin[item] = m;
+                S.vmax[item] = M;
             }
-            sm.bp[threadIdx.x] = p;
         }
-        if (threadIdx.x == 0) {
-            S.cnt[item] = nvalid;
-            S.vmin[item] = m;
-            S.vmax[item] = M;
-        }
-        // one division per element, shared by every bit-width; then scale the
-        // channel's values in place by 2^k
+        sm.bp[w * n_opts + k] = make_param(A.bits[A.opt_lo + k], m, M, R, s1, s2);
+    }
+    __syncthreads();
+
+    const int n_ld = A.n_lane + A.n_direct;
+#pragma unroll 1
+    for (int w = 0; w < W; w++) {
+        const int ch = c0 + w;
+        if (ch >= S.C) break;
+        const ChanParam cp = sm.ch[w];
+        const BitParam *bpw = sm.bp + w * n_opts;
+        const int64_t item = S.item_base + (int64_t)ch * S.n_groups + g;
         if constexpr (TM) tm_ld<EPT>(tm + (uint32_t)(w * EPT), v[0]);   // this channel's values
-        float u[EPT];
-        int slow = 0;
+        // scale by 2^k (exact), then one correctly rounded division per element,
+        // u = c / R, shared by every bit-width: q0 = c * r with r = RN(1 / R),
+        // and two corrections q' = q + RN(c - q R) r (Markstein's method; the
+        // second remainder is exact because q is then within an ulp, and the
+        // result rounds correctly because r is the correctly rounded reciprocal).
+        // A warp with a nonzero scaled value below 2^-100 takes the literal
+        // formula instead (its quotients may be subnormal, and the remainders of
+        // such tiny values need not be exact); the two paths give the same codes.
+        // (R = 0: r = 0 gives u = 0; such a group is degenerate at every width)
+        float2 cv[EPT / 2], uv[EPT / 2];
+        bool slow = false;
+        const float2 ss1 = make_float2(cp.s1, cp.s1), ss2 = make_float2(cp.s2, cp.s2);
+        const float2 rr = make_float2(cp.rcp, cp.rcp), nR = make_float2(-cp.Rs, -cp.Rs);
 #pragma unroll
-        for (int e = 0; e < EPT; e++) {
-            u[e] = R > 0.0f ? __fdiv_rn(v[0][e], R) : 0.0f;
-            slow |= (u[e] != 0.0f && fabsf(u[e]) <= FLT_MIN && e * T + (int)threadIdx.x < nvalid);
-            v[0][e] = __fmul_rn(__fmul_rn(v[0][e], s1), s2);
+        for (int e = 0; e < EPT; e += 2) {
+            const float2 c2 = fmul2(fmul2(make_float2(v[0][e], v[0][e + 1]), ss1), ss2);
+            cv[e / 2] = c2;
+            float2 q = fmul2(c2, rr);
+            q = ffma2(ffma2(q, nR, c2), rr, q);
+            uv[e / 2] = ffma2(ffma2(q, nR, c2), rr, q);
+            slow |= (fabsf(c2.x) < 7.8886090522101181e-31f && c2.x != 0.0f) ||   // 2^-100
+                    (fabsf(c2.y) < 7.8886090522101181e-31f && c2.y != 0.0f);
         }
-        const bool any_slow = __syncthreads_or(slow) != 0;   // also publishes bp
+        const bool any_slow = __any_sync(kFull, slow);
 
         uint16_t *codes = nullptr;
         if (PROBE && A.codes_out)
             codes = A.codes_out + S.code_off + (int64_t)ch * A.n_bits * S.K + gstart;
         const int64_t kstride = S.K;   // codes of consecutive options of a channel
+#define MGS_CODES(k) (codes ? codes + (A.opt_lo + (k)) * kstride : nullptr)
         // ---- bit-widths up to 12: every table of region A, no barrier between them
+        int k = 0;
 #pragma unroll 1
-        for (int k = 0; k < A.n_small; k++)
-            run_option<T, EPT, PROBE>(A, sm, k, sm.ra + A.opt_off[k], 0u, v[0], u, nvalid, lnv, full,
-                                      any_slow, codes ? codes + (A.opt_lo + k) * kstride : nullptr);
+        for (; k < A.n_lane; k++)
+            run_option<T, EPT, PROBE, kLane, false>(A, sm, k, par, bpw[k], sm.ra + A.opt_off[k], 0u, cv, uv,
+                                                    nvalid, lnv, full, any_slow, MGS_CODES(k));
+#pragma unroll 1
+        for (; k < n_ld; k++)
+            run_option<T, EPT, PROBE, kDirect, false>(A, sm, k, par, bpw[k], sm.ra + A.opt_off[k], 0u, cv,
+                                                      uv, nvalid, lnv, full, any_slow, MGS_CODES(k));
+#pragma unroll 1
+        for (; k < A.n_small; k++)
+            run_option<T, EPT, PROBE, kPair, false>(A, sm, k, par, bpw[k], sm.ra + A.opt_off[k], 0u, cv, uv,
+                                                    nvalid, lnv, full, any_slow, MGS_CODES(k));
+        uint32_t *flags = sm.flags + par * n_opts;
+        if (A.concurrent) {
+            // ---- larger bit-widths, each in its own table of region B (byte
+            // counters): no barrier until every count of the channel is in
+#pragma unroll 1
+            for (; k < n_opts; k++)
+                run_option<T, EPT, PROBE, kByte, false>(A, sm, k, par, bpw[k], sm.rb + A.opt_off[k],
+                                                        (uint32_t)A.opt_words[k], cv, uv, nvalid, lnv, full,
+                                                        any_slow, MGS_CODES(k));
+            __syncthreads();
+            finish_small<T, PROBE>(A, sm, bpw, par, nvalid, item);
+            bool any_ovf = false;
+#pragma unroll 1
+            for (int j = A.n_small; j < n_opts; j++) {
+                const BitParam &p = bpw[j];
+                uint32_t *pout = PROBE ? A.hist_out + item * A.hist_stride + A.hist_off[A.opt_lo + j] : nullptr;
+                if (p.path == kDegenerate) {
+                    if (PROBE) probe_degenerate<T>(pout, 1 << p.b, nvalid);
+                    continue;
+                }
+                if (flags[j] != 0u) {
+                    any_ovf = true;
+                    continue;
+                }
+                if (PROBE) probe_packed_clear<T>(sm.rb + A.opt_off[j], A.opt_words[j], 4, 0, 1 << p.b, pout);
+                else clear_words<T>(sm.rb + A.opt_off[j], A.opt_words[j]);
+            }
+            if (any_ovf) {   // flags are read after the barrier: the same for every thread
+#pragma unroll 1
+                for (int j = A.n_small; j < n_opts; j++) {
+                    const BitParam &p = bpw[j];
+                    if (p.path == kDegenerate || flags[j] == 0u) continue;
+                    __syncthreads();   // the other tables' readouts are done
+                    recount_pairs<T, EPT, PROBE>(
+                        A, sm, j, par, p, cv, uv, nvalid, p.path == kGeneric || any_slow,
+                        PROBE ? A.hist_out + item * A.hist_stride + A.hist_off[A.opt_lo + j] : nullptr);
+                }
+            }
+            k = n_opts;
+        }
         // ---- larger bit-widths one at a time in region B (byte counters)
 #pragma unroll 1
-        for (int k = A.n_small; k < n_opts; k++) {
-            const BitParam p = sm.bp[k];
+        for (; k < n_opts; k++) {
+            const BitParam &p = bpw[k];
             const uint32_t wn = (uint32_t)A.opt_words[k];
-            run_option<T, EPT, PROBE>(A, sm, k, sm.rb, wn, v[0], u, nvalid, lnv, full, any_slow,
-                                      codes ? codes + (A.opt_lo + k) * kstride : nullptr);
+            if (A.opt_windows[k] > 1)
+                run_option<T, EPT, PROBE, kByte, true>(A, sm, k, par, p, sm.rb, wn, cv, uv, nvalid, lnv, full,
+                                                       any_slow, MGS_CODES(k));
+            else
+                run_option<T, EPT, PROBE, kByte, false>(A, sm, k, par, p, sm.rb, wn, cv, uv, nvalid, lnv, full,
+                                                        any_slow, MGS_CODES(k));
             __syncthreads();   // every count of this pass (and of region A) is in
-            if (k == A.n_small) finish_small<T, PROBE>(A, sm, nvalid, item);
+            if (k == A.n_small) finish_small<T, PROBE>(A, sm, bpw, par, nvalid, item);
             if (p.path != kDegenerate) {
                 const bool generic = p.path == kGeneric || any_slow;
                 const int bins = 1 << p.b;
                 uint32_t *pout = PROBE ? A.hist_out + item * A.hist_stride + A.hist_off[A.opt_lo + k] : nullptr;
+                unsigned long long *hslot = sm.hpart + (par * n_opts + k) * NW + warp;
                 HistPass h;
                 h.base = (uint32_t)__cvta_generic_to_shared(sm.rb);
                 h.dtab = A.dtab;
                 h.dsm = (uint32_t)__cvta_generic_to_shared(sm.bdelta);
                 h.lane_base = h.dbase = 0u;
                 uint32_t dacc = 0, ovf = 0;
-                if (sm.flags[k] == 0u) {
+                if (flags[k] == 0u) {
                     // byte counters held: the first window is complete
                     if (PROBE) probe_packed_clear<T>(sm.rb, (int)wn, 4, 0, bins, pout);
                     else clear_words<T>(sm.rb, (int)wn);
@@ -851,18 +1029,20 @@ __device__ void process_item(const KernelArgs &A, const Smem &sm, int64_t work, 
                             __syncthreads();
                             h.wlo = (uint32_t)win * wn;
                             h.wn = wn;
-                            count_window<T, EPT, kByte>(v[0], u, nvalid, generic, p, h, dacc, ovf);
+                            h.boff = kMagicBits + 4u * h.wlo;
+                            h.wn4 = wn * 4u;
+                            count_window<T, EPT, kByte>(cv, uv, nvalid, generic, p, h, dacc, ovf);
                             __syncthreads();
                             if (PROBE) probe_packed_clear<T>(sm.rb, (int)wn, 4, (int64_t)win * wn * 4, bins, pout);
                             else clear_words<T>(sm.rb, (int)wn);
                         }
                         // a counter of a later window may have overflowed too
-                        const uint32_t any = __syncthreads_or(ovf != 0u);
+                        const uint32_t any = __syncthreads_or(ovf >= 0xFFu);
                         if (any) {
-                            if (threadIdx.x == 0) sm.flags[k] = 1u;
+                            if (threadIdx.x == 0) flags[k] = 1u;
                         } else {
                             const unsigned long long hs = warp_sum_u64_redux((unsigned long long)dacc);
-                            if (lane == 0) sm.hpart[k * NW + warp] += hs;
+                            if (lane == 0) *hslot += hs;
                         }
                         dacc = 0;
                         __syncthreads();   // the flag of the later windows is visible
@@ -870,62 +1050,25 @@ __device__ void process_item(const KernelArgs &A, const Smem &sm, int64_t work, 
                     // one window: the flag was set by the evaluation pass, before the
                     // barrier after it, and nothing has written it since
                 }
-                if (sm.flags[k] != 0u) {
-                    // some counter reached 255: count again exactly with 16-bit pairs,
-                    // in windows of region B
-                    clear_words<T>(sm.rb, A.b_words);
-                    const int rw = A.b_words;
-#pragma unroll 1
-                    for (int win = 0; win < A.opt_rwindows[k]; win++) {
-                        __syncthreads();
-                        h.wlo = (uint32_t)win * rw;
-                        h.wn = (uint32_t)rw;
-                        count_window<T, EPT, kPair>(v[0], u, nvalid, generic, p, h, dacc, ovf);
-                        __syncthreads();
-                        if (PROBE) probe_packed_clear<T>(sm.rb, rw, 2, (int64_t)win * rw * 2, bins, pout);
-                        else clear_words<T>(sm.rb, rw);
-                    }
-                    const unsigned long long hs = warp_sum_u64_redux((unsigned long long)dacc);
-                    if (lane == 0) sm.hpart[k * NW + warp] = hs;
-                }
+                if (flags[k] != 0u)   // some counter reached 255: count again exactly
+                    recount_pairs<T, EPT, PROBE>(A, sm, k, par, p, cv, uv, nvalid, generic, pout);
             } else if (PROBE) {
                 probe_degenerate<T>(A.hist_out + item * A.hist_stride + A.hist_off[A.opt_lo + k],
                                     1 << p.b, nvalid);
             }
             if (k + 1 < n_opts) __syncthreads();   // region B is clear for the next option
         }
-        if (A.n_small == n_opts) {
+#undef MGS_CODES
+        if (A.n_small == n_opts && !A.concurrent) {
             __syncthreads();
-            finish_small<T, PROBE>(A, sm, nvalid, item);
+            finish_small<T, PROBE>(A, sm, bpw, par, nvalid, item);
         }
+        // every table is clear and every partial of this channel is in; one warp
+        // reduces them while the others go on with the next channel (its partials
+        // take the other buffers)
         __syncthreads();
-        // ---- reduce the partials and write this channel's entries
-        for (int k = warp; k < n_opts; k += NW) {
-            float2 acc = make_float2(0.0f, 0.0f);
-#pragma unroll
-            for (int j = 0; j < T / 64; j++) {
-                const float2 q = sm.part2[k * (T / 2) + j * 32 + lane];
-                acc.x = __fadd_rn(acc.x, q.x);
-                acc.y = __fadd_rn(acc.y, q.y);
-            }
-            const float a = warp_sum(acc.x), b = warp_sum(acc.y);
-            float cmax = lane < NW ? sm.plinf[k * NW + lane] : 0.0f;
-            cmax = warp_max(cmax);
-            unsigned long long hs = 0;
-            for (int j = lane; j < NW; j += 32) hs += sm.hpart[k * NW + j];
-            hs = warp_sum_u64_redux(hs);
-            if (lane == 0) {
-                const int64_t o = item * A.n_bits + A.opt_lo + k;
-                // undo the 2^k scale in FP64 (exact powers of two)
-                const double inv = __longlong_as_double((long long)(1023 - kexp) << 52);
-                const double inv2 = __longlong_as_double((long long)(1023 - 2 * kexp) << 52);
-                S.sse[o] = (double)a * inv2;
-                S.l1[o] = (double)b * inv;
-                S.linf[o] = (float)((double)cmax * inv);
-                S.hbits[o] = (double)(long long)(lnv - hs) * (1.0 / 4194304.0);   // 2^-22
-                sm.flags[k] = 0u;
-            }
-        }
+        if (warp == w % NW) reduce_channel<T>(A, sm, S, par, item, cp.kexp, lnv);
+        par ^= 1;
         // the next channel takes the values of the following one (compile-time
         // register indices)
         if constexpr (!TM) {
@@ -942,7 +1085,7 @@ __global__ void __launch_bounds__(T, MINB)
     k_cost(const __grid_constant__ KernelArgs A, int unused) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n_opts = A.opt_hi - A.opt_lo;
-    size_t o[9];
+    size_t o[10];
     smem_layout(T, W, A.a_words, A.b_words, n_opts, o);
     static_assert(EPT % 2 == 0, "elements are processed in pairs");
     static_assert(T >= 64, "partials are read by whole warps");
@@ -954,11 +1097,13 @@ __global__ void __launch_bounds__(T, MINB)
     sm.hpart = reinterpret_cast<unsigned long long *>(smem_raw + o[4]);
     sm.plinf = reinterpret_cast<float *>(smem_raw + o[5]);
     sm.bp = reinterpret_cast<BitParam *>(smem_raw + o[6]);
-    sm.mm = reinterpret_cast<float *>(smem_raw + o[7]);
-    sm.flags = reinterpret_cast<uint32_t *>(smem_raw + o[8]);
+    sm.ch = reinterpret_cast<ChanParam *>(smem_raw + o[7]);
+    sm.mm = reinterpret_cast<float *>(smem_raw + o[8]);
+    sm.flags = reinterpret_cast<uint32_t *>(smem_raw + o[9]);
     for (int i = threadIdx.x; i < A.a_words + A.b_words; i += T) sm.ra[i] = 0u;
     for (int i = threadIdx.x; i < kByteDelta; i += T) sm.bdelta[i] = i <= 256 ? __ldg(&A.dtab[i]) : 0u;
-    for (int i = threadIdx.x; i < n_opts; i += T) sm.flags[i] = 0u;
+    for (int i = threadIdx.x; i < 2 * n_opts; i += T) sm.flags[i] = 0u;
+    int par = 0;   // parity of the partials' buffers
     // TMEM for the gathered tile: at most 512 / tm_cols CTAs share an SM (the
     // launch pads shared memory so), so the allocation never waits on another
     // CTA of this kernel
@@ -974,7 +1119,7 @@ __global__ void __launch_bounds__(T, MINB)
         tm = s_tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)((warp >> 2) * EPT * W);
     }
     if (A.counter == nullptr) {
-        process_item<T, EPT, W, PROBE, TM>(A, sm, blockIdx.x, tm);
+        process_item<T, EPT, W, PROBE, TM>(A, sm, blockIdx.x, tm, par);
     } else {
         __shared__ int64_t s_work;
         while (true) {
@@ -982,7 +1127,7 @@ __global__ void __launch_bounds__(T, MINB)
             __syncthreads();
             const int64_t work = s_work;
             if (work >= A.n_work) break;
-            process_item<T, EPT, W, PROBE, TM>(A, sm, work, tm);
+            process_item<T, EPT, W, PROBE, TM>(A, sm, work, tm, par);
             __syncthreads();
         }
     }
@@ -1039,7 +1184,8 @@ constexpr int kNumConfigs = sizeof(kConfigs) / sizeof(kConfigs[0]);
 // of one larger option at a time, in windows when region B is smaller than the
 // option's table.
 struct HistPlan {
-    int n_small = 0, a_words = 0, b_words = 0;
+    int n_small = 0, n_lane = 0, n_direct = 0, a_words = 0, b_words = 0;
+    bool concurrent = false;
     int8_t mode[MGS_MAX_OPTIONS] = {}, windows[MGS_MAX_OPTIONS] = {}, rwindows[MGS_MAX_OPTIONS] = {};
     int32_t off[MGS_MAX_OPTIONS] = {}, words[MGS_MAX_OPTIONS] = {};
     size_t smem = 0;
@@ -1049,12 +1195,15 @@ struct HistPlan {
 // 1 KB reserved per CTA, and up to 512 bytes of the kernel's static variables).
 size_t smem_budget(int ctas) { return std::min<size_t>(227 * 1024 - 512, (228 * 1024) / ctas - 1024 - 512); }
 
-HistPlan plan_hist(const ConfigEntry &E, const int32_t *bits, int n_opts) {
+// One layout: options up to `pair_max` bits take region A (lane columns, direct
+// counters, 16-bit pairs), larger ones byte counters in region B, either each
+// in its own table (concurrent) or one after another in the largest window that
+// fits (sequential).
+HistPlan plan_layout(const ConfigEntry &E, const int *bl, int n_opts, int pair_max, bool concurrent) {
     const CostConfig &c = E.cfg;
     HistPlan h;
+    h.concurrent = concurrent;
     const int NW = c.threads / 32;
-    int bl[MGS_MAX_OPTIONS];
-    for (int k = 0; k < n_opts; k++) bl[k] = bits ? bits[k] : MGS_MAX_BITS - n_opts + 1 + k;
     int large_words = 0;
     for (int k = 0; k < n_opts; k++) {
         const int b = bl[k];
@@ -1065,7 +1214,7 @@ HistPlan plan_hist(const ConfigEntry &E, const int32_t *bits, int n_opts) {
         } else if (b <= kDirectMaxBits) {
             mode = kDirect;
             words = 1 << b;
-        } else if (b <= kPairMaxBits) {
+        } else if (b <= pair_max) {
             mode = kPair;
             words = 1 << (b - 1);
         } else {
@@ -1074,36 +1223,58 @@ HistPlan plan_hist(const ConfigEntry &E, const int32_t *bits, int n_opts) {
         }
         words = (words + 3) & ~3;
         h.mode[k] = (int8_t)mode;
+        if (mode == kLane) h.n_lane++;
+        if (mode == kDirect) h.n_direct++;
+        h.words[k] = words;
         if (mode != kByte) {
-            // bit-widths ascend, so the small options form a prefix
+            // bit-widths ascend, so the small options form a prefix (lane, direct, pair)
             h.off[k] = h.a_words;
-            h.words[k] = words;
             h.a_words += words;
             h.n_small = k + 1;
+        } else if (concurrent) {
+            h.off[k] = h.b_words;
+            h.b_words += words;
         } else {
             large_words = std::max(large_words, words);
         }
     }
-    size_t o[9];
-    const size_t fixed = smem_layout(c.threads, c.width, h.a_words, 0, n_opts, o);
-    const size_t budget = smem_budget(E.ctas);
-    int bw = large_words;
-    if (bw > 0) {
-        // region B: the largest table that fits, in whole power-of-two windows
-        int cap = budget > fixed ? (int)((budget - fixed) / 4) : 0;
-        while (bw > cap && bw > 1024) bw >>= 1;
-        bw = std::max(bw, 1024);
+    size_t o[10];
+    if (!concurrent) {
+        const size_t fixed = smem_layout(c.threads, c.width, h.a_words, 0, n_opts, o);
+        const size_t budget = smem_budget(E.ctas);
+        int bw = large_words;
+        if (bw > 0) {
+            // region B: the largest table that fits, in whole power-of-two windows
+            int cap = budget > fixed ? (int)((budget - fixed) / 4) : 0;
+            while (bw > cap && bw > 1024) bw >>= 1;
+            bw = std::max(bw, 1024);
+        }
+        h.b_words = bw;
     }
-    h.b_words = bw;
     for (int k = h.n_small; k < n_opts; k++) {
         const int b = bl[k];
         const int need = std::max(4, 1 << (b - 2)), need_pairs = 1 << (b - 1);
-        h.words[k] = std::min(need, bw);
-        h.windows[k] = (int8_t)((need + bw - 1) / bw);
-        h.rwindows[k] = (int8_t)((need_pairs + bw - 1) / bw);
+        if (!concurrent) h.words[k] = std::min(need, h.b_words);
+        h.windows[k] = (int8_t)(concurrent ? 1 : (need + h.b_words - 1) / h.b_words);
+        h.rwindows[k] = (int8_t)((need_pairs + h.b_words - 1) / h.b_words);
     }
     h.smem = smem_layout(c.threads, c.width, h.a_words, h.b_words, n_opts, o);
     return h;
+}
+
+// The plan of a launch: every large option in its own table if that fits the
+// shared memory of `ctas` CTAs per SM (first with 11 and 12 bits as 16-bit
+// pairs in region A, then as byte counters in region B), else one large option
+// after another.
+HistPlan plan_hist(const ConfigEntry &E, const int32_t *bits, int n_opts) {
+    int bl[MGS_MAX_OPTIONS];
+    for (int k = 0; k < n_opts; k++) bl[k] = bits ? bits[k] : MGS_MAX_BITS - n_opts + 1 + k;
+    const size_t budget = smem_budget(E.ctas);
+    for (int pair_max : {kPairMaxBits, kDirectMaxBits}) {
+        const HistPlan h = plan_layout(E, bl, n_opts, pair_max, true);
+        if (h.smem <= budget) return h;
+    }
+    return plan_layout(E, bl, n_opts, kPairMaxBits, false);
 }
 
 }  // namespace
@@ -1180,6 +1351,9 @@ mgs_status cost_exec_create(mgs_ctx *ctx, const CostLaunch &L, int config, CostE
     const int n_opts = L.opt_hi - L.opt_lo;
     const HistPlan hp = plan_hist(E, L.bits + L.opt_lo, n_opts);
     A.n_small = hp.n_small;
+    A.n_lane = hp.n_lane;
+    A.n_direct = hp.n_direct;
+    A.concurrent = hp.concurrent ? 1 : 0;
     A.a_words = hp.a_words;
     A.b_words = hp.b_words;
     for (int k = 0; k < n_opts; k++) {
