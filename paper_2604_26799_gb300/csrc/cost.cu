@@ -97,6 +97,8 @@ struct KernelArgs {
     int32_t n_small;                  // options [0, n_small) share region A
     int32_t n_lane, n_direct;         // of which [0, n_lane) lane tables, then n_direct direct ones
     int32_t concurrent;               // every large option has its own table in region B
+    int32_t n_units;                  // finishing work of region A: unit u = bins [lo, hi) of option k
+    int16_t unit_opt[MGS_MAX_OPTIONS], unit_lo[MGS_MAX_OPTIONS], unit_hi[MGS_MAX_OPTIONS];
     int32_t a_words, b_words;         // region sizes in 32-bit words
     int8_t opt_mode[MGS_MAX_OPTIONS];
     int8_t opt_windows[MGS_MAX_OPTIONS];    // byte-counter passes of a large option
@@ -259,6 +261,16 @@ __device__ __forceinline__ uint32_t atom_add(uint32_t addr, uint32_t v) {
     uint32_t old;
     asm volatile("atom.shared.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(addr), "r"(v));
     return old;
+}
+// Shared-memory stores executed only where `pred` holds, as predicated
+// instructions: lanes never take different branches around them.
+__device__ __forceinline__ void sts_if(bool pred, uint32_t addr, uint32_t v) {
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q st.shared.u32 [%0], %1;\n\t}"
+                 ::"r"(addr), "r"(v), "r"((uint32_t)pred) : "memory");
+}
+__device__ __forceinline__ void sts_if(bool pred, uint32_t addr, unsigned long long v) {
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q st.shared.u64 [%0], %1;\n\t}"
+                 ::"r"(addr), "l"(v), "r"((uint32_t)pred) : "memory");
 }
 __device__ __forceinline__ uint32_t lds_u32(uint32_t addr) {
     uint32_t v;
@@ -560,57 +572,68 @@ __device__ void probe_degenerate(uint32_t *out, int bins, int nvalid) {
 }
 
 // After every count of region A is in: sum L(h) of the scanned tables, clear
-// every table, and add each option's sum to its hpart row.  Every thread takes
-// bins of every option (a lane table's bin is its 32 lane columns, read as
-// 16-byte chunks in a rotated order so that eight threads hit eight distinct
-// bank groups), so the work is spread evenly over the warps; the integer sums
-// do not depend on which thread adds what.
+// every table, and add each option's sum to the finishing warp's hpart slot.
+// The work is cut on the host into units (a range of one option's bins), one
+// per warp when there are enough: lane l of a warp takes bins lo + l, lo + l +
+// 32, ...; a lane table's bin is its 32 lane columns, read as 16-byte chunks
+// in a rotated order so that eight lanes hit eight distinct bank groups.  The
+// integer sums do not depend on which warp adds what.
 template <int T, bool PROBE>
 __device__ void finish_small(const KernelArgs &A, const Smem &sm, const BitParam *bpw, int par,
                              int nvalid, int64_t item) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int NW = T / 32;
     const int n_opts = A.opt_hi - A.opt_lo;
-    for (int k = 0; k < A.n_small; k++) {
+    const int n_ld = A.n_lane + A.n_direct;
+    for (int un = warp; un < A.n_units; un += NW) {
+        const int k = A.unit_opt[un], lo = A.unit_lo[un], hi = A.unit_hi[un];
         const BitParam &bp = bpw[k];
-        const int bins = 1 << bp.b;
         uint32_t *t = sm.ra + A.opt_off[k];
         uint32_t *pout = PROBE ? A.hist_out + item * A.hist_stride + A.hist_off[A.opt_lo + k] : nullptr;
         if (bp.path == kDegenerate) {
-            if (PROBE) probe_degenerate<T>(pout, bins, nvalid);
+            if (PROBE)
+                for (int j = lo + lane; j < hi; j += 32) pout[j] = j == 0 ? (uint32_t)nvalid : 0u;
             continue;   // table untouched; hpart written by the evaluation pass
         }
-        unsigned long long acc = 0ull;
+        unsigned long long hacc = 0ull;
         if (k < A.n_lane) {
-            for (int j = threadIdx.x; j < bins; j += T) {
-                uint4 *row = reinterpret_cast<uint4 *>(t + j * 32);
+            for (int r = lo + lane; r < hi; r += 32) {
+                uint4 *row = reinterpret_cast<uint4 *>(t + r * 32);
                 uint32_t s = 0;
 #pragma unroll
                 for (int q = 0; q < 8; q++) {
-                    const uint4 v = row[(q + j) & 7];
+                    const uint4 v = row[(q + r) & 7];
                     s += v.x + v.y + v.z + v.w;
                 }
 #pragma unroll
-                for (int q = 0; q < 8; q++) row[(q + j) & 7] = make_uint4(0u, 0u, 0u, 0u);
-                acc += ld_keep(&A.ltab[s]);
-                if (PROBE) pout[j] = s;
+                for (int q = 0; q < 8; q++) row[(q + r) & 7] = make_uint4(0u, 0u, 0u, 0u);
+                hacc += ld_keep(&A.ltab[s]);
+                if (PROBE) pout[r] = s;
             }
-        } else if (k < A.n_lane + A.n_direct) {
+        } else if (k < n_ld) {
             // L(0) = 0, so an empty bin adds nothing
-            for (int j = threadIdx.x; j < bins; j += T) {
+#pragma unroll 8
+            for (int j = lo + lane; j < hi; j += 32) {
                 const uint32_t v = t[j];
                 t[j] = 0u;
-                acc += ld_keep(&A.ltab[v]);
+                hacc += ld_keep(&A.ltab[v]);
                 if (PROBE) pout[j] = v;
             }
         } else {
-            // 16-bit pairs: the delta sums were added by the evaluation pass
-            if (PROBE) probe_packed_clear<T>(t, A.opt_words[k], 2, 0, bins, pout);
-            else clear_words<T>(t, A.opt_words[k]);
+            // 16-bit pairs (two bins a word): the delta sums were added by the evaluation pass
+            for (int j = lo / 2 + lane; j < hi / 2; j += 32) {
+                const uint32_t v = t[j];
+                t[j] = 0u;
+                if (PROBE) {
+                    pout[2 * j] = v & 0xFFFFu;
+                    pout[2 * j + 1] = v >> 16;
+                }
+            }
             continue;
         }
-        acc = warp_sum_u64_redux(acc);
-        if (lane == 0 && acc != 0ull) atomicAdd(&sm.hpart[(par * n_opts + k) * NW + warp], acc);
+        hacc = warp_sum_u64_redux(hacc);
+        if (lane == 0) sm.hpart[(par * n_opts + k) * NW + warp] += hacc;
+        __syncwarp();
     }
 }
 
@@ -659,14 +682,15 @@ __device__ __forceinline__ void run_option(const KernelArgs &A, const Smem &sm, 
     constexpr bool kDelta = MODE == kPair || MODE == kByte;
     const unsigned long long hs = warp_sum_u64_redux((unsigned long long)o.dacc + hdeg);
     const uint32_t ovf = kDelta ? __any_sync(kFull, o.ovf != 0u) : 0u;
+    // the stores are predicated, so that the warp stays converged into the
+    // collectives of the next pass
     const int slot = (par * n_opts + k) * NW + warp;
-    if (lane == 16) sm.part2[slot].y = sl;
-    if (lane == 0) {
-        sm.part2[slot].x = sl;
-        sm.plinf[slot] = __uint_as_float(lmax);
-        sm.hpart[slot] = hs;
-        if (ovf) sm.flags[par * n_opts + k] = 1u;
-    }
+    sts_if(lane == 0 || lane == 16, (uint32_t)__cvta_generic_to_shared(&sm.part2[slot]) + (lane ? 4u : 0u),
+           __float_as_uint(sl));
+    sts_if(lane == 0, (uint32_t)__cvta_generic_to_shared(&sm.plinf[slot]), lmax);
+    sts_if(lane == 0, (uint32_t)__cvta_generic_to_shared(&sm.hpart[slot]), hs);
+    sts_if(lane == 0 && ovf != 0u, (uint32_t)__cvta_generic_to_shared(&sm.flags[par * n_opts + k]), 1u);
+    __syncwarp();
 }
 
 // Sums of one channel's options over the warps' slots (fixed order), written
@@ -828,6 +852,7 @@ __device__ void process_item(const KernelArgs &A, const Smem &sm, int64_t work, 
                     for (int w = 0; w < W; w++) r[j][w] = 0.0f;
                 }
             }
+            __syncwarp();   // the stores below are warp-collective
 #pragma unroll
             for (int w = 0; w < W; w++) {
                 tm_st4(tm + (uint32_t)(w * EPT + e0), r[0][w], r[1][w], r[2][w], r[3][w]);
@@ -1068,6 +1093,7 @@ __device__ void process_item(const KernelArgs &A, const Smem &sm, int64_t work, 
         // take the other buffers)
         __syncthreads();
         if (warp == w % NW) reduce_channel<T>(A, sm, S, par, item, cp.kexp, lnv);
+        __syncwarp();   // converged again before the next channel's collectives
         par ^= 1;
         // the next channel takes the values of the following one (compile-time
         // register indices)
@@ -1186,6 +1212,8 @@ constexpr int kNumConfigs = sizeof(kConfigs) / sizeof(kConfigs[0]);
 struct HistPlan {
     int n_small = 0, n_lane = 0, n_direct = 0, a_words = 0, b_words = 0;
     bool concurrent = false;
+    int n_units = 0;
+    int16_t unit_opt[MGS_MAX_OPTIONS] = {}, unit_lo[MGS_MAX_OPTIONS] = {}, unit_hi[MGS_MAX_OPTIONS] = {};
     int8_t mode[MGS_MAX_OPTIONS] = {}, windows[MGS_MAX_OPTIONS] = {}, rwindows[MGS_MAX_OPTIONS] = {};
     int32_t off[MGS_MAX_OPTIONS] = {}, words[MGS_MAX_OPTIONS] = {};
     size_t smem = 0;
@@ -1259,6 +1287,35 @@ HistPlan plan_layout(const ConfigEntry &E, const int *bl, int n_opts, int pair_m
         h.rwindows[k] = (int8_t)((need_pairs + h.b_words - 1) / h.b_words);
     }
     h.smem = smem_layout(c.threads, c.width, h.a_words, h.b_words, n_opts, o);
+    // finishing units of region A: one per small option, then the costliest
+    // split in two (at a multiple of 32 bins, 64 for 16-bit pairs) until every
+    // warp has one; cost = the lanes' steps x the work of a step
+    auto cost = [&](int u) {
+        const int m = h.mode[h.unit_opt[u]], n = h.unit_hi[u] - h.unit_lo[u];
+        return m == kLane ? (n + 31) / 32 * 24 : m == kDirect ? (n + 31) / 32 * 4 : (n / 2 + 31) / 32;
+    };
+    for (int k = 0; k < h.n_small; k++) {
+        h.unit_opt[h.n_units] = (int16_t)k;
+        h.unit_lo[h.n_units] = 0;
+        h.unit_hi[h.n_units] = (int16_t)std::min(1 << bl[k], 32767);
+        h.n_units++;
+    }
+    while (h.n_units < NW && h.n_units < MGS_MAX_OPTIONS) {
+        int best = -1;
+        for (int u = 0; u < h.n_units; u++) {
+            const int step = h.mode[h.unit_opt[u]] == kPair ? 64 : 32;
+            if (h.unit_hi[u] - h.unit_lo[u] >= 2 * step && (best < 0 || cost(u) > cost(best))) best = u;
+        }
+        if (best < 0) break;
+        const int step = h.mode[h.unit_opt[best]] == kPair ? 64 : 32;
+        const int lo = h.unit_lo[best], hi = h.unit_hi[best];
+        const int mid = lo + (hi - lo) / 2 / step * step;
+        h.unit_opt[h.n_units] = h.unit_opt[best];
+        h.unit_lo[h.n_units] = (int16_t)mid;
+        h.unit_hi[h.n_units] = (int16_t)hi;
+        h.unit_hi[best] = (int16_t)mid;
+        h.n_units++;
+    }
     return h;
 }
 
@@ -1354,6 +1411,12 @@ mgs_status cost_exec_create(mgs_ctx *ctx, const CostLaunch &L, int config, CostE
     A.n_lane = hp.n_lane;
     A.n_direct = hp.n_direct;
     A.concurrent = hp.concurrent ? 1 : 0;
+    A.n_units = hp.n_units;
+    for (int u = 0; u < hp.n_units; u++) {
+        A.unit_opt[u] = hp.unit_opt[u];
+        A.unit_lo[u] = hp.unit_lo[u];
+        A.unit_hi[u] = hp.unit_hi[u];
+    }
     A.a_words = hp.a_words;
     A.b_words = hp.b_words;
     for (int k = 0; k < n_opts; k++) {
