@@ -61,8 +61,13 @@ def assert_table_close(got, ref, G, where=""):
         tol = 1e-5 * np.abs(r)
         bad = np.abs(g - r) > tol
         assert not bad.any(), f"{where} {key}: {np.argwhere(bad)[:5]} {g[bad][:5]} vs {r[bad][:5]}"
+    # entropy bound (Sec. III-F): the kernel sums L(h) = h log2 h from a table
+    # rounded to 2^-22 bits, one term for L(n) and one per non-empty bin, and a
+    # group of n elements has at most n non-empty bins: |error| <= (n + 1) 2^-23
+    # bits, plus the FP64 rounding of the oracle's own sum
     g, r = got["hbits"], ref["hbits"]
-    bad = np.abs(g - r) > 1e-5 * np.abs(r) + 2.0 ** -20
+    bound = (ref["cnt"].astype(np.float64)[:, None] + 1.0) * 2.0 ** -23 + 1e-12 * np.abs(r) + 1e-9
+    bad = np.abs(g - r) > bound
     assert not bad.any(), f"{where} hbits: {np.argwhere(bad)[:5]} {g[bad][:5]} vs {r[bad][:5]}"
 
 
