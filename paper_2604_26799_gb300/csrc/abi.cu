@@ -143,7 +143,7 @@ mgs_status run_cost(mgs_ctx *ctx, CostLaunch &launch, cudaStream_t st) {
     int cfg = pick_config(ctx, launch.group_size, launch.n_bits);
     CostSeg *d_segs = nullptr;
     unsigned int *d_counter = nullptr;
-    size_t seg_bytes = align256(sizeof(CostSeg) * std::max<size_t>(launch.segs.size(), 1));
+    size_t seg_bytes = align256(sizeof(CostSeg) * std::max<size_t>(launch.segs.size(), 1) * kMaxSpatialBuckets);
     void *scratch = nullptr;
     MGS_CUDA_TRY(dev_malloc_async(&scratch, seg_bytes + 256, st));
     d_segs = static_cast<CostSeg *>(scratch);
@@ -574,7 +574,7 @@ mgs_status mgs_build_cost_table_probe(mgs_ctx *ctx, const mgs_scene *scene, cons
         launch.probe_hist = hist;
         launch.probe_codes = codes;
         CostSeg *d_segs = nullptr;
-        size_t seg_bytes = align256(sizeof(CostSeg) * std::max<size_t>(launch.segs.size(), 1));
+        size_t seg_bytes = align256(sizeof(CostSeg) * std::max<size_t>(launch.segs.size(), 1) * kMaxSpatialBuckets);
         void *scratch = nullptr;
         MGS_CUDA_TRY(dev_malloc_async(&scratch, seg_bytes + 256, st));
         d_segs = static_cast<CostSeg *>(scratch);
@@ -759,7 +759,7 @@ mgs_status mgs_autotune(mgs_ctx *ctx, const mgs_scene *scene, const mgs_grid *gr
     std::vector<CostSeg> segs;
     mgs_status s = scene_segments(sc, grid, table, st, &segs);
     const int nc = cost_config_count();
-    size_t seg_bytes = align256(sizeof(CostSeg) * std::max<size_t>(segs.size(), 1));
+    size_t seg_bytes = align256(sizeof(CostSeg) * std::max<size_t>(segs.size(), 1) * kMaxSpatialBuckets);
     if (s == MGS_OK && dev_malloc_async(&scratch, seg_bytes + 256, st) != cudaSuccess) {
         set_error("autotune scratch allocation failed");
         s = MGS_ERR_OUT_OF_MEMORY;

@@ -141,6 +141,10 @@ struct CostSeg {
     float *vmax;
 };
 
+// A launch's segments are cut into at most this many runs of groups each
+// (Morton-range buckets; see cost_exec_create): size segment scratch for it.
+constexpr int kMaxSpatialBuckets = 64;
+
 struct CostLaunch {
     std::vector<CostSeg> segs;
     int32_t group_size = 0;
