@@ -60,7 +60,7 @@ def load(path: str):
     L.oracle_euler.argtypes = [P, P]
     L.oracle_euler.restype = None
     L.oracle_preprocess.argtypes = [P, i64, i32, P, ctypes.c_double, P, P, P]
-    L.oracle_raht.argtypes = [P, i64, i32, P, i32, i32, P, i64, P, P, P, P]
+    L.oracle_raht.argtypes = [P, i64, i32, P, i32, i32, P, i64, P, P, P, P, P]
     L.oracle_rans_lanes.argtypes = [i64]
     L.oracle_rans_lanes.restype = i32
     L.oracle_block_bound.argtypes = [i64, i32]
@@ -208,10 +208,13 @@ def preprocess(attrs, view_importance, beta: float, L=None):
     return out, ig, float(vq[0])
 
 
-def raht(attrs, channels, depth: int, L=None, weights: bool = False, importance=None, keep: int = 0):
+def raht(attrs, channels, depth: int, L=None, weights: bool = False, importance=None, keep: int = 0,
+         ranges: bool = False):
     """(DC [n_c], AC [V - 1, n_c], V) of the RAHT of `channels` at octree depth `depth`
-    (FP64); with weights=True also the merge weight w1 + w2 of every AC.  keep > 0
-    transforms the kept set of the `keep` most important Gaussians only."""
+    (FP64); with weights=True also the merge weight w1 + w2 of every AC, and with
+    ranges=True (after the weights) the largest |value| of a Gaussian under each AC's
+    merged node [V - 1, n_c].  keep > 0 transforms the kept set of the `keep` most
+    important Gaussians only."""
     a = np.ascontiguousarray(attrs, dtype=np.float32)
     imp = None if importance is None else np.ascontiguousarray(importance, dtype=np.float32)
     ch = np.ascontiguousarray(channels, dtype=np.int32)
@@ -219,12 +222,18 @@ def raht(attrs, channels, depth: int, L=None, weights: bool = False, importance=
     dc = np.empty(ch.shape[0])
     ac = np.empty((max(n - 1, 1), ch.shape[0]))
     aw = np.empty(max(n - 1, 1), dtype=np.int64)
+    ar = np.empty((max(n - 1, 1), ch.shape[0])) if ranges else None
     nv = np.empty(1, dtype=np.int64)
     _check((L or lib()).oracle_raht(_p(a), n, C, _p(ch), ch.shape[0], int(depth),
                                     _p(imp) if imp is not None else None, int(keep), _p(dc), _p(ac), _p(aw),
-                                    _p(nv)))
+                                    _p(ar) if ranges else None, _p(nv)))
     V = int(nv[0])
-    return (dc, ac[:V - 1], V, aw[:V - 1]) if weights else (dc, ac[:V - 1], V)
+    out = (dc, ac[:V - 1], V)
+    if weights:
+        out += (aw[:V - 1],)
+    if ranges:
+        out += (ar[:V - 1],)
+    return out
 
 
 def rans_lanes(n: int, L=None) -> int:

@@ -641,10 +641,12 @@ int oracle_preprocess(const float *attrs, int64_t n, int32_t n_channels, const f
  * `keep` most important (importance [n]), with the whole scene's Morton
  * reading.  dc_out [n_c]; ac_out [(n - 1)][n_c] (capacity); ac_w_out
  * [(n - 1)] (may be NULL) the weight w1 + w2 of each AC's merge;
- * *n_vox_out = V.  FP64. */
+ * ac_range_out [(n - 1)][n_c] (may be NULL) the largest |value| of a Gaussian
+ * under each AC's merged node, per channel (the scale its rounding errors
+ * follow); *n_vox_out = V.  FP64. */
 int oracle_raht(const float *attrs, int64_t n, int32_t n_channels, const int32_t *chan, int32_t n_c,
                 int32_t depth, const float *importance, int64_t keep, double *dc_out, double *ac_out,
-                int64_t *ac_w_out, int64_t *n_vox_out) {
+                int64_t *ac_w_out, double *ac_range_out, int64_t *n_vox_out) {
     if (n < 1 || n_c < 1 || depth < 1 || depth > 21 || keep < 0 || keep > n) return ORACLE_ERR_ARG;
     if (keep > 0 && keep < n && !importance) return ORACLE_ERR_ARG;
     for (int32_t k = 0; k < n_c; k++)
@@ -656,8 +658,9 @@ int oracle_raht(const float *attrs, int64_t n, int32_t n_channels, const int32_t
     double *x = (double *)malloc(sizeof(double) * (size_t)n * (size_t)n_c);
     int64_t *pos = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
     int32_t *rank = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
-    if (!code || !order || !key || !w || !x || !pos || !rank) {
-        free(code); free(order); free(key); free(w); free(x); free(pos); free(rank);
+    double *xr = (double *)malloc(sizeof(double) * (size_t)n * (size_t)n_c);   /* node's largest |value| */
+    if (!code || !order || !key || !w || !x || !pos || !rank || !xr) {
+        free(code); free(order); free(key); free(w); free(x); free(pos); free(rank); free(xr);
         return ORACLE_ERR_NOMEM;
     }
     int rc = oracle_morton(attrs, n, n_channels, code, order);
@@ -679,9 +682,14 @@ int oracle_raht(const float *attrs, int64_t n, int32_t n_channels, const int32_t
         int64_t q = p;
         while (q < K && (code[order[pos[q]]] >> shift) == vc) q++;
         for (int32_t k = 0; k < n_c; k++) {
-            double sum = 0.0;
-            for (int64_t t = p; t < q; t++) sum += (double)attrs[order[pos[t]] * n_channels + chan[k]];
+            double sum = 0.0, big = 0.0;
+            for (int64_t t = p; t < q; t++) {
+                const double v = (double)attrs[order[pos[t]] * n_channels + chan[k]];
+                sum += v;
+                big = fabs(v) > big ? fabs(v) : big;
+            }
             x[m * n_c + k] = q - p > 1 ? sum / (double)(q - p) : sum;
+            xr[m * n_c + k] = big;
         }
         key[m] = vc;
         w[m] = 1;
@@ -703,8 +711,12 @@ int oracle_raht(const float *attrs, int64_t n, int32_t n_channels, const int32_t
                     double x1 = x[i * n_c + k], x2 = x[(i + 1) * n_c + k];
                     double dc = t1 * x1 + t2 * x2;
                     double ac = t1 * x2 - t2 * x1;
+                    double r1 = xr[i * n_c + k], r2 = xr[(i + 1) * n_c + k];
+                    double r = r1 > r2 ? r1 : r2;
                     ac_out[n_ac * n_c + k] = ac;
+                    if (ac_range_out) ac_range_out[n_ac * n_c + k] = r;
                     x[out * n_c + k] = dc;
+                    xr[out * n_c + k] = r;
                 }
                 if (ac_w_out) ac_w_out[n_ac] = w[i] + w[i + 1];
                 n_ac++;
@@ -713,7 +725,10 @@ int oracle_raht(const float *attrs, int64_t n, int32_t n_channels, const int32_t
                 out++;
                 i += 2;
             } else {
-                for (int32_t k = 0; k < n_c; k++) x[out * n_c + k] = x[i * n_c + k];
+                for (int32_t k = 0; k < n_c; k++) {
+                    x[out * n_c + k] = x[i * n_c + k];
+                    xr[out * n_c + k] = xr[i * n_c + k];
+                }
                 w[out] = w[i];
                 key[out] = key[i] >> 1;
                 out++;
@@ -728,7 +743,7 @@ int oracle_raht(const float *attrs, int64_t n, int32_t n_channels, const int32_t
     }
     for (int32_t k = 0; k < n_c; k++) dc_out[k] = x[k];
 done:
-    free(code); free(order); free(key); free(w); free(x); free(pos); free(rank);
+    free(code); free(order); free(key); free(w); free(x); free(pos); free(rank); free(xr);
     return rc;
 }
 

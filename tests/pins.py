@@ -281,6 +281,41 @@ def check_raht_example(L):
     assert math.isclose(dc[0], 7.0 / math.sqrt(3.0), rel_tol=1e-14)
 
 
+def check_raht_ranges(L, seed: int = 11, n: int = 2500):
+    """The largest |value| under each AC's node: the hand example gives 2 for the
+    first merge and 4 for the root; in general it is the largest |x| of the
+    Gaussians in the voxels the node covers (a Morton-contiguous run of voxels,
+    found here by brute force from the voxel codes), and every AC lies within
+    sqrt(w) of it (DC^2 + AC^2 of a node is at most w times its largest |mean|^2)."""
+    a = np.zeros((3, 4), np.float32)
+    a[:, :3] = [[0, 0, 0], [1, 0, 0], [0, 1, 0]]
+    a[:, 3] = [1.0, -2.0, 4.0]
+    dc, ac, V, w, r = oracle.raht(a, [3], 1, L=L, weights=True, ranges=True)
+    assert V == 3 and list(w) == [2, 3] and list(r[:, 0]) == [2.0, 4.0]
+    rng = np.random.default_rng(seed)
+    a = rng.uniform(0, 1, (n, 5)).astype(np.float32)
+    a[:, 3:] = (rng.standard_normal((n, 2)) * rng.uniform(0.1, 10, (n, 1))).astype(np.float32)
+    depth = 5
+    dc, ac, V, w, r = oracle.raht(a, [3, 4], depth, L=L, weights=True, ranges=True)
+    assert np.all(np.abs(ac) <= np.sqrt(w)[:, None] * r * (1 + 1e-12))
+    codes, order = oracle.morton(a, L=L)
+    vc = (codes[order] >> np.uint64(3 * (21 - depth))).astype(np.uint64)
+    uniq = np.unique(vc)
+    big = np.zeros((len(uniq), 2))
+    np.maximum.at(big, np.searchsorted(uniq, vc), np.abs(a[order][:, 3:5].astype(np.float64)))
+    # node of a merge at step s: voxels whose codes agree above bit s; its range is
+    # the largest |x| over them.  The oracle lists ACs step by step in ascending code.
+    expect = []
+    for s_ in range(3 * depth):
+        prefix = uniq >> np.uint64(s_ + 1)
+        cur = uniq >> np.uint64(s_)
+        for p in np.unique(prefix):
+            sel = prefix == p
+            if len(np.unique(cur[sel])) == 2:
+                expect.append(big[sel].max(axis=0))
+    assert np.array_equal(np.array(expect), r)
+
+
 def voxel_means(attrs, channels, depth, L):
     """Voxel codes and FP64 means, from the Morton codes and numpy grouping."""
     codes, order = oracle.morton(attrs, L=L)

@@ -193,6 +193,10 @@ def test_raht_worked_example():
     pins.check_raht_example(oracle.lib())
 
 
+def test_raht_ranges():
+    pins.check_raht_ranges(oracle.lib())
+
+
 def test_raht_orthonormal():
     pins.check_raht_orthonormal(oracle.lib())
 
