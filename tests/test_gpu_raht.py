@@ -1,8 +1,9 @@
 """RAHT (Sec. III-D) on the GPU against the FP64 oracle: the voxel count is
 exact; the DC and every AC agree within the FP32 rounding of a chain of
 orthonormal merges -- a few ulp per level of the size sqrt(w) * |x| of the
-node a coefficient comes from (w the merge weight the oracle reports, |x| the
-channel's largest magnitude); edge cases; full-size parity (needs a GB300)."""
+node a coefficient comes from (w the merge weight, |x| the largest magnitude
+of a Gaussian under that node, both reported by the oracle per coefficient);
+edge cases; full-size parity (needs a GB300)."""
 import math
 
 import numpy as np
@@ -43,12 +44,14 @@ def gpu_raht(ctx, attrs, channels, depth, imp=None, keep=0):
 
 def close(gpu, attrs, channels, depth, imp=None, keep=0):
     dc, ac, V = gpu
-    rdc, rac, rV, rw = oracle.raht(attrs, channels, depth, weights=True, importance=imp, keep=keep)
+    rdc, rac, rV, rw, rr = oracle.raht(attrs, channels, depth, weights=True, importance=imp, keep=keep,
+                                        ranges=True)
     assert V == rV and ac.shape == rac.shape
     S = np.abs(attrs[:, channels]).max(axis=0).astype(np.float64)      # |x| bound per channel
     tol = 3 * depth * 2.5e-7 + 1e-6                                     # ulp-scale per level
     assert np.all(np.abs(dc - rdc) <= tol * math.sqrt(V) * S + 1e-30)
-    bound = tol * np.sqrt(rw.astype(np.float64))[:, None] * S[None, :]
+    # each AC against the magnitude under its own node, not the channel's
+    bound = tol * np.sqrt(rw.astype(np.float64))[:, None] * rr
     bad = np.argwhere(np.abs(ac.astype(np.float64) - rac) > bound)
     assert bad.size == 0, [(int(i), int(c), float(ac[i, c]), float(rac[i, c]), float(bound[i, c])) for i, c in bad[:5]]
 
