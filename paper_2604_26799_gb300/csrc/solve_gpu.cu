@@ -319,7 +319,11 @@ struct SolveArgs {
     double *chunk_sum;                  // per chunk: tree sum of the losses
     uint8_t *level_all;                 // [budget][NI]
     uint8_t *choice_all;                // [budget][NI]
+    uint64_t *next_key_all;             // [budget][NI] key of each item's next increment
+    int64_t *next_dw_all;               // [budget][NI] its rate (kNoIncrement: none left)
 };
+
+constexpr int64_t kNoIncrement = INT64_MAX;   // never fits a capacity
 
 struct ProbView {
     int64_t i0, M;
@@ -550,8 +554,13 @@ __global__ void __launch_bounds__(kSolveThreads, 1) k_order_apply(SolveArgs A) {
     }
     double d = 0.0;
     if (i < v.M) {
-        A.level_all[(int64_t)A.pin[ch.p].budget * A.H.NI + v.i0 + i] = (uint8_t)t.lvl;
+        const int64_t o = (int64_t)A.pin[ch.p].budget * A.H.NI + v.i0 + i;
+        A.level_all[o] = (uint8_t)t.lvl;
         d = A.H.d[t.lvl * A.H.NI + v.i0 + i];
+        // the item's next increment, for the greedy completion's passes
+        const bool more = t.lvl + 1 < t.n;
+        A.next_key_all[o] = more ? key_of(A.H, v.i0, i, t.lvl) : 0ull;
+        A.next_dw_all[o] = more ? dw_of(A.H, v.i0, i, t.lvl) : kNoIncrement;
     }
     const double tsum = block_tree_sum(d, sc);
     const int64_t taken = block_sum_i64(my_taken, sc);
@@ -573,12 +582,34 @@ __global__ void __launch_bounds__(kSolveThreads, 1) k_greedy(SolveArgs A) {
     if (st.target < 0) return;
     const ProbView v = prob_view(A, p);
     const int c0 = A.chunk0[p], c1 = A.chunk0[p + 1];
+    // the chunks' sums, added in chunk order by one thread (the loads in parallel)
+    __shared__ double s_cs[kSolveThreads];
+    __shared__ int64_t s_ct[kSolveThreads];
+    __shared__ double s_dsplit;
+    __shared__ int64_t s_taken;
     double d_split = 0.0;
     int64_t taken = 0;
-    for (int c = c0; c < c1; c++) {   // every thread, in chunk order
-        d_split = d_split + A.chunk_sum[c];
-        taken += A.chunk_taken[c];
+    for (int b = c0; b < c1; b += kSolveThreads) {
+        const int c = b + threadIdx.x;
+        if (c < c1) {
+            s_cs[threadIdx.x] = A.chunk_sum[c];
+            s_ct[threadIdx.x] = A.chunk_taken[c];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int j = 0; j < min(kSolveThreads, c1 - b); j++) {
+                d_split = d_split + s_cs[j];
+                taken += s_ct[j];
+            }
+        __syncthreads();
     }
+    if (threadIdx.x == 0) {
+        s_dsplit = d_split;
+        s_taken = taken;
+    }
+    __syncthreads();
+    d_split = s_dsplit;
+    taken = s_taken;
     int64_t rem = st.res - taken;
     double lp = d_split;
     if (st.split_item >= 0) {
@@ -588,7 +619,10 @@ __global__ void __launch_bounds__(kSolveThreads, 1) k_greedy(SolveArgs A) {
         const double dd = A.H.d[sl * A.H.NI + v.i0 + si] - A.H.d[(sl + 1) * A.H.NI + v.i0 + si];
         if (frac > 0) lp = lp - frac * dd;
     }
-    uint8_t *level = A.level_all + (int64_t)A.pin[p].budget * A.H.NI + v.i0;
+    const int64_t ob = (int64_t)A.pin[p].budget * A.H.NI + v.i0;
+    uint8_t *level = A.level_all + ob;
+    uint64_t *nkey = A.next_key_all + ob;
+    int64_t *ndw = A.next_dw_all + ob;
     IncPos last;
     last.key = 0;
     last.item = -1;
@@ -601,20 +635,25 @@ __global__ void __launch_bounds__(kSolveThreads, 1) k_greedy(SolveArgs A) {
         best.level = 0;
 #pragma unroll 4
         for (int64_t i = threadIdx.x; i < v.M; i += kSolveThreads) {
-            const int lvl = level[i];
-            if (lvl + 1 >= v.nv[i]) continue;
+            const int64_t dw = ndw[i];
+            if (dw > rem) continue;   // none left, or it does not fit
             IncPos c;
-            c.key = key_of(A.H, v.i0, i, lvl);
+            c.key = nkey[i];
             c.item = i;
-            c.level = lvl;
+            c.level = level[i];
             if (last.item >= 0 && !inc_first(last, c)) continue;   // passed over already
-            if (dw_of(A.H, v.i0, i, lvl) > rem) continue;
             if (inc_first(c, best)) best = c;
         }
         const IncPos f = block_first(best, s_warp, &s_first);
         if (f.item < 0) break;
-        if (threadIdx.x == 0) level[f.item] = (uint8_t)(f.level + 1);
         rem -= dw_of(A.H, v.i0, f.item, f.level);
+        if (threadIdx.x == 0) {
+            const int nl = f.level + 1;
+            level[f.item] = (uint8_t)nl;
+            const bool more = nl + 1 < v.nv[f.item];
+            nkey[f.item] = more ? key_of(A.H, v.i0, f.item, nl) : 0ull;
+            ndw[f.item] = more ? dw_of(A.H, v.i0, f.item, nl) : kNoIncrement;
+        }
         last = f;
         takes++;
         __syncthreads();
@@ -762,6 +801,8 @@ extern "C" mgs_status mgs_solve_budgets_device(mgs_ctx *ctx, const void *table,
     const size_t fine_bytes = off - o_fz;
     const size_t o_level = take((size_t)n_budgets * NI);
     const size_t o_choice = take((size_t)n_budgets * NI);
+    const size_t o_nkey = take(sizeof(uint64_t) * n_budgets * NI);
+    const size_t o_ndw = take(sizeof(int64_t) * n_budgets * NI);
     char *ws = nullptr;
     cudaError_t e = dev_malloc_async(reinterpret_cast<void **>(&ws), off, st);
     if (e != cudaSuccess) {
@@ -829,6 +870,8 @@ extern "C" mgs_status mgs_solve_budgets_device(mgs_ctx *ctx, const void *table,
     A.chunk_sum = reinterpret_cast<double *>(ws + o_csum);
     A.level_all = reinterpret_cast<uint8_t *>(ws + o_level);
     A.choice_all = reinterpret_cast<uint8_t *>(ws + o_choice);
+    A.next_key_all = reinterpret_cast<uint64_t *>(ws + o_nkey);
+    A.next_dw_all = reinterpret_cast<int64_t *>(ws + o_ndw);
     const unsigned nc = (unsigned)chunks.size();
     int launches = 1;
     k_split_coarse<<<P, kSolveThreads, 0, st>>>(A);
