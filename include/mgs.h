@@ -184,6 +184,23 @@ int64_t mgs_kernel_launches(void);
 mgs_status mgs_debug_fail_allocation(int64_t nth);
 int64_t mgs_debug_allocations(void);
 
+/*
+ * Inspection of the cost kernel's shared-memory histogram plan for tile
+ * configuration `config` (mgs_tile_config_name) and the bit-widths bits[n_bits]
+ * (ascending, 1..16), for tests of the host logic; host only, no device needed.
+ * Writes at most `capacity` int32 to `out` (may be NULL) and returns how many
+ * the plan has (negative on a bad argument):
+ *   [0] shared memory of a CTA (bytes), [1] the budget for the configuration's
+ *   CTAs per SM, [2] 1 if every large option has its own table, [3] region A
+ *   words, [4] region B words, [5] small options, [6] of them lane tables,
+ *   [7] direct tables, [8] finishing units U;
+ *   then per option k: mode (0 lane, 1 direct, 2 16-bit pairs, 3 8-bit
+ *   counters), word offset (region A for small options, region B for large
+ *   ones when [2] = 1), words, byte-counter windows, 16-bit-pair windows;
+ *   then per unit: option, first bin, end bin.
+ */
+int32_t mgs_debug_cost_plan(int32_t config, int32_t n_bits, const int32_t *bits, int32_t *out, int32_t capacity);
+
 /* ---- scenes ----------------------------------------------------------- */
 
 /*

@@ -714,6 +714,13 @@ mgs_status mgs_build_cost_tables_batched(mgs_ctx *ctx, int32_t n_scenes,
 
 int32_t mgs_tile_config_count(void) { return cost_config_count(); }
 
+int32_t mgs_debug_cost_plan(int32_t config, int32_t n_bits, const int32_t *bits, int32_t *out, int32_t capacity) {
+    clear_error();
+    const int n = mgs::cost_plan_export(config, bits, n_bits, out, capacity);
+    if (n < 0) set_error("no tile configuration %d or bad bit-widths", config);
+    return n;
+}
+
 const char *mgs_tile_config_name(int32_t config) {
     if (config < 0 || config >= cost_config_count()) return "";
     return cost_config(config).name;

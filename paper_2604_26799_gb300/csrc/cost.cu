@@ -49,6 +49,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <vector>
+#include <cstring>
 #include <cfloat>
 
 #include "internal.h"
@@ -1356,6 +1358,27 @@ int cost_default_config(int G) {
     if (G <= 4096) return 9;    // 256 x 16, slab tile in TMEM
     if (G <= 16384) return 6;   // 512 x 32, W 1
     return -1;
+}
+
+int cost_plan_export(int config, const int32_t *bits, int n_opts, int32_t *out, int cap) {
+    if (config < 0 || config >= kNumConfigs || n_opts < 1 || n_opts > MGS_MAX_OPTIONS || !bits) return -1;
+    const HistPlan h = plan_hist(kConfigs[config], bits, n_opts);
+    std::vector<int32_t> v = {(int32_t)h.smem, (int32_t)smem_budget(kConfigs[config].ctas), h.concurrent ? 1 : 0,
+                              h.a_words, h.b_words, h.n_small, h.n_lane, h.n_direct, h.n_units};
+    for (int k = 0; k < n_opts; k++) {
+        v.push_back(h.mode[k]);
+        v.push_back(h.off[k]);
+        v.push_back(h.words[k]);
+        v.push_back(h.windows[k]);
+        v.push_back(h.rwindows[k]);
+    }
+    for (int u = 0; u < h.n_units; u++) {
+        v.push_back(h.unit_opt[u]);
+        v.push_back(h.unit_lo[u]);
+        v.push_back(h.unit_hi[u]);
+    }
+    if (out && cap > 0) std::memcpy(out, v.data(), sizeof(int32_t) * std::min<size_t>(v.size(), (size_t)cap));
+    return (int)v.size();
 }
 
 bool cost_config_has_probe(int config) {

@@ -179,6 +179,8 @@ size_t cost_smem_bytes(int config, int group_size, int n_opts, const int32_t *bi
 bool cost_config_fits(int config, int group_size, int n_opts, const int32_t *bits);
 // The configuration has a probe instantiation.
 bool cost_config_has_probe(int config);
+// The histogram plan of a launch, flattened for inspection (mgs_debug_cost_plan).
+int cost_plan_export(int config, const int32_t *bits, int n_opts, int32_t *out, int cap);
 
 // A prepared launch: work layout, kernel arguments and shape, reusable and
 // capturable (cost_exec_run issues only a memset and a kernel launch).

@@ -116,6 +116,7 @@ _SIGS = {
     "mgs_build_cost_table_plain": [_P, _P, ctypes.POINTER(mgs_grid), _P, _P],
     "mgs_debug_fail_allocation": [ctypes.c_int64],
     "mgs_debug_allocations": [],
+    "mgs_debug_cost_plan": [ctypes.c_int32, ctypes.c_int32, _P, _P, ctypes.c_int32],
     "mgs_vq_set_wait_limit": [_P, ctypes.c_int64],
     "mgs_build_cost_table_probe": [_P, _P, ctypes.POINTER(mgs_grid), _P, _P, ctypes.c_int64, _P,
                                    ctypes.c_int64, _P],
@@ -228,6 +229,24 @@ def mgs_debug_fail_allocation(nth: int):
 
 def mgs_debug_allocations() -> int:
     return int(lib().mgs_debug_allocations())
+
+
+def mgs_debug_cost_plan(config: int, bits) -> dict:
+    """The cost kernel's histogram plan for a tile configuration and bit-widths
+    (host only; tests of the planner)."""
+    b = np.ascontiguousarray(bits, dtype=np.int32)
+    n = lib().mgs_debug_cost_plan(int(config), b.shape[0], b.ctypes.data, None, 0)
+    if n < 0:
+        raise MgsError(-1, lib().mgs_last_error().decode(errors="replace"))
+    out = np.zeros(n, dtype=np.int32)
+    lib().mgs_debug_cost_plan(int(config), b.shape[0], b.ctypes.data, out.ctypes.data, n)
+    k = b.shape[0]
+    per = out[9:9 + 5 * k].reshape(k, 5)
+    units = out[9 + 5 * k:].reshape(-1, 3)
+    return dict(smem=int(out[0]), budget=int(out[1]), concurrent=bool(out[2]), a_words=int(out[3]),
+                b_words=int(out[4]), n_small=int(out[5]), n_lane=int(out[6]), n_direct=int(out[7]),
+                mode=per[:, 0], off=per[:, 1], words=per[:, 2], windows=per[:, 3], rwindows=per[:, 4],
+                units=units)
 
 
 def mgs_vq_set_wait_limit(ctx: int, cycles: int):
