@@ -66,6 +66,8 @@ MUTANTS = {
                            "memcpy(xb + (int64_t)j * D, x + (int64_t)rows[j] * D + 1, sizeof(float) * (D - 1));"),
     "raht_keep_ignored": ("        K = oracle_kept(rank, order, n, keep, pos);",
                           "        for (int64_t t = 0; t < n; t++) pos[t] = t;"),
+    "raht_range_min": ("double r = r1 > r2 ? r1 : r2;", "double r = r1 < r2 ? r1 : r2;"),
+    "raht_range_not_carried": ("                    xr[out * n_c + k] = r;", "                    xr[out * n_c + k] = r1;"),
 }
 
 RUNNER = r"""
@@ -94,6 +96,7 @@ checks = [
     lambda: pins.check_raht_orthonormal(L),
     lambda: pins.check_raht_constant_and_dedup(L),
     lambda: pins.check_raht_keep(L),
+    lambda: pins.check_raht_ranges(L),
     lambda: pins.check_coder_roundtrip(L),
     lambda: pins.check_coder_entropy(L),
     lambda: pins.check_coder_normalisation(L),
