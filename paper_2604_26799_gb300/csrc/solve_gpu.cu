@@ -91,7 +91,20 @@ __global__ void k_hull(TableDev T, HullDev H, int rate_model, int norm, const in
                        unsigned long long *__restrict__ ratio_sums,
                        unsigned long long *__restrict__ hist_w, unsigned *__restrict__ hist_n) {
     __shared__ unsigned long long s_sum[2 * 64];
+    // the block's share of the coarse histograms, gathered in a small open-
+    // addressing table of (ratio, bucket) slots and added to the global
+    // histograms once per distinct slot (integer sums: the order does not matter)
+    constexpr int kSlots = 1024;
+    constexpr unsigned kEmpty = 0xFFFFFFFFu;
+    __shared__ unsigned s_key[kSlots];
+    __shared__ unsigned long long s_w[kSlots];
+    __shared__ unsigned s_n[kSlots];
     for (int k = threadIdx.x; k < 2 * nr; k += blockDim.x) s_sum[k] = 0ull;
+    for (int j = threadIdx.x; j < kSlots; j += blockDim.x) {
+        s_key[j] = kEmpty;
+        s_w[j] = 0ull;
+        s_n[j] = 0u;
+    }
     __syncthreads();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < H.NI) {
@@ -122,8 +135,21 @@ __global__ void k_hull(TableDev T, HullDev H, int rate_model, int norm, const in
             const int64_t dw = hw[l + 1] - hw[l];
             const uint64_t k = inc_key(hd[l] - hd[l + 1], dw);
             H.key[l * H.NI + i] = k;
-            atomicAdd(&hist_w[(size_t)r * kCoarseBins + (k >> 48)], (unsigned long long)dw);
-            atomicAdd(&hist_n[(size_t)r * kCoarseBins + (k >> 48)], 1u);
+            const unsigned key = (unsigned)r * kCoarseBins + (unsigned)(k >> 48);
+            unsigned h = (key * 2654435761u) >> 22;   // 10 bits
+            bool done = false;
+            for (int probe = 0; probe < 32 && !done; probe++, h = (h + 1) & (kSlots - 1)) {
+                const unsigned prev = atomicCAS(&s_key[h], kEmpty, key);
+                if (prev == kEmpty || prev == key) {
+                    atomicAdd(&s_w[h], (unsigned long long)dw);
+                    atomicAdd(&s_n[h], 1u);
+                    done = true;
+                }
+            }
+            if (!done) {   // a crowded table: straight to the global histogram
+                atomicAdd(&hist_w[(size_t)key], (unsigned long long)dw);
+                atomicAdd(&hist_n[(size_t)key], 1u);
+            }
         }
         atomicAdd(&s_sum[2 * r], (unsigned long long)hw[0]);
         atomicAdd(&s_sum[2 * r + 1], (unsigned long long)w[nb - 1]);
@@ -131,6 +157,11 @@ __global__ void k_hull(TableDev T, HullDev H, int rate_model, int norm, const in
     __syncthreads();
     for (int k = threadIdx.x; k < 2 * nr; k += blockDim.x)
         if (s_sum[k]) atomicAdd(&ratio_sums[k], s_sum[k]);
+    for (int j = threadIdx.x; j < kSlots; j += blockDim.x)
+        if (s_key[j] != kEmpty) {
+            atomicAdd(&hist_w[(size_t)s_key[j]], s_w[j]);
+            atomicAdd(&hist_n[(size_t)s_key[j]], s_n[j]);
+        }
 }
 
 // ---- block-wide helpers (blockDim.x == kSolveThreads) ----------------------
