@@ -29,19 +29,22 @@
 // Groups where a precondition fails (subnormal S or u, |Z| >= 2^22) take the
 // literal per-element formula.
 //
-// Histograms live in shared memory.  The bit-widths up to 12 of a channel are
-// counted together, each in its own table of region A, with no barrier between
-// them: per-lane columns for b <= 6 (a warp never hits one address twice) and a
-// direct table for b <= 10 (both summed by a scan once every count is in), and
-// 16-bit counter pairs for b = 11, 12, where the atomic returns the bin's old
-// count h - 1 and the thread adds delta(h) = L(h) - L(h - 1), L(h) = h log2 h in
-// units of 2^-22 bits, so the deltas telescope to sum_bins L(h) with no scan.
-// Larger bit-widths are counted one at a time in region B with 8-bit counters
-// (a quarter of the 16-bit table: b = 16 fits 64 KB), the same telescoping sum
-// and a shared-memory delta table.  A counter that reaches 255 sets an overflow
-// flag, and the bit-width is then counted again exactly with 16-bit pairs (in
-// windows of region B).  Entropy sums are integers, so they do not depend on
-// the order of the updates.
+// Histograms live in shared memory, planned on the host per launch.  The
+// bit-widths up to 12 of a channel are counted together, each in its own table
+// of region A, with no barrier between them: per-lane columns for b <= 6 (a
+// warp never hits one address twice) and a direct table for b <= 10 (both
+// summed once every count is in, in per-warp units of bins), and 16-bit
+// counter pairs for b = 11, 12, where the atomic returns the bin's old count
+// h - 1 and the thread adds delta(h) = L(h) - L(h - 1), L(h) = h log2 h in units
+// of 2^-22 bits, so the deltas telescope to sum_bins L(h) with no scan.  Larger
+// bit-widths take region B with 8-bit counters (a quarter of the 16-bit table:
+// b = 16 fits 64 KB), the same telescoping sum and a shared-memory delta table:
+// each in its own table when they all fit (then a channel needs two barriers),
+// else one at a time.  A counter that reaches 255 sets an overflow flag, and
+// the bit-width is then counted again exactly with 16-bit pairs (in windows of
+// region B).  Entropy sums are integers, so they do not depend on the order of
+// the updates.  Parameters of every (channel, bit-width) are computed once per
+// item, and the quotients u by one correctly rounded division per element.
 //
 // A probe instantiation of the kernel also writes every code and every bin of
 // every histogram to caller memory (test and inspection only).
